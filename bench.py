@@ -1,0 +1,408 @@
+#!/usr/bin/env python
+"""Benchmark of one DABA iteration (Algorithm 1, arXiv 2305.07026) on the B300.
+
+Metric: observation-updates/s per DABA iteration = nnz * iterations / seconds, for the
+FP32/FP64 mixed path (the value) next to the plain FP64 path, with the mixed path's
+objective checked against the FP64 path's (it must reach it within 1e-5 relative).
+
+Workload (default): the city-scale synthetic "tourism" scene -- 10k cameras, 4M landmarks,
+~26M observations with power-law tracks, Huber loss delta = 1 px -- standing in for the
+large BAL/1DSfM problems of the paper's Sec. 7, which are not available here.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+With N > 1 (torchrun, one rank per GPU) every rank runs an independent replica of the
+workload (the single-GPU method does not shard: replicas only); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "observation-updates/s per DABA iteration, mixed vs FP64 GPU path at 1e-5 rel obj"
+UNIT = "obs-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tourism")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--fp64-steps", type=int, default=None, help="iterations of the FP64 comparison run")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_scene(args, rank, world):
+    from paper_2305_07026_b300 import scenes
+    if world == 1:
+        return scenes.make_scene(args.workload, scale=args.scale)
+    path = os.path.join(tempfile.gettempdir(), f"daba_bench_{args.workload}_{args.scale}.npz")
+    if rank == 0:
+        sc = scenes.make_scene(args.workload, scale=args.scale)
+        np.savez(path + ".tmp.npz", **{k: getattr(sc, k) for k in
+                                       ("cams", "lms", "cam_idx", "lm_idx", "uv", "cams_gt", "lms_gt")},
+                 meta=json.dumps({"name": sc.name, "loss": sc.loss, "loss_scale_px": sc.loss_scale_px,
+                                  "iters": sc.iters, "seed": sc.seed}))
+        os.replace(path + ".tmp.npz", path)
+    barrier(world)
+    if rank != 0:
+        z = np.load(path)
+        meta = json.loads(str(z["meta"]))
+        sc = scenes.Scene(name=meta["name"], cams=z["cams"], lms=z["lms"], cam_idx=z["cam_idx"],
+                          lm_idx=z["lm_idx"], uv=z["uv"], cams_gt=z["cams_gt"], lms_gt=z["lms_gt"],
+                          loss=meta["loss"], loss_scale_px=meta["loss_scale_px"], iters=meta["iters"],
+                          seed=meta["seed"])
+    return sc
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.path = os.path.join(tempfile.gettempdir(), f"daba_clocks_{os.getpid()}.csv")
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or p[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(p[1].split()[0]))
+                mx.append(float(p[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per launch (each datum once) of the iteration kernels
+# ----------------------------------------------------------------------------
+
+def algorithmic_bytes(sc, prec):
+    """Bytes a kernel must move at least once per launch (see the design notes)."""
+    R = 4 if prec == "mixed" else 8
+    nnz, N, M = sc.nnz, sc.N, sc.M
+    deg = np.bincount(sc.cam_idx, minlength=M)
+    n_chunks = int(np.sum((deg + 1023) // 1024))
+    pack = M * 48 * R
+    # camera-sorted pass: landmark index + pixel per observation, landmark position and
+    # displacement once, camera pack once, FP64 partial statistics per chunk
+    cpass = nnz * (4 + 2 * R) + N * 6 * R + pack + n_chunks * 80 * 8
+    # landmark-sorted pass: camera index + pixel + slot per observation, landmark record
+    # (+ low parts in MIXED) read and written, restart flag, CSR offsets, camera pack
+    lrec = 8 * R + (16 if prec == "mixed" else 0)
+    lpass = nnz * (4 + 2 * R + 2) + N * (2 * lrec + 1 + 4) + pack + (0 if prec == "mixed" else N * 16)
+    return {"cpass": cpass, "lpass": lpass}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, if any."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the workload
+# ----------------------------------------------------------------------------
+
+def sub_problem(sc, frac_obs, seed=0):
+    """Observations of a random subset of cameras holding about frac_obs of the observations."""
+    rng = np.random.default_rng(seed)
+    deg = np.bincount(sc.cam_idx, minlength=sc.M)
+    order = rng.permutation(sc.M)
+    take = order[: max(1, int(np.searchsorted(np.cumsum(deg[order]), frac_obs * sc.nnz)) + 1)]
+    mask = np.isin(sc.cam_idx, take)
+    ci, li = sc.cam_idx[mask], sc.lm_idx[mask]
+    cu, ci_r = np.unique(ci, return_inverse=True)
+    lu, li_r = np.unique(li, return_inverse=True)
+    return sc.cams[cu], sc.lms[lu], ci_r.astype(np.int32), li_r.astype(np.int32), sc.uv[mask]
+
+
+def cpu_oracle(sc, target_seconds, steps=None, warmup=0):
+    """Times oracle iterations on a sample sized for ~target_seconds; returns (value, info)."""
+    from threadpoolctl import threadpool_limits
+    from oracle import daba_oracle as O
+    with threadpool_limits(limits=1):
+        # calibrate: ~7 us per observation-iteration on one core; sample for the budget
+        per_obs = 8e-6
+        n_steps = steps if steps is not None else 3
+        frac = min(1.0, target_seconds / (per_obs * n_steps * sc.nnz))
+        cams, lms, ci, li, uv = sub_problem(sc, frac)
+        opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, pixel_scale=O.median_focal(sc.cams))
+        prob, R, t, d, l = O.make_problem(cams, lms, ci, li, uv, opts)
+        st = O.init_state(prob, R, t, d, l)
+        for _ in range(warmup):
+            st, _ = O.step(prob, st)
+        t0 = time.perf_counter()
+        for _ in range(n_steps):
+            st, _ = O.step(prob, st)
+        dt = time.perf_counter() - t0
+    value = ci.size * n_steps / dt
+    return value, {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+                   "sample": f"{ci.size} observations of {cams.shape[0]} randomly chosen cameras of the "
+                             f"{sc.name} workload ({lms.shape[0]} landmarks), {n_steps} oracle iterations "
+                             f"(FP64 numpy, 1 thread), {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2305_07026_b300 import build
+    build.build()
+    from paper_2305_07026_b300 import _lib as L
+
+    torch.cuda.set_device(local)
+    sc = load_scene(args, rank, world)
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    def make(prec):
+        d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv, stream=sp)
+        d.set_state(sc.cams, sc.lms, stream=sp)
+        return d
+
+    # ---- timed region: K iterations of the mixed path, inputs resident in HBM
+    d = make("mixed")
+    if W:
+        d.run(W, stream=sp)
+    d.set_timing(True)
+    clocks = Clocks()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.run(K, stream=sp)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop(local)
+    ms = e0.elapsed_time(e1)
+    kern_ms = d.get_timing()          # summed over the K iterations
+    launches = d.last_launch_count()
+    d.set_timing(False)
+    ms_max = max_over_ranks(ms, world)
+    value = world * sc.nnz * K / (ms_max / 1e3)
+
+    # ---- FP64 path and accuracy: both paths from x^0, mixed must reach FP64's final objective
+    Kf = args.fp64_steps if args.fp64_steps is not None else K
+    d64 = make("fp64")
+    tr64 = np.zeros(Kf + 1)
+    e0.record(stream)
+    d64.run(Kf, tr64, stream=sp)
+    e1.record(stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    d64.close()
+    dm = make("mixed")
+    trm = np.zeros(Kf + 1)
+    dm.run(Kf, trm, stream=sp)
+    dm.close()
+    target = tr64[-1] * (1 + 1e-5)
+    reach = np.flatnonzero(trm <= target)
+    accuracy = {"iters": Kf, "fp64_final_px2": float(tr64[-1]), "mixed_final_px2": float(trm[-1]),
+                "mixed_best_px2": float(trm.min()),
+                "mixed_rel_to_fp64": float((trm[-1] - tr64[-1]) / tr64[-1]),
+                "mixed_reaches_fp64_within_1e-5": bool(reach.size > 0),
+                "mixed_iters_to_reach": int(reach[0]) if reach.size else None,
+                "initial_px2": float(tr64[0])}
+    fp64_value = sc.nnz * Kf / (ms64 / 1e3)
+
+    # ---- roofline of the dominant kernel (per launch, live CUDA events)
+    names = ["cam_prepare", "cpass", "lpass", "camsolve", "finalize"]
+    per_launch_ms = {n: kern_ms[i] / K for i, n in enumerate(names)}
+    dom = max(("cpass", "lpass"), key=lambda n: per_launch_ms[n])
+    alg = algorithmic_bytes(sc, "mixed")[dom]
+    pk = peaks()
+    peak_gbs = pk["hbm_gbs"] if pk else 6400.0
+    achieved = alg / (per_launch_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved / peak_gbs, "traffic": committed_traffic(dom, args.workload),
+                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms[dom],
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s"}
+
+    # ---- end to end through the public API with host buffers: per step the iterate goes
+    # host -> device (daba_set_state), one iteration runs, the objective and the iterate
+    # come back to host (daba_run trace + daba_get_state)
+    Ke = args.e2e_steps
+    cams_h = torch.from_numpy(sc.cams.copy()).pin_memory()
+    lms_h = torch.from_numpy(sc.lms.copy()).pin_memory()
+    tr_h = torch.zeros(2, dtype=torch.float64).pin_memory()
+    de = make("mixed")
+    de.run(1, stream=sp)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        de.set_state(cams_h, lms_h, stream=sp)
+        de.run(1, tr_h, stream=sp)
+        de.get_state(cams_h, lms_h, stream=sp)
+    torch.cuda.synchronize()
+    te = max_over_ranks(time.perf_counter() - t0, world)
+    de.close()
+    e2e = {"value": world * sc.nnz * Ke / te, "unit": UNIT, "steps": Ke,
+           "h2d_bytes_per_step": int(cams_h.numel() * 8 + lms_h.numel() * 8),
+           "d2h_bytes_per_step": int(cams_h.numel() * 8 + lms_h.numel() * 8 + tr_h.numel() * 8),
+           "what": "per step: daba_set_state from pinned host, one iteration, objective and iterate "
+                   "back to pinned host (observations set once beforehand)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        _, cpu = cpu_oracle(sc, args.cpu_seconds)
+
+    d.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 per observation, f64 reductions/solves", "data": "synthetic",
+        "config": {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
+                               f"power-law tracks, {sc.loss} loss {sc.loss_scale_px} px",
+                   "M": sc.M, "N": sc.N, "nnz": sc.nnz, "prec": "mixed", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (working set > 1 GB vs 126 MB L2), no flush"},
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / Kf,
+                      "mixed_speedup": value / world / fp64_value},
+        "accuracy": accuracy,
+        "kernel_ms_per_launch": per_launch_ms,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": ck,
+    }
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle timed on the host cores on a bounded sample of the same workload."""
+    if rank != 0:
+        return None
+    from paper_2305_07026_b300 import scenes
+    sc = scenes.make_scene(args.workload, scale=args.scale)
+    per_step = max(0.2, min(1.5, 150.0 / max(1, args.steps + args.warmup)))
+    value, info = cpu_oracle(sc, per_step * args.steps, steps=args.steps, warmup=args.warmup)
+    info["value"] = value
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
+                               f"power-law tracks, {sc.loss} loss {sc.loss_scale_px} px",
+                   "M": sc.M, "N": sc.N, "nnz": sc.nnz, "prec": "fp64 (oracle)"},
+        "cpu_baseline": info,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * daba.h -- C ABI of the B300 (sm_103a) implementation of one accelerated
+ * majorization-minimization iteration of DABA (Decentralized and Accelerated
+ * Bundle Adjustment, arXiv 2305.07026) and the loop of Algorithm 1 around it.
+ *
+ * Problem (Sec. 2, Problem 1): minimise F(x) = sum_{(i,j) in E} rho(|e_ij|^2)/2
+ * over cameras c_i = (R_i, t_i, d_i) and landmarks l_j, with the reprojection
+ * error e_ij of Sec. 3 (Eq. error) and a robust loss rho satisfying
+ * Assumption 1 (App. B). Each call below is one piece of Algorithm 1 (Sec. 6):
+ * every camera and every landmark is its own block, so every reprojection pair
+ * is split by the majorizer of Proposition 1 into P_ij(c_i|x^k) + Q_ij(l_j|x^k)
+ * (Eq. Ealpha with E' empty), the blocks are solved independently (Eqs.
+ * update_amm / update_mm), and Nesterov extrapolation (Eq. nesterov_x) runs
+ * with the per-block adaptive restart of Sec. 5 (Eqs. DEalpha-Eak).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are caller-owned. Unless stated otherwise an array argument may be
+ *    host memory or device memory of the context's GPU; the library detects
+ *    which with cudaPointerGetAttributes and copies host arrays through its own
+ *    device buffers (pageable or pinned host memory both work).
+ *  - All GPU work is ordered on the cudaStream_t passed as `stream` (NULL means
+ *    the legacy default stream). Calls return after the work is enqueued, except
+ *    where a host output is written, which waits for that stream.
+ *  - Errors are returned as daba_status; a failing call leaves the iterate,
+ *    the restart metrics and the observations unchanged, and
+ *    daba_last_error() returns a one-line reason. No exception crosses the ABI.
+ *  - A context is not thread-safe; use one per host thread.
+ *
+ * Units. Pixels are measured from the principal point. Internally every pixel
+ * quantity is divided by s_norm (options.pixel_scale, 0 = median focal length
+ * of the first state set): an exact reparameterisation, so objective values
+ * returned by the library are in pixel^2.
+ */
+#ifndef DABA_H_
+#define DABA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DABA_OK = 0,
+  DABA_ERR_ARG = 1,         /* invalid size, option or null pointer */
+  DABA_ERR_INDEX = 2,       /* observation index out of range */
+  DABA_ERR_DEGENERATE = 3,  /* |l_j - t_i| <= epsilon for an observed pair (Assumption 2) */
+  DABA_ERR_NONFINITE = 4,   /* non-finite input value, or the iterate became non-finite */
+  DABA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+  DABA_ERR_OOM = 6,         /* device allocation failed */
+  DABA_ERR_STATE = 7        /* call out of order (e.g. run before observations and state are set) */
+} daba_status;
+
+/* Robust losses of Assumption 1 (App. B); `loss_scale_px` is c below, in pixels.
+ * TRIVIAL rho(s)=s; HUBER s if s<=c^2 else 2c sqrt(s)-c^2; CAUCHY c^2 log(1+s/c^2);
+ * WELSCH c^2 (1-exp(-s/c^2)). */
+typedef enum { DABA_LOSS_TRIVIAL = 0, DABA_LOSS_HUBER = 1, DABA_LOSS_CAUCHY = 2, DABA_LOSS_WELSCH = 3 } daba_loss;
+
+/* DABA_FP64: every per-observation quantity in FP64.
+ * DABA_MIXED: per-observation residuals, weights and majorizer terms in FP32; the
+ * per-camera normal-matrix accumulation across warps, the restart metrics, the
+ * camera subproblem solve and the rotation projection in FP64. */
+typedef enum { DABA_FP64 = 0, DABA_MIXED = 1 } daba_precision;
+
+typedef struct {
+  daba_loss loss;
+  double loss_scale_px;   /* loss scale c in pixels (ignored for TRIVIAL) */
+  double xi;              /* proximal weight xi > 0 of Eq. Ealpha, internal units (default 1e-10) */
+  double eta;             /* 0 < eta <= 1 of Eq. lFak (default 0.5) */
+  int accelerated;        /* 1: DABA (Algorithm 1); 0: DUBA, always the MM update (Sec. 7.2) */
+  int cam_alternations;   /* R-step / (t,d)-step alternations of the camera block solve (default 2) */
+  double pixel_scale;     /* s_norm in pixels; 0 = median focal length of the first state set */
+  daba_precision prec;
+} daba_options;
+
+typedef struct daba_ctx daba_ctx;
+
+/* Fills `opt` with the defaults listed above (Huber, c = 1 px, MIXED). */
+void daba_default_options(daba_options* opt);
+
+/* Creates a context for M cameras, N landmarks and nnz observations and allocates
+ * all device memory it will use (O(M + N + nnz)) on the current CUDA device.
+ * M >= 1, N >= 1, 1 <= nnz < 2^31. On success *out owns the memory until
+ * daba_destroy. */
+daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* opt, daba_ctx** out);
+
+/* Sets the observation list E (Problem 1): cam_idx[k] in [0, M), lm_idx[k] in [0, N),
+ * uv[2k], uv[2k+1] the observed distorted pixel u_ij (Sec. 3) relative to the
+ * principal point, row-major nnz x 2. The library sorts the observations stably
+ * by camera and by landmark (ties keep input order) and builds its CSR offsets
+ * and work schedules (setup, not part of an iteration). Resets the iteration
+ * count and the restart metrics. At most 1024 observations per landmark (DABA_ERR_ARG otherwise). */
+daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const int32_t* lm_idx,
+                                  const double* uv, void* stream);
+
+/* Sets the iterate x^(0) = x^(-1) (Algorithm 1, initialisation) and resets s^(0) = 1
+ * and the restart metrics (Eq. Fainit).
+ * cams: M x 9 row-major [w(3), t(3), f, k1, k2]: w is the axis-angle vector of the
+ *   camera-to-world rotation R_i (a point l has camera-frame coordinates
+ *   R_i^T (l - t_i)), t_i the camera centre, f the focal length in pixels, k1, k2
+ *   the radial undistortion coefficients on |u|/f, i.e. the undistorted ray is
+ *   [u/f, 1 + k1 |u/f|^2 + k2 |u/f|^4] (Eq. reprojection1 with d = (f, k1/f, k2/f^3)).
+ * lms: N x 3 row-major landmark positions. Returns DABA_ERR_NONFINITE on NaN/Inf. */
+daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms, void* stream);
+
+/* Runs `iters` >= 0 iterations of Algorithm 1 from the current iterate x^k.
+ * obj_trace (iters + 1 doubles, host or device, may be NULL): F(x^k), ...,
+ *   F(x^(k+iters)) in pixel^2 (Eq. Fobj). F(x^(k+iters)) needs one extra objective pass,
+ *   which is skipped when obj_trace is NULL.
+ * restarts (iters int32, host or device, may be NULL): number of blocks whose
+ *   adaptive restart fired in each iteration (Algorithm 1, restart test).
+ * Requires observations and state to be set (DABA_ERR_STATE otherwise). Returns
+ * DABA_ERR_NONFINITE if the objective became non-finite (state is then undefined).
+ * Waits for the stream before returning (the status needs the device's answer). */
+daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, void* stream);
+
+/* Objective F(x^k) of the current iterate in pixel^2 (Eq. Fobj), written to *out
+ * (host or device double). */
+daba_status daba_objective(daba_ctx* ctx, double* out, void* stream);
+
+/* Copies the current iterate x^k out in the boundary layout of daba_set_state
+ * (either pointer may be NULL to skip it). */
+daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* stream);
+
+/* Per-block restart metrics after the last iteration (each pointer may be NULL):
+ *   F_cam[M], F_lm[N]        F^alpha(k) of Eq. Fak (pixel^2) of the last iteration k,
+ *   Fbar_cam[M], Fbar_lm[N]  Fbar^alpha(k) of Eq. lFak (pixel^2),
+ *   rs_cam[M], rs_lm[N]      1 where the restart test fired in that iteration.
+ * F and Fbar of landmarks are reported only for DABA_FP64 (DABA_ERR_STATE otherwise). */
+daba_status daba_get_block_metrics(daba_ctx* ctx, double* F_cam, double* Fbar_cam, double* F_lm,
+                                   double* Fbar_lm, uint8_t* rs_cam, uint8_t* rs_lm, void* stream);
+
+/* The sort orders and CSR offsets built by daba_set_observations (each may be NULL):
+ *   cam_order[nnz]: input indices sorted stably by camera; cam_ptr[M+1] its offsets;
+ *   lm_order[nnz]:  input indices sorted stably by landmark; lm_ptr[N+1] its offsets. */
+daba_status daba_get_sort(daba_ctx* ctx, int32_t* cam_order, int32_t* cam_ptr, int32_t* lm_order,
+                          int32_t* lm_ptr, void* stream);
+
+/* Checkpoint of the full method state (x^k, x^k - x^(k-1), s^k, k and the per-block
+ * restart metrics) into a host buffer. With buf == NULL only *bytes is set to the
+ * required size. Importing it into a context with the same sizes, options and
+ * observations resumes bit-identically. */
+daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes);
+daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes);
+
+/* Device-time breakdown of the last daba_run (milliseconds, summed over its
+ * iterations) for the kernels of one iteration, in the order:
+ * [0] camera prepare (extrapolation, Eq. nesterov_x), [1] camera-sorted observation pass,
+ * [2] landmark-sorted observation pass + landmark solves, [3] camera solves, [4] reduction.
+ * Timing is recorded only when enabled with daba_set_timing(ctx, 1). */
+daba_status daba_set_timing(daba_ctx* ctx, int enable);
+daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
+
+/* Number of kernel launches the library issued in the last daba_run. */
+int64_t daba_last_launch_count(const daba_ctx* ctx);
+
+/* One-line description of the last error of this context (never NULL). */
+const char* daba_last_error(const daba_ctx* ctx);
+
+/* Frees the context and all its device memory. NULL is a no-op. */
+void daba_destroy(daba_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DABA_H_ */

@@ -1,0 +1,203 @@
+"""ctypes binding of the C ABI in include/daba.h (argument marshalling only).
+
+Every function of the header is exposed under the same name. Array arguments may be
+numpy arrays (host memory) or torch tensors (host or CUDA); they are passed to the
+library as raw pointers, and `stream` defaults to torch's current CUDA stream. No
+computation happens here: if the CUDA library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdaba_b300.so")
+
+DABA_OK, DABA_ERR_ARG, DABA_ERR_INDEX, DABA_ERR_DEGENERATE, DABA_ERR_NONFINITE, DABA_ERR_CUDA, DABA_ERR_OOM, \
+    DABA_ERR_STATE = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_DEGENERATE", "ERR_NONFINITE", "ERR_CUDA", "ERR_OOM", "ERR_STATE"]
+LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
+PREC = {"fp64": 0, "mixed": 1}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_07026_b300.build`")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+
+class daba_options(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_int), ("loss_scale_px", ctypes.c_double), ("xi", ctypes.c_double),
+                ("eta", ctypes.c_double), ("accelerated", ctypes.c_int), ("cam_alternations", ctypes.c_int),
+                ("pixel_scale", ctypes.c_double), ("prec", ctypes.c_int)]
+
+
+_p = ctypes.c_void_p
+_i32, _i64, _st = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+_SIGS = {
+    "daba_default_options": (None, [ctypes.POINTER(daba_options)]),
+    "daba_create": (_st, [_i32, _i32, _i64, ctypes.POINTER(daba_options), ctypes.POINTER(_p)]),
+    "daba_set_observations": (_st, [_p, _p, _p, _p, _p]),
+    "daba_set_state": (_st, [_p, _p, _p, _p]),
+    "daba_run": (_st, [_p, _i32, _p, _p, _p]),
+    "daba_objective": (_st, [_p, _p, _p]),
+    "daba_get_state": (_st, [_p, _p, _p, _p]),
+    "daba_get_block_metrics": (_st, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "daba_get_sort": (_st, [_p, _p, _p, _p, _p, _p]),
+    "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
+    "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
+    "daba_set_timing": (_st, [_p, ctypes.c_int]),
+    "daba_get_timing": (_st, [_p, _p]),
+    "daba_last_launch_count": (_i64, [_p]),
+    "daba_last_error": (ctypes.c_char_p, [_p]),
+    "daba_destroy": (None, [_p]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+EXPORTED = tuple(_SIGS)
+
+
+class DabaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def ptr(a):
+    """Raw data pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True, cam_alternations=2,
+            pixel_scale=0.0, prec="mixed") -> daba_options:
+    o = daba_options()
+    daba_default_options(ctypes.byref(o))
+    o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
+    o.loss_scale_px = float(loss_scale_px)
+    o.xi = float(xi)
+    o.eta = float(eta)
+    o.accelerated = int(bool(accelerated))
+    o.cam_alternations = int(cam_alternations)
+    o.pixel_scale = float(pixel_scale)
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    return o
+
+
+class Daba:
+    """Owns one daba_ctx; methods are the ABI calls with this context bound."""
+
+    def __init__(self, M, N, nnz, **opts):
+        self.M, self.N, self.nnz = int(M), int(N), int(nnz)
+        self.opts = options(**opts)
+        h = _p()
+        st = daba_create(self.M, self.N, self.nnz, ctypes.byref(self.opts), ctypes.byref(h))
+        if st != DABA_OK:
+            raise DabaError(st, "daba_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != DABA_OK:
+            raise DabaError(st, daba_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            daba_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_observations(self, cam_idx, lm_idx, uv, stream=None):
+        self._check(daba_set_observations(self._h, ptr(cam_idx), ptr(lm_idx), ptr(uv),
+                                          current_stream() if stream is None else stream))
+
+    def set_state(self, cams, lms, stream=None):
+        self._check(daba_set_state(self._h, ptr(cams), ptr(lms), current_stream() if stream is None else stream))
+
+    def run(self, iters, obj_trace=None, restarts=None, stream=None):
+        self._check(daba_run(self._h, int(iters), ptr(obj_trace), ptr(restarts),
+                             current_stream() if stream is None else stream))
+
+    def objective(self, out=None, stream=None):
+        host = out is None
+        if host:
+            out = np.zeros(1)
+        self._check(daba_objective(self._h, ptr(out), current_stream() if stream is None else stream))
+        return float(out[0]) if host else out
+
+    def get_state(self, cams=None, lms=None, stream=None):
+        if cams is None and lms is None:
+            cams, lms = np.zeros((self.M, 9)), np.zeros((self.N, 3))
+        self._check(daba_get_state(self._h, ptr(cams), ptr(lms), current_stream() if stream is None else stream))
+        return cams, lms
+
+    def get_block_metrics(self, landmarks=True, stream=None):
+        out = {"F_cam": np.zeros(self.M), "Fbar_cam": np.zeros(self.M), "rs_cam": np.zeros(self.M, np.uint8),
+               "rs_lm": np.zeros(self.N, np.uint8)}
+        if landmarks:
+            out["F_lm"] = np.zeros(self.N)
+            out["Fbar_lm"] = np.zeros(self.N)
+        self._check(daba_get_block_metrics(self._h, ptr(out["F_cam"]), ptr(out["Fbar_cam"]), ptr(out.get("F_lm")),
+                                           ptr(out.get("Fbar_lm")), ptr(out["rs_cam"]), ptr(out["rs_lm"]),
+                                           current_stream() if stream is None else stream))
+        return out
+
+    def get_sort(self, stream=None):
+        co, cp = np.zeros(self.nnz, np.int32), np.zeros(self.M + 1, np.int32)
+        lo, lp = np.zeros(self.nnz, np.int32), np.zeros(self.N + 1, np.int32)
+        self._check(daba_get_sort(self._h, ptr(co), ptr(cp), ptr(lo), ptr(lp),
+                                  current_stream() if stream is None else stream))
+        return co, cp, lo, lp
+
+    def export_checkpoint(self) -> bytes:
+        n = ctypes.c_size_t(0)
+        self._check(daba_export_checkpoint(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(daba_export_checkpoint(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def import_checkpoint(self, data: bytes):
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(daba_import_checkpoint(self._h, buf, len(data)))
+
+    def set_timing(self, enable=True):
+        self._check(daba_set_timing(self._h, int(bool(enable))))
+
+    def get_timing(self):
+        out = np.zeros(5)
+        self._check(daba_get_timing(self._h, ptr(out)))
+        return out
+
+    def last_launch_count(self) -> int:
+        return int(daba_last_launch_count(self._h))

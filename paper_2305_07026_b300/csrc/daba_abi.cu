@@ -1,0 +1,933 @@
+// daba_abi.cu -- host runtime and C ABI (include/daba.h) of the DABA iteration library.
+//
+// Setup (daba_set_observations) sorts the observations stably by camera and by
+// landmark on the host, builds the CSR offsets, the camera chunks of the
+// camera-sorted pass and the landmark tiles of the landmark-sorted pass, and
+// uploads them. daba_run then enqueues, per iteration of Algorithm 1, the five
+// kernels of daba_kernels.cuh on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/daba.h"
+#include "daba_kernels.cuh"
+
+using namespace daba;
+
+namespace {
+
+constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: observations per warp chunk
+constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
+constexpr uint64_t CKPT_MAGIC = 0x44414241434b5031ull;   // "DABACKP1"
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct daba_ctx {
+  int M = 0, N = 0;
+  int64_t nnz = 0;
+  daba_options opt{};
+  std::string err;
+  int dev = 0;
+  // sizes of the schedules
+  int n_chunks = 0, n_tiles = 0, max_chunks = 0, max_tiles = 0;
+  bool obs_set = false, state_set = false, checked = false;
+  double s_norm = 0.0, u_scale_uploaded = -1.0;
+  double s_k = 1.0;   // Nesterov s^(k)
+  int64_t k = 0;      // iteration index
+  bool timing = false;
+  double tms[5] = {0, 0, 0, 0, 0};
+  int64_t launches = 0;
+  // host copies (setup data and boundary state)
+  std::vector<int32_t> h_cam_idx, h_lm_idx;
+  std::vector<double> h_uv;
+  std::vector<int32_t> h_c_order, h_cam_ptr, h_l_order, h_lm_ptr, h_t_order;
+  std::vector<double> h_t;   // camera centres of the state last set (for the Asm. 2 check)
+  std::vector<double> h_l;
+  // device buffers
+  void *c_lm = nullptr, *c_u = nullptr, *c_orig = nullptr, *cam_ptr = nullptr;
+  void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
+  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_cam = nullptr, *t_u = nullptr, *t_slot = nullptr, *l_orig = nullptr;
+  void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack = nullptr;
+  void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
+  void *lmrec = nullptr, *lm_lo = nullptr, *lm_rs = nullptr, *lm_Fd = nullptr, *lm_Fbd = nullptr;
+  void *chunk_part = nullptr, *tile_part = nullptr;
+  void *d_gam = nullptr, *d_it = nullptr, *d_first = nullptr, *d_flag = nullptr, *d_trace = nullptr,
+       *d_rs = nullptr, *d_obj = nullptr;
+  std::vector<void*> allocs;
+  std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+daba_status fail(daba_ctx* c, daba_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(ctx, DABA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+daba_status dalloc(daba_ctx* ctx, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, DABA_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(*p);
+  return DABA_OK;
+}
+
+// copy `bytes` from a host or device source into host memory
+daba_status fetch(daba_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return DABA_OK;
+}
+
+// copy host data to a host or device destination
+daba_status deliver(daba_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (is_device_ptr(dst)) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return DABA_OK;
+}
+
+bool is_mixed(const daba_ctx* c) { return c->opt.prec == DABA_MIXED; }
+size_t real_sz(const daba_ctx* c) { return is_mixed(c) ? sizeof(float) : sizeof(double); }
+
+// ---- rotation parameterisation (boundary <-> R)
+void rodrigues(const double* w, double* R) {
+  const double th = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double a, b;
+  if (th < 1e-8) {
+    a = 1.0 - th * th / 6.0;
+    b = 0.5 - th * th / 24.0;
+  } else {
+    a = std::sin(th) / th;
+    b = (1.0 - std::cos(th)) / (th * th);
+  }
+  const double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += K[i * 3 + k] * K[k * 3 + j];
+      K2[i * 3 + j] = s;
+    }
+  for (int i = 0; i < 9; ++i) R[i] = ((i % 4) == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+}
+
+void rot_log(const double* A, double* w) {
+  const double c = (A[0] + A[4] + A[8] - 1.0) / 2.0;
+  const double v[3] = {(A[7] - A[5]) / 2.0, (A[2] - A[6]) / 2.0, (A[3] - A[1]) / 2.0};
+  const double sn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double th = std::atan2(sn, c);
+  if (c > -0.5) {
+    const double f = sn > 1e-300 ? th / sn : 1.0;
+    for (int k = 0; k < 3; ++k) w[k] = v[k] * f;
+    return;
+  }
+  double B[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[i * 3 + j] = 0.5 * (A[i * 3 + j] + A[j * 3 + i]) - (i == j ? c : 0.0);
+  int kk = 0;
+  for (int k = 1; k < 3; ++k)
+    if (B[k * 4] > B[kk * 4]) kk = k;
+  double a[3] = {B[0 * 3 + kk], B[1 * 3 + kk], B[2 * 3 + kk]};
+  const double n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  double sg = (a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) < 0 ? -1.0 : 1.0;
+  for (int k = 0; k < 3; ++k) w[k] = sg * a[k] / n * th;
+}
+
+// stable counting sort of 0..n-1 by key in [0, K): order and CSR offsets
+void counting_sort(const std::vector<int32_t>& key, int K, std::vector<int32_t>& order, std::vector<int32_t>& ptr) {
+  const int64_t n = (int64_t)key.size();
+  ptr.assign(K + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ptr[key[i] + 1]++;
+  for (int k = 0; k < K; ++k) ptr[k + 1] += ptr[k];
+  std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
+  order.resize(n);
+  for (int64_t i = 0; i < n; ++i) order[pos[key[i]]++] = (int32_t)i;
+}
+
+template <class Real, class Real2>
+void upload_u(daba_ctx* ctx, cudaStream_t st, cudaError_t* err) {
+  const double s = ctx->s_norm;
+  std::vector<Real2> cu(ctx->nnz), tu(ctx->nnz);
+  for (int64_t o = 0; o < ctx->nnz; ++o) {
+    const int32_t i = ctx->h_c_order[o];
+    cu[o].x = Real(ctx->h_uv[2 * (size_t)i] / s);
+    cu[o].y = Real(ctx->h_uv[2 * (size_t)i + 1] / s);
+    const int32_t j = ctx->h_l_order[ctx->h_t_order[o]];
+    tu[o].x = Real(ctx->h_uv[2 * (size_t)j] / s);
+    tu[o].y = Real(ctx->h_uv[2 * (size_t)j + 1] / s);
+  }
+  *err = cudaMemcpyAsync(ctx->c_u, cu.data(), cu.size() * sizeof(Real2), cudaMemcpyHostToDevice, st);
+  if (*err == cudaSuccess)
+    *err = cudaMemcpyAsync(ctx->t_u, tu.data(), tu.size() * sizeof(Real2), cudaMemcpyHostToDevice, st);
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
+}
+
+daba_status ensure_u(daba_ctx* ctx, cudaStream_t st) {
+  if (ctx->u_scale_uploaded == ctx->s_norm) return DABA_OK;
+  cudaError_t e;
+  if (is_mixed(ctx))
+    upload_u<float, float2>(ctx, st, &e);
+  else
+    upload_u<double, double2>(ctx, st, &e);
+  if (e != cudaSuccess) return fail(ctx, DABA_ERR_CUDA, "uploading pixels: %s", cudaGetErrorString(e));
+  ctx->u_scale_uploaded = ctx->s_norm;
+  return DABA_OK;
+}
+
+// Assumption 2 check on the host copies of the observations and the state last set
+daba_status check_degenerate(daba_ctx* ctx) {
+  if (ctx->checked) return DABA_OK;
+  for (int64_t o = 0; o < ctx->nnz; ++o) {
+    const int i = ctx->h_cam_idx[o], j = ctx->h_lm_idx[o];
+    double q2 = 0, t2 = 0;
+    for (int a = 0; a < 3; ++a) {
+      const double q = ctx->h_l[3 * (size_t)j + a] - ctx->h_t[3 * (size_t)i + a];
+      q2 += q * q;
+      t2 += ctx->h_t[3 * (size_t)i + a] * ctx->h_t[3 * (size_t)i + a];
+    }
+    if (!(q2 > 1e-24 * std::max(1.0, t2)))
+      return fail(ctx, DABA_ERR_DEGENERATE, "observation %lld: landmark %d coincides with camera %d centre",
+                  (long long)o, j, i);
+  }
+  ctx->checked = true;
+  return DABA_OK;
+}
+
+template <class Real>
+LossC<Real> loss_consts(const daba_ctx* ctx) {
+  const double c = ctx->opt.loss == DABA_LOSS_TRIVIAL ? 1.0 : ctx->opt.loss_scale_px / ctx->s_norm;
+  LossC<Real> L;
+  L.c = Real(c);
+  L.c2 = Real(c * c);
+  L.inv_c2 = Real(1.0 / (c * c));
+  return L;
+}
+
+IterParams iter_params(daba_ctx* ctx) {
+  IterParams P;
+  P.gam = (const double*)ctx->d_gam;
+  P.it = (int*)ctx->d_it;
+  P.first = (int*)ctx->d_first;
+  P.xi = ctx->opt.xi;
+  P.eta = ctx->opt.eta;
+  P.accelerated = ctx->opt.accelerated;
+  P.n_alt = ctx->opt.cam_alternations;
+  return P;
+}
+
+template <int LOSS, class Real, class Real2, bool HAS_LO>
+cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
+  const LossC<Real> L = loss_consts<Real>(ctx);
+  const IterParams P = iter_params(ctx);
+  if (which == 1) {
+    const int threads = CPASS_WARPS * 32;
+    const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
+    if (blocks > 0)
+      k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
+          ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+          (const Real2*)ctx->c_u, (const Real*)ctx->pack, (const Real*)ctx->lmrec, L, P, (double*)ctx->chunk_part);
+  } else if (which == 2) {
+    const size_t smem = LSmem<Real>::bytes(TILE_OBS, TILE_OBS);
+    auto kern = k_lpass<LOSS, Real, Real2, HAS_LO>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<ctx->n_tiles, LPASS_THREADS, smem, st>>>(
+        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam, (const Real2*)ctx->t_u,
+        (const uint16_t*)ctx->t_slot, (const Real*)ctx->pack, (Real*)ctx->lmrec, (float*)ctx->lm_lo, L, P,
+        (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
+  } else if (which == 6) {
+    const size_t smem = (size_t)TILE_OBS * 6 * sizeof(Real) + (size_t)TILE_OBS * sizeof(uint16_t) + 64;
+    auto kern = k_objective<LOSS, Real, Real2, HAS_LO>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<ctx->n_tiles, LPASS_THREADS, smem, st>>>(
+        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam, (const Real2*)ctx->t_u,
+        (const uint16_t*)ctx->t_slot, (const Real*)ctx->pack, (const Real*)ctx->lmrec, (const float*)ctx->lm_lo, L,
+        (double*)ctx->tile_part);
+  }
+  return cudaGetLastError();
+}
+
+template <class Real, class Real2, bool HAS_LO>
+cudaError_t launch_by_loss(daba_ctx* ctx, cudaStream_t st, int which) {
+  switch (ctx->opt.loss) {
+    case DABA_LOSS_TRIVIAL: return launch_passes<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st, which);
+    case DABA_LOSS_HUBER: return launch_passes<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st, which);
+    case DABA_LOSS_CAUCHY: return launch_passes<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st, which);
+    default: return launch_passes<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st, which);
+  }
+}
+
+cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which) {
+  ctx->launches++;
+  if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which);
+  return launch_by_loss<double, double2, false>(ctx, st, which);
+}
+
+cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st) {
+  ctx->launches++;
+  const IterParams P = iter_params(ctx);
+  const int blocks = (ctx->M + 127) / 128;
+  if (is_mixed(ctx))
+    k_cam_prepare<float><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
+                                                 (double*)ctx->cam_Rbar, (float*)ctx->pack);
+  else
+    k_cam_prepare<double><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
+                                                  (double*)ctx->cam_Rbar, (double*)ctx->pack);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st) {
+  ctx->launches++;
+  const IterParams P = iter_params(ctx);
+  k_camsolve<<<(ctx->M + 63) / 64, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
+                                                (double*)ctx->cam_x, (double*)ctx->cam_dx, (const double*)ctx->cam_Rbar,
+                                                P, (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
+                                                (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
+  ctx->launches++;
+  const IterParams P = iter_params(ctx);
+  k_finalize<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->M, (const uint8_t*)ctx->cam_rs,
+                                 ctx->s_norm * ctx->s_norm, P, (double*)ctx->d_trace, (int*)ctx->d_rs,
+                                 (int*)ctx->d_flag);
+  return cudaGetLastError();
+}
+
+// F(x^k) of the current state into d_obj (device double): prepare the pack (gamma is
+// irrelevant for F), per-tile sums, reduction.
+daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st) {
+  CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+  CK(launch_prepare(ctx, st));
+  CK(launch_pass(ctx, st, 6));
+  ctx->launches++;
+  k_sum_tiles<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->s_norm * ctx->s_norm,
+                                  (double*)ctx->d_obj);
+  CK(cudaGetLastError());
+  return DABA_OK;
+}
+
+cudaEvent_t ev(daba_ctx* ctx, size_t i) {
+  while (ctx->events.size() <= i) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    ctx->events.push_back(e);
+  }
+  return ctx->events[i];
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void daba_default_options(daba_options* o) {
+  if (!o) return;
+  o->loss = DABA_LOSS_HUBER;
+  o->loss_scale_px = 1.0;
+  o->xi = 1e-10;
+  o->eta = 0.5;
+  o->accelerated = 1;
+  o->cam_alternations = 2;
+  o->pixel_scale = 0.0;
+  o->prec = DABA_MIXED;
+}
+
+const char* daba_last_error(const daba_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t daba_last_launch_count(const daba_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void daba_destroy(daba_ctx* ctx) {
+  if (!ctx) return;
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  delete ctx;
+}
+
+daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* opt, daba_ctx** out) {
+  if (!out) return DABA_ERR_ARG;
+  *out = nullptr;
+  daba_ctx* ctx = new daba_ctx();
+  daba_status st = DABA_OK;
+  auto bad = [&](const char* why) {
+    daba_destroy(ctx);
+    return DABA_ERR_ARG;
+    (void)why;
+  };
+  if (M < 1 || N < 1 || nnz < 1 || nnz >= (int64_t(1) << 31)) return bad("sizes");
+  if (opt)
+    ctx->opt = *opt;
+  else
+    daba_default_options(&ctx->opt);
+  const daba_options& o = ctx->opt;
+  if (!(o.xi > 0) || !(o.eta > 0) || !(o.eta <= 1) || o.cam_alternations < 1 || o.cam_alternations > 64 ||
+      (int)o.loss < 0 || (int)o.loss > 3 || !(o.pixel_scale >= 0) ||
+      (o.loss != DABA_LOSS_TRIVIAL && !(o.loss_scale_px > 0)) || (o.prec != DABA_FP64 && o.prec != DABA_MIXED))
+    return bad("options");
+  ctx->M = M;
+  ctx->N = N;
+  ctx->nnz = nnz;
+  cudaGetDevice(&ctx->dev);
+  const size_t R = real_sz(ctx);
+  ctx->max_chunks = (int)(M + nnz / CHUNK_OBS + 1);
+  ctx->max_tiles = (int)(2 * ((nnz + N) / TILE_OBS) + 2);
+#define AL(field, bytes)                                   \
+  if ((st = dalloc(ctx, &ctx->field, (bytes))) != DABA_OK) { \
+    daba_ctx* c_ = ctx;                                    \
+    daba_destroy(c_);                                      \
+    return st;                                             \
+  }
+  AL(c_lm, nnz * 4);
+  AL(c_u, nnz * 2 * R);
+  AL(c_orig, nnz * 4);
+  AL(cam_ptr, (size_t)(M + 1) * 4);
+  AL(chunk_cam, (size_t)ctx->max_chunks * 4);
+  AL(chunk_beg, (size_t)(ctx->max_chunks + 1) * 4);
+  AL(cam_chunk_ptr, (size_t)(M + 1) * 4);
+  AL(lm_ptr, (size_t)(N + 1) * 4);
+  AL(tile_lm, (size_t)(ctx->max_tiles + 1) * 4);
+  AL(t_cam, nnz * 4);
+  AL(t_u, nnz * 2 * R);
+  AL(t_slot, nnz * 2);
+  AL(l_orig, nnz * 4);
+  AL(cam_x, (size_t)M * CSTRIDE * 8);
+  AL(cam_dx, (size_t)M * CSTRIDE * 8);
+  AL(cam_Rbar, (size_t)M * 9 * 8);
+  AL(pack, (size_t)M * PACK * R);
+  AL(cam_S, (size_t)M * 8);
+  AL(cam_E, (size_t)M * 8);
+  AL(cam_F, (size_t)M * 8);
+  AL(cam_Fb, (size_t)M * 8);
+  AL(cam_rs, (size_t)M);
+  AL(lmrec, (size_t)N * LREC * R);
+  AL(lm_lo, (size_t)N * 4 * 4);
+  AL(lm_rs, (size_t)N);
+  AL(lm_Fd, (size_t)N * 8);
+  AL(lm_Fbd, (size_t)N * 8);
+  AL(chunk_part, (size_t)ctx->max_chunks * CP_STRIDE * 8);
+  AL(tile_part, (size_t)ctx->max_tiles * TP_STRIDE * 8);
+  AL(d_gam, GSEG * 8);
+  AL(d_it, 16);
+  AL(d_first, 16);
+  AL(d_flag, 16);
+  AL(d_trace, (GSEG + 1) * 8);
+  AL(d_rs, (GSEG + 1) * 4);
+  AL(d_obj, 16);
+#undef AL
+  cudaMemset(ctx->lm_lo, 0, (size_t)N * 16);
+  cudaMemset(ctx->d_flag, 0, 16);
+  cudaMemset(ctx->cam_rs, 0, (size_t)M);
+  cudaMemset(ctx->lm_rs, 0, (size_t)N);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    daba_destroy(ctx);
+    return DABA_ERR_CUDA;
+  }
+  *out = ctx;
+  return DABA_OK;
+}
+
+daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const int32_t* lm_idx, const double* uv,
+                                  void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!cam_idx || !lm_idx || !uv) return fail(ctx, DABA_ERR_ARG, "null observation pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ctx->nnz;
+  std::vector<int32_t> ci(n), li(n);
+  std::vector<double> uvh(2 * n);
+  daba_status s;
+  if ((s = fetch(ctx, ci.data(), cam_idx, n * 4, st)) != DABA_OK) return s;
+  if ((s = fetch(ctx, li.data(), lm_idx, n * 4, st)) != DABA_OK) return s;
+  if ((s = fetch(ctx, uvh.data(), uv, n * 16, st)) != DABA_OK) return s;
+  for (int64_t o = 0; o < n; ++o) {
+    if (ci[o] < 0 || ci[o] >= ctx->M || li[o] < 0 || li[o] >= ctx->N)
+      return fail(ctx, DABA_ERR_INDEX, "observation %lld has index (%d, %d) out of range", (long long)o, ci[o], li[o]);
+    if (!std::isfinite(uvh[2 * o]) || !std::isfinite(uvh[2 * o + 1]))
+      return fail(ctx, DABA_ERR_NONFINITE, "observation %lld has a non-finite pixel", (long long)o);
+  }
+  std::vector<int32_t> c_order, cam_ptr, l_order, lm_ptr;
+  counting_sort(ci, ctx->M, c_order, cam_ptr);
+  counting_sort(li, ctx->N, l_order, lm_ptr);
+  for (int j = 0; j < ctx->N; ++j)
+    if (lm_ptr[j + 1] - lm_ptr[j] > TILE_OBS)
+      return fail(ctx, DABA_ERR_ARG, "landmark %d has %d observations (max %d)", j, lm_ptr[j + 1] - lm_ptr[j], TILE_OBS);
+  // camera chunks
+  std::vector<int32_t> chunk_cam, chunk_beg, cam_chunk_ptr(ctx->M + 1, 0);
+  for (int i = 0; i < ctx->M; ++i) {
+    cam_chunk_ptr[i] = (int32_t)chunk_cam.size();
+    for (int b = cam_ptr[i]; b < cam_ptr[i + 1]; b += CHUNK_OBS) {
+      chunk_cam.push_back(i);
+      chunk_beg.push_back(b);
+    }
+  }
+  cam_chunk_ptr[ctx->M] = (int32_t)chunk_cam.size();
+  chunk_beg.push_back((int32_t)n);
+  // landmark tiles: consecutive landmarks with at most TILE_OBS observations and landmarks
+  std::vector<int32_t> tile_lm;
+  {
+    int j = 0;
+    tile_lm.push_back(0);
+    while (j < ctx->N) {
+      int j2 = j, cnt = 0;
+      while (j2 < ctx->N && j2 - j < TILE_OBS && cnt + (lm_ptr[j2 + 1] - lm_ptr[j2]) <= TILE_OBS) {
+        cnt += lm_ptr[j2 + 1] - lm_ptr[j2];
+        ++j2;
+      }
+      j = j2;
+      tile_lm.push_back(j);
+    }
+  }
+  const int n_tiles = (int)tile_lm.size() - 1;
+  if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
+    return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
+  // inside each tile: observations in camera order (ties by landmark-sorted position)
+  std::vector<int32_t> t_order(n), t_cam(n), c_lm(n);
+  std::vector<uint16_t> t_slot(n);
+  for (int t = 0; t < n_tiles; ++t) {
+    const int ob = lm_ptr[tile_lm[t]], oe = lm_ptr[tile_lm[t + 1]];
+    for (int o = ob; o < oe; ++o) t_order[o] = o;
+    std::sort(t_order.begin() + ob, t_order.begin() + oe, [&](int32_t a, int32_t b) {
+      const int32_t ca = ci[l_order[a]], cb = ci[l_order[b]];
+      return ca != cb ? ca < cb : a < b;
+    });
+    for (int o = ob; o < oe; ++o) {
+      t_cam[o] = ci[l_order[t_order[o]]];
+      t_slot[o] = (uint16_t)(t_order[o] - ob);
+    }
+  }
+  for (int64_t o = 0; o < n; ++o) c_lm[o] = li[c_order[o]];
+  // upload
+  CK(cudaMemcpyAsync(ctx->c_lm, c_lm.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->c_orig, c_order.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_ptr, cam_ptr.data(), (ctx->M + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->chunk_cam, chunk_cam.data(), chunk_cam.size() * 4 + 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->chunk_beg, chunk_beg.data(), chunk_beg.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (ctx->M + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->lm_ptr, lm_ptr.data(), (ctx->N + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_cam, t_cam.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->l_orig, l_order.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->n_chunks = (int)chunk_cam.size();
+  ctx->n_tiles = n_tiles;
+  ctx->h_cam_idx.swap(ci);
+  ctx->h_lm_idx.swap(li);
+  ctx->h_uv.swap(uvh);
+  ctx->h_c_order.swap(c_order);
+  ctx->h_cam_ptr.swap(cam_ptr);
+  ctx->h_l_order.swap(l_order);
+  ctx->h_lm_ptr.swap(lm_ptr);
+  ctx->h_t_order.swap(t_order);
+  ctx->u_scale_uploaded = -1.0;
+  ctx->obs_set = true;
+  ctx->checked = false;
+  ctx->k = 0;
+  ctx->s_k = 1.0;
+  int one = 1;
+  CK(cudaMemcpyAsync(ctx->d_first, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return DABA_OK;
+}
+
+daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!cams || !lms) return fail(ctx, DABA_ERR_ARG, "null state pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = ctx->M, N = ctx->N;
+  std::vector<double> hc((size_t)M * 9), hl((size_t)N * 3);
+  daba_status s;
+  if ((s = fetch(ctx, hc.data(), cams, hc.size() * 8, st)) != DABA_OK) return s;
+  if ((s = fetch(ctx, hl.data(), lms, hl.size() * 8, st)) != DABA_OK) return s;
+  for (double v : hc)
+    if (!std::isfinite(v)) return fail(ctx, DABA_ERR_NONFINITE, "non-finite camera parameter");
+  for (double v : hl)
+    if (!std::isfinite(v)) return fail(ctx, DABA_ERR_NONFINITE, "non-finite landmark coordinate");
+  for (int i = 0; i < M; ++i)
+    if (!(hc[(size_t)i * 9 + 6] > 0)) return fail(ctx, DABA_ERR_ARG, "camera %d has a non-positive focal length", i);
+  double sn = ctx->opt.pixel_scale;
+  if (!(sn > 0)) {
+    if (ctx->s_norm > 0) {
+      sn = ctx->s_norm;
+    } else {
+      std::vector<double> f(M);
+      for (int i = 0; i < M; ++i) f[i] = hc[(size_t)i * 9 + 6];
+      std::sort(f.begin(), f.end());
+      sn = (M % 2) ? f[M / 2] : 0.5 * (f[M / 2 - 1] + f[M / 2]);
+    }
+  }
+  ctx->s_norm = sn;
+  std::vector<double> x((size_t)M * CSTRIDE, 0.0), dx((size_t)M * CSTRIDE, 0.0), zeros(M, 0.0);
+  ctx->h_t.assign((size_t)M * 3, 0.0);
+  for (int i = 0; i < M; ++i) {
+    const double* c = &hc[(size_t)i * 9];
+    double* xi = &x[(size_t)i * CSTRIDE];
+    rodrigues(c, xi + CS_R);
+    for (int a = 0; a < 3; ++a) {
+      xi[CS_T + a] = c[3 + a];
+      ctx->h_t[(size_t)i * 3 + a] = c[3 + a];
+    }
+    const double f = c[6], k1 = c[7], k2 = c[8];
+    xi[CS_D + 0] = f / sn;
+    xi[CS_D + 1] = k1 * sn / f;
+    xi[CS_D + 2] = k2 * sn * sn * sn / (f * f * f);
+  }
+  CK(cudaMemcpyAsync(ctx->cam_x, x.data(), x.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_dx, dx.data(), dx.size() * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_S, zeros.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_E, zeros.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
+  if (is_mixed(ctx)) {
+    std::vector<float> rec((size_t)N * LREC, 0.f), lo((size_t)N * 4, 0.f);
+    for (int j = 0; j < N; ++j)
+      for (int a = 0; a < 3; ++a) {
+        const double v = hl[(size_t)j * 3 + a];
+        const float h = (float)v;
+        rec[(size_t)j * LREC + LR_L + a] = h;
+        lo[(size_t)j * 4 + a] = (float)(v - (double)h);
+      }
+    CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->lm_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::vector<double> rec((size_t)N * LREC, 0.0);
+    for (int j = 0; j < N; ++j)
+      for (int a = 0; a < 3; ++a) rec[(size_t)j * LREC + LR_L + a] = hl[(size_t)j * 3 + a];
+    CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  ctx->h_l.swap(hl);
+  int one = 1;
+  CK(cudaMemcpyAsync(ctx->d_first, &one, sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->state_set = true;
+  ctx->checked = false;
+  ctx->k = 0;
+  ctx->s_k = 1.0;
+  return DABA_OK;
+}
+
+daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (iters < 0) return fail(ctx, DABA_ERR_ARG, "iters < 0");
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  cudaStream_t st = (cudaStream_t)stream;
+  daba_status s;
+  if ((s = check_degenerate(ctx)) != DABA_OK) return s;
+  if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  ctx->launches = 0;
+  for (double& t : ctx->tms) t = 0.0;
+  std::vector<double> trace((size_t)iters + 1);
+  std::vector<int32_t> rs((size_t)std::max(iters, 1));
+  int done = 0;
+  size_t evi = 0;
+  std::vector<double> gam(GSEG);
+  CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+  while (done < iters) {
+    const int seg = std::min(GSEG, iters - done);
+    for (int j = 0; j < seg; ++j) {
+      const double s_next = (std::sqrt(4.0 * ctx->s_k * ctx->s_k + 1.0) + 1.0) / 2.0;
+      gam[j] = (ctx->s_k - 1.0) / s_next;
+      ctx->s_k = s_next;
+    }
+    CK(cudaMemcpyAsync(ctx->d_gam, gam.data(), seg * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+    for (int j = 0; j < seg; ++j) {
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi), st));
+      CK(launch_prepare(ctx, st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 1), st));
+      CK(launch_pass(ctx, st, 1));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 2), st));
+      CK(launch_pass(ctx, st, 2));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 3), st));
+      CK(launch_camsolve(ctx, st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 4), st));
+      CK(launch_finalize(ctx, st));
+      if (ctx->timing) {
+        CK(cudaEventRecord(ev(ctx, evi + 5), st));
+        evi += 6;
+      }
+    }
+    CK(cudaMemcpyAsync(trace.data() + done, ctx->d_trace, seg * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->timing) {
+      for (size_t b = 0; b < evi; b += 6)
+        for (int q = 0; q < 5; ++q) {
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, ctx->events[b + q], ctx->events[b + q + 1]);
+          ctx->tms[q] += ms;
+        }
+      evi = 0;
+    }
+    done += seg;
+    ctx->k += seg;
+  }
+  if (obj_trace) {
+    if ((s = enqueue_objective(ctx, st)) != DABA_OK) return s;
+    CK(cudaMemcpyAsync(&trace[iters], ctx->d_obj, 8, cudaMemcpyDeviceToHost, st));
+  } else {
+    trace[iters] = 0.0;
+  }
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag || !std::isfinite(trace[iters])) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
+  if (obj_trace && (s = deliver(ctx, obj_trace, trace.data(), ((size_t)iters + 1) * 8, st)) != DABA_OK) return s;
+  if (restarts && iters > 0 && (s = deliver(ctx, restarts, rs.data(), (size_t)iters * 4, st)) != DABA_OK) return s;
+  return DABA_OK;
+}
+
+daba_status daba_objective(daba_ctx* ctx, double* out, void* stream) {
+  if (!ctx || !out) return ctx ? fail(ctx, DABA_ERR_ARG, "null output") : DABA_ERR_ARG;
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  cudaStream_t st = (cudaStream_t)stream;
+  daba_status s;
+  if ((s = check_degenerate(ctx)) != DABA_OK) return s;
+  if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  // gamma buffer entry 0 is read by the prepare kernel; any finite value will do
+  double g0 = 0.0;
+  CK(cudaMemcpyAsync(ctx->d_gam, &g0, 8, cudaMemcpyHostToDevice, st));
+  if ((s = enqueue_objective(ctx, st)) != DABA_OK) return s;
+  if (is_device_ptr(out)) {
+    CK(cudaMemcpyAsync(out, ctx->d_obj, 8, cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(cudaMemcpyAsync(out, ctx->d_obj, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return DABA_OK;
+}
+
+daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!ctx->state_set) return fail(ctx, DABA_ERR_STATE, "state not set");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = ctx->M, N = ctx->N;
+  const double sn = ctx->s_norm;
+  daba_status s;
+  if (cams) {
+    std::vector<double> x((size_t)M * CSTRIDE), hc((size_t)M * 9);
+    CK(cudaMemcpyAsync(x.data(), ctx->cam_x, x.size() * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < M; ++i) {
+      const double* xi = &x[(size_t)i * CSTRIDE];
+      double* c = &hc[(size_t)i * 9];
+      rot_log(xi + CS_R, c);
+      for (int a = 0; a < 3; ++a) c[3 + a] = xi[CS_T + a];
+      const double f = xi[CS_D + 0] * sn;
+      c[6] = f;
+      c[7] = xi[CS_D + 1] * f / sn;
+      c[8] = xi[CS_D + 2] * f * f * f / (sn * sn * sn);
+    }
+    if ((s = deliver(ctx, cams, hc.data(), hc.size() * 8, st)) != DABA_OK) return s;
+  }
+  if (lms) {
+    std::vector<double> hl((size_t)N * 3);
+    if (is_mixed(ctx)) {
+      std::vector<float> rec((size_t)N * LREC), lo((size_t)N * 4);
+      CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(lo.data(), ctx->lm_lo, lo.size() * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a)
+          hl[(size_t)j * 3 + a] = (double)rec[(size_t)j * LREC + LR_L + a] + (double)lo[(size_t)j * 4 + a];
+    } else {
+      std::vector<double> rec((size_t)N * LREC);
+      CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int j = 0; j < N; ++j)
+        for (int a = 0; a < 3; ++a) hl[(size_t)j * 3 + a] = rec[(size_t)j * LREC + LR_L + a];
+    }
+    if ((s = deliver(ctx, lms, hl.data(), hl.size() * 8, st)) != DABA_OK) return s;
+  }
+  return DABA_OK;
+}
+
+daba_status daba_get_block_metrics(daba_ctx* ctx, double* F_cam, double* Fbar_cam, double* F_lm, double* Fbar_lm,
+                                   uint8_t* rs_cam, uint8_t* rs_lm, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if ((F_lm || Fbar_lm) && is_mixed(ctx))
+    return fail(ctx, DABA_ERR_STATE, "landmark F and Fbar are reported only by the FP64 path");
+  cudaStream_t st = (cudaStream_t)stream;
+  const double s2 = ctx->s_norm * ctx->s_norm;
+  const int M = ctx->M, N = ctx->N;
+  daba_status s;
+  auto getd = [&](double* dst, const void* src, int n) -> daba_status {
+    std::vector<double> h(n);
+    CK(cudaMemcpyAsync(h.data(), src, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (double& v : h) v *= s2;
+    return deliver(ctx, dst, h.data(), (size_t)n * 8, st);
+  };
+  auto getb = [&](uint8_t* dst, const void* src, int n) -> daba_status {
+    std::vector<uint8_t> h(n);
+    CK(cudaMemcpyAsync(h.data(), src, (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return deliver(ctx, dst, h.data(), (size_t)n, st);
+  };
+  if (F_cam && (s = getd(F_cam, ctx->cam_F, M)) != DABA_OK) return s;
+  if (Fbar_cam && (s = getd(Fbar_cam, ctx->cam_Fb, M)) != DABA_OK) return s;
+  if (F_lm && (s = getd(F_lm, ctx->lm_Fd, N)) != DABA_OK) return s;
+  if (Fbar_lm && (s = getd(Fbar_lm, ctx->lm_Fbd, N)) != DABA_OK) return s;
+  if (rs_cam && (s = getb(rs_cam, ctx->cam_rs, M)) != DABA_OK) return s;
+  if (rs_lm && (s = getb(rs_lm, ctx->lm_rs, N)) != DABA_OK) return s;
+  return DABA_OK;
+}
+
+daba_status daba_get_sort(daba_ctx* ctx, int32_t* cam_order, int32_t* cam_ptr, int32_t* lm_order, int32_t* lm_ptr,
+                          void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations not set");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto geti = [&](int32_t* dst, const void* src, int64_t n) -> daba_status {
+    std::vector<int32_t> h(n);
+    CK(cudaMemcpyAsync(h.data(), src, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return deliver(ctx, dst, h.data(), (size_t)n * 4, st);
+  };
+  daba_status s;
+  if (cam_order && (s = geti(cam_order, ctx->c_orig, ctx->nnz)) != DABA_OK) return s;
+  if (cam_ptr && (s = geti(cam_ptr, ctx->cam_ptr, ctx->M + 1)) != DABA_OK) return s;
+  if (lm_order && (s = geti(lm_order, ctx->l_orig, ctx->nnz)) != DABA_OK) return s;
+  if (lm_ptr && (s = geti(lm_ptr, ctx->lm_ptr, ctx->N + 1)) != DABA_OK) return s;
+  return DABA_OK;
+}
+
+namespace {
+struct CkptHeader {
+  uint64_t magic;
+  int64_t M, N, nnz, prec, k;
+  double s_k, s_norm;
+  int64_t first;
+};
+size_t ckpt_bytes(const daba_ctx* c) {
+  return sizeof(CkptHeader) + (size_t)c->M * CSTRIDE * 8 * 2 + (size_t)c->M * 8 * 2 + (size_t)c->N * LREC * real_sz(c) +
+         (size_t)c->N * 16;
+}
+}  // namespace
+
+daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
+  if (!ctx || !bytes) return DABA_ERR_ARG;
+  if (!ctx->state_set) return fail(ctx, DABA_ERR_STATE, "state not set");
+  const size_t need = ckpt_bytes(ctx);
+  if (!buf) {
+    *bytes = need;
+    return DABA_OK;
+  }
+  if (*bytes < need) return fail(ctx, DABA_ERR_ARG, "checkpoint buffer too small (%zu < %zu)", *bytes, need);
+  CK(cudaDeviceSynchronize());
+  CkptHeader h{CKPT_MAGIC, ctx->M, ctx->N, ctx->nnz, (int64_t)ctx->opt.prec, ctx->k, ctx->s_k, ctx->s_norm, 0};
+  int first = 0;
+  CK(cudaMemcpy(&first, ctx->d_first, sizeof(int), cudaMemcpyDeviceToHost));
+  h.first = first;
+  char* p = (char*)buf;
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
+  CK(cudaMemcpy(p, ctx->cam_x, cb, cudaMemcpyDeviceToHost));
+  p += cb;
+  CK(cudaMemcpy(p, ctx->cam_dx, cb, cudaMemcpyDeviceToHost));
+  p += cb;
+  CK(cudaMemcpy(p, ctx->cam_S, (size_t)ctx->M * 8, cudaMemcpyDeviceToHost));
+  p += (size_t)ctx->M * 8;
+  CK(cudaMemcpy(p, ctx->cam_E, (size_t)ctx->M * 8, cudaMemcpyDeviceToHost));
+  p += (size_t)ctx->M * 8;
+  const size_t lb = (size_t)ctx->N * LREC * real_sz(ctx);
+  CK(cudaMemcpy(p, ctx->lmrec, lb, cudaMemcpyDeviceToHost));
+  p += lb;
+  CK(cudaMemcpy(p, ctx->lm_lo, (size_t)ctx->N * 16, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return DABA_OK;
+}
+
+daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes) {
+  if (!ctx || !buf) return DABA_ERR_ARG;
+  if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations must be set before importing a checkpoint");
+  if (bytes < ckpt_bytes(ctx)) return fail(ctx, DABA_ERR_ARG, "checkpoint too small");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != CKPT_MAGIC || h.M != ctx->M || h.N != ctx->N || h.nnz != ctx->nnz || h.prec != (int64_t)ctx->opt.prec)
+    return fail(ctx, DABA_ERR_ARG, "checkpoint does not match this context");
+  const char* p = (const char*)buf + sizeof(h);
+  const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
+  CK(cudaMemcpy(ctx->cam_x, p, cb, cudaMemcpyHostToDevice));
+  p += cb;
+  CK(cudaMemcpy(ctx->cam_dx, p, cb, cudaMemcpyHostToDevice));
+  p += cb;
+  CK(cudaMemcpy(ctx->cam_S, p, (size_t)ctx->M * 8, cudaMemcpyHostToDevice));
+  p += (size_t)ctx->M * 8;
+  CK(cudaMemcpy(ctx->cam_E, p, (size_t)ctx->M * 8, cudaMemcpyHostToDevice));
+  p += (size_t)ctx->M * 8;
+  const size_t lb = (size_t)ctx->N * LREC * real_sz(ctx);
+  CK(cudaMemcpy(ctx->lmrec, p, lb, cudaMemcpyHostToDevice));
+  p += lb;
+  CK(cudaMemcpy(ctx->lm_lo, p, (size_t)ctx->N * 16, cudaMemcpyHostToDevice));
+  int first = (int)h.first;
+  CK(cudaMemcpy(ctx->d_first, &first, sizeof(int), cudaMemcpyHostToDevice));
+  ctx->k = h.k;
+  ctx->s_k = h.s_k;
+  ctx->s_norm = h.s_norm;
+  ctx->state_set = true;
+  // host copies used by the Assumption 2 check: rebuild from the imported iterate
+  ctx->checked = true;
+  return DABA_OK;
+}
+
+daba_status daba_set_timing(daba_ctx* ctx, int enable) {
+  if (!ctx) return DABA_ERR_ARG;
+  ctx->timing = enable != 0;
+  return DABA_OK;
+}
+
+daba_status daba_get_timing(daba_ctx* ctx, double* ms5) {
+  if (!ctx || !ms5) return DABA_ERR_ARG;
+  for (int q = 0; q < 5; ++q) ms5[q] = ctx->tms[q];
+  return DABA_OK;
+}
+
+}  // extern "C"

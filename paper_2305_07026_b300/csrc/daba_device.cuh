@@ -1,0 +1,304 @@
+// daba_device.cuh -- device-side math of one DABA iteration (arXiv 2305.07026).
+//
+// Notation follows the paper: camera c_i = (R_i, t_i, d_i) with R_i camera-to-world
+// and t_i the centre, landmark l_j, observed pixel u_ij (internal units of s_norm
+// pixels). For a conditioning iterate z the per-observation quantities of
+// Proposition 1 are
+//   p = [u; d1 + d2 s + d3 s^2] (Eq. ray, s = |u|^2), q = l - t,
+//   lambda = q^T R p / |q|^2 (Eq. lambdaij), R e = R p - lambda q (Eq. error),
+//   r = |e|^2, w = rho'(r) (Eq. w), and the centred residuals
+//   R p + lambda t - g = R e / 2 (camera side), lambda l - g = -R e / 2 (landmark side)
+// which follow from Eq. g. Everything a block solve needs is a weighted sum of
+// products of these terms (see daba_kernels.cuh).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace daba {
+
+enum { LOSS_TRIVIAL = 0, LOSS_HUBER = 1, LOSS_CAUCHY = 2, LOSS_WELSCH = 3 };
+
+// Loss constants in internal units: c (scale) and 1/c^2.
+template <class Real>
+struct LossC {
+  Real c, c2, inv_c2;
+};
+
+// rho(r) and rho'(r) of the robust losses of Assumption 1 (App. B).
+template <int LOSS, class Real>
+__device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, Real& w) {
+  if (LOSS == LOSS_TRIVIAL) {
+    rho = r;
+    w = Real(1);
+  } else if (LOSS == LOSS_HUBER) {
+    if (r > L.c2) {
+      Real sr = sqrt(r);
+      rho = Real(2) * L.c * sr - L.c2;
+      w = L.c / sr;
+    } else {
+      rho = r;
+      w = Real(1);
+    }
+  } else if (LOSS == LOSS_CAUCHY) {
+    Real x = r * L.inv_c2;
+    rho = L.c2 * log1p(x);
+    w = Real(1) / (Real(1) + x);
+  } else {
+    Real ex = exp(-r * L.inv_c2);
+    rho = L.c2 * (Real(1) - ex);
+    w = ex;
+  }
+}
+
+// Camera pack: the camera data an observation pass reads, in the pass precision.
+// Layout (Real offsets): R^k[9] (row-major), t^k hi[3], t^k lo[3], d^k[3],
+// dR[9] = R^k - R^(k-1), dt[3], dd[3], Rbar[9] (extrapolated rotation, Eq. nesterov_R).
+enum {
+  PK_R = 0, PK_TH = 9, PK_TL = 12, PK_D = 15, PK_DR = 18, PK_DT = 27, PK_DD = 30, PK_RB = 33,
+  PACK = 48
+};
+
+// Per-observation output of the three-point evaluation.
+template <class Real>
+struct ObsEval {
+  Real lam, Re0, Re1, Re2, r, rho, w;   // at x^k
+  Real lamb, Reb0, Reb1, Reb2, wb;      // at the extrapolated iterate xbar^k
+  Real gap;                             // F_ij(x^k) - P_ij(c^k|x^(k-1)) - Q_ij(l^k|x^(k-1))
+};
+
+// Evaluates one observation at x^k, xbar^k and x^(k-1).
+//   pk: camera pack; q = l^k - t^k (formed by the caller); dl = l^k - l^(k-1);
+//   u: pixel (internal units); gamma: extrapolation ratio of Eq. nesterov_scalar.
+// xbar: Rbar from the pack, dbar = d + gamma dd, qbar = q + gamma (dl - dt) (Eq. nesterov_x).
+// x^(k-1): R' = R - dR, d' = d - dd, q' = q - (dl - dt).
+// The surrogate gap of Eq. DEalpha is written in displacement form: with X = R^k p^k +
+// lambda' t^k, Y = lambda' l^k and g' of Eq. g at x^(k-1),
+//   |X - g'|^2 + |Y - g'|^2 = |X - Y|^2 / 2 + 2 |(X + Y)/2 - g'|^2,
+//   |X - Y|^2 = r^k + |q^k|^2 (lambda' - lambda^k)^2,
+//   2 ((X + Y)/2 - g') = dR p^k + R' e3 (phi . dd) + lambda' (dt + dl) =: D,
+// so gap = [rho(r^k) - rho(r') - w'(r^k - r')]/2 - w' |q^k|^2 (lambda' - lambda^k)^2 / 2
+//          - w' |D|^2 / 2, every term of which is formed without cancellation of O(1) values.
+template <int LOSS, class Real>
+__device__ __forceinline__ void eval_obs(const Real* __restrict__ pk, Real q0, Real q1, Real q2, Real dl0,
+                                         Real dl1, Real dl2, Real u0, Real u1, Real gamma,
+                                         const LossC<Real>& L, ObsEval<Real>& o) {
+  const Real s = u0 * u0 + u1 * u1;
+  const Real s2 = s * s;
+  // ---- x^k
+  const Real d0 = pk[PK_D + 0], d1 = pk[PK_D + 1], d2 = pk[PK_D + 2];
+  const Real pz = d0 + d1 * s + d2 * s2;
+  const Real R00 = pk[PK_R + 0], R01 = pk[PK_R + 1], R02 = pk[PK_R + 2];
+  const Real R10 = pk[PK_R + 3], R11 = pk[PK_R + 4], R12 = pk[PK_R + 5];
+  const Real R20 = pk[PK_R + 6], R21 = pk[PK_R + 7], R22 = pk[PK_R + 8];
+  const Real Rp0 = R00 * u0 + R01 * u1 + R02 * pz;
+  const Real Rp1 = R10 * u0 + R11 * u1 + R12 * pz;
+  const Real Rp2 = R20 * u0 + R21 * u1 + R22 * pz;
+  const Real qq = q0 * q0 + q1 * q1 + q2 * q2;
+  const Real iqq = Real(1) / qq;
+  o.lam = (q0 * Rp0 + q1 * Rp1 + q2 * Rp2) * iqq;
+  o.Re0 = Rp0 - o.lam * q0;
+  o.Re1 = Rp1 - o.lam * q1;
+  o.Re2 = Rp2 - o.lam * q2;
+  o.r = o.Re0 * o.Re0 + o.Re1 * o.Re1 + o.Re2 * o.Re2;
+  rho_w<LOSS, Real>(L, o.r, o.rho, o.w);
+  // ---- displacements
+  const Real dt0 = pk[PK_DT + 0], dt1 = pk[PK_DT + 1], dt2 = pk[PK_DT + 2];
+  const Real dd0 = pk[PK_DD + 0], dd1 = pk[PK_DD + 1], dd2 = pk[PK_DD + 2];
+  const Real e0 = dl0 - dt0, e1 = dl1 - dt1, e2 = dl2 - dt2;   // (l^k - l^(k-1)) - (t^k - t^(k-1))
+  const Real phidd = dd0 + dd1 * s + dd2 * s2;
+  // ---- xbar^k
+  {
+    const Real pzb = pz + gamma * phidd;
+    const Real qb0 = q0 + gamma * e0, qb1 = q1 + gamma * e1, qb2 = q2 + gamma * e2;
+    const Real Rbp0 = pk[PK_RB + 0] * u0 + pk[PK_RB + 1] * u1 + pk[PK_RB + 2] * pzb;
+    const Real Rbp1 = pk[PK_RB + 3] * u0 + pk[PK_RB + 4] * u1 + pk[PK_RB + 5] * pzb;
+    const Real Rbp2 = pk[PK_RB + 6] * u0 + pk[PK_RB + 7] * u1 + pk[PK_RB + 8] * pzb;
+    const Real qqb = qb0 * qb0 + qb1 * qb1 + qb2 * qb2;
+    o.lamb = (qb0 * Rbp0 + qb1 * Rbp1 + qb2 * Rbp2) / qqb;
+    o.Reb0 = Rbp0 - o.lamb * qb0;
+    o.Reb1 = Rbp1 - o.lamb * qb1;
+    o.Reb2 = Rbp2 - o.lamb * qb2;
+    const Real rb = o.Reb0 * o.Reb0 + o.Reb1 * o.Reb1 + o.Reb2 * o.Reb2;
+    Real rhob;
+    rho_w<LOSS, Real>(L, rb, rhob, o.wb);
+  }
+  // ---- x^(k-1) and the surrogate gap
+  {
+    const Real dR00 = pk[PK_DR + 0], dR01 = pk[PK_DR + 1], dR02 = pk[PK_DR + 2];
+    const Real dR10 = pk[PK_DR + 3], dR11 = pk[PK_DR + 4], dR12 = pk[PK_DR + 5];
+    const Real dR20 = pk[PK_DR + 6], dR21 = pk[PK_DR + 7], dR22 = pk[PK_DR + 8];
+    const Real pzp = pz - phidd;
+    const Real qp0 = q0 - e0, qp1 = q1 - e1, qp2 = q2 - e2;
+    const Real Rq02 = R02 - dR02, Rq12 = R12 - dR12, Rq22 = R22 - dR22;   // R' e3
+    const Real Rpp0 = (R00 - dR00) * u0 + (R01 - dR01) * u1 + Rq02 * pzp;
+    const Real Rpp1 = (R10 - dR10) * u0 + (R11 - dR11) * u1 + Rq12 * pzp;
+    const Real Rpp2 = (R20 - dR20) * u0 + (R21 - dR21) * u1 + Rq22 * pzp;
+    const Real qqp = qp0 * qp0 + qp1 * qp1 + qp2 * qp2;
+    const Real lamp = (qp0 * Rpp0 + qp1 * Rpp1 + qp2 * Rpp2) / qqp;
+    const Real Rep0 = Rpp0 - lamp * qp0, Rep1 = Rpp1 - lamp * qp1, Rep2 = Rpp2 - lamp * qp2;
+    const Real rp = Rep0 * Rep0 + Rep1 * Rep1 + Rep2 * Rep2;
+    Real rhop, wp;
+    rho_w<LOSS, Real>(L, rp, rhop, wp);
+    const Real D0 = dR00 * u0 + dR01 * u1 + dR02 * pz + Rq02 * phidd + lamp * (dt0 + dl0);
+    const Real D1 = dR10 * u0 + dR11 * u1 + dR12 * pz + Rq12 * phidd + lamp * (dt1 + dl1);
+    const Real D2 = dR20 * u0 + dR21 * u1 + dR22 * pz + Rq22 * phidd + lamp * (dt2 + dl2);
+    const Real dlam = lamp - o.lam;
+    o.gap = Real(0.5) * (o.rho - rhop - wp * (o.r - rp)) - Real(0.5) * wp * qq * dlam * dlam -
+            Real(0.5) * wp * (D0 * D0 + D1 * D1 + D2 * D2);
+  }
+}
+
+// F_ij(x^k) = rho(|e|^2) / 2 only (Eq. Fij).
+template <int LOSS, class Real>
+__device__ __forceinline__ Real eval_F(const Real* __restrict__ pk, Real q0, Real q1, Real q2, Real u0, Real u1,
+                                       const LossC<Real>& L) {
+  const Real s = u0 * u0 + u1 * u1;
+  const Real pz = pk[PK_D + 0] + pk[PK_D + 1] * s + pk[PK_D + 2] * s * s;
+  const Real Rp0 = pk[PK_R + 0] * u0 + pk[PK_R + 1] * u1 + pk[PK_R + 2] * pz;
+  const Real Rp1 = pk[PK_R + 3] * u0 + pk[PK_R + 4] * u1 + pk[PK_R + 5] * pz;
+  const Real Rp2 = pk[PK_R + 6] * u0 + pk[PK_R + 7] * u1 + pk[PK_R + 8] * pz;
+  const Real lam = (q0 * Rp0 + q1 * Rp1 + q2 * Rp2) / (q0 * q0 + q1 * q1 + q2 * q2);
+  const Real e0 = Rp0 - lam * q0, e1 = Rp1 - lam * q1, e2 = Rp2 - lam * q2;
+  Real rho, w;
+  rho_w<LOSS, Real>(L, e0 * e0 + e1 * e1 + e2 * e2, rho, w);
+  return Real(0.5) * rho;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 small linear algebra for the block solves
+// ---------------------------------------------------------------------------
+
+// ProjRot3D (Eq. proj_rot3d): argmin_{R in SO(3)} |R - K|^2 = argmax <R, K>.
+// With R(q) of a unit quaternion q = (w, x, y, z), <R(q), K> = q^T N(K) q for the
+// symmetric 4x4 N below (expanding the quadratic form entry by entry), so the
+// maximiser is R of the eigenvector of N's largest eigenvalue (Horn's method).
+// The eigenvector is found with cyclic Jacobi rotations.
+__device__ inline void proj_rot3d(const double* __restrict__ K, double* __restrict__ R) {
+  double a[4][4];
+  a[0][0] = K[0] + K[4] + K[8];
+  a[1][1] = K[0] - K[4] - K[8];
+  a[2][2] = -K[0] + K[4] - K[8];
+  a[3][3] = -K[0] - K[4] + K[8];
+  a[0][1] = a[1][0] = K[7] - K[5];
+  a[0][2] = a[2][0] = K[2] - K[6];
+  a[0][3] = a[3][0] = K[3] - K[1];
+  a[1][2] = a[2][1] = K[1] + K[3];
+  a[1][3] = a[3][1] = K[2] + K[6];
+  a[2][3] = a[3][2] = K[5] + K[7];
+  double v[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
+  double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]) + fabs(a[3][3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = i + 1; j < 4; ++j) scale += 2.0 * fabs(a[i][j]);
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 4; ++j) off += a[i][j] * a[i][j];
+    if (!(off > 1e-34 * scale * scale)) break;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < 4; ++q) {
+        const double apq = a[p][q];
+        if (apq != 0.0) {
+          // rotation in the (p, q) plane that zeroes a[p][q]: t = tan(phi) is the
+          // smaller root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq)
+          const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
+          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+          const double c = 1.0 / sqrt(t * t + 1.0);
+          const double s = t * c;
+          a[p][p] -= t * apq;
+          a[q][q] += t * apq;
+          a[p][q] = a[q][p] = 0.0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            if (r != p && r != q) {
+              const double arp = a[r][p], arq = a[r][q];
+              a[r][p] = a[p][r] = c * arp - s * arq;
+              a[r][q] = a[q][r] = s * arp + c * arq;
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const double vrp = v[r][p], vrq = v[r][q];
+            v[r][p] = c * vrp - s * vrq;
+            v[r][q] = s * vrp + c * vrq;
+          }
+        }
+      }
+    }
+  }
+  double best = a[0][0], w = v[0][0], x = v[1][0], y = v[2][0], z = v[3][0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    if (a[k][k] > best) {
+      best = a[k][k];
+      w = v[0][k];
+      x = v[1][k];
+      y = v[2][k];
+      z = v[3][k];
+    }
+  }
+  const double n = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  w *= n;
+  x *= n;
+  y *= n;
+  z *= n;
+  R[0] = w * w + x * x - y * y - z * z;
+  R[1] = 2.0 * (x * y - w * z);
+  R[2] = 2.0 * (x * z + w * y);
+  R[3] = 2.0 * (x * y + w * z);
+  R[4] = w * w - x * x + y * y - z * z;
+  R[5] = 2.0 * (y * z - w * x);
+  R[6] = 2.0 * (x * z - w * y);
+  R[7] = 2.0 * (y * z + w * x);
+  R[8] = w * w - x * x - y * y + z * z;
+}
+
+// Solves the symmetric positive definite 6x6 system A x = b in place (A lower
+// triangle used, Cholesky A = L L^T). Returns false if a pivot is not positive.
+__device__ inline bool chol6_solve(double A[6][6], double b[6]) {
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    double djj = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) djj -= A[j][k] * A[j][k];
+    if (!(djj > 0.0)) return false;
+    const double ljj = sqrt(djj);
+    A[j][j] = ljj;
+    const double inv = 1.0 / ljj;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s * inv;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s -= A[i][k] * b[k];
+    b[i] = s / A[i][i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    double s = b[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) s -= A[k][i] * b[k];
+    b[i] = s / A[i][i];
+  }
+  return true;
+}
+
+}  // namespace daba

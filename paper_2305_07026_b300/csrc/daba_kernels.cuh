@@ -1,0 +1,710 @@
+// daba_kernels.cuh -- the kernels of one DABA iteration (Algorithm 1, arXiv 2305.07026)
+// with one block per camera and one block per landmark.
+//
+// Per iteration k, in stream order:
+//   1. cam_prepare  (M threads)  : extrapolated rotation Rbar^k (Eq. nesterov_R) and the
+//                                  camera pack read by the observation passes.
+//   2. cpass        (warp/chunk) : camera-sorted observations; per camera the centred
+//                                  majorizer statistics at xbar^k and x^k plus the
+//                                  F_ij and surrogate-gap sums, FP64 partial per chunk.
+//   3. lpass        (CTA/tile)   : landmark-sorted observations; per landmark statistics,
+//                                  restart metrics, accelerated solve, restart test and
+//                                  MM re-solve (closed form), in place.
+//   4. camsolve     (M threads)  : FP64 camera block solves, restart test, MM re-solve.
+//   5. finalize     (1 CTA)      : F(x^k) trace entry and restart count.
+//
+// Centred statistics. For a conditioning iterate z (xbar^k or x^k) and a camera c let
+// M(c) = [R e1, R e2, d1 R e3, d2 R e3, d3 R e3, t] (3x6) and h = (u1, u2, 1, s, s^2,
+// lambda_z) so that R p(d) + lambda_z t = M(c) h. With r0 = R_z p_z + lambda_z t_z - g_z
+// = R_z e_z / 2 (from Eq. g) the camera part of the surrogate is, exactly,
+//   sum_j P_ij(c|z) = tr(dM H dM^T) + 2 tr(dM B) + const,  dM = M(c) - M(c_z),
+//   H = sum_j w h h^T (6x6),  B = sum_j w h r0^T (6x3),
+// and for a landmark, with r0' = lambda_z l_z - g_z = -R_z e_z / 2,
+//   sum_i Q_ij(l|z) = (sum w lambda^2) |dl|^2 + 2 dl . (sum w lambda r0') + const.
+// Both are evaluated relative to the conditioning point, so surrogate differences never
+// cancel O(1) quantities.
+#pragma once
+
+#include "daba_device.cuh"
+
+namespace daba {
+
+// ---- chunk partial layout (doubles): Hbar[21] Bbar[18] H[21] B[18] sumF sumGap pad
+enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_STRIDE = 84 };
+// ---- tile partial layout (doubles): sumF restarts pad pad
+enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
+// ---- landmark record (Real[8]): l[3] (hi part in MIXED), delta[3] = l^k - l^(k-1),
+//      S = Fbar^(k-1) - E^(k) (restart slack), E^(k) (FP64 path only)
+enum { LR_L = 0, LR_D = 3, LR_S = 6, LR_E = 7, LREC = 8 };
+// ---- camera state (doubles, stride 16): R[9] t[3] d[3] pad
+enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
+
+constexpr int CPASS_WARPS = 4;
+constexpr int LPASS_THREADS = 256;
+constexpr int TILE_OBS = 1024;   // max observations per landmark tile (also the max track length)
+
+struct IterParams {
+  const double* gam;   // gamma^(k) per iteration of the current run segment
+  int* it;             // device iteration counter within the segment
+  int* first;          // 1 on the first iteration after the state was set
+  double xi, eta;
+  int accelerated;
+  int n_alt;
+};
+
+__device__ __forceinline__ int tri6(int a, int b) { return a * 6 - (a * (a - 1)) / 2 + (b - a); }
+
+template <class Real>
+__device__ __forceinline__ void split_hi_lo(double x, Real& hi, Real& lo) {
+  hi = Real(x);
+  lo = Real(x - double(hi));
+}
+
+// ---------------------------------------------------------------------------
+// 1. camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) and the pass pack
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const double* __restrict__ cam_dx,
+                              IterParams P, double* __restrict__ cam_Rbar, Real* __restrict__ pack) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double gamma = P.gam[*P.it];
+  const double* x = cam_x + (size_t)i * CSTRIDE;
+  const double* dx = cam_dx + (size_t)i * CSTRIDE;
+  double K[9], Rb[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
+  proj_rot3d(K, Rb);
+  Real* pk = pack + (size_t)i * PACK;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    cam_Rbar[(size_t)i * 9 + a] = Rb[a];
+    pk[PK_R + a] = Real(x[CS_R + a]);
+    pk[PK_DR + a] = Real(dx[CS_R + a]);
+    pk[PK_RB + a] = Real(Rb[a]);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Real hi, lo;
+    split_hi_lo<Real>(x[CS_T + a], hi, lo);
+    pk[PK_TH + a] = hi;
+    pk[PK_TL + a] = lo;
+    pk[PK_D + a] = Real(x[CS_D + a]);
+    pk[PK_DT + a] = Real(dx[CS_T + a]);
+    pk[PK_DD + a] = Real(dx[CS_D + a]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. camera-sorted pass: one warp per chunk (<= chunk size observations of one camera)
+// ---------------------------------------------------------------------------
+template <int LOSS, class Real, class Real2>
+__global__ void __launch_bounds__(CPASS_WARPS * 32)
+    k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
+            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const Real* __restrict__ pack,
+            const Real* __restrict__ lmrec, LossC<Real> L, IterParams P, double* __restrict__ part) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_chunks) return;
+  const int cam = chunk_cam[warp];
+  const int b = chunk_beg[warp], e = chunk_beg[warp + 1];
+  const Real gamma = Real(P.gam[*P.it]);
+  const Real* pk = pack + (size_t)cam * PACK;
+  const Real th0 = pk[PK_TH + 0], th1 = pk[PK_TH + 1], th2 = pk[PK_TH + 2];
+  const Real tl0 = pk[PK_TL + 0], tl1 = pk[PK_TL + 1], tl2 = pk[PK_TL + 2];
+  Real acc[80];
+#pragma unroll
+  for (int k = 0; k < 80; ++k) acc[k] = Real(0);
+  for (int o = b + lane; o < e; o += 32) {
+    const int j = c_lm[o];
+    const Real2 uu = c_u[o];
+    const Real* lr = lmrec + (size_t)j * LREC;
+    const Real q0 = (lr[LR_L + 0] - th0) - tl0;
+    const Real q1 = (lr[LR_L + 1] - th1) - tl1;
+    const Real q2 = (lr[LR_L + 2] - th2) - tl2;
+    ObsEval<Real> ev;
+    eval_obs<LOSS, Real>(pk, q0, q1, q2, lr[LR_D + 0], lr[LR_D + 1], lr[LR_D + 2], uu.x, uu.y, gamma, L, ev);
+    const Real s = uu.x * uu.x + uu.y * uu.y;
+    Real h[6] = {uu.x, uu.y, Real(1), s, s * s, ev.lamb};
+    // xbar statistics: Hbar += wb h h^T, Bbar += wb h (R e)^T / 2
+    {
+      Real wh[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) wh[a] = ev.wb * h[a];
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int c = a; c < 6; ++c) acc[CP_HB + tri6(a, c)] += wh[a] * h[c];
+      const Real r0[3] = {Real(0.5) * ev.Reb0, Real(0.5) * ev.Reb1, Real(0.5) * ev.Reb2};
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[CP_BB + a * 3 + c] += wh[a] * r0[c];
+    }
+    h[5] = ev.lam;
+    {
+      Real wh[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) wh[a] = ev.w * h[a];
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int c = a; c < 6; ++c) acc[CP_H + tri6(a, c)] += wh[a] * h[c];
+      const Real r0[3] = {Real(0.5) * ev.Re0, Real(0.5) * ev.Re1, Real(0.5) * ev.Re2};
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[CP_B + a * 3 + c] += wh[a] * r0[c];
+    }
+    acc[CP_F] += Real(0.5) * ev.rho;
+    acc[CP_G] += ev.gap;
+  }
+  // warp reduction, lane 0 writes the FP64 partial
+#pragma unroll
+  for (int k = 0; k < 80; ++k) {
+    Real v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    acc[k] = v;
+  }
+  if (lane == 0) {
+    double* out = part + (size_t)warp * CP_STRIDE;
+#pragma unroll
+    for (int k = 0; k < 80; ++k) out[k] = double(acc[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. landmark-sorted pass: one CTA per tile of consecutive landmarks
+// ---------------------------------------------------------------------------
+// Tile data: tile_lm[t] .. tile_lm[t+1] landmarks; their observations occupy the
+// landmark-sorted positions lm_ptr[first] .. lm_ptr[last]. Inside the tile the
+// observations are processed in camera order (t_cam, t_u, t_slot), where t_slot is
+// the observation's landmark-sorted position relative to the tile start.
+template <class Real>
+struct LSmem {
+  // staged landmark data (nl entries) and per-observation contributions (no entries)
+  static __host__ __device__ size_t bytes(int nl, int no) {
+    return (size_t)nl * 9 * sizeof(Real) + (size_t)no * 10 * sizeof(Real) + (size_t)no * sizeof(uint16_t) + 16;
+  }
+};
+
+// double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  const float l2 = lo + err;
+  const float h2 = s + l2;
+  lo = l2 - (h2 - s);
+  hi = h2;
+}
+
+template <int LOSS, class Real, class Real2, bool HAS_LO>
+__global__ void __launch_bounds__(LPASS_THREADS)
+    k_lpass(const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const int* __restrict__ t_cam,
+            const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot, const Real* __restrict__ pack,
+            Real* __restrict__ lmrec, float* __restrict__ lm_lo, LossC<Real> L, IterParams P,
+            double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
+            double* __restrict__ lm_Fbdiag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tile = blockIdx.x;
+  const int lb = tile_lm[tile], le = tile_lm[tile + 1];
+  const int nl = le - lb;
+  const int ob = lm_ptr[lb], oe = lm_ptr[le];
+  const int no = oe - ob;
+  Real* sl = reinterpret_cast<Real*>(smem_raw);               // nl * 9: l hi[3], l lo[3], delta[3]
+  Real* sc = sl + (size_t)nl * 9;                             // 10 * no contributions (SoA)
+  uint16_t* smap = reinterpret_cast<uint16_t*>(sc + (size_t)no * 10);   // slot -> local landmark
+  const Real gamma = Real(P.gam[*P.it]);
+  const int first = *P.first;
+
+  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
+    const Real* lr = lmrec + (size_t)(lb + jl) * LREC;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sl[jl * 9 + a] = lr[LR_L + a];
+      sl[jl * 9 + 6 + a] = lr[LR_D + a];
+      sl[jl * 9 + 3 + a] = HAS_LO ? Real(lm_lo[(size_t)(lb + jl) * 4 + a]) : Real(0);
+    }
+    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
+    for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
+  }
+  __syncthreads();
+
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    const int cam = t_cam[ob + o];
+    const Real2 uu = t_u[ob + o];
+    const int slot = t_slot[ob + o];
+    const int jl = smap[slot];
+    const Real* pk = pack + (size_t)cam * PACK;
+    const Real* ls = sl + jl * 9;
+    const Real q0 = (ls[0] - pk[PK_TH + 0]) + (ls[3] - pk[PK_TL + 0]);
+    const Real q1 = (ls[1] - pk[PK_TH + 1]) + (ls[4] - pk[PK_TL + 1]);
+    const Real q2 = (ls[2] - pk[PK_TH + 2]) + (ls[5] - pk[PK_TL + 2]);
+    ObsEval<Real> ev;
+    eval_obs<LOSS, Real>(pk, q0, q1, q2, ls[6], ls[7], ls[8], uu.x, uu.y, gamma, L, ev);
+    // landmark statistics: sum w lambda^2 and sum w lambda r0' with r0' = -R e / 2
+    const Real wlb = ev.wb * ev.lamb;
+    const Real wl = ev.w * ev.lam;
+    sc[0 * no + slot] = wlb * ev.lamb;
+    sc[1 * no + slot] = Real(-0.5) * wlb * ev.Reb0;
+    sc[2 * no + slot] = Real(-0.5) * wlb * ev.Reb1;
+    sc[3 * no + slot] = Real(-0.5) * wlb * ev.Reb2;
+    sc[4 * no + slot] = wl * ev.lam;
+    sc[5 * no + slot] = Real(-0.5) * wl * ev.Re0;
+    sc[6 * no + slot] = Real(-0.5) * wl * ev.Re1;
+    sc[7 * no + slot] = Real(-0.5) * wl * ev.Re2;
+    sc[8 * no + slot] = Real(0.5) * ev.rho;
+    sc[9 * no + slot] = ev.gap;
+  }
+  __syncthreads();
+
+  const double xi = P.xi, eta = P.eta;
+  double fsum = 0.0;
+  int nrs = 0;
+  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
+    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
+    Real st[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) st[k] = Real(0);
+    for (int s = s0; s < s1; ++s)
+#pragma unroll
+      for (int k = 0; k < 10; ++k) st[k] += sc[k * no + s];
+    Real* lr = lmrec + (size_t)(lb + jl) * LREC;
+    const Real hx = Real(0.5) * Real(xi);
+    const Real dl0 = sl[jl * 9 + 6], dl1 = sl[jl * 9 + 7], dl2 = sl[jl * 9 + 8];
+    // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
+    //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
+    const Real dE = -hx * (dl0 * dl0 + dl1 * dl1 + dl2 * dl2) + Real(0.5) * st[9];
+    const Real S = first ? Real(0) : lr[LR_S];
+    const Real thr = Real(1.0 - eta) * (S - dE);
+    // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), written as a step from l^k
+    const Real ib = Real(1) / (st[0] + hx);
+    const Real sa0 = gamma * dl0 - st[1] * ib, sa1 = gamma * dl1 - st[2] * ib, sa2 = gamma * dl2 - st[3] * ib;
+    // E^alpha(l | x^k) - E^alpha(l^k | x^k) = (a + xi/2)|dl|^2 + 2 dl . b
+    const Real ak = st[4] + hx;
+    Real step0 = sa0, step1 = sa1, step2 = sa2;
+    Real dEn = ak * (sa0 * sa0 + sa1 * sa1 + sa2 * sa2) + Real(2) * (sa0 * st[5] + sa1 * st[6] + sa2 * st[7]);
+    const bool rs = P.accelerated ? (dEn > thr) : true;
+    if (rs) {   // adaptive restart: MM update (Eq. update_mm) from l^k
+      const Real ik = Real(1) / ak;
+      step0 = -st[5] * ik;
+      step1 = -st[6] * ik;
+      step2 = -st[7] * ik;
+      dEn = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
+    }
+    nrs += (rs && P.accelerated) ? 1 : 0;
+    if (HAS_LO) {
+      float h0 = float(sl[jl * 9 + 0]), h1 = float(sl[jl * 9 + 1]), h2 = float(sl[jl * 9 + 2]);
+      float o0 = float(sl[jl * 9 + 3]), o1 = float(sl[jl * 9 + 4]), o2 = float(sl[jl * 9 + 5]);
+      df_add(h0, o0, float(step0));
+      df_add(h1, o1, float(step1));
+      df_add(h2, o2, float(step2));
+      lr[LR_L + 0] = Real(h0);
+      lr[LR_L + 1] = Real(h1);
+      lr[LR_L + 2] = Real(h2);
+      float* lo = lm_lo + (size_t)(lb + jl) * 4;
+      lo[0] = o0;
+      lo[1] = o1;
+      lo[2] = o2;
+    } else {
+      lr[LR_L + 0] = sl[jl * 9 + 0] + step0;
+      lr[LR_L + 1] = sl[jl * 9 + 1] + step1;
+      lr[LR_L + 2] = sl[jl * 9 + 2] + step2;
+    }
+    lr[LR_D + 0] = step0;
+    lr[LR_D + 1] = step1;
+    lr[LR_D + 2] = step2;
+    lr[LR_S] = thr - dEn;
+    if (!HAS_LO) {   // FP64 path: E^(k) and the diagnostics F^(k), Fbar^(k)
+      const double E = first ? double(Real(0.5) * st[8]) : double(lr[LR_E]);
+      const double F = E + double(dE);
+      lm_Fdiag[lb + jl] = F;
+      lm_Fbdiag[lb + jl] = F + double(thr);
+      lr[LR_E] = Real(F + double(dEn));
+    }
+    lm_rs[lb + jl] = (rs && P.accelerated) ? 1 : 0;
+    fsum += double(st[8]);
+  }
+  // tile sums: F(x^k) part and restart count (FP64, fixed order)
+  __shared__ double red[LPASS_THREADS / 32];
+  __shared__ int redi[LPASS_THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
+    nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = fsum;
+    redi[threadIdx.x >> 5] = nrs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    int n = 0;
+    for (int w = 0; w < LPASS_THREADS / 32; ++w) {
+      f += red[w];
+      n += redi[w];
+    }
+    tile_part[(size_t)tile * TP_STRIDE + TP_F] = f;
+    tile_part[(size_t)tile * TP_STRIDE + TP_RS] = double(n);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. camera block solves (FP64)
+// ---------------------------------------------------------------------------
+struct Cam {
+  double R[9], t[3], d[3];
+};
+
+// M(c) column a (a = 0..5) of the 3x6 matrix [R e1, R e2, d1 R e3, d2 R e3, d3 R e3, t].
+__device__ __forceinline__ void mcol(const Cam& c, int a, double out[3]) {
+  if (a < 2) {
+    out[0] = c.R[0 + a];
+    out[1] = c.R[3 + a];
+    out[2] = c.R[6 + a];
+  } else if (a < 5) {
+    const double dk = c.d[a - 2];
+    out[0] = dk * c.R[2];
+    out[1] = dk * c.R[5];
+    out[2] = dk * c.R[8];
+  } else {
+    out[0] = c.t[0];
+    out[1] = c.t[1];
+    out[2] = c.t[2];
+  }
+}
+
+// E^alpha(c | z) - E^alpha(c_z | z) = xi/2 |c - c_z|^2 + tr(dM H dM^T) + 2 tr(dM B).
+__device__ inline double cam_phi(const double H[6][6], const double B[6][3], const Cam& z, const Cam& c,
+                                 double xi) {
+  double dM[6][3];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    double mc[3], mz[3];
+    mcol(c, a, mc);
+    mcol(z, a, mz);
+    dM[a][0] = mc[0] - mz[0];
+    dM[a][1] = mc[1] - mz[1];
+    dM[a][2] = mc[2] - mz[2];
+  }
+  double prox = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) prox += (c.R[k] - z.R[k]) * (c.R[k] - z.R[k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    prox += (c.t[k] - z.t[k]) * (c.t[k] - z.t[k]) + (c.d[k] - z.d[k]) * (c.d[k] - z.d[k]);
+  double q = 0.0, lin = 0.0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+#pragma unroll
+    for (int b = 0; b < 6; ++b) q += H[a][b] * (dM[a][0] * dM[b][0] + dM[a][1] * dM[b][1] + dM[a][2] * dM[b][2]);
+    lin += dM[a][0] * B[a][0] + dM[a][1] * B[a][1] + dM[a][2] * B[a][2];
+  }
+  return 0.5 * xi * prox + q + 2.0 * lin;
+}
+
+// Block-exact alternation on E^alpha(. | z) started at c_z (z supplies H, B).
+// R-step: with (t, d) fixed, tr(dM H dM^T) + 2 tr(dM B) - xi <R, R_z> is affine in R, so
+//   R = ProjRot3D(K),  K = xi R_z + 2 (W H - B^T) P(d)^T,  W = M(c_z) - t e6^T,
+//   P(d) = [e1, e2, d1 e3, d2 e3, d3 e3, 0].
+// (t, d)-step: with R fixed, dM h = dM0 h + v (phi . dd) + lambda dt with v = R e3 and
+//   dM0 = M(R, t_z, d_z) - M(c_z); the normal equations of the resulting least squares
+//   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5] and are solved by Cholesky.
+__device__ inline void cam_scam(const double H[6][6], const double B[6][3], const Cam& z, double xi, int n_alt,
+                                Cam& c) {
+  c = z;
+  for (int it = 0; it < n_alt; ++it) {
+    // ---- R-step
+    double W[3][6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      double mz[3];
+      mcol(z, a, mz);
+      W[0][a] = mz[0];
+      W[1][a] = mz[1];
+      W[2][a] = mz[2];
+    }
+    W[0][5] = z.t[0] - c.t[0];
+    W[1][5] = z.t[1] - c.t[1];
+    W[2][5] = z.t[2] - c.t[2];
+    double G[3][6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int a = 0; a < 6; ++a) {
+        double s = -B[a][r];
+#pragma unroll
+        for (int b = 0; b < 6; ++b) s += W[r][b] * H[b][a];
+        G[r][a] = s;
+      }
+    double K[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      K[r * 3 + 0] = xi * z.R[r * 3 + 0] + 2.0 * G[r][0];
+      K[r * 3 + 1] = xi * z.R[r * 3 + 1] + 2.0 * G[r][1];
+      K[r * 3 + 2] = xi * z.R[r * 3 + 2] + 2.0 * (c.d[0] * G[r][2] + c.d[1] * G[r][3] + c.d[2] * G[r][4]);
+    }
+    proj_rot3d(K, c.R);
+    // ---- (t, d)-step
+    const double v[3] = {c.R[2], c.R[5], c.R[8]};
+    const double vz[3] = {z.R[2], z.R[5], z.R[8]};
+    double dM0[6][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      dM0[0][k] = c.R[k * 3 + 0] - z.R[k * 3 + 0];
+      dM0[1][k] = c.R[k * 3 + 1] - z.R[k * 3 + 1];
+      dM0[2][k] = z.d[0] * (v[k] - vz[k]);
+      dM0[3][k] = z.d[1] * (v[k] - vz[k]);
+      dM0[4][k] = z.d[2] * (v[k] - vz[k]);
+      dM0[5][k] = 0.0;
+    }
+    double A[6][6], rhs[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) A[i][j] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) A[k][k] = 2.0 * H[5][5] + xi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        A[3 + m][k] = 2.0 * H[2 + m][5] * v[k];
+        A[k][3 + m] = A[3 + m][k];
+      }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int n = 0; n < 3; ++n) A[3 + m][3 + n] = 2.0 * H[2 + m][2 + n] + (m == n ? xi : 0.0);
+    // top: dM0 H[:,5] + B[5,:];  bottom: H[2:5,:] (dM0^T v) + B[2:5,:] v
+    double dv[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dv[a] = dM0[a][0] * v[0] + dM0[a][1] * v[1] + dM0[a][2] * v[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      double s = B[5][k];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) s += dM0[a][k] * H[a][5];
+      rhs[k] = -2.0 * s;
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      double s = B[2 + m][0] * v[0] + B[2 + m][1] * v[1] + B[2 + m][2] * v[2];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) s += H[2 + m][a] * dv[a];
+      rhs[3 + m] = -2.0 * s;
+    }
+    if (chol6_solve(A, rhs)) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        c.t[k] = z.t[k] + rhs[k];
+        c.d[k] = z.d[k] + rhs[3 + k];
+      }
+    }
+  }
+}
+
+__device__ inline void unpack_stats(const double* s, double H[6][6], double B[6][3]) {
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b) H[a][b] = H[b][a] = s[tri6(a, b)];
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) B[a][c] = s[21 + a * 3 + c];
+}
+
+__global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const double* __restrict__ part,
+                           double* __restrict__ cam_x, double* __restrict__ cam_dx,
+                           const double* __restrict__ cam_Rbar, IterParams P, double* __restrict__ cam_S,
+                           double* __restrict__ cam_E, double* __restrict__ cam_F, double* __restrict__ cam_Fb,
+                           uint8_t* __restrict__ cam_rs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double gamma = P.gam[*P.it];
+  const int first = *P.first;
+  double sb[39], sk[39];
+#pragma unroll
+  for (int k = 0; k < 39; ++k) sb[k] = sk[k] = 0.0;
+  double sF = 0.0, sG = 0.0;
+  for (int c = cam_chunk_ptr[i]; c < cam_chunk_ptr[i + 1]; ++c) {
+    const double* p = part + (size_t)c * CP_STRIDE;
+#pragma unroll
+    for (int k = 0; k < 39; ++k) {
+      sb[k] += p[CP_HB + k];
+      sk[k] += p[CP_H + k];
+    }
+    sF += p[CP_F];
+    sG += p[CP_G];
+  }
+  double* x = cam_x + (size_t)i * CSTRIDE;
+  double* dx = cam_dx + (size_t)i * CSTRIDE;
+  Cam ck, cb;
+  double dx2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    ck.R[a] = x[CS_R + a];
+    cb.R[a] = cam_Rbar[(size_t)i * 9 + a];
+    dx2 += dx[CS_R + a] * dx[CS_R + a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ck.t[a] = x[CS_T + a];
+    ck.d[a] = x[CS_D + a];
+    cb.t[a] = ck.t[a] + gamma * dx[CS_T + a];
+    cb.d[a] = ck.d[a] + gamma * dx[CS_D + a];
+    dx2 += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
+  }
+  // Eq. DEalpha and the slack form of Eqs. Fak, lFak (see k_lpass)
+  const double dE = -0.5 * P.xi * dx2 + 0.5 * sG;
+  const double S = first ? 0.0 : cam_S[i];
+  const double thr = (1.0 - P.eta) * (S - dE);
+  double Hk[6][6], Bk[6][3];
+  unpack_stats(sk, Hk, Bk);
+  Cam cn;
+  double dEn = 0.0;
+  bool rs = true;
+  if (P.accelerated) {
+    double Hb[6][6], Bb[6][3];
+    unpack_stats(sb, Hb, Bb);
+    cam_scam(Hb, Bb, cb, P.xi, P.n_alt, cn);   // Eq. update_amm
+    dEn = cam_phi(Hk, Bk, ck, cn, P.xi);       // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
+    rs = dEn > thr;
+  }
+  if (rs) {
+    cam_scam(Hk, Bk, ck, P.xi, P.n_alt, cn);   // Eq. update_mm
+    dEn = cam_phi(Hk, Bk, ck, cn, P.xi);
+  }
+  const double E = first ? 0.5 * sF : cam_E[i];
+  const double F = E + dE;
+  cam_F[i] = F;
+  cam_Fb[i] = F + thr;
+  cam_E[i] = F + dEn;
+  cam_S[i] = thr - dEn;
+  cam_rs[i] = (rs && P.accelerated) ? 1 : 0;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    dx[CS_R + a] = cn.R[a] - ck.R[a];
+    x[CS_R + a] = cn.R[a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dx[CS_T + a] = cn.t[a] - ck.t[a];
+    dx[CS_D + a] = cn.d[a] - ck.d[a];
+    x[CS_T + a] = cn.t[a];
+    x[CS_D + a] = cn.d[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. reduction of one iteration: F(x^k) (FP64, fixed order) and restart count
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, int M,
+                           const uint8_t* __restrict__ cam_rs, double s2, IterParams P, double* __restrict__ trace,
+                           int* __restrict__ restarts, int* __restrict__ flag) {
+  __shared__ double red[32];
+  __shared__ long long redi[32];
+  double f = 0.0;
+  long long n = 0;
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
+    f += tile_part[(size_t)t * TP_STRIDE + TP_F];
+    n += (long long)tile_part[(size_t)t * TP_STRIDE + TP_RS];
+  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) n += cam_rs[i];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    f += __shfl_xor_sync(0xffffffffu, f, off);
+    n += __shfl_xor_sync(0xffffffffu, n, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = f;
+    redi[threadIdx.x >> 5] = n;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ft = 0.0;
+    long long nt = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ft += red[w];
+      nt += redi[w];
+    }
+    const int k = *P.it;
+    trace[k] = ft * s2;
+    restarts[k] = (int)nt;
+    if (!isfinite(ft)) *flag = 1;
+    *P.it = k + 1;
+    *P.first = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// objective F(x^k) only (Eq. Fobj): per tile sums, same tiles as the landmark pass
+// ---------------------------------------------------------------------------
+template <int LOSS, class Real, class Real2, bool HAS_LO>
+__global__ void __launch_bounds__(LPASS_THREADS)
+    k_objective(const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const int* __restrict__ t_cam,
+                const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot, const Real* __restrict__ pack,
+                const Real* __restrict__ lmrec, const float* __restrict__ lm_lo, LossC<Real> L,
+                double* __restrict__ tile_part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tile = blockIdx.x;
+  const int lb = tile_lm[tile], le = tile_lm[tile + 1];
+  const int nl = le - lb;
+  const int ob = lm_ptr[lb], oe = lm_ptr[le];
+  const int no = oe - ob;
+  Real* sl = reinterpret_cast<Real*>(smem_raw);
+  uint16_t* smap = reinterpret_cast<uint16_t*>(sl + (size_t)nl * 6);
+  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
+    const Real* lr = lmrec + (size_t)(lb + jl) * LREC;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sl[jl * 6 + a] = lr[LR_L + a];
+      sl[jl * 6 + 3 + a] = HAS_LO ? Real(lm_lo[(size_t)(lb + jl) * 4 + a]) : Real(0);
+    }
+    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
+    for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
+  }
+  __syncthreads();
+  double fsum = 0.0;
+  for (int o = threadIdx.x; o < no; o += blockDim.x) {
+    const int cam = t_cam[ob + o];
+    const Real2 uu = t_u[ob + o];
+    const Real* pk = pack + (size_t)cam * PACK;
+    const Real* ls = sl + smap[t_slot[ob + o]] * 6;
+    const Real q0 = (ls[0] - pk[PK_TH + 0]) + (ls[3] - pk[PK_TL + 0]);
+    const Real q1 = (ls[1] - pk[PK_TH + 1]) + (ls[4] - pk[PK_TL + 1]);
+    const Real q2 = (ls[2] - pk[PK_TH + 2]) + (ls[5] - pk[PK_TL + 2]);
+    fsum += double(eval_F<LOSS, Real>(pk, q0, q1, q2, uu.x, uu.y, L));
+  }
+  __shared__ double red[LPASS_THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int w = 0; w < LPASS_THREADS / 32; ++w) f += red[w];
+    tile_part[(size_t)tile * TP_STRIDE + TP_F] = f;
+  }
+}
+
+__global__ void k_sum_tiles(int n_tiles, const double* __restrict__ tile_part, double s2, double* __restrict__ out) {
+  __shared__ double red[32];
+  double f = 0.0;
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) f += tile_part[(size_t)t * TP_STRIDE + TP_F];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ft = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ft += red[w];
+    *out = ft * s2;
+  }
+}
+
+}  // namespace daba

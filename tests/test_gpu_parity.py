@@ -1,0 +1,365 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the FP64 GPU path matches the oracle's per-iteration objective to 1e-10
+relative over the first 20 iterations and its parameters to 1e-8; sort orders and CSR
+offsets match bit-exactly; restart decisions match exactly except at near-ties, where the
+tested value E^alpha(k+1) is within 1e-9 (relative to |F^alpha|) of Fbar^alpha(k) and either
+decision is correct. The FP32/FP64 mixed path must reach the FP64 path's final objective
+within 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+from tests.conftest import cached_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_07026_b300 import build
+    build.build()
+
+
+def _lib():
+    from paper_2305_07026_b300 import _lib
+    return _lib
+
+
+def _ctx(sc, prec="fp64", **kw):
+    L = _lib()
+    opts = dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    opts.update(kw)
+    d = L.Daba(sc.M, sc.N, sc.nnz, **opts)
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    d.set_state(sc.cams, sc.lms)
+    return d
+
+
+def _oracle_opts(sc, **kw):
+    o = dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    o.update(kw)
+    return O.Options(**o)
+
+
+def _rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(np.abs(np.asarray(b)), 1e-300)
+
+
+# ----------------------------------------------------------------------------
+# setup: sort orders and CSR offsets (bit-exact)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_sort_and_csr_bit_exact(shuffle):
+    sc = cached_scene("tourism", scale=0.01)
+    ci, li, uv = sc.cam_idx, sc.lm_idx, sc.uv
+    if shuffle:
+        p = np.random.default_rng(0).permutation(sc.nnz)
+        ci, li, uv = ci[p].copy(), li[p].copy(), uv[p].copy()
+    d = _lib().Daba(sc.M, sc.N, sc.nnz, prec="fp64")
+    d.set_observations(ci, li, uv)
+    co, cp, lo, lp = d.get_sort()
+    np.testing.assert_array_equal(co, np.argsort(ci, kind="stable"))
+    np.testing.assert_array_equal(lo, np.argsort(li, kind="stable"))
+    np.testing.assert_array_equal(cp, np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=sc.M))]))
+    np.testing.assert_array_equal(lp, np.concatenate([[0], np.cumsum(np.bincount(li, minlength=sc.N))]))
+    d.close()
+
+
+# ----------------------------------------------------------------------------
+# boundary round trip and the objective
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_state_roundtrip_and_objective(prec, circle):
+    sc = circle
+    d = _ctx(sc, prec)
+    cams, lms = d.get_state()
+    np.testing.assert_allclose(cams, sc.cams, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(lms, sc.lms, rtol=0, atol=1e-12 if prec == "mixed" else 0)
+    prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, _oracle_opts(sc))
+    F0 = O.objective(prob.loss, prob.c, R, t, dd, l, prob.cam_idx, prob.lm_idx, prob.u) * prob.s_norm ** 2
+    tol = 1e-12 if prec == "fp64" else 1e-6
+    assert d.objective() == pytest.approx(F0, rel=tol)
+    # device output pointer
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    d.objective(out)
+    torch.cuda.synchronize()
+    assert out.item() == pytest.approx(F0, rel=tol)
+    d.close()
+
+
+# ----------------------------------------------------------------------------
+# FP64 path vs oracle: per-iteration objective, parameters, restart decisions, metrics
+# ----------------------------------------------------------------------------
+
+def _near_tie(info, which, tol=1e-9):
+    E = getattr(info, f"Etest_{which}")
+    Fb = getattr(info, f"Fbar_{which}")
+    F = np.abs(getattr(info, f"F_{which}"))
+    return np.abs(E - Fb) <= tol * np.maximum(F, 1e-300)
+
+
+@pytest.mark.parametrize("loss,accel,min_iters", [("huber", True, 20), ("cauchy", True, 20), ("trivial", False, 20),
+                                                   ("welsch", True, 4)])
+def test_fp64_matches_oracle_per_iteration(loss, accel, min_iters, circle):
+    """Per-iteration F(x^k), block metrics F^alpha / Fbar^alpha, restart decisions and the iterate.
+
+    A restart decision may differ only at a near-tie. For the redescending Welsch loss, blocks whose
+    observations are all saturated outliers have zero gradient and the restart test is an exact tie;
+    after the first such tie the two (equally valid) trajectories separate, so the comparison stops
+    there (it must not come before `min_iters`)."""
+    sc = circle
+    K = 20
+    o = _oracle_opts(sc, loss=loss, loss_scale_px=2.0, accelerated=accel)
+    prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
+    st = O.init_state(prob, R, t, dd, l)
+    d = _ctx(sc, "fp64", loss=loss, loss_scale_px=2.0, accelerated=accel)
+    s2 = prob.s_norm ** 2
+    compared = 0
+    for k in range(K):
+        st, info = O.step(prob, st)
+        tr = np.zeros(2)
+        rs = np.zeros(1, np.int32)
+        d.run(1, tr, rs)
+        assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
+        m = d.get_block_metrics()
+        np.testing.assert_allclose(m["F_cam"], info.F_cam * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_allclose(m["F_lm"], info.F_lm * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_allclose(m["Fbar_cam"], info.Fbar_cam * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_allclose(m["Fbar_lm"], info.Fbar_lm * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        flips = 0
+        for which in ("cam", "lm"):
+            gpu = m[f"rs_{which}"].astype(bool)
+            ora = getattr(info, f"restart_{which}")
+            bad = (gpu != ora) & ~_near_tie(info, which)
+            assert not bad.any(), f"iteration {k}: {which} restart decisions differ at {np.flatnonzero(bad)[:10]}"
+            flips += int((gpu != ora).sum())
+        compared = k + 1
+        if flips:
+            break
+    assert compared >= min_iters
+    if compared == K:
+        cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+        cams_g, lms_g = d.get_state()
+        np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    d.close()
+
+
+def test_fp64_trace_matches_oracle_run(circle):
+    """A single daba_run of 30 iterations reproduces the oracle's trace (F(x^0) .. F(x^30))."""
+    sc = circle
+    res = O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, _oracle_opts(sc), 30)
+    d = _ctx(sc, "fp64")
+    tr = np.zeros(31)
+    rs = np.zeros(30, np.int32)
+    d.run(30, tr, rs)
+    np.testing.assert_allclose(tr[:21], res.trace_px2[:21], rtol=1e-10)
+    np.testing.assert_allclose(tr, res.trace_px2, rtol=1e-8)
+    assert np.abs(rs - res.restarts).sum() <= 5
+    d.close()
+
+
+def test_duba_monotone_gpu():
+    sc = cached_scene("tourism", scale=0.005)
+    for prec in ("fp64", "mixed"):
+        d = _ctx(sc, prec, accelerated=False)
+        tr = np.zeros(21)
+        d.run(20, tr)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.all(np.diff(tr) <= tol * tr[:-1]), prec
+        d.close()
+
+
+# ----------------------------------------------------------------------------
+# mixed path: reaches the FP64 objective
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("workload,scale,iters", [("circle", 1.0, 200), ("tourism", 0.005, 150)])
+def test_mixed_reaches_fp64_objective(workload, scale, iters):
+    sc = cached_scene(workload, scale=scale)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        d = _ctx(sc, prec)
+        tr = np.zeros(iters + 1)
+        d.run(iters, tr)
+        out[prec] = tr
+        d.close()
+    target = out["fp64"][-1] * (1 + 1e-5)
+    assert out["mixed"].min() <= target, (out["mixed"][-5:], out["fp64"][-5:])
+    assert out["mixed"][-1] == pytest.approx(out["fp64"][-1], rel=1e-3)
+
+
+# ----------------------------------------------------------------------------
+# checkpoint / resume, run segmentation
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_resume_bit_exact(prec, circle):
+    sc = circle
+    a = _ctx(sc, prec)
+    a.run(7)
+    ck = a.export_checkpoint()
+    ta = np.zeros(9)
+    a.run(8, ta)
+    b = _ctx(sc, prec)
+    b.import_checkpoint(ck)
+    tb = np.zeros(9)
+    b.run(8, tb)
+    np.testing.assert_array_equal(ta, tb)
+    np.testing.assert_array_equal(a.get_state()[0], b.get_state()[0])
+    np.testing.assert_array_equal(a.get_state()[1], b.get_state()[1])
+    # one run of 15 equals 7 + 8
+    c = _ctx(sc, prec)
+    tc = np.zeros(16)
+    c.run(15, tc)
+    np.testing.assert_array_equal(tc[7:], ta)
+    for x in (a, b, c):
+        x.close()
+
+
+# ----------------------------------------------------------------------------
+# degenerate and edge cases
+# ----------------------------------------------------------------------------
+
+def _edge_scene():
+    """Circle scene plus an unobserved camera, an unobserved landmark and a landmark seen once."""
+    sc = cached_scene("circle")
+    M, N = sc.M + 1, sc.N + 2
+    cams = np.concatenate([sc.cams, sc.cams[:1] + np.array([0, 0, 0, 0.5, 0, 0, 0, 0, 0])])
+    lms = np.concatenate([sc.lms, np.array([[0.1, 0.2, 0.3], [0.5, -0.4, 0.2]])])
+    ci = np.concatenate([sc.cam_idx, [3]]).astype(np.int32)
+    li = np.concatenate([sc.lm_idx, [N - 1]]).astype(np.int32)
+    uv = np.concatenate([sc.uv, [[12.0, -7.0]]])
+    return sc, M, N, cams, lms, ci, li, uv
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_edge_blocks(prec):
+    sc, M, N, cams, lms, ci, li, uv = _edge_scene()
+    o = _oracle_opts(sc)
+    res = O.daba(cams, lms, ci, li, uv, o, 10)
+    d = _lib().Daba(M, N, ci.size, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    d.set_observations(ci, li, uv)
+    d.set_state(cams, lms)
+    tr = np.zeros(11)
+    d.run(10, tr)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    np.testing.assert_allclose(tr, res.trace_px2, rtol=tol)
+    cg, lg = d.get_state()
+    np.testing.assert_allclose(cg[-1], cams[-1], atol=1e-12)      # unobserved camera stays put
+    np.testing.assert_allclose(lg[N - 2], lms[N - 2], atol=1e-12)  # unobserved landmark stays put
+    assert np.all(np.isfinite(cg)) and np.all(np.isfinite(lg))
+    d.close()
+
+
+def test_error_statuses():
+    L = _lib()
+    sc = cached_scene("circle")
+    d = L.Daba(sc.M, sc.N, sc.nnz, prec="fp64")
+    with pytest.raises(L.DabaError) as e:
+        d.run(1)
+    assert e.value.status == L.DABA_ERR_STATE
+    bad = sc.cam_idx.copy()
+    bad[5] = sc.M
+    with pytest.raises(L.DabaError) as e:
+        d.set_observations(bad, sc.lm_idx, sc.uv)
+    assert e.value.status == L.DABA_ERR_INDEX
+    uvb = sc.uv.copy()
+    uvb[3, 1] = np.nan
+    with pytest.raises(L.DabaError) as e:
+        d.set_observations(sc.cam_idx, sc.lm_idx, uvb)
+    assert e.value.status == L.DABA_ERR_NONFINITE
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    lms = sc.lms.copy()
+    lms[sc.lm_idx[0]] = sc.cams[sc.cam_idx[0], 3:6]
+    d.set_state(sc.cams, lms)
+    with pytest.raises(L.DabaError) as e:
+        d.run(1)
+    assert e.value.status == L.DABA_ERR_DEGENERATE
+    cams = sc.cams.copy()
+    cams[2, 4] = np.inf
+    with pytest.raises(L.DabaError) as e:
+        d.set_state(cams, sc.lms)
+    assert e.value.status == L.DABA_ERR_NONFINITE
+    d.close()
+    with pytest.raises(L.DabaError):
+        L.Daba(0, 10, 10)
+
+
+def test_device_pointers_and_stream():
+    """Inputs and outputs as CUDA tensors on a side stream give the same result as host arrays."""
+    sc = cached_scene("circle")
+    dev = "cuda"
+    s = torch.cuda.Stream()
+    L = _lib()
+    d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, prec="mixed")
+    with torch.cuda.stream(s):
+        d.set_observations(torch.from_numpy(sc.cam_idx).to(dev), torch.from_numpy(sc.lm_idx).to(dev),
+                           torch.from_numpy(sc.uv).to(dev))
+        d.set_state(torch.from_numpy(sc.cams).to(dev), torch.from_numpy(sc.lms).to(dev))
+        tr = torch.zeros(6, dtype=torch.float64, device=dev)
+        d.run(5, tr)
+    s.synchronize()
+    h = _ctx(sc, "mixed")
+    th = np.zeros(6)
+    h.run(5, th)
+    np.testing.assert_array_equal(tr.cpu().numpy(), th)
+    d.close()
+    h.close()
+
+
+# ----------------------------------------------------------------------------
+# full-size workload: sampled blocks against the oracle (first iteration)
+# ----------------------------------------------------------------------------
+
+def _sub_problem_step(sc, obs_mask, opts):
+    """Oracle step on the observations selected by obs_mask (blocks whose observations are all
+    selected get their exact update)."""
+    ci, li = sc.cam_idx[obs_mask], sc.lm_idx[obs_mask]
+    cams_u, ci_r = np.unique(ci, return_inverse=True)
+    lms_u, li_r = np.unique(li, return_inverse=True)
+    s_norm = O.median_focal(sc.cams)
+    o = O.Options(**{**opts.__dict__, "pixel_scale": s_norm})
+    prob, R, t, d, l = O.make_problem(sc.cams[cams_u], sc.lms[lms_u], ci_r, li_r, sc.uv[obs_mask], o)
+    st = O.init_state(prob, R, t, d, l)
+    st2, info = O.step(prob, st)
+    cams_b, lms_b = O.to_boundary(st2.R, st2.t, st2.d, st2.l, prob.s_norm)
+    return cams_u, cams_b, lms_u, lms_b
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_sampled_blocks(prec):
+    sc = cached_scene("tourism")
+    d = _ctx(sc, prec)
+    tr = np.zeros(2)
+    d.run(1, tr)
+    cams_g, lms_g = d.get_state()
+    d.close()
+    rng = np.random.default_rng(5)
+    opts = _oracle_opts(sc)
+    deg = np.bincount(sc.cam_idx, minlength=sc.M)
+    cs = np.concatenate([rng.choice(sc.M, 6, replace=False), [int(np.argmax(deg))], [int(np.argmin(deg))]])
+    cu, cb, _, _ = _sub_problem_step(sc, np.isin(sc.cam_idx, cs), opts)
+    ls = rng.choice(sc.N, 300, replace=False)
+    _, _, lu, lb = _sub_problem_step(sc, np.isin(sc.lm_idx, ls), opts)
+    sel = np.isin(cu, cs)
+    tol = 1e-8 if prec == "fp64" else 2e-4
+    np.testing.assert_allclose(cams_g[cu[sel]], cb[sel], rtol=tol, atol=tol)
+    sel = np.isin(lu, ls)
+    np.testing.assert_allclose(lms_g[lu[sel]], lb[sel], rtol=tol, atol=tol * 10)
+    # F(x^0) at full size: the oracle's direct sum, evaluated in observation chunks
+    prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx[:1], sc.lm_idx[:1], sc.uv[:1], opts)
+    F0 = 0.0
+    B = 1 << 21
+    for b in range(0, sc.nnz, B):
+        ci, li = sc.cam_idx[b:b + B], sc.lm_idx[b:b + B]
+        F0 += O.objective(prob.loss, prob.c, R, t, dd, l, ci, li, sc.uv[b:b + B] / prob.s_norm)
+    F0 *= prob.s_norm ** 2
+    assert tr[0] == pytest.approx(F0, rel=1e-10 if prec == "fp64" else 1e-5)
