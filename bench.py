@@ -23,7 +23,11 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# the CPU baseline (the FP64 oracle) is reported for one host core: pin BLAS/OpenMP pools
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -212,9 +216,14 @@ def sub_problem(sc, frac_obs, seed=0):
 
 def cpu_oracle(sc, target_seconds, steps=None, warmup=0):
     """Times oracle iterations on a sample sized for ~target_seconds; returns (value, info)."""
-    from threadpoolctl import threadpool_limits
+    import contextlib
     from oracle import daba_oracle as O
-    with threadpool_limits(limits=1):
+    try:
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(limits=1)
+    except ImportError:   # numpy's element-wise work is single-threaded; only BLAS could thread
+        limit = contextlib.nullcontext()
+    with limit:
         # calibrate: ~7 us per observation-iteration on one core; sample for the budget
         per_obs = 8e-6
         n_steps = steps if steps is not None else 3
