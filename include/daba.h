@@ -155,6 +155,26 @@ daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
 /* Number of kernel launches the library issued in the last daba_run. */
 int64_t daba_last_launch_count(const daba_ctx* ctx);
 
+/* Objective F(x) in pixel^2 (Eq. Fobj) of caller-provided device arrays, allocating no
+ * device memory. The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a framework whose memory pool owns the device, a real-time loop
+ * that must not allocate, a plugin limited to the buffers it is handed).
+ *   cams (M x 9), lms (N x 3), cam_idx, lm_idx (nnz), uv (nnz x 2): as in daba_set_state and
+ *   daba_set_observations, but all of them, and `out` (one double), must be device memory.
+ *   loss is a daba_loss value; pixel_scale > 0 is the internal unit in pixels (the result
+ *   depends on it only through rounding).
+ * Its scratch is one file-scope __device__ array of about 2.4 MB that every GPU which loads
+ * the library holds until the process exits; it limits M to 16384 (DABA_ERR_ARG beyond that,
+ * as for other invalid sizes, options or host pointers). The first call on a device looks up
+ * that array's address with cudaGetSymbolAddress, so make the first call before any stream
+ * capture. All calls share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. Observation indices out of range, or a
+ * landmark at a camera centre (Assumption 2), make *out NaN instead of returning an error
+ * (the call does not wait for the GPU). Returns DABA_ERR_CUDA if a launch fails. */
+daba_status daba_objective_noalloc(int32_t M, int32_t N, int64_t nnz, const double* cams, const double* lms,
+                                   const int32_t* cam_idx, const int32_t* lm_idx, const double* uv, int32_t loss,
+                                   double loss_scale_px, double pixel_scale, double* out, void* stream);
+
 /* One-line description of the last error of this context (never NULL). */
 const char* daba_last_error(const daba_ctx* ctx);
 

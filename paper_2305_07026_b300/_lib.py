@@ -50,6 +50,8 @@ _SIGS = {
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
+    "daba_objective_noalloc": (_st, [_i32, _i32, _i64, _p, _p, _p, _p, _p, _i32, ctypes.c_double, ctypes.c_double,
+                                     _p, _p]),
     "daba_last_error": (ctypes.c_char_p, [_p]),
     "daba_destroy": (None, [_p]),
 }

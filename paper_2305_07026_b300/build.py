@@ -9,8 +9,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libdaba_b300.so")
-SOURCES = ["daba_abi.cu"]
-DEPS = ["daba_abi.cu", "daba_kernels.cuh", "daba_device.cuh"]
+SOURCES = ["daba_abi.cu", "daba_noalloc.cu"]
+DEPS = ["daba_abi.cu", "daba_noalloc.cu", "daba_kernels.cuh", "daba_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
