@@ -318,7 +318,7 @@ def run_ours(args, rank, world, local):
 
     # ---- roofline of the dominant kernel (per launch, live CUDA events)
     names = ["cam_prepare", "cpass", "lpass", "camsolve", "finalize"]
-    per_launch_ms = {n: kern_ms[i] / K for i, n in enumerate(names)}
+    per_launch_ms = {n: kern_ms[i] / (K if i else -(-K // 1024)) for i, n in enumerate(names)}
     dom = max(("cpass", "lpass"), key=lambda n: per_launch_ms[n])
     alg = algorithmic_bytes(sc, "mixed")[dom]
     pk = peaks()

@@ -146,8 +146,8 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
 
 /* Device-time breakdown of the last daba_run (milliseconds, summed over its
  * iterations) for the kernels of one iteration, in the order:
- * [0] camera prepare (extrapolation, Eq. nesterov_x), [1] camera-sorted observation pass,
- * [2] landmark-sorted observation pass + landmark solves, [3] camera solves, [4] reduction.
+ * [0] camera prepare of the first iteration (extrapolation, Eq. nesterov_x), [1] camera-sorted observation pass,
+ * [2] landmark-sorted observation pass + landmark solves, [3] camera solves + next extrapolation, [4] reduction.
  * Timing is recorded only when enabled with daba_set_timing(ctx, 1). */
 daba_status daba_set_timing(daba_ctx* ctx, int enable);
 daba_status daba_get_timing(daba_ctx* ctx, double* ms5);

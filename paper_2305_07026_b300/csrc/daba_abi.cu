@@ -24,12 +24,9 @@ namespace {
 
 constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: observations per warp chunk
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
-constexpr uint64_t CKPT_MAGIC = 0x44414241434b5031ull;   // "DABACKP1"
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
+constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
+constexpr int LR_L = 0;           // offset of l in the record
+constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
 
@@ -40,7 +37,7 @@ struct daba_ctx {
   std::string err;
   int dev = 0;
   // sizes of the schedules
-  int n_chunks = 0, n_tiles = 0, max_chunks = 0, max_tiles = 0;
+  int n_chunks = 0, n_tiles = 0, n_small_tiles = 0, max_chunks = 0, max_tiles = 0;
   bool obs_set = false, state_set = false, checked = false;
   double s_norm = 0.0, u_scale_uploaded = -1.0;
   double s_k = 1.0;   // Nesterov s^(k)
@@ -52,6 +49,8 @@ struct daba_ctx {
   std::vector<int32_t> h_cam_idx, h_lm_idx;
   std::vector<double> h_uv;
   std::vector<int32_t> h_c_order, h_cam_ptr, h_l_order, h_lm_ptr, h_t_order;
+  std::vector<int32_t> h_li_order;          // observations sorted by internal landmark id
+  std::vector<int32_t> h_lperm, h_linv;     // internal -> external landmark id and inverse
   std::vector<double> h_t;   // camera centres of the state last set (for the Asm. 2 check)
   std::vector<double> h_l;
   // device buffers
@@ -131,6 +130,9 @@ daba_status deliver(daba_ctx* ctx, void* dst, const void* src, size_t bytes, cud
 }
 
 bool is_mixed(const daba_ctx* c) { return c->opt.prec == DABA_MIXED; }
+
+// internal (device) index of external landmark j (identity until observations are set)
+inline size_t lm_internal(const daba_ctx* c, int j) { return c->h_linv.empty() ? (size_t)j : (size_t)c->h_linv[j]; }
 size_t real_sz(const daba_ctx* c) { return is_mixed(c) ? sizeof(float) : sizeof(double); }
 
 // ---- rotation parameterisation (boundary <-> R)
@@ -196,7 +198,7 @@ void upload_u(daba_ctx* ctx, cudaStream_t st, cudaError_t* err) {
     const int32_t i = ctx->h_c_order[o];
     cu[o].x = Real(ctx->h_uv[2 * (size_t)i] / s);
     cu[o].y = Real(ctx->h_uv[2 * (size_t)i + 1] / s);
-    const int32_t j = ctx->h_l_order[ctx->h_t_order[o]];
+    const int32_t j = ctx->h_li_order[ctx->h_t_order[o]];
     tu[o].x = Real(ctx->h_uv[2 * (size_t)j] / s);
     tu[o].y = Real(ctx->h_uv[2 * (size_t)j + 1] / s);
   }
@@ -263,29 +265,44 @@ template <int LOSS, class Real, class Real2, bool HAS_LO>
 cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
   const LossC<Real> L = loss_consts<Real>(ctx);
   const IterParams P = iter_params(ctx);
+  const int n_small = ctx->n_small_tiles, n_big = ctx->n_tiles - ctx->n_small_tiles;
   if (which == 1) {
     const int threads = CPASS_WARPS * 32;
     const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
     if (blocks > 0)
       k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
           ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
-          (const Real2*)ctx->c_u, (const Real*)ctx->pack, (const Real*)ctx->lmrec, L, P, (double*)ctx->chunk_part);
+          (const Real2*)ctx->c_u, (const V4<Real>*)ctx->pack, (const V4<Real>*)ctx->lmrec, L, P,
+          (double*)ctx->chunk_part);
   } else if (which == 2) {
-    const size_t smem = LSmem<Real>::bytes(TILE_OBS, TILE_OBS);
     auto kern = k_lpass<LOSS, Real, Real2, HAS_LO>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<ctx->n_tiles, LPASS_THREADS, smem, st>>>(
-        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam, (const Real2*)ctx->t_u,
-        (const uint16_t*)ctx->t_slot, (const Real*)ctx->pack, (Real*)ctx->lmrec, (float*)ctx->lm_lo, L, P,
-        (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
+    const int caps[2][2] = {{TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
+    const int t0[2] = {0, n_small}, nt[2] = {n_small, n_big};
+    for (int c = 0; c < 2; ++c) {
+      if (nt[c] == 0) continue;
+      const size_t smem = lpass_smem_bytes<Real>(caps[c][0], caps[c][1]);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<nt[c], LPASS_THREADS, smem, st>>>(
+          t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
+          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->pack, (V4<Real>*)ctx->lmrec,
+          (V4<float>*)ctx->lm_lo, L, P, (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd,
+          (double*)ctx->lm_Fbd);
+      if (c == 1) ctx->launches++;
+    }
   } else if (which == 6) {
-    const size_t smem = (size_t)TILE_OBS * 6 * sizeof(Real) + (size_t)TILE_OBS * sizeof(uint16_t) + 64;
     auto kern = k_objective<LOSS, Real, Real2, HAS_LO>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kern<<<ctx->n_tiles, LPASS_THREADS, smem, st>>>(
-        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam, (const Real2*)ctx->t_u,
-        (const uint16_t*)ctx->t_slot, (const Real*)ctx->pack, (const Real*)ctx->lmrec, (const float*)ctx->lm_lo, L,
-        (double*)ctx->tile_part);
+    const int caps[2][2] = {{TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
+    const int t0[2] = {0, n_small}, nt[2] = {n_small, n_big};
+    for (int c = 0; c < 2; ++c) {
+      if (nt[c] == 0) continue;
+      const size_t smem = (size_t)caps[c][1] * 2 * sizeof(V4<Real>) + (size_t)caps[c][0] * 2 + 16;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<nt[c], LPASS_THREADS, smem, st>>>(
+          t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
+          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->pack,
+          (const V4<Real>*)ctx->lmrec, (const V4<float>*)ctx->lm_lo, L, (double*)ctx->tile_part);
+      if (c == 1) ctx->launches++;
+    }
   }
   return cudaGetLastError();
 }
@@ -312,20 +329,28 @@ cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st) {
   const int blocks = (ctx->M + 127) / 128;
   if (is_mixed(ctx))
     k_cam_prepare<float><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
-                                                 (double*)ctx->cam_Rbar, (float*)ctx->pack);
+                                                 (double*)ctx->cam_Rbar, (V4<float>*)ctx->pack);
   else
     k_cam_prepare<double><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
-                                                  (double*)ctx->cam_Rbar, (double*)ctx->pack);
+                                                  (double*)ctx->cam_Rbar, (V4<double>*)ctx->pack);
   return cudaGetLastError();
 }
 
 cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
-  k_camsolve<<<(ctx->M + 63) / 64, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
-                                                (double*)ctx->cam_x, (double*)ctx->cam_dx, (const double*)ctx->cam_Rbar,
-                                                P, (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
-                                                (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs);
+  const int blocks = (ctx->M + 63) / 64;
+  if (is_mixed(ctx))
+    k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
+                                             (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
+                                             (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
+                                             (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (V4<float>*)ctx->pack);
+  else
+    k_camsolve<double><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
+                                              (const double*)ctx->chunk_part, (double*)ctx->cam_x,
+                                              (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
+                                              (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,
+                                              (uint8_t*)ctx->cam_rs, (V4<double>*)ctx->pack);
   return cudaGetLastError();
 }
 
@@ -338,11 +363,15 @@ cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// F(x^k) of the current state into d_obj (device double): prepare the pack (gamma is
-// irrelevant for F), per-tile sums, reduction.
-daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st) {
-  CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
-  CK(launch_prepare(ctx, st));
+// F(x^k) of the current state into d_obj (device double): per-tile sums and their
+// reduction. With prepare, the pack is first rebuilt from the state (gamma entry 0 is
+// read; it does not affect F).
+daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st, bool prepare) {
+  if (prepare) {
+    CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(ctx->d_gam, 0, sizeof(double), st));
+    CK(launch_prepare(ctx, st));
+  }
   CK(launch_pass(ctx, st, 6));
   ctx->launches++;
   k_sum_tiles<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->s_norm * ctx->s_norm,
@@ -416,7 +445,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   cudaGetDevice(&ctx->dev);
   const size_t R = real_sz(ctx);
   ctx->max_chunks = (int)(M + nnz / CHUNK_OBS + 1);
-  ctx->max_tiles = (int)(2 * ((nnz + N) / TILE_OBS) + 2);
+  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS) + nnz / TILE_OBS + 4);
 #define AL(field, bytes)                                   \
   if ((st = dalloc(ctx, &ctx->field, (bytes))) != DABA_OK) { \
     daba_ctx* c_ = ctx;                                    \
@@ -439,7 +468,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(cam_x, (size_t)M * CSTRIDE * 8);
   AL(cam_dx, (size_t)M * CSTRIDE * 8);
   AL(cam_Rbar, (size_t)M * 9 * 8);
-  AL(pack, (size_t)M * PACK * R);
+  AL(pack, (size_t)M * P4N * 4 * R);
   AL(cam_S, (size_t)M * 8);
   AL(cam_E, (size_t)M * 8);
   AL(cam_F, (size_t)M * 8);
@@ -452,7 +481,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(lm_Fbd, (size_t)N * 8);
   AL(chunk_part, (size_t)ctx->max_chunks * CP_STRIDE * 8);
   AL(tile_part, (size_t)ctx->max_tiles * TP_STRIDE * 8);
-  AL(d_gam, GSEG * 8);
+  AL(d_gam, (GSEG + 1) * 8);
   AL(d_it, 16);
   AL(d_first, 16);
   AL(d_flag, 16);
@@ -491,38 +520,60 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
     if (!std::isfinite(uvh[2 * o]) || !std::isfinite(uvh[2 * o + 1]))
       return fail(ctx, DABA_ERR_NONFINITE, "observation %lld has a non-finite pixel", (long long)o);
   }
+  const int M = ctx->M, N = ctx->N;
   std::vector<int32_t> c_order, cam_ptr, l_order, lm_ptr;
-  counting_sort(ci, ctx->M, c_order, cam_ptr);
-  counting_sort(li, ctx->N, l_order, lm_ptr);
-  for (int j = 0; j < ctx->N; ++j)
-    if (lm_ptr[j + 1] - lm_ptr[j] > TILE_OBS)
-      return fail(ctx, DABA_ERR_ARG, "landmark %d has %d observations (max %d)", j, lm_ptr[j + 1] - lm_ptr[j], TILE_OBS);
+  counting_sort(ci, M, c_order, cam_ptr);
+  counting_sort(li, N, l_order, lm_ptr);
+  for (int j = 0; j < N; ++j)
+    if (lm_ptr[j + 1] - lm_ptr[j] > MAX_TRACK)
+      return fail(ctx, DABA_ERR_ARG, "landmark %d has %d observations (max %d)", j, lm_ptr[j + 1] - lm_ptr[j], MAX_TRACK);
+  // internal landmark numbering: by the first camera that observes the landmark (landmarks
+  // seen by the same cameras become neighbours), landmarks with long tracks last
+  std::vector<int32_t> min_cam(N, M);
+  for (int64_t o = 0; o < n; ++o) min_cam[li[o]] = std::min(min_cam[li[o]], ci[o]);
+  std::vector<int32_t> lperm(N), linv(N);
+  for (int j = 0; j < N; ++j) lperm[j] = j;
+  auto is_big = [&](int j) { return lm_ptr[j + 1] - lm_ptr[j] > TILE_OBS; };
+  std::stable_sort(lperm.begin(), lperm.end(), [&](int32_t a, int32_t b) {
+    const bool ba = is_big(a), bb = is_big(b);
+    if (ba != bb) return bb;
+    return min_cam[a] < min_cam[b];
+  });
+  for (int q = 0; q < N; ++q) linv[lperm[q]] = q;
+  int n_small_lms = 0;
+  while (n_small_lms < N && !is_big(lperm[n_small_lms])) ++n_small_lms;
+  std::vector<int32_t> lii(n), li_order, lmi_ptr;
+  for (int64_t o = 0; o < n; ++o) lii[o] = linv[li[o]];
+  counting_sort(lii, N, li_order, lmi_ptr);
   // camera chunks
-  std::vector<int32_t> chunk_cam, chunk_beg, cam_chunk_ptr(ctx->M + 1, 0);
-  for (int i = 0; i < ctx->M; ++i) {
+  std::vector<int32_t> chunk_cam, chunk_beg, cam_chunk_ptr(M + 1, 0);
+  for (int i = 0; i < M; ++i) {
     cam_chunk_ptr[i] = (int32_t)chunk_cam.size();
     for (int b = cam_ptr[i]; b < cam_ptr[i + 1]; b += CHUNK_OBS) {
       chunk_cam.push_back(i);
       chunk_beg.push_back(b);
     }
   }
-  cam_chunk_ptr[ctx->M] = (int32_t)chunk_cam.size();
+  cam_chunk_ptr[M] = (int32_t)chunk_cam.size();
   chunk_beg.push_back((int32_t)n);
-  // landmark tiles: consecutive landmarks with at most TILE_OBS observations and landmarks
+  // landmark tiles over internal ids: small tiles of consecutive landmarks (at most TILE_OBS
+  // observations and TILE_LMS landmarks), then one big tile per long-track landmark
   std::vector<int32_t> tile_lm;
+  tile_lm.push_back(0);
   {
     int j = 0;
-    tile_lm.push_back(0);
-    while (j < ctx->N) {
+    while (j < n_small_lms) {
       int j2 = j, cnt = 0;
-      while (j2 < ctx->N && j2 - j < TILE_OBS && cnt + (lm_ptr[j2 + 1] - lm_ptr[j2]) <= TILE_OBS) {
-        cnt += lm_ptr[j2 + 1] - lm_ptr[j2];
+      while (j2 < n_small_lms && j2 - j < TILE_LMS && cnt + (lmi_ptr[j2 + 1] - lmi_ptr[j2]) <= TILE_OBS) {
+        cnt += lmi_ptr[j2 + 1] - lmi_ptr[j2];
         ++j2;
       }
       j = j2;
       tile_lm.push_back(j);
     }
   }
+  const int n_small_tiles = (int)tile_lm.size() - 1;
+  for (int j = n_small_lms; j < N; ++j) tile_lm.push_back(j + 1);
   const int n_tiles = (int)tile_lm.size() - 1;
   if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
     return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
@@ -530,26 +581,34 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   std::vector<int32_t> t_order(n), t_cam(n), c_lm(n);
   std::vector<uint16_t> t_slot(n);
   for (int t = 0; t < n_tiles; ++t) {
-    const int ob = lm_ptr[tile_lm[t]], oe = lm_ptr[tile_lm[t + 1]];
+    const int ob = lmi_ptr[tile_lm[t]], oe = lmi_ptr[tile_lm[t + 1]];
     for (int o = ob; o < oe; ++o) t_order[o] = o;
     std::sort(t_order.begin() + ob, t_order.begin() + oe, [&](int32_t a, int32_t b) {
-      const int32_t ca = ci[l_order[a]], cb = ci[l_order[b]];
+      const int32_t ca = ci[li_order[a]], cb = ci[li_order[b]];
       return ca != cb ? ca < cb : a < b;
     });
     for (int o = ob; o < oe; ++o) {
-      t_cam[o] = ci[l_order[t_order[o]]];
+      t_cam[o] = ci[li_order[t_order[o]]];
       t_slot[o] = (uint16_t)(t_order[o] - ob);
     }
   }
-  for (int64_t o = 0; o < n; ++o) c_lm[o] = li[c_order[o]];
+  for (int64_t o = 0; o < n; ++o) c_lm[o] = lii[c_order[o]];
+  // keep the current iterate (if any) across the renumbering; displacements and the
+  // restart metrics are reset (x^(k-1) = x^k, S = 0)
+  std::vector<double> keep_l;
+  if (ctx->state_set) {
+    daba_status s2 = DABA_OK;
+    keep_l.resize((size_t)N * 3);
+    if ((s2 = daba_get_state(ctx, nullptr, keep_l.data(), stream)) != DABA_OK) return s2;
+  }
   // upload
   CK(cudaMemcpyAsync(ctx->c_lm, c_lm.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->c_orig, c_order.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_ptr, cam_ptr.data(), (ctx->M + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_ptr, cam_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->chunk_cam, chunk_cam.data(), chunk_cam.size() * 4 + 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->chunk_beg, chunk_beg.data(), chunk_beg.size() * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (ctx->M + 1) * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->lm_ptr, lm_ptr.data(), (ctx->N + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->lm_ptr, lmi_ptr.data(), (N + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->t_cam, t_cam.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
@@ -557,6 +616,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
   ctx->n_tiles = n_tiles;
+  ctx->n_small_tiles = n_small_tiles;
   ctx->h_cam_idx.swap(ci);
   ctx->h_lm_idx.swap(li);
   ctx->h_uv.swap(uvh);
@@ -565,9 +625,20 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_l_order.swap(l_order);
   ctx->h_lm_ptr.swap(lm_ptr);
   ctx->h_t_order.swap(t_order);
+  ctx->h_li_order.swap(li_order);
+  ctx->h_lperm.swap(lperm);
+  ctx->h_linv.swap(linv);
   ctx->u_scale_uploaded = -1.0;
   ctx->obs_set = true;
   ctx->checked = false;
+  if (ctx->state_set) {
+    std::vector<double> cams((size_t)M * 9);
+    daba_status s2;
+    if ((s2 = daba_get_state(ctx, cams.data(), nullptr, stream)) != DABA_OK) return s2;
+    const double keep_scale = ctx->s_norm;
+    if ((s2 = daba_set_state(ctx, cams.data(), keep_l.data(), stream)) != DABA_OK) return s2;
+    ctx->s_norm = keep_scale;
+  }
   ctx->k = 0;
   ctx->s_k = 1.0;
   int one = 1;
@@ -624,20 +695,22 @@ daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms,
   CK(cudaMemcpyAsync(ctx->cam_E, zeros.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
   if (is_mixed(ctx)) {
     std::vector<float> rec((size_t)N * LREC, 0.f), lo((size_t)N * 4, 0.f);
-    for (int j = 0; j < N; ++j)
+    for (int j = 0; j < N; ++j) {
+      const size_t q = lm_internal(ctx, j);
       for (int a = 0; a < 3; ++a) {
         const double v = hl[(size_t)j * 3 + a];
         const float h = (float)v;
-        rec[(size_t)j * LREC + LR_L + a] = h;
-        lo[(size_t)j * 4 + a] = (float)(v - (double)h);
+        rec[q * LREC + LR_L + a] = h;
+        lo[q * 4 + a] = (float)(v - (double)h);
       }
+    }
     CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->lm_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   } else {
     std::vector<double> rec((size_t)N * LREC, 0.0);
     for (int j = 0; j < N; ++j)
-      for (int a = 0; a < 3; ++a) rec[(size_t)j * LREC + LR_L + a] = hl[(size_t)j * 3 + a];
+      for (int a = 0; a < 3; ++a) rec[lm_internal(ctx, j) * LREC + LR_L + a] = hl[(size_t)j * 3 + a];
     CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 8, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
@@ -665,51 +738,55 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   std::vector<double> trace((size_t)iters + 1);
   std::vector<int32_t> rs((size_t)std::max(iters, 1));
   int done = 0;
-  size_t evi = 0;
-  std::vector<double> gam(GSEG);
+  std::vector<double> gam(GSEG + 1);
   CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
   while (done < iters) {
     const int seg = std::min(GSEG, iters - done);
-    for (int j = 0; j < seg; ++j) {
-      const double s_next = (std::sqrt(4.0 * ctx->s_k * ctx->s_k + 1.0) + 1.0) / 2.0;
-      gam[j] = (ctx->s_k - 1.0) / s_next;
-      ctx->s_k = s_next;
+    // gamma^(k) .. gamma^(k+seg) (Eq. nesterov_scalar); the last one is the look-ahead used
+    // by the camera solve to extrapolate iteration k+seg
+    double sk = ctx->s_k;
+    for (int j = 0; j <= seg; ++j) {
+      const double s_next = (std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0;
+      gam[j] = (sk - 1.0) / s_next;
+      sk = s_next;
+      if (j == seg - 1) ctx->s_k = sk;
     }
-    CK(cudaMemcpyAsync(ctx->d_gam, gam.data(), seg * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_gam, gam.data(), (seg + 1) * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+    size_t evi = 0;
+    if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
+    CK(launch_prepare(ctx, st));
+    if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     for (int j = 0; j < seg; ++j) {
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi), st));
-      CK(launch_prepare(ctx, st));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 1), st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_pass(ctx, st, 1));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 2), st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_pass(ctx, st, 2));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 3), st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_camsolve(ctx, st));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 4), st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_finalize(ctx, st));
-      if (ctx->timing) {
-        CK(cudaEventRecord(ev(ctx, evi + 5), st));
-        evi += 6;
-      }
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     }
     CK(cudaMemcpyAsync(trace.data() + done, ctx->d_trace, seg * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ctx->timing) {
-      for (size_t b = 0; b < evi; b += 6)
-        for (int q = 0; q < 5; ++q) {
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, ctx->events[b + q], ctx->events[b + q + 1]);
-          ctx->tms[q] += ms;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]);
+      ctx->tms[0] += ms;
+      for (int j = 0; j < seg; ++j)
+        for (int q = 0; q < 4; ++q) {
+          const size_t b = 2 + (size_t)j * 5 + q;
+          cudaEventElapsedTime(&ms, ctx->events[b], ctx->events[b + 1]);
+          ctx->tms[1 + q] += ms;
         }
-      evi = 0;
     }
     done += seg;
     ctx->k += seg;
   }
   if (obj_trace) {
-    if ((s = enqueue_objective(ctx, st)) != DABA_OK) return s;
+    if ((s = enqueue_objective(ctx, st, iters == 0)) != DABA_OK) return s;
     CK(cudaMemcpyAsync(&trace[iters], ctx->d_obj, 8, cudaMemcpyDeviceToHost, st));
   } else {
     trace[iters] = 0.0;
@@ -733,7 +810,7 @@ daba_status daba_objective(daba_ctx* ctx, double* out, void* stream) {
   // gamma buffer entry 0 is read by the prepare kernel; any finite value will do
   double g0 = 0.0;
   CK(cudaMemcpyAsync(ctx->d_gam, &g0, 8, cudaMemcpyHostToDevice, st));
-  if ((s = enqueue_objective(ctx, st)) != DABA_OK) return s;
+  if ((s = enqueue_objective(ctx, st, true)) != DABA_OK) return s;
   if (is_device_ptr(out)) {
     CK(cudaMemcpyAsync(out, ctx->d_obj, 8, cudaMemcpyDeviceToDevice, st));
   } else {
@@ -773,15 +850,17 @@ daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* strea
       CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 4, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(lo.data(), ctx->lm_lo, lo.size() * 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
-      for (int j = 0; j < N; ++j)
+      for (int j = 0; j < N; ++j) {
+        const size_t q = lm_internal(ctx, j);
         for (int a = 0; a < 3; ++a)
-          hl[(size_t)j * 3 + a] = (double)rec[(size_t)j * LREC + LR_L + a] + (double)lo[(size_t)j * 4 + a];
+          hl[(size_t)j * 3 + a] = (double)rec[q * LREC + LR_L + a] + (double)lo[q * 4 + a];
+      }
     } else {
       std::vector<double> rec((size_t)N * LREC);
       CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int j = 0; j < N; ++j)
-        for (int a = 0; a < 3; ++a) hl[(size_t)j * 3 + a] = rec[(size_t)j * LREC + LR_L + a];
+        for (int a = 0; a < 3; ++a) hl[(size_t)j * 3 + a] = rec[lm_internal(ctx, j) * LREC + LR_L + a];
     }
     if ((s = deliver(ctx, lms, hl.data(), hl.size() * 8, st)) != DABA_OK) return s;
   }
@@ -797,25 +876,27 @@ daba_status daba_get_block_metrics(daba_ctx* ctx, double* F_cam, double* Fbar_ca
   const double s2 = ctx->s_norm * ctx->s_norm;
   const int M = ctx->M, N = ctx->N;
   daba_status s;
-  auto getd = [&](double* dst, const void* src, int n) -> daba_status {
-    std::vector<double> h(n);
+  // landmark arrays live in the internal order; `lm` maps them back to external ids
+  auto getd = [&](double* dst, const void* src, int n, bool lm) -> daba_status {
+    std::vector<double> h(n), o(n);
     CK(cudaMemcpyAsync(h.data(), src, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    for (double& v : h) v *= s2;
-    return deliver(ctx, dst, h.data(), (size_t)n * 8, st);
+    for (int j = 0; j < n; ++j) o[j] = s2 * h[lm ? lm_internal(ctx, j) : (size_t)j];
+    return deliver(ctx, dst, o.data(), (size_t)n * 8, st);
   };
-  auto getb = [&](uint8_t* dst, const void* src, int n) -> daba_status {
-    std::vector<uint8_t> h(n);
+  auto getb = [&](uint8_t* dst, const void* src, int n, bool lm) -> daba_status {
+    std::vector<uint8_t> h(n), o(n);
     CK(cudaMemcpyAsync(h.data(), src, (size_t)n, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return deliver(ctx, dst, h.data(), (size_t)n, st);
+    for (int j = 0; j < n; ++j) o[j] = h[lm ? lm_internal(ctx, j) : (size_t)j];
+    return deliver(ctx, dst, o.data(), (size_t)n, st);
   };
-  if (F_cam && (s = getd(F_cam, ctx->cam_F, M)) != DABA_OK) return s;
-  if (Fbar_cam && (s = getd(Fbar_cam, ctx->cam_Fb, M)) != DABA_OK) return s;
-  if (F_lm && (s = getd(F_lm, ctx->lm_Fd, N)) != DABA_OK) return s;
-  if (Fbar_lm && (s = getd(Fbar_lm, ctx->lm_Fbd, N)) != DABA_OK) return s;
-  if (rs_cam && (s = getb(rs_cam, ctx->cam_rs, M)) != DABA_OK) return s;
-  if (rs_lm && (s = getb(rs_lm, ctx->lm_rs, N)) != DABA_OK) return s;
+  if (F_cam && (s = getd(F_cam, ctx->cam_F, M, false)) != DABA_OK) return s;
+  if (Fbar_cam && (s = getd(Fbar_cam, ctx->cam_Fb, M, false)) != DABA_OK) return s;
+  if (F_lm && (s = getd(F_lm, ctx->lm_Fd, N, true)) != DABA_OK) return s;
+  if (Fbar_lm && (s = getd(Fbar_lm, ctx->lm_Fbd, N, true)) != DABA_OK) return s;
+  if (rs_cam && (s = getb(rs_cam, ctx->cam_rs, M, false)) != DABA_OK) return s;
+  if (rs_lm && (s = getb(rs_lm, ctx->lm_rs, N, true)) != DABA_OK) return s;
   return DABA_OK;
 }
 
@@ -834,7 +915,8 @@ daba_status daba_get_sort(daba_ctx* ctx, int32_t* cam_order, int32_t* cam_ptr, i
   if (cam_order && (s = geti(cam_order, ctx->c_orig, ctx->nnz)) != DABA_OK) return s;
   if (cam_ptr && (s = geti(cam_ptr, ctx->cam_ptr, ctx->M + 1)) != DABA_OK) return s;
   if (lm_order && (s = geti(lm_order, ctx->l_orig, ctx->nnz)) != DABA_OK) return s;
-  if (lm_ptr && (s = geti(lm_ptr, ctx->lm_ptr, ctx->N + 1)) != DABA_OK) return s;
+  // the device CSR runs over the internal landmark numbering; the external one is kept on the host
+  if (lm_ptr && (s = deliver(ctx, lm_ptr, ctx->h_lm_ptr.data(), (size_t)(ctx->N + 1) * 4, st)) != DABA_OK) return s;
   return DABA_OK;
 }
 

@@ -26,6 +26,13 @@ struct LossC {
   Real c, c2, inv_c2;
 };
 
+// Division and reciprocal square root: the FP32 path uses the fast approximate
+// instructions (a few ulp); FP64 is exact.
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float frsqrt(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double frsqrt(double a) { return 1.0 / sqrt(a); }
+
 // rho(r) and rho'(r) of the robust losses of Assumption 1 (App. B).
 template <int LOSS, class Real>
 __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, Real& w) {
@@ -34,9 +41,9 @@ __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, R
     w = Real(1);
   } else if (LOSS == LOSS_HUBER) {
     if (r > L.c2) {
-      Real sr = sqrt(r);
-      rho = Real(2) * L.c * sr - L.c2;
-      w = L.c / sr;
+      const Real is = frsqrt(r);
+      rho = Real(2) * L.c * (r * is) - L.c2;
+      w = L.c * is;
     } else {
       rho = r;
       w = Real(1);
@@ -44,7 +51,7 @@ __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, R
   } else if (LOSS == LOSS_CAUCHY) {
     Real x = r * L.inv_c2;
     rho = L.c2 * log1p(x);
-    w = Real(1) / (Real(1) + x);
+    w = fdiv(Real(1), Real(1) + x);
   } else {
     Real ex = exp(-r * L.inv_c2);
     rho = L.c2 * (Real(1) - ex);
@@ -52,13 +59,22 @@ __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, R
   }
 }
 
-// Camera pack: the camera data an observation pass reads, in the pass precision.
-// Layout (Real offsets): R^k[9] (row-major), t^k hi[3], t^k lo[3], d^k[3],
-// dR[9] = R^k - R^(k-1), dt[3], dd[3], Rbar[9] (extrapolated rotation, Eq. nesterov_R).
-enum {
-  PK_R = 0, PK_TH = 9, PK_TL = 12, PK_D = 15, PK_DR = 18, PK_DT = 27, PK_DD = 30, PK_RB = 33,
-  PACK = 48
+// Flat camera layout read by eval_F (Real offsets): R[9] (row-major), t[3], pad[3], d[3].
+enum { PK_R = 0, PK_TH = 9, PK_D = 15 };
+
+// 16-byte (float) / 32-byte (double) vector used for the camera pack and landmark records.
+template <class Real>
+struct alignas(4 * sizeof(Real)) V4 {
+  Real x, y, z, w;
 };
+
+// Camera pack read by the observation passes (V4 entries, one pack per camera):
+//   [P4_RK + r] = (R^k row r, t^k_r hi)      [P4_RB + r] = (Rbar row r, dt_r)
+//   [P4_RP + r] = (R' row r, t^k_r lo)       [P4_DR + r] = (dR row r, 0)
+//   [P4_D] = (d^k, 0)                        [P4_DD] = (dd, 0)
+// with R' = R^(k-1) = R^k - dR, dt = t^k - t^(k-1), dd = d^k - d^(k-1) formed in FP64, and
+// Rbar the extrapolated rotation of Eq. nesterov_R.
+enum { P4_RK = 0, P4_RB = 3, P4_RP = 6, P4_DR = 9, P4_D = 12, P4_DD = 13, P4N = 14 };
 
 // Per-observation output of the three-point evaluation.
 template <class Real>
@@ -69,10 +85,12 @@ struct ObsEval {
 };
 
 // Evaluates one observation at x^k, xbar^k and x^(k-1).
-//   pk: camera pack; q = l^k - t^k (formed by the caller); dl = l^k - l^(k-1);
-//   u: pixel (internal units); gamma: extrapolation ratio of Eq. nesterov_scalar.
-// xbar: Rbar from the pack, dbar = d + gamma dd, qbar = q + gamma (dl - dt) (Eq. nesterov_x).
-// x^(k-1): R' = R - dR, d' = d - dd, q' = q - (dl - dt).
+//   pk: camera pack; (l0,l1,l2) + (o0,o1,o2): landmark position l^k as high and low parts
+//   (the low part is zero in FP64); dl = l^k - l^(k-1); u: pixel (internal units);
+//   gamma: extrapolation ratio of Eq. nesterov_scalar.
+// q^k = l^k - t^k is formed from high and low parts so that it keeps FP32 relative accuracy.
+// xbar: Rbar, dbar = d + gamma dd, qbar = q + gamma (dl - dt) (Eq. nesterov_x).
+// x^(k-1): R', d' = d - dd, q' = q - (dl - dt).
 // The surrogate gap of Eq. DEalpha is written in displacement form: with X = R^k p^k +
 // lambda' t^k, Y = lambda' l^k and g' of Eq. g at x^(k-1),
 //   |X - g'|^2 + |Y - g'|^2 = |X - Y|^2 / 2 + 2 |(X + Y)/2 - g'|^2,
@@ -81,42 +99,42 @@ struct ObsEval {
 // so gap = [rho(r^k) - rho(r') - w'(r^k - r')]/2 - w' |q^k|^2 (lambda' - lambda^k)^2 / 2
 //          - w' |D|^2 / 2, every term of which is formed without cancellation of O(1) values.
 template <int LOSS, class Real>
-__device__ __forceinline__ void eval_obs(const Real* __restrict__ pk, Real q0, Real q1, Real q2, Real dl0,
-                                         Real dl1, Real dl2, Real u0, Real u1, Real gamma,
-                                         const LossC<Real>& L, ObsEval<Real>& o) {
+__device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l0, Real l1, Real l2, Real o0,
+                                         Real o1, Real o2, Real dl0, Real dl1, Real dl2, Real u0, Real u1,
+                                         Real gamma, const LossC<Real>& L, ObsEval<Real>& o) {
+  const V4<Real> a0 = pk[P4_RK + 0], a1 = pk[P4_RK + 1], a2 = pk[P4_RK + 2];
+  const V4<Real> c0 = pk[P4_RP + 0], c1 = pk[P4_RP + 1], c2 = pk[P4_RP + 2];
+  const V4<Real> b0 = pk[P4_RB + 0], b1 = pk[P4_RB + 1], b2 = pk[P4_RB + 2];
+  const V4<Real> dd = pk[P4_DD], d = pk[P4_D];
   const Real s = u0 * u0 + u1 * u1;
   const Real s2 = s * s;
+  const Real q0 = (l0 - a0.w) + (o0 - c0.w);
+  const Real q1 = (l1 - a1.w) + (o1 - c1.w);
+  const Real q2 = (l2 - a2.w) + (o2 - c2.w);
   // ---- x^k
-  const Real d0 = pk[PK_D + 0], d1 = pk[PK_D + 1], d2 = pk[PK_D + 2];
-  const Real pz = d0 + d1 * s + d2 * s2;
-  const Real R00 = pk[PK_R + 0], R01 = pk[PK_R + 1], R02 = pk[PK_R + 2];
-  const Real R10 = pk[PK_R + 3], R11 = pk[PK_R + 4], R12 = pk[PK_R + 5];
-  const Real R20 = pk[PK_R + 6], R21 = pk[PK_R + 7], R22 = pk[PK_R + 8];
-  const Real Rp0 = R00 * u0 + R01 * u1 + R02 * pz;
-  const Real Rp1 = R10 * u0 + R11 * u1 + R12 * pz;
-  const Real Rp2 = R20 * u0 + R21 * u1 + R22 * pz;
+  const Real pz = d.x + d.y * s + d.z * s2;
+  const Real Rp0 = a0.x * u0 + a0.y * u1 + a0.z * pz;
+  const Real Rp1 = a1.x * u0 + a1.y * u1 + a1.z * pz;
+  const Real Rp2 = a2.x * u0 + a2.y * u1 + a2.z * pz;
   const Real qq = q0 * q0 + q1 * q1 + q2 * q2;
-  const Real iqq = Real(1) / qq;
-  o.lam = (q0 * Rp0 + q1 * Rp1 + q2 * Rp2) * iqq;
+  o.lam = fdiv(q0 * Rp0 + q1 * Rp1 + q2 * Rp2, qq);
   o.Re0 = Rp0 - o.lam * q0;
   o.Re1 = Rp1 - o.lam * q1;
   o.Re2 = Rp2 - o.lam * q2;
   o.r = o.Re0 * o.Re0 + o.Re1 * o.Re1 + o.Re2 * o.Re2;
   rho_w<LOSS, Real>(L, o.r, o.rho, o.w);
-  // ---- displacements
-  const Real dt0 = pk[PK_DT + 0], dt1 = pk[PK_DT + 1], dt2 = pk[PK_DT + 2];
-  const Real dd0 = pk[PK_DD + 0], dd1 = pk[PK_DD + 1], dd2 = pk[PK_DD + 2];
-  const Real e0 = dl0 - dt0, e1 = dl1 - dt1, e2 = dl2 - dt2;   // (l^k - l^(k-1)) - (t^k - t^(k-1))
-  const Real phidd = dd0 + dd1 * s + dd2 * s2;
+  // ---- displacements: (l^k - l^(k-1)) - (t^k - t^(k-1)) and phi . dd
+  const Real e0 = dl0 - b0.w, e1 = dl1 - b1.w, e2 = dl2 - b2.w;
+  const Real phidd = dd.x + dd.y * s + dd.z * s2;
   // ---- xbar^k
   {
     const Real pzb = pz + gamma * phidd;
     const Real qb0 = q0 + gamma * e0, qb1 = q1 + gamma * e1, qb2 = q2 + gamma * e2;
-    const Real Rbp0 = pk[PK_RB + 0] * u0 + pk[PK_RB + 1] * u1 + pk[PK_RB + 2] * pzb;
-    const Real Rbp1 = pk[PK_RB + 3] * u0 + pk[PK_RB + 4] * u1 + pk[PK_RB + 5] * pzb;
-    const Real Rbp2 = pk[PK_RB + 6] * u0 + pk[PK_RB + 7] * u1 + pk[PK_RB + 8] * pzb;
+    const Real Rbp0 = b0.x * u0 + b0.y * u1 + b0.z * pzb;
+    const Real Rbp1 = b1.x * u0 + b1.y * u1 + b1.z * pzb;
+    const Real Rbp2 = b2.x * u0 + b2.y * u1 + b2.z * pzb;
     const Real qqb = qb0 * qb0 + qb1 * qb1 + qb2 * qb2;
-    o.lamb = (qb0 * Rbp0 + qb1 * Rbp1 + qb2 * Rbp2) / qqb;
+    o.lamb = fdiv(qb0 * Rbp0 + qb1 * Rbp1 + qb2 * Rbp2, qqb);
     o.Reb0 = Rbp0 - o.lamb * qb0;
     o.Reb1 = Rbp1 - o.lamb * qb1;
     o.Reb2 = Rbp2 - o.lamb * qb2;
@@ -126,31 +144,50 @@ __device__ __forceinline__ void eval_obs(const Real* __restrict__ pk, Real q0, R
   }
   // ---- x^(k-1) and the surrogate gap
   {
-    const Real dR00 = pk[PK_DR + 0], dR01 = pk[PK_DR + 1], dR02 = pk[PK_DR + 2];
-    const Real dR10 = pk[PK_DR + 3], dR11 = pk[PK_DR + 4], dR12 = pk[PK_DR + 5];
-    const Real dR20 = pk[PK_DR + 6], dR21 = pk[PK_DR + 7], dR22 = pk[PK_DR + 8];
+    const V4<Real> g0 = pk[P4_DR + 0], g1 = pk[P4_DR + 1], g2 = pk[P4_DR + 2];
     const Real pzp = pz - phidd;
     const Real qp0 = q0 - e0, qp1 = q1 - e1, qp2 = q2 - e2;
-    const Real Rq02 = R02 - dR02, Rq12 = R12 - dR12, Rq22 = R22 - dR22;   // R' e3
-    const Real Rpp0 = (R00 - dR00) * u0 + (R01 - dR01) * u1 + Rq02 * pzp;
-    const Real Rpp1 = (R10 - dR10) * u0 + (R11 - dR11) * u1 + Rq12 * pzp;
-    const Real Rpp2 = (R20 - dR20) * u0 + (R21 - dR21) * u1 + Rq22 * pzp;
+    const Real Rpp0 = c0.x * u0 + c0.y * u1 + c0.z * pzp;
+    const Real Rpp1 = c1.x * u0 + c1.y * u1 + c1.z * pzp;
+    const Real Rpp2 = c2.x * u0 + c2.y * u1 + c2.z * pzp;
     const Real qqp = qp0 * qp0 + qp1 * qp1 + qp2 * qp2;
-    const Real lamp = (qp0 * Rpp0 + qp1 * Rpp1 + qp2 * Rpp2) / qqp;
+    const Real lamp = fdiv(qp0 * Rpp0 + qp1 * Rpp1 + qp2 * Rpp2, qqp);
     const Real Rep0 = Rpp0 - lamp * qp0, Rep1 = Rpp1 - lamp * qp1, Rep2 = Rpp2 - lamp * qp2;
     const Real rp = Rep0 * Rep0 + Rep1 * Rep1 + Rep2 * Rep2;
     Real rhop, wp;
     rho_w<LOSS, Real>(L, rp, rhop, wp);
-    const Real D0 = dR00 * u0 + dR01 * u1 + dR02 * pz + Rq02 * phidd + lamp * (dt0 + dl0);
-    const Real D1 = dR10 * u0 + dR11 * u1 + dR12 * pz + Rq12 * phidd + lamp * (dt1 + dl1);
-    const Real D2 = dR20 * u0 + dR21 * u1 + dR22 * pz + Rq22 * phidd + lamp * (dt2 + dl2);
+    const Real D0 = g0.x * u0 + g0.y * u1 + g0.z * pz + c0.z * phidd + lamp * (b0.w + dl0);
+    const Real D1 = g1.x * u0 + g1.y * u1 + g1.z * pz + c1.z * phidd + lamp * (b1.w + dl1);
+    const Real D2 = g2.x * u0 + g2.y * u1 + g2.z * pz + c2.z * phidd + lamp * (b2.w + dl2);
     const Real dlam = lamp - o.lam;
     o.gap = Real(0.5) * (o.rho - rhop - wp * (o.r - rp)) - Real(0.5) * wp * qq * dlam * dlam -
             Real(0.5) * wp * (D0 * D0 + D1 * D1 + D2 * D2);
   }
 }
 
-// F_ij(x^k) = rho(|e|^2) / 2 only (Eq. Fij).
+// F_ij(x^k) = rho(|e|^2) / 2 from the camera pack (Eq. Fij).
+template <int LOSS, class Real>
+__device__ __forceinline__ Real eval_F4(const V4<Real>* __restrict__ pk, Real l0, Real l1, Real l2, Real o0,
+                                        Real o1, Real o2, Real u0, Real u1, const LossC<Real>& L) {
+  const V4<Real> a0 = pk[P4_RK + 0], a1 = pk[P4_RK + 1], a2 = pk[P4_RK + 2];
+  const V4<Real> c0 = pk[P4_RP + 0], c1 = pk[P4_RP + 1], c2 = pk[P4_RP + 2];
+  const V4<Real> d = pk[P4_D];
+  const Real q0 = (l0 - a0.w) + (o0 - c0.w);
+  const Real q1 = (l1 - a1.w) + (o1 - c1.w);
+  const Real q2 = (l2 - a2.w) + (o2 - c2.w);
+  const Real s = u0 * u0 + u1 * u1;
+  const Real pz = d.x + d.y * s + d.z * s * s;
+  const Real Rp0 = a0.x * u0 + a0.y * u1 + a0.z * pz;
+  const Real Rp1 = a1.x * u0 + a1.y * u1 + a1.z * pz;
+  const Real Rp2 = a2.x * u0 + a2.y * u1 + a2.z * pz;
+  const Real lam = fdiv(q0 * Rp0 + q1 * Rp1 + q2 * Rp2, q0 * q0 + q1 * q1 + q2 * q2);
+  const Real e0 = Rp0 - lam * q0, e1 = Rp1 - lam * q1, e2 = Rp2 - lam * q2;
+  Real rho, w;
+  rho_w<LOSS, Real>(L, e0 * e0 + e1 * e1 + e2 * e2, rho, w);
+  return Real(0.5) * rho;
+}
+
+// F_ij(x^k) = rho(|e|^2) / 2 only (Eq. Fij), flat camera layout, q formed by the caller.
 template <int LOSS, class Real>
 __device__ __forceinline__ Real eval_F(const Real* __restrict__ pk, Real q0, Real q1, Real q2, Real u0, Real u1,
                                        const LossC<Real>& L) {

@@ -2,16 +2,16 @@
 // with one block per camera and one block per landmark.
 //
 // Per iteration k, in stream order:
-//   1. cam_prepare  (M threads)  : extrapolated rotation Rbar^k (Eq. nesterov_R) and the
-//                                  camera pack read by the observation passes.
-//   2. cpass        (warp/chunk) : camera-sorted observations; per camera the centred
-//                                  majorizer statistics at xbar^k and x^k plus the
-//                                  F_ij and surrogate-gap sums, FP64 partial per chunk.
-//   3. lpass        (CTA/tile)   : landmark-sorted observations; per landmark statistics,
-//                                  restart metrics, accelerated solve, restart test and
-//                                  MM re-solve (closed form), in place.
-//   4. camsolve     (M threads)  : FP64 camera block solves, restart test, MM re-solve.
-//   5. finalize     (1 CTA)      : F(x^k) trace entry and restart count.
+//   1. cpass     (warp/chunk) : camera-sorted observations; per camera the centred
+//                               majorizer statistics at xbar^k and x^k plus the F_ij and
+//                               surrogate-gap sums, one FP64 partial per chunk.
+//   2. lpass     (CTA/tile)   : landmark-sorted observations; per landmark statistics,
+//                               restart metrics, accelerated solve, restart test and MM
+//                               re-solve (closed form), in place.
+//   3. camsolve  (M threads)  : FP64 camera block solves, restart test, MM re-solve, and
+//                               the extrapolated rotation and pack of iteration k+1.
+//   4. finalize  (1 CTA)      : F(x^k) trace entry and restart count.
+// cam_prepare builds the pack of the first iteration of a run.
 //
 // Centred statistics. For a conditioning iterate z (xbar^k or x^k) and a camera c let
 // M(c) = [R e1, R e2, d1 R e3, d2 R e3, d3 R e3, t] (3x6) and h = (u1, u2, 1, s, s^2,
@@ -33,18 +33,21 @@ namespace daba {
 enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_STRIDE = 84 };
 // ---- tile partial layout (doubles): sumF restarts pad pad
 enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
-// ---- landmark record (Real[8]): l[3] (hi part in MIXED), delta[3] = l^k - l^(k-1),
-//      S = Fbar^(k-1) - E^(k) (restart slack), E^(k) (FP64 path only)
-enum { LR_L = 0, LR_D = 3, LR_S = 6, LR_E = 7, LREC = 8 };
+// ---- landmark record (two V4): (l[3], delta0) (delta1, delta2, S, E), with l the high part
+//      in MIXED, delta = l^k - l^(k-1), S = Fbar^(k-1) - E^(k) the restart slack and E^(k)
+//      kept by the FP64 path only; MIXED keeps the low part of l in a separate V4 array.
 // ---- camera state (doubles, stride 16): R[9] t[3] d[3] pad
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
 constexpr int CPASS_WARPS = 4;
 constexpr int LPASS_THREADS = 256;
-constexpr int TILE_OBS = 1024;   // max observations per landmark tile (also the max track length)
+constexpr int TILE_OBS = 512;     // observations of a small landmark tile
+constexpr int TILE_LMS = 256;     // landmarks of a small landmark tile
+constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own
+constexpr int MAX_TRACK = BIG_TILE_OBS;
 
 struct IterParams {
-  const double* gam;   // gamma^(k) per iteration of the current run segment
+  const double* gam;   // gamma^(k) per iteration of the current run segment (+1 look-ahead)
   int* it;             // device iteration counter within the segment
   int* first;          // 1 on the first iteration after the state was set
   double xi, eta;
@@ -54,18 +57,55 @@ struct IterParams {
 
 __device__ __forceinline__ int tri6(int a, int b) { return a * 6 - (a * (a - 1)) / 2 + (b - a); }
 
+// Writes the pass pack of one camera from its FP64 state, its displacement and Rbar.
 template <class Real>
-__device__ __forceinline__ void split_hi_lo(double x, Real& hi, Real& lo) {
-  hi = Real(x);
-  lo = Real(x - double(hi));
+__device__ __forceinline__ void write_pack(const double* x, const double* dx, const double* Rb, V4<Real>* pk) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double t = x[CS_T + r];
+    const Real th = Real(t);
+    const Real tl = Real(t - double(th));
+    V4<Real> a, b, c, g;
+    a.x = Real(x[CS_R + 3 * r + 0]);
+    a.y = Real(x[CS_R + 3 * r + 1]);
+    a.z = Real(x[CS_R + 3 * r + 2]);
+    a.w = th;
+    b.x = Real(Rb[3 * r + 0]);
+    b.y = Real(Rb[3 * r + 1]);
+    b.z = Real(Rb[3 * r + 2]);
+    b.w = Real(dx[CS_T + r]);
+    c.x = Real(x[CS_R + 3 * r + 0] - dx[CS_R + 3 * r + 0]);
+    c.y = Real(x[CS_R + 3 * r + 1] - dx[CS_R + 3 * r + 1]);
+    c.z = Real(x[CS_R + 3 * r + 2] - dx[CS_R + 3 * r + 2]);
+    c.w = tl;
+    g.x = Real(dx[CS_R + 3 * r + 0]);
+    g.y = Real(dx[CS_R + 3 * r + 1]);
+    g.z = Real(dx[CS_R + 3 * r + 2]);
+    g.w = Real(0);
+    pk[P4_RK + r] = a;
+    pk[P4_RB + r] = b;
+    pk[P4_RP + r] = c;
+    pk[P4_DR + r] = g;
+  }
+  V4<Real> d, e;
+  d.x = Real(x[CS_D + 0]);
+  d.y = Real(x[CS_D + 1]);
+  d.z = Real(x[CS_D + 2]);
+  d.w = Real(0);
+  e.x = Real(dx[CS_D + 0]);
+  e.y = Real(dx[CS_D + 1]);
+  e.z = Real(dx[CS_D + 2]);
+  e.w = Real(0);
+  pk[P4_D] = d;
+  pk[P4_DD] = e;
 }
 
 // ---------------------------------------------------------------------------
-// 1. camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) and the pass pack
+// camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) (Eq. nesterov_R) and the pack
 // ---------------------------------------------------------------------------
 template <class Real>
 __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const double* __restrict__ cam_dx,
-                              IterParams P, double* __restrict__ cam_Rbar, Real* __restrict__ pack) {
+                              IterParams P, double* __restrict__ cam_Rbar, V4<Real>* __restrict__ pack) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const double gamma = P.gam[*P.it];
@@ -75,89 +115,100 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
 #pragma unroll
   for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
   proj_rot3d(K, Rb);
-  Real* pk = pack + (size_t)i * PACK;
 #pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    cam_Rbar[(size_t)i * 9 + a] = Rb[a];
-    pk[PK_R + a] = Real(x[CS_R + a]);
-    pk[PK_DR + a] = Real(dx[CS_R + a]);
-    pk[PK_RB + a] = Real(Rb[a]);
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    Real hi, lo;
-    split_hi_lo<Real>(x[CS_T + a], hi, lo);
-    pk[PK_TH + a] = hi;
-    pk[PK_TL + a] = lo;
-    pk[PK_D + a] = Real(x[CS_D + a]);
-    pk[PK_DT + a] = Real(dx[CS_T + a]);
-    pk[PK_DD + a] = Real(dx[CS_D + a]);
-  }
+  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
+  write_pack<Real>(x, dx, Rb, pack + (size_t)i * P4N);
 }
 
 // ---------------------------------------------------------------------------
-// 2. camera-sorted pass: one warp per chunk (<= chunk size observations of one camera)
+// 1. camera-sorted pass: one warp per chunk (<= chunk size observations of one camera)
 // ---------------------------------------------------------------------------
+template <class Real>
+__device__ __forceinline__ void accumulate_cam(Real* acc, const ObsEval<Real>& ev, Real u0, Real u1) {
+  const Real s = u0 * u0 + u1 * u1;
+  Real h[6] = {u0, u1, Real(1), s, s * s, ev.lamb};
+  {  // xbar statistics: Hbar += wb h h^T, Bbar += wb h (R e)^T / 2
+    Real wh[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) wh[a] = ev.wb * h[a];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = a; c < 6; ++c) acc[CP_HB + tri6(a, c)] += wh[a] * h[c];
+    const Real r0[3] = {Real(0.5) * ev.Reb0, Real(0.5) * ev.Reb1, Real(0.5) * ev.Reb2};
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[CP_BB + a * 3 + c] += wh[a] * r0[c];
+  }
+  h[5] = ev.lam;
+  {  // x^k statistics
+    Real wh[6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) wh[a] = ev.w * h[a];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = a; c < 6; ++c) acc[CP_H + tri6(a, c)] += wh[a] * h[c];
+    const Real r0[3] = {Real(0.5) * ev.Re0, Real(0.5) * ev.Re1, Real(0.5) * ev.Re2};
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[CP_B + a * 3 + c] += wh[a] * r0[c];
+  }
+  acc[CP_F] += Real(0.5) * ev.rho;
+  acc[CP_G] += ev.gap;
+}
+
 template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
-            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const Real* __restrict__ pack,
-            const Real* __restrict__ lmrec, LossC<Real> L, IterParams P, double* __restrict__ part) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
+            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, double* __restrict__ part) {
+  __shared__ V4<Real> spk[CPASS_WARPS][P4N];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * CPASS_WARPS + wib;
   const int lane = threadIdx.x & 31;
   if (warp >= n_chunks) return;
   const int cam = chunk_cam[warp];
   const int b = chunk_beg[warp], e = chunk_beg[warp + 1];
+  if (lane < P4N) spk[wib][lane] = pack[(size_t)cam * P4N + lane];
+  __syncwarp();
+  const V4<Real>* pk = spk[wib];
   const Real gamma = Real(P.gam[*P.it]);
-  const Real* pk = pack + (size_t)cam * PACK;
-  const Real th0 = pk[PK_TH + 0], th1 = pk[PK_TH + 1], th2 = pk[PK_TH + 2];
-  const Real tl0 = pk[PK_TL + 0], tl1 = pk[PK_TL + 1], tl2 = pk[PK_TL + 2];
   Real acc[80];
 #pragma unroll
   for (int k = 0; k < 80; ++k) acc[k] = Real(0);
-  for (int o = b + lane; o < e; o += 32) {
+  // software pipeline: landmark record one step ahead, landmark index two steps ahead
+  int o = b + lane;
+  V4<Real> r0, r1;
+  Real2 uu;
+  int jn = 0;
+  if (o < e) {
     const int j = c_lm[o];
-    const Real2 uu = c_u[o];
-    const Real* lr = lmrec + (size_t)j * LREC;
-    const Real q0 = (lr[LR_L + 0] - th0) - tl0;
-    const Real q1 = (lr[LR_L + 1] - th1) - tl1;
-    const Real q2 = (lr[LR_L + 2] - th2) - tl2;
+    uu = c_u[o];
+    r0 = lmrec[2 * (size_t)j];
+    r1 = lmrec[2 * (size_t)j + 1];
+  }
+  if (o + 32 < e) jn = c_lm[o + 32];
+  for (; o < e; o += 32) {
+    V4<Real> n0, n1;
+    Real2 un;
+    int jnn = 0;
+    if (o + 32 < e) {
+      n0 = lmrec[2 * (size_t)jn];
+      n1 = lmrec[2 * (size_t)jn + 1];
+      un = c_u[o + 32];
+      if (o + 64 < e) jnn = c_lm[o + 64];
+    }
     ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, q0, q1, q2, lr[LR_D + 0], lr[LR_D + 1], lr[LR_D + 2], uu.x, uu.y, gamma, L, ev);
-    const Real s = uu.x * uu.x + uu.y * uu.y;
-    Real h[6] = {uu.x, uu.y, Real(1), s, s * s, ev.lamb};
-    // xbar statistics: Hbar += wb h h^T, Bbar += wb h (R e)^T / 2
-    {
-      Real wh[6];
-#pragma unroll
-      for (int a = 0; a < 6; ++a) wh[a] = ev.wb * h[a];
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int c = a; c < 6; ++c) acc[CP_HB + tri6(a, c)] += wh[a] * h[c];
-      const Real r0[3] = {Real(0.5) * ev.Reb0, Real(0.5) * ev.Reb1, Real(0.5) * ev.Reb2};
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[CP_BB + a * 3 + c] += wh[a] * r0[c];
-    }
-    h[5] = ev.lam;
-    {
-      Real wh[6];
-#pragma unroll
-      for (int a = 0; a < 6; ++a) wh[a] = ev.w * h[a];
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int c = a; c < 6; ++c) acc[CP_H + tri6(a, c)] += wh[a] * h[c];
-      const Real r0[3] = {Real(0.5) * ev.Re0, Real(0.5) * ev.Re1, Real(0.5) * ev.Re2};
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[CP_B + a * 3 + c] += wh[a] * r0[c];
-    }
-    acc[CP_F] += Real(0.5) * ev.rho;
-    acc[CP_G] += ev.gap;
+    eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
+                         ev);
+    accumulate_cam<Real>(acc, ev, uu.x, uu.y);
+    r0 = n0;
+    r1 = n1;
+    uu = un;
+    jn = jnn;
   }
   // warp reduction, lane 0 writes the FP64 partial
 #pragma unroll
@@ -175,19 +226,17 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 }
 
 // ---------------------------------------------------------------------------
-// 3. landmark-sorted pass: one CTA per tile of consecutive landmarks
+// 2. landmark-sorted pass: one CTA per tile of consecutive landmarks
 // ---------------------------------------------------------------------------
 // Tile data: tile_lm[t] .. tile_lm[t+1] landmarks; their observations occupy the
 // landmark-sorted positions lm_ptr[first] .. lm_ptr[last]. Inside the tile the
 // observations are processed in camera order (t_cam, t_u, t_slot), where t_slot is
 // the observation's landmark-sorted position relative to the tile start.
+// Shared memory: nl_cap x 3 V4 staged landmarks, no_cap x 10 contributions, slot map.
 template <class Real>
-struct LSmem {
-  // staged landmark data (nl entries) and per-observation contributions (no entries)
-  static __host__ __device__ size_t bytes(int nl, int no) {
-    return (size_t)nl * 9 * sizeof(Real) + (size_t)no * 10 * sizeof(Real) + (size_t)no * sizeof(uint16_t) + 16;
-  }
-};
+__host__ __device__ inline size_t lpass_smem_bytes(int no_cap, int nl_cap) {
+  return (size_t)nl_cap * 3 * sizeof(V4<Real>) + (size_t)no_cap * 10 * sizeof(Real) + (size_t)no_cap * 2 + 16;
+}
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
 __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
@@ -202,31 +251,38 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 
 template <int LOSS, class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
-    k_lpass(const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const int* __restrict__ t_cam,
-            const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot, const Real* __restrict__ pack,
-            Real* __restrict__ lmrec, float* __restrict__ lm_lo, LossC<Real> L, IterParams P,
-            double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
-            double* __restrict__ lm_Fbdiag) {
+    k_lpass(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
+            const int* __restrict__ t_cam, const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot,
+            const V4<Real>* __restrict__ pack, V4<Real>* __restrict__ lmrec, V4<float>* __restrict__ lm_lo,
+            LossC<Real> L, IterParams P, double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs,
+            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tile = blockIdx.x;
+  const int tile = tile0 + blockIdx.x;
   const int lb = tile_lm[tile], le = tile_lm[tile + 1];
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  Real* sl = reinterpret_cast<Real*>(smem_raw);               // nl * 9: l hi[3], l lo[3], delta[3]
-  Real* sc = sl + (size_t)nl * 9;                             // 10 * no contributions (SoA)
-  uint16_t* smap = reinterpret_cast<uint16_t*>(sc + (size_t)no * 10);   // slot -> local landmark
+  V4<Real>* sl = reinterpret_cast<V4<Real>*>(smem_raw);                  // nl_cap x 3
+  Real* sc = reinterpret_cast<Real*>(sl + (size_t)nl_cap * 3);           // 10 x no_cap (SoA)
+  uint16_t* smap = reinterpret_cast<uint16_t*>(sc + (size_t)no_cap * 10);   // slot -> local landmark
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
 
   for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
-    const Real* lr = lmrec + (size_t)(lb + jl) * LREC;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sl[jl * 9 + a] = lr[LR_L + a];
-      sl[jl * 9 + 6 + a] = lr[LR_D + a];
-      sl[jl * 9 + 3 + a] = HAS_LO ? Real(lm_lo[(size_t)(lb + jl) * 4 + a]) : Real(0);
+    const size_t g = (size_t)(lb + jl);
+    sl[jl * 3 + 0] = lmrec[2 * g];
+    sl[jl * 3 + 1] = lmrec[2 * g + 1];
+    V4<Real> lo;
+    if (HAS_LO) {
+      const V4<float> f = lm_lo[g];
+      lo.x = Real(f.x);
+      lo.y = Real(f.y);
+      lo.z = Real(f.z);
+    } else {
+      lo.x = lo.y = lo.z = Real(0);
     }
+    lo.w = Real(0);
+    sl[jl * 3 + 2] = lo;
     const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
     for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
   }
@@ -237,26 +293,23 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     const Real2 uu = t_u[ob + o];
     const int slot = t_slot[ob + o];
     const int jl = smap[slot];
-    const Real* pk = pack + (size_t)cam * PACK;
-    const Real* ls = sl + jl * 9;
-    const Real q0 = (ls[0] - pk[PK_TH + 0]) + (ls[3] - pk[PK_TL + 0]);
-    const Real q1 = (ls[1] - pk[PK_TH + 1]) + (ls[4] - pk[PK_TL + 1]);
-    const Real q2 = (ls[2] - pk[PK_TH + 2]) + (ls[5] - pk[PK_TL + 2]);
+    const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
     ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, q0, q1, q2, ls[6], ls[7], ls[8], uu.x, uu.y, gamma, L, ev);
+    eval_obs<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, A.w, B.x, B.y, uu.x, uu.y, gamma,
+                         L, ev);
     // landmark statistics: sum w lambda^2 and sum w lambda r0' with r0' = -R e / 2
     const Real wlb = ev.wb * ev.lamb;
     const Real wl = ev.w * ev.lam;
-    sc[0 * no + slot] = wlb * ev.lamb;
-    sc[1 * no + slot] = Real(-0.5) * wlb * ev.Reb0;
-    sc[2 * no + slot] = Real(-0.5) * wlb * ev.Reb1;
-    sc[3 * no + slot] = Real(-0.5) * wlb * ev.Reb2;
-    sc[4 * no + slot] = wl * ev.lam;
-    sc[5 * no + slot] = Real(-0.5) * wl * ev.Re0;
-    sc[6 * no + slot] = Real(-0.5) * wl * ev.Re1;
-    sc[7 * no + slot] = Real(-0.5) * wl * ev.Re2;
-    sc[8 * no + slot] = Real(0.5) * ev.rho;
-    sc[9 * no + slot] = ev.gap;
+    sc[0 * no_cap + slot] = wlb * ev.lamb;
+    sc[1 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb0;
+    sc[2 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb1;
+    sc[3 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb2;
+    sc[4 * no_cap + slot] = wl * ev.lam;
+    sc[5 * no_cap + slot] = Real(-0.5) * wl * ev.Re0;
+    sc[6 * no_cap + slot] = Real(-0.5) * wl * ev.Re1;
+    sc[7 * no_cap + slot] = Real(-0.5) * wl * ev.Re2;
+    sc[8 * no_cap + slot] = Real(0.5) * ev.rho;
+    sc[9 * no_cap + slot] = ev.gap;
   }
   __syncthreads();
 
@@ -270,17 +323,17 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     for (int k = 0; k < 10; ++k) st[k] = Real(0);
     for (int s = s0; s < s1; ++s)
 #pragma unroll
-      for (int k = 0; k < 10; ++k) st[k] += sc[k * no + s];
-    Real* lr = lmrec + (size_t)(lb + jl) * LREC;
+      for (int k = 0; k < 10; ++k) st[k] += sc[k * no_cap + s];
+    const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
     const Real hx = Real(0.5) * Real(xi);
-    const Real dl0 = sl[jl * 9 + 6], dl1 = sl[jl * 9 + 7], dl2 = sl[jl * 9 + 8];
+    const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
     // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
     //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
     const Real dE = -hx * (dl0 * dl0 + dl1 * dl1 + dl2 * dl2) + Real(0.5) * st[9];
-    const Real S = first ? Real(0) : lr[LR_S];
+    const Real S = first ? Real(0) : B.z;
     const Real thr = Real(1.0 - eta) * (S - dE);
-    // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), written as a step from l^k
-    const Real ib = Real(1) / (st[0] + hx);
+    // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), as a step from l^k
+    const Real ib = fdiv(Real(1), st[0] + hx);
     const Real sa0 = gamma * dl0 - st[1] * ib, sa1 = gamma * dl1 - st[2] * ib, sa2 = gamma * dl2 - st[3] * ib;
     // E^alpha(l | x^k) - E^alpha(l^k | x^k) = (a + xi/2)|dl|^2 + 2 dl . b
     const Real ak = st[4] + hx;
@@ -288,43 +341,50 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     Real dEn = ak * (sa0 * sa0 + sa1 * sa1 + sa2 * sa2) + Real(2) * (sa0 * st[5] + sa1 * st[6] + sa2 * st[7]);
     const bool rs = P.accelerated ? (dEn > thr) : true;
     if (rs) {   // adaptive restart: MM update (Eq. update_mm) from l^k
-      const Real ik = Real(1) / ak;
+      const Real ik = fdiv(Real(1), ak);
       step0 = -st[5] * ik;
       step1 = -st[6] * ik;
       step2 = -st[7] * ik;
       dEn = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
     }
     nrs += (rs && P.accelerated) ? 1 : 0;
+    V4<Real> nA, nB;
+    const size_t g = (size_t)(lb + jl);
     if (HAS_LO) {
-      float h0 = float(sl[jl * 9 + 0]), h1 = float(sl[jl * 9 + 1]), h2 = float(sl[jl * 9 + 2]);
-      float o0 = float(sl[jl * 9 + 3]), o1 = float(sl[jl * 9 + 4]), o2 = float(sl[jl * 9 + 5]);
+      float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
+      float o0 = float(C.x), o1 = float(C.y), o2 = float(C.z);
       df_add(h0, o0, float(step0));
       df_add(h1, o1, float(step1));
       df_add(h2, o2, float(step2));
-      lr[LR_L + 0] = Real(h0);
-      lr[LR_L + 1] = Real(h1);
-      lr[LR_L + 2] = Real(h2);
-      float* lo = lm_lo + (size_t)(lb + jl) * 4;
-      lo[0] = o0;
-      lo[1] = o1;
-      lo[2] = o2;
+      nA.x = Real(h0);
+      nA.y = Real(h1);
+      nA.z = Real(h2);
+      V4<float> lo;
+      lo.x = o0;
+      lo.y = o1;
+      lo.z = o2;
+      lo.w = 0.f;
+      lm_lo[g] = lo;
     } else {
-      lr[LR_L + 0] = sl[jl * 9 + 0] + step0;
-      lr[LR_L + 1] = sl[jl * 9 + 1] + step1;
-      lr[LR_L + 2] = sl[jl * 9 + 2] + step2;
+      nA.x = A.x + step0;
+      nA.y = A.y + step1;
+      nA.z = A.z + step2;
     }
-    lr[LR_D + 0] = step0;
-    lr[LR_D + 1] = step1;
-    lr[LR_D + 2] = step2;
-    lr[LR_S] = thr - dEn;
+    nA.w = step0;
+    nB.x = step1;
+    nB.y = step2;
+    nB.z = thr - dEn;
+    nB.w = B.w;
     if (!HAS_LO) {   // FP64 path: E^(k) and the diagnostics F^(k), Fbar^(k)
-      const double E = first ? double(Real(0.5) * st[8]) : double(lr[LR_E]);
+      const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
       const double F = E + double(dE);
-      lm_Fdiag[lb + jl] = F;
-      lm_Fbdiag[lb + jl] = F + double(thr);
-      lr[LR_E] = Real(F + double(dEn));
+      lm_Fdiag[g] = F;
+      lm_Fbdiag[g] = F + double(thr);
+      nB.w = Real(F + double(dEn));
     }
-    lm_rs[lb + jl] = (rs && P.accelerated) ? 1 : 0;
+    lmrec[2 * g] = nA;
+    lmrec[2 * g + 1] = nB;
+    lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
     fsum += double(st[8]);
   }
   // tile sums: F(x^k) part and restart count (FP64, fixed order)
@@ -353,7 +413,7 @@ __global__ void __launch_bounds__(LPASS_THREADS)
 }
 
 // ---------------------------------------------------------------------------
-// 4. camera block solves (FP64)
+// 3. camera block solves (FP64)
 // ---------------------------------------------------------------------------
 struct Cam {
   double R[9], t[3], d[3];
@@ -518,14 +578,16 @@ __device__ inline void unpack_stats(const double* s, double H[6][6], double B[6]
     for (int c = 0; c < 3; ++c) B[a][c] = s[21 + a * 3 + c];
 }
 
+template <class Real>
 __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const double* __restrict__ part,
-                           double* __restrict__ cam_x, double* __restrict__ cam_dx,
-                           const double* __restrict__ cam_Rbar, IterParams P, double* __restrict__ cam_S,
-                           double* __restrict__ cam_E, double* __restrict__ cam_F, double* __restrict__ cam_Fb,
-                           uint8_t* __restrict__ cam_rs) {
+                           double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
+                           IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
+                           double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
+                           V4<Real>* __restrict__ pack) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
-  const double gamma = P.gam[*P.it];
+  const int it = *P.it;
+  const double gamma = P.gam[it];
   const int first = *P.first;
   double sb[39], sk[39];
 #pragma unroll
@@ -586,22 +648,37 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const d
   cam_E[i] = F + dEn;
   cam_S[i] = thr - dEn;
   cam_rs[i] = (rs && P.accelerated) ? 1 : 0;
+  double nx[CSTRIDE], ndx[CSTRIDE];
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    dx[CS_R + a] = cn.R[a] - ck.R[a];
-    x[CS_R + a] = cn.R[a];
+    ndx[CS_R + a] = cn.R[a] - ck.R[a];
+    nx[CS_R + a] = cn.R[a];
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    dx[CS_T + a] = cn.t[a] - ck.t[a];
-    dx[CS_D + a] = cn.d[a] - ck.d[a];
-    x[CS_T + a] = cn.t[a];
-    x[CS_D + a] = cn.d[a];
+    ndx[CS_T + a] = cn.t[a] - ck.t[a];
+    ndx[CS_D + a] = cn.d[a] - ck.d[a];
+    nx[CS_T + a] = cn.t[a];
+    nx[CS_D + a] = cn.d[a];
   }
+#pragma unroll
+  for (int a = 0; a < 15; ++a) {
+    x[a] = nx[a];
+    dx[a] = ndx[a];
+  }
+  // extrapolation of iteration k+1 (Eq. nesterov_R) and its pass pack
+  const double gn = P.gam[it + 1];
+  double K[9], Rb[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) K[a] = nx[CS_R + a] + gn * ndx[CS_R + a];
+  proj_rot3d(K, Rb);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
+  write_pack<Real>(nx, ndx, Rb, pack + (size_t)i * P4N);
 }
 
 // ---------------------------------------------------------------------------
-// 5. reduction of one iteration: F(x^k) (FP64, fixed order) and restart count
+// 4. reduction of one iteration: F(x^k) (FP64, fixed order) and restart count
 // ---------------------------------------------------------------------------
 __global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, int M,
                            const uint8_t* __restrict__ cam_rs, double s2, IterParams P, double* __restrict__ trace,
@@ -642,29 +719,36 @@ __global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, in
 }
 
 // ---------------------------------------------------------------------------
-// objective F(x^k) only (Eq. Fobj): per tile sums, same tiles as the landmark pass
+// objective F(x^k) only (Eq. Fobj): per tile sums over the landmark tiles
 // ---------------------------------------------------------------------------
 template <int LOSS, class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
-    k_objective(const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const int* __restrict__ t_cam,
-                const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot, const Real* __restrict__ pack,
-                const Real* __restrict__ lmrec, const float* __restrict__ lm_lo, LossC<Real> L,
-                double* __restrict__ tile_part) {
+    k_objective(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
+                const int* __restrict__ t_cam, const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot,
+                const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec,
+                const V4<float>* __restrict__ lm_lo, LossC<Real> L, double* __restrict__ tile_part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tile = blockIdx.x;
+  const int tile = tile0 + blockIdx.x;
   const int lb = tile_lm[tile], le = tile_lm[tile + 1];
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  Real* sl = reinterpret_cast<Real*>(smem_raw);
-  uint16_t* smap = reinterpret_cast<uint16_t*>(sl + (size_t)nl * 6);
+  V4<Real>* sl = reinterpret_cast<V4<Real>*>(smem_raw);   // nl_cap x 2: l hi, l lo
+  uint16_t* smap = reinterpret_cast<uint16_t*>(sl + (size_t)nl_cap * 2);
   for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
-    const Real* lr = lmrec + (size_t)(lb + jl) * LREC;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sl[jl * 6 + a] = lr[LR_L + a];
-      sl[jl * 6 + 3 + a] = HAS_LO ? Real(lm_lo[(size_t)(lb + jl) * 4 + a]) : Real(0);
+    const size_t g = (size_t)(lb + jl);
+    sl[jl * 2] = lmrec[2 * g];
+    V4<Real> lo;
+    if (HAS_LO) {
+      const V4<float> f = lm_lo[g];
+      lo.x = Real(f.x);
+      lo.y = Real(f.y);
+      lo.z = Real(f.z);
+    } else {
+      lo.x = lo.y = lo.z = Real(0);
     }
+    lo.w = Real(0);
+    sl[jl * 2 + 1] = lo;
     const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
     for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
   }
@@ -673,12 +757,9 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   for (int o = threadIdx.x; o < no; o += blockDim.x) {
     const int cam = t_cam[ob + o];
     const Real2 uu = t_u[ob + o];
-    const Real* pk = pack + (size_t)cam * PACK;
-    const Real* ls = sl + smap[t_slot[ob + o]] * 6;
-    const Real q0 = (ls[0] - pk[PK_TH + 0]) + (ls[3] - pk[PK_TL + 0]);
-    const Real q1 = (ls[1] - pk[PK_TH + 1]) + (ls[4] - pk[PK_TL + 1]);
-    const Real q2 = (ls[2] - pk[PK_TH + 2]) + (ls[5] - pk[PK_TL + 2]);
-    fsum += double(eval_F<LOSS, Real>(pk, q0, q1, q2, uu.x, uu.y, L));
+    const int jl = smap[t_slot[ob + o]];
+    const V4<Real> A = sl[jl * 2], C = sl[jl * 2 + 1];
+    fsum += double(eval_F4<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, uu.x, uu.y, L));
   }
   __shared__ double red[LPASS_THREADS / 32];
 #pragma unroll
