@@ -57,14 +57,17 @@ struct daba_ctx {
   void *c_lm = nullptr, *c_u = nullptr, *c_orig = nullptr, *cam_ptr = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
   void *lm_ptr = nullptr, *tile_lm = nullptr, *t_cam = nullptr, *t_u = nullptr, *t_slot = nullptr, *l_orig = nullptr;
-  void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack = nullptr;
+  void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack2[2] = {nullptr, nullptr};
   void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
-  void *lmrec = nullptr, *lm_lo = nullptr, *lm_rs = nullptr, *lm_Fd = nullptr, *lm_Fbd = nullptr;
+  void *lmrec2[2] = {nullptr, nullptr}, *lm_lo2[2] = {nullptr, nullptr};   // double-buffered landmark state
+  void *lm_rs = nullptr, *lm_Fd = nullptr, *lm_Fbd = nullptr;
   void *chunk_part = nullptr, *tile_part = nullptr;
   void *d_gam = nullptr, *d_it = nullptr, *d_first = nullptr, *d_flag = nullptr, *d_trace = nullptr,
        *d_rs = nullptr, *d_obj = nullptr;
   std::vector<void*> allocs;
   std::vector<cudaEvent_t> events;
+  cudaStream_t s_hi = nullptr, s_lo = nullptr;   // camera pass + solves (high priority), landmark pass
+  cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
 };
 
 namespace {
@@ -130,6 +133,11 @@ daba_status deliver(daba_ctx* ctx, void* dst, const void* src, size_t bytes, cud
 }
 
 bool is_mixed(const daba_ctx* c) { return c->opt.prec == DABA_MIXED; }
+
+// buffers of iteration k (the landmark state and the camera pack alternate between two)
+inline void* pack_at(const daba_ctx* c, int64_t k) { return c->pack2[k & 1]; }
+inline void* lmrec_at(const daba_ctx* c, int64_t k) { return c->lmrec2[k & 1]; }
+inline void* lmlo_at(const daba_ctx* c, int64_t k) { return c->lm_lo2[k & 1]; }
 
 // internal (device) index of external landmark j (identity until observations are set)
 inline size_t lm_internal(const daba_ctx* c, int j) { return c->h_linv.empty() ? (size_t)j : (size_t)c->h_linv[j]; }
@@ -262,7 +270,7 @@ IterParams iter_params(daba_ctx* ctx) {
 }
 
 template <int LOSS, class Real, class Real2, bool HAS_LO>
-cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
+cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   const LossC<Real> L = loss_consts<Real>(ctx);
   const IterParams P = iter_params(ctx);
   const int n_small = ctx->n_small_tiles, n_big = ctx->n_tiles - ctx->n_small_tiles;
@@ -272,7 +280,7 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
     if (blocks > 0)
       k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
           ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
-          (const Real2*)ctx->c_u, (const V4<Real>*)ctx->pack, (const V4<Real>*)ctx->lmrec, L, P,
+          (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
           (double*)ctx->chunk_part);
   } else if (which == 2) {
     auto kern = k_lpass<LOSS, Real, Real2, HAS_LO>;
@@ -284,9 +292,10 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt[c], LPASS_THREADS, smem, st>>>(
           t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
-          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->pack, (V4<Real>*)ctx->lmrec,
-          (V4<float>*)ctx->lm_lo, L, P, (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd,
-          (double*)ctx->lm_Fbd);
+          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)pack_at(ctx, k),
+          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), (V4<Real>*)lmrec_at(ctx, k + 1),
+          (V4<float>*)lmlo_at(ctx, k + 1), L, P, (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs,
+          (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
       if (c == 1) ctx->launches++;
     }
   } else if (which == 6) {
@@ -299,8 +308,8 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt[c], LPASS_THREADS, smem, st>>>(
           t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
-          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->pack,
-          (const V4<Real>*)ctx->lmrec, (const V4<float>*)ctx->lm_lo, L, (double*)ctx->tile_part);
+          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)pack_at(ctx, k),
+          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), L, (double*)ctx->tile_part);
       if (c == 1) ctx->launches++;
     }
   }
@@ -308,35 +317,35 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which) {
 }
 
 template <class Real, class Real2, bool HAS_LO>
-cudaError_t launch_by_loss(daba_ctx* ctx, cudaStream_t st, int which) {
+cudaError_t launch_by_loss(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   switch (ctx->opt.loss) {
-    case DABA_LOSS_TRIVIAL: return launch_passes<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st, which);
-    case DABA_LOSS_HUBER: return launch_passes<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st, which);
-    case DABA_LOSS_CAUCHY: return launch_passes<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st, which);
-    default: return launch_passes<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st, which);
+    case DABA_LOSS_TRIVIAL: return launch_passes<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st, which, k);
+    case DABA_LOSS_HUBER: return launch_passes<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st, which, k);
+    case DABA_LOSS_CAUCHY: return launch_passes<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st, which, k);
+    default: return launch_passes<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st, which, k);
   }
 }
 
-cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which) {
+cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   ctx->launches++;
-  if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which);
-  return launch_by_loss<double, double2, false>(ctx, st, which);
+  if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which, k);
+  return launch_by_loss<double, double2, false>(ctx, st, which, k);
 }
 
-cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st) {
+cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
   const int blocks = (ctx->M + 127) / 128;
   if (is_mixed(ctx))
     k_cam_prepare<float><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
-                                                 (double*)ctx->cam_Rbar, (V4<float>*)ctx->pack);
+                                                 (double*)ctx->cam_Rbar, (V4<float>*)pack_at(ctx, k));
   else
     k_cam_prepare<double><<<blocks, 128, 0, st>>>(ctx->M, (const double*)ctx->cam_x, (const double*)ctx->cam_dx, P,
-                                                  (double*)ctx->cam_Rbar, (V4<double>*)ctx->pack);
+                                                  (double*)ctx->cam_Rbar, (V4<double>*)pack_at(ctx, k));
   return cudaGetLastError();
 }
 
-cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st) {
+cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
   const int blocks = (ctx->M + 63) / 64;
@@ -344,13 +353,14 @@ cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st) {
     k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
-                                             (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (V4<float>*)ctx->pack);
+                                             (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs,
+                                             (V4<float>*)pack_at(ctx, k + 1));
   else
     k_camsolve<double><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
                                               (const double*)ctx->chunk_part, (double*)ctx->cam_x,
                                               (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
                                               (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,
-                                              (uint8_t*)ctx->cam_rs, (V4<double>*)ctx->pack);
+                                              (uint8_t*)ctx->cam_rs, (V4<double>*)pack_at(ctx, k + 1));
   return cudaGetLastError();
 }
 
@@ -370,9 +380,9 @@ daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st, bool prepare) {
   if (prepare) {
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     CK(cudaMemsetAsync(ctx->d_gam, 0, sizeof(double), st));
-    CK(launch_prepare(ctx, st));
+    CK(launch_prepare(ctx, st, ctx->k));
   }
-  CK(launch_pass(ctx, st, 6));
+  CK(launch_pass(ctx, st, 6, ctx->k));
   ctx->launches++;
   k_sum_tiles<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->s_norm * ctx->s_norm,
                                   (double*)ctx->d_obj);
@@ -414,8 +424,14 @@ int64_t daba_last_launch_count(const daba_ctx* ctx) { return ctx ? ctx->launches
 
 void daba_destroy(daba_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->s_hi) cudaStreamSynchronize(ctx->s_hi);
+  if (ctx->s_lo) cudaStreamSynchronize(ctx->s_lo);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_hi, ctx->ev_lo})
+    if (e) cudaEventDestroy(e);
+  if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
+  if (ctx->s_lo) cudaStreamDestroy(ctx->s_lo);
   delete ctx;
 }
 
@@ -468,14 +484,17 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(cam_x, (size_t)M * CSTRIDE * 8);
   AL(cam_dx, (size_t)M * CSTRIDE * 8);
   AL(cam_Rbar, (size_t)M * 9 * 8);
-  AL(pack, (size_t)M * P4N * 4 * R);
+  AL(pack2[0], (size_t)M * P4N * 4 * R);
+  AL(pack2[1], (size_t)M * P4N * 4 * R);
   AL(cam_S, (size_t)M * 8);
   AL(cam_E, (size_t)M * 8);
   AL(cam_F, (size_t)M * 8);
   AL(cam_Fb, (size_t)M * 8);
   AL(cam_rs, (size_t)M);
-  AL(lmrec, (size_t)N * LREC * R);
-  AL(lm_lo, (size_t)N * 4 * 4);
+  AL(lmrec2[0], (size_t)N * LREC * R);
+  AL(lmrec2[1], (size_t)N * LREC * R);
+  AL(lm_lo2[0], (size_t)N * 4 * 4);
+  AL(lm_lo2[1], (size_t)N * 4 * 4);
   AL(lm_rs, (size_t)N);
   AL(lm_Fd, (size_t)N * 8);
   AL(lm_Fbd, (size_t)N * 8);
@@ -489,7 +508,19 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_rs, (GSEG + 1) * 4);
   AL(d_obj, 16);
 #undef AL
-  cudaMemset(ctx->lm_lo, 0, (size_t)N * 16);
+  cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
+  cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (cudaStreamCreateWithPriority(&ctx->s_hi, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->s_lo, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_hi, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_lo, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    daba_destroy(ctx);
+    return DABA_ERR_CUDA;
+  }
   cudaMemset(ctx->d_flag, 0, 16);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
@@ -704,14 +735,14 @@ daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms,
         lo[q * 4 + a] = (float)(v - (double)h);
       }
     }
-    CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->lm_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->lmrec2[0], rec.data(), rec.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->lm_lo2[0], lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   } else {
     std::vector<double> rec((size_t)N * LREC, 0.0);
     for (int j = 0; j < N; ++j)
       for (int a = 0; a < 3; ++a) rec[lm_internal(ctx, j) * LREC + LR_L + a] = hl[(size_t)j * 3 + a];
-    CK(cudaMemcpyAsync(ctx->lmrec, rec.data(), rec.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->lmrec2[0], rec.data(), rec.size() * 8, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
   }
   ctx->h_l.swap(hl);
@@ -755,18 +786,31 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-    CK(launch_prepare(ctx, st));
+    CK(launch_prepare(ctx, st, ctx->k));
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     for (int j = 0; j < seg; ++j) {
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-      CK(launch_pass(ctx, st, 1));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-      CK(launch_pass(ctx, st, 2));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-      CK(launch_camsolve(ctx, st));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
+      const int64_t kk = ctx->k + j;
+      // fork: the landmark pass on a low-priority stream, the camera pass and the camera
+      // solves (the latency-bound critical path) on a high-priority one; join on `st`
+      CK(cudaEventRecord(ctx->ev_fork, st));
+      CK(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
+      CK(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_fork, 0));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 0), ctx->s_hi));
+      CK(launch_pass(ctx, ctx->s_hi, 1, kk));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 1), ctx->s_hi));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 3), ctx->s_lo));
+      CK(launch_pass(ctx, ctx->s_lo, 2, kk));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 4), ctx->s_lo));
+      CK(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
+      CK(launch_camsolve(ctx, ctx->s_hi, kk));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 2), ctx->s_hi));
+      CK(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
+      CK(cudaStreamWaitEvent(st, ctx->ev_hi, 0));
+      CK(cudaStreamWaitEvent(st, ctx->ev_lo, 0));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 5), st));
       CK(launch_finalize(ctx, st));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
+      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 6), st));
+      if (ctx->timing) evi += 7;
     }
     CK(cudaMemcpyAsync(trace.data() + done, ctx->d_trace, seg * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
@@ -775,12 +819,16 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]);
       ctx->tms[0] += ms;
-      for (int j = 0; j < seg; ++j)
+      // per iteration: [0] cpass start, [1] cpass end, [2] camsolve end, [3] lpass start,
+      // [4] lpass end (side stream), [5] finalize start, [6] finalize end
+      for (int j = 0; j < seg; ++j) {
+        const size_t b = 2 + (size_t)j * 7;
+        const int pairs[4][2] = {{0, 1}, {3, 4}, {1, 2}, {5, 6}};
         for (int q = 0; q < 4; ++q) {
-          const size_t b = 2 + (size_t)j * 5 + q;
-          cudaEventElapsedTime(&ms, ctx->events[b], ctx->events[b + 1]);
+          cudaEventElapsedTime(&ms, ctx->events[b + pairs[q][0]], ctx->events[b + pairs[q][1]]);
           ctx->tms[1 + q] += ms;
         }
+      }
     }
     done += seg;
     ctx->k += seg;
@@ -847,8 +895,8 @@ daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* strea
     std::vector<double> hl((size_t)N * 3);
     if (is_mixed(ctx)) {
       std::vector<float> rec((size_t)N * LREC), lo((size_t)N * 4);
-      CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(lo.data(), ctx->lm_lo, lo.size() * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(rec.data(), lmrec_at(ctx, ctx->k), rec.size() * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(lo.data(), lmlo_at(ctx, ctx->k), lo.size() * 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int j = 0; j < N; ++j) {
         const size_t q = lm_internal(ctx, j);
@@ -857,7 +905,7 @@ daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* strea
       }
     } else {
       std::vector<double> rec((size_t)N * LREC);
-      CK(cudaMemcpyAsync(rec.data(), ctx->lmrec, rec.size() * 8, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(rec.data(), lmrec_at(ctx, ctx->k), rec.size() * 8, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int j = 0; j < N; ++j)
         for (int a = 0; a < 3; ++a) hl[(size_t)j * 3 + a] = rec[lm_internal(ctx, j) * LREC + LR_L + a];
@@ -960,9 +1008,9 @@ daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
   CK(cudaMemcpy(p, ctx->cam_E, (size_t)ctx->M * 8, cudaMemcpyDeviceToHost));
   p += (size_t)ctx->M * 8;
   const size_t lb = (size_t)ctx->N * LREC * real_sz(ctx);
-  CK(cudaMemcpy(p, ctx->lmrec, lb, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(p, lmrec_at(ctx, ctx->k), lb, cudaMemcpyDeviceToHost));
   p += lb;
-  CK(cudaMemcpy(p, ctx->lm_lo, (size_t)ctx->N * 16, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(p, lmlo_at(ctx, ctx->k), (size_t)ctx->N * 16, cudaMemcpyDeviceToHost));
   *bytes = need;
   return DABA_OK;
 }
@@ -986,9 +1034,9 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
   CK(cudaMemcpy(ctx->cam_E, p, (size_t)ctx->M * 8, cudaMemcpyHostToDevice));
   p += (size_t)ctx->M * 8;
   const size_t lb = (size_t)ctx->N * LREC * real_sz(ctx);
-  CK(cudaMemcpy(ctx->lmrec, p, lb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(lmrec_at(ctx, h.k), p, lb, cudaMemcpyHostToDevice));
   p += lb;
-  CK(cudaMemcpy(ctx->lm_lo, p, (size_t)ctx->N * 16, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(lmlo_at(ctx, h.k), p, (size_t)ctx->N * 16, cudaMemcpyHostToDevice));
   int first = (int)h.first;
   CK(cudaMemcpy(ctx->d_first, &first, sizeof(int), cudaMemcpyHostToDevice));
   ctx->k = h.k;

@@ -301,6 +301,54 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
   R[8] = w * w - x * x - y * y + z * z;
 }
 
+// ProjRot3D of a matrix K close to a rotation (the extrapolation R + gamma dR of
+// Eq. nesterov_R): for det K > 0 the projection is the orthogonal polar factor of K, reached
+// by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2, which converges quadratically when
+// |X^T X - I| < 1. Falls back to proj_rot3d when K is not close enough or det K <= 0.
+__device__ inline void proj_rot3d_near(const double* __restrict__ K, double* __restrict__ R) {
+  const double det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
+                     K[2] * (K[3] * K[7] - K[4] * K[6]);
+  double X[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) X[a] = K[a];
+  bool ok = det > 0.0;
+  for (int it = 0; it < 8 && ok; ++it) {
+    double S[9];   // X^T X
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) S[i * 3 + j] = X[0 * 3 + i] * X[0 * 3 + j] + X[1 * 3 + i] * X[1 * 3 + j] + X[2 * 3 + i] * X[2 * 3 + j];
+    double dev = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double dij = S[i * 3 + j] - (i == j ? 1.0 : 0.0);
+        dev += dij * dij;
+      }
+    if (it == 0 && !(dev < 0.25)) {
+      ok = false;
+      break;
+    }
+    if (dev < 1e-30) break;
+    double Y[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Y[i * 3 + j] = 0.5 * (3.0 * X[i * 3 + j] - (X[i * 3 + 0] * S[0 * 3 + j] + X[i * 3 + 1] * S[1 * 3 + j] + X[i * 3 + 2] * S[2 * 3 + j]));
+#pragma unroll
+    for (int a = 0; a < 9; ++a) X[a] = Y[a];
+    if (it == 7) ok = false;
+  }
+  if (ok) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) R[a] = X[a];
+  } else {
+    proj_rot3d(K, R);
+  }
+}
+
 // Solves the symmetric positive definite 6x6 system A x = b in place (A lower
 // triangle used, Cholesky A = L L^T). Returns false if a pivot is not positive.
 __device__ inline bool chol6_solve(double A[6][6], double b[6]) {

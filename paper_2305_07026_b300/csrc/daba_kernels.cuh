@@ -1,16 +1,19 @@
 // daba_kernels.cuh -- the kernels of one DABA iteration (Algorithm 1, arXiv 2305.07026)
 // with one block per camera and one block per landmark.
 //
-// Per iteration k, in stream order:
+// Per iteration k:
 //   1. cpass     (warp/chunk) : camera-sorted observations; per camera the centred
 //                               majorizer statistics at xbar^k and x^k plus the F_ij and
 //                               surrogate-gap sums, one FP64 partial per chunk.
 //   2. lpass     (CTA/tile)   : landmark-sorted observations; per landmark statistics,
 //                               restart metrics, accelerated solve, restart test and MM
-//                               re-solve (closed form), in place.
+//                               re-solve (closed form); writes the other landmark buffer.
 //   3. camsolve  (M threads)  : FP64 camera block solves, restart test, MM re-solve, and
-//                               the extrapolated rotation and pack of iteration k+1.
+//                               the extrapolated rotation and pack of iteration k+1 (written
+//                               to the other pack buffer).
 //   4. finalize  (1 CTA)      : F(x^k) trace entry and restart count.
+// The landmark state and the camera pack are double-buffered, so lpass (on a second
+// stream) runs concurrently with cpass -> camsolve; finalize joins both.
 // cam_prepare builds the pack of the first iteration of a run.
 //
 // Centred statistics. For a conditioning iterate z (xbar^k or x^k) and a camera c let
@@ -114,7 +117,7 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
   double K[9], Rb[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
-  proj_rot3d(K, Rb);
+  proj_rot3d_near(K, Rb);
 #pragma unroll
   for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
   write_pack<Real>(x, dx, Rb, pack + (size_t)i * P4N);
@@ -228,6 +231,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // ---------------------------------------------------------------------------
 // 2. landmark-sorted pass: one CTA per tile of consecutive landmarks
 // ---------------------------------------------------------------------------
+// Reads the landmark state of iteration k (lmrec, lm_lo) and writes that of k+1 to the
+// other buffer, so that it can run concurrently with the camera-sorted pass.
 // Tile data: tile_lm[t] .. tile_lm[t+1] landmarks; their observations occupy the
 // landmark-sorted positions lm_ptr[first] .. lm_ptr[last]. Inside the tile the
 // observations are processed in camera order (t_cam, t_u, t_slot), where t_slot is
@@ -253,9 +258,10 @@ template <int LOSS, class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_lpass(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
             const int* __restrict__ t_cam, const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot,
-            const V4<Real>* __restrict__ pack, V4<Real>* __restrict__ lmrec, V4<float>* __restrict__ lm_lo,
-            LossC<Real> L, IterParams P, double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs,
-            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag) {
+            const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo,
+            V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out, LossC<Real> L, IterParams P,
+            double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
+            double* __restrict__ lm_Fbdiag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tile = tile0 + blockIdx.x;
   const int lb = tile_lm[tile], le = tile_lm[tile + 1];
@@ -364,7 +370,7 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       lo.y = o1;
       lo.z = o2;
       lo.w = 0.f;
-      lm_lo[g] = lo;
+      lm_lo_out[g] = lo;
     } else {
       nA.x = A.x + step0;
       nA.y = A.y + step1;
@@ -382,8 +388,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       lm_Fbdiag[g] = F + double(thr);
       nB.w = Real(F + double(dEn));
     }
-    lmrec[2 * g] = nA;
-    lmrec[2 * g + 1] = nB;
+    lmrec_out[2 * g] = nA;
+    lmrec_out[2 * g + 1] = nB;
     lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
     fsum += double(st[8]);
   }
@@ -583,7 +589,7 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const d
                            double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
                            IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
                            double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
-                           V4<Real>* __restrict__ pack) {
+                           V4<Real>* __restrict__ pack_next) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int it = *P.it;
@@ -671,10 +677,10 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const d
   double K[9], Rb[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) K[a] = nx[CS_R + a] + gn * ndx[CS_R + a];
-  proj_rot3d(K, Rb);
+  proj_rot3d_near(K, Rb);
 #pragma unroll
   for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
-  write_pack<Real>(nx, ndx, Rb, pack + (size_t)i * P4N);
+  write_pack<Real>(nx, ndx, Rb, pack_next + (size_t)i * P4N);
 }
 
 // ---------------------------------------------------------------------------
