@@ -264,6 +264,10 @@ IterParams iter_params(daba_ctx* ctx) {
   P.first = (int*)ctx->d_first;
   P.xi = ctx->opt.xi;
   P.eta = ctx->opt.eta;
+  P.eta1 = 1.0 - ctx->opt.eta;
+  P.hxi = 0.5 * ctx->opt.xi;
+  P.eta1f = (float)P.eta1;
+  P.hxif = (float)P.hxi;
   P.accelerated = ctx->opt.accelerated;
   P.n_alt = ctx->opt.cam_alternations;
   return P;
@@ -281,7 +285,7 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) 
       k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
           ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
           (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
-          (double*)ctx->chunk_part);
+          (Real*)ctx->chunk_part);
   } else if (which == 2) {
     auto kern = k_lpass<LOSS, Real, Real2, HAS_LO>;
     const int caps[2][2] = {{TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
@@ -350,7 +354,7 @@ cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   const IterParams P = iter_params(ctx);
   const int blocks = (ctx->M + 63) / 64;
   if (is_mixed(ctx))
-    k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
+    k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
                                              (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs,

@@ -70,11 +70,10 @@ struct alignas(4 * sizeof(Real)) V4 {
 
 // Camera pack read by the observation passes (V4 entries, one pack per camera):
 //   [P4_RK + r] = (R^k row r, t^k_r hi)      [P4_RB + r] = (Rbar row r, dt_r)
-//   [P4_RP + r] = (R' row r, t^k_r lo)       [P4_DR + r] = (dR row r, 0)
-//   [P4_D] = (d^k, 0)                        [P4_DD] = (dd, 0)
-// with R' = R^(k-1) = R^k - dR, dt = t^k - t^(k-1), dd = d^k - d^(k-1) formed in FP64, and
-// Rbar the extrapolated rotation of Eq. nesterov_R.
-enum { P4_RK = 0, P4_RB = 3, P4_RP = 6, P4_DR = 9, P4_D = 12, P4_DD = 13, P4N = 14 };
+//   [P4_DR + r] = (dR row r, t^k_r lo)       [P4_D] = (d^k, 0)      [P4_DD] = (dd, 0)
+// with dR = R^k - R^(k-1), dt = t^k - t^(k-1), dd = d^k - d^(k-1) formed in FP64 and
+// Rbar the extrapolated rotation of Eq. nesterov_R. R^(k-1) = R^k - dR is formed in registers.
+enum { P4_RK = 0, P4_RB = 3, P4_DR = 6, P4_D = 9, P4_DD = 10, P4N = 12 };
 
 // Per-observation output of the three-point evaluation.
 template <class Real>
@@ -103,14 +102,14 @@ __device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l
                                          Real o1, Real o2, Real dl0, Real dl1, Real dl2, Real u0, Real u1,
                                          Real gamma, const LossC<Real>& L, ObsEval<Real>& o) {
   const V4<Real> a0 = pk[P4_RK + 0], a1 = pk[P4_RK + 1], a2 = pk[P4_RK + 2];
-  const V4<Real> c0 = pk[P4_RP + 0], c1 = pk[P4_RP + 1], c2 = pk[P4_RP + 2];
+  const V4<Real> g0 = pk[P4_DR + 0], g1 = pk[P4_DR + 1], g2 = pk[P4_DR + 2];
   const V4<Real> b0 = pk[P4_RB + 0], b1 = pk[P4_RB + 1], b2 = pk[P4_RB + 2];
   const V4<Real> dd = pk[P4_DD], d = pk[P4_D];
   const Real s = u0 * u0 + u1 * u1;
   const Real s2 = s * s;
-  const Real q0 = (l0 - a0.w) + (o0 - c0.w);
-  const Real q1 = (l1 - a1.w) + (o1 - c1.w);
-  const Real q2 = (l2 - a2.w) + (o2 - c2.w);
+  const Real q0 = (l0 - a0.w) + (o0 - g0.w);
+  const Real q1 = (l1 - a1.w) + (o1 - g1.w);
+  const Real q2 = (l2 - a2.w) + (o2 - g2.w);
   // ---- x^k
   const Real pz = d.x + d.y * s + d.z * s2;
   const Real Rp0 = a0.x * u0 + a0.y * u1 + a0.z * pz;
@@ -144,7 +143,10 @@ __device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l
   }
   // ---- x^(k-1) and the surrogate gap
   {
-    const V4<Real> g0 = pk[P4_DR + 0], g1 = pk[P4_DR + 1], g2 = pk[P4_DR + 2];
+    V4<Real> c0, c1, c2;   // rows of R' = R^k - dR
+    c0.x = a0.x - g0.x, c0.y = a0.y - g0.y, c0.z = a0.z - g0.z;
+    c1.x = a1.x - g1.x, c1.y = a1.y - g1.y, c1.z = a1.z - g1.z;
+    c2.x = a2.x - g2.x, c2.y = a2.y - g2.y, c2.z = a2.z - g2.z;
     const Real pzp = pz - phidd;
     const Real qp0 = q0 - e0, qp1 = q1 - e1, qp2 = q2 - e2;
     const Real Rpp0 = c0.x * u0 + c0.y * u1 + c0.z * pzp;
@@ -170,11 +172,11 @@ template <int LOSS, class Real>
 __device__ __forceinline__ Real eval_F4(const V4<Real>* __restrict__ pk, Real l0, Real l1, Real l2, Real o0,
                                         Real o1, Real o2, Real u0, Real u1, const LossC<Real>& L) {
   const V4<Real> a0 = pk[P4_RK + 0], a1 = pk[P4_RK + 1], a2 = pk[P4_RK + 2];
-  const V4<Real> c0 = pk[P4_RP + 0], c1 = pk[P4_RP + 1], c2 = pk[P4_RP + 2];
+  const V4<Real> g0 = pk[P4_DR + 0], g1 = pk[P4_DR + 1], g2 = pk[P4_DR + 2];
   const V4<Real> d = pk[P4_D];
-  const Real q0 = (l0 - a0.w) + (o0 - c0.w);
-  const Real q1 = (l1 - a1.w) + (o1 - c1.w);
-  const Real q2 = (l2 - a2.w) + (o2 - c2.w);
+  const Real q0 = (l0 - a0.w) + (o0 - g0.w);
+  const Real q1 = (l1 - a1.w) + (o1 - g1.w);
+  const Real q2 = (l2 - a2.w) + (o2 - g2.w);
   const Real s = u0 * u0 + u1 * u1;
   const Real pz = d.x + d.y * s + d.z * s * s;
   const Real Rp0 = a0.x * u0 + a0.y * u1 + a0.z * pz;
@@ -301,6 +303,57 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
   R[8] = w * w - x * x - y * y + z * z;
 }
 
+// ProjRot3D for det K > 0: the projection onto SO(3) is then the orthogonal polar factor of
+// K, computed with Higham's scaled Newton iteration X <- (z X + X^{-T} / z) / 2 with the
+// Frobenius-norm scaling z = sqrt(|X^{-1}| / |X|), switched off once the iteration is close.
+// Falls back to the Jacobi method above when det K <= 0 or the iteration does not settle.
+__device__ inline void proj_rot3d_polar(const double* __restrict__ K, double* __restrict__ R) {
+  double X[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) X[a] = K[a];
+  bool scaled = true;
+  for (int it = 0; it < 40; ++it) {
+    double C[9];   // cofactor matrix: X^{-T} = C / det X
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    const double det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    if (!(det > 0.0)) break;
+    const double idet = 1.0 / det;
+    double z = 1.0;
+    if (scaled) {
+      double nx = 0.0, nc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        nx += X[a] * X[a];
+        nc += C[a] * C[a];
+      }
+      z = sqrt(sqrt(nc / nx) * idet);
+    }
+    const double hz = 0.5 * z, hiz = 0.5 * idet / z;
+    double dif = 0.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const double y = hz * X[a] + hiz * C[a];
+      dif += (y - X[a]) * (y - X[a]);
+      X[a] = y;
+    }
+    if (dif < 1e-6) scaled = false;
+    if (dif < 1e-30) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) R[a] = X[a];
+      return;
+    }
+  }
+  proj_rot3d(K, R);
+}
+
 // ProjRot3D of a matrix K close to a rotation (the extrapolation R + gamma dR of
 // Eq. nesterov_R): for det K > 0 the projection is the orthogonal polar factor of K, reached
 // by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2, which converges quadratically when
@@ -350,7 +403,8 @@ __device__ inline void proj_rot3d_near(const double* __restrict__ K, double* __r
 }
 
 // Solves the symmetric positive definite 6x6 system A x = b in place (A lower
-// triangle used, Cholesky A = L L^T). Returns false if a pivot is not positive.
+// triangle used, Cholesky A = L L^T; the diagonal keeps 1 / L[j][j]). Returns false if a
+// pivot is not positive.
 __device__ inline bool chol6_solve(double A[6][6], double b[6]) {
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
@@ -358,9 +412,8 @@ __device__ inline bool chol6_solve(double A[6][6], double b[6]) {
 #pragma unroll
     for (int k = 0; k < j; ++k) djj -= A[j][k] * A[j][k];
     if (!(djj > 0.0)) return false;
-    const double ljj = sqrt(djj);
-    A[j][j] = ljj;
-    const double inv = 1.0 / ljj;
+    const double inv = 1.0 / sqrt(djj);   // 1 / L[j][j]
+    A[j][j] = inv;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
       double s = A[i][j];
@@ -369,19 +422,20 @@ __device__ inline bool chol6_solve(double A[6][6], double b[6]) {
       A[i][j] = s * inv;
     }
   }
+  // A[j][j] now holds 1 / L[j][j]
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     double s = b[i];
 #pragma unroll
     for (int k = 0; k < i; ++k) s -= A[i][k] * b[k];
-    b[i] = s / A[i][i];
+    b[i] = s * A[i][i];
   }
 #pragma unroll
   for (int i = 5; i >= 0; --i) {
     double s = b[i];
 #pragma unroll
     for (int k = i + 1; k < 6; ++k) s -= A[k][i] * b[k];
-    b[i] = s / A[i][i];
+    b[i] = s * A[i][i];
   }
   return true;
 }

@@ -32,7 +32,7 @@
 
 namespace daba {
 
-// ---- chunk partial layout (doubles): Hbar[21] Bbar[18] H[21] B[18] sumF sumGap pad
+// ---- chunk partial layout (pass precision): Hbar[21] Bbar[18] H[21] B[18] sumF sumGap pad
 enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_STRIDE = 84 };
 // ---- tile partial layout (doubles): sumF restarts pad pad
 enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
@@ -43,9 +43,9 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
 constexpr int CPASS_WARPS = 4;
-constexpr int LPASS_THREADS = 256;
-constexpr int TILE_OBS = 512;     // observations of a small landmark tile
-constexpr int TILE_LMS = 256;     // landmarks of a small landmark tile
+constexpr int LPASS_THREADS = 128;
+constexpr int TILE_OBS = 256;     // observations of a small landmark tile
+constexpr int TILE_LMS = 128;     // landmarks of a small landmark tile
 constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own
 constexpr int MAX_TRACK = BIG_TILE_OBS;
 
@@ -54,9 +54,24 @@ struct IterParams {
   int* it;             // device iteration counter within the segment
   int* first;          // 1 on the first iteration after the state was set
   double xi, eta;
+  double eta1, hxi;    // 1 - eta and xi / 2
+  float eta1f, hxif;   // the same in FP32 (no FP64 instruction in the FP32 passes)
   int accelerated;
   int n_alt;
 };
+
+template <class Real>
+__device__ __forceinline__ Real eta1_of(const IterParams& P);
+template <>
+__device__ __forceinline__ float eta1_of<float>(const IterParams& P) { return P.eta1f; }
+template <>
+__device__ __forceinline__ double eta1_of<double>(const IterParams& P) { return P.eta1; }
+template <class Real>
+__device__ __forceinline__ Real hxi_of(const IterParams& P);
+template <>
+__device__ __forceinline__ float hxi_of<float>(const IterParams& P) { return P.hxif; }
+template <>
+__device__ __forceinline__ double hxi_of<double>(const IterParams& P) { return P.hxi; }
 
 __device__ __forceinline__ int tri6(int a, int b) { return a * 6 - (a * (a - 1)) / 2 + (b - a); }
 
@@ -68,7 +83,7 @@ __device__ __forceinline__ void write_pack(const double* x, const double* dx, co
     const double t = x[CS_T + r];
     const Real th = Real(t);
     const Real tl = Real(t - double(th));
-    V4<Real> a, b, c, g;
+    V4<Real> a, b, g;
     a.x = Real(x[CS_R + 3 * r + 0]);
     a.y = Real(x[CS_R + 3 * r + 1]);
     a.z = Real(x[CS_R + 3 * r + 2]);
@@ -77,17 +92,12 @@ __device__ __forceinline__ void write_pack(const double* x, const double* dx, co
     b.y = Real(Rb[3 * r + 1]);
     b.z = Real(Rb[3 * r + 2]);
     b.w = Real(dx[CS_T + r]);
-    c.x = Real(x[CS_R + 3 * r + 0] - dx[CS_R + 3 * r + 0]);
-    c.y = Real(x[CS_R + 3 * r + 1] - dx[CS_R + 3 * r + 1]);
-    c.z = Real(x[CS_R + 3 * r + 2] - dx[CS_R + 3 * r + 2]);
-    c.w = tl;
     g.x = Real(dx[CS_R + 3 * r + 0]);
     g.y = Real(dx[CS_R + 3 * r + 1]);
     g.z = Real(dx[CS_R + 3 * r + 2]);
-    g.w = Real(0);
+    g.w = tl;
     pk[P4_RK + r] = a;
     pk[P4_RB + r] = b;
-    pk[P4_RP + r] = c;
     pk[P4_DR + r] = g;
   }
   V4<Real> d, e;
@@ -167,7 +177,7 @@ template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
             const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
-            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, double* __restrict__ part) {
+            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
   const int wib = threadIdx.x >> 5;
   const int warp = blockIdx.x * CPASS_WARPS + wib;
@@ -213,7 +223,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
     uu = un;
     jn = jnn;
   }
-  // warp reduction, lane 0 writes the FP64 partial
+  // warp reduction; the partial is stored in the pass precision and summed over the
+  // camera's chunks in FP64 by the camera solve
 #pragma unroll
   for (int k = 0; k < 80; ++k) {
     Real v = acc[k];
@@ -222,9 +233,9 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
     acc[k] = v;
   }
   if (lane == 0) {
-    double* out = part + (size_t)warp * CP_STRIDE;
+    Real* out = part + (size_t)warp * CP_STRIDE;
 #pragma unroll
-    for (int k = 0; k < 80; ++k) out[k] = double(acc[k]);
+    for (int k = 0; k < 80; ++k) out[k] = acc[k];
   }
 }
 
@@ -319,9 +330,9 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   }
   __syncthreads();
 
-  const double xi = P.xi, eta = P.eta;
-  double fsum = 0.0;
+  Real fsum = Real(0);
   int nrs = 0;
+  const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
   for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
     const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
     Real st[10];
@@ -331,13 +342,12 @@ __global__ void __launch_bounds__(LPASS_THREADS)
 #pragma unroll
       for (int k = 0; k < 10; ++k) st[k] += sc[k * no_cap + s];
     const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
-    const Real hx = Real(0.5) * Real(xi);
     const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
     // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
     //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
     const Real dE = -hx * (dl0 * dl0 + dl1 * dl1 + dl2 * dl2) + Real(0.5) * st[9];
     const Real S = first ? Real(0) : B.z;
-    const Real thr = Real(1.0 - eta) * (S - dE);
+    const Real thr = eta1 * (S - dE);
     // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), as a step from l^k
     const Real ib = fdiv(Real(1), st[0] + hx);
     const Real sa0 = gamma * dl0 - st[1] * ib, sa1 = gamma * dl1 - st[2] * ib, sa2 = gamma * dl2 - st[3] * ib;
@@ -391,9 +401,10 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     lmrec_out[2 * g] = nA;
     lmrec_out[2 * g + 1] = nB;
     lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
-    fsum += double(st[8]);
+    fsum += st[8];
   }
-  // tile sums: F(x^k) part and restart count (FP64, fixed order)
+  // tile sums: F(x^k) part (per warp in the pass precision, across warps in FP64) and the
+  // restart count, in a fixed order
   __shared__ double red[LPASS_THREADS / 32];
   __shared__ int redi[LPASS_THREADS / 32];
 #pragma unroll
@@ -402,7 +413,7 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
   }
   if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = fsum;
+    red[threadIdx.x >> 5] = double(fsum);
     redi[threadIdx.x >> 5] = nrs;
   }
   __syncthreads();
@@ -513,7 +524,7 @@ __device__ inline void cam_scam(const double H[6][6], const double B[6][3], cons
       K[r * 3 + 1] = xi * z.R[r * 3 + 1] + 2.0 * G[r][1];
       K[r * 3 + 2] = xi * z.R[r * 3 + 2] + 2.0 * (c.d[0] * G[r][2] + c.d[1] * G[r][3] + c.d[2] * G[r][4]);
     }
-    proj_rot3d(K, c.R);
+    proj_rot3d_polar(K, c.R);
     // ---- (t, d)-step
     const double v[3] = {c.R[2], c.R[5], c.R[8]};
     const double vz[3] = {z.R[2], z.R[5], z.R[8]};
@@ -585,7 +596,7 @@ __device__ inline void unpack_stats(const double* s, double H[6][6], double B[6]
 }
 
 template <class Real>
-__global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const double* __restrict__ part,
+__global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
                            double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
                            IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
                            double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
@@ -599,15 +610,15 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const d
 #pragma unroll
   for (int k = 0; k < 39; ++k) sb[k] = sk[k] = 0.0;
   double sF = 0.0, sG = 0.0;
-  for (int c = cam_chunk_ptr[i]; c < cam_chunk_ptr[i + 1]; ++c) {
-    const double* p = part + (size_t)c * CP_STRIDE;
+  for (int c = cam_chunk_ptr[i]; c < cam_chunk_ptr[i + 1]; ++c) {   // FP64 accumulation
+    const Real* p = part + (size_t)c * CP_STRIDE;
 #pragma unroll
     for (int k = 0; k < 39; ++k) {
-      sb[k] += p[CP_HB + k];
-      sk[k] += p[CP_H + k];
+      sb[k] += double(p[CP_HB + k]);
+      sk[k] += double(p[CP_H + k]);
     }
-    sF += p[CP_F];
-    sG += p[CP_G];
+    sF += double(p[CP_F]);
+    sG += double(p[CP_G]);
   }
   double* x = cam_x + (size_t)i * CSTRIDE;
   double* dx = cam_dx + (size_t)i * CSTRIDE;
@@ -759,18 +770,18 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
   }
   __syncthreads();
-  double fsum = 0.0;
+  Real fsum = Real(0);
   for (int o = threadIdx.x; o < no; o += blockDim.x) {
     const int cam = t_cam[ob + o];
     const Real2 uu = t_u[ob + o];
     const int jl = smap[t_slot[ob + o]];
     const V4<Real> A = sl[jl * 2], C = sl[jl * 2 + 1];
-    fsum += double(eval_F4<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, uu.x, uu.y, L));
+    fsum += eval_F4<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, uu.x, uu.y, L);
   }
   __shared__ double red[LPASS_THREADS / 32];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fsum;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = double(fsum);
   __syncthreads();
   if (threadIdx.x == 0) {
     double f = 0.0;
