@@ -173,12 +173,37 @@ __device__ __forceinline__ void accumulate_cam(Real* acc, const ObsEval<Real>& e
   acc[CP_G] += ev.gap;
 }
 
+// asynchronous global -> shared copies (cp.async) used to stage gathered records
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int CPASS_STAGES = 4;   // batches of 32 observations in flight per warp
+
+// Per lane and stage: the landmark record (two V4) and the pixel.
+template <class Real, class Real2>
+struct CpassStage {
+  V4<Real> rec[2];
+  Real2 u;
+};
+
 template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
             const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
             const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
+  __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
   const int wib = threadIdx.x >> 5;
   const int warp = blockIdx.x * CPASS_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -192,37 +217,49 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   Real acc[80];
 #pragma unroll
   for (int k = 0; k < 80; ++k) acc[k] = Real(0);
-  // software pipeline: landmark record one step ahead, landmark index two steps ahead
-  int o = b + lane;
-  V4<Real> r0, r1;
-  Real2 uu;
-  int jn = 0;
-  if (o < e) {
-    const int j = c_lm[o];
-    uu = c_u[o];
-    r0 = lmrec[2 * (size_t)j];
-    r1 = lmrec[2 * (size_t)j + 1];
-  }
-  if (o + 32 < e) jn = c_lm[o + 32];
-  for (; o < e; o += 32) {
-    V4<Real> n0, n1;
-    Real2 un;
-    int jnn = 0;
-    if (o + 32 < e) {
-      n0 = lmrec[2 * (size_t)jn];
-      n1 = lmrec[2 * (size_t)jn + 1];
-      un = c_u[o + 32];
-      if (o + 64 < e) jnn = c_lm[o + 64];
+  // Pipeline over batches t of 32 observations (one per lane): the landmark index of batch
+  // t + S is loaded while the records of batch t + S - 1 are copied asynchronously and batch
+  // t is evaluated. Each lane only touches its own staging slots.
+  const int nb = (e - b + 31) >> 5;
+  CpassStage<Real, Real2>(*stg)[32] = sbuf[wib];
+  auto issue = [&](int t, int j) {
+    const int o = b + 32 * t + lane;
+    if (o < e) {
+      CpassStage<Real, Real2>& d = stg[t % CPASS_STAGES][lane];
+      const V4<Real>* src = lmrec + 2 * (size_t)j;
+#pragma unroll
+      for (int q = 0; q < (int)(2 * sizeof(V4<Real>) / 16); ++q)
+        cp_async16(reinterpret_cast<char*>(d.rec) + 16 * q, reinterpret_cast<const char*>(src) + 16 * q);
+      if (sizeof(Real2) == 16)
+        cp_async16(&d.u, c_u + o);
+      else
+        cp_async8(&d.u, c_u + o);
     }
-    ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
-                         ev);
-    accumulate_cam<Real>(acc, ev, uu.x, uu.y);
-    r0 = n0;
-    r1 = n1;
-    uu = un;
-    jn = jnn;
+    cp_async_commit();
+  };
+  auto index_of = [&](int t) -> int {
+    const int o = b + 32 * t + lane;
+    return o < e ? c_lm[o] : 0;
+  };
+#pragma unroll
+  for (int t = 0; t < CPASS_STAGES - 1; ++t) issue(t, index_of(t));
+  int jn = index_of(CPASS_STAGES - 1);
+  for (int t = 0; t < nb; ++t) {
+    issue(t + CPASS_STAGES - 1, jn);
+    jn = index_of(t + CPASS_STAGES);
+    cp_async_wait<CPASS_STAGES - 1>();
+    const int o = b + 32 * t + lane;
+    if (o < e) {
+      const CpassStage<Real, Real2>& d = stg[t % CPASS_STAGES][lane];
+      const V4<Real> r0 = d.rec[0], r1 = d.rec[1];
+      const Real2 uu = d.u;
+      ObsEval<Real> ev;
+      eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
+                           ev);
+      accumulate_cam<Real>(acc, ev, uu.x, uu.y);
+    }
   }
+  cp_async_wait<0>();
   // warp reduction; the partial is stored in the pass precision and summed over the
   // camera's chunks in FP64 by the camera solve
 #pragma unroll
