@@ -37,7 +37,8 @@ struct daba_ctx {
   std::string err;
   int dev = 0;
   // sizes of the schedules
-  int n_chunks = 0, n_tiles = 0, n_small_tiles = 0, max_chunks = 0, max_tiles = 0;
+  int n_chunks = 0, n_tiles = 0, max_chunks = 0, max_tiles = 0;
+  int tile_class_end[3] = {0, 0, 0};   // tiles [0, e0): staged cameras, [e0, e1): unstaged, [e1, e2): big
   bool obs_set = false, state_set = false, checked = false;
   double s_norm = 0.0, u_scale_uploaded = -1.0;
   double s_k = 1.0;   // Nesterov s^(k)
@@ -56,7 +57,8 @@ struct daba_ctx {
   // device buffers
   void *c_lm = nullptr, *c_u = nullptr, *c_orig = nullptr, *cam_ptr = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
-  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_cam = nullptr, *t_u = nullptr, *t_slot = nullptr, *l_orig = nullptr;
+  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_key = nullptr, *t_u = nullptr, *l_orig = nullptr;
+  void *tile_cam_ptr = nullptr, *tile_cams = nullptr;
   void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack2[2] = {nullptr, nullptr};
   void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
   void *lmrec2[2] = {nullptr, nullptr}, *lm_lo2[2] = {nullptr, nullptr};   // double-buffered landmark state
@@ -277,7 +279,6 @@ template <int LOSS, class Real, class Real2, bool HAS_LO>
 cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   const LossC<Real> L = loss_consts<Real>(ctx);
   const IterParams P = iter_params(ctx);
-  const int n_small = ctx->n_small_tiles, n_big = ctx->n_tiles - ctx->n_small_tiles;
   if (which == 1) {
     const int threads = CPASS_WARPS * 32;
     const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
@@ -287,34 +288,42 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) 
           (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
           (Real*)ctx->chunk_part);
   } else if (which == 2) {
-    auto kern = k_lpass<LOSS, Real, Real2, HAS_LO>;
-    const int caps[2][2] = {{TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
-    const int t0[2] = {0, n_small}, nt[2] = {n_small, n_big};
-    for (int c = 0; c < 2; ++c) {
-      if (nt[c] == 0) continue;
-      const size_t smem = lpass_smem_bytes<Real>(caps[c][0], caps[c][1]);
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<nt[c], LPASS_THREADS, smem, st>>>(
-          t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
-          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)pack_at(ctx, k),
-          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), (V4<Real>*)lmrec_at(ctx, k + 1),
-          (V4<float>*)lmlo_at(ctx, k + 1), L, P, (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs,
-          (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
-      if (c == 1) ctx->launches++;
+    // three tile classes: cameras staged in smem, unstaged small tiles, one-landmark big tiles
+    const int caps[3][3] = {{TILE_OBS, TILE_LMS, TILE_CAMS}, {TILE_OBS, TILE_LMS, 0}, {BIG_TILE_OBS, 1, 0}};
+    int t0 = 0;
+    for (int c = 0; c < 3; ++c) {
+      const int nt = ctx->tile_class_end[c] - t0;
+      if (nt > 0) {
+        const size_t smem = lpass_smem_bytes<Real>(caps[c][0], caps[c][1], caps[c][2]);
+        auto kern = c == 0 ? k_lpass<LOSS, Real, Real2, HAS_LO, true> : k_lpass<LOSS, Real, Real2, HAS_LO, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<nt, LPASS_THREADS, smem, st>>>(
+            t0, caps[c][0], caps[c][1], caps[c][2], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr,
+            (const int*)ctx->tile_cam_ptr, (const int*)ctx->tile_cams, (const uint32_t*)ctx->t_key,
+            (const Real2*)ctx->t_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k),
+            (const V4<float>*)lmlo_at(ctx, k), (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), L, P,
+            (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
+        if (c) ctx->launches++;
+      }
+      t0 = ctx->tile_class_end[c];
     }
   } else if (which == 6) {
     auto kern = k_objective<LOSS, Real, Real2, HAS_LO>;
-    const int caps[2][2] = {{TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
-    const int t0[2] = {0, n_small}, nt[2] = {n_small, n_big};
-    for (int c = 0; c < 2; ++c) {
-      if (nt[c] == 0) continue;
-      const size_t smem = (size_t)caps[c][1] * 2 * sizeof(V4<Real>) + (size_t)caps[c][0] * 2 + 16;
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      kern<<<nt[c], LPASS_THREADS, smem, st>>>(
-          t0[c], caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cam,
-          (const Real2*)ctx->t_u, (const uint16_t*)ctx->t_slot, (const V4<Real>*)pack_at(ctx, k),
-          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), L, (double*)ctx->tile_part);
-      if (c == 1) ctx->launches++;
+    const int caps[3][2] = {{TILE_OBS, TILE_LMS}, {TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
+    int t0 = 0;
+    for (int c = 0; c < 3; ++c) {
+      const int nt = ctx->tile_class_end[c] - t0;
+      if (nt > 0) {
+        const size_t smem = (size_t)caps[c][1] * 2 * sizeof(V4<Real>) + (size_t)caps[c][0] * 2 + 16;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<nt, LPASS_THREADS, smem, st>>>(
+            t0, caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr,
+            (const int*)ctx->tile_cam_ptr, (const int*)ctx->tile_cams, (const uint32_t*)ctx->t_key,
+            (const Real2*)ctx->t_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k),
+            (const V4<float>*)lmlo_at(ctx, k), L, (double*)ctx->tile_part);
+        if (c) ctx->launches++;
+      }
+      t0 = ctx->tile_class_end[c];
     }
   }
   return cudaGetLastError();
@@ -465,7 +474,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   cudaGetDevice(&ctx->dev);
   const size_t R = real_sz(ctx);
   ctx->max_chunks = (int)(M + nnz / CHUNK_OBS + 1);
-  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS) + nnz / TILE_OBS + 4);
+  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS + nnz / TILE_CAMS) + nnz / TILE_OBS + 8);
 #define AL(field, bytes)                                   \
   if ((st = dalloc(ctx, &ctx->field, (bytes))) != DABA_OK) { \
     daba_ctx* c_ = ctx;                                    \
@@ -481,9 +490,10 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(cam_chunk_ptr, (size_t)(M + 1) * 4);
   AL(lm_ptr, (size_t)(N + 1) * 4);
   AL(tile_lm, (size_t)(ctx->max_tiles + 1) * 4);
-  AL(t_cam, nnz * 4);
+  AL(t_key, nnz * 4);
   AL(t_u, nnz * 2 * R);
-  AL(t_slot, nnz * 2);
+  AL(tile_cam_ptr, (size_t)(ctx->max_tiles + 1) * 4);
+  AL(tile_cams, nnz * 4);
   AL(l_orig, nnz * 4);
   AL(cam_x, (size_t)M * CSTRIDE * 8);
   AL(cam_dx, (size_t)M * CSTRIDE * 8);
@@ -566,17 +576,20 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   // seen by the same cameras become neighbours), landmarks with long tracks last
   std::vector<int32_t> min_cam(N, M);
   for (int64_t o = 0; o < n; ++o) min_cam[li[o]] = std::min(min_cam[li[o]], ci[o]);
+  // tile class of a landmark: 0 = at most TILE_CAMS observations (camera packs staged in
+  // shared memory), 1 = at most TILE_OBS, 2 = longer (a tile of its own)
+  auto lclass = [&](int j) {
+    const int dg = lm_ptr[j + 1] - lm_ptr[j];
+    return dg <= TILE_CAMS ? 0 : (dg <= TILE_OBS ? 1 : 2);
+  };
   std::vector<int32_t> lperm(N), linv(N);
   for (int j = 0; j < N; ++j) lperm[j] = j;
-  auto is_big = [&](int j) { return lm_ptr[j + 1] - lm_ptr[j] > TILE_OBS; };
   std::stable_sort(lperm.begin(), lperm.end(), [&](int32_t a, int32_t b) {
-    const bool ba = is_big(a), bb = is_big(b);
-    if (ba != bb) return bb;
+    const int ca = lclass(a), cb = lclass(b);
+    if (ca != cb) return ca < cb;
     return min_cam[a] < min_cam[b];
   });
   for (int q = 0; q < N; ++q) linv[lperm[q]] = q;
-  int n_small_lms = 0;
-  while (n_small_lms < N && !is_big(lperm[n_small_lms])) ++n_small_lms;
   std::vector<int32_t> lii(n), li_order, lmi_ptr;
   for (int64_t o = 0; o < n; ++o) lii[o] = linv[li[o]];
   counting_sort(lii, N, li_order, lmi_ptr);
@@ -591,30 +604,50 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   }
   cam_chunk_ptr[M] = (int32_t)chunk_cam.size();
   chunk_beg.push_back((int32_t)n);
-  // landmark tiles over internal ids: small tiles of consecutive landmarks (at most TILE_OBS
-  // observations and TILE_LMS landmarks), then one big tile per long-track landmark
+  // landmark tiles over internal ids, class by class: consecutive landmarks with at most
+  // TILE_OBS observations, TILE_LMS landmarks and (class 0) TILE_CAMS distinct cameras
   std::vector<int32_t> tile_lm;
   tile_lm.push_back(0);
+  int class_end[3] = {0, 0, 0};
   {
+    std::vector<int32_t> stamp(M, -1);
     int j = 0;
-    while (j < n_small_lms) {
-      int j2 = j, cnt = 0;
-      while (j2 < n_small_lms && j2 - j < TILE_LMS && cnt + (lmi_ptr[j2 + 1] - lmi_ptr[j2]) <= TILE_OBS) {
-        cnt += lmi_ptr[j2 + 1] - lmi_ptr[j2];
-        ++j2;
+    for (int c = 0; c < 3; ++c) {
+      while (j < N && lclass(lperm[j]) == c) {
+        const int tid = (int)tile_lm.size() - 1;
+        int j2 = j, cnt = 0, ncam = 0;
+        while (j2 < N && lclass(lperm[j2]) == c) {
+          const int dg = lmi_ptr[j2 + 1] - lmi_ptr[j2];
+          if (j2 > j && (c == 2 || j2 - j >= TILE_LMS || cnt + dg > TILE_OBS)) break;
+          int fresh = 0;
+          if (c == 0) {
+            for (int o = lmi_ptr[j2]; o < lmi_ptr[j2 + 1]; ++o) {
+              const int cam = ci[li_order[o]];
+              if (stamp[cam] != tid) {
+                stamp[cam] = tid;
+                ++fresh;
+              }
+            }
+            if (j2 > j && ncam + fresh > TILE_CAMS) break;   // the next tile gets a new stamp
+          }
+          ncam += fresh;
+          cnt += dg;
+          ++j2;
+        }
+        j = j2;
+        tile_lm.push_back(j);
       }
-      j = j2;
-      tile_lm.push_back(j);
+      class_end[c] = (int)tile_lm.size() - 1;
     }
   }
-  const int n_small_tiles = (int)tile_lm.size() - 1;
-  for (int j = n_small_lms; j < N; ++j) tile_lm.push_back(j + 1);
   const int n_tiles = (int)tile_lm.size() - 1;
   if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
     return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
-  // inside each tile: observations in camera order (ties by landmark-sorted position)
-  std::vector<int32_t> t_order(n), t_cam(n), c_lm(n);
-  std::vector<uint16_t> t_slot(n);
+  // inside each tile: observations in camera order (ties by landmark-sorted position), the
+  // tile's distinct cameras and per-observation keys (local camera << 16 | slot)
+  std::vector<int32_t> t_order(n), c_lm(n), tile_cam_ptr(n_tiles + 1, 0), tile_cams;
+  std::vector<uint32_t> t_key(n);
+  tile_cams.reserve(n / 4 + 16);
   for (int t = 0; t < n_tiles; ++t) {
     const int ob = lmi_ptr[tile_lm[t]], oe = lmi_ptr[tile_lm[t + 1]];
     for (int o = ob; o < oe; ++o) t_order[o] = o;
@@ -622,11 +655,19 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
       const int32_t ca = ci[li_order[a]], cb = ci[li_order[b]];
       return ca != cb ? ca < cb : a < b;
     });
+    tile_cam_ptr[t] = (int32_t)tile_cams.size();
+    int last = -1;
     for (int o = ob; o < oe; ++o) {
-      t_cam[o] = ci[li_order[t_order[o]]];
-      t_slot[o] = (uint16_t)(t_order[o] - ob);
+      const int cam = ci[li_order[t_order[o]]];
+      if (cam != last) {
+        tile_cams.push_back(cam);
+        last = cam;
+      }
+      const uint32_t lc = (uint32_t)(tile_cams.size() - 1 - tile_cam_ptr[t]);
+      t_key[o] = (lc << 16) | (uint32_t)(t_order[o] - ob);
     }
   }
+  tile_cam_ptr[n_tiles] = (int32_t)tile_cams.size();
   for (int64_t o = 0; o < n; ++o) c_lm[o] = lii[c_order[o]];
   // keep the current iterate (if any) across the renumbering; displacements and the
   // restart metrics are reset (x^(k-1) = x^k, S = 0)
@@ -645,13 +686,14 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->lm_ptr, lmi_ptr.data(), (N + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->t_cam, t_cam.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_key, t_key.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->tile_cam_ptr, tile_cam_ptr.data(), tile_cam_ptr.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->tile_cams, tile_cams.data(), tile_cams.size() * 4 + 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->l_orig, l_order.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
   ctx->n_tiles = n_tiles;
-  ctx->n_small_tiles = n_small_tiles;
+  for (int c = 0; c < 3; ++c) ctx->tile_class_end[c] = class_end[c];
   ctx->h_cam_idx.swap(ci);
   ctx->h_lm_idx.swap(li);
   ctx->h_uv.swap(uvh);

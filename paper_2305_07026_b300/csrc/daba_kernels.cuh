@@ -45,7 +45,8 @@ enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 constexpr int CPASS_WARPS = 4;
 constexpr int LPASS_THREADS = 128;
 constexpr int TILE_OBS = 256;     // observations of a small landmark tile
-constexpr int TILE_LMS = 128;     // landmarks of a small landmark tile
+constexpr int TILE_LMS = 64;      // landmarks of a small landmark tile
+constexpr int TILE_CAMS = 64;     // distinct cameras of a small landmark tile (packs staged in smem)
 constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own
 constexpr int MAX_TRACK = BIG_TILE_OBS;
 
@@ -282,13 +283,16 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // Reads the landmark state of iteration k (lmrec, lm_lo) and writes that of k+1 to the
 // other buffer, so that it can run concurrently with the camera-sorted pass.
 // Tile data: tile_lm[t] .. tile_lm[t+1] landmarks; their observations occupy the
-// landmark-sorted positions lm_ptr[first] .. lm_ptr[last]. Inside the tile the
-// observations are processed in camera order (t_cam, t_u, t_slot), where t_slot is
-// the observation's landmark-sorted position relative to the tile start.
-// Shared memory: nl_cap x 3 V4 staged landmarks, no_cap x 10 contributions, slot map.
+// landmark-sorted positions lm_ptr[first] .. lm_ptr[last]; the tile's distinct cameras are
+// tile_cams[tile_cam_ptr[t] .. tile_cam_ptr[t+1]]. Inside the tile the observations are
+// processed in camera order: t_key = (local camera << 16) | slot, where slot is the
+// observation's landmark-sorted position relative to the tile start, and t_u its pixel.
+// Shared memory: nc_cap camera packs (small tiles), nl_cap x 3 V4 staged landmarks,
+// no_cap x 10 contributions, slot map.
 template <class Real>
-__host__ __device__ inline size_t lpass_smem_bytes(int no_cap, int nl_cap) {
-  return (size_t)nl_cap * 3 * sizeof(V4<Real>) + (size_t)no_cap * 10 * sizeof(Real) + (size_t)no_cap * 2 + 16;
+__host__ __device__ inline size_t lpass_smem_bytes(int no_cap, int nl_cap, int nc_cap) {
+  return (size_t)nc_cap * P4N * sizeof(V4<Real>) + (size_t)nl_cap * 3 * sizeof(V4<Real>) +
+         (size_t)no_cap * 10 * sizeof(Real) + (size_t)no_cap * 2 + 16;
 }
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
@@ -302,10 +306,11 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   hi = h2;
 }
 
-template <int LOSS, class Real, class Real2, bool HAS_LO>
+template <int LOSS, class Real, class Real2, bool HAS_LO, bool STAGE>
 __global__ void __launch_bounds__(LPASS_THREADS)
-    k_lpass(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-            const int* __restrict__ t_cam, const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot,
+    k_lpass(int tile0, int no_cap, int nl_cap, int nc_cap, const int* __restrict__ tile_lm,
+            const int* __restrict__ lm_ptr, const int* __restrict__ tile_cam_ptr, const int* __restrict__ tile_cams,
+            const uint32_t* __restrict__ t_key, const Real2* __restrict__ t_u,
             const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo,
             V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out, LossC<Real> L, IterParams P,
             double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
@@ -316,12 +321,16 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  V4<Real>* sl = reinterpret_cast<V4<Real>*>(smem_raw);                  // nl_cap x 3
+  const int cb = tile_cam_ptr[tile], nc = tile_cam_ptr[tile + 1] - cb;
+  V4<Real>* spk = reinterpret_cast<V4<Real>*>(smem_raw);                 // nc_cap x P4N camera packs
+  V4<Real>* sl = spk + (size_t)nc_cap * P4N;                              // nl_cap x 3
   Real* sc = reinterpret_cast<Real*>(sl + (size_t)nl_cap * 3);           // 10 x no_cap (SoA)
   uint16_t* smap = reinterpret_cast<uint16_t*>(sc + (size_t)no_cap * 10);   // slot -> local landmark
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
 
+  if (STAGE)
+    for (int q = threadIdx.x; q < nc * P4N; q += blockDim.x) spk[q] = pack[(size_t)tile_cams[cb + q / P4N] * P4N + q % P4N];
   for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
     const size_t g = (size_t)(lb + jl);
     sl[jl * 3 + 0] = lmrec[2 * g];
@@ -343,14 +352,15 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   __syncthreads();
 
   for (int o = threadIdx.x; o < no; o += blockDim.x) {
-    const int cam = t_cam[ob + o];
+    const uint32_t key = t_key[ob + o];
     const Real2 uu = t_u[ob + o];
-    const int slot = t_slot[ob + o];
+    const int lc = (int)(key >> 16);
+    const int slot = (int)(key & 0xffffu);
     const int jl = smap[slot];
     const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
+    const V4<Real>* pk = STAGE ? spk + (size_t)lc * P4N : pack + (size_t)tile_cams[cb + lc] * P4N;
     ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, A.w, B.x, B.y, uu.x, uu.y, gamma,
-                         L, ev);
+    eval_obs<LOSS, Real>(pk, A.x, A.y, A.z, C.x, C.y, C.z, A.w, B.x, B.y, uu.x, uu.y, gamma, L, ev);
     // landmark statistics: sum w lambda^2 and sum w lambda r0' with r0' = -R e / 2
     const Real wlb = ev.wb * ev.lamb;
     const Real wl = ev.w * ev.lam;
@@ -778,7 +788,8 @@ __global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, in
 template <int LOSS, class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_objective(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-                const int* __restrict__ t_cam, const Real2* __restrict__ t_u, const uint16_t* __restrict__ t_slot,
+                const int* __restrict__ tile_cam_ptr, const int* __restrict__ tile_cams,
+                const uint32_t* __restrict__ t_key, const Real2* __restrict__ t_u,
                 const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec,
                 const V4<float>* __restrict__ lm_lo, LossC<Real> L, double* __restrict__ tile_part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -808,10 +819,12 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   }
   __syncthreads();
   Real fsum = Real(0);
+  const int cb = tile_cam_ptr[tile];
   for (int o = threadIdx.x; o < no; o += blockDim.x) {
-    const int cam = t_cam[ob + o];
+    const uint32_t key = t_key[ob + o];
+    const int cam = tile_cams[cb + (int)(key >> 16)];
     const Real2 uu = t_u[ob + o];
-    const int jl = smap[t_slot[ob + o]];
+    const int jl = smap[key & 0xffffu];
     const V4<Real> A = sl[jl * 2], C = sl[jl * 2 + 1];
     fsum += eval_F4<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, uu.x, uu.y, L);
   }
