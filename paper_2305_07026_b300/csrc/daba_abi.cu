@@ -38,7 +38,7 @@ struct daba_ctx {
   int dev = 0;
   // sizes of the schedules
   int n_chunks = 0, n_tiles = 0, max_chunks = 0, max_tiles = 0;
-  int tile_class_end[3] = {0, 0, 0};   // tiles [0, e0): staged cameras, [e0, e1): unstaged, [e1, e2): big
+  int tile_class_end[2] = {0, 0};   // tiles [0, e0): small, [e0, e1): one long-track landmark each
   bool obs_set = false, state_set = false, checked = false;
   double s_norm = 0.0, u_scale_uploaded = -1.0;
   double s_k = 1.0;   // Nesterov s^(k)
@@ -51,19 +51,21 @@ struct daba_ctx {
   std::vector<double> h_uv;
   std::vector<int32_t> h_c_order, h_cam_ptr, h_l_order, h_lm_ptr, h_t_order;
   std::vector<int32_t> h_li_order;          // observations sorted by internal landmark id
+  std::vector<int32_t> h_ci_order;          // observations in the device's camera order
   std::vector<int32_t> h_lperm, h_linv;     // internal -> external landmark id and inverse
   std::vector<double> h_t;   // camera centres of the state last set (for the Asm. 2 check)
   std::vector<double> h_l;
   // device buffers
-  void *c_lm = nullptr, *c_u = nullptr, *c_orig = nullptr, *cam_ptr = nullptr;
+  void *c_lm = nullptr, *c_u = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
-  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_key = nullptr, *t_u = nullptr, *l_orig = nullptr;
-  void *tile_cam_ptr = nullptr, *tile_cams = nullptr;
+  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_cpos = nullptr, *t_slot = nullptr;
+  void *rec_a = nullptr, *rec_b = nullptr, *rec_c = nullptr;   // landmark-side records in camera order
   void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack2[2] = {nullptr, nullptr};
   void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
   void *lmrec2[2] = {nullptr, nullptr}, *lm_lo2[2] = {nullptr, nullptr};   // double-buffered landmark state
   void *lm_rs = nullptr, *lm_Fd = nullptr, *lm_Fbd = nullptr;
-  void *chunk_part = nullptr, *tile_part = nullptr;
+  void *chunk_part = nullptr, *chunk_f = nullptr, *tile_rs = nullptr, *cam_Fsum = nullptr;
+  void *fin_blk = nullptr, *fin_ticket = nullptr;
   void *d_gam = nullptr, *d_it = nullptr, *d_first = nullptr, *d_flag = nullptr, *d_trace = nullptr,
        *d_rs = nullptr, *d_obj = nullptr;
   std::vector<void*> allocs;
@@ -203,18 +205,13 @@ void counting_sort(const std::vector<int32_t>& key, int K, std::vector<int32_t>&
 template <class Real, class Real2>
 void upload_u(daba_ctx* ctx, cudaStream_t st, cudaError_t* err) {
   const double s = ctx->s_norm;
-  std::vector<Real2> cu(ctx->nnz), tu(ctx->nnz);
+  std::vector<Real2> cu(ctx->nnz);
   for (int64_t o = 0; o < ctx->nnz; ++o) {
-    const int32_t i = ctx->h_c_order[o];
+    const int32_t i = ctx->h_ci_order[o];
     cu[o].x = Real(ctx->h_uv[2 * (size_t)i] / s);
     cu[o].y = Real(ctx->h_uv[2 * (size_t)i + 1] / s);
-    const int32_t j = ctx->h_li_order[ctx->h_t_order[o]];
-    tu[o].x = Real(ctx->h_uv[2 * (size_t)j] / s);
-    tu[o].y = Real(ctx->h_uv[2 * (size_t)j + 1] / s);
   }
   *err = cudaMemcpyAsync(ctx->c_u, cu.data(), cu.size() * sizeof(Real2), cudaMemcpyHostToDevice, st);
-  if (*err == cudaSuccess)
-    *err = cudaMemcpyAsync(ctx->t_u, tu.data(), tu.size() * sizeof(Real2), cudaMemcpyHostToDevice, st);
   if (*err == cudaSuccess) *err = cudaStreamSynchronize(st);
 }
 
@@ -279,52 +276,19 @@ template <int LOSS, class Real, class Real2, bool HAS_LO>
 cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   const LossC<Real> L = loss_consts<Real>(ctx);
   const IterParams P = iter_params(ctx);
+  const int threads = CPASS_WARPS * 32;
+  const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
+  if (blocks == 0) return cudaSuccess;
   if (which == 1) {
-    const int threads = CPASS_WARPS * 32;
-    const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
-    if (blocks > 0)
-      k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
-          ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
-          (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
-          (Real*)ctx->chunk_part);
-  } else if (which == 2) {
-    // three tile classes: cameras staged in smem, unstaged small tiles, one-landmark big tiles
-    const int caps[3][3] = {{TILE_OBS, TILE_LMS, TILE_CAMS}, {TILE_OBS, TILE_LMS, 0}, {BIG_TILE_OBS, 1, 0}};
-    int t0 = 0;
-    for (int c = 0; c < 3; ++c) {
-      const int nt = ctx->tile_class_end[c] - t0;
-      if (nt > 0) {
-        const size_t smem = lpass_smem_bytes<Real>(caps[c][0], caps[c][1], caps[c][2]);
-        auto kern = c == 0 ? k_lpass<LOSS, Real, Real2, HAS_LO, true> : k_lpass<LOSS, Real, Real2, HAS_LO, false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<nt, LPASS_THREADS, smem, st>>>(
-            t0, caps[c][0], caps[c][1], caps[c][2], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr,
-            (const int*)ctx->tile_cam_ptr, (const int*)ctx->tile_cams, (const uint32_t*)ctx->t_key,
-            (const Real2*)ctx->t_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k),
-            (const V4<float>*)lmlo_at(ctx, k), (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), L, P,
-            (double*)ctx->tile_part, (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
-        if (c) ctx->launches++;
-      }
-      t0 = ctx->tile_class_end[c];
-    }
+    k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
+        ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+        (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
+        (Real*)ctx->chunk_part, (V4<Real>*)ctx->rec_a, (V4<Real>*)ctx->rec_b, (Real2*)ctx->rec_c);
   } else if (which == 6) {
-    auto kern = k_objective<LOSS, Real, Real2, HAS_LO>;
-    const int caps[3][2] = {{TILE_OBS, TILE_LMS}, {TILE_OBS, TILE_LMS}, {BIG_TILE_OBS, 1}};
-    int t0 = 0;
-    for (int c = 0; c < 3; ++c) {
-      const int nt = ctx->tile_class_end[c] - t0;
-      if (nt > 0) {
-        const size_t smem = (size_t)caps[c][1] * 2 * sizeof(V4<Real>) + (size_t)caps[c][0] * 2 + 16;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<nt, LPASS_THREADS, smem, st>>>(
-            t0, caps[c][0], caps[c][1], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr,
-            (const int*)ctx->tile_cam_ptr, (const int*)ctx->tile_cams, (const uint32_t*)ctx->t_key,
-            (const Real2*)ctx->t_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k),
-            (const V4<float>*)lmlo_at(ctx, k), L, (double*)ctx->tile_part);
-        if (c) ctx->launches++;
-      }
-      t0 = ctx->tile_class_end[c];
-    }
+    k_objective<LOSS, Real, Real2, HAS_LO><<<blocks, threads, 0, st>>>(
+        ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+        (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k),
+        (const V4<float>*)lmlo_at(ctx, k), L, (Real*)ctx->chunk_f);
   }
   return cudaGetLastError();
 }
@@ -343,6 +307,36 @@ cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
   ctx->launches++;
   if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which, k);
   return launch_by_loss<double, double2, false>(ctx, st, which, k);
+}
+
+// landmark pass: small tiles, then the one-landmark tiles of long tracks
+template <class Real, class Real2, bool HAS_LO>
+cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  const IterParams P = iter_params(ctx);
+  const int caps[2] = {TILE_OBS, BIG_TILE_OBS};
+  auto kern = k_lpass<Real, Real2, HAS_LO>;
+  int t0 = 0;
+  for (int c = 0; c < 2; ++c) {
+    const int nt = ctx->tile_class_end[c] - t0;
+    if (nt > 0) {
+      const size_t smem = lpass_smem_bytes<Real>(caps[c]);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<nt, LPASS_THREADS, smem, st>>>(
+          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cpos,
+          (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
+          (const Real2*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
+          (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
+          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
+      ctx->launches++;
+    }
+    t0 = ctx->tile_class_end[c];
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lpass(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  if (is_mixed(ctx)) return launch_lpass_t<float, float2, true>(ctx, st, k);
+  return launch_lpass_t<double, double2, false>(ctx, st, k);
 }
 
 cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
@@ -366,23 +360,25 @@ cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
     k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
-                                             (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs,
+                                             (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
                                              (V4<float>*)pack_at(ctx, k + 1));
   else
     k_camsolve<double><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
                                               (const double*)ctx->chunk_part, (double*)ctx->cam_x,
                                               (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
                                               (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,
-                                              (uint8_t*)ctx->cam_rs, (V4<double>*)pack_at(ctx, k + 1));
+                                              (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
+                                              (V4<double>*)pack_at(ctx, k + 1));
   return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
-  k_finalize<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->M, (const uint8_t*)ctx->cam_rs,
-                                 ctx->s_norm * ctx->s_norm, P, (double*)ctx->d_trace, (int*)ctx->d_rs,
-                                 (int*)ctx->d_flag);
+  k_finalize<<<FIN_BLOCKS, FIN_THREADS, 0, st>>>(ctx->M, (const double*)ctx->cam_Fsum, (const uint8_t*)ctx->cam_rs,
+                                                  ctx->n_tiles, (const int*)ctx->tile_rs, ctx->s_norm * ctx->s_norm, P,
+                                                  (double*)ctx->fin_blk, (unsigned int*)ctx->fin_ticket,
+                                                  (double*)ctx->d_trace, (int*)ctx->d_rs, (int*)ctx->d_flag);
   return cudaGetLastError();
 }
 
@@ -397,8 +393,12 @@ daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st, bool prepare) {
   }
   CK(launch_pass(ctx, st, 6, ctx->k));
   ctx->launches++;
-  k_sum_tiles<<<1, 1024, 0, st>>>(ctx->n_tiles, (const double*)ctx->tile_part, ctx->s_norm * ctx->s_norm,
-                                  (double*)ctx->d_obj);
+  if (is_mixed(ctx))
+    k_sum<float><<<1, 1024, 0, st>>>(ctx->n_chunks, (const float*)ctx->chunk_f, ctx->s_norm * ctx->s_norm,
+                                     (double*)ctx->d_obj);
+  else
+    k_sum<double><<<1, 1024, 0, st>>>(ctx->n_chunks, (const double*)ctx->chunk_f, ctx->s_norm * ctx->s_norm,
+                                      (double*)ctx->d_obj);
   CK(cudaGetLastError());
   return DABA_OK;
 }
@@ -474,7 +474,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   cudaGetDevice(&ctx->dev);
   const size_t R = real_sz(ctx);
   ctx->max_chunks = (int)(M + nnz / CHUNK_OBS + 1);
-  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS + nnz / TILE_CAMS) + nnz / TILE_OBS + 8);
+  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS) + nnz / TILE_OBS + 8);
 #define AL(field, bytes)                                   \
   if ((st = dalloc(ctx, &ctx->field, (bytes))) != DABA_OK) { \
     daba_ctx* c_ = ctx;                                    \
@@ -483,18 +483,16 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   }
   AL(c_lm, nnz * 4);
   AL(c_u, nnz * 2 * R);
-  AL(c_orig, nnz * 4);
-  AL(cam_ptr, (size_t)(M + 1) * 4);
   AL(chunk_cam, (size_t)ctx->max_chunks * 4);
   AL(chunk_beg, (size_t)(ctx->max_chunks + 1) * 4);
   AL(cam_chunk_ptr, (size_t)(M + 1) * 4);
   AL(lm_ptr, (size_t)(N + 1) * 4);
   AL(tile_lm, (size_t)(ctx->max_tiles + 1) * 4);
-  AL(t_key, nnz * 4);
-  AL(t_u, nnz * 2 * R);
-  AL(tile_cam_ptr, (size_t)(ctx->max_tiles + 1) * 4);
-  AL(tile_cams, nnz * 4);
-  AL(l_orig, nnz * 4);
+  AL(t_cpos, nnz * 4);
+  AL(t_slot, nnz * 2);
+  AL(rec_a, nnz * 4 * R);
+  AL(rec_b, nnz * 4 * R);
+  AL(rec_c, nnz * 2 * R);
   AL(cam_x, (size_t)M * CSTRIDE * 8);
   AL(cam_dx, (size_t)M * CSTRIDE * 8);
   AL(cam_Rbar, (size_t)M * 9 * 8);
@@ -512,8 +510,12 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(lm_rs, (size_t)N);
   AL(lm_Fd, (size_t)N * 8);
   AL(lm_Fbd, (size_t)N * 8);
-  AL(chunk_part, (size_t)ctx->max_chunks * CP_STRIDE * 8);
-  AL(tile_part, (size_t)ctx->max_tiles * TP_STRIDE * 8);
+  AL(chunk_part, (size_t)ctx->max_chunks * CP_STRIDE * R);
+  AL(chunk_f, (size_t)ctx->max_chunks * R);
+  AL(tile_rs, (size_t)ctx->max_tiles * 4);
+  AL(cam_Fsum, (size_t)M * 8);
+  AL(fin_blk, (size_t)FIN_BLOCKS * 2 * 8);
+  AL(fin_ticket, 16);
   AL(d_gam, (GSEG + 1) * 8);
   AL(d_it, 16);
   AL(d_first, 16);
@@ -536,6 +538,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     return DABA_ERR_CUDA;
   }
   cudaMemset(ctx->d_flag, 0, 16);
+  cudaMemset(ctx->fin_ticket, 0, 16);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -576,12 +579,9 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   // seen by the same cameras become neighbours), landmarks with long tracks last
   std::vector<int32_t> min_cam(N, M);
   for (int64_t o = 0; o < n; ++o) min_cam[li[o]] = std::min(min_cam[li[o]], ci[o]);
-  // tile class of a landmark: 0 = at most TILE_CAMS observations (camera packs staged in
-  // shared memory), 1 = at most TILE_OBS, 2 = longer (a tile of its own)
-  auto lclass = [&](int j) {
-    const int dg = lm_ptr[j + 1] - lm_ptr[j];
-    return dg <= TILE_CAMS ? 0 : (dg <= TILE_OBS ? 1 : 2);
-  };
+  // tile class of a landmark: 0 = at most TILE_OBS observations (small tiles),
+  // 1 = longer (a tile of its own)
+  auto lclass = [&](int j) { return lm_ptr[j + 1] - lm_ptr[j] <= TILE_OBS ? 0 : 1; };
   std::vector<int32_t> lperm(N), linv(N);
   for (int j = 0; j < N; ++j) lperm[j] = j;
   std::stable_sort(lperm.begin(), lperm.end(), [&](int32_t a, int32_t b) {
@@ -593,6 +593,19 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   std::vector<int32_t> lii(n), li_order, lmi_ptr;
   for (int64_t o = 0; o < n; ++o) lii[o] = linv[li[o]];
   counting_sort(lii, N, li_order, lmi_ptr);
+  // device camera order: by camera, then internal landmark id, then input index (a stable
+  // counting sort by camera of the landmark-sorted order), so that the observations of one
+  // camera inside a landmark tile are contiguous
+  std::vector<int32_t> ci_order(n);
+  {
+    std::vector<int32_t> pos(cam_ptr.begin(), cam_ptr.end() - 1);
+    for (int64_t q = 0; q < n; ++q) {
+      const int32_t o = li_order[q];
+      ci_order[pos[ci[o]]++] = o;
+    }
+  }
+  std::vector<int32_t> cpos_of(n);
+  for (int64_t q = 0; q < n; ++q) cpos_of[ci_order[q]] = (int32_t)q;
   // camera chunks
   std::vector<int32_t> chunk_cam, chunk_beg, cam_chunk_ptr(M + 1, 0);
   for (int i = 0; i < M; ++i) {
@@ -604,33 +617,19 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   }
   cam_chunk_ptr[M] = (int32_t)chunk_cam.size();
   chunk_beg.push_back((int32_t)n);
-  // landmark tiles over internal ids, class by class: consecutive landmarks with at most
-  // TILE_OBS observations, TILE_LMS landmarks and (class 0) TILE_CAMS distinct cameras
+  // landmark tiles over internal ids: consecutive landmarks with at most TILE_OBS
+  // observations and TILE_LMS landmarks, then one tile per long-track landmark
   std::vector<int32_t> tile_lm;
   tile_lm.push_back(0);
-  int class_end[3] = {0, 0, 0};
+  int class_end[2] = {0, 0};
   {
-    std::vector<int32_t> stamp(M, -1);
     int j = 0;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 2; ++c) {
       while (j < N && lclass(lperm[j]) == c) {
-        const int tid = (int)tile_lm.size() - 1;
-        int j2 = j, cnt = 0, ncam = 0;
+        int j2 = j, cnt = 0;
         while (j2 < N && lclass(lperm[j2]) == c) {
           const int dg = lmi_ptr[j2 + 1] - lmi_ptr[j2];
-          if (j2 > j && (c == 2 || j2 - j >= TILE_LMS || cnt + dg > TILE_OBS)) break;
-          int fresh = 0;
-          if (c == 0) {
-            for (int o = lmi_ptr[j2]; o < lmi_ptr[j2 + 1]; ++o) {
-              const int cam = ci[li_order[o]];
-              if (stamp[cam] != tid) {
-                stamp[cam] = tid;
-                ++fresh;
-              }
-            }
-            if (j2 > j && ncam + fresh > TILE_CAMS) break;   // the next tile gets a new stamp
-          }
-          ncam += fresh;
+          if (j2 > j && (c == 1 || j2 - j >= TILE_LMS || cnt + dg > TILE_OBS)) break;
           cnt += dg;
           ++j2;
         }
@@ -643,32 +642,22 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   const int n_tiles = (int)tile_lm.size() - 1;
   if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
     return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
-  // inside each tile: observations in camera order (ties by landmark-sorted position), the
-  // tile's distinct cameras and per-observation keys (local camera << 16 | slot)
-  std::vector<int32_t> t_order(n), c_lm(n), tile_cam_ptr(n_tiles + 1, 0), tile_cams;
-  std::vector<uint32_t> t_key(n);
-  tile_cams.reserve(n / 4 + 16);
+  // inside each tile: observations by camera-sorted position (records of one camera are
+  // contiguous), with their landmark-sorted slot relative to the tile start
+  std::vector<int32_t> t_cpos(n), c_lm(n);
+  std::vector<uint16_t> t_slot(n);
+  std::vector<int32_t> t_order(n);
   for (int t = 0; t < n_tiles; ++t) {
     const int ob = lmi_ptr[tile_lm[t]], oe = lmi_ptr[tile_lm[t + 1]];
     for (int o = ob; o < oe; ++o) t_order[o] = o;
-    std::sort(t_order.begin() + ob, t_order.begin() + oe, [&](int32_t a, int32_t b) {
-      const int32_t ca = ci[li_order[a]], cb = ci[li_order[b]];
-      return ca != cb ? ca < cb : a < b;
-    });
-    tile_cam_ptr[t] = (int32_t)tile_cams.size();
-    int last = -1;
+    std::sort(t_order.begin() + ob, t_order.begin() + oe,
+              [&](int32_t a, int32_t b) { return cpos_of[li_order[a]] < cpos_of[li_order[b]]; });
     for (int o = ob; o < oe; ++o) {
-      const int cam = ci[li_order[t_order[o]]];
-      if (cam != last) {
-        tile_cams.push_back(cam);
-        last = cam;
-      }
-      const uint32_t lc = (uint32_t)(tile_cams.size() - 1 - tile_cam_ptr[t]);
-      t_key[o] = (lc << 16) | (uint32_t)(t_order[o] - ob);
+      t_cpos[o] = cpos_of[li_order[t_order[o]]];
+      t_slot[o] = (uint16_t)(t_order[o] - ob);
     }
   }
-  tile_cam_ptr[n_tiles] = (int32_t)tile_cams.size();
-  for (int64_t o = 0; o < n; ++o) c_lm[o] = lii[c_order[o]];
+  for (int64_t q = 0; q < n; ++q) c_lm[q] = lii[ci_order[q]];
   // keep the current iterate (if any) across the renumbering; displacements and the
   // restart metrics are reset (x^(k-1) = x^k, S = 0)
   std::vector<double> keep_l;
@@ -679,21 +668,17 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   }
   // upload
   CK(cudaMemcpyAsync(ctx->c_lm, c_lm.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->c_orig, c_order.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_ptr, cam_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->chunk_cam, chunk_cam.data(), chunk_cam.size() * 4 + 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->chunk_beg, chunk_beg.data(), chunk_beg.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->lm_ptr, lmi_ptr.data(), (N + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->t_key, t_key.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->tile_cam_ptr, tile_cam_ptr.data(), tile_cam_ptr.size() * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->tile_cams, tile_cams.data(), tile_cams.size() * 4 + 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->l_orig, l_order.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_cpos, t_cpos.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
   ctx->n_tiles = n_tiles;
-  for (int c = 0; c < 3; ++c) ctx->tile_class_end[c] = class_end[c];
+  for (int c = 0; c < 2; ++c) ctx->tile_class_end[c] = class_end[c];
   ctx->h_cam_idx.swap(ci);
   ctx->h_lm_idx.swap(li);
   ctx->h_uv.swap(uvh);
@@ -703,6 +688,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_lm_ptr.swap(lm_ptr);
   ctx->h_t_order.swap(t_order);
   ctx->h_li_order.swap(li_order);
+  ctx->h_ci_order.swap(ci_order);
   ctx->h_lperm.swap(lperm);
   ctx->h_linv.swap(linv);
   ctx->u_scale_uploaded = -1.0;
@@ -836,16 +822,17 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     for (int j = 0; j < seg; ++j) {
       const int64_t kk = ctx->k + j;
-      // fork: the landmark pass on a low-priority stream, the camera pass and the camera
-      // solves (the latency-bound critical path) on a high-priority one; join on `st`
+      // the camera pass on a high-priority stream; then the landmark pass (low priority)
+      // and the camera solves (the latency-bound critical path, high priority) concurrently
       CK(cudaEventRecord(ctx->ev_fork, st));
       CK(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
-      CK(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_fork, 0));
       if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 0), ctx->s_hi));
       CK(launch_pass(ctx, ctx->s_hi, 1, kk));
       if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 1), ctx->s_hi));
+      CK(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
+      CK(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_hi, 0));
       if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 3), ctx->s_lo));
-      CK(launch_pass(ctx, ctx->s_lo, 2, kk));
+      CK(launch_lpass(ctx, ctx->s_lo, kk));
       if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 4), ctx->s_lo));
       CK(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
       CK(launch_camsolve(ctx, ctx->s_hi, kk));
@@ -999,17 +986,11 @@ daba_status daba_get_sort(daba_ctx* ctx, int32_t* cam_order, int32_t* cam_ptr, i
   if (!ctx) return DABA_ERR_ARG;
   if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations not set");
   cudaStream_t st = (cudaStream_t)stream;
-  auto geti = [&](int32_t* dst, const void* src, int64_t n) -> daba_status {
-    std::vector<int32_t> h(n);
-    CK(cudaMemcpyAsync(h.data(), src, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    return deliver(ctx, dst, h.data(), (size_t)n * 4, st);
-  };
   daba_status s;
-  if (cam_order && (s = geti(cam_order, ctx->c_orig, ctx->nnz)) != DABA_OK) return s;
-  if (cam_ptr && (s = geti(cam_ptr, ctx->cam_ptr, ctx->M + 1)) != DABA_OK) return s;
-  if (lm_order && (s = geti(lm_order, ctx->l_orig, ctx->nnz)) != DABA_OK) return s;
-  // the device CSR runs over the internal landmark numbering; the external one is kept on the host
+  // the stable sorts built by daba_set_observations (the device schedules are derived from them)
+  if (cam_order && (s = deliver(ctx, cam_order, ctx->h_c_order.data(), (size_t)ctx->nnz * 4, st)) != DABA_OK) return s;
+  if (cam_ptr && (s = deliver(ctx, cam_ptr, ctx->h_cam_ptr.data(), (size_t)(ctx->M + 1) * 4, st)) != DABA_OK) return s;
+  if (lm_order && (s = deliver(ctx, lm_order, ctx->h_l_order.data(), (size_t)ctx->nnz * 4, st)) != DABA_OK) return s;
   if (lm_ptr && (s = deliver(ctx, lm_ptr, ctx->h_lm_ptr.data(), (size_t)(ctx->N + 1) * 4, st)) != DABA_OK) return s;
   return DABA_OK;
 }

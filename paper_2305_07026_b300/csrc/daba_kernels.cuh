@@ -2,18 +2,18 @@
 // with one block per camera and one block per landmark.
 //
 // Per iteration k:
-//   1. cpass     (warp/chunk) : camera-sorted observations; per camera the centred
-//                               majorizer statistics at xbar^k and x^k plus the F_ij and
-//                               surrogate-gap sums, one FP64 partial per chunk.
-//   2. lpass     (CTA/tile)   : landmark-sorted observations; per landmark statistics,
-//                               restart metrics, accelerated solve, restart test and MM
-//                               re-solve (closed form); writes the other landmark buffer.
-//   3. camsolve  (M threads)  : FP64 camera block solves, restart test, MM re-solve, and
-//                               the extrapolated rotation and pack of iteration k+1 (written
-//                               to the other pack buffer).
-//   4. finalize  (1 CTA)      : F(x^k) trace entry and restart count.
-// The landmark state and the camera pack are double-buffered, so lpass (on a second
-// stream) runs concurrently with cpass -> camsolve; finalize joins both.
+//   1. cpass     (warp/chunk) : camera-sorted observations; evaluates each observation at
+//                               x^k, xbar^k and x^(k-1) once, reduces the camera's centred
+//                               majorizer statistics (one partial per chunk) and stores the
+//                               observation's landmark-side terms as a record in camera order.
+//   2. lpass     (CTA/tile)   : per landmark, sums its records and runs the restart metrics,
+//                               accelerated solve, restart test and MM re-solve (closed form);
+//                               writes the other landmark buffer.
+//   3. camsolve  (M threads)  : FP64 camera block solves, restart test, MM re-solve, and the
+//                               extrapolated rotation and pack of iteration k+1.
+//   4. finalize  (grid)       : F(x^k) trace entry and restart count (deterministic order).
+// lpass and camsolve both only need cpass, so they run concurrently (camsolve, the
+// latency-bound FP64 path, on the higher-priority stream).
 // cam_prepare builds the pack of the first iteration of a run.
 //
 // Centred statistics. For a conditioning iterate z (xbar^k or x^k) and a camera c let
@@ -43,11 +43,10 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
 constexpr int CPASS_WARPS = 4;
-constexpr int LPASS_THREADS = 128;
-constexpr int TILE_OBS = 256;     // observations of a small landmark tile
-constexpr int TILE_LMS = 64;      // landmarks of a small landmark tile
-constexpr int TILE_CAMS = 64;     // distinct cameras of a small landmark tile (packs staged in smem)
-constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own
+constexpr int LPASS_THREADS = 256;
+constexpr int TILE_OBS = 1024;    // observations of a small landmark tile
+constexpr int TILE_LMS = 256;     // landmarks of a small landmark tile
+constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own (max track)
 constexpr int MAX_TRACK = BIG_TILE_OBS;
 
 struct IterParams {
@@ -198,11 +197,16 @@ struct CpassStage {
   Real2 u;
 };
 
+// Landmark-side record of one observation, stored at its camera-sorted position:
+//   rec_a = (wb lamb^2, -wb lamb (Rbar ebar) / 2)   terms of sum_i Q_ij(l | xbar^k)
+//   rec_b = (w lam^2, -w lam (R e) / 2)             terms of sum_i Q_ij(l | x^k)
+//   rec_c = (F_ij(x^k), surrogate gap)
 template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
             const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
-            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part) {
+            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
+            V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b, Real2* __restrict__ rec_c) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
   __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
   const int wib = threadIdx.x >> 5;
@@ -258,6 +262,22 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
       accumulate_cam<Real>(acc, ev, uu.x, uu.y);
+      const Real wlb = ev.wb * ev.lamb, wl = ev.w * ev.lam;
+      V4<Real> ra, rb;
+      ra.x = wlb * ev.lamb;
+      ra.y = Real(-0.5) * wlb * ev.Reb0;
+      ra.z = Real(-0.5) * wlb * ev.Reb1;
+      ra.w = Real(-0.5) * wlb * ev.Reb2;
+      rb.x = wl * ev.lam;
+      rb.y = Real(-0.5) * wl * ev.Re0;
+      rb.z = Real(-0.5) * wl * ev.Re1;
+      rb.w = Real(-0.5) * wl * ev.Re2;
+      Real2 rc;
+      rc.x = Real(0.5) * ev.rho;
+      rc.y = ev.gap;
+      rec_a[o] = ra;
+      rec_b[o] = rb;
+      rec_c[o] = rc;
     }
   }
   cp_async_wait<0>();
@@ -278,21 +298,17 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 }
 
 // ---------------------------------------------------------------------------
-// 2. landmark-sorted pass: one CTA per tile of consecutive landmarks
+// 2. landmark pass: one CTA per tile of consecutive landmarks (internal numbering)
 // ---------------------------------------------------------------------------
-// Reads the landmark state of iteration k (lmrec, lm_lo) and writes that of k+1 to the
-// other buffer, so that it can run concurrently with the camera-sorted pass.
-// Tile data: tile_lm[t] .. tile_lm[t+1] landmarks; their observations occupy the
-// landmark-sorted positions lm_ptr[first] .. lm_ptr[last]; the tile's distinct cameras are
-// tile_cams[tile_cam_ptr[t] .. tile_cam_ptr[t+1]]. Inside the tile the observations are
-// processed in camera order: t_key = (local camera << 16) | slot, where slot is the
-// observation's landmark-sorted position relative to the tile start, and t_u its pixel.
-// Shared memory: nc_cap camera packs (small tiles), nl_cap x 3 V4 staged landmarks,
-// no_cap x 10 contributions, slot map.
+// Tile data: landmarks tile_lm[t] .. tile_lm[t+1]; their observations occupy the
+// landmark-sorted slots lm_ptr[first] .. lm_ptr[last]. Inside the tile they are visited in
+// camera-sorted order, t_cpos being the observation's camera-sorted position (where cpass
+// stored its record) and t_slot its landmark-sorted slot relative to the tile start; the
+// records of one camera are contiguous there. Reads the landmark state of iteration k and
+// writes that of k+1 to the other buffer.
 template <class Real>
-__host__ __device__ inline size_t lpass_smem_bytes(int no_cap, int nl_cap, int nc_cap) {
-  return (size_t)nc_cap * P4N * sizeof(V4<Real>) + (size_t)nl_cap * 3 * sizeof(V4<Real>) +
-         (size_t)no_cap * 10 * sizeof(Real) + (size_t)no_cap * 2 + 16;
+__host__ __device__ inline size_t lpass_smem_bytes(int no_cap) {
+  return (size_t)no_cap * 10 * sizeof(Real) + 16;
 }
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
@@ -306,14 +322,13 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   hi = h2;
 }
 
-template <int LOSS, class Real, class Real2, bool HAS_LO, bool STAGE>
+template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
-    k_lpass(int tile0, int no_cap, int nl_cap, int nc_cap, const int* __restrict__ tile_lm,
-            const int* __restrict__ lm_ptr, const int* __restrict__ tile_cam_ptr, const int* __restrict__ tile_cams,
-            const uint32_t* __restrict__ t_key, const Real2* __restrict__ t_u,
-            const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo,
-            V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out, LossC<Real> L, IterParams P,
-            double* __restrict__ tile_part, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
+    k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
+            const int* __restrict__ t_cpos, const uint16_t* __restrict__ t_slot, const V4<Real>* __restrict__ rec_a,
+            const V4<Real>* __restrict__ rec_b, const Real2* __restrict__ rec_c, const V4<Real>* __restrict__ lmrec,
+            const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out,
+            IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
             double* __restrict__ lm_Fbdiag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tile = tile0 + blockIdx.x;
@@ -321,63 +336,28 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  const int cb = tile_cam_ptr[tile], nc = tile_cam_ptr[tile + 1] - cb;
-  V4<Real>* spk = reinterpret_cast<V4<Real>*>(smem_raw);                 // nc_cap x P4N camera packs
-  V4<Real>* sl = spk + (size_t)nc_cap * P4N;                              // nl_cap x 3
-  Real* sc = reinterpret_cast<Real*>(sl + (size_t)nl_cap * 3);           // 10 x no_cap (SoA)
-  uint16_t* smap = reinterpret_cast<uint16_t*>(sc + (size_t)no_cap * 10);   // slot -> local landmark
+  Real* sc = reinterpret_cast<Real*>(smem_raw);   // 10 x no_cap (SoA), indexed by slot
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
 
-  if (STAGE)
-    for (int q = threadIdx.x; q < nc * P4N; q += blockDim.x) spk[q] = pack[(size_t)tile_cams[cb + q / P4N] * P4N + q % P4N];
-  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
-    const size_t g = (size_t)(lb + jl);
-    sl[jl * 3 + 0] = lmrec[2 * g];
-    sl[jl * 3 + 1] = lmrec[2 * g + 1];
-    V4<Real> lo;
-    if (HAS_LO) {
-      const V4<float> f = lm_lo[g];
-      lo.x = Real(f.x);
-      lo.y = Real(f.y);
-      lo.z = Real(f.z);
-    } else {
-      lo.x = lo.y = lo.z = Real(0);
-    }
-    lo.w = Real(0);
-    sl[jl * 3 + 2] = lo;
-    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
-    for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
-  }
-  __syncthreads();
-
   for (int o = threadIdx.x; o < no; o += blockDim.x) {
-    const uint32_t key = t_key[ob + o];
-    const Real2 uu = t_u[ob + o];
-    const int lc = (int)(key >> 16);
-    const int slot = (int)(key & 0xffffu);
-    const int jl = smap[slot];
-    const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
-    const V4<Real>* pk = STAGE ? spk + (size_t)lc * P4N : pack + (size_t)tile_cams[cb + lc] * P4N;
-    ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, A.x, A.y, A.z, C.x, C.y, C.z, A.w, B.x, B.y, uu.x, uu.y, gamma, L, ev);
-    // landmark statistics: sum w lambda^2 and sum w lambda r0' with r0' = -R e / 2
-    const Real wlb = ev.wb * ev.lamb;
-    const Real wl = ev.w * ev.lam;
-    sc[0 * no_cap + slot] = wlb * ev.lamb;
-    sc[1 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb0;
-    sc[2 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb1;
-    sc[3 * no_cap + slot] = Real(-0.5) * wlb * ev.Reb2;
-    sc[4 * no_cap + slot] = wl * ev.lam;
-    sc[5 * no_cap + slot] = Real(-0.5) * wl * ev.Re0;
-    sc[6 * no_cap + slot] = Real(-0.5) * wl * ev.Re1;
-    sc[7 * no_cap + slot] = Real(-0.5) * wl * ev.Re2;
-    sc[8 * no_cap + slot] = Real(0.5) * ev.rho;
-    sc[9 * no_cap + slot] = ev.gap;
+    const int p = t_cpos[ob + o];
+    const int slot = t_slot[ob + o];
+    const V4<Real> ra = rec_a[p], rb = rec_b[p];
+    const Real2 rc = rec_c[p];
+    sc[0 * no_cap + slot] = ra.x;
+    sc[1 * no_cap + slot] = ra.y;
+    sc[2 * no_cap + slot] = ra.z;
+    sc[3 * no_cap + slot] = ra.w;
+    sc[4 * no_cap + slot] = rb.x;
+    sc[5 * no_cap + slot] = rb.y;
+    sc[6 * no_cap + slot] = rb.z;
+    sc[7 * no_cap + slot] = rb.w;
+    sc[8 * no_cap + slot] = rc.x;
+    sc[9 * no_cap + slot] = rc.y;
   }
   __syncthreads();
 
-  Real fsum = Real(0);
   int nrs = 0;
   const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
   for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
@@ -388,7 +368,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     for (int s = s0; s < s1; ++s)
 #pragma unroll
       for (int k = 0; k < 10; ++k) st[k] += sc[k * no_cap + s];
-    const V4<Real> A = sl[jl * 3 + 0], B = sl[jl * 3 + 1], C = sl[jl * 3 + 2];
+    const size_t g = (size_t)(lb + jl);
+    const V4<Real> A = lmrec[2 * g], B = lmrec[2 * g + 1];
     const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
     // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
     //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
@@ -412,22 +393,22 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     }
     nrs += (rs && P.accelerated) ? 1 : 0;
     V4<Real> nA, nB;
-    const size_t g = (size_t)(lb + jl);
     if (HAS_LO) {
+      const V4<float> lo = lm_lo[g];
       float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
-      float o0 = float(C.x), o1 = float(C.y), o2 = float(C.z);
+      float o0 = lo.x, o1 = lo.y, o2 = lo.z;
       df_add(h0, o0, float(step0));
       df_add(h1, o1, float(step1));
       df_add(h2, o2, float(step2));
       nA.x = Real(h0);
       nA.y = Real(h1);
       nA.z = Real(h2);
-      V4<float> lo;
-      lo.x = o0;
-      lo.y = o1;
-      lo.z = o2;
-      lo.w = 0.f;
-      lm_lo_out[g] = lo;
+      V4<float> nlo;
+      nlo.x = o0;
+      nlo.y = o1;
+      nlo.z = o2;
+      nlo.w = 0.f;
+      lm_lo_out[g] = nlo;
     } else {
       nA.x = A.x + step0;
       nA.y = A.y + step1;
@@ -448,31 +429,17 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     lmrec_out[2 * g] = nA;
     lmrec_out[2 * g + 1] = nB;
     lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
-    fsum += st[8];
   }
-  // tile sums: F(x^k) part (per warp in the pass precision, across warps in FP64) and the
-  // restart count, in a fixed order
-  __shared__ double red[LPASS_THREADS / 32];
+  // restart count of the tile
   __shared__ int redi[LPASS_THREADS / 32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
-    nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = double(fsum);
-    redi[threadIdx.x >> 5] = nrs;
-  }
+  for (int off = 16; off > 0; off >>= 1) nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
+  if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = nrs;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double f = 0.0;
     int n = 0;
-    for (int w = 0; w < LPASS_THREADS / 32; ++w) {
-      f += red[w];
-      n += redi[w];
-    }
-    tile_part[(size_t)tile * TP_STRIDE + TP_F] = f;
-    tile_part[(size_t)tile * TP_STRIDE + TP_RS] = double(n);
+    for (int w = 0; w < LPASS_THREADS / 32; ++w) n += redi[w];
+    tile_rs[tile] = n;
   }
 }
 
@@ -647,7 +614,7 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const R
                            double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
                            IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
                            double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
-                           V4<Real>* __restrict__ pack_next) {
+                           double* __restrict__ cam_Fsum, V4<Real>* __restrict__ pack_next) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int it = *P.it;
@@ -707,6 +674,7 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const R
   }
   const double E = first ? 0.5 * sF : cam_E[i];
   const double F = E + dE;
+  cam_Fsum[i] = sF;   // sum of F_ij(x^k) over the camera's observations (objective trace)
   cam_F[i] = F;
   cam_Fb[i] = F + thr;
   cam_E[i] = F + dEn;
@@ -742,36 +710,64 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const R
 }
 
 // ---------------------------------------------------------------------------
-// 4. reduction of one iteration: F(x^k) (FP64, fixed order) and restart count
+// 4. reduction of one iteration: F(x^k) = sum over cameras of their F_ij sums (FP64) and
+//    the restart count. Every block reduces a fixed slice; the last block to finish (a
+//    ticket counter, no waiting) combines the block results in block order.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, int M,
-                           const uint8_t* __restrict__ cam_rs, double s2, IterParams P, double* __restrict__ trace,
-                           int* __restrict__ restarts, int* __restrict__ flag) {
-  __shared__ double red[32];
-  __shared__ long long redi[32];
-  double f = 0.0;
-  long long n = 0;
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-    f += tile_part[(size_t)t * TP_STRIDE + TP_F];
-    n += (long long)tile_part[(size_t)t * TP_STRIDE + TP_RS];
-  }
-  for (int i = threadIdx.x; i < M; i += blockDim.x) n += cam_rs[i];
+constexpr int FIN_BLOCKS = 64;
+constexpr int FIN_THREADS = 256;
+
+__device__ __forceinline__ void block_sum2(double& f, long long& n, double* sf, long long* sn) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     f += __shfl_xor_sync(0xffffffffu, f, off);
     n += __shfl_xor_sync(0xffffffffu, n, off);
   }
   if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = f;
-    redi[threadIdx.x >> 5] = n;
+    sf[threadIdx.x >> 5] = f;
+    sn[threadIdx.x >> 5] = n;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ft = 0.0;
-    long long nt = 0;
+    f = 0.0;
+    n = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      ft += red[w];
-      nt += redi[w];
+      f += sf[w];
+      n += sn[w];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(FIN_THREADS)
+    k_finalize(int M, const double* __restrict__ cam_Fsum, const uint8_t* __restrict__ cam_rs, int n_tiles,
+               const int* __restrict__ tile_rs, double s2, IterParams P, double* __restrict__ blk,
+               unsigned int* __restrict__ ticket, double* __restrict__ trace, int* __restrict__ restarts,
+               int* __restrict__ flag) {
+  __shared__ double sf[FIN_THREADS / 32];
+  __shared__ long long sn[FIN_THREADS / 32];
+  __shared__ bool last;
+  double f = 0.0;
+  long long n = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+    f += cam_Fsum[i];
+    n += cam_rs[i];
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) n += tile_rs[t];
+  block_sum2(f, n, sf, sn);
+  if (threadIdx.x == 0) {
+    blk[2 * blockIdx.x] = f;
+    blk[2 * blockIdx.x + 1] = (double)n;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double ft = 0.0, nt = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      ft += ((volatile double*)blk)[2 * b];
+      nt += ((volatile double*)blk)[2 * b + 1];
     }
     const int k = *P.it;
     trace[k] = ft * s2;
@@ -779,71 +775,54 @@ __global__ void k_finalize(int n_tiles, const double* __restrict__ tile_part, in
     if (!isfinite(ft)) *flag = 1;
     *P.it = k + 1;
     *P.first = 0;
+    *ticket = 0u;
   }
 }
 
 // ---------------------------------------------------------------------------
-// objective F(x^k) only (Eq. Fobj): per tile sums over the landmark tiles
+// objective F(x^k) only (Eq. Fobj): camera-sorted chunks, landmark position from its
+// high and low parts; one partial per chunk
 // ---------------------------------------------------------------------------
 template <int LOSS, class Real, class Real2, bool HAS_LO>
-__global__ void __launch_bounds__(LPASS_THREADS)
-    k_objective(int tile0, int no_cap, int nl_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-                const int* __restrict__ tile_cam_ptr, const int* __restrict__ tile_cams,
-                const uint32_t* __restrict__ t_key, const Real2* __restrict__ t_u,
-                const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec,
-                const V4<float>* __restrict__ lm_lo, LossC<Real> L, double* __restrict__ tile_part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tile = tile0 + blockIdx.x;
-  const int lb = tile_lm[tile], le = tile_lm[tile + 1];
-  const int nl = le - lb;
-  const int ob = lm_ptr[lb], oe = lm_ptr[le];
-  const int no = oe - ob;
-  V4<Real>* sl = reinterpret_cast<V4<Real>*>(smem_raw);   // nl_cap x 2: l hi, l lo
-  uint16_t* smap = reinterpret_cast<uint16_t*>(sl + (size_t)nl_cap * 2);
-  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
-    const size_t g = (size_t)(lb + jl);
-    sl[jl * 2] = lmrec[2 * g];
-    V4<Real> lo;
+__global__ void __launch_bounds__(CPASS_WARPS * 32)
+    k_objective(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
+                const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
+                const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, LossC<Real> L,
+                Real* __restrict__ chunk_f) {
+  __shared__ V4<Real> spk[CPASS_WARPS][P4N];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * CPASS_WARPS + wib;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_chunks) return;
+  const int cam = chunk_cam[warp];
+  const int b = chunk_beg[warp], e = chunk_beg[warp + 1];
+  if (lane < P4N) spk[wib][lane] = pack[(size_t)cam * P4N + lane];
+  __syncwarp();
+  Real f = Real(0);
+  for (int o = b + lane; o < e; o += 32) {
+    const int j = c_lm[o];
+    const Real2 uu = c_u[o];
+    const V4<Real> A = lmrec[2 * (size_t)j];
+    Real o0 = Real(0), o1 = Real(0), o2 = Real(0);
     if (HAS_LO) {
-      const V4<float> f = lm_lo[g];
-      lo.x = Real(f.x);
-      lo.y = Real(f.y);
-      lo.z = Real(f.z);
-    } else {
-      lo.x = lo.y = lo.z = Real(0);
+      const V4<float> lo = lm_lo[j];
+      o0 = Real(lo.x);
+      o1 = Real(lo.y);
+      o2 = Real(lo.z);
     }
-    lo.w = Real(0);
-    sl[jl * 2 + 1] = lo;
-    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
-    for (int s = s0; s < s1; ++s) smap[s] = (uint16_t)jl;
+    f += eval_F4<LOSS, Real>(spk[wib], A.x, A.y, A.z, o0, o1, o2, uu.x, uu.y, L);
   }
-  __syncthreads();
-  Real fsum = Real(0);
-  const int cb = tile_cam_ptr[tile];
-  for (int o = threadIdx.x; o < no; o += blockDim.x) {
-    const uint32_t key = t_key[ob + o];
-    const int cam = tile_cams[cb + (int)(key >> 16)];
-    const Real2 uu = t_u[ob + o];
-    const int jl = smap[key & 0xffffu];
-    const V4<Real> A = sl[jl * 2], C = sl[jl * 2 + 1];
-    fsum += eval_F4<LOSS, Real>(pack + (size_t)cam * P4N, A.x, A.y, A.z, C.x, C.y, C.z, uu.x, uu.y, L);
-  }
-  __shared__ double red[LPASS_THREADS / 32];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) fsum += __shfl_xor_sync(0xffffffffu, fsum, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = double(fsum);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double f = 0.0;
-    for (int w = 0; w < LPASS_THREADS / 32; ++w) f += red[w];
-    tile_part[(size_t)tile * TP_STRIDE + TP_F] = f;
-  }
+  for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+  if (lane == 0) chunk_f[warp] = f;
 }
 
-__global__ void k_sum_tiles(int n_tiles, const double* __restrict__ tile_part, double s2, double* __restrict__ out) {
+// FP64 sum of n values (one block, fixed order) times s2 into *out
+template <class Real>
+__global__ void k_sum(int n, const Real* __restrict__ v, double s2, double* __restrict__ out) {
   __shared__ double red[32];
   double f = 0.0;
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) f += tile_part[(size_t)t * TP_STRIDE + TP_F];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) f += double(v[t]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
