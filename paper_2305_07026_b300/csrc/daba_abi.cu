@@ -58,7 +58,7 @@ struct daba_ctx {
   // device buffers
   void *c_lm = nullptr, *c_u = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
-  void *lm_ptr = nullptr, *tile_lm = nullptr, *t_cpos = nullptr, *t_slot = nullptr;
+  void *lm_ptr = nullptr, *tile_lm = nullptr, *c_rpos = nullptr, *t_slot = nullptr;
   void *rec_a = nullptr, *rec_b = nullptr, *rec_c = nullptr;   // landmark-side records in camera order
   void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack2[2] = {nullptr, nullptr};
   void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
@@ -283,7 +283,8 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) 
     k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
         ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
         (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
-        (Real*)ctx->chunk_part, (V4<Real>*)ctx->rec_a, (V4<Real>*)ctx->rec_b, (Real2*)ctx->rec_c);
+        (Real*)ctx->chunk_part, (const int*)ctx->c_rpos, (V4<Real>*)ctx->rec_a, (V4<Real>*)ctx->rec_b,
+        (Real2*)ctx->rec_c);
   } else if (which == 6) {
     k_objective<LOSS, Real, Real2, HAS_LO><<<blocks, threads, 0, st>>>(
         ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
@@ -322,8 +323,7 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
       const size_t smem = lpass_smem_bytes<Real>(caps[c]);
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt, LPASS_THREADS, smem, st>>>(
-          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const int*)ctx->t_cpos,
-          (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
+          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
           (const Real2*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
           (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
           (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
@@ -488,7 +488,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(cam_chunk_ptr, (size_t)(M + 1) * 4);
   AL(lm_ptr, (size_t)(N + 1) * 4);
   AL(tile_lm, (size_t)(ctx->max_tiles + 1) * 4);
-  AL(t_cpos, nnz * 4);
+  AL(c_rpos, nnz * 4);
   AL(t_slot, nnz * 2);
   AL(rec_a, nnz * 4 * R);
   AL(rec_b, nnz * 4 * R);
@@ -642,9 +642,10 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   const int n_tiles = (int)tile_lm.size() - 1;
   if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
     return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
-  // inside each tile: observations by camera-sorted position (records of one camera are
-  // contiguous), with their landmark-sorted slot relative to the tile start
-  std::vector<int32_t> t_cpos(n), c_lm(n);
+  // inside each tile the records are kept in camera-sorted order: c_rpos gives each
+  // camera-sorted observation its record position, t_slot a record's landmark-sorted slot
+  // relative to the tile start
+  std::vector<int32_t> c_rpos(n), c_lm(n);
   std::vector<uint16_t> t_slot(n);
   std::vector<int32_t> t_order(n);
   for (int t = 0; t < n_tiles; ++t) {
@@ -653,7 +654,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
     std::sort(t_order.begin() + ob, t_order.begin() + oe,
               [&](int32_t a, int32_t b) { return cpos_of[li_order[a]] < cpos_of[li_order[b]]; });
     for (int o = ob; o < oe; ++o) {
-      t_cpos[o] = cpos_of[li_order[t_order[o]]];
+      c_rpos[cpos_of[li_order[t_order[o]]]] = o;
       t_slot[o] = (uint16_t)(t_order[o] - ob);
     }
   }
@@ -673,7 +674,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaMemcpyAsync(ctx->cam_chunk_ptr, cam_chunk_ptr.data(), (M + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->lm_ptr, lmi_ptr.data(), (N + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->t_cpos, t_cpos.data(), n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->c_rpos, c_rpos.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();

@@ -43,9 +43,10 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
 constexpr int CPASS_WARPS = 4;
-constexpr int LPASS_THREADS = 256;
-constexpr int TILE_OBS = 1024;    // observations of a small landmark tile
-constexpr int TILE_LMS = 256;     // landmarks of a small landmark tile
+constexpr int LPASS_THREADS = 128;
+constexpr int LPASS_UNROLL = 4;   // observations whose records a thread loads before storing any
+constexpr int TILE_OBS = 512;     // observations of a small landmark tile
+constexpr int TILE_LMS = 128;     // landmarks of a small landmark tile
 constexpr int BIG_TILE_OBS = 2048;   // a landmark with more observations gets a tile of its own (max track)
 constexpr int MAX_TRACK = BIG_TILE_OBS;
 
@@ -197,7 +198,8 @@ struct CpassStage {
   Real2 u;
 };
 
-// Landmark-side record of one observation, stored at its camera-sorted position:
+// Landmark-side record of one observation, stored at c_rpos[o], its position in the landmark
+// tiles' processing order (so that the landmark pass streams the records sequentially):
 //   rec_a = (wb lamb^2, -wb lamb (Rbar ebar) / 2)   terms of sum_i Q_ij(l | xbar^k)
 //   rec_b = (w lam^2, -w lam (R e) / 2)             terms of sum_i Q_ij(l | x^k)
 //   rec_c = (F_ij(x^k), surrogate gap)
@@ -206,7 +208,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
             const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
             const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
-            V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b, Real2* __restrict__ rec_c) {
+            const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b,
+            Real2* __restrict__ rec_c) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
   __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
   const int wib = threadIdx.x >> 5;
@@ -275,9 +278,10 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       Real2 rc;
       rc.x = Real(0.5) * ev.rho;
       rc.y = ev.gap;
-      rec_a[o] = ra;
-      rec_b[o] = rb;
-      rec_c[o] = rc;
+      const int rp = c_rpos[o];
+      rec_a[rp] = ra;
+      rec_b[rp] = rb;
+      rec_c[rp] = rc;
     }
   }
   cp_async_wait<0>();
@@ -301,14 +305,14 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // 2. landmark pass: one CTA per tile of consecutive landmarks (internal numbering)
 // ---------------------------------------------------------------------------
 // Tile data: landmarks tile_lm[t] .. tile_lm[t+1]; their observations occupy the
-// landmark-sorted slots lm_ptr[first] .. lm_ptr[last]. Inside the tile they are visited in
-// camera-sorted order, t_cpos being the observation's camera-sorted position (where cpass
-// stored its record) and t_slot its landmark-sorted slot relative to the tile start; the
-// records of one camera are contiguous there. Reads the landmark state of iteration k and
-// writes that of k+1 to the other buffer.
+// landmark-sorted slots lm_ptr[first] .. lm_ptr[last] and the same range of record positions,
+// where cpass stored them in camera-sorted order; t_slot maps a record position to its
+// landmark-sorted slot relative to the tile start. Reads the landmark state of iteration k
+// and writes that of k+1 to the other buffer.
+// Shared memory: one 3 x V4 record per slot, (a-terms at xbar), (a-terms at x^k), (F, gap).
 template <class Real>
 __host__ __device__ inline size_t lpass_smem_bytes(int no_cap) {
-  return (size_t)no_cap * 10 * sizeof(Real) + 16;
+  return (size_t)no_cap * 3 * sizeof(V4<Real>) + 16;
 }
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
@@ -325,7 +329,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-            const int* __restrict__ t_cpos, const uint16_t* __restrict__ t_slot, const V4<Real>* __restrict__ rec_a,
+            const uint16_t* __restrict__ t_slot, const V4<Real>* __restrict__ rec_a,
             const V4<Real>* __restrict__ rec_b, const Real2* __restrict__ rec_c, const V4<Real>* __restrict__ lmrec,
             const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out,
             IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
@@ -336,25 +340,41 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  Real* sc = reinterpret_cast<Real*>(smem_raw);   // 10 x no_cap (SoA), indexed by slot
+  V4<Real>* sc = reinterpret_cast<V4<Real>*>(smem_raw);   // no_cap x 3 V4, indexed by slot
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
 
-  for (int o = threadIdx.x; o < no; o += blockDim.x) {
-    const int p = t_cpos[ob + o];
-    const int slot = t_slot[ob + o];
-    const V4<Real> ra = rec_a[p], rb = rec_b[p];
-    const Real2 rc = rec_c[p];
-    sc[0 * no_cap + slot] = ra.x;
-    sc[1 * no_cap + slot] = ra.y;
-    sc[2 * no_cap + slot] = ra.z;
-    sc[3 * no_cap + slot] = ra.w;
-    sc[4 * no_cap + slot] = rb.x;
-    sc[5 * no_cap + slot] = rb.y;
-    sc[6 * no_cap + slot] = rb.z;
-    sc[7 * no_cap + slot] = rb.w;
-    sc[8 * no_cap + slot] = rc.x;
-    sc[9 * no_cap + slot] = rc.y;
+  // stream the tile's records into slot order; each thread issues all loads of
+  // LPASS_UNROLL records before storing any
+  for (int o0 = 0; o0 < no; o0 += LPASS_THREADS * LPASS_UNROLL) {
+    int pos[LPASS_UNROLL], slot[LPASS_UNROLL];
+    V4<Real> ra[LPASS_UNROLL], rb[LPASS_UNROLL];
+    Real2 rc[LPASS_UNROLL];
+#pragma unroll
+    for (int u = 0; u < LPASS_UNROLL; ++u) {
+      const int o = o0 + u * LPASS_THREADS + threadIdx.x;
+      pos[u] = o < no ? ob + o : -1;
+      slot[u] = o < no ? t_slot[ob + o] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < LPASS_UNROLL; ++u)
+      if (pos[u] >= 0) {
+        ra[u] = rec_a[pos[u]];
+        rb[u] = rec_b[pos[u]];
+        rc[u] = rec_c[pos[u]];
+      }
+#pragma unroll
+    for (int u = 0; u < LPASS_UNROLL; ++u)
+      if (pos[u] >= 0) {
+        V4<Real> c;
+        c.x = rc[u].x;
+        c.y = rc[u].y;
+        c.z = Real(0);
+        c.w = Real(0);
+        sc[3 * slot[u] + 0] = ra[u];
+        sc[3 * slot[u] + 1] = rb[u];
+        sc[3 * slot[u] + 2] = c;
+      }
   }
   __syncthreads();
 
@@ -365,9 +385,19 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     Real st[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) st[k] = Real(0);
-    for (int s = s0; s < s1; ++s)
-#pragma unroll
-      for (int k = 0; k < 10; ++k) st[k] += sc[k * no_cap + s];
+    for (int s = s0; s < s1; ++s) {
+      const V4<Real> a = sc[3 * s], b = sc[3 * s + 1], c = sc[3 * s + 2];
+      st[0] += a.x;
+      st[1] += a.y;
+      st[2] += a.z;
+      st[3] += a.w;
+      st[4] += b.x;
+      st[5] += b.y;
+      st[6] += b.z;
+      st[7] += b.w;
+      st[8] += c.x;
+      st[9] += c.y;
+    }
     const size_t g = (size_t)(lb + jl);
     const V4<Real> A = lmrec[2 * g], B = lmrec[2 * g + 1];
     const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
