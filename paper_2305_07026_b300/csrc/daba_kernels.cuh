@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // where cpass stored them in camera-sorted order; t_slot maps a record position to its
 // landmark-sorted slot relative to the tile start. Reads the landmark state of iteration k
 // and writes that of k+1 to the other buffer.
-// Shared memory: one 3 x V4 record per slot, (a-terms at xbar), (a-terms at x^k), (F, gap).
+// Shared memory: three V4 arrays indexed by slot: (terms at xbar), (terms at x^k), (F, gap).
 template <class Real>
 __host__ __device__ inline size_t lpass_smem_bytes(int no_cap) {
   return (size_t)no_cap * 3 * sizeof(V4<Real>) + 16;
@@ -340,9 +340,23 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  V4<Real>* sc = reinterpret_cast<V4<Real>*>(smem_raw);   // no_cap x 3 V4, indexed by slot
+  V4<Real>* sca = reinterpret_cast<V4<Real>*>(smem_raw);   // three V4 arrays of no_cap, by slot
+  V4<Real>* scb = sca + no_cap;
+  V4<Real>* scc = scb + no_cap;
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
+  // the landmark state of this thread's landmark (at most one: nl <= blockDim.x) is loaded
+  // first so that its latency overlaps the record stream below
+  static_assert(TILE_LMS <= LPASS_THREADS, "one landmark per thread");
+  const int jl = threadIdx.x;
+  const size_t g = (size_t)(lb + jl);
+  V4<Real> A, B;
+  V4<float> lo0;
+  if (jl < nl) {
+    A = lmrec[2 * g];
+    B = lmrec[2 * g + 1];
+    if (HAS_LO) lo0 = lm_lo[g];
+  }
 
   // stream the tile's records into slot order; each thread issues all loads of
   // LPASS_UNROLL records before storing any
@@ -371,22 +385,22 @@ __global__ void __launch_bounds__(LPASS_THREADS)
         c.y = rc[u].y;
         c.z = Real(0);
         c.w = Real(0);
-        sc[3 * slot[u] + 0] = ra[u];
-        sc[3 * slot[u] + 1] = rb[u];
-        sc[3 * slot[u] + 2] = c;
+        sca[slot[u]] = ra[u];
+        scb[slot[u]] = rb[u];
+        scc[slot[u]] = c;
       }
   }
   __syncthreads();
 
   int nrs = 0;
   const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
-  for (int jl = threadIdx.x; jl < nl; jl += blockDim.x) {
+  if (jl < nl) {
     const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
     Real st[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) st[k] = Real(0);
     for (int s = s0; s < s1; ++s) {
-      const V4<Real> a = sc[3 * s], b = sc[3 * s + 1], c = sc[3 * s + 2];
+      const V4<Real> a = sca[s], b = scb[s], c = scc[s];
       st[0] += a.x;
       st[1] += a.y;
       st[2] += a.z;
@@ -398,8 +412,6 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       st[8] += c.x;
       st[9] += c.y;
     }
-    const size_t g = (size_t)(lb + jl);
-    const V4<Real> A = lmrec[2 * g], B = lmrec[2 * g + 1];
     const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
     // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
     //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
@@ -424,9 +436,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     nrs += (rs && P.accelerated) ? 1 : 0;
     V4<Real> nA, nB;
     if (HAS_LO) {
-      const V4<float> lo = lm_lo[g];
       float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
-      float o0 = lo.x, o1 = lo.y, o2 = lo.z;
+      float o0 = lo0.x, o1 = lo0.y, o2 = lo0.z;
       df_add(h0, o0, float(step0));
       df_add(h1, o1, float(step1));
       df_add(h2, o2, float(step2));
