@@ -39,7 +39,7 @@ UNIT = "obs-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tourism")
@@ -74,20 +74,23 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Max of a host scalar over the ranks (CUDA tensors with NCCL, host tensors with gloo)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
 def load_scene(args, rank, world):
+    """Rank 0 generates the workload; with several ranks it hands it to the others via a file."""
     from paper_2305_07026_b300 import scenes
     if world == 1:
         return scenes.make_scene(args.workload, scale=args.scale)
-    path = os.path.join(tempfile.gettempdir(), f"daba_bench_{args.workload}_{args.scale}.npz")
+    path = os.path.join(tempfile.gettempdir(), f"daba_bench_{args.workload}_{args.scale}_{os.environ.get('MASTER_PORT', '0')}.npz")
     if rank == 0:
         sc = scenes.make_scene(args.workload, scale=args.scale)
         np.savez(path + ".tmp.npz", **{k: getattr(sc, k) for k in
@@ -111,7 +114,8 @@ def load_scene(args, rank, world):
 # ----------------------------------------------------------------------------
 
 class Clocks:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms) kept only when taken inside the timed window."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -123,11 +127,15 @@ class Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
 
-    def stop(self, gpu_index):
+    def mark(self):
+        return time.time()
+
+    def stop(self, gpu_index, t0=None, t1=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -138,16 +146,20 @@ class Clocks:
         self.fh.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
         for line in open(self.path):
             p = [x.strip() for x in line.split(",")]
-            if len(p) < 9 or p[0] != str(gpu_index):
+            if len(p) < 10 or p[1] != str(gpu_index):
                 continue
             try:
-                sm.append(float(p[1].split()[0]))
-                mx.append(float(p[2].split()[0]))
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t0 is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
+                    continue
+                sm.append(float(p[2].split()[0]))
+                mx.append(float(p[3].split()[0]))
             except ValueError:
                 continue
-            for nm, v in zip(names, p[5:9]):
+            for nm, v in zip(names, p[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
@@ -161,19 +173,23 @@ class Clocks:
 # ----------------------------------------------------------------------------
 
 def algorithmic_bytes(sc, prec):
-    """Bytes a kernel must move at least once per launch (see the design notes)."""
+    """Bytes each pass must move at least once per launch (each datum once; see the design notes).
+
+    cpass: per observation the landmark index, the pixel and the record position (4 + 2R + 4)
+           are read and the 10-value landmark-side record (10R) is written; each landmark's
+           position and displacement (6R) and each camera pack (48R) are read once; one partial
+           of 80 values (80R) is written per chunk of at most 1024 observations.
+    lpass: per observation the record (10R) and its slot (2) are read; per landmark its state
+           record (8R, plus 16 B of low parts in MIXED) is read and written, its restart flag
+           written and its CSR offset read (4).
+    """
     R = 4 if prec == "mixed" else 8
     nnz, N, M = sc.nnz, sc.N, sc.M
     deg = np.bincount(sc.cam_idx, minlength=M)
     n_chunks = int(np.sum((deg + 1023) // 1024))
-    pack = M * 48 * R
-    # camera-sorted pass: landmark index + pixel per observation, landmark position and
-    # displacement once, camera pack once, FP64 partial statistics per chunk
-    cpass = nnz * (4 + 2 * R) + N * 6 * R + pack + n_chunks * 80 * 8
-    # landmark-sorted pass: camera index + pixel + slot per observation, landmark record
-    # (+ low parts in MIXED) read and written, restart flag, CSR offsets, camera pack
+    cpass = nnz * (4 + 2 * R + 4 + 10 * R) + N * 6 * R + M * 48 * R + n_chunks * 80 * R
     lrec = 8 * R + (16 if prec == "mixed" else 0)
-    lpass = nnz * (4 + 2 * R + 2) + N * (2 * lrec + 1 + 4) + pack + (0 if prec == "mixed" else N * 16)
+    lpass = nnz * (10 * R + 2) + N * (2 * lrec + 1 + 4)
     return {"cpass": cpass, "lpass": lpass}
 
 
@@ -277,14 +293,16 @@ def run_ours(args, rank, world, local):
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
+    t_wall0 = clocks.mark()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     d.run(K, stream=sp)
     e1.record(stream)
     e1.synchronize()
+    t_wall1 = clocks.mark()
     torch.cuda.synchronize()
     barrier(world)
-    ck = clocks.stop(local)
+    ck = clocks.stop(local, t_wall0, t_wall1)
     ms = e0.elapsed_time(e1)
     kern_ms = d.get_timing()          # summed over the K iterations
     launches = d.last_launch_count()
@@ -319,15 +337,18 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel (per launch, live CUDA events)
     names = ["cam_prepare", "cpass", "lpass", "camsolve", "finalize"]
     per_launch_ms = {n: kern_ms[i] / (K if i else -(-K // 1024)) for i, n in enumerate(names)}
-    dom = max(("cpass", "lpass"), key=lambda n: per_launch_ms[n])
-    alg = algorithmic_bytes(sc, "mixed")[dom]
     pk = peaks()
     peak_gbs = pk["hbm_gbs"] if pk else 6400.0
-    achieved = alg / (per_launch_ms[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": achieved / peak_gbs, "traffic": committed_traffic(dom, args.workload),
-                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms[dom],
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s"}
+    algb = algorithmic_bytes(sc, "mixed")
+    per_kernel = {}
+    for n in ("cpass", "lpass"):
+        ach = algb[n] / (per_launch_ms[n] / 1e3) / 1e9
+        per_kernel[n] = {"bound": "hbm", "achieved": ach, "peak": peak_gbs, "unit": "GB/s", "frac": ach / peak_gbs,
+                         "traffic": committed_traffic(n, args.workload), "algorithmic_bytes_per_launch": algb[n],
+                         "launch_ms": per_launch_ms[n]}
+    dom = max(("cpass", "lpass"), key=lambda n: per_launch_ms[n])
+    roofline = dict(per_kernel[dom], kernel=dom,
+                    peak_source="measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6.4 TB/s")
 
     # ---- end to end through the public API with host buffers: per step the iterate goes
     # host -> device (daba_set_state), one iteration runs, the objective and the iterate
@@ -373,7 +394,8 @@ def run_ours(args, rank, world, local):
                       "mixed_speedup": value / world / fp64_value},
         "accuracy": accuracy,
         "kernel_ms_per_launch": per_launch_ms,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roofline, "roofline_kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches),
         "clocks": ck,
     }
 
