@@ -17,6 +17,7 @@
 
 #include "../../include/daba.h"
 #include "daba_kernels.cuh"
+#include "daba_state.cuh"
 
 using namespace daba;
 
@@ -25,7 +26,6 @@ namespace {
 constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: observations per warp chunk
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
-constexpr int LR_L = 0;           // offset of l in the record
 constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
@@ -53,8 +53,6 @@ struct daba_ctx {
   std::vector<int32_t> h_li_order;          // observations sorted by internal landmark id
   std::vector<int32_t> h_ci_order;          // observations in the device's camera order
   std::vector<int32_t> h_lperm, h_linv;     // internal -> external landmark id and inverse
-  std::vector<double> h_t;   // camera centres of the state last set (for the Asm. 2 check)
-  std::vector<double> h_l;
   // device buffers
   void *c_lm = nullptr, *c_u = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
@@ -68,6 +66,8 @@ struct daba_ctx {
   void *fin_blk = nullptr, *fin_ticket = nullptr;
   void *d_gam = nullptr, *d_it = nullptr, *d_first = nullptr, *d_flag = nullptr, *d_trace = nullptr,
        *d_rs = nullptr, *d_obj = nullptr;
+  // state I/O: staging of boundary-layout state, external -> internal landmark id, checks
+  void *st_cam = nullptr, *st_lm = nullptr, *d_linv = nullptr, *d_chk = nullptr, *d_bad = nullptr;
   std::vector<void*> allocs;
   std::vector<cudaEvent_t> events;
   cudaStream_t s_hi = nullptr, s_lo = nullptr;   // camera pass + solves (high priority), landmark pass
@@ -147,50 +147,6 @@ inline void* lmlo_at(const daba_ctx* c, int64_t k) { return c->lm_lo2[k & 1]; }
 inline size_t lm_internal(const daba_ctx* c, int j) { return c->h_linv.empty() ? (size_t)j : (size_t)c->h_linv[j]; }
 size_t real_sz(const daba_ctx* c) { return is_mixed(c) ? sizeof(float) : sizeof(double); }
 
-// ---- rotation parameterisation (boundary <-> R)
-void rodrigues(const double* w, double* R) {
-  const double th = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-  double a, b;
-  if (th < 1e-8) {
-    a = 1.0 - th * th / 6.0;
-    b = 0.5 - th * th / 24.0;
-  } else {
-    a = std::sin(th) / th;
-    b = (1.0 - std::cos(th)) / (th * th);
-  }
-  const double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
-  double K2[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double s = 0;
-      for (int k = 0; k < 3; ++k) s += K[i * 3 + k] * K[k * 3 + j];
-      K2[i * 3 + j] = s;
-    }
-  for (int i = 0; i < 9; ++i) R[i] = ((i % 4) == 0 ? 1.0 : 0.0) + a * K[i] + b * K2[i];
-}
-
-void rot_log(const double* A, double* w) {
-  const double c = (A[0] + A[4] + A[8] - 1.0) / 2.0;
-  const double v[3] = {(A[7] - A[5]) / 2.0, (A[2] - A[6]) / 2.0, (A[3] - A[1]) / 2.0};
-  const double sn = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-  const double th = std::atan2(sn, c);
-  if (c > -0.5) {
-    const double f = sn > 1e-300 ? th / sn : 1.0;
-    for (int k = 0; k < 3; ++k) w[k] = v[k] * f;
-    return;
-  }
-  double B[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) B[i * 3 + j] = 0.5 * (A[i * 3 + j] + A[j * 3 + i]) - (i == j ? c : 0.0);
-  int kk = 0;
-  for (int k = 1; k < 3; ++k)
-    if (B[k * 4] > B[kk * 4]) kk = k;
-  double a[3] = {B[0 * 3 + kk], B[1 * 3 + kk], B[2 * 3 + kk]};
-  const double n = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-  double sg = (a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) < 0 ? -1.0 : 1.0;
-  for (int k = 0; k < 3; ++k) w[k] = sg * a[k] / n * th;
-}
-
 // stable counting sort of 0..n-1 by key in [0, K): order and CSR offsets
 void counting_sort(const std::vector<int32_t>& key, int K, std::vector<int32_t>& order, std::vector<int32_t>& ptr) {
   const int64_t n = (int64_t)key.size();
@@ -227,20 +183,27 @@ daba_status ensure_u(daba_ctx* ctx, cudaStream_t st) {
   return DABA_OK;
 }
 
-// Assumption 2 check on the host copies of the observations and the state last set
-daba_status check_degenerate(daba_ctx* ctx) {
+// Assumption 2 check of the current iterate on the device (once per state set)
+daba_status check_degenerate(daba_ctx* ctx, cudaStream_t st) {
   if (ctx->checked) return DABA_OK;
-  for (int64_t o = 0; o < ctx->nnz; ++o) {
-    const int i = ctx->h_cam_idx[o], j = ctx->h_lm_idx[o];
-    double q2 = 0, t2 = 0;
-    for (int a = 0; a < 3; ++a) {
-      const double q = ctx->h_l[3 * (size_t)j + a] - ctx->h_t[3 * (size_t)i + a];
-      q2 += q * q;
-      t2 += ctx->h_t[3 * (size_t)i + a] * ctx->h_t[3 * (size_t)i + a];
-    }
-    if (!(q2 > 1e-24 * std::max(1.0, t2)))
-      return fail(ctx, DABA_ERR_DEGENERATE, "observation %lld: landmark %d coincides with camera %d centre",
-                  (long long)o, j, i);
+  k_chk_init<<<1, 32, 0, st>>>((int*)ctx->d_chk, (unsigned long long*)ctx->d_bad);
+  if (is_mixed(ctx))
+    k_check_degenerate<float, true><<<ctx->n_chunks, 256, 0, st>>>(
+        (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm, (const double*)ctx->cam_x,
+        (const V4<float>*)lmrec_at(ctx, ctx->k), (const V4<float>*)lmlo_at(ctx, ctx->k),
+        (unsigned long long*)ctx->d_bad);
+  else
+    k_check_degenerate<double, false><<<ctx->n_chunks, 256, 0, st>>>(
+        (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm, (const double*)ctx->cam_x,
+        (const V4<double>*)lmrec_at(ctx, ctx->k), nullptr, (unsigned long long*)ctx->d_bad);
+  CK(cudaGetLastError());
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_bad, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad != ~0ull) {
+    const int32_t o = ctx->h_ci_order[(size_t)bad];   // input index of that observation
+    return fail(ctx, DABA_ERR_DEGENERATE, "observation %d: landmark %d coincides with camera %d centre", o,
+                ctx->h_lm_idx[o], ctx->h_cam_idx[o]);
   }
   ctx->checked = true;
   return DABA_OK;
@@ -523,6 +486,11 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_trace, (GSEG + 1) * 8);
   AL(d_rs, (GSEG + 1) * 4);
   AL(d_obj, 16);
+  AL(st_cam, (size_t)M * 9 * 8);
+  AL(st_lm, (size_t)N * 3 * 8);
+  AL(d_linv, (size_t)N * 4);
+  AL(d_chk, CHK_N * 4);
+  AL(d_bad, 16);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -538,6 +506,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     return DABA_ERR_CUDA;
   }
   cudaMemset(ctx->d_flag, 0, 16);
+  k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_linv);   // identity numbering until observations are set
   cudaMemset(ctx->fin_ticket, 0, 16);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
@@ -676,6 +645,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->c_rpos, c_rpos.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_linv, linv.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
   ctx->n_tiles = n_tiles;
@@ -716,69 +686,52 @@ daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms,
   if (!cams || !lms) return fail(ctx, DABA_ERR_ARG, "null state pointer");
   cudaStream_t st = (cudaStream_t)stream;
   const int M = ctx->M, N = ctx->N;
-  std::vector<double> hc((size_t)M * 9), hl((size_t)N * 3);
-  daba_status s;
-  if ((s = fetch(ctx, hc.data(), cams, hc.size() * 8, st)) != DABA_OK) return s;
-  if ((s = fetch(ctx, hl.data(), lms, hl.size() * 8, st)) != DABA_OK) return s;
-  for (double v : hc)
-    if (!std::isfinite(v)) return fail(ctx, DABA_ERR_NONFINITE, "non-finite camera parameter");
-  for (double v : hl)
-    if (!std::isfinite(v)) return fail(ctx, DABA_ERR_NONFINITE, "non-finite landmark coordinate");
-  for (int i = 0; i < M; ++i)
-    if (!(hc[(size_t)i * 9 + 6] > 0)) return fail(ctx, DABA_ERR_ARG, "camera %d has a non-positive focal length", i);
+  // device views of the inputs: the caller's device buffers, else one copy into staging
+  const bool cdev = is_device_ptr(cams), ldev = is_device_ptr(lms);
+  const double* dc = cdev ? cams : (const double*)ctx->st_cam;
+  const double* dl = ldev ? lms : (const double*)ctx->st_lm;
+  if (!cdev) CK(cudaMemcpyAsync(ctx->st_cam, cams, (size_t)M * 9 * 8, cudaMemcpyHostToDevice, st));
+  if (!ldev) CK(cudaMemcpyAsync(ctx->st_lm, lms, (size_t)N * 3 * 8, cudaMemcpyHostToDevice, st));
+  // validation before anything of the current state is overwritten
+  k_chk_init<<<1, 32, 0, st>>>((int*)ctx->d_chk, (unsigned long long*)ctx->d_bad);
+  k_check_state<<<148 * 4, 256, 0, st>>>(M, N, dc, dl, (int*)ctx->d_chk);
+  CK(cudaGetLastError());
+  int chk[CHK_N];
+  CK(cudaMemcpyAsync(chk, ctx->d_chk, sizeof(chk), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (chk[CHK_CAM_NONFINITE] != INT_MAX)
+    return fail(ctx, DABA_ERR_NONFINITE, "camera %d has a non-finite parameter", chk[CHK_CAM_NONFINITE]);
+  if (chk[CHK_LM_NONFINITE] != INT_MAX)
+    return fail(ctx, DABA_ERR_NONFINITE, "landmark %d has a non-finite coordinate", chk[CHK_LM_NONFINITE]);
+  if (chk[CHK_FOCAL] != INT_MAX)
+    return fail(ctx, DABA_ERR_ARG, "camera %d has a non-positive focal length", chk[CHK_FOCAL]);
+  // internal unit s: the option, else the one fixed by the first state, else the median focal
   double sn = ctx->opt.pixel_scale;
   if (!(sn > 0)) {
     if (ctx->s_norm > 0) {
       sn = ctx->s_norm;
     } else {
       std::vector<double> f(M);
-      for (int i = 0; i < M; ++i) f[i] = hc[(size_t)i * 9 + 6];
+      if (cdev) {
+        CK(cudaMemcpy2DAsync(f.data(), 8, cams + 6, 9 * 8, 8, M, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+      } else {
+        for (int i = 0; i < M; ++i) f[i] = cams[(size_t)i * 9 + 6];
+      }
       std::sort(f.begin(), f.end());
       sn = (M % 2) ? f[M / 2] : 0.5 * (f[M / 2 - 1] + f[M / 2]);
     }
   }
   ctx->s_norm = sn;
-  std::vector<double> x((size_t)M * CSTRIDE, 0.0), dx((size_t)M * CSTRIDE, 0.0), zeros(M, 0.0);
-  ctx->h_t.assign((size_t)M * 3, 0.0);
-  for (int i = 0; i < M; ++i) {
-    const double* c = &hc[(size_t)i * 9];
-    double* xi = &x[(size_t)i * CSTRIDE];
-    rodrigues(c, xi + CS_R);
-    for (int a = 0; a < 3; ++a) {
-      xi[CS_T + a] = c[3 + a];
-      ctx->h_t[(size_t)i * 3 + a] = c[3 + a];
-    }
-    const double f = c[6], k1 = c[7], k2 = c[8];
-    xi[CS_D + 0] = f / sn;
-    xi[CS_D + 1] = k1 * sn / f;
-    xi[CS_D + 2] = k2 * sn * sn * sn / (f * f * f);
-  }
-  CK(cudaMemcpyAsync(ctx->cam_x, x.data(), x.size() * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_dx, dx.data(), dx.size() * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_S, zeros.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->cam_E, zeros.data(), (size_t)M * 8, cudaMemcpyHostToDevice, st));
-  if (is_mixed(ctx)) {
-    std::vector<float> rec((size_t)N * LREC, 0.f), lo((size_t)N * 4, 0.f);
-    for (int j = 0; j < N; ++j) {
-      const size_t q = lm_internal(ctx, j);
-      for (int a = 0; a < 3; ++a) {
-        const double v = hl[(size_t)j * 3 + a];
-        const float h = (float)v;
-        rec[q * LREC + LR_L + a] = h;
-        lo[q * 4 + a] = (float)(v - (double)h);
-      }
-    }
-    CK(cudaMemcpyAsync(ctx->lmrec2[0], rec.data(), rec.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->lm_lo2[0], lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-  } else {
-    std::vector<double> rec((size_t)N * LREC, 0.0);
-    for (int j = 0; j < N; ++j)
-      for (int a = 0; a < 3; ++a) rec[lm_internal(ctx, j) * LREC + LR_L + a] = hl[(size_t)j * 3 + a];
-    CK(cudaMemcpyAsync(ctx->lmrec2[0], rec.data(), rec.size() * 8, cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-  }
-  ctx->h_l.swap(hl);
+  k_set_cams<<<(M + 127) / 128, 128, 0, st>>>(M, dc, sn, (double*)ctx->cam_x, (double*)ctx->cam_dx,
+                                               (double*)ctx->cam_S, (double*)ctx->cam_E);
+  if (is_mixed(ctx))
+    k_set_lms<float, true><<<(N + 255) / 256, 256, 0, st>>>(N, dl, (const int*)ctx->d_linv,
+                                                            (V4<float>*)ctx->lmrec2[0], (V4<float>*)ctx->lm_lo2[0]);
+  else
+    k_set_lms<double, false><<<(N + 255) / 256, 256, 0, st>>>(N, dl, (const int*)ctx->d_linv,
+                                                              (V4<double>*)ctx->lmrec2[0], nullptr);
+  CK(cudaGetLastError());
   int one = 1;
   CK(cudaMemcpyAsync(ctx->d_first, &one, sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
@@ -795,7 +748,7 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   cudaStream_t st = (cudaStream_t)stream;
   daba_status s;
-  if ((s = check_degenerate(ctx)) != DABA_OK) return s;
+  if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
   if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
   ctx->launches = 0;
   for (double& t : ctx->tms) t = 0.0;
@@ -887,7 +840,7 @@ daba_status daba_objective(daba_ctx* ctx, double* out, void* stream) {
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   cudaStream_t st = (cudaStream_t)stream;
   daba_status s;
-  if ((s = check_degenerate(ctx)) != DABA_OK) return s;
+  if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
   if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
   // gamma buffer entry 0 is read by the prepare kernel; any finite value will do
   double g0 = 0.0;
@@ -907,45 +860,28 @@ daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* strea
   if (!ctx->state_set) return fail(ctx, DABA_ERR_STATE, "state not set");
   cudaStream_t st = (cudaStream_t)stream;
   const int M = ctx->M, N = ctx->N;
-  const double sn = ctx->s_norm;
-  daba_status s;
+  // converted on the device into the caller's device buffer, else into staging + one copy
   if (cams) {
-    std::vector<double> x((size_t)M * CSTRIDE), hc((size_t)M * 9);
-    CK(cudaMemcpyAsync(x.data(), ctx->cam_x, x.size() * 8, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    for (int i = 0; i < M; ++i) {
-      const double* xi = &x[(size_t)i * CSTRIDE];
-      double* c = &hc[(size_t)i * 9];
-      rot_log(xi + CS_R, c);
-      for (int a = 0; a < 3; ++a) c[3 + a] = xi[CS_T + a];
-      const double f = xi[CS_D + 0] * sn;
-      c[6] = f;
-      c[7] = xi[CS_D + 1] * f / sn;
-      c[8] = xi[CS_D + 2] * f * f * f / (sn * sn * sn);
-    }
-    if ((s = deliver(ctx, cams, hc.data(), hc.size() * 8, st)) != DABA_OK) return s;
+    const bool dev = is_device_ptr(cams);
+    double* out = dev ? cams : (double*)ctx->st_cam;
+    k_get_cams<<<(M + 127) / 128, 128, 0, st>>>(M, (const double*)ctx->cam_x, ctx->s_norm, out);
+    CK(cudaGetLastError());
+    if (!dev) CK(cudaMemcpyAsync(cams, out, (size_t)M * 9 * 8, cudaMemcpyDeviceToHost, st));
   }
   if (lms) {
-    std::vector<double> hl((size_t)N * 3);
-    if (is_mixed(ctx)) {
-      std::vector<float> rec((size_t)N * LREC), lo((size_t)N * 4);
-      CK(cudaMemcpyAsync(rec.data(), lmrec_at(ctx, ctx->k), rec.size() * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(lo.data(), lmlo_at(ctx, ctx->k), lo.size() * 4, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int j = 0; j < N; ++j) {
-        const size_t q = lm_internal(ctx, j);
-        for (int a = 0; a < 3; ++a)
-          hl[(size_t)j * 3 + a] = (double)rec[q * LREC + LR_L + a] + (double)lo[q * 4 + a];
-      }
-    } else {
-      std::vector<double> rec((size_t)N * LREC);
-      CK(cudaMemcpyAsync(rec.data(), lmrec_at(ctx, ctx->k), rec.size() * 8, cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int j = 0; j < N; ++j)
-        for (int a = 0; a < 3; ++a) hl[(size_t)j * 3 + a] = rec[lm_internal(ctx, j) * LREC + LR_L + a];
-    }
-    if ((s = deliver(ctx, lms, hl.data(), hl.size() * 8, st)) != DABA_OK) return s;
+    const bool dev = is_device_ptr(lms);
+    double* out = dev ? lms : (double*)ctx->st_lm;
+    if (is_mixed(ctx))
+      k_get_lms<float, true><<<(N + 255) / 256, 256, 0, st>>>(N, (const V4<float>*)lmrec_at(ctx, ctx->k),
+                                                              (const V4<float>*)lmlo_at(ctx, ctx->k),
+                                                              (const int*)ctx->d_linv, out);
+    else
+      k_get_lms<double, false><<<(N + 255) / 256, 256, 0, st>>>(N, (const V4<double>*)lmrec_at(ctx, ctx->k), nullptr,
+                                                                (const int*)ctx->d_linv, out);
+    CK(cudaGetLastError());
+    if (!dev) CK(cudaMemcpyAsync(lms, out, (size_t)N * 3 * 8, cudaMemcpyDeviceToHost, st));
   }
+  CK(cudaStreamSynchronize(st));
   return DABA_OK;
 }
 

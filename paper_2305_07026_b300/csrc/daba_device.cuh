@@ -440,4 +440,54 @@ __device__ inline bool chol6_solve(double A[6][6], double b[6]) {
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Boundary rotation parameterisation (host and device): axis-angle w <-> R.
+// ---------------------------------------------------------------------------
+
+// R = exp([w]x) = I + a [w]x + b [w]x^2 with a = sin(th)/th, b = (1 - cos(th))/th^2 (Rodrigues'
+// formula), th = |w|; the series of a and b below 1e-8.
+__host__ __device__ inline void rodrigues(const double* w, double* R) {
+  const double th = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double a, b;
+  if (th < 1e-8) {
+    a = 1.0 - th * th / 6.0;
+    b = 0.5 - th * th / 24.0;
+  } else {
+    a = sin(th) / th;
+    b = (1.0 - cos(th)) / (th * th);
+  }
+  const double K[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double k2 = 0.0;
+      for (int m = 0; m < 3; ++m) k2 += K[i * 3 + m] * K[m * 3 + j];
+      R[i * 3 + j] = (i == j ? 1.0 : 0.0) + a * K[i * 3 + j] + b * k2;
+    }
+}
+
+// w = log(R): the angle from atan2(|v|, (tr R - 1)/2) with v the axial vector of the
+// antisymmetric part; for angles beyond 2 pi / 3 the axis comes from the largest column of
+// the symmetric part (R + R^T)/2 - cos(th) I = (1 - cos th) n n^T, its sign from v.
+__host__ __device__ inline void rot_log(const double* A, double* w) {
+  const double c = (A[0] + A[4] + A[8] - 1.0) / 2.0;
+  const double v[3] = {(A[7] - A[5]) / 2.0, (A[2] - A[6]) / 2.0, (A[3] - A[1]) / 2.0};
+  const double sn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double th = atan2(sn, c);
+  if (c > -0.5) {
+    const double f = sn > 1e-300 ? th / sn : 1.0;
+    for (int k = 0; k < 3; ++k) w[k] = v[k] * f;
+    return;
+  }
+  double B[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[i * 3 + j] = 0.5 * (A[i * 3 + j] + A[j * 3 + i]) - (i == j ? c : 0.0);
+  int kk = 0;
+  for (int k = 1; k < 3; ++k)
+    if (B[k * 4] > B[kk * 4]) kk = k;
+  const double a[3] = {B[0 * 3 + kk], B[1 * 3 + kk], B[2 * 3 + kk]};
+  const double n = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const double sg = (a[0] * v[0] + a[1] * v[1] + a[2] * v[2]) < 0 ? -1.0 : 1.0;
+  for (int k = 0; k < 3; ++k) w[k] = sg * a[k] / n * th;
+}
+
 }  // namespace daba

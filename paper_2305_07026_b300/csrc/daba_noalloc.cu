@@ -68,28 +68,8 @@ __global__ void k_na_cams(int M, const double* __restrict__ cams, double s, doub
   if (i == 0) scratch[NA_FLAG] = 0.0;   // clear the invalid-input flag of this call
   if (i >= M) return;
   const double* c = cams + (size_t)i * 9;
-  const double w0 = c[0], w1 = c[1], w2 = c[2];
-  const double th = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
-  double a, b;
-  if (th < 1e-8) {
-    a = 1.0 - th * th / 6.0;
-    b = 0.5 - th * th / 24.0;
-  } else {
-    a = sin(th) / th;
-    b = (1.0 - cos(th)) / (th * th);
-  }
-  // R = I + a [w]x + b [w]x^2 (Rodrigues)
-  const double K[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
   double* o = scratch + (size_t)i * NA_CAM_STRIDE;
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double k2 = 0.0;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) k2 += K[r * 3 + m] * K[m * 3 + q];
-      o[daba::PK_R + r * 3 + q] = (r == q ? 1.0 : 0.0) + a * K[r * 3 + q] + b * k2;
-    }
+  daba::rodrigues(c, o + daba::PK_R);
   const double f = c[6];
   o[daba::PK_TH + 0] = c[3];
   o[daba::PK_TH + 1] = c[4];
