@@ -320,17 +320,26 @@ def run_ours(args, rank, world, local):
     e1.synchronize()
     ms64 = e0.elapsed_time(e1)
     d64.close()
+    # the mixed path from the same x^0: its iteration count to reach FP64's final objective
+    # within 1e-5 (run on, untimed, up to 3 Kf iterations when it needs more than Kf)
+    target = tr64[-1] * (1 + 1e-5)
     dm = make("mixed")
     trm = np.zeros(Kf + 1)
     dm.run(Kf, trm, stream=sp)
+    while not np.any(trm <= target) and len(trm) - 1 < 3 * Kf:
+        seg = np.zeros(Kf + 1)
+        dm.run(Kf, seg, stream=sp)
+        trm = np.concatenate([trm, seg[1:]])
     dm.close()
-    target = tr64[-1] * (1 + 1e-5)
     reach = np.flatnonzero(trm <= target)
-    accuracy = {"iters": Kf, "fp64_final_px2": float(tr64[-1]), "mixed_final_px2": float(trm[-1]),
-                "mixed_best_px2": float(trm.min()),
-                "mixed_rel_to_fp64": float((trm[-1] - tr64[-1]) / tr64[-1]),
+    mixed_ms_iter = ms / K
+    accuracy = {"iters": Kf, "fp64_final_px2": float(tr64[-1]), "mixed_final_px2": float(trm[Kf]),
+                "mixed_rel_to_fp64": float((trm[Kf] - tr64[-1]) / tr64[-1]),
                 "mixed_reaches_fp64_within_1e-5": bool(reach.size > 0),
                 "mixed_iters_to_reach": int(reach[0]) if reach.size else None,
+                "mixed_iters_run": int(len(trm) - 1),
+                "speedup_at_equal_objective": (float(ms64 / (mixed_ms_iter * reach[0])) if reach.size and reach[0] > 0
+                                               else None),
                 "initial_px2": float(tr64[0])}
     fp64_value = sc.nnz * Kf / (ms64 / 1e3)
 

@@ -90,7 +90,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
  * principal point, row-major nnz x 2. The library sorts the observations stably
  * by camera and by landmark (ties keep input order) and builds its CSR offsets
  * and work schedules (setup, not part of an iteration). Resets the iteration
- * count and the restart metrics. At most 1024 observations per landmark (DABA_ERR_ARG otherwise). */
+ * count and the restart metrics. At most 2048 observations per landmark (DABA_ERR_ARG otherwise). */
 daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const int32_t* lm_idx,
                                   const double* uv, void* stream);
 

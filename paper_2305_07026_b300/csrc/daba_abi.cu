@@ -318,15 +318,15 @@ cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
 cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
-  const int blocks = (ctx->M + 63) / 64;
+  const int blocks = (ctx->M + CAMSOLVE_THREADS - 1) / CAMSOLVE_THREADS;
   if (is_mixed(ctx))
-    k_camsolve<float><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
+    k_camsolve<float><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
                                              (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
                                              (V4<float>*)pack_at(ctx, k + 1));
   else
-    k_camsolve<double><<<blocks, 64, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
+    k_camsolve<double><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
                                               (const double*)ctx->chunk_part, (double*)ctx->cam_x,
                                               (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
                                               (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,

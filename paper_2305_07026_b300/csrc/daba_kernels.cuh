@@ -32,8 +32,12 @@
 
 namespace daba {
 
-// ---- chunk partial layout (pass precision): Hbar[21] Bbar[18] H[21] B[18] sumF sumGap pad
-enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_STRIDE = 84 };
+// ---- camera-pass accumulators (registers): Hbar[21] Bbar[18] H[21] B[18] sumF sumGap
+enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_NACC = 80 };
+// ---- chunk partial in memory (pass precision), each statistics set padded to 40 so that
+//      it starts on a 16-byte boundary: [Hbar Bbar pad] [H B pad] sumF sumGap pad pad
+enum { PART_XB = 0, PART_XK = 40, PART_F = 80, PART_G = 81, CP_STRIDE = 84 };
+__host__ __device__ constexpr int part_slot(int k) { return k < 39 ? k : (k < 78 ? k + 1 : k + 2); }
 // ---- tile partial layout (doubles): sumF restarts pad pad
 enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 // ---- landmark record (two V4): (l[3], delta0) (delta1, delta2, S, E), with l the high part
@@ -43,6 +47,7 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
 constexpr int CPASS_WARPS = 4;
+constexpr int CAMSOLVE_THREADS = 64;   // one camera per active thread
 constexpr int LPASS_THREADS = 128;
 constexpr int LPASS_UNROLL = 4;   // observations whose records a thread loads before storing any
 constexpr int TILE_OBS = 512;     // observations of a small landmark tile
@@ -183,6 +188,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -191,11 +200,12 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int CPASS_STAGES = 4;   // batches of 32 observations in flight per warp
 
-// Per lane and stage: the landmark record (two V4) and the pixel.
+// Per lane and stage: the landmark record (two V4), the pixel and the record position.
 template <class Real, class Real2>
 struct CpassStage {
   V4<Real> rec[2];
   Real2 u;
+  int rpos;
 };
 
 // Landmark-side record of one observation, stored at c_rpos[o], its position in the landmark
@@ -242,6 +252,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
         cp_async16(&d.u, c_u + o);
       else
         cp_async8(&d.u, c_u + o);
+      cp_async4(&d.rpos, c_rpos + o);
     }
     cp_async_commit();
   };
@@ -278,7 +289,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       Real2 rc;
       rc.x = Real(0.5) * ev.rho;
       rc.y = ev.gap;
-      const int rp = c_rpos[o];
+      const int rp = d.rpos;
       rec_a[rp] = ra;
       rec_b[rp] = rb;
       rec_c[rp] = rc;
@@ -297,7 +308,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   if (lane == 0) {
     Real* out = part + (size_t)warp * CP_STRIDE;
 #pragma unroll
-    for (int k = 0; k < 80; ++k) out[k] = acc[k];
+    for (int k = 0; k < CP_NACC; ++k) out[part_slot(k)] = acc[k];
+    out[39] = out[79] = out[82] = out[83] = Real(0);
   }
 }
 
@@ -509,9 +521,12 @@ __device__ __forceinline__ void mcol(const Cam& c, int a, double out[3]) {
   }
 }
 
+// Packed camera statistics: H (upper triangle, row-major, 21 values) then B (6x3, 18 values).
+__device__ __forceinline__ double st_H(const double* s, int a, int b) { return a <= b ? s[tri6(a, b)] : s[tri6(b, a)]; }
+__device__ __forceinline__ double st_B(const double* s, int a, int c) { return s[21 + a * 3 + c]; }
+
 // E^alpha(c | z) - E^alpha(c_z | z) = xi/2 |c - c_z|^2 + tr(dM H dM^T) + 2 tr(dM B).
-__device__ inline double cam_phi(const double H[6][6], const double B[6][3], const Cam& z, const Cam& c,
-                                 double xi) {
+__device__ inline double cam_phi(const double* st, const Cam& z, const Cam& c, double xi) {
   double dM[6][3];
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
@@ -531,9 +546,11 @@ __device__ inline double cam_phi(const double H[6][6], const double B[6][3], con
   double q = 0.0, lin = 0.0;
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
+    q += st_H(st, a, a) * (dM[a][0] * dM[a][0] + dM[a][1] * dM[a][1] + dM[a][2] * dM[a][2]);
 #pragma unroll
-    for (int b = 0; b < 6; ++b) q += H[a][b] * (dM[a][0] * dM[b][0] + dM[a][1] * dM[b][1] + dM[a][2] * dM[b][2]);
-    lin += dM[a][0] * B[a][0] + dM[a][1] * B[a][1] + dM[a][2] * B[a][2];
+    for (int b = a + 1; b < 6; ++b)
+      q += 2.0 * st_H(st, a, b) * (dM[a][0] * dM[b][0] + dM[a][1] * dM[b][1] + dM[a][2] * dM[b][2]);
+    lin += dM[a][0] * st_B(st, a, 0) + dM[a][1] * st_B(st, a, 1) + dM[a][2] * st_B(st, a, 2);
   }
   return 0.5 * xi * prox + q + 2.0 * lin;
 }
@@ -545,8 +562,7 @@ __device__ inline double cam_phi(const double H[6][6], const double B[6][3], con
 // (t, d)-step: with R fixed, dM h = dM0 h + v (phi . dd) + lambda dt with v = R e3 and
 //   dM0 = M(R, t_z, d_z) - M(c_z); the normal equations of the resulting least squares
 //   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5] and are solved by Cholesky.
-__device__ inline void cam_scam(const double H[6][6], const double B[6][3], const Cam& z, double xi, int n_alt,
-                                Cam& c) {
+__device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n_alt, Cam& c) {
   c = z;
   for (int it = 0; it < n_alt; ++it) {
     // ---- R-step
@@ -567,9 +583,9 @@ __device__ inline void cam_scam(const double H[6][6], const double B[6][3], cons
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        double s = -B[a][r];
+        double s = -st_B(st, a, r);
 #pragma unroll
-        for (int b = 0; b < 6; ++b) s += W[r][b] * H[b][a];
+        for (int b = 0; b < 6; ++b) s += W[r][b] * st_H(st, b, a);
         G[r][a] = s;
       }
     double K[9];
@@ -599,34 +615,34 @@ __device__ inline void cam_scam(const double H[6][6], const double B[6][3], cons
 #pragma unroll
       for (int j = 0; j < 6; ++j) A[i][j] = 0.0;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) A[k][k] = 2.0 * H[5][5] + xi;
+    for (int k = 0; k < 3; ++k) A[k][k] = 2.0 * st_H(st, 5, 5) + xi;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        A[3 + m][k] = 2.0 * H[2 + m][5] * v[k];
+        A[3 + m][k] = 2.0 * st_H(st, 2 + m, 5) * v[k];
         A[k][3 + m] = A[3 + m][k];
       }
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int n = 0; n < 3; ++n) A[3 + m][3 + n] = 2.0 * H[2 + m][2 + n] + (m == n ? xi : 0.0);
+      for (int n = 0; n < 3; ++n) A[3 + m][3 + n] = 2.0 * st_H(st, 2 + m, 2 + n) + (m == n ? xi : 0.0);
     // top: dM0 H[:,5] + B[5,:];  bottom: H[2:5,:] (dM0^T v) + B[2:5,:] v
     double dv[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) dv[a] = dM0[a][0] * v[0] + dM0[a][1] * v[1] + dM0[a][2] * v[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double s = B[5][k];
+      double s = st_B(st, 5, k);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) s += dM0[a][k] * H[a][5];
+      for (int a = 0; a < 6; ++a) s += dM0[a][k] * st_H(st, a, 5);
       rhs[k] = -2.0 * s;
     }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      double s = B[2 + m][0] * v[0] + B[2 + m][1] * v[1] + B[2 + m][2] * v[2];
+      double s = st_B(st, 2 + m, 0) * v[0] + st_B(st, 2 + m, 1) * v[1] + st_B(st, 2 + m, 2) * v[2];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) s += H[2 + m][a] * dv[a];
+      for (int a = 0; a < 6; ++a) s += st_H(st, 2 + m, a) * dv[a];
       rhs[3 + m] = -2.0 * s;
     }
     if (chol6_solve(A, rhs)) {
@@ -639,19 +655,56 @@ __device__ inline void cam_scam(const double H[6][6], const double B[6][3], cons
   }
 }
 
-__device__ inline void unpack_stats(const double* s, double H[6][6], double B[6][3]) {
+// Exact FP32 -> FP64 widening with integer operations (IEEE-754 binary32 -> binary64:
+// exponent rebiased by 1023 - 127, mantissa shifted by 29); FP32 subnormals become signed
+// zero. Keeps the conversions of the camera solve off the FP64 unit.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  const unsigned long long ed = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
+  return __longlong_as_double((long long)(sgn | (ed << 52) | (e == 0u ? 0ull : m)));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// FP64 sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial
+template <class Real>
+__device__ __forceinline__ void sum_stats(const Real* __restrict__ part, int c0, int c1, int off, double* st);
+template <>
+__device__ __forceinline__ void sum_stats<float>(const float* __restrict__ part, int c0, int c1, int off, double* st) {
 #pragma unroll
-  for (int a = 0; a < 6; ++a)
+  for (int k = 0; k < 39; ++k) st[k] = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const float4* p = reinterpret_cast<const float4*>(part + (size_t)c * CP_STRIDE + off);
 #pragma unroll
-    for (int b = a; b < 6; ++b) H[a][b] = H[b][a] = s[tri6(a, b)];
+    for (int v = 0; v < 10; ++v) {
+      const float4 x = __ldg(p + v);
+      st[4 * v + 0] += widen(x.x);
+      st[4 * v + 1] += widen(x.y);
+      st[4 * v + 2] += widen(x.z);
+      if (v < 9) st[4 * v + 3] += widen(x.w);
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void sum_stats<double>(const double* __restrict__ part, int c0, int c1, int off,
+                                                  double* st) {
 #pragma unroll
-  for (int a = 0; a < 6; ++a)
+  for (int k = 0; k < 39; ++k) st[k] = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    const double2* p = reinterpret_cast<const double2*>(part + (size_t)c * CP_STRIDE + off);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) B[a][c] = s[21 + a * 3 + c];
+    for (int v = 0; v < 20; ++v) {
+      const double2 x = __ldg(p + v);
+      st[2 * v] += x.x;
+      if (v < 19) st[2 * v + 1] += x.y;
+    }
+  }
 }
 
 template <class Real>
-__global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
+__global__ void __launch_bounds__(CAMSOLVE_THREADS) k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
                            double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
                            IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
                            double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
@@ -661,20 +714,7 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const R
   const int it = *P.it;
   const double gamma = P.gam[it];
   const int first = *P.first;
-  double sb[39], sk[39];
-#pragma unroll
-  for (int k = 0; k < 39; ++k) sb[k] = sk[k] = 0.0;
-  double sF = 0.0, sG = 0.0;
-  for (int c = cam_chunk_ptr[i]; c < cam_chunk_ptr[i + 1]; ++c) {   // FP64 accumulation
-    const Real* p = part + (size_t)c * CP_STRIDE;
-#pragma unroll
-    for (int k = 0; k < 39; ++k) {
-      sb[k] += double(p[CP_HB + k]);
-      sk[k] += double(p[CP_H + k]);
-    }
-    sF += double(p[CP_F]);
-    sG += double(p[CP_G]);
-  }
+  const int c0 = cam_chunk_ptr[i], c1 = cam_chunk_ptr[i + 1];
   double* x = cam_x + (size_t)i * CSTRIDE;
   double* dx = cam_dx + (size_t)i * CSTRIDE;
   Cam ck, cb;
@@ -693,25 +733,33 @@ __global__ void k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const R
     cb.d[a] = ck.d[a] + gamma * dx[CS_D + a];
     dx2 += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
   }
+  // one statistics set is live at a time: the xbar set for the accelerated solve, then the
+  // x^k set for the restart test and the MM re-solve
+  double st[39];
+  Cam cn;
+  if (P.accelerated) {
+    sum_stats<Real>(part, c0, c1, PART_XB, st);
+    cam_scam(st, cb, P.xi, P.n_alt, cn);   // Eq. update_amm
+  }
+  sum_stats<Real>(part, c0, c1, PART_XK, st);
+  double sF = 0.0, sG = 0.0;
+  for (int c = c0; c < c1; ++c) {
+    sF += widen(part[(size_t)c * CP_STRIDE + PART_F]);
+    sG += widen(part[(size_t)c * CP_STRIDE + PART_G]);
+  }
   // Eq. DEalpha and the slack form of Eqs. Fak, lFak (see k_lpass)
   const double dE = -0.5 * P.xi * dx2 + 0.5 * sG;
   const double S = first ? 0.0 : cam_S[i];
   const double thr = (1.0 - P.eta) * (S - dE);
-  double Hk[6][6], Bk[6][3];
-  unpack_stats(sk, Hk, Bk);
-  Cam cn;
   double dEn = 0.0;
   bool rs = true;
   if (P.accelerated) {
-    double Hb[6][6], Bb[6][3];
-    unpack_stats(sb, Hb, Bb);
-    cam_scam(Hb, Bb, cb, P.xi, P.n_alt, cn);   // Eq. update_amm
-    dEn = cam_phi(Hk, Bk, ck, cn, P.xi);       // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
+    dEn = cam_phi(st, ck, cn, P.xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
     rs = dEn > thr;
   }
   if (rs) {
-    cam_scam(Hk, Bk, ck, P.xi, P.n_alt, cn);   // Eq. update_mm
-    dEn = cam_phi(Hk, Bk, ck, cn, P.xi);
+    cam_scam(st, ck, P.xi, P.n_alt, cn);   // Eq. update_mm
+    dEn = cam_phi(st, ck, cn, P.xi);
   }
   const double E = first ? 0.5 * sF : cam_E[i];
   const double F = E + dE;
