@@ -440,6 +440,82 @@ __device__ inline bool chol6_solve(double A[6][6], double b[6]) {
   return true;
 }
 
+// Exact FP32 -> FP64 widening with integer operations (IEEE-754 binary32 -> binary64:
+// exponent rebiased by 1023 - 127, mantissa shifted by 29); FP32 subnormals become signed
+// zero. Keeps the conversions of the camera solve off the FP64 unit.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
+  const unsigned long long ed = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
+  return __longlong_as_double((long long)(sgn | (ed << 52) | (e == 0u ? 0ull : m)));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+// FP64 -> FP32 conversions with integer operations on the IEEE-754 encodings (no FP64
+// instruction). narrow(d) = the float nearest to d (ties to even); split_df(d) also gives
+// lo = the float nearest to d - hi, so that hi + lo carries d to about 2^-48 relative.
+// Magnitudes below the FP32 normal range give signed zero, above it infinity; a low part
+// that would be subnormal is flushed to zero.
+__device__ __forceinline__ void split_df_impl(double d, float& hi, float& lo, bool want_lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sgn = (unsigned)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  lo = 0.f;
+  if (e < -126) {
+    hi = __uint_as_float(sgn);
+    return;
+  }
+  if (e > 127) {
+    hi = __uint_as_float(sgn | 0x7f800000u | ((e == 1024 && mant) ? 0x400000u : 0u));
+    return;
+  }
+  const unsigned long long sig = mant | (1ull << 52);   // 53-bit significand
+  unsigned long long q = sig >> 29;                     // 24 bits
+  const unsigned long long rem = sig & ((1ull << 29) - 1ull);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (q & 1ull))) q += 1ull;
+  const long long r = (long long)sig - (long long)(q << 29);   // |r| <= 2^28, units of 2^(e-52)
+  int eh = e;
+  if (q == (1ull << 24)) {
+    q >>= 1;
+    eh += 1;
+  }
+  if (eh > 127) {
+    hi = __uint_as_float(sgn | 0x7f800000u);
+    return;
+  }
+  hi = __uint_as_float(sgn | ((unsigned)(eh + 127) << 23) | (unsigned)(q & 0x7fffffull));
+  if (want_lo) {
+    const int es = e - 52;
+    if (es >= -126) {
+      const float l = (float)(int)r * __uint_as_float((unsigned)(es + 127) << 23);
+      lo = sgn ? -l : l;
+    }
+  }
+}
+__device__ __forceinline__ float narrow(double d) {
+  float h, l;
+  split_df_impl(d, h, l, false);
+  return h;
+}
+__device__ __forceinline__ void split_df(double d, float& hi, float& lo) { split_df_impl(d, hi, lo, true); }
+
+// d in the pass precision: FP32 via narrow, FP64 unchanged; split_real also gives the low
+// part (zero in FP64)
+template <class Real>
+__device__ __forceinline__ Real to_real(double d);
+template <>
+__device__ __forceinline__ float to_real<float>(double d) { return narrow(d); }
+template <>
+__device__ __forceinline__ double to_real<double>(double d) { return d; }
+__device__ __forceinline__ void split_real(double d, float& hi, float& lo) { split_df(d, hi, lo); }
+__device__ __forceinline__ void split_real(double d, double& hi, double& lo) {
+  hi = d;
+  lo = 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Boundary rotation parameterisation (host and device): axis-angle w <-> R.
 // ---------------------------------------------------------------------------

@@ -86,34 +86,33 @@ template <class Real>
 __device__ __forceinline__ void write_pack(const double* x, const double* dx, const double* Rb, V4<Real>* pk) {
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    const double t = x[CS_T + r];
-    const Real th = Real(t);
-    const Real tl = Real(t - double(th));
+    Real th, tl;
+    split_real(x[CS_T + r], th, tl);
     V4<Real> a, b, g;
-    a.x = Real(x[CS_R + 3 * r + 0]);
-    a.y = Real(x[CS_R + 3 * r + 1]);
-    a.z = Real(x[CS_R + 3 * r + 2]);
+    a.x = to_real<Real>(x[CS_R + 3 * r + 0]);
+    a.y = to_real<Real>(x[CS_R + 3 * r + 1]);
+    a.z = to_real<Real>(x[CS_R + 3 * r + 2]);
     a.w = th;
-    b.x = Real(Rb[3 * r + 0]);
-    b.y = Real(Rb[3 * r + 1]);
-    b.z = Real(Rb[3 * r + 2]);
-    b.w = Real(dx[CS_T + r]);
-    g.x = Real(dx[CS_R + 3 * r + 0]);
-    g.y = Real(dx[CS_R + 3 * r + 1]);
-    g.z = Real(dx[CS_R + 3 * r + 2]);
+    b.x = to_real<Real>(Rb[3 * r + 0]);
+    b.y = to_real<Real>(Rb[3 * r + 1]);
+    b.z = to_real<Real>(Rb[3 * r + 2]);
+    b.w = to_real<Real>(dx[CS_T + r]);
+    g.x = to_real<Real>(dx[CS_R + 3 * r + 0]);
+    g.y = to_real<Real>(dx[CS_R + 3 * r + 1]);
+    g.z = to_real<Real>(dx[CS_R + 3 * r + 2]);
     g.w = tl;
     pk[P4_RK + r] = a;
     pk[P4_RB + r] = b;
     pk[P4_DR + r] = g;
   }
   V4<Real> d, e;
-  d.x = Real(x[CS_D + 0]);
-  d.y = Real(x[CS_D + 1]);
-  d.z = Real(x[CS_D + 2]);
+  d.x = to_real<Real>(x[CS_D + 0]);
+  d.y = to_real<Real>(x[CS_D + 1]);
+  d.z = to_real<Real>(x[CS_D + 2]);
   d.w = Real(0);
-  e.x = Real(dx[CS_D + 0]);
-  e.y = Real(dx[CS_D + 1]);
-  e.z = Real(dx[CS_D + 2]);
+  e.x = to_real<Real>(dx[CS_D + 0]);
+  e.y = to_real<Real>(dx[CS_D + 1]);
+  e.z = to_real<Real>(dx[CS_D + 2]);
   e.w = Real(0);
   pk[P4_D] = d;
   pk[P4_DD] = e;
@@ -655,18 +654,6 @@ __device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n
   }
 }
 
-// Exact FP32 -> FP64 widening with integer operations (IEEE-754 binary32 -> binary64:
-// exponent rebiased by 1023 - 127, mantissa shifted by 29); FP32 subnormals become signed
-// zero. Keeps the conversions of the camera solve off the FP64 unit.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xffu;
-  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
-  const unsigned long long m = (unsigned long long)(u & 0x7fffffu) << 29;
-  const unsigned long long ed = e == 0u ? 0ull : (e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u));
-  return __longlong_as_double((long long)(sgn | (ed << 52) | (e == 0u ? 0ull : m)));
-}
-__device__ __forceinline__ double widen(double d) { return d; }
 
 // FP64 sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial
 template <class Real>

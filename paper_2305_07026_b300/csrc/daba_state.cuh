@@ -79,18 +79,19 @@ __global__ void k_set_lms(int N, const double* __restrict__ lms, const int* __re
   const size_t q = (size_t)linv[j];
   const double v0 = lms[(size_t)j * 3 + 0], v1 = lms[(size_t)j * 3 + 1], v2 = lms[(size_t)j * 3 + 2];
   V4<Real> A, Z;
-  A.x = Real(v0);
-  A.y = Real(v1);
-  A.z = Real(v2);
+  Real l0, l1, l2;
+  split_real(v0, A.x, l0);
+  split_real(v1, A.y, l1);
+  split_real(v2, A.z, l2);
   A.w = Real(0);
   Z.x = Z.y = Z.z = Z.w = Real(0);
   rec[2 * q] = A;
   rec[2 * q + 1] = Z;
   if (HAS_LO) {
     V4<float> L;
-    L.x = float(v0 - double(A.x));
-    L.y = float(v1 - double(A.y));
-    L.z = float(v2 - double(A.z));
+    L.x = float(l0);
+    L.y = float(l1);
+    L.z = float(l2);
     L.w = 0.f;
     lo[q] = L;
   }
@@ -136,6 +137,9 @@ __global__ void k_get_lms(int N, const V4<Real>* __restrict__ rec, const V4<floa
 
 // Assumption 2 on the current iterate: |l_j - t_i|^2 > 1e-24 max(1, |t_i|^2) for every
 // observation; one block per camera chunk, the smallest failing device position kept.
+// FP64 path: in FP64. MIXED: l and t as FP32 high + low parts and q = (l_hi - t_hi) +
+// (l_lo - t_lo) in FP32 (the high-part difference is exact when l is near t, so q keeps
+// about 2^-48 relative accuracy where the test matters), no FP64 instruction per observation.
 template <class Real, bool HAS_LO>
 __global__ void k_check_degenerate(const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
                                    const int* __restrict__ c_lm, const double* __restrict__ cam_x,
@@ -144,20 +148,21 @@ __global__ void k_check_degenerate(const int* __restrict__ chunk_cam, const int*
   const int cam = chunk_cam[blockIdx.x];
   const int b = chunk_beg[blockIdx.x], e = chunk_beg[blockIdx.x + 1];
   const double* x = cam_x + (size_t)cam * CSTRIDE;
-  const double t0 = x[CS_T + 0], t1 = x[CS_T + 1], t2 = x[CS_T + 2];
-  const double tt = t0 * t0 + t1 * t1 + t2 * t2;
-  const double thr = 1e-24 * (tt > 1.0 ? tt : 1.0);
+  Real th[3], tl[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) split_real(x[CS_T + a], th[a], tl[a]);
+  const Real tt = th[0] * th[0] + th[1] * th[1] + th[2] * th[2];
+  const Real thr = Real(1e-24) * (tt > Real(1) ? tt : Real(1));
   for (int o = b + threadIdx.x; o < e; o += blockDim.x) {
     const size_t j = (size_t)c_lm[o];
     const V4<Real> A = rec[2 * j];
-    double l0 = double(A.x), l1 = double(A.y), l2 = double(A.z);
+    Real q0 = A.x - th[0], q1 = A.y - th[1], q2 = A.z - th[2];
     if (HAS_LO) {
       const V4<float> L = lo[j];
-      l0 += double(L.x);
-      l1 += double(L.y);
-      l2 += double(L.z);
+      q0 += Real(L.x) - tl[0];
+      q1 += Real(L.y) - tl[1];
+      q2 += Real(L.z) - tl[2];
     }
-    const double q0 = l0 - t0, q1 = l1 - t1, q2 = l2 - t2;
     if (!(q0 * q0 + q1 * q1 + q2 * q2 > thr)) atomicMin(bad_obs, (unsigned long long)o);
   }
 }
