@@ -176,10 +176,11 @@ def algorithmic_bytes(sc, prec):
     """Bytes each pass must move at least once per launch (each datum once; see the design notes).
 
     cpass: per observation the landmark index, the pixel and the record position (4 + 2R + 4)
-           are read and the 10-value landmark-side record (10R) is written; each landmark's
-           position and displacement (6R) and each camera pack (48R) are read once; one partial
-           of 80 values (80R) is written per chunk of at most 1024 observations.
-    lpass: per observation the record (10R) and its slot (2) are read; per landmark its state
+           are read and the landmark-side record is written (rec = 8R + R in MIXED: the gap
+           only in its third part; 8R + 2R in FP64); each landmark's position and displacement
+           (6R) and each camera pack (48R) are read once; one partial of 84 values is written
+           per chunk of at most 1024 observations.
+    lpass: per observation the record (rec) and its slot (2) are read; per landmark its state
            record (8R, plus 16 B of low parts in MIXED) is read and written, its restart flag
            written and its CSR offset read (4).
     """
@@ -187,9 +188,10 @@ def algorithmic_bytes(sc, prec):
     nnz, N, M = sc.nnz, sc.N, sc.M
     deg = np.bincount(sc.cam_idx, minlength=M)
     n_chunks = int(np.sum((deg + 1023) // 1024))
-    cpass = nnz * (4 + 2 * R + 4 + 10 * R) + N * 6 * R + M * 48 * R + n_chunks * 80 * R
+    rec = 8 * R + (R if prec == "mixed" else 2 * R)
+    cpass = nnz * (4 + 2 * R + 4 + rec) + N * 6 * R + M * 48 * R + n_chunks * 84 * R
     lrec = 8 * R + (16 if prec == "mixed" else 0)
-    lpass = nnz * (10 * R + 2) + N * (2 * lrec + 1 + 4)
+    lpass = nnz * (rec + 2) + N * (2 * lrec + 1 + 4)
     return {"cpass": cpass, "lpass": lpass}
 
 

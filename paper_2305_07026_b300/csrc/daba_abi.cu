@@ -247,7 +247,7 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) 
         ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
         (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
         (Real*)ctx->chunk_part, (const int*)ctx->c_rpos, (V4<Real>*)ctx->rec_a, (V4<Real>*)ctx->rec_b,
-        (Real2*)ctx->rec_c);
+        (typename RecC<Real>::type*)ctx->rec_c);
   } else if (which == 6) {
     k_objective<LOSS, Real, Real2, HAS_LO><<<blocks, threads, 0, st>>>(
         ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
@@ -287,7 +287,7 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt, LPASS_THREADS, smem, st>>>(
           t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
-          (const Real2*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
+          (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
           (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
           (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
       ctx->launches++;

@@ -303,143 +303,6 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
   R[8] = w * w - x * x - y * y + z * z;
 }
 
-// ProjRot3D for det K > 0: the projection onto SO(3) is then the orthogonal polar factor of
-// K, computed with Higham's scaled Newton iteration X <- (z X + X^{-T} / z) / 2 with the
-// Frobenius-norm scaling z = sqrt(|X^{-1}| / |X|), switched off once the iteration is close.
-// Falls back to the Jacobi method above when det K <= 0 or the iteration does not settle.
-__device__ inline void proj_rot3d_polar(const double* __restrict__ K, double* __restrict__ R) {
-  double X[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) X[a] = K[a];
-  bool scaled = true;
-  for (int it = 0; it < 40; ++it) {
-    double C[9];   // cofactor matrix: X^{-T} = C / det X
-    C[0] = X[4] * X[8] - X[5] * X[7];
-    C[1] = X[5] * X[6] - X[3] * X[8];
-    C[2] = X[3] * X[7] - X[4] * X[6];
-    C[3] = X[2] * X[7] - X[1] * X[8];
-    C[4] = X[0] * X[8] - X[2] * X[6];
-    C[5] = X[1] * X[6] - X[0] * X[7];
-    C[6] = X[1] * X[5] - X[2] * X[4];
-    C[7] = X[2] * X[3] - X[0] * X[5];
-    C[8] = X[0] * X[4] - X[1] * X[3];
-    const double det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
-    if (!(det > 0.0)) break;
-    const double idet = 1.0 / det;
-    double z = 1.0;
-    if (scaled) {
-      double nx = 0.0, nc = 0.0;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        nx += X[a] * X[a];
-        nc += C[a] * C[a];
-      }
-      z = sqrt(sqrt(nc / nx) * idet);
-    }
-    const double hz = 0.5 * z, hiz = 0.5 * idet / z;
-    double dif = 0.0;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      const double y = hz * X[a] + hiz * C[a];
-      dif += (y - X[a]) * (y - X[a]);
-      X[a] = y;
-    }
-    if (dif < 1e-6) scaled = false;
-    if (dif < 1e-30) {
-#pragma unroll
-      for (int a = 0; a < 9; ++a) R[a] = X[a];
-      return;
-    }
-  }
-  proj_rot3d(K, R);
-}
-
-// ProjRot3D of a matrix K close to a rotation (the extrapolation R + gamma dR of
-// Eq. nesterov_R): for det K > 0 the projection is the orthogonal polar factor of K, reached
-// by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2, which converges quadratically when
-// |X^T X - I| < 1. Falls back to proj_rot3d when K is not close enough or det K <= 0.
-__device__ inline void proj_rot3d_near(const double* __restrict__ K, double* __restrict__ R) {
-  const double det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
-                     K[2] * (K[3] * K[7] - K[4] * K[6]);
-  double X[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) X[a] = K[a];
-  bool ok = det > 0.0;
-  for (int it = 0; it < 8 && ok; ++it) {
-    double S[9];   // X^T X
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) S[i * 3 + j] = X[0 * 3 + i] * X[0 * 3 + j] + X[1 * 3 + i] * X[1 * 3 + j] + X[2 * 3 + i] * X[2 * 3 + j];
-    double dev = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double dij = S[i * 3 + j] - (i == j ? 1.0 : 0.0);
-        dev += dij * dij;
-      }
-    if (it == 0 && !(dev < 0.25)) {
-      ok = false;
-      break;
-    }
-    if (dev < 1e-30) break;
-    double Y[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Y[i * 3 + j] = 0.5 * (3.0 * X[i * 3 + j] - (X[i * 3 + 0] * S[0 * 3 + j] + X[i * 3 + 1] * S[1 * 3 + j] + X[i * 3 + 2] * S[2 * 3 + j]));
-#pragma unroll
-    for (int a = 0; a < 9; ++a) X[a] = Y[a];
-    if (it == 7) ok = false;
-  }
-  if (ok) {
-#pragma unroll
-    for (int a = 0; a < 9; ++a) R[a] = X[a];
-  } else {
-    proj_rot3d(K, R);
-  }
-}
-
-// Solves the symmetric positive definite 6x6 system A x = b in place (A lower
-// triangle used, Cholesky A = L L^T; the diagonal keeps 1 / L[j][j]). Returns false if a
-// pivot is not positive.
-__device__ inline bool chol6_solve(double A[6][6], double b[6]) {
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    double djj = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) djj -= A[j][k] * A[j][k];
-    if (!(djj > 0.0)) return false;
-    const double inv = 1.0 / sqrt(djj);   // 1 / L[j][j]
-    A[j][j] = inv;
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      double s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s * inv;
-    }
-  }
-  // A[j][j] now holds 1 / L[j][j]
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double s = b[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) s -= A[i][k] * b[k];
-    b[i] = s * A[i][i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    double s = b[i];
-#pragma unroll
-    for (int k = i + 1; k < 6; ++k) s -= A[k][i] * b[k];
-    b[i] = s * A[i][i];
-  }
-  return true;
-}
-
 // Exact FP32 -> FP64 widening with integer operations (IEEE-754 binary32 -> binary64:
 // exponent rebiased by 1023 - 127, mantissa shifted by 29); FP32 subnormals become signed
 // zero. Keeps the conversions of the camera solve off the FP64 unit.
@@ -514,6 +377,185 @@ __device__ __forceinline__ void split_real(double d, float& hi, float& lo) { spl
 __device__ __forceinline__ void split_real(double d, double& hi, double& lo) {
   hi = d;
   lo = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Number type of the block solves. The solves are written over a number type T; Num<T>
+// supplies its constants, the scalar of the convergence tests, reciprocal square root and
+// reciprocal, and conversions. Both precisions solve in T = double.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Num;
+
+template <>
+struct Num<double> {
+  using S = double;
+  static __device__ __forceinline__ double c(float x) { return (double)x; }
+  static __device__ __forceinline__ S hi(double x) { return x; }
+  static __device__ __forceinline__ bool pos(double x) { return x > 0.0; }
+  static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double to_double(double x) { return x; }
+  // coefficients of the scaled Newton step X <- hz X + hiz C with C = det(X) X^{-T}
+  static __device__ __forceinline__ void newton(const double* X, const double* C, double det, bool scaled,
+                                                double& hz, double& hiz) {
+    const double idet = 1.0 / det;
+    double z = 1.0;
+    if (scaled) {
+      double nx = 0.0, nc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        nx += X[a] * X[a];
+        nc += C[a] * C[a];
+      }
+      z = sqrt(sqrt(nc / nx) * idet);
+    }
+    hz = 0.5 * z;
+    hiz = 0.5 * idet / z;
+  }
+};
+
+// ProjRot3D for det K > 0: the projection onto SO(3) is then the orthogonal polar factor of
+// K, computed with Higham's scaled Newton iteration X <- (z X + X^{-T} / z) / 2 with the
+// Frobenius-norm scaling z = sqrt(|X^{-1}| / |X|), switched off once the iteration is close.
+// The iteration converges quadratically, so once a step changes X by less than 1e-10 the new
+// X is the polar factor to about 1e-20. Falls back to the Jacobi method above when det K <= 0
+// or the iteration does not settle.
+template <class T>
+__device__ inline void proj_rot3d_polar(const T* __restrict__ K, T* __restrict__ R) {
+  using N = Num<T>;
+  using S = typename N::S;
+  T X[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) X[a] = K[a];
+  bool scaled = true;
+  for (int it = 0; it < 40; ++it) {
+    T C[9];   // cofactor matrix: X^{-T} = C / det X
+    C[0] = X[4] * X[8] - X[5] * X[7];
+    C[1] = X[5] * X[6] - X[3] * X[8];
+    C[2] = X[3] * X[7] - X[4] * X[6];
+    C[3] = X[2] * X[7] - X[1] * X[8];
+    C[4] = X[0] * X[8] - X[2] * X[6];
+    C[5] = X[1] * X[6] - X[0] * X[7];
+    C[6] = X[1] * X[5] - X[2] * X[4];
+    C[7] = X[2] * X[3] - X[0] * X[5];
+    C[8] = X[0] * X[4] - X[1] * X[3];
+    const T det = X[0] * C[0] + X[1] * C[1] + X[2] * C[2];
+    if (!N::pos(det)) break;
+    T hz, hiz;
+    N::newton(X, C, det, scaled, hz, hiz);
+    S dif = S(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      const T y = hz * X[a] + hiz * C[a];
+      const S d = N::hi(y - X[a]);
+      dif += d * d;
+      X[a] = y;
+    }
+    if (dif < S(1e-6)) scaled = false;
+    if (dif < S(1e-20)) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) R[a] = X[a];
+      return;
+    }
+  }
+  proj_rot3d(K, R);
+}
+
+// ProjRot3D of a matrix K close to a rotation (the extrapolation R + gamma dR of
+// Eq. nesterov_R): for det K > 0 the projection is the orthogonal polar factor of K, reached
+// by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2, which converges quadratically when
+// |X^T X - I| < 1: once |X^T X - I|_F^2 < 1e-20 one more step reaches the polar factor.
+// Falls back to proj_rot3d when K is not close enough or det K <= 0.
+template <class T>
+__device__ inline void proj_rot3d_near(const T* __restrict__ K, T* __restrict__ R) {
+  using N = Num<T>;
+  using S = typename N::S;
+  const T det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
+                K[2] * (K[3] * K[7] - K[4] * K[6]);
+  T X[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) X[a] = K[a];
+  bool ok = N::pos(det);
+  for (int it = 0; it < 8 && ok; ++it) {
+    T Sm[9];   // X^T X
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Sm[i * 3 + j] = X[0 * 3 + i] * X[0 * 3 + j] + X[1 * 3 + i] * X[1 * 3 + j] + X[2 * 3 + i] * X[2 * 3 + j];
+    S dev = S(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const S dij = N::hi(i == j ? Sm[i * 3 + j] - N::c(1.0f) : Sm[i * 3 + j]);
+        dev += dij * dij;
+      }
+    if (it == 0 && !(dev < S(0.25))) {
+      ok = false;
+      break;
+    }
+    T Y[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Y[i * 3 + j] = N::c(0.5f) * (N::c(3.0f) * X[i * 3 + j] -
+                                     (X[i * 3 + 0] * Sm[0 * 3 + j] + X[i * 3 + 1] * Sm[1 * 3 + j] +
+                                      X[i * 3 + 2] * Sm[2 * 3 + j]));
+#pragma unroll
+    for (int a = 0; a < 9; ++a) X[a] = Y[a];
+    if (dev < S(1e-20)) break;
+    if (it == 7) ok = false;
+  }
+  if (ok) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) R[a] = X[a];
+  } else {
+    proj_rot3d(K, R);
+  }
+}
+
+// Solves the symmetric positive definite 6x6 system A x = b in place (A lower
+// triangle used, Cholesky A = L L^T; the diagonal keeps 1 / L[j][j]). Returns false if a
+// pivot is not positive.
+template <class T>
+__device__ inline bool chol6_solve(T A[6][6], T b[6]) {
+  using N = Num<T>;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    T djj = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) djj = djj - A[j][k] * A[j][k];
+    if (!N::pos(djj)) return false;
+    const T inv = N::rsqrt(djj);   // 1 / L[j][j]
+    A[j][j] = inv;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      T s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s = s - A[i][k] * A[j][k];
+      A[i][j] = s * inv;
+    }
+  }
+  // A[j][j] now holds 1 / L[j][j]
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T s = b[i];
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = s - A[i][k] * b[k];
+    b[i] = s * A[i][i];
+  }
+#pragma unroll
+  for (int i = 5; i >= 0; --i) {
+    T s = b[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; ++k) s = s - A[k][i] * b[k];
+    b[i] = s * A[i][i];
+  }
+  return true;
 }
 
 // ---------------------------------------------------------------------------

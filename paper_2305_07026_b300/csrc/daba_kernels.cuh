@@ -199,6 +199,25 @@ __device__ __forceinline__ void cp_async_wait() {
 
 constexpr int CPASS_STAGES = 4;   // batches of 32 observations in flight per warp
 
+// Third landmark-side record of an observation: FP64 path (F_ij(x^k), surrogate gap); MIXED
+// the gap only (F_ij only enters the FP64 path's per-landmark diagnostics).
+template <class Real>
+struct RecC;
+template <>
+struct RecC<float> {
+  using type = float;
+  static __device__ __forceinline__ float make(float, float gap) { return gap; }
+  static __device__ __forceinline__ float F(float) { return 0.f; }
+  static __device__ __forceinline__ float gap(float c) { return c; }
+};
+template <>
+struct RecC<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 make(double f, double gap) { return make_double2(f, gap); }
+  static __device__ __forceinline__ double F(double2 c) { return c.x; }
+  static __device__ __forceinline__ double gap(double2 c) { return c.y; }
+};
+
 // Per lane and stage: the landmark record (two V4), the pixel and the record position.
 template <class Real, class Real2>
 struct CpassStage {
@@ -211,14 +230,14 @@ struct CpassStage {
 // tiles' processing order (so that the landmark pass streams the records sequentially):
 //   rec_a = (wb lamb^2, -wb lamb (Rbar ebar) / 2)   terms of sum_i Q_ij(l | xbar^k)
 //   rec_b = (w lam^2, -w lam (R e) / 2)             terms of sum_i Q_ij(l | x^k)
-//   rec_c = (F_ij(x^k), surrogate gap)
+//   rec_c = (F_ij(x^k), surrogate gap), MIXED the gap only (RecC)
 template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
     k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
             const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
             const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
             const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b,
-            Real2* __restrict__ rec_c) {
+            typename RecC<Real>::type* __restrict__ rec_c) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
   __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
   const int wib = threadIdx.x >> 5;
@@ -285,13 +304,10 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       rb.y = Real(-0.5) * wl * ev.Re0;
       rb.z = Real(-0.5) * wl * ev.Re1;
       rb.w = Real(-0.5) * wl * ev.Re2;
-      Real2 rc;
-      rc.x = Real(0.5) * ev.rho;
-      rc.y = ev.gap;
       const int rp = d.rpos;
       rec_a[rp] = ra;
       rec_b[rp] = rb;
-      rec_c[rp] = rc;
+      rec_c[rp] = RecC<Real>::make(Real(0.5) * ev.rho, ev.gap);
     }
   }
   cp_async_wait<0>();
@@ -320,10 +336,11 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // where cpass stored them in camera-sorted order; t_slot maps a record position to its
 // landmark-sorted slot relative to the tile start. Reads the landmark state of iteration k
 // and writes that of k+1 to the other buffer.
-// Shared memory: three V4 arrays indexed by slot: (terms at xbar), (terms at x^k), (F, gap).
+// Shared memory, indexed by slot: two V4 arrays (terms at xbar), (terms at x^k) and the
+// third record (RecC).
 template <class Real>
 __host__ __device__ inline size_t lpass_smem_bytes(int no_cap) {
-  return (size_t)no_cap * 3 * sizeof(V4<Real>) + 16;
+  return (size_t)no_cap * (2 * sizeof(V4<Real>) + (sizeof(Real) == 4 ? 4 : 16)) + 16;
 }
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
@@ -341,7 +358,8 @@ template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
             const uint16_t* __restrict__ t_slot, const V4<Real>* __restrict__ rec_a,
-            const V4<Real>* __restrict__ rec_b, const Real2* __restrict__ rec_c, const V4<Real>* __restrict__ lmrec,
+            const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
+            const V4<Real>* __restrict__ lmrec,
             const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out,
             IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
             double* __restrict__ lm_Fbdiag) {
@@ -351,9 +369,10 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  V4<Real>* sca = reinterpret_cast<V4<Real>*>(smem_raw);   // three V4 arrays of no_cap, by slot
+  using RC = typename RecC<Real>::type;
+  V4<Real>* sca = reinterpret_cast<V4<Real>*>(smem_raw);   // arrays of no_cap entries, by slot
   V4<Real>* scb = sca + no_cap;
-  V4<Real>* scc = scb + no_cap;
+  RC* scc = reinterpret_cast<RC*>(scb + no_cap);
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
   // the landmark state of this thread's landmark (at most one: nl <= blockDim.x) is loaded
@@ -374,7 +393,7 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   for (int o0 = 0; o0 < no; o0 += LPASS_THREADS * LPASS_UNROLL) {
     int pos[LPASS_UNROLL], slot[LPASS_UNROLL];
     V4<Real> ra[LPASS_UNROLL], rb[LPASS_UNROLL];
-    Real2 rc[LPASS_UNROLL];
+    RC rc[LPASS_UNROLL];
 #pragma unroll
     for (int u = 0; u < LPASS_UNROLL; ++u) {
       const int o = o0 + u * LPASS_THREADS + threadIdx.x;
@@ -391,14 +410,9 @@ __global__ void __launch_bounds__(LPASS_THREADS)
 #pragma unroll
     for (int u = 0; u < LPASS_UNROLL; ++u)
       if (pos[u] >= 0) {
-        V4<Real> c;
-        c.x = rc[u].x;
-        c.y = rc[u].y;
-        c.z = Real(0);
-        c.w = Real(0);
         sca[slot[u]] = ra[u];
         scb[slot[u]] = rb[u];
-        scc[slot[u]] = c;
+        scc[slot[u]] = rc[u];
       }
   }
   __syncthreads();
@@ -411,7 +425,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
 #pragma unroll
     for (int k = 0; k < 10; ++k) st[k] = Real(0);
     for (int s = s0; s < s1; ++s) {
-      const V4<Real> a = sca[s], b = scb[s], c = scc[s];
+      const V4<Real> a = sca[s], b = scb[s];
+      const RC c = scc[s];
       st[0] += a.x;
       st[1] += a.y;
       st[2] += a.z;
@@ -420,8 +435,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       st[5] += b.y;
       st[6] += b.z;
       st[7] += b.w;
-      st[8] += c.x;
-      st[9] += c.y;
+      st[8] += RecC<Real>::F(c);
+      st[9] += RecC<Real>::gap(c);
     }
     const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
     // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
@@ -498,18 +513,20 @@ __global__ void __launch_bounds__(LPASS_THREADS)
 // ---------------------------------------------------------------------------
 // 3. camera block solves (FP64)
 // ---------------------------------------------------------------------------
-struct Cam {
-  double R[9], t[3], d[3];
+template <class T>
+struct CamT {
+  T R[9], t[3], d[3];
 };
 
 // M(c) column a (a = 0..5) of the 3x6 matrix [R e1, R e2, d1 R e3, d2 R e3, d3 R e3, t].
-__device__ __forceinline__ void mcol(const Cam& c, int a, double out[3]) {
+template <class T>
+__device__ __forceinline__ void mcol(const CamT<T>& c, int a, T out[3]) {
   if (a < 2) {
     out[0] = c.R[0 + a];
     out[1] = c.R[3 + a];
     out[2] = c.R[6 + a];
   } else if (a < 5) {
-    const double dk = c.d[a - 2];
+    const T dk = c.d[a - 2];
     out[0] = dk * c.R[2];
     out[1] = dk * c.R[5];
     out[2] = dk * c.R[8];
@@ -521,37 +538,41 @@ __device__ __forceinline__ void mcol(const Cam& c, int a, double out[3]) {
 }
 
 // Packed camera statistics: H (upper triangle, row-major, 21 values) then B (6x3, 18 values).
-__device__ __forceinline__ double st_H(const double* s, int a, int b) { return a <= b ? s[tri6(a, b)] : s[tri6(b, a)]; }
-__device__ __forceinline__ double st_B(const double* s, int a, int c) { return s[21 + a * 3 + c]; }
+template <class T>
+__device__ __forceinline__ T st_H(const T* s, int a, int b) { return a <= b ? s[tri6(a, b)] : s[tri6(b, a)]; }
+template <class T>
+__device__ __forceinline__ T st_B(const T* s, int a, int c) { return s[21 + a * 3 + c]; }
 
 // E^alpha(c | z) - E^alpha(c_z | z) = xi/2 |c - c_z|^2 + tr(dM H dM^T) + 2 tr(dM B).
-__device__ inline double cam_phi(const double* st, const Cam& z, const Cam& c, double xi) {
-  double dM[6][3];
+template <class T>
+__device__ inline T cam_phi(const T* st, const CamT<T>& z, const CamT<T>& c, T xi) {
+  using N = Num<T>;
+  T dM[6][3];
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    double mc[3], mz[3];
+    T mc[3], mz[3];
     mcol(c, a, mc);
     mcol(z, a, mz);
     dM[a][0] = mc[0] - mz[0];
     dM[a][1] = mc[1] - mz[1];
     dM[a][2] = mc[2] - mz[2];
   }
-  double prox = 0.0;
+  T prox = N::c(0.f);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) prox += (c.R[k] - z.R[k]) * (c.R[k] - z.R[k]);
+  for (int k = 0; k < 9; ++k) prox = prox + (c.R[k] - z.R[k]) * (c.R[k] - z.R[k]);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    prox += (c.t[k] - z.t[k]) * (c.t[k] - z.t[k]) + (c.d[k] - z.d[k]) * (c.d[k] - z.d[k]);
-  double q = 0.0, lin = 0.0;
+    prox = prox + (c.t[k] - z.t[k]) * (c.t[k] - z.t[k]) + (c.d[k] - z.d[k]) * (c.d[k] - z.d[k]);
+  T q = N::c(0.f), lin = N::c(0.f);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    q += st_H(st, a, a) * (dM[a][0] * dM[a][0] + dM[a][1] * dM[a][1] + dM[a][2] * dM[a][2]);
+    q = q + st_H(st, a, a) * (dM[a][0] * dM[a][0] + dM[a][1] * dM[a][1] + dM[a][2] * dM[a][2]);
 #pragma unroll
     for (int b = a + 1; b < 6; ++b)
-      q += 2.0 * st_H(st, a, b) * (dM[a][0] * dM[b][0] + dM[a][1] * dM[b][1] + dM[a][2] * dM[b][2]);
-    lin += dM[a][0] * st_B(st, a, 0) + dM[a][1] * st_B(st, a, 1) + dM[a][2] * st_B(st, a, 2);
+      q = q + N::c(2.0f) * st_H(st, a, b) * (dM[a][0] * dM[b][0] + dM[a][1] * dM[b][1] + dM[a][2] * dM[b][2]);
+    lin = lin + dM[a][0] * st_B(st, a, 0) + dM[a][1] * st_B(st, a, 1) + dM[a][2] * st_B(st, a, 2);
   }
-  return 0.5 * xi * prox + q + 2.0 * lin;
+  return N::c(0.5f) * xi * prox + q + N::c(2.0f) * lin;
 }
 
 // Block-exact alternation on E^alpha(. | z) started at c_z (z supplies H, B).
@@ -561,14 +582,16 @@ __device__ inline double cam_phi(const double* st, const Cam& z, const Cam& c, d
 // (t, d)-step: with R fixed, dM h = dM0 h + v (phi . dd) + lambda dt with v = R e3 and
 //   dM0 = M(R, t_z, d_z) - M(c_z); the normal equations of the resulting least squares
 //   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5] and are solved by Cholesky.
-__device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n_alt, Cam& c) {
+template <class T>
+__device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, CamT<T>& c) {
+  using N = Num<T>;
   c = z;
   for (int it = 0; it < n_alt; ++it) {
     // ---- R-step
-    double W[3][6];
+    T W[3][6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-      double mz[3];
+      T mz[3];
       mcol(z, a, mz);
       W[0][a] = mz[0];
       W[1][a] = mz[1];
@@ -577,28 +600,28 @@ __device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n
     W[0][5] = z.t[0] - c.t[0];
     W[1][5] = z.t[1] - c.t[1];
     W[2][5] = z.t[2] - c.t[2];
-    double G[3][6];
+    T G[3][6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int a = 0; a < 6; ++a) {
-        double s = -st_B(st, a, r);
+        T s = -st_B(st, a, r);
 #pragma unroll
-        for (int b = 0; b < 6; ++b) s += W[r][b] * st_H(st, b, a);
+        for (int b = 0; b < 6; ++b) s = s + W[r][b] * st_H(st, b, a);
         G[r][a] = s;
       }
-    double K[9];
+    T K[9];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      K[r * 3 + 0] = xi * z.R[r * 3 + 0] + 2.0 * G[r][0];
-      K[r * 3 + 1] = xi * z.R[r * 3 + 1] + 2.0 * G[r][1];
-      K[r * 3 + 2] = xi * z.R[r * 3 + 2] + 2.0 * (c.d[0] * G[r][2] + c.d[1] * G[r][3] + c.d[2] * G[r][4]);
+      K[r * 3 + 0] = xi * z.R[r * 3 + 0] + N::c(2.0f) * G[r][0];
+      K[r * 3 + 1] = xi * z.R[r * 3 + 1] + N::c(2.0f) * G[r][1];
+      K[r * 3 + 2] = xi * z.R[r * 3 + 2] + N::c(2.0f) * (c.d[0] * G[r][2] + c.d[1] * G[r][3] + c.d[2] * G[r][4]);
     }
     proj_rot3d_polar(K, c.R);
     // ---- (t, d)-step
-    const double v[3] = {c.R[2], c.R[5], c.R[8]};
-    const double vz[3] = {z.R[2], z.R[5], z.R[8]};
-    double dM0[6][3];
+    const T v[3] = {c.R[2], c.R[5], c.R[8]};
+    const T vz[3] = {z.R[2], z.R[5], z.R[8]};
+    T dM0[6][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       dM0[0][k] = c.R[k * 3 + 0] - z.R[k * 3 + 0];
@@ -606,43 +629,44 @@ __device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n
       dM0[2][k] = z.d[0] * (v[k] - vz[k]);
       dM0[3][k] = z.d[1] * (v[k] - vz[k]);
       dM0[4][k] = z.d[2] * (v[k] - vz[k]);
-      dM0[5][k] = 0.0;
+      dM0[5][k] = N::c(0.f);
     }
-    double A[6][6], rhs[6];
+    T A[6][6], rhs[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-      for (int j = 0; j < 6; ++j) A[i][j] = 0.0;
+      for (int j = 0; j < 6; ++j) A[i][j] = N::c(0.f);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) A[k][k] = 2.0 * st_H(st, 5, 5) + xi;
+    for (int k = 0; k < 3; ++k) A[k][k] = N::c(2.0f) * st_H(st, 5, 5) + xi;
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        A[3 + m][k] = 2.0 * st_H(st, 2 + m, 5) * v[k];
+        A[3 + m][k] = N::c(2.0f) * st_H(st, 2 + m, 5) * v[k];
         A[k][3 + m] = A[3 + m][k];
       }
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int n = 0; n < 3; ++n) A[3 + m][3 + n] = 2.0 * st_H(st, 2 + m, 2 + n) + (m == n ? xi : 0.0);
+      for (int n = 0; n < 3; ++n)
+        A[3 + m][3 + n] = m == n ? N::c(2.0f) * st_H(st, 2 + m, 2 + n) + xi : N::c(2.0f) * st_H(st, 2 + m, 2 + n);
     // top: dM0 H[:,5] + B[5,:];  bottom: H[2:5,:] (dM0^T v) + B[2:5,:] v
-    double dv[6];
+    T dv[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) dv[a] = dM0[a][0] * v[0] + dM0[a][1] * v[1] + dM0[a][2] * v[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      double s = st_B(st, 5, k);
+      T s = st_B(st, 5, k);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) s += dM0[a][k] * st_H(st, a, 5);
-      rhs[k] = -2.0 * s;
+      for (int a = 0; a < 6; ++a) s = s + dM0[a][k] * st_H(st, a, 5);
+      rhs[k] = N::c(-2.0f) * s;
     }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      double s = st_B(st, 2 + m, 0) * v[0] + st_B(st, 2 + m, 1) * v[1] + st_B(st, 2 + m, 2) * v[2];
+      T s = st_B(st, 2 + m, 0) * v[0] + st_B(st, 2 + m, 1) * v[1] + st_B(st, 2 + m, 2) * v[2];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) s += st_H(st, 2 + m, a) * dv[a];
-      rhs[3 + m] = -2.0 * s;
+      for (int a = 0; a < 6; ++a) s = s + st_H(st, 2 + m, a) * dv[a];
+      rhs[3 + m] = N::c(-2.0f) * s;
     }
     if (chol6_solve(A, rhs)) {
 #pragma unroll
@@ -654,12 +678,15 @@ __device__ inline void cam_scam(const double* st, const Cam& z, double xi, int n
   }
 }
 
+__device__ __forceinline__ void acc_add(double& a, float x) { a += widen(x); }
+__device__ __forceinline__ void acc_add(double& a, double x) { a += x; }
 
-// FP64 sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial
-template <class Real>
-__device__ __forceinline__ void sum_stats(const Real* __restrict__ part, int c0, int c1, int off, double* st);
+// Sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial
+template <class Real, class T>
+__device__ __forceinline__ void sum_stats(const Real* __restrict__ part, int c0, int c1, int off, T* st);
 template <>
-__device__ __forceinline__ void sum_stats<float>(const float* __restrict__ part, int c0, int c1, int off, double* st) {
+__device__ __forceinline__ void sum_stats<float, double>(const float* __restrict__ part, int c0, int c1, int off,
+                                                         double* st) {
 #pragma unroll
   for (int k = 0; k < 39; ++k) st[k] = 0.0;
   for (int c = c0; c < c1; ++c) {
@@ -667,16 +694,16 @@ __device__ __forceinline__ void sum_stats<float>(const float* __restrict__ part,
 #pragma unroll
     for (int v = 0; v < 10; ++v) {
       const float4 x = __ldg(p + v);
-      st[4 * v + 0] += widen(x.x);
-      st[4 * v + 1] += widen(x.y);
-      st[4 * v + 2] += widen(x.z);
-      if (v < 9) st[4 * v + 3] += widen(x.w);
+      acc_add(st[4 * v + 0], x.x);
+      acc_add(st[4 * v + 1], x.y);
+      acc_add(st[4 * v + 2], x.z);
+      if (v < 9) acc_add(st[4 * v + 3], x.w);
     }
   }
 }
 template <>
-__device__ __forceinline__ void sum_stats<double>(const double* __restrict__ part, int c0, int c1, int off,
-                                                  double* st) {
+__device__ __forceinline__ void sum_stats<double, double>(const double* __restrict__ part, int c0, int c1, int off,
+                                                          double* st) {
 #pragma unroll
   for (int k = 0; k < 39; ++k) st[k] = 0.0;
   for (int c = c0; c < c1; ++c) {
@@ -690,99 +717,149 @@ __device__ __forceinline__ void sum_stats<double>(const double* __restrict__ par
   }
 }
 
+// pass pack from the FP64 solve results (FP32: nearest floats, the camera centre as high and
+// low parts)
 template <class Real>
-__global__ void __launch_bounds__(CAMSOLVE_THREADS) k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
-                           double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
-                           IterParams P, double* __restrict__ cam_S, double* __restrict__ cam_E,
-                           double* __restrict__ cam_F, double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
-                           double* __restrict__ cam_Fsum, V4<Real>* __restrict__ pack_next) {
+__device__ __forceinline__ void write_pack_t(const CamT<double>& x, const CamT<double>& dx, const double* Rb,
+                                             V4<Real>* pk) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Real th, tl;
+    split_real(x.t[r], th, tl);
+    V4<Real> a, b, g;
+    a.x = to_real<Real>(x.R[3 * r + 0]);
+    a.y = to_real<Real>(x.R[3 * r + 1]);
+    a.z = to_real<Real>(x.R[3 * r + 2]);
+    a.w = th;
+    b.x = to_real<Real>(Rb[3 * r + 0]);
+    b.y = to_real<Real>(Rb[3 * r + 1]);
+    b.z = to_real<Real>(Rb[3 * r + 2]);
+    b.w = to_real<Real>(dx.t[r]);
+    g.x = to_real<Real>(dx.R[3 * r + 0]);
+    g.y = to_real<Real>(dx.R[3 * r + 1]);
+    g.z = to_real<Real>(dx.R[3 * r + 2]);
+    g.w = tl;
+    pk[P4_RK + r] = a;
+    pk[P4_RB + r] = b;
+    pk[P4_DR + r] = g;
+  }
+  V4<Real> d, e;
+  d.x = to_real<Real>(x.d[0]);
+  d.y = to_real<Real>(x.d[1]);
+  d.z = to_real<Real>(x.d[2]);
+  d.w = Real(0);
+  e.x = to_real<Real>(dx.d[0]);
+  e.y = to_real<Real>(dx.d[1]);
+  e.z = to_real<Real>(dx.d[2]);
+  e.w = Real(0);
+  pk[P4_D] = d;
+  pk[P4_DD] = e;
+}
+
+// One thread per camera, in FP64: the statistics summed over the camera's chunks, the
+// accelerated S-CAM solve, the restart metrics and test, the MM re-solve, and the
+// extrapolated rotation and pack of iteration k+1.
+template <class Real>
+__global__ void __launch_bounds__(CAMSOLVE_THREADS)
+    k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
+               double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
+               double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
+               double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs, double* __restrict__ cam_Fsum,
+               V4<Real>* __restrict__ pack_next) {
+  using T = double;
+  using N = Num<T>;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const int it = *P.it;
-  const double gamma = P.gam[it];
+  const T gamma = N::from(P.gam[it]);
   const int first = *P.first;
   const int c0 = cam_chunk_ptr[i], c1 = cam_chunk_ptr[i + 1];
   double* x = cam_x + (size_t)i * CSTRIDE;
   double* dx = cam_dx + (size_t)i * CSTRIDE;
-  Cam ck, cb;
-  double dx2 = 0.0;
+  CamT<T> ck, cb;
+  T dx2 = N::c(0.f);
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    ck.R[a] = x[CS_R + a];
-    cb.R[a] = cam_Rbar[(size_t)i * 9 + a];
-    dx2 += dx[CS_R + a] * dx[CS_R + a];
+    ck.R[a] = N::from(x[CS_R + a]);
+    cb.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
+    const T d = N::from(dx[CS_R + a]);
+    dx2 = dx2 + d * d;
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    ck.t[a] = x[CS_T + a];
-    ck.d[a] = x[CS_D + a];
-    cb.t[a] = ck.t[a] + gamma * dx[CS_T + a];
-    cb.d[a] = ck.d[a] + gamma * dx[CS_D + a];
-    dx2 += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
+    ck.t[a] = N::from(x[CS_T + a]);
+    ck.d[a] = N::from(x[CS_D + a]);
+    const T dt = N::from(dx[CS_T + a]), dd = N::from(dx[CS_D + a]);
+    cb.t[a] = ck.t[a] + gamma * dt;
+    cb.d[a] = ck.d[a] + gamma * dd;
+    dx2 = dx2 + dt * dt + dd * dd;
   }
+  const T xi = N::from(P.xi);
   // one statistics set is live at a time: the xbar set for the accelerated solve, then the
   // x^k set for the restart test and the MM re-solve
-  double st[39];
-  Cam cn;
+  T st[39];
+  CamT<T> cn;
   if (P.accelerated) {
-    sum_stats<Real>(part, c0, c1, PART_XB, st);
-    cam_scam(st, cb, P.xi, P.n_alt, cn);   // Eq. update_amm
+    sum_stats<Real, T>(part, c0, c1, PART_XB, st);
+    cam_scam(st, cb, xi, P.n_alt, cn);   // Eq. update_amm
   }
-  sum_stats<Real>(part, c0, c1, PART_XK, st);
-  double sF = 0.0, sG = 0.0;
+  sum_stats<Real, T>(part, c0, c1, PART_XK, st);
+  T sF = N::c(0.f), sG = N::c(0.f);
   for (int c = c0; c < c1; ++c) {
-    sF += widen(part[(size_t)c * CP_STRIDE + PART_F]);
-    sG += widen(part[(size_t)c * CP_STRIDE + PART_G]);
+    acc_add(sF, part[(size_t)c * CP_STRIDE + PART_F]);
+    acc_add(sG, part[(size_t)c * CP_STRIDE + PART_G]);
   }
   // Eq. DEalpha and the slack form of Eqs. Fak, lFak (see k_lpass)
-  const double dE = -0.5 * P.xi * dx2 + 0.5 * sG;
-  const double S = first ? 0.0 : cam_S[i];
-  const double thr = (1.0 - P.eta) * (S - dE);
-  double dEn = 0.0;
+  const T dE = N::c(-0.5f) * xi * dx2 + N::c(0.5f) * sG;
+  const T S = first ? N::c(0.f) : N::from(cam_S[i]);
+  const T thr = N::from(P.eta1) * (S - dE);
+  T dEn = N::c(0.f);
   bool rs = true;
   if (P.accelerated) {
-    dEn = cam_phi(st, ck, cn, P.xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
+    dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
     rs = dEn > thr;
   }
   if (rs) {
-    cam_scam(st, ck, P.xi, P.n_alt, cn);   // Eq. update_mm
-    dEn = cam_phi(st, ck, cn, P.xi);
+    cam_scam(st, ck, xi, P.n_alt, cn);   // Eq. update_mm
+    dEn = cam_phi(st, ck, cn, xi);
   }
-  const double E = first ? 0.5 * sF : cam_E[i];
-  const double F = E + dE;
-  cam_Fsum[i] = sF;   // sum of F_ij(x^k) over the camera's observations (objective trace)
-  cam_F[i] = F;
-  cam_Fb[i] = F + thr;
-  cam_E[i] = F + dEn;
-  cam_S[i] = thr - dEn;
+  const T E = first ? N::c(0.5f) * sF : N::from(cam_E[i]);
+  const T F = E + dE;
+  cam_Fsum[i] = N::to_double(sF);   // sum of F_ij(x^k) over the camera's observations (objective trace)
+  cam_F[i] = N::to_double(F);
+  cam_Fb[i] = N::to_double(F + thr);
+  cam_E[i] = N::to_double(F + dEn);
+  cam_S[i] = N::to_double(thr - dEn);
   cam_rs[i] = (rs && P.accelerated) ? 1 : 0;
-  double nx[CSTRIDE], ndx[CSTRIDE];
+  CamT<T> ndx;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) ndx.R[a] = cn.R[a] - ck.R[a];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ndx.t[a] = cn.t[a] - ck.t[a];
+    ndx.d[a] = cn.d[a] - ck.d[a];
+  }
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    ndx[CS_R + a] = cn.R[a] - ck.R[a];
-    nx[CS_R + a] = cn.R[a];
+    x[CS_R + a] = N::to_double(cn.R[a]);
+    dx[CS_R + a] = N::to_double(ndx.R[a]);
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    ndx[CS_T + a] = cn.t[a] - ck.t[a];
-    ndx[CS_D + a] = cn.d[a] - ck.d[a];
-    nx[CS_T + a] = cn.t[a];
-    nx[CS_D + a] = cn.d[a];
-  }
-#pragma unroll
-  for (int a = 0; a < 15; ++a) {
-    x[a] = nx[a];
-    dx[a] = ndx[a];
+    x[CS_T + a] = N::to_double(cn.t[a]);
+    dx[CS_T + a] = N::to_double(ndx.t[a]);
+    x[CS_D + a] = N::to_double(cn.d[a]);
+    dx[CS_D + a] = N::to_double(ndx.d[a]);
   }
   // extrapolation of iteration k+1 (Eq. nesterov_R) and its pass pack
-  const double gn = P.gam[it + 1];
-  double K[9], Rb[9];
+  const T gn = N::from(P.gam[it + 1]);
+  T K[9], Rb[9];
 #pragma unroll
-  for (int a = 0; a < 9; ++a) K[a] = nx[CS_R + a] + gn * ndx[CS_R + a];
+  for (int a = 0; a < 9; ++a) K[a] = cn.R[a] + gn * ndx.R[a];
   proj_rot3d_near(K, Rb);
 #pragma unroll
-  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
-  write_pack<Real>(nx, ndx, Rb, pack_next + (size_t)i * P4N);
+  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = N::to_double(Rb[a]);
+  write_pack_t<Real>(cn, ndx, Rb, pack_next + (size_t)i * P4N);
 }
 
 // ---------------------------------------------------------------------------
