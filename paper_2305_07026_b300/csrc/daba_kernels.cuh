@@ -46,7 +46,7 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 // ---- camera state (doubles, stride 16): R[9] t[3] d[3] pad
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
-constexpr int CPASS_WARPS = 4;
+constexpr int CPASS_WARPS = 1;   // one warp per CTA: 13 resident warps per SM at 147 registers (12 with 4-warp CTAs)
 constexpr int CAMSOLVE_THREADS = 64;   // one camera per active thread
 constexpr int LPASS_THREADS = 128;
 constexpr int LPASS_UNROLL = 4;   // observations whose records a thread loads before storing any
