@@ -56,7 +56,7 @@ struct daba_ctx {
   // device buffers
   void *c_lm = nullptr, *c_u = nullptr;
   void *chunk_cam = nullptr, *chunk_beg = nullptr, *cam_chunk_ptr = nullptr;
-  void *lm_ptr = nullptr, *tile_lm = nullptr, *c_rpos = nullptr, *t_slot = nullptr;
+  void *lm_ptr = nullptr, *tile_lm = nullptr, *c_rpos = nullptr, *t_inv = nullptr;
   void *rec_a = nullptr, *rec_b = nullptr, *rec_c = nullptr;   // landmark-side records in camera order
   void *cam_x = nullptr, *cam_dx = nullptr, *cam_Rbar = nullptr, *pack2[2] = {nullptr, nullptr};
   void *cam_S = nullptr, *cam_E = nullptr, *cam_F = nullptr, *cam_Fb = nullptr, *cam_rs = nullptr;
@@ -232,6 +232,7 @@ IterParams iter_params(daba_ctx* ctx) {
   P.hxif = (float)P.hxi;
   P.accelerated = ctx->opt.accelerated;
   P.n_alt = ctx->opt.cam_alternations;
+  P.flag = (int*)ctx->d_flag;
   return P;
 }
 
@@ -286,7 +287,7 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
       const size_t smem = lpass_smem_bytes<Real>(caps[c]);
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt, LPASS_THREADS, smem, st>>>(
-          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_slot, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
+          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
           (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
           (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
           (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
@@ -452,10 +453,10 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(lm_ptr, (size_t)(N + 1) * 4);
   AL(tile_lm, (size_t)(ctx->max_tiles + 1) * 4);
   AL(c_rpos, nnz * 4);
-  AL(t_slot, nnz * 2);
+  AL(t_inv, nnz * 2 + 16);   // + room for the 16-byte widening of the landmark pass copies
   AL(rec_a, nnz * 4 * R);
   AL(rec_b, nnz * 4 * R);
-  AL(rec_c, nnz * 2 * R);
+  AL(rec_c, nnz * 2 * R + 16);
   AL(cam_x, (size_t)M * CSTRIDE * 8);
   AL(cam_dx, (size_t)M * CSTRIDE * 8);
   AL(cam_Rbar, (size_t)M * 9 * 8);
@@ -612,10 +613,10 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   if ((int)chunk_cam.size() > ctx->max_chunks || n_tiles > ctx->max_tiles)
     return fail(ctx, DABA_ERR_ARG, "internal schedule bound exceeded");
   // inside each tile the records are kept in camera-sorted order: c_rpos gives each
-  // camera-sorted observation its record position, t_slot a record's landmark-sorted slot
+  // camera-sorted observation its record position, t_inv a landmark-sorted slot's record position
   // relative to the tile start
   std::vector<int32_t> c_rpos(n), c_lm(n);
-  std::vector<uint16_t> t_slot(n);
+  std::vector<uint16_t> t_inv(n);
   std::vector<int32_t> t_order(n);
   for (int t = 0; t < n_tiles; ++t) {
     const int ob = lmi_ptr[tile_lm[t]], oe = lmi_ptr[tile_lm[t + 1]];
@@ -624,7 +625,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
               [&](int32_t a, int32_t b) { return cpos_of[li_order[a]] < cpos_of[li_order[b]]; });
     for (int o = ob; o < oe; ++o) {
       c_rpos[cpos_of[li_order[t_order[o]]]] = o;
-      t_slot[o] = (uint16_t)(t_order[o] - ob);
+      t_inv[t_order[o]] = (uint16_t)(o - ob);
     }
   }
   for (int64_t q = 0; q < n; ++q) c_lm[q] = lii[ci_order[q]];
@@ -644,7 +645,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaMemcpyAsync(ctx->lm_ptr, lmi_ptr.data(), (N + 1) * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->tile_lm, tile_lm.data(), tile_lm.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->c_rpos, c_rpos.data(), n * 4, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(ctx->t_slot, t_slot.data(), n * 2, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->t_inv, t_inv.data(), n * 2, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->d_linv, linv.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
@@ -829,6 +830,7 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (flag & 2) return fail(ctx, DABA_ERR_CUDA, "a landmark-pass copy did not complete (bounded wait ran out)");
   if (flag || !std::isfinite(trace[iters])) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
   if (obj_trace && (s = deliver(ctx, obj_trace, trace.data(), ((size_t)iters + 1) * 8, st)) != DABA_OK) return s;
   if (restarts && iters > 0 && (s = deliver(ctx, restarts, rs.data(), (size_t)iters * 4, st)) != DABA_OK) return s;

@@ -64,6 +64,7 @@ struct IterParams {
   float eta1f, hxif;   // the same in FP32 (no FP64 instruction in the FP32 passes)
   int accelerated;
   int n_alt;
+  int* flag;           // error bits: 1 non-finite objective, 2 a bounded wait ran out
 };
 
 template <class Real>
@@ -333,14 +334,62 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // ---------------------------------------------------------------------------
 // Tile data: landmarks tile_lm[t] .. tile_lm[t+1]; their observations occupy the
 // landmark-sorted slots lm_ptr[first] .. lm_ptr[last] and the same range of record positions,
-// where cpass stored them in camera-sorted order; t_slot maps a record position to its
-// landmark-sorted slot relative to the tile start. Reads the landmark state of iteration k
+// where cpass stored them in camera-sorted order; t_inv maps a slot (relative to the tile
+// start) to its record position. One thread issues TMA bulk copies of the tile's three record
+// ranges and of its slice of t_inv into shared memory, completing on an mbarrier; each thread
+// then reduces its landmark's records through t_inv. Reads the landmark state of iteration k
 // and writes that of k+1 to the other buffer.
-// Shared memory, indexed by slot: two V4 arrays (terms at xbar), (terms at x^k) and the
-// third record (RecC).
+constexpr long long LPASS_WAIT_LIMIT = 1ll << 26;   // mbarrier polls before giving up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// 1D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Shared memory of a tile of at most no_cap observations: two V4 arrays (terms at xbar and at
+// x^k), the third records (RecC) and the slot map, each with room for the alignment of its
+// copy to 16 bytes, then the mbarrier.
+template <class Real>
+struct LpassSmem {
+  using RC = typename RecC<Real>::type;
+  static constexpr int kC = 16 / (int)sizeof(RC);   // elements per 16 bytes
+  static __host__ __device__ size_t a_off(int) { return 0; }
+  static __host__ __device__ size_t b_off(int cap) { return (size_t)cap * sizeof(V4<Real>); }
+  static __host__ __device__ size_t c_off(int cap) { return 2 * (size_t)cap * sizeof(V4<Real>); }
+  // a copy widened at both ends holds at most cap + 2 (kC - 1) third records and cap + 14
+  // slot-map entries
+  static __host__ __device__ size_t i_off(int cap) {
+    return c_off(cap) + (((size_t)(cap + 2 * kC) * sizeof(RC) + 15) & ~(size_t)15);
+  }
+  static __host__ __device__ size_t bar_off(int cap) {
+    return i_off(cap) + (((size_t)(cap + 16) * 2 + 15) & ~(size_t)15);
+  }
+  static __host__ __device__ size_t bytes(int cap) { return bar_off(cap) + 16; }
+};
 template <class Real>
 __host__ __device__ inline size_t lpass_smem_bytes(int no_cap) {
-  return (size_t)no_cap * (2 * sizeof(V4<Real>) + (sizeof(Real) == 4 ? 4 : 16)) + 16;
+  return LpassSmem<Real>::bytes(no_cap);
 }
 
 // double-float addition: (hi, lo) + x with |lo| <= ulp(hi)/2 afterwards
@@ -357,76 +406,80 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-            const uint16_t* __restrict__ t_slot, const V4<Real>* __restrict__ rec_a,
+            const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
             const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
-            const V4<Real>* __restrict__ lmrec,
-            const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out, V4<float>* __restrict__ lm_lo_out,
-            IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs, double* __restrict__ lm_Fdiag,
-            double* __restrict__ lm_Fbdiag) {
+            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out,
+            V4<float>* __restrict__ lm_lo_out, IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs,
+            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag) {
+  using RC = typename RecC<Real>::type;
+  using SM = LpassSmem<Real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tile = tile0 + blockIdx.x;
   const int lb = tile_lm[tile], le = tile_lm[tile + 1];
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
   const int no = oe - ob;
-  using RC = typename RecC<Real>::type;
-  V4<Real>* sca = reinterpret_cast<V4<Real>*>(smem_raw);   // arrays of no_cap entries, by slot
-  V4<Real>* scb = sca + no_cap;
-  RC* scc = reinterpret_cast<RC*>(scb + no_cap);
+  V4<Real>* sca = reinterpret_cast<V4<Real>*>(smem_raw + SM::a_off(no_cap));
+  V4<Real>* scb = reinterpret_cast<V4<Real>*>(smem_raw + SM::b_off(no_cap));
+  RC* scc = reinterpret_cast<RC*>(smem_raw + SM::c_off(no_cap));
+  uint16_t* sinv = reinterpret_cast<uint16_t*>(smem_raw + SM::i_off(no_cap));
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + SM::bar_off(no_cap));
+  // copy ranges, widened to 16-byte boundaries for the third records and the slot map
+  const int cs = ob & ~(SM::kC - 1), ce = (oe + SM::kC - 1) & ~(SM::kC - 1);
+  const int is = ob & ~7, ie = (oe + 7) & ~7;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    if (no > 0) {
+      const unsigned ba = (unsigned)no * (unsigned)sizeof(V4<Real>);
+      const unsigned bc = (unsigned)(ce - cs) * (unsigned)sizeof(RC);
+      const unsigned bi = (unsigned)(ie - is) * 2u;
+      mbar_arrive_expect_tx(bar, 2u * ba + bc + bi);
+      bulk_g2s(sca, rec_a + ob, ba, bar);
+      bulk_g2s(scb, rec_b + ob, ba, bar);
+      bulk_g2s(scc, rec_c + cs, bc, bar);
+      bulk_g2s(sinv, t_inv + is, bi, bar);
+    } else {
+      mbar_arrive_expect_tx(bar, 0u);
+    }
+  }
   const Real gamma = Real(P.gam[*P.it]);
   const int first = *P.first;
   // the landmark state of this thread's landmark (at most one: nl <= blockDim.x) is loaded
-  // first so that its latency overlaps the record stream below
+  // while the copies are in flight
   static_assert(TILE_LMS <= LPASS_THREADS, "one landmark per thread");
   const int jl = threadIdx.x;
   const size_t g = (size_t)(lb + jl);
   V4<Real> A, B;
   V4<float> lo0;
+  int s0 = 0, s1 = 0;
   if (jl < nl) {
     A = lmrec[2 * g];
     B = lmrec[2 * g + 1];
     if (HAS_LO) lo0 = lm_lo[g];
+    s0 = lm_ptr[lb + jl] - ob;
+    s1 = lm_ptr[lb + jl + 1] - ob;
   }
-
-  // stream the tile's records into slot order; each thread issues all loads of
-  // LPASS_UNROLL records before storing any
-  for (int o0 = 0; o0 < no; o0 += LPASS_THREADS * LPASS_UNROLL) {
-    int pos[LPASS_UNROLL], slot[LPASS_UNROLL];
-    V4<Real> ra[LPASS_UNROLL], rb[LPASS_UNROLL];
-    RC rc[LPASS_UNROLL];
-#pragma unroll
-    for (int u = 0; u < LPASS_UNROLL; ++u) {
-      const int o = o0 + u * LPASS_THREADS + threadIdx.x;
-      pos[u] = o < no ? ob + o : -1;
-      slot[u] = o < no ? t_slot[ob + o] : 0;
-    }
-#pragma unroll
-    for (int u = 0; u < LPASS_UNROLL; ++u)
-      if (pos[u] >= 0) {
-        ra[u] = rec_a[pos[u]];
-        rb[u] = rec_b[pos[u]];
-        rc[u] = rec_c[pos[u]];
-      }
-#pragma unroll
-    for (int u = 0; u < LPASS_UNROLL; ++u)
-      if (pos[u] >= 0) {
-        sca[slot[u]] = ra[u];
-        scb[slot[u]] = rb[u];
-        scc[slot[u]] = rc[u];
-      }
+  __syncthreads();   // the mbarrier is initialised
+  bool done = false;
+  for (long long w = 0; w < LPASS_WAIT_LIMIT && !done; ++w) done = mbar_try_wait(bar, 0u);
+  if (!done) {   // copies did not complete: report, wait (bounded) once more, give up the tile
+    atomicOr(P.flag, 2);
+    for (long long w = 0; w < LPASS_WAIT_LIMIT && !done; ++w) done = mbar_try_wait(bar, 0u);
+    return;
   }
-  __syncthreads();
 
   int nrs = 0;
   const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
   if (jl < nl) {
-    const int s0 = lm_ptr[lb + jl] - ob, s1 = lm_ptr[lb + jl + 1] - ob;
     Real st[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) st[k] = Real(0);
+    const uint16_t* inv = sinv + (ob - is);
+    const RC* cc = scc + (ob - cs);
     for (int s = s0; s < s1; ++s) {
-      const V4<Real> a = sca[s], b = scb[s];
-      const RC c = scc[s];
+      const int q = inv[s];
+      const V4<Real> a = sca[q], b = scb[q];
+      const RC c = cc[q];
       st[0] += a.x;
       st[1] += a.y;
       st[2] += a.z;
@@ -925,7 +978,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     const int k = *P.it;
     trace[k] = ft * s2;
     restarts[k] = (int)nt;
-    if (!isfinite(ft)) *flag = 1;
+    if (!isfinite(ft)) atomicOr(flag, 1);
     *P.it = k + 1;
     *P.first = 0;
     *ticket = 0u;
