@@ -137,6 +137,21 @@ daba_status daba_get_block_metrics(daba_ctx* ctx, double* F_cam, double* Fbar_ca
 daba_status daba_get_sort(daba_ctx* ctx, int32_t* cam_order, int32_t* cam_ptr, int32_t* lm_order,
                           int32_t* lm_ptr, void* stream);
 
+/* Declares the problem a batch of independent scenes: cameras [cam_begin[s], cam_begin[s+1])
+ * form scene s (cam_begin[0] = 0, cam_begin[n_scenes] = M, non-decreasing; host array of
+ * n_scenes + 1 int32), and each landmark belongs to the scene of the cameras observing it
+ * (DABA_ERR_ARG if a landmark is observed from two scenes). With every camera and landmark a
+ * block of its own (Sec. 5), blocks of different scenes share no term, and the Nesterov
+ * scalars (Eq. nesterov_scalar) depend only on k, so one daba_run iteration over the batch is
+ * one iteration of Algorithm 1 for every scene at once; results equal those of separate runs
+ * with the same pixel_scale. Call after daba_set_observations (which clears the partition).
+ * DABA_ERR_STATE before observations are set. */
+daba_status daba_set_scenes(daba_ctx* ctx, int32_t n_scenes, const int32_t* cam_begin);
+
+/* F(x^k) of every scene of the batch (Eq. Fobj over the scene's observations), pixel^2, into
+ * out[n_scenes] (host or device doubles). DABA_ERR_STATE without a scene partition. */
+daba_status daba_scene_objectives(daba_ctx* ctx, double* out, void* stream);
+
 /* Checkpoint of the full method state (x^k, x^k - x^(k-1), s^k, k and the per-block
  * restart metrics) into a host buffer. With buf == NULL only *bytes is set to the
  * required size. Importing it into a context with the same sizes, options and

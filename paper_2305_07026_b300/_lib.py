@@ -45,6 +45,8 @@ _SIGS = {
     "daba_get_state": (_st, [_p, _p, _p, _p]),
     "daba_get_block_metrics": (_st, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "daba_get_sort": (_st, [_p, _p, _p, _p, _p, _p]),
+    "daba_set_scenes": (_st, [_p, _i32, _p]),
+    "daba_scene_objectives": (_st, [_p, _p, _p]),
     "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
@@ -181,6 +183,18 @@ class Daba:
         self._check(daba_get_sort(self._h, ptr(co), ptr(cp), ptr(lo), ptr(lp),
                                   current_stream() if stream is None else stream))
         return co, cp, lo, lp
+
+    def set_scenes(self, cam_begin):
+        cb = np.ascontiguousarray(cam_begin, dtype=np.int32)
+        self._check(daba_set_scenes(self._h, int(cb.size - 1), ptr(cb)))
+        self.n_scenes = int(cb.size - 1)
+
+    def scene_objectives(self, out=None, stream=None):
+        host = out is None
+        if host:
+            out = np.zeros(self.n_scenes)
+        self._check(daba_scene_objectives(self._h, ptr(out), current_stream() if stream is None else stream))
+        return out
 
     def export_checkpoint(self) -> bytes:
         n = ctypes.c_size_t(0)

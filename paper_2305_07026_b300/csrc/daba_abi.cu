@@ -26,6 +26,7 @@ namespace {
 constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: observations per warp chunk
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
+constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
 constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
@@ -72,6 +73,16 @@ struct daba_ctx {
   std::vector<cudaEvent_t> events;
   cudaStream_t s_hi = nullptr, s_lo = nullptr;   // camera pass + solves (high priority), landmark pass
   cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
+  // CUDA graphs of GRAPH_ITERS and of 1 iteration(s) starting at an even / odd k (the double
+  // buffers alternate with k), captured on s_cap at the first untimed run
+  cudaStream_t s_cap = nullptr;
+  cudaEvent_t ev_cap0 = nullptr, ev_cap1 = nullptr;
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [GRAPH_ITERS or 1][k & 1]
+  int64_t graph_nl[2] = {0, 0};                                                // kernel launches per graph
+  // a batch of independent scenes: camera ranges, chunk ranges per scene (device), outputs
+  int n_scenes = 1;
+  std::vector<int32_t> h_scene_cam;
+  void *d_scene_chunk = nullptr, *d_scene_f = nullptr;
 };
 
 namespace {
@@ -285,7 +296,6 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
     const int nt = ctx->tile_class_end[c] - t0;
     if (nt > 0) {
       const size_t smem = lpass_smem_bytes<Real>(caps[c]);
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       kern<<<nt, LPASS_THREADS, smem, st>>>(
           t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
           (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
@@ -376,6 +386,81 @@ cudaEvent_t ev(daba_ctx* ctx, size_t i) {
   return ctx->events[i];
 }
 
+void drop_graphs(daba_ctx* ctx) {
+  for (auto& row : ctx->graph)
+    for (cudaGraphExec_t& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Enqueues n iterations of Algorithm 1 starting at an iteration of parity k0 & 1 on stream st
+// (the camera pass, then the landmark pass and the camera solves on two priority streams,
+// joined before the reduction); with timing, records the per-kernel events from index evi.
+cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, size_t evi) {
+#define CE(call)                             \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
+  for (int j = 0; j < n; ++j) {
+    const int64_t kk = k0 + j;
+    CE(cudaEventRecord(ctx->ev_fork, st));
+    CE(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 0), ctx->s_hi));
+    CE(launch_pass(ctx, ctx->s_hi, 1, kk));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 1), ctx->s_hi));
+    CE(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
+    CE(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_hi, 0));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 3), ctx->s_lo));
+    CE(launch_lpass(ctx, ctx->s_lo, kk));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 4), ctx->s_lo));
+    CE(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
+    CE(launch_camsolve(ctx, ctx->s_hi, kk));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 2), ctx->s_hi));
+    CE(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
+    CE(cudaStreamWaitEvent(st, ctx->ev_hi, 0));
+    CE(cudaStreamWaitEvent(st, ctx->ev_lo, 0));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 5), st));
+    CE(launch_finalize(ctx, st));
+    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 6), st));
+    if (ctx->timing) evi += 7;
+  }
+  return cudaSuccess;
+#undef CE
+}
+
+// Captures the four iteration graphs (GRAPH_ITERS and 1 iterations, even and odd start) on
+// s_cap; their launch counts go to graph_nl.
+daba_status ensure_graphs(daba_ctx* ctx) {
+  if (ctx->graph[0][0]) return DABA_OK;
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  for (int gi = 0; gi < 2; ++gi)
+    for (int par = 0; par < 2; ++par) {
+      const int64_t l0 = ctx->launches;
+      cudaError_t e = cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t e1 = enqueue_iters(ctx, ctx->s_cap, par, gi == 0 ? GRAPH_ITERS : 1, 0);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
+        e = e1 != cudaSuccess ? e1 : e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph[gi][par], g, 0);
+        if (g) cudaGraphDestroy(g);
+      }
+      ctx->graph_nl[gi] = ctx->launches - l0;
+      ctx->launches = l0;
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        drop_graphs(ctx);
+        ctx->timing = timing;
+        return fail(ctx, DABA_ERR_CUDA, "capturing the iteration graph: %s", cudaGetErrorString(e));
+      }
+    }
+  ctx->timing = timing;
+  return DABA_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -403,12 +488,15 @@ void daba_destroy(daba_ctx* ctx) {
   if (!ctx) return;
   if (ctx->s_hi) cudaStreamSynchronize(ctx->s_hi);
   if (ctx->s_lo) cudaStreamSynchronize(ctx->s_lo);
+  if (ctx->s_cap) cudaStreamSynchronize(ctx->s_cap);
+  drop_graphs(ctx);
   for (void* p : ctx->allocs) cudaFree(p);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
-  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_hi, ctx->ev_lo})
+  for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_hi, ctx->ev_lo, ctx->ev_cap0, ctx->ev_cap1})
     if (e) cudaEventDestroy(e);
   if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
   if (ctx->s_lo) cudaStreamDestroy(ctx->s_lo);
+  if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
   delete ctx;
 }
 
@@ -492,6 +580,8 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_linv, (size_t)N * 4);
   AL(d_chk, CHK_N * 4);
   AL(d_bad, 16);
+  AL(d_scene_chunk, (size_t)(M + 1) * 4);
+  AL(d_scene_f, (size_t)M * 8);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -501,11 +591,19 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
       cudaStreamCreateWithPriority(&ctx->s_lo, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_hi, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_lo, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_lo, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->s_cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_cap0, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_cap1, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     daba_destroy(ctx);
     return DABA_ERR_CUDA;
   }
+  // the landmark pass's largest dynamic shared memory (one-landmark tiles), set once
+  cudaFuncSetAttribute(k_lpass<float, float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)lpass_smem_bytes<float>(BIG_TILE_OBS));
+  cudaFuncSetAttribute(k_lpass<double, double2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)lpass_smem_bytes<double>(BIG_TILE_OBS));
   cudaMemset(ctx->d_flag, 0, 16);
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_linv);   // identity numbering until observations are set
   cudaMemset(ctx->fin_ticket, 0, 16);
@@ -664,6 +762,9 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_lperm.swap(lperm);
   ctx->h_linv.swap(linv);
   ctx->u_scale_uploaded = -1.0;
+  drop_graphs(ctx);   // the graphs hold the old schedule sizes
+  ctx->h_scene_cam.clear();
+  ctx->n_scenes = 1;
   ctx->obs_set = true;
   ctx->checked = false;
   if (ctx->state_set) {
@@ -775,30 +876,20 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     CK(launch_prepare(ctx, st, ctx->k));
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-    for (int j = 0; j < seg; ++j) {
-      const int64_t kk = ctx->k + j;
-      // the camera pass on a high-priority stream; then the landmark pass (low priority)
-      // and the camera solves (the latency-bound critical path, high priority) concurrently
-      CK(cudaEventRecord(ctx->ev_fork, st));
-      CK(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 0), ctx->s_hi));
-      CK(launch_pass(ctx, ctx->s_hi, 1, kk));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 1), ctx->s_hi));
-      CK(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
-      CK(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_hi, 0));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 3), ctx->s_lo));
-      CK(launch_lpass(ctx, ctx->s_lo, kk));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 4), ctx->s_lo));
-      CK(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
-      CK(launch_camsolve(ctx, ctx->s_hi, kk));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 2), ctx->s_hi));
-      CK(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
-      CK(cudaStreamWaitEvent(st, ctx->ev_hi, 0));
-      CK(cudaStreamWaitEvent(st, ctx->ev_lo, 0));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 5), st));
-      CK(launch_finalize(ctx, st));
-      if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi + 6), st));
-      if (ctx->timing) evi += 7;
+    if (ctx->timing) {   // direct launches with per-kernel events
+      CK(enqueue_iters(ctx, st, ctx->k, seg, evi));
+    } else {   // captured graphs on s_cap, joined to st
+      if ((s = ensure_graphs(ctx)) != DABA_OK) return s;
+      CK(cudaEventRecord(ctx->ev_cap0, st));
+      CK(cudaStreamWaitEvent(ctx->s_cap, ctx->ev_cap0, 0));
+      for (int j = 0; j < seg;) {
+        const int gi = seg - j >= GRAPH_ITERS ? 0 : 1;
+        CK(cudaGraphLaunch(ctx->graph[gi][(ctx->k + j) & 1], ctx->s_cap));
+        ctx->launches += ctx->graph_nl[gi];
+        j += gi == 0 ? GRAPH_ITERS : 1;
+      }
+      CK(cudaEventRecord(ctx->ev_cap1, ctx->s_cap));
+      CK(cudaStreamWaitEvent(st, ctx->ev_cap1, 0));
     }
     CK(cudaMemcpyAsync(trace.data() + done, ctx->d_trace, seg * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
@@ -854,6 +945,59 @@ daba_status daba_objective(daba_ctx* ctx, double* out, void* stream) {
     CK(cudaMemcpyAsync(out, ctx->d_obj, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
   }
+  return DABA_OK;
+}
+
+daba_status daba_set_scenes(daba_ctx* ctx, int32_t n_scenes, const int32_t* cam_begin) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations must be set first");
+  if (n_scenes < 1 || n_scenes > ctx->M || !cam_begin) return fail(ctx, DABA_ERR_ARG, "n_scenes out of range");
+  std::vector<int32_t> cb(cam_begin, cam_begin + n_scenes + 1);
+  if (cb[0] != 0 || cb[n_scenes] != ctx->M) return fail(ctx, DABA_ERR_ARG, "cam_begin must run from 0 to M");
+  for (int s = 0; s < n_scenes; ++s)
+    if (cb[s + 1] < cb[s]) return fail(ctx, DABA_ERR_ARG, "cam_begin must be non-decreasing");
+  // every landmark must be observed by the cameras of one scene only
+  std::vector<int32_t> scene_of_cam(ctx->M), lm_scene(ctx->N, -1);
+  for (int s = 0; s < n_scenes; ++s)
+    for (int i = cb[s]; i < cb[s + 1]; ++i) scene_of_cam[i] = s;
+  for (int64_t o = 0; o < ctx->nnz; ++o) {
+    const int j = ctx->h_lm_idx[o], sc = scene_of_cam[ctx->h_cam_idx[o]];
+    if (lm_scene[j] < 0) lm_scene[j] = sc;
+    if (lm_scene[j] != sc)
+      return fail(ctx, DABA_ERR_ARG, "landmark %d is observed by cameras of scenes %d and %d", j, lm_scene[j], sc);
+  }
+  // chunk ranges: the chunks of a camera are consecutive, in camera order
+  std::vector<int32_t> cc(ctx->M + 1);
+  CK(cudaMemcpy(cc.data(), ctx->cam_chunk_ptr, (size_t)(ctx->M + 1) * 4, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> sc(n_scenes + 1);
+  for (int s = 0; s <= n_scenes; ++s) sc[s] = cc[cb[s]];
+  CK(cudaMemcpy(ctx->d_scene_chunk, sc.data(), (size_t)(n_scenes + 1) * 4, cudaMemcpyHostToDevice));
+  ctx->h_scene_cam.swap(cb);
+  ctx->n_scenes = n_scenes;
+  return DABA_OK;
+}
+
+daba_status daba_scene_objectives(daba_ctx* ctx, double* out, void* stream) {
+  if (!ctx || !out) return ctx ? fail(ctx, DABA_ERR_ARG, "null output") : DABA_ERR_ARG;
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  if (ctx->h_scene_cam.empty()) return fail(ctx, DABA_ERR_STATE, "no scene partition set");
+  cudaStream_t st = (cudaStream_t)stream;
+  daba_status s;
+  if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
+  if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  if ((s = enqueue_objective(ctx, st, true)) != DABA_OK) return s;
+  const double s2 = ctx->s_norm * ctx->s_norm;
+  if (is_mixed(ctx))
+    k_segment_sum<float><<<ctx->n_scenes, 256, 0, st>>>((const int*)ctx->d_scene_chunk, (const float*)ctx->chunk_f,
+                                                       s2, (double*)ctx->d_scene_f);
+  else
+    k_segment_sum<double><<<ctx->n_scenes, 256, 0, st>>>((const int*)ctx->d_scene_chunk,
+                                                        (const double*)ctx->chunk_f, s2, (double*)ctx->d_scene_f);
+  CK(cudaGetLastError());
+  const size_t bytes = (size_t)ctx->n_scenes * 8;
+  CK(cudaMemcpyAsync(out, ctx->d_scene_f, bytes, is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     st));
+  CK(cudaStreamSynchronize(st));
   return DABA_OK;
 }
 

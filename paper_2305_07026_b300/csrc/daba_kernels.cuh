@@ -1040,4 +1040,24 @@ __global__ void k_sum(int n, const Real* __restrict__ v, double s2, double* __re
   }
 }
 
+// F per segment of chunks (a batch of independent scenes: one block per scene, its chunks
+// summed in FP64 in a fixed order) times s2 into out[scene]
+template <class Real>
+__global__ void k_segment_sum(const int* __restrict__ seg_ptr, const Real* __restrict__ v, double s2,
+                              double* __restrict__ out) {
+  __shared__ double red[32];
+  const int b = seg_ptr[blockIdx.x], e = seg_ptr[blockIdx.x + 1];
+  double f = 0.0;
+  for (int t = b + threadIdx.x; t < e; t += blockDim.x) f += widen(v[t]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ft = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) ft += red[w];
+    out[blockIdx.x] = ft * s2;
+  }
+}
+
 }  // namespace daba

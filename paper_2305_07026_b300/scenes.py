@@ -487,6 +487,39 @@ def tourism_scene(seed=2, n_cams=10_000, n_lms=4_000_000, n_sites=100, site_spac
 
 
 # ----------------------------------------------------------------------------
+# batch of small independent scenes (serving-style workload)
+# ----------------------------------------------------------------------------
+
+def small_scene(seed, n_cams, n_lms, track_mean=4.0, radius=10.0, half=2.0, outlier_frac=0.03, loss="huber",
+                scale=1.0, iters=100):
+    """A circle-of-cameras scene (as ``circle``) whose landmarks have geometric track lengths
+    (mean ``track_mean``, at least 2): landmark j is seen by a window of consecutive cameras
+    starting at a random one. Every landmark of the 4 m cube projects inside the image of
+    every camera on the 10 m circle, so no visibility test is needed."""
+    rng = np.random.default_rng(seed)
+    ang = 2 * np.pi * np.arange(n_cams) / n_cams
+    t = np.stack([radius * np.cos(ang), radius * np.sin(ang), np.zeros(n_cams)], 1)
+    R = look_at(t, np.zeros_like(t))
+    f, k1, k2 = _intrinsics(rng, n_cams)
+    L = rng.uniform(-half, half, size=(n_lms, 3))
+    tl = np.minimum(np.maximum(2, rng.geometric(1.0 / track_mean, n_lms)), n_cams)
+    first = rng.integers(0, n_cams, n_lms)
+    rep = np.repeat(np.arange(n_lms), tl)
+    k = np.arange(rep.size) - np.repeat(np.cumsum(tl) - tl, tl)
+    cam_idx = (first[rep] + k) % n_cams
+    return _finish("small", rng, R, t, f, k1, k2, L, cam_idx, rep, outlier_frac, loss, scale, iters, seed)
+
+
+def batch_scenes(n_scenes=512, seed=4, cams=(5, 200), lms=(100, 20_000), track_mean=4.0):
+    """``n_scenes`` independent small scenes with log-uniform camera and landmark counts."""
+    rng = np.random.default_rng(seed)
+    mc = np.exp(rng.uniform(np.log(cams[0]), np.log(cams[1]), n_scenes)).round().astype(int)
+    nl = np.exp(rng.uniform(np.log(lms[0]), np.log(lms[1]), n_scenes)).round().astype(int)
+    seeds = rng.integers(0, 2 ** 31, n_scenes)
+    return [small_scene(int(sd), int(m), int(n), track_mean) for sd, m, n in zip(seeds, mc, nl)]
+
+
+# ----------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------
 

@@ -1,0 +1,100 @@
+"""A batch of independent scenes run as one problem (scene partition of the C ABI) against
+separate runs of each scene: with every camera and landmark a block of its own, scenes share
+no term and the Nesterov scalars depend only on k, so the per-block arithmetic is the same
+and the iterates agree bit for bit (same pixel_scale); per-scene objectives agree to rounding
+of their final sums. Also the oracle's objective for one scene of the batch."""
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIXEL_SCALE = 650.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_07026_b300 import build
+    build.build()
+
+
+def _scenes():
+    from paper_2305_07026_b300 import scenes
+    sizes = [(5, 100), (40, 900), (12, 300), (120, 2500), (7, 150), (60, 1200)]
+    return [scenes.small_scene(100 + i, m, n) for i, (m, n) in enumerate(sizes)]
+
+
+def _ctx(L, M, N, nnz, prec):
+    return L.Daba(M, N, nnz, loss="huber", loss_scale_px=1.0, prec=prec, pixel_scale=PIXEL_SCALE)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_separate_runs(prec):
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch
+    scs = _scenes()
+    b = batch.merge(scs)
+    K = 12
+    d = _ctx(L, b.M, b.N, b.nnz, prec)
+    d.set_observations(b.cam_idx, b.lm_idx, b.uv)
+    d.set_state(b.cams, b.lms)
+    d.set_scenes(b.cam_begin)
+    f0 = d.scene_objectives()
+    d.run(K)
+    fK = d.scene_objectives()
+    cams, lms = d.get_state()
+    d.close()
+    for i, (sc, (cb, lb)) in enumerate(zip(scs, batch.split(b, cams, lms))):
+        e = _ctx(L, sc.M, sc.N, sc.nnz, prec)
+        e.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        e.set_state(sc.cams, sc.lms)
+        g0 = e.objective()
+        e.run(K)
+        gK = e.objective()
+        c1, l1 = e.get_state()
+        e.close()
+        np.testing.assert_array_equal(cb, c1, err_msg=f"scene {i}")
+        np.testing.assert_array_equal(lb, l1, err_msg=f"scene {i}")
+        assert f0[i] == pytest.approx(g0, rel=1e-12)
+        assert fK[i] == pytest.approx(gK, rel=1e-12)
+
+
+def test_scene_objective_matches_oracle():
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch
+    scs = _scenes()
+    b = batch.merge(scs)
+    d = _ctx(L, b.M, b.N, b.nnz, "fp64")
+    d.set_observations(b.cam_idx, b.lm_idx, b.uv)
+    d.set_state(b.cams, b.lms)
+    d.set_scenes(b.cam_begin)
+    f = d.scene_objectives()
+    d.close()
+    for i, sc in enumerate(scs):
+        o = O.Options(loss="huber", loss_scale_px=1.0, pixel_scale=PIXEL_SCALE)
+        prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
+        F = O.objective(prob.loss, prob.c, R, t, dd, l, prob.cam_idx, prob.lm_idx, prob.u) * prob.s_norm ** 2
+        assert f[i] == pytest.approx(F, rel=1e-11), i
+
+
+def test_scene_partition_is_validated():
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch
+    scs = _scenes()[:2]
+    b = batch.merge(scs)
+    d = _ctx(L, b.M, b.N, b.nnz, "mixed")
+    d.set_observations(b.cam_idx, b.lm_idx, b.uv)
+    d.set_state(b.cams, b.lms)
+    with pytest.raises(L.DabaError) as e:     # scene 0 ends one camera early: its last camera's
+        d.set_scenes(np.array([0, b.cam_begin[1] - 1, b.M]))   # landmarks are seen from both sides
+    assert e.value.status == L.DABA_ERR_ARG
+    with pytest.raises(L.DabaError) as e:
+        d.set_scenes(np.array([0, b.M - 1]))
+    assert e.value.status == L.DABA_ERR_ARG
+    d.set_scenes(b.cam_begin)
+    assert d.scene_objectives().shape == (2,)
+    d.close()

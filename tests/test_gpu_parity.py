@@ -260,6 +260,58 @@ def test_edge_blocks(prec):
     d.close()
 
 
+def _long_track_scene():
+    """700 cameras around a 4 m cube: 24 landmarks seen by ~700 cameras each (tracks above the
+    512-observation tile size, so each gets a tile of its own) and 40 landmarks cut to 3-9
+    observations (small tiles), in one problem."""
+    from paper_2305_07026_b300 import scenes
+    sc = scenes.circle_scene(seed=5, n_cams=700, n_lms=64, cap=700)
+    rng = np.random.default_rng(5)
+    keep = np.ones(sc.nnz, bool)
+    for j in range(24, sc.N):
+        o = np.flatnonzero(sc.lm_idx == j)
+        keep[o[rng.integers(3, 10):]] = False
+    ci, li, uv = sc.cam_idx[keep], sc.lm_idx[keep], sc.uv[keep]
+    deg = np.bincount(li, minlength=sc.N)
+    assert deg[:24].min() > 512 and deg[24:].max() < 10
+    return sc, ci, li, uv
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_long_tracks_big_tiles(prec):
+    """Landmarks with more observations than a small tile holds take the one-landmark tile path
+    of the landmark pass (records copied in 2048-entry tiles); per-iteration objective against
+    the oracle."""
+    sc, ci, li, uv = _long_track_scene()
+    res = O.daba(sc.cams, sc.lms, ci, li, uv, _oracle_opts(sc), 8)
+    d = _lib().Daba(sc.M, sc.N, ci.size, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    d.set_observations(ci, li, uv)
+    d.set_state(sc.cams, sc.lms)
+    tr = np.zeros(9)
+    d.run(8, tr)
+    tol = 1e-10 if prec == "fp64" else 1e-4
+    np.testing.assert_allclose(tr, res.trace_px2, rtol=tol)
+    if prec == "fp64":
+        cams_o, lms_o = O.boundary_state(res)
+        cg, lg = d.get_state()
+        np.testing.assert_allclose(lg, lms_o, rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(cg, cams_o, rtol=1e-8, atol=1e-8)
+    d.close()
+
+
+def test_track_longer_than_the_limit_is_rejected():
+    L = _lib()
+    M = 2049
+    ci = np.arange(M, dtype=np.int32)
+    li = np.zeros(M, np.int32)
+    uv = np.zeros((M, 2))
+    d = L.Daba(M, 1, M, prec="mixed")
+    with pytest.raises(L.DabaError) as e:
+        d.set_observations(ci, li, uv)
+    assert e.value.status == L.DABA_ERR_ARG
+    d.close()
+
+
 def test_error_statuses():
     L = _lib()
     sc = cached_scene("circle")
