@@ -503,3 +503,69 @@ def grad_F_obs(loss, c, R, t, d, l, u):
     gd = (w * e[:, 2])[:, None] * phi
     gR = -(w * lm)[:, None, None] * (l - t)[:, :, None] * e[:, None, :]
     return gt, gl, gd, gR
+
+
+def grad_F_obs_u(loss, c, R, t, d, l, u):
+    """Per-observation gradient of F_ij w.r.t. the pixel u (internal units).
+
+    p = (u_1, u_2, d_1 + d_2 s + d_3 s^2) (Eq. ray) and, lambda being the minimiser of
+    |p - lambda R^T (l - t)|^2 (Eq. lambdaij), dF/dp = w e (camera frame), so
+      dF/du_a = w (e_a + e_3 * 2 u_a (d_2 + 2 d_3 s)).
+    """
+    p = ray(u, d)
+    e = reproj_error(R, t, l, p)
+    r = np.einsum("na,na->n", e, e)
+    _, w = rho(loss, c, r)
+    s = u[:, 0] ** 2 + u[:, 1] ** 2
+    dpz = 2.0 * (d[:, 1] + 2.0 * d[:, 2] * s)
+    return w[:, None] * (e[:, 0:2] + (e[:, 2] * dpz)[:, None] * u)
+
+
+def so3_right_jacobian(w):
+    """J_r(w) with Exp(w + dw) = Exp(w) Exp(J_r(w) dw) + O(dw^2):
+    J_r = I - (1 - cos th)/th^2 [w]x + (th - sin th)/th^3 [w]x^2 (series below 1e-6)."""
+    w = np.asarray(w, dtype=np.float64)
+    th = np.linalg.norm(w, axis=-1)[..., None, None]
+    K = np.zeros(w.shape[:-1] + (3, 3))
+    K[..., 0, 1], K[..., 0, 2], K[..., 1, 2] = -w[..., 2], w[..., 1], -w[..., 0]
+    K[..., 1, 0], K[..., 2, 0], K[..., 2, 1] = w[..., 2], -w[..., 1], w[..., 0]
+    small = th < 1e-6
+    ths = np.where(small, 1.0, th)
+    a = np.where(small, 0.5 - th ** 2 / 24.0, (1.0 - np.cos(ths)) / ths ** 2)
+    b = np.where(small, 1.0 / 6.0 - th ** 2 / 120.0, (ths - np.sin(ths)) / ths ** 3)
+    return np.eye(3) - a * K + b * (K @ K)
+
+
+def grad_objective_boundary(cams, lms, cam_idx, lm_idx, uv, opts: Options):
+    """F(x) in pixel^2 (Eq. Fobj) and its gradient w.r.t. the boundary parameters: cameras
+    [w, t, f, k1, k2] (M x 9), landmarks (N x 3) and observed pixels (nnz x 2).
+
+    Per observation the Euclidean gradients of Eq. DFij (grad_F_obs) and of the pixel
+    (grad_F_obs_u) are summed per camera and landmark, then carried to the boundary:
+    rotation through F(R Exp(phi)) (tangent gradient vee(R^T G - G^T R)) and the right
+    Jacobian of Exp; intrinsics through d = (f/s, k1 s/f, k2 s^3/f^3); pixels through
+    u' = u/s. F_px = s^2 F' with s the internal unit, which leaves F_px independent of s.
+    """
+    prob, R, t, d, l = make_problem(cams, lms, cam_idx, lm_idx, uv, opts)
+    ci, li, u, s = prob.cam_idx, prob.lm_idx, prob.u, prob.s_norm
+    Ri, ti, di, lj = R[ci], t[ci], d[ci], l[li]
+    F = float(np.sum(F_obs(prob.loss, prob.c, Ri, ti, di, lj, u))) * s * s
+    gt, gl, gd, gR = grad_F_obs(prob.loss, prob.c, Ri, ti, di, lj, u)
+    gu = grad_F_obs_u(prob.loss, prob.c, Ri, ti, di, lj, u)
+    M, N = prob.M, prob.N
+    G = segsum(ci, gR.reshape(-1, 9), M).reshape(M, 3, 3)
+    Gt = segsum(ci, gt, M)
+    Gd = segsum(ci, gd, M)
+    Gl = segsum(li, gl, N)
+    RtG = np.einsum("nba,nbc->nac", R, G)
+    S = RtG - np.transpose(RtG, (0, 2, 1))
+    gphi = np.stack([S[:, 2, 1], S[:, 0, 2], S[:, 1, 0]], 1)
+    cams = np.asarray(cams, dtype=np.float64)
+    Jr = so3_right_jacobian(cams[:, 0:3])
+    gw = np.einsum("nba,nb->na", Jr, gphi)
+    f, k1, k2 = cams[:, 6], cams[:, 7], cams[:, 8]
+    gf = Gd[:, 0] / s - Gd[:, 1] * k1 * s / f ** 2 - 3.0 * Gd[:, 2] * k2 * s ** 3 / f ** 4
+    gk1 = Gd[:, 1] * s / f
+    gk2 = Gd[:, 2] * s ** 3 / f ** 3
+    g_cams = np.concatenate([gw, Gt, gf[:, None], gk1[:, None], gk2[:, None]], 1) * s * s
+    return F, g_cams, Gl * s * s, gu * s

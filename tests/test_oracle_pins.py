@@ -501,3 +501,46 @@ def test_fixed_point_at_truth():
     np.testing.assert_allclose(lms, sc.lms_gt, atol=1e-9)
     np.testing.assert_allclose(cams, sc.cams_gt, atol=1e-8)
     assert res.trace_px2.max() < 1e-14 * sc.nnz
+
+
+@pytest.mark.parametrize("loss", ["huber", "cauchy", "trivial"])
+def test_boundary_gradient_fd(loss):
+    """Gradient of F (pixel^2) w.r.t. the boundary cameras [w, t, f, k1, k2], landmarks and pixels
+    against FP64 central differences of the objective along random directions."""
+    from paper_2305_07026_b300 import scenes
+    sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+    o = O.Options(loss=loss, loss_scale_px=2.0)
+    F, gc, gl, gu = O.grad_objective_boundary(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
+
+    def Fx(c, l, u):
+        prob, R, t, d, lm = O.make_problem(c, l, sc.cam_idx, sc.lm_idx, u, o)
+        return O.objective(prob.loss, prob.c, R, t, d, lm, prob.cam_idx, prob.lm_idx, prob.u) * prob.s_norm ** 2
+
+    assert F == pytest.approx(Fx(sc.cams, sc.lms, sc.uv), rel=1e-14)
+    rng = np.random.default_rng(3)
+    cscale = np.array([1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 0.5, 1e-4, 1e-6])
+    for _ in range(16):
+        vc = rng.normal(size=sc.cams.shape) * cscale
+        vl = rng.normal(size=sc.lms.shape) * 1e-3
+        vu = rng.normal(size=sc.uv.shape) * 1e-2
+        h = 1e-3
+        fd = (Fx(sc.cams + h * vc, sc.lms + h * vl, sc.uv + h * vu) -
+              Fx(sc.cams - h * vc, sc.lms - h * vl, sc.uv - h * vu)) / (2 * h)
+        an = np.sum(gc * vc) + np.sum(gl * vl) + np.sum(gu * vu)
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-9 * abs(F))
+    # each block separately (a wrong chain rule in one part cannot hide behind the others)
+    for part in range(3):
+        v = [np.zeros_like(sc.cams), np.zeros_like(sc.lms), np.zeros_like(sc.uv)]
+        v[part] = rng.normal(size=v[part].shape) * (cscale if part == 0 else (1e-3 if part == 1 else 1e-2))
+        h = 1e-3
+        fd = (Fx(sc.cams + h * v[0], sc.lms + h * v[1], sc.uv + h * v[2]) -
+              Fx(sc.cams - h * v[0], sc.lms - h * v[1], sc.uv - h * v[2])) / (2 * h)
+        an = np.sum(gc * v[0]) + np.sum(gl * v[1]) + np.sum(gu * v[2])
+        assert an == pytest.approx(fd, rel=1e-6), part
+    # each camera parameter column separately
+    for k in range(9):
+        v = np.zeros_like(sc.cams)
+        v[:, k] = rng.normal(size=sc.M) * cscale[k]
+        h = 1e-3
+        fd = (Fx(sc.cams + h * v, sc.lms, sc.uv) - Fx(sc.cams - h * v, sc.lms, sc.uv)) / (2 * h)
+        assert np.sum(gc * v) == pytest.approx(fd, rel=1e-5, abs=1e-12 * abs(F)), k
