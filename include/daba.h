@@ -119,6 +119,24 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
  * (host or device double). */
 daba_status daba_objective(daba_ctx* ctx, double* out, void* stream);
 
+/* F(x^k) (Eq. Fobj, pixel^2) and its gradient w.r.t. the boundary parameters, by adjoint
+ * kernels of the per-observation gradients of Eq. DFij (App. D):
+ *   F:      1 double;
+ *   g_cams: M x 9, d F / d [w(3), t(3), f, k1, k2] of daba_set_state (the rotation part is
+ *           w.r.t. the axis-angle vector of norm <= pi that daba_get_state returns);
+ *   g_lms:  N x 3, d F / d l_j;
+ *   g_uv:   nnz x 2, d F / d u_ij (input observation order).
+ * Each output may be NULL, host or device memory. Evaluated in the context's precision
+ * (MIXED: FP32 per observation, FP64 per-camera and per-landmark sums). Uses the library's
+ * scratch buffers: do not overlap with daba_run on another stream. */
+daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double* g_lms, double* g_uv,
+                                void* stream);
+
+/* Replaces the observed pixels (nnz x 2, input observation order, host or device) without
+ * re-sorting: the observation list stays that of daba_set_observations. Requires the state to
+ * be set (the internal unit s is fixed by then). DABA_ERR_NONFINITE on NaN/Inf. */
+daba_status daba_set_pixels(daba_ctx* ctx, const double* uv, void* stream);
+
 /* Copies the current iterate x^k out in the boundary layout of daba_set_state
  * (either pointer may be NULL to skip it). */
 daba_status daba_get_state(daba_ctx* ctx, double* cams, double* lms, void* stream);

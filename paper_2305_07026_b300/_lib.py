@@ -46,6 +46,8 @@ _SIGS = {
     "daba_get_block_metrics": (_st, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "daba_get_sort": (_st, [_p, _p, _p, _p, _p, _p]),
     "daba_set_scenes": (_st, [_p, _i32, _p]),
+    "daba_objective_grad": (_st, [_p, _p, _p, _p, _p, _p]),
+    "daba_set_pixels": (_st, [_p, _p, _p]),
     "daba_scene_objectives": (_st, [_p, _p, _p]),
     "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
@@ -183,6 +185,21 @@ class Daba:
         self._check(daba_get_sort(self._h, ptr(co), ptr(cp), ptr(lo), ptr(lp),
                                   current_stream() if stream is None else stream))
         return co, cp, lo, lp
+
+    def objective_grad(self, F=None, g_cams=None, g_lms=None, g_uv=None, stream=None):
+        """F(x^k) and its gradients w.r.t. cameras (M x 9), landmarks (N x 3) and pixels (nnz x 2);
+        with no arguments, host arrays of all four are returned."""
+        if F is None and g_cams is None and g_lms is None and g_uv is None:
+            F, g_cams, g_lms, g_uv = np.zeros(1), np.zeros((self.M, 9)), np.zeros((self.N, 3)), np.zeros((self.nnz, 2))
+            self._check(daba_objective_grad(self._h, ptr(F), ptr(g_cams), ptr(g_lms), ptr(g_uv),
+                                            current_stream() if stream is None else stream))
+            return float(F[0]), g_cams, g_lms, g_uv
+        self._check(daba_objective_grad(self._h, ptr(F), ptr(g_cams), ptr(g_lms), ptr(g_uv),
+                                        current_stream() if stream is None else stream))
+        return F, g_cams, g_lms, g_uv
+
+    def set_pixels(self, uv, stream=None):
+        self._check(daba_set_pixels(self._h, ptr(uv), current_stream() if stream is None else stream))
 
     def set_scenes(self, cam_begin):
         cb = np.ascontiguousarray(cam_begin, dtype=np.int32)

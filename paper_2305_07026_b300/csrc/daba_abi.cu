@@ -18,6 +18,7 @@
 #include "../../include/daba.h"
 #include "daba_kernels.cuh"
 #include "daba_state.cuh"
+#include "daba_grad.cuh"
 
 using namespace daba;
 
@@ -42,6 +43,7 @@ struct daba_ctx {
   int tile_class_end[2] = {0, 0};   // tiles [0, e0): small, [e0, e1): one long-track landmark each
   bool obs_set = false, state_set = false, checked = false;
   double s_norm = 0.0, u_scale_uploaded = -1.0;
+  bool h_uv_stale = false;   // pixels last set from device memory (the host copy is older)
   double s_k = 1.0;   // Nesterov s^(k)
   int64_t k = 0;      // iteration index
   bool timing = false;
@@ -69,6 +71,9 @@ struct daba_ctx {
        *d_rs = nullptr, *d_obj = nullptr;
   // state I/O: staging of boundary-layout state, external -> internal landmark id, checks
   void *st_cam = nullptr, *st_lm = nullptr, *d_linv = nullptr, *d_chk = nullptr, *d_bad = nullptr;
+  // device copies of the camera order (device position -> input index) and of the internal ->
+  // external landmark map (gradient outputs, pixel updates)
+  void *d_ci_order = nullptr, *d_lperm = nullptr;
   std::vector<void*> allocs;
   std::vector<cudaEvent_t> events;
   cudaStream_t s_hi = nullptr, s_lo = nullptr;   // camera pass + solves (high priority), landmark pass
@@ -184,6 +189,7 @@ void upload_u(daba_ctx* ctx, cudaStream_t st, cudaError_t* err) {
 
 daba_status ensure_u(daba_ctx* ctx, cudaStream_t st) {
   if (ctx->u_scale_uploaded == ctx->s_norm) return DABA_OK;
+  if (ctx->h_uv_stale) return fail(ctx, DABA_ERR_STATE, "pixels set from device memory cannot be re-scaled");
   cudaError_t e;
   if (is_mixed(ctx))
     upload_u<float, float2>(ctx, st, &e);
@@ -461,6 +467,28 @@ daba_status ensure_graphs(daba_ctx* ctx) {
   return DABA_OK;
 }
 
+template <int LOSS, class Real, class Real2, bool HAS_LO>
+cudaError_t launch_grad_t(daba_ctx* ctx, cudaStream_t st) {
+  const LossC<Real> L = loss_consts<Real>(ctx);
+  if (ctx->n_chunks == 0) return cudaSuccess;
+  k_grad_obs<LOSS, Real, Real2, HAS_LO><<<ctx->n_chunks, 32, 0, st>>>(
+      ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+      (const Real2*)ctx->c_u, (const int*)ctx->c_rpos, (const int*)ctx->d_ci_order, (const V4<Real>*)pack_at(ctx, ctx->k),
+      (const V4<Real>*)lmrec_at(ctx, ctx->k), (const V4<float>*)lmlo_at(ctx, ctx->k), L, ctx->s_norm,
+      (Real*)ctx->chunk_part, (V4<Real>*)ctx->rec_a, (double2*)ctx->rec_b);
+  return cudaGetLastError();
+}
+
+template <class Real, class Real2, bool HAS_LO>
+cudaError_t launch_grad_by_loss(daba_ctx* ctx, cudaStream_t st) {
+  switch (ctx->opt.loss) {
+    case DABA_LOSS_TRIVIAL: return launch_grad_t<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st);
+    case DABA_LOSS_HUBER: return launch_grad_t<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st);
+    case DABA_LOSS_CAUCHY: return launch_grad_t<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st);
+    default: return launch_grad_t<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st);
+  }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -581,6 +609,8 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_chk, CHK_N * 4);
   AL(d_bad, 16);
   AL(d_scene_chunk, (size_t)(M + 1) * 4);
+  AL(d_ci_order, nnz * 4);
+  AL(d_lperm, (size_t)N * 4);
   AL(d_scene_f, (size_t)M * 8);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
@@ -606,6 +636,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
                        (int)lpass_smem_bytes<double>(BIG_TILE_OBS));
   cudaMemset(ctx->d_flag, 0, 16);
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_linv);   // identity numbering until observations are set
+  k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_lperm);
   cudaMemset(ctx->fin_ticket, 0, 16);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
@@ -745,6 +776,8 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   CK(cudaMemcpyAsync(ctx->c_rpos, c_rpos.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->t_inv, t_inv.data(), n * 2, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->d_linv, linv.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_lperm, lperm.data(), (size_t)N * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_ci_order, ci_order.data(), n * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->n_chunks = (int)chunk_cam.size();
   ctx->n_tiles = n_tiles;
@@ -762,6 +795,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_lperm.swap(lperm);
   ctx->h_linv.swap(linv);
   ctx->u_scale_uploaded = -1.0;
+  ctx->h_uv_stale = false;
   drop_graphs(ctx);   // the graphs hold the old schedule sizes
   ctx->h_scene_cam.clear();
   ctx->n_scenes = 1;
@@ -998,6 +1032,88 @@ daba_status daba_scene_objectives(daba_ctx* ctx, double* out, void* stream) {
   CK(cudaMemcpyAsync(out, ctx->d_scene_f, bytes, is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      st));
   CK(cudaStreamSynchronize(st));
+  return DABA_OK;
+}
+
+daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double* g_lms, double* g_uv,
+                                void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  cudaStream_t st = (cudaStream_t)stream;
+  daba_status s;
+  if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
+  if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  // the pass pack of x^k (gamma = 0), as for the objective
+  CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_gam, 0, sizeof(double), st));
+  CK(launch_prepare(ctx, st, ctx->k));
+  if (is_mixed(ctx))
+    CK((launch_grad_by_loss<float, float2, true>(ctx, st)));
+  else
+    CK((launch_grad_by_loss<double, double2, false>(ctx, st)));
+  const int M = ctx->M, N = ctx->N;
+  const double sn = ctx->s_norm;
+  const bool cdev = g_cams && is_device_ptr(g_cams), ldev = g_lms && is_device_ptr(g_lms);
+  double* gc = cdev ? g_cams : (double*)ctx->st_cam;
+  double* gl = ldev ? g_lms : (double*)ctx->st_lm;
+  if (is_mixed(ctx))
+    k_grad_cams<float><<<(M + 127) / 128, 128, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
+                                                       (const double*)ctx->cam_x, sn, gc, (double*)ctx->cam_Fsum);
+  else
+    k_grad_cams<double><<<(M + 127) / 128, 128, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr,
+                                                        (const double*)ctx->chunk_part, (const double*)ctx->cam_x, sn,
+                                                        gc, (double*)ctx->cam_Fsum);
+  k_sum<double><<<1, 1024, 0, st>>>(M, (const double*)ctx->cam_Fsum, sn * sn, (double*)ctx->d_obj);
+  if (ctx->n_tiles > 0) {
+    if (is_mixed(ctx))
+      k_grad_lms<float><<<ctx->n_tiles, LPASS_THREADS, 0, st>>>(
+          (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<float>*)ctx->rec_a,
+          (const int*)ctx->d_lperm, sn * sn, gl);
+    else
+      k_grad_lms<double><<<ctx->n_tiles, LPASS_THREADS, 0, st>>>(
+          (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv,
+          (const V4<double>*)ctx->rec_a, (const int*)ctx->d_lperm, sn * sn, gl);
+  }
+  CK(cudaGetLastError());
+  // every landmark is in one tile (those without observations get a zero gradient)
+  if (F) CK(cudaMemcpyAsync(F, ctx->d_obj, 8, is_device_ptr(F) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  if (g_cams && !cdev) CK(cudaMemcpyAsync(g_cams, gc, (size_t)M * 9 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_lms && !ldev) CK(cudaMemcpyAsync(g_lms, gl, (size_t)N * 3 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_uv)
+    CK(cudaMemcpyAsync(g_uv, ctx->rec_b, (size_t)ctx->nnz * 16,
+                       is_device_ptr(g_uv) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return DABA_OK;
+}
+
+daba_status daba_set_pixels(daba_ctx* ctx, const double* uv, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!uv) return fail(ctx, DABA_ERR_ARG, "null pixel pointer");
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = ctx->nnz;
+  const bool dev = is_device_ptr(uv);
+  if (!dev) std::memcpy(ctx->h_uv.data(), uv, (size_t)n * 16);   // the host copy stays current
+  const double* du = uv;
+  if (!dev) {   // staged through rec_b (nnz x 16 bytes)
+    CK(cudaMemcpyAsync(ctx->rec_b, uv, (size_t)n * 16, cudaMemcpyHostToDevice, st));
+    du = (const double*)ctx->rec_b;
+  }
+  k_chk_init<<<1, 32, 0, st>>>((int*)ctx->d_chk, (unsigned long long*)ctx->d_bad);
+  const int blocks = (int)((n + 255) / 256);
+  if (is_mixed(ctx))
+    k_set_pixels<float2><<<blocks, 256, 0, st>>>(n, (const int*)ctx->d_ci_order, du, ctx->s_norm, (float2*)ctx->c_u,
+                                                 (int*)ctx->d_chk);
+  else
+    k_set_pixels<double2><<<blocks, 256, 0, st>>>(n, (const int*)ctx->d_ci_order, du, ctx->s_norm,
+                                                  (double2*)ctx->c_u, (int*)ctx->d_chk);
+  CK(cudaGetLastError());
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_chk, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->u_scale_uploaded = ctx->s_norm;
+  if (dev) ctx->h_uv_stale = true;
+  if (bad != INT_MAX) return fail(ctx, DABA_ERR_NONFINITE, "observation %d has a non-finite pixel", bad);
   return DABA_OK;
 }
 

@@ -1,0 +1,111 @@
+"""Gradient of the objective through the C ABI (adjoint kernels) and the PyTorch autograd
+function: against the oracle's boundary gradient (itself pinned by FP64 central differences)
+and against FP64 central differences of the library's own objective along random directions."""
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+from tests.conftest import cached_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_07026_b300 import build
+    build.build()
+
+
+def _ctx(sc, prec, **kw):
+    from paper_2305_07026_b300 import _lib as L
+    o = dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    o.update(kw)
+    d = L.Daba(sc.M, sc.N, sc.nnz, **o)
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    d.set_state(sc.cams, sc.lms)
+    return d
+
+
+def _close(a, b, tol):
+    a, b = np.asarray(a), np.asarray(b)
+    np.testing.assert_allclose(a, b, rtol=tol, atol=tol * np.abs(b).max())
+
+
+@pytest.mark.parametrize("workload,scale,prec", [("circle", 1.0, "fp64"), ("circle", 1.0, "mixed"),
+                                                 ("tourism", 0.005, "fp64"), ("street", 0.05, "fp64")])
+def test_objective_grad_matches_oracle(workload, scale, prec):
+    sc = cached_scene(workload, scale=scale)
+    F, gc, gl, gu = O.grad_objective_boundary(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv,
+                                              O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px))
+    d = _ctx(sc, prec)
+    Fg, gcg, glg, gug = d.objective_grad()
+    tol = 1e-9 if prec == "fp64" else 2e-4
+    assert Fg == pytest.approx(F, rel=1e-11 if prec == "fp64" else 1e-5)
+    _close(gcg, gc, tol)
+    _close(glg, gl, tol)
+    _close(gug, gu, tol)
+    # after iterations the gradient is taken at the new iterate
+    d.run(3)
+    cams, lms = d.get_state()
+    F3, gc3, gl3, gu3 = O.grad_objective_boundary(cams, lms, sc.cam_idx, sc.lm_idx, sc.uv,
+                                                  O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px))
+    Fg3, gcg3, glg3, gug3 = d.objective_grad()
+    assert Fg3 == pytest.approx(F3, rel=1e-10 if prec == "fp64" else 1e-5)
+    _close(glg3, gl3, tol)
+    d.close()
+
+
+def test_autograd_matches_central_differences():
+    """Differentiation workload: 200 cameras of the street generator, FP64 path; autograd
+    gradient against FP64 central differences (h = 1e-6 relative) on 64 random directions."""
+    from paper_2305_07026_b300.autograd import objective
+    sc = cached_scene("street", scale=0.2)
+    d = _ctx(sc, "fp64")
+    dev = "cuda"
+    cams = torch.tensor(sc.cams, device=dev, requires_grad=True)
+    lms = torch.tensor(sc.lms, device=dev, requires_grad=True)
+    uv = torch.tensor(sc.uv, device=dev, requires_grad=True)
+    F = objective(d, cams, lms, uv)
+    F.backward()
+    gc, gl, gu = cams.grad.detach().clone(), lms.grad.detach().clone(), uv.grad.detach().clone()
+    rng = np.random.default_rng(7)
+    cscale = torch.tensor([1e-3, 1e-3, 1e-3, 1e-2, 1e-2, 1e-2, 1.0, 1e-4, 1e-6], dtype=torch.float64, device=dev)
+    h = 1e-6 / 1e-3
+    with torch.no_grad():
+        for k in range(64):
+            vc = torch.tensor(rng.normal(size=sc.cams.shape), device=dev) * cscale * 1e-3
+            vl = torch.tensor(rng.normal(size=sc.lms.shape), device=dev) * 1e-5
+            vu = torch.tensor(rng.normal(size=sc.uv.shape), device=dev) * 1e-4
+            fp = objective(d, cams + h * vc, lms + h * vl, uv + h * vu).item()
+            fm = objective(d, cams - h * vc, lms - h * vl, uv - h * vu).item()
+            fd = (fp - fm) / (2 * h)
+            an = float((gc * vc).sum() + (gl * vl).sum() + (gu * vu).sum())
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-10 * F.item()), k
+    d.close()
+
+
+def test_set_pixels_matches_set_observations():
+    sc = cached_scene("circle")
+    rng = np.random.default_rng(3)
+    uv2 = sc.uv + rng.normal(0, 0.5, sc.uv.shape)
+    from paper_2305_07026_b300 import _lib as L
+    for prec in ("fp64", "mixed"):
+        a = _ctx(sc, prec)
+        a.set_pixels(uv2)
+        b = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+        b.set_observations(sc.cam_idx, sc.lm_idx, uv2)
+        b.set_state(sc.cams, sc.lms)
+        ta, tb = np.zeros(6), np.zeros(6)
+        a.run(5, ta)
+        b.run(5, tb)
+        np.testing.assert_array_equal(ta, tb)
+        bad = uv2.copy()
+        bad[4, 0] = np.nan
+        with pytest.raises(L.DabaError) as e:
+            a.set_pixels(bad)
+        assert e.value.status == L.DABA_ERR_NONFINITE
+        a.close()
+        b.close()
