@@ -494,11 +494,53 @@ def run_batch(args, rank, world, local):
     }
 
 
+def run_reference_batch(args, world):
+    """The oracle on the batch workload: scenes of the batch run one after another for a few
+    iterations each (about 20 s in total), the mean time per scene-iteration scaled to
+    ``--steps`` iterations per scene."""
+    from oracle import daba_oracle as O
+    from paper_2305_07026_b300 import scenes
+    import contextlib
+    try:
+        from threadpoolctl import threadpool_limits
+        limit = threadpool_limits(limits=1)
+    except ImportError:
+        limit = contextlib.nullcontext()
+    scs = scenes.batch_scenes(args.n_scenes)
+    iters = 3
+    t_used, done, obs = 0.0, 0, 0
+    with limit:
+        for sc in scs:
+            if t_used > 20.0:
+                break
+            o = O.Options(loss="huber", loss_scale_px=1.0, pixel_scale=650.0)
+            t0 = time.perf_counter()
+            O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, iters)
+            t_used += time.perf_counter() - t0
+            done += 1
+            obs += sc.nnz
+    per_scene_iter = t_used / (done * iters)
+    value = 1.0 / (per_scene_iter * args.steps)
+    return {
+        "metric": f"scenes/s ({args.steps} DABA iterations per scene, batched)", "value": value, "unit": "scenes/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"batch: {len(scs)} circle scenes (the batch workload of the GPU arm)", "prec": "fp64 (oracle)"},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "scenes/s",
+                         "sample": f"the first {done} scenes ({obs} observations), {iters} oracle iterations each, "
+                                   f"{t_used:.1f} s, scaled to {args.steps} iterations per scene"},
+        "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, rank, world):
     """The FP64 oracle timed on the host cores on a bounded sample of the same workload."""
     if rank != 0:
         return None
     from paper_2305_07026_b300 import scenes
+    if args.workload == "batch":
+        return run_reference_batch(args, world)
     sc = scenes.make_scene(args.workload, scale=args.scale)
     per_step = max(0.2, min(1.5, 150.0 / max(1, args.steps + args.warmup)))
     value, info = cpu_oracle(sc, per_step * args.steps, steps=args.steps, warmup=args.warmup)

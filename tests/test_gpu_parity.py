@@ -105,17 +105,21 @@ def _near_tie(info, which, tol=1e-9):
     return np.abs(E - Fb) <= tol * np.maximum(F, 1e-300)
 
 
-@pytest.mark.parametrize("loss,scale,accel,min_iters", [("huber", 2.0, True, 20), ("cauchy", 2.0, True, 20),
-                                                         ("trivial", 1.0, False, 20), ("welsch", 60.0, True, 20)])
-def test_fp64_matches_oracle_per_iteration(loss, scale, accel, min_iters, circle):
+@pytest.mark.parametrize("workload,loss,scale,accel,min_iters", [
+    ("circle", "huber", 2.0, True, 20), ("circle", "cauchy", 2.0, True, 20), ("circle", "trivial", 1.0, False, 20),
+    ("circle", "welsch", 60.0, True, 20), ("street", "cauchy", 2.0, True, 20), ("tourism", "huber", 1.0, True, 20)])
+def test_fp64_matches_oracle_per_iteration(workload, loss, scale, accel, min_iters, circle):
     """Per-iteration F(x^k), block metrics F^alpha / Fbar^alpha, restart decisions and the iterate.
 
     A restart decision may differ only at a near-tie. With a redescending loss (Welsch) whose scale
     is far below the residuals every observation of a block can saturate; its gradient is then zero
     and the restart test an exact tie, after which the two (equally valid) trajectories separate, so
     the comparison stops at the first tie (it must not come before `min_iters`). The Welsch scale
-    here is above the ~20 px residuals of the initial iterate, so no block saturates."""
-    sc = circle
+    here is above the ~20 px residuals of the initial iterate, so no block saturates. Besides the
+    circle workload: the street workload (Cauchy, facades along a street grid, 50 cameras) and the
+    tourism workload (power-law tracks, 60 cameras), both scaled down so that the oracle runs in
+    seconds."""
+    sc = circle if workload == "circle" else cached_scene(workload, scale={"street": 0.05, "tourism": 0.005}[workload])
     K = 20
     o = _oracle_opts(sc, loss=loss, loss_scale_px=scale, accelerated=accel)
     prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
@@ -182,7 +186,7 @@ def test_duba_monotone_gpu():
 # mixed path: reaches the FP64 objective
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("workload,scale,iters", [("circle", 1.0, 200), ("tourism", 0.005, 150)])
+@pytest.mark.parametrize("workload,scale,iters", [("circle", 1.0, 200), ("tourism", 0.005, 150), ("street", 0.05, 150)])
 def test_mixed_reaches_fp64_objective(workload, scale, iters):
     sc = cached_scene(workload, scale=scale)
     out = {}
