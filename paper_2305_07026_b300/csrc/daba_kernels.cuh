@@ -198,7 +198,7 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-constexpr int CPASS_STAGES = 4;   // batches of 32 observations in flight per warp
+constexpr int CPASS_STAGES = 3;   // batches of 32 observations in flight per warp
 
 // Third landmark-side record of an observation: FP64 path (F_ij(x^k), surrogate gap); MIXED
 // the gap only (F_ij only enters the FP64 path's per-landmark diagnostics).
