@@ -335,7 +335,7 @@ cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
 cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
-  const int blocks = (ctx->M + CAMSOLVE_THREADS - 1) / CAMSOLVE_THREADS;
+  const int blocks = (ctx->M + 31) / 32;   // 32 cameras per CTA (two warps)
   if (is_mixed(ctx))
     k_camsolve<float><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,

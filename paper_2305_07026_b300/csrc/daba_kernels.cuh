@@ -819,62 +819,97 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
                double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
                double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs, double* __restrict__ cam_Fsum,
                V4<Real>* __restrict__ pack_next) {
+  // 32 cameras per CTA, two warps: warp 0 takes the accelerated solve (Eq. update_amm) and
+  // the restart test, warp 1 the MM solve (Eq. update_mm) of the same cameras; the MM solve is
+  // computed whether or not the camera restarts, so that the two FP64 chains run side by side
+  // instead of one after the other. Warp 1 hands its solution to warp 0 through shared memory.
+  static_assert(CAMSOLVE_THREADS == 64, "two warps per CTA");
   using T = double;
   using N = Num<T>;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
+  __shared__ T sh_mm[32][16];   // MM solution R(9) t(3) d(3) and its dEn
+  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + lane;
+  const bool valid = i < M;
   const int it = *P.it;
-  const T gamma = N::from(P.gam[it]);
-  const int first = *P.first;
-  const int c0 = cam_chunk_ptr[i], c1 = cam_chunk_ptr[i + 1];
-  double* x = cam_x + (size_t)i * CSTRIDE;
-  double* dx = cam_dx + (size_t)i * CSTRIDE;
-  CamT<T> ck, cb;
-  T dx2 = N::c(0.f);
+  const T xi = N::from(P.xi);
+  CamT<T> ck, cn;
+  T st[39];
+  int c0 = 0, c1 = 0;
+  double *x = nullptr, *dx = nullptr;
+  T dx2 = N::c(0.f), dEn = N::c(0.f);
+  if (valid) {
+    c0 = cam_chunk_ptr[i];
+    c1 = cam_chunk_ptr[i + 1];
+    x = cam_x + (size_t)i * CSTRIDE;
+    dx = cam_dx + (size_t)i * CSTRIDE;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) ck.R[a] = N::from(x[CS_R + a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ck.t[a] = N::from(x[CS_T + a]);
+      ck.d[a] = N::from(x[CS_D + a]);
+    }
+    if (role == 1) {   // MM solve from x^k with the x^k statistics
+      sum_stats<Real, T>(part, c0, c1, PART_XK, st);
+      CamT<T> cm;
+      cam_scam(st, ck, xi, P.n_alt, cm);
+      const T dm = cam_phi(st, ck, cm, xi);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) sh_mm[lane][a] = cm.R[a];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sh_mm[lane][9 + a] = cm.t[a];
+        sh_mm[lane][12 + a] = cm.d[a];
+      }
+      sh_mm[lane][15] = dm;
+    } else if (P.accelerated) {   // accelerated solve from xbar^k with the xbar statistics
+      const T gamma = N::from(P.gam[it]);
+      CamT<T> cb;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) cb.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        cb.t[a] = ck.t[a] + gamma * N::from(dx[CS_T + a]);
+        cb.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
+      }
+      sum_stats<Real, T>(part, c0, c1, PART_XB, st);
+      cam_scam(st, cb, xi, P.n_alt, cn);
+      sum_stats<Real, T>(part, c0, c1, PART_XK, st);
+      dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
+    }
+  }
+  __syncthreads();
+  if (role != 0 || !valid) return;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    ck.R[a] = N::from(x[CS_R + a]);
-    cb.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
     const T d = N::from(dx[CS_R + a]);
     dx2 = dx2 + d * d;
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    ck.t[a] = N::from(x[CS_T + a]);
-    ck.d[a] = N::from(x[CS_D + a]);
     const T dt = N::from(dx[CS_T + a]), dd = N::from(dx[CS_D + a]);
-    cb.t[a] = ck.t[a] + gamma * dt;
-    cb.d[a] = ck.d[a] + gamma * dd;
     dx2 = dx2 + dt * dt + dd * dd;
   }
-  const T xi = N::from(P.xi);
-  // one statistics set is live at a time: the xbar set for the accelerated solve, then the
-  // x^k set for the restart test and the MM re-solve
-  T st[39];
-  CamT<T> cn;
-  if (P.accelerated) {
-    sum_stats<Real, T>(part, c0, c1, PART_XB, st);
-    cam_scam(st, cb, xi, P.n_alt, cn);   // Eq. update_amm
-  }
-  sum_stats<Real, T>(part, c0, c1, PART_XK, st);
   T sF = N::c(0.f), sG = N::c(0.f);
   for (int c = c0; c < c1; ++c) {
     acc_add(sF, part[(size_t)c * CP_STRIDE + PART_F]);
     acc_add(sG, part[(size_t)c * CP_STRIDE + PART_G]);
   }
   // Eq. DEalpha and the slack form of Eqs. Fak, lFak (see k_lpass)
+  const int first = *P.first;
   const T dE = N::c(-0.5f) * xi * dx2 + N::c(0.5f) * sG;
   const T S = first ? N::c(0.f) : N::from(cam_S[i]);
   const T thr = N::from(P.eta1) * (S - dE);
-  T dEn = N::c(0.f);
-  bool rs = true;
-  if (P.accelerated) {
-    dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
-    rs = dEn > thr;
-  }
-  if (rs) {
-    cam_scam(st, ck, xi, P.n_alt, cn);   // Eq. update_mm
-    dEn = cam_phi(st, ck, cn, xi);
+  const bool rs = P.accelerated ? (dEn > thr) : true;
+  if (rs) {   // restart: the MM solution of warp 1
+#pragma unroll
+    for (int a = 0; a < 9; ++a) cn.R[a] = sh_mm[lane][a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cn.t[a] = sh_mm[lane][9 + a];
+      cn.d[a] = sh_mm[lane][12 + a];
+    }
+    dEn = sh_mm[lane][15];
   }
   const T E = first ? N::c(0.5f) * sF : N::from(cam_E[i]);
   const T F = E + dE;
