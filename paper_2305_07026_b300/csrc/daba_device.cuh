@@ -463,6 +463,77 @@ __device__ inline void proj_rot3d_polar(const T* __restrict__ K, T* __restrict__
   proj_rot3d(K, R);
 }
 
+// ProjRot3D(K) for det K > 0 from a rotation Q0 near the answer (the previous R-step's
+// rotation or the conditioning rotation R_z). Newton's method on f(Q) = tr(Q^T K) over SO(3):
+// with B = Q^T K, f(Q Exp(w)) = tr B + w . b - w^T H w / 2 + O(|w|^3),
+//   b = (B21 - B12, B02 - B20, B10 - B01),  H = tr(B) I - (B + B^T) / 2,
+// so the step solves H w = b (Cramer's rule) and Q <- Q Cay(w), the rotation of the
+// quaternion (1, w/2) (equal to Exp(w) to second order, so the convergence stays quadratic).
+// A fixed point has B = Q^T K symmetric; with H positive definite (leading minors checked) and
+// det K > 0 it is positive definite, so Q is the polar factor: the maximiser. Once |w| <
+// 1e-10 the next iterate is exact to rounding. Returns false (R untouched) if a step fails the
+// checks or 8 steps do not settle; the caller then uses proj_rot3d_polar.
+template <class T>
+__device__ inline bool proj_rot3d_from(const T* __restrict__ K, const T* __restrict__ Q0, T* __restrict__ R) {
+  using N = Num<T>;
+  using S = typename N::S;
+  const T detK = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) +
+                 K[2] * (K[3] * K[7] - K[4] * K[6]);
+  if (!N::pos(detK)) return false;
+  T Q[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) Q[a] = Q0[a];
+  for (int it = 0; it < 8; ++it) {
+    T B[9];   // Q^T K
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) B[r * 3 + c] = Q[0 * 3 + r] * K[0 * 3 + c] + Q[1 * 3 + r] * K[1 * 3 + c] + Q[2 * 3 + r] * K[2 * 3 + c];
+    const T b0 = B[7] - B[5], b1 = B[2] - B[6], b2 = B[3] - B[1];
+    const T tr = B[0] + B[4] + B[8];
+    const T h00 = tr - B[0], h11 = tr - B[4], h22 = tr - B[8];
+    const T h01 = N::c(-0.5f) * (B[1] + B[3]), h02 = N::c(-0.5f) * (B[2] + B[6]), h12 = N::c(-0.5f) * (B[5] + B[7]);
+    // Cramer's rule with the leading minors as the positive-definiteness test
+    const T m1 = h00 * h11 - h01 * h01;
+    const T c00 = h11 * h22 - h12 * h12, c01 = h02 * h12 - h01 * h22, c02 = h01 * h12 - h02 * h11;
+    const T c11 = h00 * h22 - h02 * h02, c12 = h01 * h02 - h00 * h12;
+    const T det = h00 * c00 + h01 * c01 + h02 * c02;
+    if (!N::pos(h00) || !N::pos(m1) || !N::pos(det)) return false;
+    const T id = N::rcp(det);
+    const T w0 = (c00 * b0 + c01 * b1 + c02 * b2) * id;
+    const T w1 = (c01 * b0 + c11 * b1 + c12 * b2) * id;
+    const T w2 = (c02 * b0 + c12 * b1 + m1 * b2) * id;
+    // Q <- Q Cay(w), quaternion (1, w/2) normalised through 1 / (1 + |w|^2/4)
+    const T x = N::c(0.5f) * w0, y = N::c(0.5f) * w1, z = N::c(0.5f) * w2;
+    const T xx = x * x, yy = y * y, zz = z * z;
+    const T in = N::rcp(N::c(1.0f) + xx + yy + zz);
+    T C[9];
+    C[0] = (N::c(1.0f) + xx - yy - zz) * in;
+    C[1] = N::c(2.0f) * (x * y - z) * in;
+    C[2] = N::c(2.0f) * (x * z + y) * in;
+    C[3] = N::c(2.0f) * (x * y + z) * in;
+    C[4] = (N::c(1.0f) - xx + yy - zz) * in;
+    C[5] = N::c(2.0f) * (y * z - x) * in;
+    C[6] = N::c(2.0f) * (x * z - y) * in;
+    C[7] = N::c(2.0f) * (y * z + x) * in;
+    C[8] = (N::c(1.0f) - xx - yy + zz) * in;
+    T Qn[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Qn[r * 3 + c] = Q[r * 3 + 0] * C[0 * 3 + c] + Q[r * 3 + 1] * C[1 * 3 + c] + Q[r * 3 + 2] * C[2 * 3 + c];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Q[a] = Qn[a];
+    const S ww = N::hi(w0 * w0 + w1 * w1 + w2 * w2);
+    if (ww < S(1e-20)) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) R[a] = Q[a];
+      return true;
+    }
+  }
+  return false;
+}
+
 // ProjRot3D of a matrix K close to a rotation (the extrapolation R + gamma dR of
 // Eq. nesterov_R): for det K > 0 the projection is the orthogonal polar factor of K, reached
 // by the Newton-Schulz iteration X <- X (3 I - X^T X) / 2, which converges quadratically when

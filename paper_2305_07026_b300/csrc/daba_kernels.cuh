@@ -670,7 +670,14 @@ __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, 
       K[r * 3 + 1] = xi * z.R[r * 3 + 1] + N::c(2.0f) * G[r][1];
       K[r * 3 + 2] = xi * z.R[r * 3 + 2] + N::c(2.0f) * (c.d[0] * G[r][2] + c.d[1] * G[r][3] + c.d[2] * G[r][4]);
     }
-    proj_rot3d_polar(K, c.R);
+    // warm start from the rotation of the previous alternation (first: the conditioning one)
+    T Rn[9];
+    if (proj_rot3d_from(K, c.R, Rn)) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) c.R[a] = Rn[a];
+    } else {
+      proj_rot3d_polar(K, c.R);
+    }
     // ---- (t, d)-step
     const T v[3] = {c.R[2], c.R[5], c.R[8]};
     const T vz[3] = {z.R[2], z.R[5], z.R[8]};
