@@ -589,46 +589,6 @@ __device__ inline void proj_rot3d_near(const T* __restrict__ K, T* __restrict__ 
   }
 }
 
-// Solves the symmetric positive definite 6x6 system A x = b in place (A lower
-// triangle used, Cholesky A = L L^T; the diagonal keeps 1 / L[j][j]). Returns false if a
-// pivot is not positive.
-template <class T>
-__device__ inline bool chol6_solve(T A[6][6], T b[6]) {
-  using N = Num<T>;
-#pragma unroll
-  for (int j = 0; j < 6; ++j) {
-    T djj = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) djj = djj - A[j][k] * A[j][k];
-    if (!N::pos(djj)) return false;
-    const T inv = N::rsqrt(djj);   // 1 / L[j][j]
-    A[j][j] = inv;
-#pragma unroll
-    for (int i = j + 1; i < 6; ++i) {
-      T s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s = s - A[i][k] * A[j][k];
-      A[i][j] = s * inv;
-    }
-  }
-  // A[j][j] now holds 1 / L[j][j]
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    T s = b[i];
-#pragma unroll
-    for (int k = 0; k < i; ++k) s = s - A[i][k] * b[k];
-    b[i] = s * A[i][i];
-  }
-#pragma unroll
-  for (int i = 5; i >= 0; --i) {
-    T s = b[i];
-#pragma unroll
-    for (int k = i + 1; k < 6; ++k) s = s - A[k][i] * b[k];
-    b[i] = s * A[i][i];
-  }
-  return true;
-}
-
 // ---------------------------------------------------------------------------
 // Boundary rotation parameterisation (host and device): axis-angle w <-> R.
 // ---------------------------------------------------------------------------

@@ -691,26 +691,8 @@ __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, 
       dM0[4][k] = z.d[2] * (v[k] - vz[k]);
       dM0[5][k] = N::c(0.f);
     }
-    T A[6][6], rhs[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) A[i][j] = N::c(0.f);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) A[k][k] = N::c(2.0f) * st_H(st, 5, 5) + xi;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        A[3 + m][k] = N::c(2.0f) * st_H(st, 2 + m, 5) * v[k];
-        A[k][3 + m] = A[3 + m][k];
-      }
-#pragma unroll
-    for (int m = 0; m < 3; ++m)
-#pragma unroll
-      for (int n = 0; n < 3; ++n)
-        A[3 + m][3 + n] = m == n ? N::c(2.0f) * st_H(st, 2 + m, 2 + n) + xi : N::c(2.0f) * st_H(st, 2 + m, 2 + n);
-    // top: dM0 H[:,5] + B[5,:];  bottom: H[2:5,:] (dM0^T v) + B[2:5,:] v
+    // right-hand side: top dM0 H[:,5] + B[5,:];  bottom H[2:5,:] (dM0^T v) + B[2:5,:] v
+    T rhs[6];
     T dv[6];
 #pragma unroll
     for (int a = 0; a < 6; ++a) dv[a] = dM0[a][0] * v[0] + dM0[a][1] * v[1] + dM0[a][2] * v[2];
@@ -728,11 +710,42 @@ __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, 
       for (int a = 0; a < 6; ++a) s = s + st_H(st, 2 + m, a) * dv[a];
       rhs[3 + m] = N::c(-2.0f) * s;
     }
-    if (chol6_solve(A, rhs)) {
+    // normal equations [alpha I, Bc; Bc^T, D] (dt, dd) = rhs with alpha = 2 H55 + xi,
+    // Bc = 2 v h^T (h = H[2:5,5]) and D = 2 H[2:5,2:5] + xi I: eliminate dt (Schur complement)
+    //   (D - (4 |v|^2 / alpha) h h^T) dd = rhs_d - (2 (v . rhs_t) / alpha) h,
+    //   dt = (rhs_t - 2 v (h . dd)) / alpha,
+    // a 3x3 solve (Cramer's rule; leading minors as the positive-definiteness test)
+    const T alpha = N::c(2.0f) * st_H(st, 5, 5) + xi;
+    if (N::pos(alpha)) {
+      const T ia = N::rcp(alpha);
+      const T h[3] = {st_H(st, 2, 5), st_H(st, 3, 5), st_H(st, 4, 5)};
+      const T vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      const T vr = v[0] * rhs[0] + v[1] * rhs[1] + v[2] * rhs[2];
+      const T f4 = N::c(4.0f) * vv * ia, f2 = N::c(2.0f) * vr * ia;
+      T Sm[3][3], r[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        c.t[k] = z.t[k] + rhs[k];
-        c.d[k] = z.d[k] + rhs[3 + k];
+      for (int m = 0; m < 3; ++m) {
+#pragma unroll
+        for (int n = 0; n < 3; ++n) Sm[m][n] = N::c(2.0f) * st_H(st, 2 + m, 2 + n) - f4 * h[m] * h[n];
+        Sm[m][m] = Sm[m][m] + xi;
+        r[m] = rhs[3 + m] - f2 * h[m];
+      }
+      const T m1 = Sm[0][0] * Sm[1][1] - Sm[0][1] * Sm[0][1];
+      const T c00 = Sm[1][1] * Sm[2][2] - Sm[1][2] * Sm[1][2], c01 = Sm[0][2] * Sm[1][2] - Sm[0][1] * Sm[2][2];
+      const T c02 = Sm[0][1] * Sm[1][2] - Sm[0][2] * Sm[1][1], c11 = Sm[0][0] * Sm[2][2] - Sm[0][2] * Sm[0][2];
+      const T c12 = Sm[0][1] * Sm[0][2] - Sm[0][0] * Sm[1][2];
+      const T det = Sm[0][0] * c00 + Sm[0][1] * c01 + Sm[0][2] * c02;
+      if (N::pos(Sm[0][0]) && N::pos(m1) && N::pos(det)) {
+        const T id = N::rcp(det);
+        const T y0 = (c00 * r[0] + c01 * r[1] + c02 * r[2]) * id;
+        const T y1 = (c01 * r[0] + c11 * r[1] + c12 * r[2]) * id;
+        const T y2 = (c02 * r[0] + c12 * r[1] + m1 * r[2]) * id;
+        const T hy = N::c(2.0f) * (h[0] * y0 + h[1] * y1 + h[2] * y2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.t[k] = z.t[k] + (rhs[k] - v[k] * hy) * ia;
+        c.d[0] = z.d[0] + y0;
+        c.d[1] = z.d[1] + y1;
+        c.d[2] = z.d[2] + y2;
       }
     }
   }
