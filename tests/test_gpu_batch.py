@@ -98,3 +98,31 @@ def test_scene_partition_is_validated():
     d.set_scenes(b.cam_begin)
     assert d.scene_objectives().shape == (2,)
     d.close()
+
+
+def test_large_batch_equals_separate_runs():
+    """4,400 five-camera scenes (22,000 cameras: more camera-solve CTAs than one wave holds);
+    sampled scenes equal their separate runs bit for bit."""
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch, scenes
+    scs = [scenes.small_scene(1000 + i, 5, 60) for i in range(4400)]
+    b = batch.merge(scs)
+    K = 6
+    d = _ctx(L, b.M, b.N, b.nnz, "mixed")
+    d.set_observations(b.cam_idx, b.lm_idx, b.uv)
+    d.set_state(b.cams, b.lms)
+    d.set_scenes(b.cam_begin)
+    d.run(K)
+    cams, lms = d.get_state()
+    d.close()
+    parts = batch.split(b, cams, lms)
+    for i in range(0, len(scs), 440):
+        sc = scs[i]
+        e = _ctx(L, sc.M, sc.N, sc.nnz, "mixed")
+        e.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        e.set_state(sc.cams, sc.lms)
+        e.run(K)
+        c1, l1 = e.get_state()
+        e.close()
+        np.testing.assert_array_equal(parts[i][0], c1, err_msg=f"scene {i}")
+        np.testing.assert_array_equal(parts[i][1], l1, err_msg=f"scene {i}")
