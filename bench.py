@@ -429,8 +429,11 @@ def run_batch(args, rank, world, local):
     sp = stream.cuda_stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     opts = dict(loss="huber", loss_scale_px=1.0, prec="mixed", pixel_scale=650.0)
+    # schedule autotuning (untimed setup): chunk and tile sizes by coordinate descent
+    from paper_2305_07026_b300 import autotune
+    sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv, opts)
 
-    d = L.Daba(b.M, b.N, b.nnz, **opts)
+    d = L.Daba(b.M, b.N, b.nnz, **opts, **sched)
     d.set_observations(b.cam_idx, b.lm_idx, b.uv, stream=sp)
     d.set_scenes(b.cam_begin)
     d.set_state(b.cams, b.lms, stream=sp)
@@ -483,6 +486,7 @@ def run_batch(args, rank, world, local):
                                f"{b.nnz} observations", "M": b.M, "N": b.N, "nnz": b.nnz, "prec": "mixed",
                    "parallelism": f"replicas x{world}", "l2": "working set > 126 MB L2, no flush"},
         "obs_updates_per_s": world * b.nnz * K / (ms / 1e3),
+        "schedule": {"chosen": sched, "ms_per_iteration_tried": tried},
         "latency_ms": {"p50": ms, "p99": ms, "note": "every scene of the batch completes with the batch"},
         "separate": {"value": n / (sep_ms.sum() / 1e3), "unit": "scenes/s",
                      "isolated_ms": {"p50": float(np.percentile(sep_ms, 50)), "p99": float(np.percentile(sep_ms, 99))},

@@ -72,6 +72,12 @@ typedef struct {
   int cam_alternations;   /* R-step / (t,d)-step alternations of the camera block solve (default 2) */
   double pixel_scale;     /* s_norm in pixels; 0 = median focal length of the first state set */
   daba_precision prec;
+  /* work schedule (0 = default; results do not depend on it except for the order of FP
+   * sums): observations per camera-pass chunk (32..65536, default 1024), observations per
+   * landmark tile (32..2048, default 512) and landmarks per tile (1..128, default 128). */
+  int32_t chunk_obs;
+  int32_t tile_obs;
+  int32_t tile_lms;
 } daba_options;
 
 typedef struct daba_ctx daba_ctx;

@@ -30,7 +30,8 @@ lib = ctypes.CDLL(LIB_PATH)
 class daba_options(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_int), ("loss_scale_px", ctypes.c_double), ("xi", ctypes.c_double),
                 ("eta", ctypes.c_double), ("accelerated", ctypes.c_int), ("cam_alternations", ctypes.c_int),
-                ("pixel_scale", ctypes.c_double), ("prec", ctypes.c_int)]
+                ("pixel_scale", ctypes.c_double), ("prec", ctypes.c_int), ("chunk_obs", ctypes.c_int32),
+                ("tile_obs", ctypes.c_int32), ("tile_lms", ctypes.c_int32)]
 
 
 _p = ctypes.c_void_p
@@ -100,7 +101,7 @@ def current_stream():
 
 
 def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True, cam_alternations=2,
-            pixel_scale=0.0, prec="mixed") -> daba_options:
+            pixel_scale=0.0, prec="mixed", chunk_obs=0, tile_obs=0, tile_lms=0) -> daba_options:
     o = daba_options()
     daba_default_options(ctypes.byref(o))
     o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
@@ -111,6 +112,7 @@ def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True
     o.cam_alternations = int(cam_alternations)
     o.pixel_scale = float(pixel_scale)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.chunk_obs, o.tile_obs, o.tile_lms = int(chunk_obs), int(tile_obs), int(tile_lms)
     return o
 
 

@@ -1,0 +1,52 @@
+"""Schedule autotuner: picks the camera-pass chunk size and the landmark-tile sizes of a
+problem by timing a few iterations of each candidate on the GPU (coordinate descent: chunk,
+then observations per tile, then landmarks per tile). The schedule changes only how the work
+is cut into warps and CTAs, not the method (results differ at most in the order of FP sums).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CHUNKS = (512, 1024, 2048)
+TILE_OBS = (256, 512, 1024)
+TILE_LMS = (64, 128)
+
+
+def time_schedule(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2):
+    """Milliseconds per iteration of one schedule (CUDA events around ``iters`` iterations)."""
+    import torch
+    d = L.Daba(cams.shape[0], lms.shape[0], cam_idx.size, **opts, **sched)
+    try:
+        d.set_observations(cam_idx, lm_idx, uv)
+        d.set_state(cams, lms)
+        d.run(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        d.run(iters)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / iters
+    finally:
+        d.close()
+
+
+def tune(cams, lms, cam_idx, lm_idx, uv, opts=None, iters=8, log=None):
+    """Returns (best schedule dict, {schedule: ms per iteration}) for this problem."""
+    from paper_2305_07026_b300 import _lib as L
+    opts = dict(opts or {})
+    best = {"chunk_obs": 1024, "tile_obs": 512, "tile_lms": 128}
+    seen = {}
+
+    def measure(s):
+        key = (s["chunk_obs"], s["tile_obs"], s["tile_lms"])
+        if key not in seen:
+            seen[key] = time_schedule(L, cams, lms, cam_idx, lm_idx, uv, opts, s, iters)
+            if log:
+                log(f"schedule {key}: {seen[key]:.4f} ms/iteration")
+        return seen[key]
+
+    for name, cands in (("chunk_obs", CHUNKS), ("tile_obs", TILE_OBS), ("tile_lms", TILE_LMS)):
+        times = {c: measure(dict(best, **{name: c})) for c in cands}
+        best[name] = min(times, key=times.get)
+    return best, {f"{k[0]}/{k[1]}/{k[2]}": v for k, v in seen.items()}

@@ -24,7 +24,7 @@ using namespace daba;
 
 namespace {
 
-constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: observations per warp chunk
+constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: default observations per warp chunk
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
 constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
@@ -295,7 +295,7 @@ cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
 template <class Real, class Real2, bool HAS_LO>
 cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   const IterParams P = iter_params(ctx);
-  const int caps[2] = {TILE_OBS, BIG_TILE_OBS};
+  const int caps[2] = {ctx->opt.tile_obs, BIG_TILE_OBS};
   auto kern = k_lpass<Real, Real2, HAS_LO>;
   int t0 = 0;
   for (int c = 0; c < 2; ++c) {
@@ -506,6 +506,9 @@ void daba_default_options(daba_options* o) {
   o->cam_alternations = 2;
   o->pixel_scale = 0.0;
   o->prec = DABA_MIXED;
+  o->chunk_obs = 0;
+  o->tile_obs = 0;
+  o->tile_lms = 0;
 }
 
 const char* daba_last_error(const daba_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -543,7 +546,13 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     ctx->opt = *opt;
   else
     daba_default_options(&ctx->opt);
-  const daba_options& o = ctx->opt;
+  daba_options& o = ctx->opt;
+  if (o.chunk_obs == 0) o.chunk_obs = CHUNK_OBS;
+  if (o.tile_obs == 0) o.tile_obs = TILE_OBS;
+  if (o.tile_lms == 0) o.tile_lms = TILE_LMS;
+  if (o.chunk_obs < 32 || o.chunk_obs > 65536 || o.tile_obs < 32 || o.tile_obs > BIG_TILE_OBS || o.tile_lms < 1 ||
+      o.tile_lms > LPASS_THREADS)
+    return bad("schedule");
   if (!(o.xi > 0) || !(o.eta > 0) || !(o.eta <= 1) || o.cam_alternations < 1 || o.cam_alternations > 64 ||
       (int)o.loss < 0 || (int)o.loss > 3 || !(o.pixel_scale >= 0) ||
       (o.loss != DABA_LOSS_TRIVIAL && !(o.loss_scale_px > 0)) || (o.prec != DABA_FP64 && o.prec != DABA_MIXED))
@@ -553,8 +562,8 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   ctx->nnz = nnz;
   cudaGetDevice(&ctx->dev);
   const size_t R = real_sz(ctx);
-  ctx->max_chunks = (int)(M + nnz / CHUNK_OBS + 1);
-  ctx->max_tiles = (int)(2 * (nnz / TILE_OBS + N / TILE_LMS) + nnz / TILE_OBS + 8);
+  ctx->max_chunks = (int)(M + nnz / o.chunk_obs + 1);
+  ctx->max_tiles = (int)(2 * (nnz / o.tile_obs + N / o.tile_lms) + nnz / o.tile_obs + 8);
 #define AL(field, bytes)                                   \
   if ((st = dalloc(ctx, &ctx->field, (bytes))) != DABA_OK) { \
     daba_ctx* c_ = ctx;                                    \
@@ -680,7 +689,8 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   for (int64_t o = 0; o < n; ++o) min_cam[li[o]] = std::min(min_cam[li[o]], ci[o]);
   // tile class of a landmark: 0 = at most TILE_OBS observations (small tiles),
   // 1 = longer (a tile of its own)
-  auto lclass = [&](int j) { return lm_ptr[j + 1] - lm_ptr[j] <= TILE_OBS ? 0 : 1; };
+  const int tile_obs = ctx->opt.tile_obs, tile_lms = ctx->opt.tile_lms, chunk_obs = ctx->opt.chunk_obs;
+  auto lclass = [&](int j) { return lm_ptr[j + 1] - lm_ptr[j] <= tile_obs ? 0 : 1; };
   std::vector<int32_t> lperm(N), linv(N);
   for (int j = 0; j < N; ++j) lperm[j] = j;
   std::stable_sort(lperm.begin(), lperm.end(), [&](int32_t a, int32_t b) {
@@ -709,7 +719,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   std::vector<int32_t> chunk_cam, chunk_beg, cam_chunk_ptr(M + 1, 0);
   for (int i = 0; i < M; ++i) {
     cam_chunk_ptr[i] = (int32_t)chunk_cam.size();
-    for (int b = cam_ptr[i]; b < cam_ptr[i + 1]; b += CHUNK_OBS) {
+    for (int b = cam_ptr[i]; b < cam_ptr[i + 1]; b += chunk_obs) {
       chunk_cam.push_back(i);
       chunk_beg.push_back(b);
     }
@@ -728,7 +738,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
         int j2 = j, cnt = 0;
         while (j2 < N && lclass(lperm[j2]) == c) {
           const int dg = lmi_ptr[j2 + 1] - lmi_ptr[j2];
-          if (j2 > j && (c == 1 || j2 - j >= TILE_LMS || cnt + dg > TILE_OBS)) break;
+          if (j2 > j && (c == 1 || j2 - j >= tile_lms || cnt + dg > tile_obs)) break;
           cnt += dg;
           ++j2;
         }

@@ -126,3 +126,29 @@ def test_large_batch_equals_separate_runs():
         e.close()
         np.testing.assert_array_equal(parts[i][0], c1, err_msg=f"scene {i}")
         np.testing.assert_array_equal(parts[i][1], l1, err_msg=f"scene {i}")
+
+
+def test_schedule_changes_only_sum_order():
+    """Other chunk and tile sizes give the same iteration up to the order of FP64 sums, and the
+    autotuner returns one of its candidates with a time for each schedule it tried."""
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import autotune
+    from tests.conftest import cached_scene
+    sc = cached_scene("tourism", scale=0.005)
+    traces = []
+    for sched in ({}, {"chunk_obs": 96, "tile_obs": 64, "tile_lms": 7}, {"chunk_obs": 4096, "tile_obs": 2048}):
+        d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64", **sched)
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        tr = np.zeros(11)
+        d.run(10, tr)
+        d.close()
+        traces.append(tr)
+    np.testing.assert_allclose(traces[1], traces[0], rtol=1e-10)
+    np.testing.assert_allclose(traces[2], traces[0], rtol=1e-10)
+    best, tried = autotune.tune(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv,
+                                dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px), iters=3)
+    assert best["chunk_obs"] in autotune.CHUNKS and best["tile_obs"] in autotune.TILE_OBS
+    assert len(tried) >= 6 and all(v > 0 for v in tried.values())
+    with pytest.raises(L.DabaError):
+        L.Daba(sc.M, sc.N, sc.nnz, tile_lms=129)
