@@ -9,11 +9,13 @@
 //   2. lpass     (CTA/tile)   : per landmark, sums its records and runs the restart metrics,
 //                               accelerated solve, restart test and MM re-solve (closed form);
 //                               writes the other landmark buffer.
-//   3. camsolve  (M threads)  : FP64 camera block solves, restart test, MM re-solve, and the
-//                               extrapolated rotation and pack of iteration k+1.
+//   3. camsolve  (2 warps per 32 cameras): FP64 camera block solves, the accelerated and the
+//                               MM solve side by side, restart test, and the extrapolated
+//                               rotation and pack of iteration k+1.
 //   4. finalize  (grid)       : F(x^k) trace entry and restart count (deterministic order).
 // lpass and camsolve both only need cpass, so they run concurrently (camsolve, the
-// latency-bound FP64 path, on the higher-priority stream).
+// latency-bound FP64 path, on the higher-priority stream). Kernel launch order and the
+// streams are set by the host runtime (daba_abi.cu).
 // cam_prepare builds the pack of the first iteration of a run.
 //
 // Centred statistics. For a conditioning iterate z (xbar^k or x^k) and a camera c let
@@ -81,63 +83,6 @@ template <>
 __device__ __forceinline__ double hxi_of<double>(const IterParams& P) { return P.hxi; }
 
 __device__ __forceinline__ int tri6(int a, int b) { return a * 6 - (a * (a - 1)) / 2 + (b - a); }
-
-// Writes the pass pack of one camera from its FP64 state, its displacement and Rbar.
-template <class Real>
-__device__ __forceinline__ void write_pack(const double* x, const double* dx, const double* Rb, V4<Real>* pk) {
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    Real th, tl;
-    split_real(x[CS_T + r], th, tl);
-    V4<Real> a, b, g;
-    a.x = to_real<Real>(x[CS_R + 3 * r + 0]);
-    a.y = to_real<Real>(x[CS_R + 3 * r + 1]);
-    a.z = to_real<Real>(x[CS_R + 3 * r + 2]);
-    a.w = th;
-    b.x = to_real<Real>(Rb[3 * r + 0]);
-    b.y = to_real<Real>(Rb[3 * r + 1]);
-    b.z = to_real<Real>(Rb[3 * r + 2]);
-    b.w = to_real<Real>(dx[CS_T + r]);
-    g.x = to_real<Real>(dx[CS_R + 3 * r + 0]);
-    g.y = to_real<Real>(dx[CS_R + 3 * r + 1]);
-    g.z = to_real<Real>(dx[CS_R + 3 * r + 2]);
-    g.w = tl;
-    pk[P4_RK + r] = a;
-    pk[P4_RB + r] = b;
-    pk[P4_DR + r] = g;
-  }
-  V4<Real> d, e;
-  d.x = to_real<Real>(x[CS_D + 0]);
-  d.y = to_real<Real>(x[CS_D + 1]);
-  d.z = to_real<Real>(x[CS_D + 2]);
-  d.w = Real(0);
-  e.x = to_real<Real>(dx[CS_D + 0]);
-  e.y = to_real<Real>(dx[CS_D + 1]);
-  e.z = to_real<Real>(dx[CS_D + 2]);
-  e.w = Real(0);
-  pk[P4_D] = d;
-  pk[P4_DD] = e;
-}
-
-// ---------------------------------------------------------------------------
-// camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) (Eq. nesterov_R) and the pack
-// ---------------------------------------------------------------------------
-template <class Real>
-__global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const double* __restrict__ cam_dx,
-                              IterParams P, double* __restrict__ cam_Rbar, V4<Real>* __restrict__ pack) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const double gamma = P.gam[*P.it];
-  const double* x = cam_x + (size_t)i * CSTRIDE;
-  const double* dx = cam_dx + (size_t)i * CSTRIDE;
-  double K[9], Rb[9];
-#pragma unroll
-  for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
-  proj_rot3d_near(K, Rb);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
-  write_pack<Real>(x, dx, Rb, pack + (size_t)i * P4N);
-}
 
 // ---------------------------------------------------------------------------
 // 1. camera-sorted pass: one warp per chunk (<= chunk size observations of one camera)
@@ -634,7 +579,8 @@ __device__ inline T cam_phi(const T* st, const CamT<T>& z, const CamT<T>& c, T x
 //   P(d) = [e1, e2, d1 e3, d2 e3, d3 e3, 0].
 // (t, d)-step: with R fixed, dM h = dM0 h + v (phi . dd) + lambda dt with v = R e3 and
 //   dM0 = M(R, t_z, d_z) - M(c_z); the normal equations of the resulting least squares
-//   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5] and are solved by Cholesky.
+//   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5]; they are solved through the 3x3 Schur
+//   complement of their scaled-identity dt block (below).
 template <class T>
 __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, CamT<T>& c) {
   using N = Num<T>;
@@ -829,9 +775,42 @@ __device__ __forceinline__ void write_pack_t(const CamT<double>& x, const CamT<d
   pk[P4_DD] = e;
 }
 
-// One thread per camera, in FP64: the statistics summed over the camera's chunks, the
-// accelerated S-CAM solve, the restart metrics and test, the MM re-solve, and the
-// extrapolated rotation and pack of iteration k+1.
+// ---------------------------------------------------------------------------
+// camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) (Eq. nesterov_R) and the pack
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const double* __restrict__ cam_dx,
+                              IterParams P, double* __restrict__ cam_Rbar, V4<Real>* __restrict__ pack) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double gamma = P.gam[*P.it];
+  const double* x = cam_x + (size_t)i * CSTRIDE;
+  const double* dx = cam_dx + (size_t)i * CSTRIDE;
+  double K[9], Rb[9];
+#pragma unroll
+  for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
+  proj_rot3d_near(K, Rb);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
+  CamT<double> cx, cdx;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    cx.R[a] = x[CS_R + a];
+    cdx.R[a] = dx[CS_R + a];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cx.t[a] = x[CS_T + a];
+    cdx.t[a] = dx[CS_T + a];
+    cx.d[a] = x[CS_D + a];
+    cdx.d[a] = dx[CS_D + a];
+  }
+  write_pack_t<Real>(cx, cdx, Rb, pack + (size_t)i * P4N);
+}
+
+// Camera block solves in FP64: the statistics summed over the camera's chunks, the
+// accelerated S-CAM solve, the restart metrics and test, the MM solve, and the extrapolated
+// rotation and pack of iteration k+1.
 template <class Real>
 __global__ void __launch_bounds__(CAMSOLVE_THREADS)
     k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
