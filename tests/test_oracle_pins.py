@@ -544,3 +544,36 @@ def test_boundary_gradient_fd(loss):
         h = 1e-3
         fd = (Fx(sc.cams + h * v, sc.lms, sc.uv) - Fx(sc.cams - h * v, sc.lms, sc.uv)) / (2 * h)
         assert np.sum(gc * v) == pytest.approx(fd, rel=1e-5, abs=1e-12 * abs(F)), k
+
+
+@pytest.mark.parametrize("loss,accel,K", [("huber", True, 6), ("cauchy", True, 12), ("trivial", False, 8)])
+def test_unrolled_gradient_fd(loss, accel, K):
+    """Gradient of a linear functional of the state after K iterations (autograd through the
+    PyTorch restatement of the update, restart decisions fixed) against FP64 central
+    differences of the numpy oracle's K-iteration map along random directions."""
+    from oracle import daba_unrolled as U
+    from paper_2305_07026_b300 import scenes
+    sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+    o = O.Options(loss=loss, loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0)
+    rng = np.random.default_rng(4)
+    g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
+    gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
+    cams_o, lms_o = O.boundary_state(res)
+    np.testing.assert_allclose(oc, cams_o, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(ol, lms_o, rtol=1e-9, atol=1e-9)
+
+    def J(c, l, u):
+        r = O.daba(c, l, sc.cam_idx, sc.lm_idx, u, o, K)
+        cc, ll = O.boundary_state(r)
+        return float(np.sum(cc * g_c) + np.sum(ll * g_l))
+
+    cscale = np.array([1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 0.5, 1e-4, 1e-6])
+    for part in range(3):
+        v = [np.zeros_like(sc.cams), np.zeros_like(sc.lms), np.zeros_like(sc.uv)]
+        v[part] = rng.normal(size=v[part].shape) * (cscale if part == 0 else (1e-3 if part == 1 else 1e-2))
+        # steps above the rounding noise of J and below the curvature of each part
+        h = (1e-3, 1e-2, 1e-2)[part]
+        fd = (J(sc.cams + h * v[0], sc.lms + h * v[1], sc.uv + h * v[2]) -
+              J(sc.cams - h * v[0], sc.lms - h * v[1], sc.uv - h * v[2])) / (2 * h)
+        an = np.sum(gc * v[0]) + np.sum(gl * v[1]) + np.sum(gu * v[2])
+        assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), part
