@@ -387,6 +387,25 @@ def run_ours(args, rank, world, local):
            "what": "per step: daba_set_state from pinned host, one iteration, objective and iterate "
                    "back to pinned host (observations set once beforehand)"}
 
+    # gradient of F w.r.t. cameras, landmarks and pixels (adjoint kernels), device outputs
+    dg = make("mixed")
+    g_c = torch.empty((sc.M, 9), dtype=torch.float64, device="cuda")
+    g_l = torch.empty((sc.N, 3), dtype=torch.float64, device="cuda")
+    g_u = torch.empty((sc.nnz, 2), dtype=torch.float64, device="cuda")
+    Fg = torch.empty(1, dtype=torch.float64, device="cuda")
+    dg.objective_grad(Fg, g_c, g_l, g_u, stream=sp)
+    ng = 5
+    e0.record(stream)
+    for _ in range(ng):
+        dg.objective_grad(Fg, g_c, g_l, g_u, stream=sp)
+    e1.record(stream)
+    e1.synchronize()
+    ms_g = e0.elapsed_time(e1) / ng
+    dg.close()
+    grad = {"what": "daba_objective_grad: F and dF/d(cameras, landmarks, pixels), MIXED, device outputs "
+                    "(includes the prepare kernel and the host synchronisation of the call)",
+            "ms": ms_g, "obs_per_s": sc.nnz / (ms_g / 1e3)}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         _, cpu = cpu_oracle(sc, args.cpu_seconds)
@@ -406,7 +425,7 @@ def run_ours(args, rank, world, local):
                       "mixed_speedup": value / world / fp64_value},
         "accuracy": accuracy,
         "kernel_ms_per_launch": per_launch_ms,
-        "roofline": roofline, "roofline_kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "roofline_kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gradient": grad,
         "gpu_launches": int(launches),
         "clocks": ck,
     }
