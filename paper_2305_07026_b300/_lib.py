@@ -49,6 +49,7 @@ _SIGS = {
     "daba_set_scenes": (_st, [_p, _i32, _p]),
     "daba_objective_grad": (_st, [_p, _p, _p, _p, _p, _p]),
     "daba_set_pixels": (_st, [_p, _p, _p]),
+    "daba_unrolled_grad": (_st, [_p, _i32, _p, _p, _p, _p, _p, _p]),
     "daba_scene_objectives": (_st, [_p, _p, _p]),
     "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
@@ -199,6 +200,20 @@ class Daba:
         self._check(daba_objective_grad(self._h, ptr(F), ptr(g_cams), ptr(g_lms), ptr(g_uv),
                                         current_stream() if stream is None else stream))
         return F, g_cams, g_lms, g_uv
+
+    def unrolled_grad(self, K, seed_cams, seed_lms, g_cams=None, g_lms=None, g_uv=None, stream=None):
+        """Vector-Jacobian product of K iterations from the state last set: the gradient of
+        <seed_cams, cams_K> + <seed_lms, lms_K> w.r.t. the set cameras (M x 9), landmarks
+        (N x 3) and pixels (nnz x 2). Leaves the state after K iterations. With no output
+        arguments, host arrays are returned."""
+        host = g_cams is None and g_lms is None and g_uv is None
+        if host:
+            g_cams, g_lms, g_uv = np.zeros((self.M, 9)), np.zeros((self.N, 3)), np.zeros((self.nnz, 2))
+            seed_cams = np.ascontiguousarray(seed_cams, dtype=np.float64)
+            seed_lms = np.ascontiguousarray(seed_lms, dtype=np.float64)
+        self._check(daba_unrolled_grad(self._h, int(K), ptr(seed_cams), ptr(seed_lms), ptr(g_cams), ptr(g_lms),
+                                       ptr(g_uv), current_stream() if stream is None else stream))
+        return g_cams, g_lms, g_uv
 
     def set_pixels(self, uv, stream=None):
         self._check(daba_set_pixels(self._h, ptr(uv), current_stream() if stream is None else stream))

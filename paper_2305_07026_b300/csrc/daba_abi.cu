@@ -18,7 +18,7 @@
 #include "../../include/daba.h"
 #include "daba_kernels.cuh"
 #include "daba_state.cuh"
-#include "daba_grad.cuh"
+#include "daba_adjoint.cuh"
 
 using namespace daba;
 
@@ -88,6 +88,13 @@ struct daba_ctx {
   int n_scenes = 1;
   std::vector<int32_t> h_scene_cam;
   void *d_scene_chunk = nullptr, *d_scene_f = nullptr;
+  // reverse mode (daba_unrolled_grad), allocated at first use: adjoints of x^(k+1), x^k, x^(k-1)
+  // (cameras, landmarks), of the two conditioning points, of the statistics, of the pixels,
+  // and copies of the iteration state
+  void *adj_c[3] = {nullptr, nullptr, nullptr}, *adj_l[3] = {nullptr, nullptr, nullptr};
+  void *zb_c[2] = {nullptr, nullptr}, *zb_l[2] = {nullptr, nullptr};
+  void *st_bar = nullptr, *ab_bar = nullptr, *g_u = nullptr;
+  std::vector<void*> slots;
 };
 
 namespace {
@@ -486,6 +493,178 @@ cudaError_t launch_grad_by_loss(daba_ctx* ctx, cudaStream_t st) {
     case DABA_LOSS_HUBER: return launch_grad_t<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st);
     case DABA_LOSS_CAUCHY: return launch_grad_t<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st);
     default: return launch_grad_t<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st);
+  }
+}
+
+// ---- reverse mode -----------------------------------------------------------
+constexpr int ADJ_CKPT = 10;   // iterations between the states kept by the forward sweep
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// A copy of everything an iteration reads besides the fixed setup: the camera state, its
+// restart slack and accumulated E, the landmark records and the first-iteration flag.
+struct SlotLayout {
+  size_t x, dx, S, E, lm, first, bytes;
+};
+SlotLayout slot_layout(const daba_ctx* c) {
+  SlotLayout L;
+  size_t o = 0;
+  L.x = o;
+  o = align256(o + (size_t)c->M * CSTRIDE * 8);
+  L.dx = o;
+  o = align256(o + (size_t)c->M * CSTRIDE * 8);
+  L.S = o;
+  o = align256(o + (size_t)c->M * 8);
+  L.E = o;
+  o = align256(o + (size_t)c->M * 8);
+  L.lm = o;
+  o = align256(o + (size_t)c->N * LREC * 8);
+  L.first = o;
+  o = align256(o + 16);
+  L.bytes = o;
+  return L;
+}
+
+daba_status ensure_adjoint(daba_ctx* ctx, size_t n_slots) {
+  daba_status s;
+  const size_t M = ctx->M, N = ctx->N;
+  if (!ctx->st_bar) {
+    for (int q = 0; q < 3; ++q) {
+      if ((s = dalloc(ctx, &ctx->adj_c[q], M * AC_N * 8)) != DABA_OK) return s;
+      if ((s = dalloc(ctx, &ctx->adj_l[q], N * AL_N * 8)) != DABA_OK) return s;
+    }
+    for (int q = 0; q < 2; ++q) {
+      if ((s = dalloc(ctx, &ctx->zb_c[q], M * AC_N * 8)) != DABA_OK) return s;
+      if ((s = dalloc(ctx, &ctx->zb_l[q], N * AL_N * 8)) != DABA_OK) return s;
+    }
+    if ((s = dalloc(ctx, &ctx->ab_bar, N * 4 * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->g_u, (size_t)ctx->nnz * 16)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->st_bar, M * 40 * 8)) != DABA_OK) return s;
+  }
+  const size_t b = slot_layout(ctx).bytes;
+  while (ctx->slots.size() < n_slots) {
+    void* p = nullptr;
+    if ((s = dalloc(ctx, &p, b)) != DABA_OK) return s;
+    ctx->slots.push_back(p);
+  }
+  return DABA_OK;
+}
+
+cudaError_t save_state(daba_ctx* ctx, void* slot, cudaStream_t st) {
+  const SlotLayout L = slot_layout(ctx);
+  char* b = (char*)slot;
+  const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b + L.x, ctx->cam_x, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(b + L.dx, ctx->cam_dx, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(b + L.S, ctx->cam_S, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b + L.E, ctx->cam_E, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b + L.lm, lmrec_at(ctx, ctx->k), (size_t)ctx->N * LREC * 8, cudaMemcpyDeviceToDevice,
+                           st)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(b + L.first, ctx->d_first, sizeof(int), cudaMemcpyDeviceToDevice, st);
+}
+
+// restores a copy taken at iteration k (the landmark records go to the buffer of k's parity)
+cudaError_t restore_state(daba_ctx* ctx, const void* slot, int64_t k, double s_k, cudaStream_t st) {
+  const SlotLayout L = slot_layout(ctx);
+  const char* b = (const char*)slot;
+  const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(ctx->cam_x, b + L.x, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(ctx->cam_dx, b + L.dx, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(ctx->cam_S, b + L.S, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(ctx->cam_E, b + L.E, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(lmrec_at(ctx, k), b + L.lm, (size_t)ctx->N * LREC * 8, cudaMemcpyDeviceToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  ctx->k = k;
+  ctx->s_k = s_k;
+  return cudaMemcpyAsync(ctx->d_first, b + L.first, sizeof(int), cudaMemcpyDeviceToDevice, st);
+}
+
+// n iterations from the current state with direct launches (as daba_run without its
+// synchronisation and objective trace)
+cudaError_t advance(daba_ctx* ctx, cudaStream_t st, int n) {
+  std::vector<double> gam((size_t)n + 1);
+  double sk = ctx->s_k;
+  for (int j = 0; j <= n; ++j) {
+    const double s_next = (std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0;
+    gam[j] = (sk - 1.0) / s_next;
+    sk = s_next;
+    if (j == n - 1) ctx->s_k = sk;
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(ctx->d_gam, gam.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = launch_prepare(ctx, st, ctx->k)) != cudaSuccess) return e;
+  if ((e = enqueue_iters(ctx, st, ctx->k, n, 0)) != cudaSuccess) return e;
+  ctx->k += n;
+  return cudaSuccess;
+}
+
+// The adjoint of iteration k, whose forward results (statistics, records, decisions, pass
+// pack) are in the live buffers; slot holds x^k and x^k - x^(k-1) of the cameras.
+// a1: adjoint of x^(k+1) (read); a0, am: adjoints of x^k and x^(k-1) (accumulated).
+template <int LOSS>
+cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot, int a1, int a0,
+                         int am) {
+  const SlotLayout Ly = slot_layout(ctx);
+  const double* sx = (const double*)((const char*)slot + Ly.x);
+  const double* sdx = (const double*)((const char*)slot + Ly.dx);
+  const int M = ctx->M, N = ctx->N;
+  const int acc = ctx->opt.accelerated;
+  const double xi = ctx->opt.xi;
+  cudaError_t e;
+  for (int q = 0; q < 2; ++q) {
+    if ((e = cudaMemsetAsync(ctx->zb_c[q], 0, (size_t)M * AC_N * 8, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ctx->zb_l[q], 0, (size_t)N * AL_N * 8, st)) != cudaSuccess) return e;
+  }
+  if (M > 0)
+    k_adj_cams<<<(M + 63) / 64, 64, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part, sx, sdx,
+                                             gamma, (const uint8_t*)ctx->cam_rs, acc, xi, ctx->opt.cam_alternations,
+                                             (const double*)ctx->adj_c[a1], (double*)ctx->st_bar,
+                                             (double*)ctx->zb_c[0], (double*)ctx->zb_c[1]);
+  if (ctx->n_tiles > 0)
+    k_adj_lms<<<ctx->n_tiles, LPASS_THREADS, 0, st>>>(
+        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<double>*)ctx->rec_a,
+        (const V4<double>*)ctx->rec_b, (const uint8_t*)ctx->lm_rs, acc, xi, (const double*)ctx->adj_l[a1],
+        (double*)ctx->ab_bar, (double*)ctx->zb_l[0], (double*)ctx->zb_l[1]);
+  // the records are consumed: rec_a / rec_b now take the landmark terms at xbar / x^k
+  if (ctx->n_chunks > 0)
+    k_adj_obs<LOSS><<<ctx->n_chunks, 32, 0, st>>>(
+        ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+        (const double2*)ctx->c_u, (const int*)ctx->c_rpos, (const int*)ctx->d_ci_order,
+        (const V4<double>*)pack_at(ctx, k), (const V4<double>*)lmrec_at(ctx, k), gamma, (const uint8_t*)ctx->cam_rs,
+        (const uint8_t*)ctx->lm_rs, acc, loss_consts<double>(ctx), 1.0 / ctx->s_norm, (const double*)ctx->st_bar,
+        (const double*)ctx->ab_bar, (double*)ctx->chunk_part, (V4<double>*)ctx->rec_a, (V4<double>*)ctx->rec_b,
+        (double2*)ctx->g_u);
+  if (M > 0)
+    k_adj_cams_sum<<<(M + 127) / 128, 128, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part,
+                                                    sx, sdx, gamma, (const double*)ctx->zb_c[0],
+                                                    (const double*)ctx->zb_c[1], (double*)ctx->adj_c[a0],
+                                                    (double*)ctx->adj_c[am]);
+  if (ctx->n_tiles > 0)
+    k_adj_lms_sum<<<ctx->n_tiles, LPASS_THREADS, 0, st>>>(
+        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<double>*)ctx->rec_a,
+        (const V4<double>*)ctx->rec_b, (const double*)ctx->zb_l[0], (const double*)ctx->zb_l[1], gamma,
+        (double*)ctx->adj_l[a0], (double*)ctx->adj_l[am]);
+  ctx->launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t adjoint_iter_by_loss(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot, int a1,
+                                 int a0, int am) {
+  switch (ctx->opt.loss) {
+    case DABA_LOSS_TRIVIAL: return adjoint_iter<LOSS_TRIVIAL>(ctx, st, k, gamma, slot, a1, a0, am);
+    case DABA_LOSS_HUBER: return adjoint_iter<LOSS_HUBER>(ctx, st, k, gamma, slot, a1, a0, am);
+    case DABA_LOSS_CAUCHY: return adjoint_iter<LOSS_CAUCHY>(ctx, st, k, gamma, slot, a1, a0, am);
+    default: return adjoint_iter<LOSS_WELSCH>(ctx, st, k, gamma, slot, a1, a0, am);
   }
 }
 
@@ -1093,6 +1272,119 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
     CK(cudaMemcpyAsync(g_uv, ctx->rec_b, (size_t)ctx->nnz * 16,
                        is_device_ptr(g_uv) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return DABA_OK;
+}
+
+daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
+                               double* g_cams, double* g_lms, double* g_uv, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (K < 1) return fail(ctx, DABA_ERR_ARG, "K must be >= 1");
+  if (!seed_cams || !seed_lms) return fail(ctx, DABA_ERR_ARG, "null seed pointer");
+  if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient needs an FP64 context");
+  if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
+  if (ctx->k != 0) return fail(ctx, DABA_ERR_STATE, "iterations have run since the state was set");
+  cudaStream_t st = (cudaStream_t)stream;
+  daba_status s;
+  if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
+  if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  const int C = ADJ_CKPT;
+  const int n_seg = (K + C - 1) / C;
+  // slots: [0, n_seg) the states at k = 0, C, 2C, ...; [n_seg, n_seg + C) the states of one
+  // segment; n_seg + C the state after K iterations
+  if ((s = ensure_adjoint(ctx, (size_t)n_seg + C + 1)) != DABA_OK) return s;
+  struct TimingOff {   // direct launches without per-kernel events; restored on every return
+    daba_ctx* c;
+    bool was;
+    ~TimingOff() { c->timing = was; }
+  } timing_off{ctx, ctx->timing};
+  ctx->timing = false;
+  const int M = ctx->M, N = ctx->N;
+  const size_t nnz = (size_t)ctx->nnz;
+  std::vector<double> s_hist((size_t)K + 1);   // s^(k) before iteration k
+  CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+  // forward sweep, keeping every C-th state
+  for (int sg = 0; sg < n_seg; ++sg) {
+    const int n = std::min(C, K - sg * C);
+    CK(save_state(ctx, ctx->slots[sg], st));
+    for (int j = 0; j < n; ++j) {
+      s_hist[(size_t)sg * C + j] = ctx->s_k;
+      CK(advance(ctx, st, 1));
+    }
+  }
+  s_hist[K] = ctx->s_k;
+  void* fin = ctx->slots[(size_t)n_seg + C];
+  CK(save_state(ctx, fin, st));
+  // seed: adjoint of x^K
+  const bool cdev = is_device_ptr(seed_cams), ldev = is_device_ptr(seed_lms);
+  const double* dsc = cdev ? seed_cams : (const double*)ctx->st_cam;
+  const double* dsl = ldev ? seed_lms : (const double*)ctx->st_lm;
+  if (!cdev) CK(cudaMemcpyAsync(ctx->st_cam, seed_cams, (size_t)M * 9 * 8, cudaMemcpyHostToDevice, st));
+  if (!ldev) CK(cudaMemcpyAsync(ctx->st_lm, seed_lms, (size_t)N * 3 * 8, cudaMemcpyHostToDevice, st));
+  int i1 = 0, i0 = 1, im = 2;
+  for (int q = 0; q < 3; ++q) {
+    CK(cudaMemsetAsync(ctx->adj_c[q], 0, (size_t)M * AC_N * 8, st));
+    CK(cudaMemsetAsync(ctx->adj_l[q], 0, (size_t)N * AL_N * 8, st));
+  }
+  CK(cudaMemsetAsync(ctx->g_u, 0, nnz * 16, st));
+  if (M > 0)
+    k_adj_seed_cams<<<(M + 127) / 128, 128, 0, st>>>(M, (const double*)ctx->cam_x, dsc, ctx->s_norm,
+                                                     (double*)ctx->adj_c[i1]);
+  if (N > 0)
+    k_adj_seed_lms<<<(N + 255) / 256, 256, 0, st>>>(N, dsl, (const int*)ctx->d_linv, (double*)ctx->adj_l[i1]);
+  CK(cudaGetLastError());
+  // backward over the segments: recompute the segment's states, then per iteration replay it
+  // (statistics, records, decisions) and run its adjoint
+  for (int sg = n_seg - 1; sg >= 0; --sg) {
+    const int kb = sg * C, ke = std::min(K, kb + C);
+    CK(restore_state(ctx, ctx->slots[sg], kb, s_hist[kb], st));
+    for (int k = kb; k < ke; ++k) {
+      CK(save_state(ctx, ctx->slots[(size_t)n_seg + (k - kb)], st));
+      CK(advance(ctx, st, 1));
+    }
+    for (int k = ke - 1; k >= kb; --k) {
+      const void* slot = ctx->slots[(size_t)n_seg + (k - kb)];
+      if (k != ke - 1) {   // the live buffers hold iteration ke - 1 after the segment sweep
+        CK(restore_state(ctx, slot, k, s_hist[k], st));
+        CK(advance(ctx, st, 1));
+      }
+      const double sk = s_hist[k];
+      const double gamma = (sk - 1.0) / ((std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0);
+      CK(adjoint_iter_by_loss(ctx, st, k, gamma, slot, i1, i0, im));
+      if (k > 0) {
+        const int t = i1;
+        i1 = i0;
+        i0 = im;
+        im = t;
+        CK(cudaMemsetAsync(ctx->adj_c[im], 0, (size_t)M * AC_N * 8, st));
+        CK(cudaMemsetAsync(ctx->adj_l[im], 0, (size_t)N * AL_N * 8, st));
+      }
+    }
+  }
+  // adjoint of x^0 = x^(-1) to the boundary
+  const SlotLayout Ly = slot_layout(ctx);
+  const bool gcdev = g_cams && is_device_ptr(g_cams), gldev = g_lms && is_device_ptr(g_lms);
+  double* gc = gcdev ? g_cams : (double*)ctx->st_cam;
+  double* gl = gldev ? g_lms : (double*)ctx->st_lm;
+  if (M > 0)
+    k_adj_out_cams<<<(M + 127) / 128, 128, 0, st>>>(M, (const double*)((const char*)ctx->slots[0] + Ly.x),
+                                                    (const double*)ctx->adj_c[i0], (const double*)ctx->adj_c[im],
+                                                    ctx->s_norm, gc);
+  if (N > 0)
+    k_adj_out_lms<<<(N + 255) / 256, 256, 0, st>>>(N, (const double*)ctx->adj_l[i0], (const double*)ctx->adj_l[im],
+                                                   (const int*)ctx->d_lperm, gl);
+  CK(cudaGetLastError());
+  if (g_cams && !gcdev) CK(cudaMemcpyAsync(g_cams, gc, (size_t)M * 9 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_lms && !gldev) CK(cudaMemcpyAsync(g_lms, gl, (size_t)N * 3 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_uv)
+    CK(cudaMemcpyAsync(g_uv, ctx->g_u, nnz * 16, is_device_ptr(g_uv) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+  // leave the state after K iterations
+  CK(restore_state(ctx, fin, K, s_hist[K], st));
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (flag & 2) return fail(ctx, DABA_ERR_CUDA, "a landmark-pass copy did not complete (bounded wait ran out)");
+  if (flag) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
   return DABA_OK;
 }
 

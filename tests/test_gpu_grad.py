@@ -109,3 +109,83 @@ def test_set_pixels_matches_set_observations():
         assert e.value.status == L.DABA_ERR_NONFINITE
         a.close()
         b.close()
+
+
+def _rel_err(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("case", ["small-huber-6", "small-cauchy-12", "small-trivial-mm-8", "circle-tiles-12",
+                                  "street-12"])
+def test_unrolled_grad_matches_oracle(case):
+    """Vector-Jacobian product of K iterations (the CUDA adjoint kernels, states kept every 10
+    iterations and recomputed) against autograd through the oracle's PyTorch restatement of the
+    update, which is itself pinned by FP64 central differences of the numpy oracle."""
+    from oracle import daba_unrolled as U
+    from paper_2305_07026_b300 import _lib as L, scenes
+    kw = {}
+    if case.startswith("small"):
+        sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+        loss, K = case.split("-")[1], int(case.split("-")[-1])
+        accel = "mm" not in case
+        scale_px = 2.0
+    elif case == "circle-tiles-12":   # several chunks per camera and many landmark tiles
+        sc = scenes.circle_scene(seed=3)
+        loss, K, accel, scale_px = "huber", 12, True, 2.0
+        kw = dict(chunk_obs=64, tile_obs=128, tile_lms=16)
+    else:
+        sc = cached_scene("street", scale=0.05)
+        loss, K, accel, scale_px = sc.loss, 12, True, sc.loss_scale_px
+    o = O.Options(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0)
+    rng = np.random.default_rng(4)
+    g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
+    gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
+    opts = dict(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0, prec="fp64", **kw)
+    # the restart decisions the adjoint replays are those of the oracle's run
+    with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        rs = np.zeros(K, np.int32)
+        d.run(K, restarts=rs)
+        want = [int(np.sum(i.restart_cam)) + int(np.sum(i.restart_lm)) for i in res.infos] if accel else [0] * K
+        assert rs.tolist() == want
+    with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        gcg, glg, gug = d.unrolled_grad(K, g_c, g_l)
+        cams, lms = d.get_state()   # left at x^K
+        np.testing.assert_allclose(cams, oc, rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(lms, ol, rtol=1e-8, atol=1e-8)
+        errs = {"cams": _rel_err(gcg, gc), "lms": _rel_err(glg, gl), "uv": _rel_err(gug, gu)}
+        assert max(errs.values()) < 1e-7, errs
+        with pytest.raises(L.DabaError):   # iterations have run since the state was set
+            d.unrolled_grad(K, g_c, g_l)
+
+
+def test_unrolled_grad_linear_in_seed():
+    """The product is linear in the seed and K = 1 of a seed on one landmark touches only what
+    that landmark's update reads."""
+    from paper_2305_07026_b300 import _lib as L, scenes
+    sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+    rng = np.random.default_rng(9)
+    s1 = (rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape))
+    s2 = (rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape))
+
+    def vjp(seed, K):
+        with L.Daba(sc.M, sc.N, sc.nnz, loss="huber", loss_scale_px=2.0, prec="fp64") as d:
+            d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+            d.set_state(sc.cams, sc.lms)
+            return d.unrolled_grad(K, *seed)
+    a, b = vjp(s1, 5), vjp(s2, 5)
+    c = vjp((2.0 * s1[0] - s2[0], 2.0 * s1[1] - s2[1]), 5)
+    for x, y, z in zip(a, b, c):
+        np.testing.assert_allclose(z, 2.0 * x - y, rtol=1e-9, atol=1e-9 * np.abs(z).max())
+    seed = (np.zeros_like(sc.cams), np.zeros_like(sc.lms))
+    seed[1][7] = [1.0, -2.0, 0.5]
+    gc, gl, gu = vjp(seed, 1)
+    obs = np.flatnonzero(sc.lm_idx == 7)
+    others = np.setdiff1d(np.arange(sc.nnz), obs)
+    assert np.all(gu[others] == 0.0) and np.any(gu[obs] != 0.0)
+    assert np.all(np.delete(gl, 7, axis=0) == 0.0)
+    assert np.all(np.delete(gc, np.unique(sc.cam_idx[obs]), axis=0) == 0.0)
