@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--fp64-steps", type=int, default=None, help="iterations of the FP64 comparison run")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--unrolled-steps", type=int, default=10,
+                    help="iterations differentiated by the timed reverse-mode call (FP64; 0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-scenes", type=int, default=512, help="scenes of the batch workload")
@@ -322,6 +324,29 @@ def run_ours(args, rank, world, local):
     e1.record(stream)
     e1.synchronize()
     ms64 = e0.elapsed_time(e1)
+    # reverse mode: vector-Jacobian product of Ku iterations from x^0 (FP64, device seeds and
+    # outputs); one untimed call first allocates the kept states
+    unrolled = None
+    Ku = args.unrolled_steps
+    if Ku > 0:
+        gen = torch.Generator(device="cuda").manual_seed(5)
+        seed_c = torch.randn((sc.M, 9), dtype=torch.float64, device="cuda", generator=gen)
+        seed_l = torch.randn((sc.N, 3), dtype=torch.float64, device="cuda", generator=gen)
+        u_c, u_l = torch.empty_like(seed_c), torch.empty_like(seed_l)
+        u_u = torch.empty((sc.nnz, 2), dtype=torch.float64, device="cuda")
+        d64.set_state(sc.cams, sc.lms)
+        d64.unrolled_grad(Ku, seed_c, seed_l, u_c, u_l, u_u, stream=sp)
+        d64.set_state(sc.cams, sc.lms)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        d64.unrolled_grad(Ku, seed_c, seed_l, u_c, u_l, u_u, stream=sp)
+        e1.record(stream)
+        e1.synchronize()
+        ms_u = e0.elapsed_time(e1)
+        unrolled = {"what": "daba_unrolled_grad: d(<seed, x^K>)/d(cameras, landmarks, pixels) of K FP64 iterations "
+                            "from x^0 (forward sweep, states kept every 10 iterations and recomputed, adjoint kernels)",
+                    "K": Ku, "ms": ms_u, "ms_per_iteration": ms_u / Ku,
+                    "ratio_to_fp64_forward": ms_u / (Ku * ms64 / Kf)}
     d64.close()
     # the mixed path from the same x^0: its iteration count to reach FP64's final objective
     # within 1e-5 (run on, untimed, up to 3 Kf iterations when it needs more than Kf)
@@ -426,6 +451,7 @@ def run_ours(args, rank, world, local):
         "accuracy": accuracy,
         "kernel_ms_per_launch": per_launch_ms,
         "roofline": roofline, "roofline_kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gradient": grad,
+        "unrolled_gradient": unrolled,
         "gpu_launches": int(launches),
         "clocks": ck,
     }

@@ -189,3 +189,41 @@ def test_unrolled_grad_linear_in_seed():
     assert np.all(gu[others] == 0.0) and np.any(gu[obs] != 0.0)
     assert np.all(np.delete(gl, 7, axis=0) == 0.0)
     assert np.all(np.delete(gc, np.unique(sc.cam_idx[obs]), axis=0) == 0.0)
+
+
+def test_unrolled_autograd_matches_central_differences():
+    """torch.autograd through K iterations of the library (backward: the CUDA adjoint) against
+    FP64 central differences of the library's own K-iteration map along random directions."""
+    from paper_2305_07026_b300 import _lib as L, autograd as A, scenes
+    sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+    K = 7
+    dev = torch.device("cuda:0")
+    d = L.Daba(sc.M, sc.N, sc.nnz, loss="huber", loss_scale_px=2.0, pixel_scale=650.0, prec="fp64")
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    d.set_state(sc.cams, sc.lms)
+    c0 = torch.tensor(sc.cams, device=dev, requires_grad=True)
+    l0 = torch.tensor(sc.lms, device=dev, requires_grad=True)
+    u0 = torch.tensor(sc.uv, device=dev, requires_grad=True)
+    rng = np.random.default_rng(2)
+    wc = torch.tensor(rng.normal(size=sc.cams.shape), device=dev)
+    wl = torch.tensor(rng.normal(size=sc.lms.shape), device=dev)
+    oc, ol = A.unrolled(d, c0, l0, u0, K)
+    y = (oc * wc).sum() + (ol * wl).sum()
+    gc, gl, gu = torch.autograd.grad(y, (c0, l0, u0))
+
+    def J(c, l, u):
+        with torch.no_grad():
+            a, b = A.unrolled(d, c, l, u, K)
+            return float((a * wc).sum() + (b * wl).sum())
+    cscale = torch.tensor([1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 0.5, 1e-4, 1e-6], device=dev, dtype=torch.float64)
+    for part in range(3):
+        for rep in range(3):
+            v = [torch.zeros_like(c0), torch.zeros_like(l0), torch.zeros_like(u0)]
+            r = torch.tensor(rng.normal(size=tuple(v[part].shape)), device=dev)
+            v[part] = r * (cscale if part == 0 else (1e-3 if part == 1 else 1e-2))
+            h = (1e-3, 1e-2, 1e-2)[part]
+            c, l, u = c0.detach(), l0.detach(), u0.detach()
+            fd = (J(c + h * v[0], l + h * v[1], u + h * v[2]) - J(c - h * v[0], l - h * v[1], u - h * v[2])) / (2 * h)
+            an = float((gc * v[0]).sum() + (gl * v[1]).sum() + (gu * v[2]).sum())
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (part, rep)
+    d.close()
