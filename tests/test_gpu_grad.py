@@ -116,8 +116,8 @@ def _rel_err(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("case", ["small-huber-6", "small-cauchy-12", "small-trivial-mm-8", "circle-tiles-12",
-                                  "street-12"])
+@pytest.mark.parametrize("case", ["small-huber-6", "small-cauchy-12", "small-trivial-mm-8", "small-huber-50",
+                                  "circle-tiles-12", "circle-welsch-20", "street-12"])
 def test_unrolled_grad_matches_oracle(case):
     """Vector-Jacobian product of K iterations (the CUDA adjoint kernels, states kept every 10
     iterations and recomputed) against autograd through the oracle's PyTorch restatement of the
@@ -134,6 +134,9 @@ def test_unrolled_grad_matches_oracle(case):
         sc = scenes.circle_scene(seed=3)
         loss, K, accel, scale_px = "huber", 12, True, 2.0
         kw = dict(chunk_obs=64, tile_obs=128, tile_lms=16)
+    elif case == "circle-welsch-20":
+        sc = scenes.circle_scene(seed=5)
+        loss, K, accel, scale_px = "welsch", 20, True, 3.0
     else:
         sc = cached_scene("street", scale=0.05)
         loss, K, accel, scale_px = sc.loss, 12, True, sc.loss_scale_px
