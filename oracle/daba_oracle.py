@@ -33,6 +33,16 @@ Readings where the paper is silent (each is also listed in the design notes):
   R-step (ProjRot3D of a 3x3 matrix) and a (t, d)-step (6x6 normal equations).
 * Nesterov s^k is global (Algorithm 1 never resets it); the restart test uses
   strict '>' (no restart on equality).
+
+Method variant (not Algorithm 1 as printed; Options.restart = "global"): one
+restart test for the whole problem on the sums of the block metrics,
+sum_alpha E^alpha(k+1) > sum_alpha Fbar^alpha(k), which a single device can
+evaluate because it holds every block; when it fires every block takes its MM
+update (Eq. update_mm). Since the recursions of Eqs. Fak, lFak and Eak are
+linear, the sums are the same metrics for one block made of everything, so the
+convergence argument of App. C.3 applies unchanged. With
+Options.momentum_reset the Nesterov scalar restarts too: after an iteration
+whose global test fired, s^(k+1) = 1, so gamma^(k+1) = 0.
 """
 from __future__ import annotations
 
@@ -318,6 +328,8 @@ class Options:
     accelerated: bool = True
     cam_alternations: int = 2
     pixel_scale: float = 0.0     # 0: median focal length
+    restart: str = "block"       # "block": Algorithm 1; "global": one test on the summed block metrics
+    momentum_reset: bool = False  # with restart="global": s <- 1 after a restart
 
 
 @dataclasses.dataclass
@@ -424,8 +436,16 @@ def step(prob: Problem, st: State):
         # Eq. Eak for the accelerated update, then the adaptive restart test
         Ea_cam = E_cam(xi, mj_k, Ra, ta, da, st.R, st.t, st.d, ci, u, M) + F_cam - E0_cam
         Ea_lm = E_lm(xi, mj_k, la, st.l, li, N) + F_lm - E0_lm
-        rs_cam = Ea_cam > Fbar_cam
-        rs_lm = Ea_lm > Fbar_lm
+        if o.restart == "global":
+            # the test of Algorithm 1 for the single block made of every camera and landmark
+            fire = bool(np.sum(Ea_cam) + np.sum(Ea_lm) > np.sum(Fbar_cam) + np.sum(Fbar_lm))
+            rs_cam = np.full(M, fire)
+            rs_lm = np.full(N, fire)
+            if fire and o.momentum_reset:
+                s_next = 1.0
+        else:
+            rs_cam = Ea_cam > Fbar_cam
+            rs_lm = Ea_lm > Fbar_lm
     else:
         Ra, ta, da, la = Rm, tm, dm, lm_mm
         Ea_cam, Ea_lm = Emm_cam, Emm_lm

@@ -466,6 +466,45 @@ def test_algorithm1_invariants(circle, eta):
         assert nrs > 0   # the adaptive restart is exercised on this scene
 
 
+@pytest.mark.parametrize("eta,reset", [(0.5, False), (1.0, False), (0.5, True)])
+def test_global_restart_invariants(circle, eta, reset):
+    """Global restart variant: Lemma 1 and Eq. FklFk0 for the single block made of everything
+    (the sums of the block metrics), all-or-nothing decisions, a monotone objective at eta = 1
+    (then Fbar = F), and gamma = 0 after a restart when the momentum is reset."""
+    sc = circle
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, eta=eta, xi=1e-8, restart="global",
+                     momentum_reset=reset)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    st = O.init_state(prob, R, t, d, l)
+    Fbar = O.objective(prob.loss, prob.c, R, t, d, l, prob.cam_idx, prob.lm_idx, prob.u)
+    fired, gammas, F_prev = [], [], None
+    for k in range(40):
+        prev = st
+        st, info = O.step(prob, prev)
+        F = info.F
+        gammas.append(info.gamma)
+        assert info.F_cam.sum() + info.F_lm.sum() == pytest.approx(F, rel=1e-11)
+        Fbar = (1 - eta) * Fbar + eta * F
+        assert info.Fbar_cam.sum() + info.Fbar_lm.sum() == pytest.approx(Fbar, rel=1e-11)
+        rc, rl = info.restart_cam, info.restart_lm
+        assert (rc.all() and rl.all()) or not (rc.any() or rl.any())
+        fired.append(bool(rc.all()))
+        # the restart test of the single block: sum E(k+1) <= sum Fbar(k)
+        assert info.Enext_cam.sum() + info.Enext_lm.sum() <= Fbar + 1e-12 * abs(Fbar)
+        Fn = O.objective(prob.loss, prob.c, st.R, st.t, st.d, st.l, prob.cam_idx, prob.lm_idx, prob.u)
+        dx2 = O.cam_sqdist(st.R, st.t, st.d, prev.R, prev.t, prev.d).sum() + np.sum((st.l - prev.l) ** 2)
+        assert Fn - Fbar <= -0.5 * opts.xi * dx2 + 1e-12 * Fbar
+        if eta == 1.0:
+            assert Fn <= F * (1 + 1e-12)
+        F_prev = F
+    assert any(fired) and not all(fired)
+    for k in range(1, 40):
+        if reset and fired[k - 1]:
+            assert gammas[k] == 0.0
+        elif k > 1 and not reset:
+            assert gammas[k] > 0.0
+
+
 @pytest.mark.parametrize("loss", ["trivial", "huber", "cauchy", "welsch"])
 def test_duba_monotone(loss):
     """DUBA (always the MM update, Sec. 7.2) never increases F (Sec. 4)."""
