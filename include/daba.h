@@ -78,7 +78,17 @@ typedef struct {
   int32_t chunk_obs;
   int32_t tile_obs;
   int32_t tile_lms;
+  /* restart test (method variant; default DABA_RESTART_BLOCK, Algorithm 1): with
+   * DABA_RESTART_GLOBAL one test decides for all blocks, sum_alpha E^alpha(k+1) >
+   * sum_alpha Fbar^alpha(k) (the test of Algorithm 1 for the single block made of every camera
+   * and landmark, whose metrics are the sums because Eqs. Fak, lFak, Eak are linear); when it
+   * fires every block takes its MM update (Eq. update_mm). momentum_reset = 1 (global only)
+   * also restarts Nesterov's scalar: s^(k+1) = 1 after an iteration whose test fired. */
+  int32_t restart_mode;
+  int32_t momentum_reset;
 } daba_options;
+
+typedef enum { DABA_RESTART_BLOCK = 0, DABA_RESTART_GLOBAL = 1 } daba_restart_mode;
 
 typedef struct daba_ctx daba_ctx;
 
@@ -151,7 +161,8 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
  * would), keeps the state every 10 iterations and recomputes the others, so that it costs
  * about three forward runs plus the adjoint kernels and holds about K/10 + 11 copies of the
  * state. Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
- * (DABA_ERR_ARG for MIXED); DABA_ERR_STATE if iterations have run since the state was set. */
+ * (DABA_ERR_ARG for MIXED and for momentum_reset, whose Nesterov scalars live on the device);
+ * DABA_ERR_STATE if iterations have run since the state was set. */
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream);
 

@@ -20,6 +20,7 @@ DABA_OK, DABA_ERR_ARG, DABA_ERR_INDEX, DABA_ERR_DEGENERATE, DABA_ERR_NONFINITE, 
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_DEGENERATE", "ERR_NONFINITE", "ERR_CUDA", "ERR_OOM", "ERR_STATE"]
 LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
 PREC = {"fp64": 0, "mixed": 1}
+RESTART = {"block": 0, "global": 1}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_07026_b300.build`")
@@ -31,7 +32,8 @@ class daba_options(ctypes.Structure):
     _fields_ = [("loss", ctypes.c_int), ("loss_scale_px", ctypes.c_double), ("xi", ctypes.c_double),
                 ("eta", ctypes.c_double), ("accelerated", ctypes.c_int), ("cam_alternations", ctypes.c_int),
                 ("pixel_scale", ctypes.c_double), ("prec", ctypes.c_int), ("chunk_obs", ctypes.c_int32),
-                ("tile_obs", ctypes.c_int32), ("tile_lms", ctypes.c_int32)]
+                ("tile_obs", ctypes.c_int32), ("tile_lms", ctypes.c_int32), ("restart_mode", ctypes.c_int32),
+                ("momentum_reset", ctypes.c_int32)]
 
 
 _p = ctypes.c_void_p
@@ -102,7 +104,8 @@ def current_stream():
 
 
 def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True, cam_alternations=2,
-            pixel_scale=0.0, prec="mixed", chunk_obs=0, tile_obs=0, tile_lms=0) -> daba_options:
+            pixel_scale=0.0, prec="mixed", chunk_obs=0, tile_obs=0, tile_lms=0, restart="block",
+            momentum_reset=False) -> daba_options:
     o = daba_options()
     daba_default_options(ctypes.byref(o))
     o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
@@ -114,6 +117,8 @@ def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True
     o.pixel_scale = float(pixel_scale)
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     o.chunk_obs, o.tile_obs, o.tile_lms = int(chunk_obs), int(tile_obs), int(tile_lms)
+    o.restart_mode = RESTART[restart] if isinstance(restart, str) else int(restart)
+    o.momentum_reset = int(bool(momentum_reset))
     return o
 
 

@@ -95,6 +95,10 @@ struct daba_ctx {
   void *zb_c[2] = {nullptr, nullptr}, *zb_l[2] = {nullptr, nullptr};
   void *st_bar = nullptr, *ab_bar = nullptr, *g_u = nullptr;
   std::vector<void*> slots;
+  // global restart variant (allocated when restart_mode is global): per-block terms of the test,
+  // the MM alternatives, the decision and the device Nesterov scalar
+  void *g_cam = nullptr, *g_tile = nullptr, *cam_alt = nullptr, *lm_alt = nullptr, *g_fire = nullptr,
+       *s_dev = nullptr;
 };
 
 namespace {
@@ -257,6 +261,13 @@ IterParams iter_params(daba_ctx* ctx) {
   P.accelerated = ctx->opt.accelerated;
   P.n_alt = ctx->opt.cam_alternations;
   P.flag = (int*)ctx->d_flag;
+  P.restart_global = ctx->opt.restart_mode == DABA_RESTART_GLOBAL ? 1 : 0;
+  P.reset_s = ctx->opt.momentum_reset;
+  P.g_cam = (double*)ctx->g_cam;
+  P.g_tile = (double*)ctx->g_tile;
+  P.cam_alt = (double*)ctx->cam_alt;
+  P.g_fire = (int*)ctx->g_fire;
+  P.s_dev = (double*)ctx->s_dev;
   return P;
 }
 
@@ -313,7 +324,7 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
           t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
           (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
           (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
-          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd);
+          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd, (V4<Real>*)ctx->lm_alt);
       ctx->launches++;
     }
     t0 = ctx->tile_class_end[c];
@@ -363,9 +374,36 @@ cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
   k_finalize<<<FIN_BLOCKS, FIN_THREADS, 0, st>>>(ctx->M, (const double*)ctx->cam_Fsum, (const uint8_t*)ctx->cam_rs,
-                                                  ctx->n_tiles, (const int*)ctx->tile_rs, ctx->s_norm * ctx->s_norm, P,
+                                                  ctx->n_tiles, (const int*)ctx->tile_rs, ctx->M + ctx->N,
+                                                  ctx->s_norm * ctx->s_norm, P,
                                                   (double*)ctx->fin_blk, (unsigned int*)ctx->fin_ticket,
                                                   (double*)ctx->d_trace, (int*)ctx->d_rs, (int*)ctx->d_flag);
+  return cudaGetLastError();
+}
+
+// global restart variant: apply the MM alternatives when the reduction's test fired (the
+// kernels return at once otherwise)
+cudaError_t launch_fixups(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  if (!(ctx->opt.accelerated && ctx->opt.restart_mode == DABA_RESTART_GLOBAL)) return cudaSuccess;
+  const IterParams P = iter_params(ctx);
+  const int M = ctx->M, N = ctx->N;
+  if (is_mixed(ctx)) {
+    k_fix_cams<float><<<(M + 127) / 128, 128, 0, st>>>(M, P, (double*)ctx->cam_x, (double*)ctx->cam_dx,
+                                                       (double*)ctx->cam_Rbar, (double*)ctx->cam_S, (double*)ctx->cam_E,
+                                                       (uint8_t*)ctx->cam_rs, (V4<float>*)pack_at(ctx, k + 1));
+    k_fix_lms<float, true><<<(N + 255) / 256, 256, 0, st>>>(
+        N, P, (const V4<float>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), (const V4<float>*)ctx->lm_alt,
+        (V4<float>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), (uint8_t*)ctx->lm_rs);
+  } else {
+    k_fix_cams<double><<<(M + 127) / 128, 128, 0, st>>>(M, P, (double*)ctx->cam_x, (double*)ctx->cam_dx,
+                                                        (double*)ctx->cam_Rbar, (double*)ctx->cam_S,
+                                                        (double*)ctx->cam_E, (uint8_t*)ctx->cam_rs,
+                                                        (V4<double>*)pack_at(ctx, k + 1));
+    k_fix_lms<double, false><<<(N + 255) / 256, 256, 0, st>>>(
+        N, P, (const V4<double>*)lmrec_at(ctx, k), nullptr, (const V4<double>*)ctx->lm_alt,
+        (V4<double>*)lmrec_at(ctx, k + 1), nullptr, (uint8_t*)ctx->lm_rs);
+  }
+  ctx->launches += 2;
   return cudaGetLastError();
 }
 
@@ -436,6 +474,7 @@ cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, siz
     CE(cudaStreamWaitEvent(st, ctx->ev_lo, 0));
     if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 5), st));
     CE(launch_finalize(ctx, st));
+    CE(launch_fixups(ctx, st, kk));
     if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 6), st));
     if (ctx->timing) evi += 7;
   }
@@ -688,6 +727,8 @@ void daba_default_options(daba_options* o) {
   o->chunk_obs = 0;
   o->tile_obs = 0;
   o->tile_lms = 0;
+  o->restart_mode = DABA_RESTART_BLOCK;
+  o->momentum_reset = 0;
 }
 
 const char* daba_last_error(const daba_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -734,7 +775,10 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     return bad("schedule");
   if (!(o.xi > 0) || !(o.eta > 0) || !(o.eta <= 1) || o.cam_alternations < 1 || o.cam_alternations > 64 ||
       (int)o.loss < 0 || (int)o.loss > 3 || !(o.pixel_scale >= 0) ||
-      (o.loss != DABA_LOSS_TRIVIAL && !(o.loss_scale_px > 0)) || (o.prec != DABA_FP64 && o.prec != DABA_MIXED))
+      (o.loss != DABA_LOSS_TRIVIAL && !(o.loss_scale_px > 0)) || (o.prec != DABA_FP64 && o.prec != DABA_MIXED) ||
+      (o.restart_mode != DABA_RESTART_BLOCK && o.restart_mode != DABA_RESTART_GLOBAL) ||
+      (o.momentum_reset != 0 && o.momentum_reset != 1) ||
+      (o.momentum_reset && o.restart_mode != DABA_RESTART_GLOBAL))
     return bad("options");
   ctx->M = M;
   ctx->N = N;
@@ -782,9 +826,9 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(chunk_f, (size_t)ctx->max_chunks * R);
   AL(tile_rs, (size_t)ctx->max_tiles * 4);
   AL(cam_Fsum, (size_t)M * 8);
-  AL(fin_blk, (size_t)FIN_BLOCKS * 2 * 8);
+  AL(fin_blk, (size_t)FIN_BLOCKS * 3 * 8);
   AL(fin_ticket, 16);
-  AL(d_gam, (GSEG + 1) * 8);
+  AL(d_gam, (GSEG + 2) * 8);
   AL(d_it, 16);
   AL(d_first, 16);
   AL(d_flag, 16);
@@ -798,6 +842,14 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_bad, 16);
   AL(d_scene_chunk, (size_t)(M + 1) * 4);
   AL(d_ci_order, nnz * 4);
+  if (o.restart_mode == DABA_RESTART_GLOBAL) {
+    AL(g_cam, (size_t)M * 8);
+    AL(g_tile, (size_t)ctx->max_tiles * 8);
+    AL(cam_alt, (size_t)M * 32 * 8);
+    AL(lm_alt, (size_t)N * 2 * 4 * R);
+    AL(g_fire, 16);
+    AL(s_dev, 16);
+  }
   AL(d_lperm, (size_t)N * 4);
   AL(d_scene_f, (size_t)M * 8);
 #undef AL
@@ -1086,7 +1138,8 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     const int seg = std::min(GSEG, iters - done);
     // gamma^(k) .. gamma^(k+seg) (Eq. nesterov_scalar); the last one is the look-ahead used
     // by the camera solve to extrapolate iteration k+seg
-    double sk = ctx->s_k;
+    const double s_start = ctx->s_k;
+    double sk = s_start;
     for (int j = 0; j <= seg; ++j) {
       const double s_next = (std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0;
       gam[j] = (sk - 1.0) / s_next;
@@ -1094,6 +1147,8 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
       if (j == seg - 1) ctx->s_k = sk;
     }
     CK(cudaMemcpyAsync(ctx->d_gam, gam.data(), (seg + 1) * 8, cudaMemcpyHostToDevice, st));
+    // momentum reset: the reduction continues s and the gamma table on the device from s^(k)
+    if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(ctx->s_dev, &s_start, 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
     if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
@@ -1116,6 +1171,7 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     }
     CK(cudaMemcpyAsync(trace.data() + done, ctx->d_trace, seg * 8, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
+    if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(&ctx->s_k, ctx->s_dev, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (ctx->timing) {
       float ms = 0.f;
@@ -1281,6 +1337,8 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   if (K < 1) return fail(ctx, DABA_ERR_ARG, "K must be >= 1");
   if (!seed_cams || !seed_lms) return fail(ctx, DABA_ERR_ARG, "null seed pointer");
   if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient needs an FP64 context");
+  if (ctx->opt.momentum_reset)
+    return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   if (ctx->k != 0) return fail(ctx, DABA_ERR_STATE, "iterations have run since the state was set");
   cudaStream_t st = (cudaStream_t)stream;

@@ -67,6 +67,16 @@ struct IterParams {
   int accelerated;
   int n_alt;
   int* flag;           // error bits: 1 non-finite objective, 2 a bounded wait ran out
+  // global restart variant (restart_global = 1): one test on the sums of the block metrics.
+  // The block kernels take the accelerated update and keep the MM alternative; the reduction
+  // decides; the fix-up kernels apply the MM alternative everywhere if the test fired.
+  int restart_global;
+  int reset_s;         // with restart_global: s <- 1 after a restart (gamma table continued on the device)
+  double* g_cam;       // per camera: E(k+1) - Fbar(k) of its accelerated update
+  double* g_tile;      // per landmark tile: the sum of the same over its landmarks
+  double* cam_alt;     // per camera (32 doubles): MM alternative R t d, its dx, E(k+1), S(k+1)
+  int* g_fire;         // 1 if the global test fired in the current iteration
+  double* s_dev;       // Nesterov s^(k) on the device (reset_s)
 };
 
 template <class Real>
@@ -355,7 +365,7 @@ __global__ void __launch_bounds__(LPASS_THREADS)
             const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
             const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out,
             V4<float>* __restrict__ lm_lo_out, IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs,
-            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag) {
+            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag, V4<Real>* __restrict__ lm_alt) {
   using RC = typename RecC<Real>::type;
   using SM = LpassSmem<Real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -414,6 +424,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   }
 
   int nrs = 0;
+  double gsum = 0.0;   // global restart variant: this thread's E(k+1) - Fbar(k)
+  const bool global = P.accelerated && P.restart_global;
   const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
   if (jl < nl) {
     Real st[10];
@@ -449,13 +461,28 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     const Real ak = st[4] + hx;
     Real step0 = sa0, step1 = sa1, step2 = sa2;
     Real dEn = ak * (sa0 * sa0 + sa1 * sa1 + sa2 * sa2) + Real(2) * (sa0 * st[5] + sa1 * st[6] + sa2 * st[7]);
-    const bool rs = P.accelerated ? (dEn > thr) : true;
-    if (rs) {   // adaptive restart: MM update (Eq. update_mm) from l^k
+    const bool rs = P.accelerated ? (!global && dEn > thr) : true;
+    if (rs || global) {   // adaptive restart: MM update (Eq. update_mm) from l^k
       const Real ik = fdiv(Real(1), ak);
-      step0 = -st[5] * ik;
-      step1 = -st[6] * ik;
-      step2 = -st[7] * ik;
-      dEn = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
+      const Real m0 = -st[5] * ik, m1 = -st[6] * ik, m2 = -st[7] * ik;
+      const Real dEm = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
+      if (rs) {
+        step0 = m0;
+        step1 = m1;
+        step2 = m2;
+        dEn = dEm;
+      } else {   // global variant: keep the MM alternative and this block's term of the test
+        V4<Real> a0, a1;
+        a0.x = m0, a0.y = m1, a0.z = m2, a0.w = thr - dEm;
+        a1.x = a1.y = a1.z = a1.w = Real(0);
+        if (!HAS_LO) {
+          const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
+          a1.x = Real(E + double(dE) + double(dEm));
+        }
+        lm_alt[2 * g] = a0;
+        lm_alt[2 * g + 1] = a1;
+        gsum = double(dEn) - double(thr);
+      }
     }
     nrs += (rs && P.accelerated) ? 1 : 0;
     V4<Real> nA, nB;
@@ -505,6 +532,18 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     int n = 0;
     for (int w = 0; w < LPASS_THREADS / 32; ++w) n += redi[w];
     tile_rs[tile] = n;
+  }
+  if (global) {   // the tile's sum for the global test (fixed order)
+    __shared__ double redg[LPASS_THREADS / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
+    if ((threadIdx.x & 31) == 0) redg[threadIdx.x >> 5] = gsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < LPASS_THREADS / 32; ++w) t += redg[w];
+      P.g_tile[tile] = t;
+    }
   }
 }
 
@@ -899,7 +938,28 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
   const T dE = N::c(-0.5f) * xi * dx2 + N::c(0.5f) * sG;
   const T S = first ? N::c(0.f) : N::from(cam_S[i]);
   const T thr = N::from(P.eta1) * (S - dE);
-  const bool rs = P.accelerated ? (dEn > thr) : true;
+  const bool global = P.accelerated && P.restart_global;
+  const bool rs = P.accelerated ? (!global && dEn > thr) : true;
+  const T E = first ? N::c(0.5f) * sF : N::from(cam_E[i]);
+  const T F = E + dE;
+  if (global) {   // keep the MM alternative (warp 1's) and this block's term of the global test
+    double* alt = P.cam_alt + (size_t)i * 32;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      alt[a] = N::to_double(sh_mm[lane][a]);
+      alt[15 + a] = N::to_double(sh_mm[lane][a] - ck.R[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      alt[9 + a] = N::to_double(sh_mm[lane][9 + a]);
+      alt[12 + a] = N::to_double(sh_mm[lane][12 + a]);
+      alt[24 + a] = N::to_double(sh_mm[lane][9 + a] - ck.t[a]);
+      alt[27 + a] = N::to_double(sh_mm[lane][12 + a] - ck.d[a]);
+    }
+    alt[30] = N::to_double(F + sh_mm[lane][15]);
+    alt[31] = N::to_double(thr - sh_mm[lane][15]);
+    P.g_cam[i] = N::to_double(dEn - thr);
+  }
   if (rs) {   // restart: the MM solution of warp 1
 #pragma unroll
     for (int a = 0; a < 9; ++a) cn.R[a] = sh_mm[lane][a];
@@ -910,8 +970,6 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
     }
     dEn = sh_mm[lane][15];
   }
-  const T E = first ? N::c(0.5f) * sF : N::from(cam_E[i]);
-  const T F = E + dE;
   cam_Fsum[i] = N::to_double(sF);   // sum of F_ij(x^k) over the camera's observations (objective trace)
   cam_F[i] = N::to_double(F);
   cam_Fb[i] = N::to_double(F + thr);
@@ -978,9 +1036,15 @@ __device__ __forceinline__ void block_sum2(double& f, long long& n, double* sf, 
   }
 }
 
+// s^(k+1) = (sqrt(4 s^2 + 1) + 1) / 2 (Eq. nesterov_scalar) with every operation rounded
+// separately (no contraction), as the host computes the table of a run
+__device__ __forceinline__ double nesterov_next(double s) {
+  return __dmul_rn(__dadd_rn(sqrt(__dadd_rn(__dmul_rn(__dmul_rn(4.0, s), s), 1.0)), 1.0), 0.5);
+}
+
 __global__ void __launch_bounds__(FIN_THREADS)
     k_finalize(int M, const double* __restrict__ cam_Fsum, const uint8_t* __restrict__ cam_rs, int n_tiles,
-               const int* __restrict__ tile_rs, double s2, IterParams P, double* __restrict__ blk,
+               const int* __restrict__ tile_rs, int n_blocks, double s2, IterParams P, double* __restrict__ blk,
                unsigned int* __restrict__ ticket, double* __restrict__ trace, int* __restrict__ restarts,
                int* __restrict__ flag) {
   __shared__ double sf[FIN_THREADS / 32];
@@ -995,28 +1059,156 @@ __global__ void __launch_bounds__(FIN_THREADS)
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) n += tile_rs[t];
   block_sum2(f, n, sf, sn);
+  const bool global = P.accelerated && P.restart_global;
+  double g = 0.0;
+  if (global) {   // global restart variant: sum over every block of E(k+1) - Fbar(k)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) g += P.g_cam[i];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) g += P.g_tile[t];
+    __syncthreads();   // thread 0 has read the first sums out of sf / sn
+    long long dummy = 0;
+    block_sum2(g, dummy, sf, sn);
+  }
   if (threadIdx.x == 0) {
-    blk[2 * blockIdx.x] = f;
-    blk[2 * blockIdx.x + 1] = (double)n;
+    blk[3 * blockIdx.x] = f;
+    blk[3 * blockIdx.x + 1] = (double)n;
+    blk[3 * blockIdx.x + 2] = g;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    double ft = 0.0, nt = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      ft += ((volatile double*)blk)[2 * b];
-      nt += ((volatile double*)blk)[2 * b + 1];
-    }
+  if (!last || threadIdx.x >= 32) return;
+  // the last block's first warp combines the block results: lane l takes blocks l, l + 32, ...
+  // in order, then a fixed shuffle tree (the same order on every run)
+  __threadfence();
+  double ft = 0.0, nt = 0.0, gt = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+    ft += ((volatile double*)blk)[3 * b];
+    nt += ((volatile double*)blk)[3 * b + 1];
+    if (global) gt += ((volatile double*)blk)[3 * b + 2];
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    ft += __shfl_xor_sync(0xffffffffu, ft, off);
+    nt += __shfl_xor_sync(0xffffffffu, nt, off);
+    gt += __shfl_xor_sync(0xffffffffu, gt, off);
+  }
+  if (threadIdx.x == 0) {
     const int k = *P.it;
     trace[k] = ft * s2;
-    restarts[k] = (int)nt;
+    if (global) {
+      // the test of Algorithm 1 for the block made of everything: sum E(k+1) > sum Fbar(k)
+      const int fire = gt > 0.0 ? 1 : 0;
+      *P.g_fire = fire;
+      restarts[k] = fire ? n_blocks : 0;
+      if (P.reset_s) {   // Eq. nesterov_scalar continued on the device, s <- 1 after a restart
+        const double s1 = fire ? 1.0 : nesterov_next(*P.s_dev);
+        const double s2n = nesterov_next(s1), s3n = nesterov_next(s2n);
+        *P.s_dev = s1;
+        const_cast<double*>(P.gam)[k + 1] = __ddiv_rn(__dsub_rn(s1, 1.0), s2n);
+        const_cast<double*>(P.gam)[k + 2] = __ddiv_rn(__dsub_rn(s2n, 1.0), s3n);
+      }
+    } else {
+      restarts[k] = (int)nt;
+    }
     if (!isfinite(ft)) atomicOr(flag, 1);
     *P.it = k + 1;
     *P.first = 0;
     *ticket = 0u;
   }
+}
+
+// Global restart variant, after the reduction: when the test fired, every camera takes the MM
+// alternative kept by the camera solve, with its restart metrics, the extrapolated rotation of
+// iteration k+1 and the pass pack (gamma^(k+1) read after the reduction advanced the counter;
+// 0 after a momentum reset).
+template <class Real>
+__global__ void k_fix_cams(int M, IterParams P, double* __restrict__ cam_x, double* __restrict__ cam_dx,
+                           double* __restrict__ cam_Rbar, double* __restrict__ cam_S, double* __restrict__ cam_E,
+                           uint8_t* __restrict__ cam_rs, V4<Real>* __restrict__ pack_next) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M || !*P.g_fire) return;
+  const double* a = P.cam_alt + (size_t)i * 32;
+  CamT<double> cn, ndx;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    cn.R[q] = a[q];
+    ndx.R[q] = a[15 + q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    cn.t[q] = a[9 + q];
+    cn.d[q] = a[12 + q];
+    ndx.t[q] = a[24 + q];
+    ndx.d[q] = a[27 + q];
+  }
+  double* x = cam_x + (size_t)i * CSTRIDE;
+  double* dx = cam_dx + (size_t)i * CSTRIDE;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    x[CS_R + q] = cn.R[q];
+    dx[CS_R + q] = ndx.R[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    x[CS_T + q] = cn.t[q];
+    dx[CS_T + q] = ndx.t[q];
+    x[CS_D + q] = cn.d[q];
+    dx[CS_D + q] = ndx.d[q];
+  }
+  cam_E[i] = a[30];
+  cam_S[i] = a[31];
+  cam_rs[i] = 1;
+  const double gn = P.gam[*P.it];
+  double K[9], Rb[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) K[q] = cn.R[q] + gn * ndx.R[q];
+  proj_rot3d_near(K, Rb);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) cam_Rbar[(size_t)i * 9 + q] = Rb[q];
+  write_pack_t<Real>(cn, ndx, Rb, pack_next + (size_t)i * P4N);
+}
+
+// Global restart variant: when the test fired, every landmark takes its MM alternative, stepped
+// from l^k as the landmark pass steps (double-float in MIXED).
+template <class Real, bool HAS_LO>
+__global__ void k_fix_lms(int N, IterParams P, const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo,
+                          const V4<Real>* __restrict__ lm_alt, V4<Real>* __restrict__ lmrec_out,
+                          V4<float>* __restrict__ lm_lo_out, uint8_t* __restrict__ lm_rs) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N || !*P.g_fire) return;
+  const size_t g = (size_t)j;
+  const V4<Real> A = lmrec[2 * g];
+  const V4<Real> a0 = lm_alt[2 * g], a1 = lm_alt[2 * g + 1];
+  V4<Real> nA, nB = lmrec_out[2 * g + 1];
+  if (HAS_LO) {
+    const V4<float> lo0 = lm_lo[g];
+    float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
+    float o0 = lo0.x, o1 = lo0.y, o2 = lo0.z;
+    df_add(h0, o0, float(a0.x));
+    df_add(h1, o1, float(a0.y));
+    df_add(h2, o2, float(a0.z));
+    nA.x = Real(h0);
+    nA.y = Real(h1);
+    nA.z = Real(h2);
+    V4<float> nlo;
+    nlo.x = o0;
+    nlo.y = o1;
+    nlo.z = o2;
+    nlo.w = 0.f;
+    lm_lo_out[g] = nlo;
+  } else {
+    nA.x = A.x + a0.x;
+    nA.y = A.y + a0.y;
+    nA.z = A.z + a0.z;
+    nB.w = a1.x;
+  }
+  nA.w = a0.x;
+  nB.x = a0.y;
+  nB.y = a0.z;
+  nB.z = a0.w;
+  lmrec_out[2 * g] = nA;
+  lmrec_out[2 * g + 1] = nB;
+  lm_rs[g] = 1;
 }
 
 // ---------------------------------------------------------------------------

@@ -136,7 +136,7 @@ def test_unrolled_grad_matches_oracle(case):
         kw = dict(chunk_obs=64, tile_obs=128, tile_lms=16)
     elif case == "circle-welsch-20":
         sc = scenes.circle_scene(seed=5)
-        loss, K, accel, scale_px = "welsch", 20, True, 3.0
+        loss, K, accel, scale_px = "welsch", 20, True, 60.0   # no saturated block (no exact restart ties)
     else:
         sc = cached_scene("street", scale=0.05)
         loss, K, accel, scale_px = sc.loss, 12, True, sc.loss_scale_px

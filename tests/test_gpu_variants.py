@@ -1,0 +1,154 @@
+"""Method variant on the CUDA path: the global adaptive restart (one test on the summed block
+metrics, all blocks restart together) with and without the momentum reset, against the FP64
+oracle's restatement of the same variant."""
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+from tests.conftest import cached_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_07026_b300 import build
+    build.build()
+
+
+def _ctx(sc, prec="fp64", **kw):
+    from paper_2305_07026_b300 import _lib as L
+    opts = dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    opts.update(kw)
+    d = L.Daba(sc.M, sc.N, sc.nnz, **opts)
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    d.set_state(sc.cams, sc.lms)
+    return d
+
+
+@pytest.mark.parametrize("workload,reset,eta", [("circle", False, 0.5), ("circle", True, 0.5), ("circle", False, 1.0),
+                                                ("street", True, 0.5)])
+def test_global_restart_matches_oracle_per_iteration(workload, reset, eta):
+    """F(x^k) within 1e-10 per iteration, the all-or-nothing decisions exactly (unless the global
+    test is a near-tie, after which the comparison stops), block metrics and the final iterate."""
+    sc = cached_scene("circle") if workload == "circle" else cached_scene("street", scale=0.05)
+    K = 30
+    o = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, eta=eta, restart="global", momentum_reset=reset)
+    prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
+    st = O.init_state(prob, R, t, dd, l)
+    d = _ctx(sc, "fp64", eta=eta, restart="global", momentum_reset=reset)
+    s2 = prob.s_norm ** 2
+    fired = compared = 0
+    for k in range(K):
+        st, info = O.step(prob, st)
+        tr = np.zeros(2)
+        rs = np.zeros(1, np.int32)
+        d.run(1, tr, rs)
+        assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
+        m = d.get_block_metrics()
+        np.testing.assert_allclose(m["Fbar_cam"], info.Fbar_cam * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_allclose(m["Fbar_lm"], info.Fbar_lm * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        want = int(info.restart_cam.sum() + info.restart_lm.sum())
+        gap = info.Etest_cam.sum() + info.Etest_lm.sum() - info.Fbar_cam.sum() - info.Fbar_lm.sum()
+        compared = k + 1
+        if abs(gap) <= 1e-9 * abs(info.F):
+            break
+        assert rs[0] == want, f"iteration {k}"
+        assert np.all(m["rs_cam"] == (want > 0)) and np.all(m["rs_lm"] == (want > 0))
+        fired += want > 0
+    assert compared == K and fired > 0
+    cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+    cams_g, lms_g = d.get_state()
+    np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    d.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_global_restart_runs_and_checkpoints_bit_exact(prec):
+    """One run of 40 iterations (CUDA graphs) equals 40 runs of one (direct launches), and a
+    checkpoint taken after 17 iterations resumes bit-exactly, the device Nesterov scalar included."""
+    sc = cached_scene("circle")
+    kw = dict(restart="global", momentum_reset=True)
+    a = _ctx(sc, prec, **kw)
+    ta = np.zeros(41)
+    ra = np.zeros(40, np.int32)
+    a.run(40, ta, ra)
+    b = _ctx(sc, prec, **kw)
+    tb, rb = [], []
+    for k in range(40):
+        t1 = np.zeros(2)
+        r1 = np.zeros(1, np.int32)
+        b.run(1, t1, r1)
+        tb.append(t1[0])
+        rb.append(r1[0])
+        if k == 16:
+            ck = b.export_checkpoint()
+    np.testing.assert_array_equal(ta[:40], np.array(tb))
+    np.testing.assert_array_equal(ra, np.array(rb))
+    assert (ra > 0).any()
+    c = _ctx(sc, prec, **kw)
+    c.import_checkpoint(ck)
+    tc = np.zeros(24)
+    c.run(23, tc)
+    np.testing.assert_array_equal(tc[:23], ta[17:40])
+    for x in (a, b, c):
+        x.close()
+
+
+def test_global_restart_mixed_reaches_fp64_objective():
+    sc = cached_scene("tourism", scale=0.005)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        d = _ctx(sc, prec, restart="global", momentum_reset=True)
+        tr = np.zeros(151)
+        d.run(150, tr)
+        out[prec] = tr
+        d.close()
+    assert out["mixed"].min() <= out["fp64"][-1] * (1 + 1e-5)
+
+
+def test_global_restart_monotone_at_eta_one():
+    """With eta = 1, Fbar^(k) = F(x^k), so the global test keeps F non-increasing."""
+    sc = cached_scene("tourism", scale=0.005)
+    d = _ctx(sc, "fp64", eta=1.0, restart="global")
+    tr = np.zeros(61)
+    d.run(60, tr)
+    assert np.all(np.diff(tr) <= 1e-12 * tr[:-1])
+    d.close()
+
+
+def test_global_restart_unrolled_grad():
+    """The reverse mode replays the global decisions (set on every block by the fix-up)."""
+    from oracle import daba_unrolled as U
+    from paper_2305_07026_b300 import _lib as L, scenes
+    sc = scenes.circle_scene(seed=3)
+    K = 15
+    o = O.Options(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, restart="global", eta=1.0)
+    rng = np.random.default_rng(4)
+    g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
+    gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
+    assert any(i.restart_cam.all() for i in res.infos)
+    opts = dict(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, prec="fp64", restart="global", eta=1.0)
+    with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        gcg, glg, gug = d.unrolled_grad(K, g_c, g_l)
+    for a, b in ((gcg, gc), (glg, gl), (gug, gu)):
+        assert np.max(np.abs(a - b)) <= 1e-7 * np.max(np.abs(b))
+    with L.Daba(sc.M, sc.N, sc.nnz, **dict(opts, momentum_reset=True)) as d:
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        with pytest.raises(L.DabaError):
+            d.unrolled_grad(K, g_c, g_l)
+
+
+def test_variant_options_validated():
+    from paper_2305_07026_b300 import _lib as L
+    with pytest.raises(L.DabaError):
+        L.Daba(4, 4, 8, restart="block", momentum_reset=True)
+    with pytest.raises(L.DabaError):
+        L.Daba(4, 4, 8, restart=7)
