@@ -315,6 +315,71 @@ def solve_cameras(xi, mj, Rz, tz, dz, cam_idx, u, M, n_alt):
     return R, t, d
 
 
+def skew(v):
+    """[v]x, the cross-product matrix (v [..., 3] -> [..., 3, 3])."""
+    z = np.zeros(v.shape[:-1])
+    return np.stack([np.stack([z, -v[..., 2], v[..., 1]], -1), np.stack([v[..., 2], z, -v[..., 0]], -1),
+                     np.stack([-v[..., 1], v[..., 0], z], -1)], -2)
+
+
+LM_MU0 = 1e-3      # initial damping of the camera LM step (relative to diag of the model Hessian)
+LM_TRIES = 8       # damping increases (x10) before the step is given up
+
+
+def lm_model(xi, mj, Rz, tz, dz, cam_idx, u, M):
+    """Gauss-Newton model of E^alpha(. | z) of every camera at c_z in theta = (phi, tau, delta)
+    (see solve_cameras_lm): Hessian A (M, 9, 9), gradient b (M, 9), and per observation the
+    residual r(0) and ray p(d_z)."""
+    s = u[:, 0] ** 2 + u[:, 1] ** 2
+    phi_u = np.stack([np.ones_like(s), s, s * s], 1)
+    p0 = ray(u, dz[cam_idx])
+    Rzi = Rz[cam_idx]
+    r0 = np.einsum("nab,nb->na", Rzi, p0) + mj.lam[:, None] * tz[cam_idx] - mj.g
+    J = np.zeros((u.shape[0], 3, 9))
+    J[:, :, 0:3] = -np.einsum("nab,nbc->nac", Rzi, skew(p0))
+    J[:, 0, 3] = J[:, 1, 4] = J[:, 2, 5] = mj.lam
+    J[:, :, 6:9] = Rzi[:, :, 2][:, :, None] * phi_u[:, None, :]
+    w = mj.w
+    A = 2.0 * segsum(cam_idx, w[:, None, None] * np.einsum("nai,naj->nij", J, J), M)
+    A += xi * np.diag([2.0, 2.0, 2.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0])[None]
+    b = 2.0 * segsum(cam_idx, w[:, None] * np.einsum("nai,na->ni", J, r0), M)
+    return A, b, r0, p0
+
+
+def solve_cameras_lm(xi, mj, Rz, tz, dz, cam_idx, u, M):
+    """One successful Levenberg-Marquardt step on E^alpha(c | z) of every camera, from c_z
+    (the subproblem solver the paper reports for DABA: one successful inner LM step).
+
+    Parameters theta = (phi, tau, delta): R = R_z Exp(phi), t = t_z + tau, d = d_z + delta.
+    Per observation the residual of Eq. P is r = R p(d) + lambda t - g with Jacobian at theta = 0
+    J = [-R_z [p_z]x, lambda I, (R_z e3) (1, s, s^2)]. Gauss-Newton model of the block surrogate:
+    Hessian A = 2 sum w J^T J + xi diag(2 I, I, I) (the proximal term xi/2 |R - R_z|^2 to second
+    order is xi |phi|^2), gradient b = 2 sum w J^T r(0). The step solves (A + mu diag A) theta = -b;
+    it is taken if the surrogate decreases, E(c | z) < E(c_z | z), else mu grows tenfold; after
+    LM_TRIES failures the camera stays at c_z. The decrease is evaluated from the residual
+    differences r(c) - r(0), so that no O(F) values cancel."""
+    A, b, r0, p0 = lm_model(xi, mj, Rz, tz, dz, cam_idx, u, M)
+    w = mj.w
+    R, t, d = Rz.copy(), tz.copy(), dz.copy()
+    for i in range(M):
+        obs = np.flatnonzero(cam_idx == i)
+        mu = LM_MU0
+        for _ in range(LM_TRIES):
+            Ad = A[i] + mu * np.diag(np.diag(A[i]))
+            th = np.linalg.solve(Ad, -b[i])
+            Rc = Rz[i] @ so3_exp(th[0:3])[0]
+            tc, dc = tz[i] + th[3:6], dz[i] + th[6:9]
+            dr = (np.einsum("ab,nb->na", Rc, ray(u[obs], np.broadcast_to(dc, (obs.size, 3))))
+                  - np.einsum("ab,nb->na", Rz[i], p0[obs]) + mj.lam[obs, None] * (tc - tz[i]))
+            dE = np.sum(w[obs] * np.einsum("na,na->n", dr, dr + 2.0 * r0[obs])) \
+                + 0.5 * xi * (np.sum((Rc - Rz[i]) ** 2) + np.sum((tc - tz[i]) ** 2) + np.sum((dc - dz[i]) ** 2))
+            if dE < 0.0:
+                R[i], t[i], d[i] = Rc, tc, dc
+                break
+            mu *= 10.0
+    return R, t, d
+
+
 # ----------------------------------------------------------------------------
 # Algorithm 1
 # ----------------------------------------------------------------------------
@@ -330,6 +395,7 @@ class Options:
     pixel_scale: float = 0.0     # 0: median focal length
     restart: str = "block"       # "block": Algorithm 1; "global": one test on the summed block metrics
     momentum_reset: bool = False  # with restart="global": s <- 1 after a restart
+    cam_solver: str = "scam"     # "scam": block-exact alternations; "lm": one successful LM step
 
 
 @dataclasses.dataclass
@@ -424,14 +490,16 @@ def step(prob: Problem, st: State):
     Fbar_cam = (1.0 - eta) * st.Fbar_cam + eta * F_cam
     Fbar_lm = (1.0 - eta) * st.Fbar_lm + eta * F_lm
     # minimization: accelerated (Eq. update_amm) or plain MM (Eq. update_mm)
-    Rm, tm, dm = solve_cameras(xi, mj_k, st.R, st.t, st.d, ci, u, M, o.cam_alternations)
+    cams_solve = (lambda mj, Rz, tz, dz: solve_cameras_lm(xi, mj, Rz, tz, dz, ci, u, M)) if o.cam_solver == "lm" \
+        else (lambda mj, Rz, tz, dz: solve_cameras(xi, mj, Rz, tz, dz, ci, u, M, o.cam_alternations))
+    Rm, tm, dm = cams_solve(mj_k, st.R, st.t, st.d)
     lm_mm = solve_landmarks(xi, mj_k, st.l, li, N)
     E0_cam = E_cam(xi, mj_k, st.R, st.t, st.d, st.R, st.t, st.d, ci, u, M)   # E^alpha(x^k | x^k)
     E0_lm = E_lm(xi, mj_k, st.l, st.l, li, N)
     Emm_cam = E_cam(xi, mj_k, Rm, tm, dm, st.R, st.t, st.d, ci, u, M) + F_cam - E0_cam
     Emm_lm = E_lm(xi, mj_k, lm_mm, st.l, li, N) + F_lm - E0_lm
     if o.accelerated:
-        Ra, ta, da = solve_cameras(xi, mj_b, Rb, tb, db, ci, u, M, o.cam_alternations)
+        Ra, ta, da = cams_solve(mj_b, Rb, tb, db)
         la = solve_landmarks(xi, mj_b, lb, li, N)
         # Eq. Eak for the accelerated update, then the adaptive restart test
         Ea_cam = E_cam(xi, mj_k, Ra, ta, da, st.R, st.t, st.d, ci, u, M) + F_cam - E0_cam

@@ -430,14 +430,68 @@ def test_camera_solve_brute_force_tiny():
     assert E2 <= bf.fun * (1 + 1e-6) + 1e-14
 
 
+def _lm_energy(xi, mj, Rz, tz, dz, ci, u, M, i, th):
+    """E^alpha(c | z) of camera i at R = R_z Exp(phi), t = t_z + tau, d = d_z + delta (every other
+    camera at its conditioning point)."""
+    R, t, d = Rz.copy(), tz.copy(), dz.copy()
+    R[i] = Rz[i] @ O.so3_exp(th[0:3])[0]
+    t[i] = tz[i] + th[3:6]
+    d[i] = dz[i] + th[6:9]
+    return O.E_cam(xi, mj, R, t, d, Rz, tz, dz, ci, u, M)[i]
+
+
+@pytest.mark.parametrize("noise_free", [False, True])
+def test_lm_model_matches_surrogate_derivatives(noise_free):
+    """The camera LM model: its gradient is the surrogate's gradient in (phi, tau, delta) by central
+    differences; at a zero-residual point (noise-free truth, r(0) = 0) its Gauss-Newton Hessian is
+    the exact Hessian (second differences)."""
+    sc = cached_scene("circle", noise_free=noise_free)
+    opts = O.Options(loss="huber", loss_scale_px=2.0, xi=1e-3)
+    cams = sc.cams_gt if noise_free else sc.cams
+    lms = sc.lms_gt if noise_free else sc.lms
+    prob, R, t, d, l = O.make_problem(cams, lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    ci, li, u = prob.cam_idx, prob.lm_idx, prob.u
+    mj = O.majorizer(prob.loss, prob.c, R[ci], t[ci], d[ci], l[li], u)
+    A, b, r0, _ = O.lm_model(opts.xi, mj, R, t, d, ci, u, prob.M)
+    scale = np.array([1e-3] * 3 + [1e-3] * 3 + [1e-3, 1e-3, 1e-3])
+    for i in (0, 7):
+        E = lambda th: _lm_energy(opts.xi, mj, R, t, d, ci, u, prob.M, i, th)
+        g = np.array([(E(h * e) - E(-h * e)) / (2 * h) for e, h in zip(np.eye(9), scale * 1e-2)])
+        if not noise_free:
+            np.testing.assert_allclose(b[i], g, rtol=1e-5, atol=1e-7 * np.abs(b[i]).max())
+            continue
+        assert np.abs(r0).max() < 1e-9
+        H = np.zeros((9, 9))
+        for a in range(9):
+            for c in range(9):
+                ea, ec = np.eye(9)[a] * scale[a], np.eye(9)[c] * scale[c]
+                H[a, c] = (E(ea + ec) - E(ea - ec) - E(-ea + ec) + E(-ea - ec)) / (4 * scale[a] * scale[c])
+        np.testing.assert_allclose(A[i], H, rtol=1e-4, atol=1e-6 * np.abs(A[i]).max())
+
+
+def test_lm_step_decreases_surrogate(circle):
+    """One successful LM step lowers E^alpha(. | z) of every camera with a nonzero gradient."""
+    sc = circle
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    ci, li, u = prob.cam_idx, prob.lm_idx, prob.u
+    mj = O.majorizer(prob.loss, prob.c, R[ci], t[ci], d[ci], l[li], u)
+    E0 = O.E_cam(opts.xi, mj, R, t, d, R, t, d, ci, u, prob.M)
+    Rl, tl, dl = O.solve_cameras_lm(opts.xi, mj, R, t, d, ci, u, prob.M)
+    El = O.E_cam(opts.xi, mj, Rl, tl, dl, R, t, d, ci, u, prob.M)
+    assert np.all(El < E0)
+
+
 # ----------------------------------------------------------------------------
 # Algorithm 1: Lemma 1, Eq. FklFk0, DUBA monotonicity, convergence, fixed point
 # ----------------------------------------------------------------------------
 
-@pytest.mark.parametrize("eta", [0.1, 0.5, 1.0])
-def test_algorithm1_invariants(circle, eta):
+@pytest.mark.parametrize("eta,solver", [(0.1, "scam"), (0.5, "scam"), (1.0, "scam"), (0.5, "lm")])
+def test_algorithm1_invariants(circle, eta, solver):
+    """Lemma 1a-c, Eq. FakplFk1 and Eq. FklFk0 every iteration, for both camera solvers (any
+    solver that does not increase E^alpha(. | z) from c_z keeps them)."""
     sc = circle
-    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, eta=eta, xi=1e-8)
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, eta=eta, xi=1e-8, cam_solver=solver)
     prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
     st = O.init_state(prob, R, t, d, l)
     Fbar_global = O.objective(prob.loss, prob.c, R, t, d, l, prob.cam_idx, prob.lm_idx, prob.u)
@@ -505,11 +559,12 @@ def test_global_restart_invariants(circle, eta, reset):
             assert gammas[k] > 0.0
 
 
-@pytest.mark.parametrize("loss", ["trivial", "huber", "cauchy", "welsch"])
-def test_duba_monotone(loss):
+@pytest.mark.parametrize("loss,solver", [("trivial", "scam"), ("huber", "scam"), ("cauchy", "scam"),
+                                         ("welsch", "scam"), ("huber", "lm")])
+def test_duba_monotone(loss, solver):
     """DUBA (always the MM update, Sec. 7.2) never increases F (Sec. 4)."""
     sc = cached_scene("circle")
-    opts = O.Options(loss=loss, loss_scale_px=2.0, accelerated=False)
+    opts = O.Options(loss=loss, loss_scale_px=2.0, accelerated=False, cam_solver=solver)
     res = O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts, 15)
     assert np.all(np.diff(res.trace_px2) <= 1e-12 * res.trace_px2[:-1])
     assert res.trace_px2[-1] < 0.9 * res.trace_px2[0]
