@@ -86,7 +86,16 @@ typedef struct {
    * also restarts Nesterov's scalar: s^(k+1) = 1 after an iteration whose test fired. */
   int32_t restart_mode;
   int32_t momentum_reset;
+  /* camera block solver (method variant; default DABA_CAM_SCAM): DABA_CAM_SCAM runs
+   * cam_alternations block-exact alternations (R-step: ProjRot3D, (t, d)-step: normal
+   * equations); DABA_CAM_LM takes one successful Levenberg-Marquardt step (Sec. 7.1 reports one
+   * successful inner LM step per subproblem) on the Gauss-Newton model in R_z Exp(phi), t, d,
+   * damping 1e-3 x diag, raised tenfold up to 8 times, the step kept only if E^alpha(. | z)
+   * decreases. */
+  int32_t cam_solver;
 } daba_options;
+
+typedef enum { DABA_CAM_SCAM = 0, DABA_CAM_LM = 1 } daba_cam_solver;
 
 typedef enum { DABA_RESTART_BLOCK = 0, DABA_RESTART_GLOBAL = 1 } daba_restart_mode;
 
@@ -161,7 +170,8 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
  * would), keeps the state every 10 iterations and recomputes the others, so that it costs
  * about three forward runs plus the adjoint kernels and holds about K/10 + 11 copies of the
  * state. Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
- * (DABA_ERR_ARG for MIXED and for momentum_reset, whose Nesterov scalars live on the device);
+ * (DABA_ERR_ARG for MIXED, for momentum_reset, whose Nesterov scalars live on the device, and for
+ * DABA_CAM_LM, whose step acceptance has no adjoint here);
  * DABA_ERR_STATE if iterations have run since the state was set. */
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream);

@@ -21,6 +21,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_DEGENERATE", "ERR_NONFINITE",
 LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
 PREC = {"fp64": 0, "mixed": 1}
 RESTART = {"block": 0, "global": 1}
+CAM_SOLVERS = {"scam": 0, "lm": 1}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_07026_b300.build`")
@@ -33,7 +34,7 @@ class daba_options(ctypes.Structure):
                 ("eta", ctypes.c_double), ("accelerated", ctypes.c_int), ("cam_alternations", ctypes.c_int),
                 ("pixel_scale", ctypes.c_double), ("prec", ctypes.c_int), ("chunk_obs", ctypes.c_int32),
                 ("tile_obs", ctypes.c_int32), ("tile_lms", ctypes.c_int32), ("restart_mode", ctypes.c_int32),
-                ("momentum_reset", ctypes.c_int32)]
+                ("momentum_reset", ctypes.c_int32), ("cam_solver", ctypes.c_int32)]
 
 
 _p = ctypes.c_void_p
@@ -105,7 +106,7 @@ def current_stream():
 
 def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True, cam_alternations=2,
             pixel_scale=0.0, prec="mixed", chunk_obs=0, tile_obs=0, tile_lms=0, restart="block",
-            momentum_reset=False) -> daba_options:
+            momentum_reset=False, cam_solver="scam") -> daba_options:
     o = daba_options()
     daba_default_options(ctypes.byref(o))
     o.loss = LOSSES[loss] if isinstance(loss, str) else int(loss)
@@ -119,6 +120,7 @@ def options(loss="huber", loss_scale_px=1.0, xi=1e-10, eta=0.5, accelerated=True
     o.chunk_obs, o.tile_obs, o.tile_lms = int(chunk_obs), int(tile_obs), int(tile_lms)
     o.restart_mode = RESTART[restart] if isinstance(restart, str) else int(restart)
     o.momentum_reset = int(bool(momentum_reset))
+    o.cam_solver = CAM_SOLVERS[cam_solver] if isinstance(cam_solver, str) else int(cam_solver)
     return o
 
 

@@ -350,24 +350,30 @@ cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+template <int SOLVER>
+cudaError_t launch_camsolve_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   ctx->launches++;
   const IterParams P = iter_params(ctx);
   const int blocks = (ctx->M + 31) / 32;   // 32 cameras per CTA (two warps)
   if (is_mixed(ctx))
-    k_camsolve<float><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
+    k_camsolve<float, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
                                              (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
                                              (V4<float>*)pack_at(ctx, k + 1));
   else
-    k_camsolve<double><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
+    k_camsolve<double, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
                                               (const double*)ctx->chunk_part, (double*)ctx->cam_x,
                                               (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
                                               (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,
                                               (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
                                               (V4<double>*)pack_at(ctx, k + 1));
   return cudaGetLastError();
+}
+
+cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  if (ctx->opt.cam_solver == DABA_CAM_LM) return launch_camsolve_t<CAM_LM>(ctx, st, k);
+  return launch_camsolve_t<CAM_SCAM>(ctx, st, k);
 }
 
 cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
@@ -729,6 +735,7 @@ void daba_default_options(daba_options* o) {
   o->tile_lms = 0;
   o->restart_mode = DABA_RESTART_BLOCK;
   o->momentum_reset = 0;
+  o->cam_solver = DABA_CAM_SCAM;
 }
 
 const char* daba_last_error(const daba_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -778,7 +785,8 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
       (o.loss != DABA_LOSS_TRIVIAL && !(o.loss_scale_px > 0)) || (o.prec != DABA_FP64 && o.prec != DABA_MIXED) ||
       (o.restart_mode != DABA_RESTART_BLOCK && o.restart_mode != DABA_RESTART_GLOBAL) ||
       (o.momentum_reset != 0 && o.momentum_reset != 1) ||
-      (o.momentum_reset && o.restart_mode != DABA_RESTART_GLOBAL))
+      (o.momentum_reset && o.restart_mode != DABA_RESTART_GLOBAL) ||
+      (o.cam_solver != DABA_CAM_SCAM && o.cam_solver != DABA_CAM_LM))
     return bad("options");
   ctx->M = M;
   ctx->N = N;
@@ -1339,6 +1347,8 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient needs an FP64 context");
   if (ctx->opt.momentum_reset)
     return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
+  if (ctx->opt.cam_solver != DABA_CAM_SCAM)
+    return fail(ctx, DABA_ERR_ARG, "the unrolled gradient supports the S-CAM camera solver only");
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   if (ctx->k != 0) return fail(ctx, DABA_ERR_STATE, "iterations have run since the state was set");
   cudaStream_t st = (cudaStream_t)stream;

@@ -736,6 +736,149 @@ __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, 
   }
 }
 
+// Camera solver variant: one successful Levenberg-Marquardt step on E^alpha(. | z) from c_z.
+// Parameters theta = (phi, tau, delta) with R = R_z Exp(phi), t = t_z + tau, d = d_z + delta.
+// With sigma_a the camera-frame direction of column a of M (e1, e2, d_m e3) the Gauss-Newton
+// model of the surrogate in the statistics is (camera frame, q_b = sum_a<5 H_ab sigma_a,
+// Q = sum w p p^T = [q_0, q_1, sum_m d_m q_(2+m)], b_a = R_z^T B_a, r_c = row c of R_z):
+//   A_phiphi = 2 (tr Q I - Q) + 2 xi I     A_phitau[:, c] = -2 r_c x q_5
+//   A_phidel[:, n] = 2 (q_(2+n),y, -q_(2+n),x, 0)
+//   A_tautau = (2 H_55 + xi) I             A_taudel[c][n] = 2 H_(5,2+n) R_z[c][2]
+//   A_deldel = 2 H[2:5, 2:5] + xi I
+//   g_phi = 2 sum_a<5 sigma_a x b_a        g_tau = 2 B_5      g_del[n] = 2 (R_z e3) . B_(2+n)
+// The step solves (A + mu diag A) theta = -g (Cholesky) and is taken if cam_phi < 0; mu starts
+// at LM_MU0 and grows tenfold, at most LM_TRIES times; otherwise the camera stays at c_z.
+constexpr double LM_MU0 = 1e-3;
+constexpr int LM_TRIES = 8;
+
+__device__ __forceinline__ int lt9(int i, int j) { return i * (i + 1) / 2 + j; }   // packed lower, j <= i
+
+// the model (A packed lower, g) at c_z
+__device__ inline void cam_lm_model(const double* st, const CamT<double>& z, double xi, double* A, double* g) {
+  {
+    double q[6][3];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      q[b][0] = st_H(st, 0, b);
+      q[b][1] = st_H(st, 1, b);
+      q[b][2] = z.d[0] * st_H(st, 2, b) + z.d[1] * st_H(st, 3, b) + z.d[2] * st_H(st, 4, b);
+    }
+    double Q[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      Q[r][0] = q[0][r];
+      Q[r][1] = q[1][r];
+      Q[r][2] = z.d[0] * q[2][r] + z.d[1] * q[3][r] + z.d[2] * q[4][r];
+    }
+    const double trQ = Q[0][0] + Q[1][1] + Q[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) A[lt9(i, j)] = 2.0 * ((i == j ? trQ : 0.0) - 0.5 * (Q[i][j] + Q[j][i])) + (i == j ? 2.0 * xi : 0.0);
+    // tau rows (3..5): A[3 + c][i] for phi column i = (-2 r_c x q_5)_i
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const double r0 = z.R[cc * 3 + 0], r1 = z.R[cc * 3 + 1], r2 = z.R[cc * 3 + 2];
+      A[lt9(3 + cc, 0)] = -2.0 * (r1 * q[5][2] - r2 * q[5][1]);
+      A[lt9(3 + cc, 1)] = -2.0 * (r2 * q[5][0] - r0 * q[5][2]);
+      A[lt9(3 + cc, 2)] = -2.0 * (r0 * q[5][1] - r1 * q[5][0]);
+#pragma unroll
+      for (int j = 0; j <= cc; ++j) A[lt9(3 + cc, 3 + j)] = cc == j ? 2.0 * st_H(st, 5, 5) + xi : 0.0;
+    }
+    // delta rows (6..8)
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+      A[lt9(6 + n, 0)] = 2.0 * q[2 + n][1];
+      A[lt9(6 + n, 1)] = -2.0 * q[2 + n][0];
+      A[lt9(6 + n, 2)] = 0.0;
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) A[lt9(6 + n, 3 + cc)] = 2.0 * st_H(st, 5, 2 + n) * z.R[cc * 3 + 2];
+#pragma unroll
+      for (int m = 0; m <= n; ++m) A[lt9(6 + n, 6 + m)] = 2.0 * st_H(st, 2 + n, 2 + m) + (m == n ? xi : 0.0);
+    }
+    // gradient
+    double bc[5][3];   // b_a = R_z^T B_a (camera frame)
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        bc[a][k] = z.R[0 * 3 + k] * st_B(st, a, 0) + z.R[1 * 3 + k] * st_B(st, a, 1) + z.R[2 * 3 + k] * st_B(st, a, 2);
+    // sigma_a x b_a: e1 x b = (0, -b_z, b_y), e2 x b = (b_z, 0, -b_x), d_m e3 x b = d_m (-b_y, b_x, 0)
+    g[0] = 2.0 * (bc[1][2] - z.d[0] * bc[2][1] - z.d[1] * bc[3][1] - z.d[2] * bc[4][1]);
+    g[1] = 2.0 * (-bc[0][2] + z.d[0] * bc[2][0] + z.d[1] * bc[3][0] + z.d[2] * bc[4][0]);
+    g[2] = 2.0 * (bc[0][1] - bc[1][0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[3 + k] = 2.0 * st_B(st, 5, k);
+#pragma unroll
+    for (int n = 0; n < 3; ++n)
+      g[6 + n] = 2.0 * (z.R[2] * st_B(st, 2 + n, 0) + z.R[5] * st_B(st, 2 + n, 1) + z.R[8] * st_B(st, 2 + n, 2));
+  }
+}
+
+__device__ inline void cam_lm(const double* st, const CamT<double>& z, double xi, CamT<double>& c) {
+  c = z;
+  double A[45], g[9];
+  cam_lm_model(st, z, xi, A, g);
+  double mu = LM_MU0;
+  for (int tr = 0; tr < LM_TRIES; ++tr, mu *= 10.0) {
+    // Cholesky of A + mu diag(A), then the two triangular solves
+    double L[45];
+    bool ok = true;
+    for (int i = 0; i < 9; ++i) {
+      for (int j = 0; j <= i; ++j) {
+        double v = A[lt9(i, j)] * (i == j ? 1.0 + mu : 1.0);
+        for (int k = 0; k < j; ++k) v -= L[lt9(i, k)] * L[lt9(j, k)];
+        if (i == j) {
+          if (!(v > 0.0)) ok = false;
+          L[lt9(i, i)] = sqrt(ok ? v : 1.0);
+        } else {
+          L[lt9(i, j)] = v / L[lt9(j, j)];
+        }
+      }
+    }
+    if (!ok) continue;
+    double y[9], th[9];
+    for (int i = 0; i < 9; ++i) {
+      double v = -g[i];
+      for (int k = 0; k < i; ++k) v -= L[lt9(i, k)] * y[k];
+      y[i] = v / L[lt9(i, i)];
+    }
+    for (int i = 8; i >= 0; --i) {
+      double v = y[i];
+      for (int k = i + 1; k < 9; ++k) v -= L[lt9(k, i)] * th[k];
+      th[i] = v / L[lt9(i, i)];
+    }
+    CamT<double> cand;
+    double E[9];
+    rodrigues(th, E);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc)
+        cand.R[r * 3 + cc] = z.R[r * 3 + 0] * E[0 * 3 + cc] + z.R[r * 3 + 1] * E[1 * 3 + cc] + z.R[r * 3 + 2] * E[2 * 3 + cc];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cand.t[k] = z.t[k] + th[3 + k];
+      cand.d[k] = z.d[k] + th[6 + k];
+    }
+    if (cam_phi(st, z, cand, xi) < 0.0) {
+      c = cand;
+      return;
+    }
+  }
+}
+
+// the camera block solver of the variant in use
+enum { CAM_SCAM = 0, CAM_LM = 1 };
+template <int SOLVER>
+__device__ __forceinline__ void cam_solve(const double* st, const CamT<double>& z, double xi, int n_alt,
+                                          CamT<double>& c) {
+  if (SOLVER == CAM_LM)
+    cam_lm(st, z, xi, c);
+  else
+    cam_scam(st, z, xi, n_alt, c);
+}
+
 __device__ __forceinline__ void acc_add(double& a, float x) { a += widen(x); }
 __device__ __forceinline__ void acc_add(double& a, double x) { a += x; }
 
@@ -850,7 +993,7 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
 // Camera block solves in FP64: the statistics summed over the camera's chunks, the
 // accelerated S-CAM solve, the restart metrics and test, the MM solve, and the extrapolated
 // rotation and pack of iteration k+1.
-template <class Real>
+template <class Real, int SOLVER>
 __global__ void __launch_bounds__(CAMSOLVE_THREADS)
     k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
                double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
@@ -890,7 +1033,7 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
     if (role == 1) {   // MM solve from x^k with the x^k statistics
       sum_stats<Real, T>(part, c0, c1, PART_XK, st);
       CamT<T> cm;
-      cam_scam(st, ck, xi, P.n_alt, cm);
+      cam_solve<SOLVER>(st, ck, xi, P.n_alt, cm);
       const T dm = cam_phi(st, ck, cm, xi);
 #pragma unroll
       for (int a = 0; a < 9; ++a) sh_mm[lane][a] = cm.R[a];
@@ -911,7 +1054,7 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
         cb.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
       }
       sum_stats<Real, T>(part, c0, c1, PART_XB, st);
-      cam_scam(st, cb, xi, P.n_alt, cn);
+      cam_solve<SOLVER>(st, cb, xi, P.n_alt, cn);
       sum_stats<Real, T>(part, c0, c1, PART_XK, st);
       dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
     }

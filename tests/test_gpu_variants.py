@@ -152,3 +152,61 @@ def test_variant_options_validated():
         L.Daba(4, 4, 8, restart="block", momentum_reset=True)
     with pytest.raises(L.DabaError):
         L.Daba(4, 4, 8, restart=7)
+
+
+@pytest.mark.parametrize("workload,accel", [("circle", True), ("street", True), ("circle", False)])
+def test_lm_camera_solver_matches_oracle_per_iteration(workload, accel):
+    """One successful LM step per camera subproblem (the paper's reported inner solver): F(x^k)
+    within 1e-10 per iteration, restart decisions exactly (unless a near-tie), final iterate."""
+    sc = cached_scene("circle") if workload == "circle" else cached_scene("street", scale=0.05)
+    K = 20
+    o = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, accelerated=accel, cam_solver="lm")
+    prob, R, t, dd, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o)
+    st = O.init_state(prob, R, t, dd, l)
+    d = _ctx(sc, "fp64", accelerated=accel, cam_solver="lm")
+    s2 = prob.s_norm ** 2
+    for k in range(K):
+        st, info = O.step(prob, st)
+        tr = np.zeros(2)
+        rs = np.zeros(1, np.int32)
+        d.run(1, tr, rs)
+        assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
+        m = d.get_block_metrics()
+        flips = 0
+        for which in ("cam", "lm"):
+            gpu = m[f"rs_{which}"].astype(bool)
+            ora = getattr(info, f"restart_{which}")
+            E, Fb, F = (getattr(info, f"Etest_{which}"), getattr(info, f"Fbar_{which}"),
+                        np.abs(getattr(info, f"F_{which}")))
+            tie = np.abs(E - Fb) <= 1e-9 * np.maximum(F, 1e-300)
+            assert not ((gpu != ora) & ~tie).any(), f"iteration {k}: {which}"
+            flips += int((gpu != ora).sum())
+        assert flips == 0, f"iteration {k}: near-tie restart decision"
+    cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+    cams_g, lms_g = d.get_state()
+    np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    d.close()
+
+
+def test_lm_camera_solver_mixed_reaches_fp64_objective():
+    sc = cached_scene("tourism", scale=0.005)
+    out = {}
+    for prec in ("fp64", "mixed"):
+        d = _ctx(sc, prec, cam_solver="lm")
+        tr = np.zeros(151)
+        d.run(150, tr)
+        out[prec] = tr
+        d.close()
+    assert out["mixed"].min() <= out["fp64"][-1] * (1 + 1e-5)
+
+
+def test_lm_camera_solver_not_differentiated():
+    from paper_2305_07026_b300 import _lib as L
+    sc = cached_scene("circle")
+    d = _ctx(sc, "fp64", cam_solver="lm")
+    with pytest.raises(L.DabaError):
+        d.unrolled_grad(3, np.zeros((sc.M, 9)), np.zeros((sc.N, 3)))
+    d.close()
+    with pytest.raises(L.DabaError):
+        L.Daba(4, 4, 8, cam_solver=5)
