@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--fp64-steps", type=int, default=None, help="iterations of the FP64 comparison run")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-variants", action="store_true", help="skip the method-variant leg")
     ap.add_argument("--unrolled-steps", type=int, default=10,
                     help="iterations differentiated by the timed reverse-mode call (FP64; 0 skips it)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
@@ -371,6 +372,33 @@ def run_ours(args, rank, world, local):
                 "initial_px2": float(tr64[0])}
     fp64_value = sc.nnz * Kf / (ms64 / 1e3)
 
+    # ---- method variants (MIXED, same x^0 and iteration count as the accuracy leg): time per
+    # iteration and the objective reached, against Algorithm 1 with the S-CAM camera solver
+    variants = None
+    if not args.no_variants:
+        variants = {"iters": Kf, "reference_final_px2": float(trm[Kf])}
+        for name, kw in (("global_restart", dict(restart="global")),
+                         ("global_restart_momentum_reset", dict(restart="global", momentum_reset=True)),
+                         ("lm_camera_solver", dict(cam_solver="lm"))):
+            t_setup = time.perf_counter()
+            dv = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="mixed", **kw)
+            dv.set_observations(sc.cam_idx, sc.lm_idx, sc.uv, stream=sp)
+            dv.set_state(sc.cams, sc.lms, stream=sp)
+            t_setup = time.perf_counter() - t_setup
+            # one untimed iteration (pixel upload, checks, graph capture), then x^0 again
+            dv.run(1, stream=sp)
+            dv.set_state(sc.cams, sc.lms, stream=sp)
+            trv = np.zeros(Kf + 1)
+            rsv = np.zeros(Kf, np.int32)
+            e0.record(stream)
+            dv.run(Kf, trv, rsv, stream=sp)
+            e1.record(stream)
+            e1.synchronize()
+            dv.close()
+            variants[name] = {"ms_per_iteration": e0.elapsed_time(e1) / Kf, "final_px2": float(trv[Kf]),
+                              "final_rel_to_reference": float((trv[Kf] - trm[Kf]) / trm[Kf]),
+                              "restart_iterations": int(np.count_nonzero(rsv)), "setup_s": t_setup}
+
     # ---- roofline of the dominant kernel (per launch, live CUDA events)
     names = ["cam_prepare", "cpass", "lpass", "camsolve", "finalize"]
     per_launch_ms = {n: kern_ms[i] / (K if i else -(-K // 1024)) for i, n in enumerate(names)}
@@ -451,7 +479,7 @@ def run_ours(args, rank, world, local):
         "accuracy": accuracy,
         "kernel_ms_per_launch": per_launch_ms,
         "roofline": roofline, "roofline_kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gradient": grad,
-        "unrolled_gradient": unrolled,
+        "unrolled_gradient": unrolled, "variants": variants,
         "gpu_launches": int(launches),
         "clocks": ck,
     }
