@@ -48,7 +48,7 @@ enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
 // ---- camera state (doubles, stride 16): R[9] t[3] d[3] pad
 enum { CS_R = 0, CS_T = 9, CS_D = 12, CSTRIDE = 16 };
 
-constexpr int CPASS_WARPS = 1;   // one warp per CTA: 13 resident warps per SM at 147 registers (12 with 4-warp CTAs)
+constexpr int CPASS_WARPS = 1;   // one warp per CTA: 12 resident warps per SM at 156 registers
 constexpr int CAMSOLVE_THREADS = 64;   // one camera per active thread
 constexpr int LPASS_THREADS = 128;
 constexpr int LPASS_UNROLL = 4;   // observations whose records a thread loads before storing any
@@ -134,6 +134,97 @@ __device__ __forceinline__ void accumulate_cam(Real* acc, const ObsEval<Real>& e
   acc[CP_G] += ev.gap;
 }
 
+// Per-lane camera statistics of the camera pass and their chunk reduction. FP64: the 80
+// accumulators in CP_* order. FP32: the x̄^k and x^k statistics side by side as float2 pairs
+// (x: x̄^k, y: x^k), accumulated with the packed FP32 instructions of sm_100+ (__ffma2_rn and
+// friends; per component the same rounding as the scalar FMA), so one instruction serves both
+// sets. Both store the chunk partial in the layout of PART_*.
+template <class Real>
+struct CamAcc {
+  Real a[CP_NACC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < CP_NACC; ++k) a[k] = Real(0);
+  }
+  __device__ __forceinline__ void add(const ObsEval<Real>& ev, Real u0, Real u1) { accumulate_cam<Real>(a, ev, u0, u1); }
+  __device__ __forceinline__ void reduce_store(int lane, Real* out) {
+#pragma unroll
+    for (int k = 0; k < CP_NACC; ++k) {
+      Real v = a[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      a[k] = v;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < CP_NACC; ++k) out[part_slot(k)] = a[k];
+      out[39] = out[79] = out[82] = out[83] = Real(0);
+    }
+  }
+};
+
+template <>
+struct CamAcc<float> {
+  float2 s[39];   // H (21, packed) then B (18); x: at x̄^k, y: at x^k
+  float f, g;     // sum F_ij / 2 and the surrogate gap
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 39; ++k) s[k] = make_float2(0.f, 0.f);
+    f = g = 0.f;
+  }
+  __device__ __forceinline__ void add(const ObsEval<float>& ev, float u0, float u1) {
+    const float sq = u0 * u0 + u1 * u1;
+    const float h[5] = {u0, u1, 1.f, sq, sq * sq};
+    const float2 wv = make_float2(ev.wb, ev.w);
+    float2 wh[6], hc[6];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      hc[a] = make_float2(h[a], h[a]);
+      wh[a] = __fmul2_rn(wv, hc[a]);
+    }
+    hc[5] = make_float2(ev.lamb, ev.lam);
+    wh[5] = __fmul2_rn(wv, hc[5]);
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = a; c < 6; ++c) s[tri6(a, c)] = __ffma2_rn(wh[a], hc[c], s[tri6(a, c)]);
+    const float2 half = make_float2(0.5f, 0.5f);
+    const float2 r0[3] = {__fmul2_rn(half, make_float2(ev.Reb0, ev.Re0)), __fmul2_rn(half, make_float2(ev.Reb1, ev.Re1)),
+                          __fmul2_rn(half, make_float2(ev.Reb2, ev.Re2))};
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s[21 + a * 3 + c] = __ffma2_rn(wh[a], r0[c], s[21 + a * 3 + c]);
+    f += 0.5f * ev.rho;
+    g += ev.gap;
+  }
+  __device__ __forceinline__ void reduce_store(int lane, float* out) {
+#pragma unroll
+    for (int k = 0; k < 39; ++k) {
+      float2 v = s[k];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1)
+        v = __fadd2_rn(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off)));
+      s[k] = v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      f += __shfl_xor_sync(0xffffffffu, f, off);
+      g += __shfl_xor_sync(0xffffffffu, g, off);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 39; ++k) {
+        out[PART_XB + k] = s[k].x;
+        out[PART_XK + k] = s[k].y;
+      }
+      out[PART_F] = f;
+      out[PART_G] = g;
+      out[39] = out[79] = out[82] = out[83] = 0.f;
+    }
+  }
+};
+
 // asynchronous global -> shared copies (cp.async) used to stage gathered records
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -206,9 +297,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   __syncwarp();
   const V4<Real>* pk = spk[wib];
   const Real gamma = Real(P.gam[*P.it]);
-  Real acc[80];
-#pragma unroll
-  for (int k = 0; k < 80; ++k) acc[k] = Real(0);
+  CamAcc<Real> acc;
+  acc.zero();
   // Pipeline over batches t of 32 observations (one per lane): the landmark index of batch
   // t + S is loaded while the records of batch t + S - 1 are copied asynchronously and batch
   // t is evaluated. Each lane only touches its own staging slots.
@@ -249,7 +339,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       ObsEval<Real> ev;
       eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
-      accumulate_cam<Real>(acc, ev, uu.x, uu.y);
+      acc.add(ev, uu.x, uu.y);
       const Real wlb = ev.wb * ev.lamb, wl = ev.w * ev.lam;
       V4<Real> ra, rb;
       ra.x = wlb * ev.lamb;
@@ -269,19 +359,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   cp_async_wait<0>();
   // warp reduction; the partial is stored in the pass precision and summed over the
   // camera's chunks in FP64 by the camera solve
-#pragma unroll
-  for (int k = 0; k < 80; ++k) {
-    Real v = acc[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    acc[k] = v;
-  }
-  if (lane == 0) {
-    Real* out = part + (size_t)warp * CP_STRIDE;
-#pragma unroll
-    for (int k = 0; k < CP_NACC; ++k) out[part_slot(k)] = acc[k];
-    out[39] = out[79] = out[82] = out[83] = Real(0);
-  }
+  acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE);
 }
 
 // ---------------------------------------------------------------------------
