@@ -176,6 +176,9 @@ class Clocks:
 # algorithmic bytes per launch (each datum once) of the iteration kernels
 # ----------------------------------------------------------------------------
 
+CHUNK_OBS = 2048   # default observations per camera-pass chunk (daba_options.chunk_obs = 0)
+
+
 def algorithmic_bytes(sc, prec):
     """Bytes each pass must move at least once per launch (each datum once; see the design notes).
 
@@ -183,7 +186,7 @@ def algorithmic_bytes(sc, prec):
            are read and the landmark-side record is written (rec = 8R + R in MIXED: the gap
            only in its third part; 8R + 2R in FP64); each landmark's position and displacement
            (6R) and each camera pack (48R) are read once; one partial of 84 values is written
-           per chunk of at most 1024 observations.
+           per chunk of at most CHUNK_OBS observations (the library's default chunk).
     lpass: per observation the record (rec) and its slot (2) are read; per landmark its state
            record (8R, plus 16 B of low parts in MIXED) is read and written, its restart flag
            written and its CSR offset read (4).
@@ -191,7 +194,7 @@ def algorithmic_bytes(sc, prec):
     R = 4 if prec == "mixed" else 8
     nnz, N, M = sc.nnz, sc.N, sc.M
     deg = np.bincount(sc.cam_idx, minlength=M)
-    n_chunks = int(np.sum((deg + 1023) // 1024))
+    n_chunks = int(np.sum((deg + CHUNK_OBS - 1) // CHUNK_OBS))
     rec = 8 * R + (R if prec == "mixed" else 2 * R)
     cpass = nnz * (4 + 2 * R + 4 + rec) + N * 6 * R + M * 48 * R + n_chunks * 84 * R
     lrec = 8 * R + (16 if prec == "mixed" else 0)

@@ -73,7 +73,7 @@ typedef struct {
   double pixel_scale;     /* s_norm in pixels; 0 = median focal length of the first state set */
   daba_precision prec;
   /* work schedule (0 = default; results do not depend on it except for the order of FP
-   * sums): observations per camera-pass chunk (32..65536, default 1024), observations per
+   * sums): observations per camera-pass chunk (32..65536, default 2048), observations per
    * landmark tile (32..2048, default 512) and landmarks per tile (1..128, default 128). */
   int32_t chunk_obs;
   int32_t tile_obs;

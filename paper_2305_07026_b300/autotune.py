@@ -7,7 +7,7 @@ from __future__ import annotations
 
 import numpy as np
 
-CHUNKS = (512, 1024, 2048)
+CHUNKS = (1024, 2048, 4096)
 TILE_OBS = (256, 512, 1024)
 TILE_LMS = (64, 128)
 
@@ -35,7 +35,7 @@ def tune(cams, lms, cam_idx, lm_idx, uv, opts=None, iters=8, log=None):
     """Returns (best schedule dict, {schedule: ms per iteration}) for this problem."""
     from paper_2305_07026_b300 import _lib as L
     opts = dict(opts or {})
-    best = {"chunk_obs": 1024, "tile_obs": 512, "tile_lms": 128}
+    best = {"chunk_obs": 2048, "tile_obs": 512, "tile_lms": 128}
     seen = {}
 
     def measure(s):

@@ -24,7 +24,7 @@ using namespace daba;
 
 namespace {
 
-constexpr int CHUNK_OBS = 1024;   // camera-sorted pass: default observations per warp chunk
+constexpr int CHUNK_OBS = 2048;   // camera-sorted pass: default observations per warp chunk
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
 constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
