@@ -57,10 +57,11 @@ typedef enum {
  * WELSCH c^2 (1-exp(-s/c^2)). */
 typedef enum { DABA_LOSS_TRIVIAL = 0, DABA_LOSS_HUBER = 1, DABA_LOSS_CAUCHY = 2, DABA_LOSS_WELSCH = 3 } daba_loss;
 
-/* DABA_FP64: every per-observation quantity in FP64.
+/* DABA_FP64: every quantity in FP64.
  * DABA_MIXED: per-observation residuals, weights and majorizer terms in FP32; the
- * per-camera normal-matrix accumulation across warps, the restart metrics, the
- * camera subproblem solve and the rotation projection in FP64. */
+ * per-camera sums across warps, the camera state and the camera restart metrics in FP64;
+ * the camera subproblem solve (S-CAM) and the extrapolated rotation in FP32 on displacements
+ * from the FP64 state; landmark solves and metrics in FP32 with double-float positions. */
 typedef enum { DABA_FP64 = 0, DABA_MIXED = 1 } daba_precision;
 
 typedef struct {

@@ -397,6 +397,8 @@ struct Num<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double from(double x) { return x; }
   static __device__ __forceinline__ double to_double(double x) { return x; }
+  // squared step below which the rotation iterations stop (the next iterate is exact to rounding)
+  static __device__ __forceinline__ S tiny() { return 1e-20; }
   // coefficients of the scaled Newton step X <- hz X + hiz C with C = det(X) X^{-T}
   static __device__ __forceinline__ void newton(const double* X, const double* C, double det, bool scaled,
                                                 double& hz, double& hiz) {
@@ -415,6 +417,46 @@ struct Num<double> {
     hiz = 0.5 * idet / z;
   }
 };
+
+// FP32 solves (the MIXED camera solves): constants and conversions on the FP32 pipe (narrow and
+// widen use integer operations).
+template <>
+struct Num<float> {
+  using S = float;
+  static __device__ __forceinline__ float c(float x) { return x; }
+  static __device__ __forceinline__ S hi(float x) { return x; }
+  static __device__ __forceinline__ bool pos(float x) { return x > 0.f; }
+  static __device__ __forceinline__ float rsqrt(float x) { return 1.f / sqrtf(x); }
+  static __device__ __forceinline__ float rcp(float x) { return 1.f / x; }
+  static __device__ __forceinline__ float from(double x) { return narrow(x); }
+  static __device__ __forceinline__ double to_double(float x) { return widen(x); }
+  static __device__ __forceinline__ S tiny() { return 1e-12f; }
+  static __device__ __forceinline__ void newton(const float* X, const float* C, float det, bool scaled, float& hz,
+                                                float& hiz) {
+    const float idet = 1.f / det;
+    float z = 1.f;
+    if (scaled) {
+      float nx = 0.f, nc = 0.f;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        nx += X[a] * X[a];
+        nc += C[a] * C[a];
+      }
+      z = sqrtf(sqrtf(nc / nx) * idet);
+    }
+    hz = 0.5f * z;
+    hiz = 0.5f * idet / z;
+  }
+};
+
+// the same for an FP32 matrix (the rare fallback of the FP32 iterations), through FP64
+__device__ inline void proj_rot3d(const float* __restrict__ K, float* __restrict__ R) {
+  double Kd[9], Rd[9];
+  for (int a = 0; a < 9; ++a) Kd[a] = widen(K[a]);
+  proj_rot3d(Kd, Rd);
+  for (int a = 0; a < 9; ++a) R[a] = narrow(Rd[a]);
+}
+
 
 // ProjRot3D for det K > 0: the projection onto SO(3) is then the orthogonal polar factor of
 // K, computed with Higham's scaled Newton iteration X <- (z X + X^{-T} / z) / 2 with the
@@ -454,7 +496,7 @@ __device__ inline void proj_rot3d_polar(const T* __restrict__ K, T* __restrict__
       X[a] = y;
     }
     if (dif < S(1e-6)) scaled = false;
-    if (dif < S(1e-20)) {
+    if (dif < N::tiny()) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) R[a] = X[a];
       return;
@@ -525,7 +567,7 @@ __device__ inline bool proj_rot3d_from(const T* __restrict__ K, const T* __restr
 #pragma unroll
     for (int a = 0; a < 9; ++a) Q[a] = Qn[a];
     const S ww = N::hi(w0 * w0 + w1 * w1 + w2 * w2);
-    if (ww < S(1e-20)) {
+    if (ww < N::tiny()) {
 #pragma unroll
       for (int a = 0; a < 9; ++a) R[a] = Q[a];
       return true;
@@ -578,7 +620,7 @@ __device__ inline void proj_rot3d_near(const T* __restrict__ K, T* __restrict__ 
                                       X[i * 3 + 2] * Sm[2 * 3 + j]));
 #pragma unroll
     for (int a = 0; a < 9; ++a) X[a] = Y[a];
-    if (dev < S(1e-20)) break;
+    if (dev < N::tiny()) break;
     if (it == 7) ok = false;
   }
   if (ok) {

@@ -709,10 +709,16 @@ __device__ inline T cam_phi(const T* st, const CamT<T>& z, const CamT<T>& c, T x
 //   dM0 = M(R, t_z, d_z) - M(c_z); the normal equations of the resulting least squares
 //   in y = (dt, dd) use H[5,5], H[5,2:5], H[2:5,2:5]; they are solved through the 3x3 Schur
 //   complement of their scaled-identity dt block (below).
+// y_out (optional): the (t, d) displacement from z of the last (t, d)-step taken (zero if none),
+// exact to the solve's rounding even where c.t = z.t + y rounds it away.
 template <class T>
-__device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, CamT<T>& c) {
+__device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, CamT<T>& c, T* y_out = nullptr) {
   using N = Num<T>;
   c = z;
+  if (y_out) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) y_out[k] = N::c(0.f);
+  }
   for (int it = 0; it < n_alt; ++it) {
     // ---- R-step
     T W[3][6];
@@ -816,10 +822,19 @@ __device__ inline void cam_scam(const T* st, const CamT<T>& z, T xi, int n_alt, 
         const T y2 = (c02 * r[0] + c12 * r[1] + m1 * r[2]) * id;
         const T hy = N::c(2.0f) * (h[0] * y0 + h[1] * y1 + h[2] * y2);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.t[k] = z.t[k] + (rhs[k] - v[k] * hy) * ia;
+        for (int k = 0; k < 3; ++k) {
+          const T yt = (rhs[k] - v[k] * hy) * ia;
+          c.t[k] = z.t[k] + yt;
+          if (y_out) y_out[k] = yt;
+        }
         c.d[0] = z.d[0] + y0;
         c.d[1] = z.d[1] + y1;
         c.d[2] = z.d[2] + y2;
+        if (y_out) {
+          y_out[3] = y0;
+          y_out[4] = y1;
+          y_out[5] = y2;
+        }
       }
     }
   }
@@ -959,11 +974,40 @@ __device__ inline void cam_lm(const double* st, const CamT<double>& z, double xi
 
 // the camera block solver of the variant in use
 enum { CAM_SCAM = 0, CAM_LM = 1 };
-template <int SOLVER>
+
+// S-CAM in FP32 for the MIXED path: the statistics (FP32 partials summed in FP64) and the
+// conditioning point are rounded to FP32 with the origin of t moved to z.t; the solve returns
+// the rotation and the (t, d) displacements, which are added to z in FP64, so a small step
+// keeps its relative accuracy. The restart metrics are evaluated in FP64 by the caller.
+__device__ inline void cam_scam_f32(const double* st, const CamT<double>& z, double xi, int n_alt, CamT<double>& c) {
+  float sf[39];
+#pragma unroll
+  for (int k = 0; k < 39; ++k) sf[k] = narrow(st[k]);
+  CamT<float> zf, cf;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) zf.R[a] = narrow(z.R[a]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    zf.t[k] = 0.f;
+    zf.d[k] = narrow(z.d[k]);
+  }
+  float y[6];
+  cam_scam<float>(sf, zf, narrow(xi), n_alt, cf, y);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) c.R[a] = widen(cf.R[a]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c.t[k] = z.t[k] + widen(y[k]);
+    c.d[k] = z.d[k] + widen(y[3 + k]);
+  }
+}
+template <int SOLVER, class Real>
 __device__ __forceinline__ void cam_solve(const double* st, const CamT<double>& z, double xi, int n_alt,
                                           CamT<double>& c) {
   if (SOLVER == CAM_LM)
     cam_lm(st, z, xi, c);
+  else if (sizeof(Real) == 4)
+    cam_scam_f32(st, z, xi, n_alt, c);
   else
     cam_scam(st, z, xi, n_alt, c);
 }
@@ -1046,6 +1090,23 @@ __device__ __forceinline__ void write_pack_t(const CamT<double>& x, const CamT<d
   pk[P4_DD] = e;
 }
 
+// Rbar = ProjRot3D(K) of the extrapolation K = R + gamma dR (Eq. nesterov_R): in FP64 on the
+// FP64 path; on the MIXED path K is rounded to FP32 and projected in FP32 (the pass reads Rbar
+// in FP32, and the FP32 camera solve rounds it to FP32 as its conditioning rotation).
+template <class Real>
+__device__ __forceinline__ void extrap_rotation(const double* K, double* Rb) {
+  if (sizeof(Real) == 4) {
+    float Kf[9], Rf[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Kf[a] = narrow(K[a]);
+    proj_rot3d_near<float>(Kf, Rf);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) Rb[a] = widen(Rf[a]);
+  } else {
+    proj_rot3d_near<double>(K, Rb);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // camera prepare: Rbar^k = ProjRot3D(R^k + gamma dR^k) (Eq. nesterov_R) and the pack
 // ---------------------------------------------------------------------------
@@ -1060,7 +1121,7 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
   double K[9], Rb[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) K[a] = x[CS_R + a] + gamma * dx[CS_R + a];
-  proj_rot3d_near(K, Rb);
+  extrap_rotation<Real>(K, Rb);
 #pragma unroll
   for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = Rb[a];
   CamT<double> cx, cdx;
@@ -1122,7 +1183,7 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
     if (role == 1) {   // MM solve from x^k with the x^k statistics
       sum_stats<Real, T>(part, c0, c1, PART_XK, st);
       CamT<T> cm;
-      cam_solve<SOLVER>(st, ck, xi, P.n_alt, cm);
+      cam_solve<SOLVER, Real>(st, ck, xi, P.n_alt, cm);
       const T dm = cam_phi(st, ck, cm, xi);
 #pragma unroll
       for (int a = 0; a < 9; ++a) sh_mm[lane][a] = cm.R[a];
@@ -1143,7 +1204,7 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
         cb.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
       }
       sum_stats<Real, T>(part, c0, c1, PART_XB, st);
-      cam_solve<SOLVER>(st, cb, xi, P.n_alt, cn);
+      cam_solve<SOLVER, Real>(st, cb, xi, P.n_alt, cn);
       sum_stats<Real, T>(part, c0, c1, PART_XK, st);
       dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
     }
@@ -1233,7 +1294,7 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS)
   T K[9], Rb[9];
 #pragma unroll
   for (int a = 0; a < 9; ++a) K[a] = cn.R[a] + gn * ndx.R[a];
-  proj_rot3d_near(K, Rb);
+  extrap_rotation<Real>(K, Rb);
 #pragma unroll
   for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = N::to_double(Rb[a]);
   write_pack_t<Real>(cn, ndx, Rb, pack_next + (size_t)i * P4N);
@@ -1394,7 +1455,7 @@ __global__ void k_fix_cams(int M, IterParams P, double* __restrict__ cam_x, doub
   double K[9], Rb[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) K[q] = cn.R[q] + gn * ndx.R[q];
-  proj_rot3d_near(K, Rb);
+  extrap_rotation<Real>(K, Rb);
 #pragma unroll
   for (int q = 0; q < 9; ++q) cam_Rbar[(size_t)i * 9 + q] = Rb[q];
   write_pack_t<Real>(cn, ndx, Rb, pack_next + (size_t)i * P4N);
