@@ -265,12 +265,12 @@ struct RecC<double> {
   static __device__ __forceinline__ double gap(double2 c) { return c.y; }
 };
 
-// Per lane and stage: the landmark record (two V4), the pixel and the record position.
+// Per lane and stage: the landmark record (two V4); the pixel and the record position are kept
+// in arrays of their own (consecutive lanes in consecutive words, no bank conflicts).
 template <class Real, class Real2>
 struct CpassStage {
   V4<Real> rec[2];
-  Real2 u;
-  int rpos;
+  Real pad[2];   // 48 B per lane in FP32: eight lanes' 16 B copies fall in distinct banks
 };
 
 // Landmark-side record of one observation, stored at c_rpos[o], its position in the landmark
@@ -287,6 +287,8 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
             typename RecC<Real>::type* __restrict__ rec_c) {
   __shared__ V4<Real> spk[CPASS_WARPS][P4N];
   __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
+  __shared__ Real2 su[CPASS_WARPS][CPASS_STAGES][32];
+  __shared__ int srp[CPASS_WARPS][CPASS_STAGES][32];
   const int wib = threadIdx.x >> 5;
   const int warp = blockIdx.x * CPASS_WARPS + wib;
   const int lane = threadIdx.x & 31;
@@ -314,10 +316,10 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       for (int q = 0; q < (int)(2 * sizeof(V4<Real>) / 16); ++q)
         cp_async16(reinterpret_cast<char*>(d.rec) + 16 * q, reinterpret_cast<const char*>(src) + 16 * q);
       if (sizeof(Real2) == 16)
-        cp_async16(&d.u, c_u + o);
+        cp_async16(&su[wib][t % CPASS_STAGES][lane], c_u + o);
       else
-        cp_async8(&d.u, c_u + o);
-      cp_async4(&d.rpos, c_rpos + o);
+        cp_async8(&su[wib][t % CPASS_STAGES][lane], c_u + o);
+      cp_async4(&srp[wib][t % CPASS_STAGES][lane], c_rpos + o);
     }
     cp_async_commit();
   };
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
     if (o < e) {
       const CpassStage<Real, Real2>& d = stg[t % CPASS_STAGES][lane];
       const V4<Real> r0 = d.rec[0], r1 = d.rec[1];
-      const Real2 uu = d.u;
+      const Real2 uu = su[wib][t % CPASS_STAGES][lane];
       ObsEval<Real> ev;
       eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       rb.y = Real(-0.5) * wl * ev.Re0;
       rb.z = Real(-0.5) * wl * ev.Re1;
       rb.w = Real(-0.5) * wl * ev.Re2;
-      const int rp = d.rpos;
+      const int rp = srp[wib][t % CPASS_STAGES][lane];
       rec_a[rp] = ra;
       rec_b[rp] = rb;
       rec_c[rp] = RecC<Real>::make(Real(0.5) * ev.rho, ev.gap);
