@@ -348,7 +348,8 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         ms_u = e0.elapsed_time(e1)
         unrolled = {"what": "daba_unrolled_grad: d(<seed, x^K>)/d(cameras, landmarks, pixels) of K FP64 iterations "
-                            "from x^0 (forward sweep, states kept every 10 iterations and recomputed, adjoint kernels)",
+                            "from x^0 (forward sweep keeping every 10th state, each segment run again keeping its "
+                            "iterations' statistics, adjoint kernels)",
                     "K": Ku, "ms": ms_u, "ms_per_iteration": ms_u / Ku,
                     "ratio_to_fp64_forward": ms_u / (Ku * ms64 / Kf)}
     d64.close()

@@ -168,9 +168,10 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
  *   g_uv:   nnz x 2, dy / d u_ij (input observation order).
  * The per-block restart decisions are piecewise constant and are held at those of the
  * forward run. Runs the K iterations itself (leaving the state at x^K, as daba_run(K)
- * would), keeps the state every 10 iterations and recomputes the others, so that it costs
- * about three forward runs plus the adjoint kernels and holds about K/10 + 11 copies of the
- * state. Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
+ * would), keeps the state every 10 iterations and, per segment of 10 iterations from the last,
+ * runs the segment again keeping each iteration's state, camera statistics, landmark sums and
+ * decisions; it costs about two forward runs plus the adjoint kernels and holds about K/10 + 11
+ * copies of the state and 10 of the per-iteration data (about 64 B per landmark). Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
  * (DABA_ERR_ARG for MIXED, for momentum_reset, whose Nesterov scalars live on the device, and for
  * DABA_CAM_LM, whose step acceptance has no adjoint here);
  * DABA_ERR_STATE if iterations have run since the state was set. */

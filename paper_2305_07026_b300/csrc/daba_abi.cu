@@ -95,6 +95,8 @@ struct daba_ctx {
   void *zb_c[2] = {nullptr, nullptr}, *zb_l[2] = {nullptr, nullptr};
   void *st_bar = nullptr, *ab_bar = nullptr, *g_u = nullptr;
   std::vector<void*> slots;
+  std::vector<void*> itslots;         // per iteration of a segment: statistics, landmark sums, decisions
+  void* lm_sums_out = nullptr;        // set while the segment sweep runs: the landmark pass's (a, b) sums
   // global restart variant (allocated when restart_mode is global): per-block terms of the test,
   // the MM alternatives, the decision and the device Nesterov scalar
   void *g_cam = nullptr, *g_tile = nullptr, *cam_alt = nullptr, *lm_alt = nullptr, *g_fire = nullptr,
@@ -324,7 +326,8 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
           t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
           (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
           (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
-          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd, (V4<Real>*)ctx->lm_alt);
+          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd, (V4<Real>*)ctx->lm_alt,
+          (double*)ctx->lm_sums_out);
       ctx->launches++;
     }
     t0 = ctx->tile_class_end[c];
@@ -570,6 +573,26 @@ SlotLayout slot_layout(const daba_ctx* c) {
   return L;
 }
 
+// What the adjoint of one iteration reads besides the state: the chunk partials of the camera
+// statistics, the landmarks' (a, b) sums at x̄ and x^k, and the restart decisions.
+struct ItLayout {
+  size_t part, sums, rs_cam, rs_lm, bytes;
+};
+ItLayout it_layout(const daba_ctx* c) {
+  ItLayout L;
+  size_t o = 0;
+  L.part = o;
+  o = align256(o + (size_t)c->max_chunks * CP_STRIDE * 8);
+  L.sums = o;
+  o = align256(o + (size_t)c->N * 8 * 8);
+  L.rs_cam = o;
+  o = align256(o + (size_t)c->M);
+  L.rs_lm = o;
+  o = align256(o + (size_t)c->N);
+  L.bytes = o;
+  return L;
+}
+
 daba_status ensure_adjoint(daba_ctx* ctx, size_t n_slots) {
   daba_status s;
   const size_t M = ctx->M, N = ctx->N;
@@ -592,7 +615,27 @@ daba_status ensure_adjoint(daba_ctx* ctx, size_t n_slots) {
     if ((s = dalloc(ctx, &p, b)) != DABA_OK) return s;
     ctx->slots.push_back(p);
   }
+  const size_t bi = it_layout(ctx).bytes;
+  while (ctx->itslots.size() < (size_t)ADJ_CKPT) {
+    void* p = nullptr;
+    if ((s = dalloc(ctx, &p, bi)) != DABA_OK) return s;
+    ctx->itslots.push_back(p);
+  }
   return DABA_OK;
+}
+
+// keeps the statistics and decisions of the iteration just run (its landmark sums were written
+// by the landmark pass through lm_sums_out)
+cudaError_t save_iteration(daba_ctx* ctx, void* slot, cudaStream_t st) {
+  const ItLayout L = it_layout(ctx);
+  char* b = (char*)slot;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b + L.part, ctx->chunk_part, (size_t)ctx->n_chunks * CP_STRIDE * 8, cudaMemcpyDeviceToDevice,
+                           st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b + L.rs_cam, ctx->cam_rs, (size_t)ctx->M, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  return cudaMemcpyAsync(b + L.rs_lm, ctx->lm_rs, (size_t)ctx->N, cudaMemcpyDeviceToDevice, st);
 }
 
 cudaError_t save_state(daba_ctx* ctx, void* slot, cudaStream_t st) {
@@ -657,11 +700,16 @@ cudaError_t advance(daba_ctx* ctx, cudaStream_t st, int n) {
 // pack) are in the live buffers; slot holds x^k and x^k - x^(k-1) of the cameras.
 // a1: adjoint of x^(k+1) (read); a0, am: adjoints of x^k and x^(k-1) (accumulated).
 template <int LOSS>
-cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot, int a1, int a0,
-                         int am) {
+cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot, const void* itslot,
+                         int a1, int a0, int am) {
   const SlotLayout Ly = slot_layout(ctx);
+  const ItLayout Li = it_layout(ctx);
   const double* sx = (const double*)((const char*)slot + Ly.x);
   const double* sdx = (const double*)((const char*)slot + Ly.dx);
+  const double* part = (const double*)((const char*)itslot + Li.part);
+  const double* sums = (const double*)((const char*)itslot + Li.sums);
+  const uint8_t* rs_cam = (const uint8_t*)((const char*)itslot + Li.rs_cam);
+  const uint8_t* rs_lm = (const uint8_t*)((const char*)itslot + Li.rs_lm);
   const int M = ctx->M, N = ctx->N;
   const int acc = ctx->opt.accelerated;
   const double xi = ctx->opt.xi;
@@ -671,22 +719,20 @@ cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma
     if ((e = cudaMemsetAsync(ctx->zb_l[q], 0, (size_t)N * AL_N * 8, st)) != cudaSuccess) return e;
   }
   if (M > 0)
-    k_adj_cams<<<(M + 63) / 64, 64, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, (const double*)ctx->chunk_part, sx, sdx,
-                                             gamma, (const uint8_t*)ctx->cam_rs, acc, xi, ctx->opt.cam_alternations,
+    k_adj_cams<<<(M + 63) / 64, 64, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, part, sx, sdx,
+                                             gamma, rs_cam, acc, xi, ctx->opt.cam_alternations,
                                              (const double*)ctx->adj_c[a1], (double*)ctx->st_bar,
                                              (double*)ctx->zb_c[0], (double*)ctx->zb_c[1]);
-  if (ctx->n_tiles > 0)
-    k_adj_lms<<<ctx->n_tiles, LPASS_THREADS, 0, st>>>(
-        (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<double>*)ctx->rec_a,
-        (const V4<double>*)ctx->rec_b, (const uint8_t*)ctx->lm_rs, acc, xi, (const double*)ctx->adj_l[a1],
-        (double*)ctx->ab_bar, (double*)ctx->zb_l[0], (double*)ctx->zb_l[1]);
-  // the records are consumed: rec_a / rec_b now take the landmark terms at xbar / x^k
+  if (N > 0)
+    k_adj_lms<<<(N + 255) / 256, 256, 0, st>>>(N, sums, rs_lm, acc, xi, (const double*)ctx->adj_l[a1],
+                                               (double*)ctx->ab_bar, (double*)ctx->zb_l[0], (double*)ctx->zb_l[1]);
+  // rec_a / rec_b (free here) take the landmark terms at xbar / x^k
   if (ctx->n_chunks > 0)
     k_adj_obs<LOSS><<<ctx->n_chunks, 32, 0, st>>>(
         ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
         (const double2*)ctx->c_u, (const int*)ctx->c_rpos, (const int*)ctx->d_ci_order,
-        (const V4<double>*)pack_at(ctx, k), (const V4<double>*)lmrec_at(ctx, k), gamma, (const uint8_t*)ctx->cam_rs,
-        (const uint8_t*)ctx->lm_rs, acc, loss_consts<double>(ctx), 1.0 / ctx->s_norm, (const double*)ctx->st_bar,
+        (const V4<double>*)pack_at(ctx, k), (const V4<double>*)lmrec_at(ctx, k), gamma, rs_cam,
+        rs_lm, acc, loss_consts<double>(ctx), 1.0 / ctx->s_norm, (const double*)ctx->st_bar,
         (const double*)ctx->ab_bar, (double*)ctx->chunk_part, (V4<double>*)ctx->rec_a, (V4<double>*)ctx->rec_b,
         (double2*)ctx->g_u);
   if (M > 0)
@@ -703,13 +749,13 @@ cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma
   return cudaGetLastError();
 }
 
-cudaError_t adjoint_iter_by_loss(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot, int a1,
-                                 int a0, int am) {
+cudaError_t adjoint_iter_by_loss(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma, const void* slot,
+                                 const void* itslot, int a1, int a0, int am) {
   switch (ctx->opt.loss) {
-    case DABA_LOSS_TRIVIAL: return adjoint_iter<LOSS_TRIVIAL>(ctx, st, k, gamma, slot, a1, a0, am);
-    case DABA_LOSS_HUBER: return adjoint_iter<LOSS_HUBER>(ctx, st, k, gamma, slot, a1, a0, am);
-    case DABA_LOSS_CAUCHY: return adjoint_iter<LOSS_CAUCHY>(ctx, st, k, gamma, slot, a1, a0, am);
-    default: return adjoint_iter<LOSS_WELSCH>(ctx, st, k, gamma, slot, a1, a0, am);
+    case DABA_LOSS_TRIVIAL: return adjoint_iter<LOSS_TRIVIAL>(ctx, st, k, gamma, slot, itslot, a1, a0, am);
+    case DABA_LOSS_HUBER: return adjoint_iter<LOSS_HUBER>(ctx, st, k, gamma, slot, itslot, a1, a0, am);
+    case DABA_LOSS_CAUCHY: return adjoint_iter<LOSS_CAUCHY>(ctx, st, k, gamma, slot, itslot, a1, a0, am);
+    default: return adjoint_iter<LOSS_WELSCH>(ctx, st, k, gamma, slot, itslot, a1, a0, am);
   }
 }
 
@@ -1402,22 +1448,29 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   CK(cudaGetLastError());
   // backward over the segments: recompute the segment's states, then per iteration replay it
   // (statistics, records, decisions) and run its adjoint
+  const ItLayout Li = it_layout(ctx);
   for (int sg = n_seg - 1; sg >= 0; --sg) {
     const int kb = sg * C, ke = std::min(K, kb + C);
+    // the segment's forward sweep keeps each state and what its adjoint reads
     CK(restore_state(ctx, ctx->slots[sg], kb, s_hist[kb], st));
     for (int k = kb; k < ke; ++k) {
       CK(save_state(ctx, ctx->slots[(size_t)n_seg + (k - kb)], st));
-      CK(advance(ctx, st, 1));
+      ctx->lm_sums_out = (char*)ctx->itslots[k - kb] + Li.sums;
+      const cudaError_t e = advance(ctx, st, 1);
+      ctx->lm_sums_out = nullptr;
+      CK(e);
+      CK(save_iteration(ctx, ctx->itslots[k - kb], st));
     }
     for (int k = ke - 1; k >= kb; --k) {
       const void* slot = ctx->slots[(size_t)n_seg + (k - kb)];
-      if (k != ke - 1) {   // the live buffers hold iteration ke - 1 after the segment sweep
-        CK(restore_state(ctx, slot, k, s_hist[k], st));
-        CK(advance(ctx, st, 1));
-      }
       const double sk = s_hist[k];
       const double gamma = (sk - 1.0) / ((std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0);
-      CK(adjoint_iter_by_loss(ctx, st, k, gamma, slot, i1, i0, im));
+      // x^k in the live buffers (the landmark records of k's parity) and its pass pack
+      CK(restore_state(ctx, slot, k, s_hist[k], st));
+      CK(cudaMemcpyAsync(ctx->d_gam, &gamma, 8, cudaMemcpyHostToDevice, st));
+      CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
+      CK(launch_prepare(ctx, st, k));
+      CK(adjoint_iter_by_loss(ctx, st, k, gamma, slot, ctx->itslots[k - kb], i1, i0, im));
       if (k > 0) {
         const int t = i1;
         i1 = i0;

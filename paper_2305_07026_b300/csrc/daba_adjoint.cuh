@@ -433,28 +433,17 @@ __global__ void k_adj_cams(int M, const int* __restrict__ cam_chunk_ptr, const d
   }
 }
 
-// 2. the landmark solve reversed, per landmark of a tile: l = l_z - b / (a + xi/2) with (a, b)
-//    the sums of its records at the chosen point; writes (abar, bbar) and adds the adjoint of l_z.
-__global__ void __launch_bounds__(LPASS_THREADS)
-    k_adj_lms(const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const uint16_t* __restrict__ t_inv,
-              const V4<double>* __restrict__ rec_a, const V4<double>* __restrict__ rec_b,
-              const uint8_t* __restrict__ rs_lm, int accelerated, double xi, const double* __restrict__ a_next,
-              double* __restrict__ ab_bar, double* __restrict__ zb_bar, double* __restrict__ zb_k) {
-  const int lb = tile_lm[blockIdx.x], le = tile_lm[blockIdx.x + 1];
-  const int jl = threadIdx.x;
-  if (jl >= le - lb) return;
-  const int j = lb + jl;
+// 2. the landmark solve reversed, per landmark: l = l_z - b / (a + xi/2) with (a, b) the sums of
+//    its records at the chosen point (kept by the landmark pass of the forward sweep: x̄ in
+//    sums[0..3], x^k in sums[4..7]); writes (abar, bbar) and adds the adjoint of l_z.
+__global__ void k_adj_lms(int N, const double* __restrict__ sums, const uint8_t* __restrict__ rs_lm, int accelerated,
+                          double xi, const double* __restrict__ a_next, double* __restrict__ ab_bar,
+                          double* __restrict__ zb_bar, double* __restrict__ zb_k) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
   const bool mm = !accelerated || rs_lm[j];
-  const V4<double>* rec = mm ? rec_b : rec_a;
-  const int ob = lm_ptr[lb];
-  double a = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
-  for (int sl = lm_ptr[j]; sl < lm_ptr[j + 1]; ++sl) {
-    const V4<double> r = rec[ob + t_inv[sl]];
-    a += r.x;
-    b0 += r.y;
-    b1 += r.z;
-    b2 += r.w;
-  }
+  const double* sm = sums + (size_t)j * 8 + (mm ? 4 : 0);
+  const double a = sm[0], b0 = sm[1], b1 = sm[2], b2 = sm[3];
   const double den = a + 0.5 * xi;
   const double* an = a_next + (size_t)j * AL_N;
   const double g0 = an[0], g1 = an[1], g2 = an[2];

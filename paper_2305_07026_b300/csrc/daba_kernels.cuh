@@ -456,7 +456,8 @@ __global__ void __launch_bounds__(LPASS_THREADS)
             const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
             const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out,
             V4<float>* __restrict__ lm_lo_out, IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs,
-            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag, V4<Real>* __restrict__ lm_alt) {
+            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag, V4<Real>* __restrict__ lm_alt,
+            double* __restrict__ lm_sums) {
   using RC = typename RecC<Real>::type;
   using SM = LpassSmem<Real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -608,6 +609,10 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       lm_Fdiag[g] = F;
       lm_Fbdiag[g] = F + double(thr);
       nB.w = Real(F + double(dEn));
+      if (lm_sums) {   // the reverse mode keeps (a, b) at x̄ and at x^k of every landmark
+#pragma unroll
+        for (int k = 0; k < 8; ++k) lm_sums[g * 8 + k] = double(st[k]);
+      }
     }
     lmrec_out[2 * g] = nA;
     lmrec_out[2 * g + 1] = nB;
