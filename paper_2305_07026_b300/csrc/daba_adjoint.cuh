@@ -4,12 +4,13 @@
 // nesterov_R), per block a conditioning point z (x̄^k for the accelerated update, x^k after a
 // restart), the centred statistics of every observation at z, and the block solves
 // (landmarks in closed form, cameras by S-CAM). The restart decisions are piecewise constant
-// in the inputs and carry no derivative; the adjoint replays them from the forward run.
+// in the inputs and carry no derivative; the adjoint takes them, with the camera statistics
+// and the landmark (a, b) sums, from a forward run of the same iterations.
 //
 // Adjoints of the camera state are ambient: 3x3 for R (only the component tangent to SO(3)
 // matters downstream, since every R enters through a polar factor or the boundary), 3 for t,
 // 3 for d; of a landmark 3. The adjoint of one iteration has five kernels:
-//   k_adj_cams  (thread per camera)   : S-CAM replayed with its intermediates, then reversed:
+//   k_adj_cams  (thread per camera)   : S-CAM run again with its intermediates, then reversed:
 //                                       adjoint of the 39 statistics and of the conditioning
 //                                       point from the adjoint of x^(k+1);
 //   k_adj_lms   (thread per landmark) : the same for l = l_z - b / (a + xi/2): adjoint of (a, b)
