@@ -208,3 +208,23 @@ def test_lm_camera_solver_not_differentiated():
     d.close()
     with pytest.raises(L.DabaError):
         L.Daba(4, 4, 8, cam_solver=5)
+
+
+@pytest.mark.parametrize("kw", [dict(restart="global", cam_solver="lm"),
+                                dict(restart="global", momentum_reset=True, cam_solver="lm", eta=1.0),
+                                dict(restart="global", accelerated=False)])
+def test_variant_combinations_match_oracle(kw):
+    """The variants combined (global restart with the LM camera solver, with the momentum reset at
+    eta = 1, and DUBA, where the restart mode has no effect): F(x^k) within 1e-10 for 15 iterations
+    and the restart counts exactly."""
+    sc = cached_scene("circle")
+    ok = dict(kw)
+    o = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, **ok)
+    res = O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, 15, keep_infos=15)
+    d = _ctx(sc, "fp64", **kw)
+    tr = np.zeros(16)
+    rs = np.zeros(15, np.int32)
+    d.run(15, tr, rs)
+    d.close()
+    np.testing.assert_allclose(tr, res.trace_px2, rtol=1e-10)
+    assert rs.tolist() == res.restarts.tolist()
