@@ -214,8 +214,9 @@ __device__ __forceinline__ Real eval_F(const Real* __restrict__ pk, Real q0, Rea
 // symmetric 4x4 N below (expanding the quadratic form entry by entry), so the
 // maximiser is R of the eigenvector of N's largest eigenvalue (Horn's method).
 // The eigenvector is found with cyclic Jacobi rotations.
-__device__ inline void proj_rot3d(const double* __restrict__ K, double* __restrict__ R) {
-  double a[4][4];
+template <class T>
+__device__ inline void proj_rot3d(const T* __restrict__ K, T* __restrict__ R) {
+  T a[4][4];
   a[0][0] = K[0] + K[4] + K[8];
   a[1][1] = K[0] - K[4] - K[8];
   a[2][2] = -K[0] + K[4] - K[8];
@@ -226,49 +227,49 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
   a[1][2] = a[2][1] = K[1] + K[3];
   a[1][3] = a[3][1] = K[2] + K[6];
   a[2][3] = a[3][2] = K[5] + K[7];
-  double v[4][4];
+  T v[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
-  double scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]) + fabs(a[3][3]);
+    for (int j = 0; j < 4; ++j) v[i][j] = (i == j) ? T(1) : T(0);
+  T scale = fabs(a[0][0]) + fabs(a[1][1]) + fabs(a[2][2]) + fabs(a[3][3]);
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = i + 1; j < 4; ++j) scale += 2.0 * fabs(a[i][j]);
+    for (int j = i + 1; j < 4; ++j) scale += T(2) * fabs(a[i][j]);
   for (int sweep = 0; sweep < 20; ++sweep) {
-    double off = 0.0;
+    T off = T(0);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = i + 1; j < 4; ++j) off += a[i][j] * a[i][j];
-    if (!(off > 1e-34 * scale * scale)) break;
+    if (!(off > (sizeof(T) == 4 ? T(1e-13) : T(1e-34)) * scale * scale)) break;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
 #pragma unroll
       for (int q = p + 1; q < 4; ++q) {
-        const double apq = a[p][q];
-        if (apq != 0.0) {
+        const T apq = a[p][q];
+        if (apq != T(0)) {
           // rotation in the (p, q) plane that zeroes a[p][q]: t = tan(phi) is the
           // smaller root of t^2 + 2 theta t - 1 = 0, theta = (a_qq - a_pp) / (2 a_pq)
-          const double theta = (a[q][q] - a[p][p]) / (2.0 * apq);
-          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-          const double c = 1.0 / sqrt(t * t + 1.0);
-          const double s = t * c;
+          const T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
+          const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+          const T c = T(1) / sqrt(t * t + T(1));
+          const T s = t * c;
           a[p][p] -= t * apq;
           a[q][q] += t * apq;
-          a[p][q] = a[q][p] = 0.0;
+          a[p][q] = a[q][p] = T(0);
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             if (r != p && r != q) {
-              const double arp = a[r][p], arq = a[r][q];
+              const T arp = a[r][p], arq = a[r][q];
               a[r][p] = a[p][r] = c * arp - s * arq;
               a[r][q] = a[q][r] = s * arp + c * arq;
             }
           }
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            const double vrp = v[r][p], vrq = v[r][q];
+            const T vrp = v[r][p], vrq = v[r][q];
             v[r][p] = c * vrp - s * vrq;
             v[r][q] = s * vrp + c * vrq;
           }
@@ -276,7 +277,7 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
       }
     }
   }
-  double best = a[0][0], w = v[0][0], x = v[1][0], y = v[2][0], z = v[3][0];
+  T best = a[0][0], w = v[0][0], x = v[1][0], y = v[2][0], z = v[3][0];
 #pragma unroll
   for (int k = 1; k < 4; ++k) {
     if (a[k][k] > best) {
@@ -287,19 +288,19 @@ __device__ inline void proj_rot3d(const double* __restrict__ K, double* __restri
       z = v[3][k];
     }
   }
-  const double n = 1.0 / sqrt(w * w + x * x + y * y + z * z);
+  const T n = T(1) / sqrt(w * w + x * x + y * y + z * z);
   w *= n;
   x *= n;
   y *= n;
   z *= n;
   R[0] = w * w + x * x - y * y - z * z;
-  R[1] = 2.0 * (x * y - w * z);
-  R[2] = 2.0 * (x * z + w * y);
-  R[3] = 2.0 * (x * y + w * z);
+  R[1] = T(2) * (x * y - w * z);
+  R[2] = T(2) * (x * z + w * y);
+  R[3] = T(2) * (x * y + w * z);
   R[4] = w * w - x * x + y * y - z * z;
-  R[5] = 2.0 * (y * z - w * x);
-  R[6] = 2.0 * (x * z - w * y);
-  R[7] = 2.0 * (y * z + w * x);
+  R[5] = T(2) * (y * z - w * x);
+  R[6] = T(2) * (x * z - w * y);
+  R[7] = T(2) * (y * z + w * x);
   R[8] = w * w - x * x - y * y + z * z;
 }
 
@@ -449,13 +450,6 @@ struct Num<float> {
   }
 };
 
-// the same for an FP32 matrix (the rare fallback of the FP32 iterations), through FP64
-__device__ inline void proj_rot3d(const float* __restrict__ K, float* __restrict__ R) {
-  double Kd[9], Rd[9];
-  for (int a = 0; a < 9; ++a) Kd[a] = widen(K[a]);
-  proj_rot3d(Kd, Rd);
-  for (int a = 0; a < 9; ++a) R[a] = narrow(Rd[a]);
-}
 
 
 // ProjRot3D for det K > 0: the projection onto SO(3) is then the orthogonal polar factor of
