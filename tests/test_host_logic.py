@@ -1,0 +1,63 @@
+"""Host-side logic that needs no GPU: option validation in daba_create (before any device
+call), the batch merge/split of independent scenes, and the autotuner's coordinate descent."""
+import numpy as np
+import pytest
+
+
+@pytest.mark.parametrize("bad", [dict(restart=7), dict(restart="block", momentum_reset=True), dict(cam_solver=5),
+                                 dict(chunk_obs=16), dict(tile_obs=4096), dict(tile_lms=200), dict(eta=0.0),
+                                 dict(eta=1.5), dict(xi=0.0), dict(cam_alternations=0), dict(prec=3),
+                                 dict(loss=9), dict(loss="huber", loss_scale_px=0.0)])
+def test_invalid_options_rejected_before_device_work(bad):
+    from paper_2305_07026_b300 import build
+    build.build()
+    from paper_2305_07026_b300 import _lib as L
+    with pytest.raises(L.DabaError) as e:
+        L.Daba(4, 4, 8, **bad)
+    assert e.value.status == L.DABA_ERR_ARG
+
+
+def test_variant_option_values():
+    from paper_2305_07026_b300 import _lib as L
+    o = L.options(restart="global", momentum_reset=True, cam_solver="lm")
+    assert (o.restart_mode, o.momentum_reset, o.cam_solver) == (1, 1, 1)
+    o = L.options()
+    assert (o.restart_mode, o.momentum_reset, o.cam_solver) == (0, 0, 0)
+
+
+def test_batch_merge_split_round_trip():
+    from paper_2305_07026_b300 import batch, scenes
+    scs = scenes.batch_scenes(7)
+    b = batch.merge(scs)
+    assert b.M == sum(s.cams.shape[0] for s in scs) and b.N == sum(s.lms.shape[0] for s in scs)
+    assert b.nnz == sum(s.cam_idx.size for s in scs)
+    for i, s in enumerate(scs):
+        o0, o1 = b.obs_begin[i], b.obs_begin[i + 1]
+        np.testing.assert_array_equal(b.cam_idx[o0:o1] - b.cam_begin[i], s.cam_idx)
+        np.testing.assert_array_equal(b.lm_idx[o0:o1] - b.lm_begin[i], s.lm_idx)
+        np.testing.assert_array_equal(b.uv[o0:o1], s.uv)
+        # every observation of scene i refers to scene i's cameras and landmarks only
+        assert b.cam_idx[o0:o1].min() >= b.cam_begin[i] and b.cam_idx[o0:o1].max() < b.cam_begin[i + 1]
+        assert b.lm_idx[o0:o1].min() >= b.lm_begin[i] and b.lm_idx[o0:o1].max() < b.lm_begin[i + 1]
+    parts = batch.split(b, b.cams, b.lms)
+    for (c, l), s in zip(parts, scs):
+        np.testing.assert_array_equal(c, s.cams)
+        np.testing.assert_array_equal(l, s.lms)
+
+
+def test_autotune_coordinate_descent(monkeypatch):
+    """The tuner walks chunk, then observations per tile, then landmarks per tile, keeping the
+    best of each and timing every schedule once."""
+    from paper_2305_07026_b300 import autotune
+    cost = {}
+
+    def fake(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2):
+        key = (sched["chunk_obs"], sched["tile_obs"], sched["tile_lms"])
+        cost[key] = cost.get(key, 0) + 1
+        return abs(key[0] - 4096) / 1e3 + abs(key[1] - 256) / 1e2 + abs(key[2] - 64) / 10.0
+    monkeypatch.setattr(autotune, "time_schedule", fake)
+    z = np.zeros((1, 9))
+    best, tried = autotune.tune(z, np.zeros((1, 3)), np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros((1, 2)))
+    assert best == {"chunk_obs": 4096, "tile_obs": 256, "tile_lms": 64}
+    assert all(v == 1 for v in cost.values())
+    assert len(tried) == len(cost)
