@@ -43,6 +43,12 @@ linear, the sums are the same metrics for one block made of everything, so the
 convergence argument of App. C.3 applies unchanged. With
 Options.momentum_reset the Nesterov scalar restarts too: after an iteration
 whose global test fired, s^(k+1) = 1, so gamma^(k+1) = 0.
+
+Method variant (Options.cam_solver = "lm"): each camera subproblem takes one
+successful Levenberg-Marquardt step (Sec. 7.1 reports one successful inner LM
+step). Its parameterisation, Gauss-Newton model and damping schedule are
+readings (the paper gives none); the model is pinned against the surrogate's
+derivatives, but parity with the paper's own LM implementation is unpinned.
 """
 from __future__ import annotations
 
