@@ -134,6 +134,8 @@ def test_fp64_matches_oracle_per_iteration(workload, loss, scale, accel, min_ite
         d.run(1, tr, rs)
         assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
         m = d.get_block_metrics()
+        # Lemma 1a on the GPU's own metrics: the block metrics sum to the objective
+        assert m["F_cam"].sum() + m["F_lm"].sum() == pytest.approx(tr[0], rel=1e-10)
         np.testing.assert_allclose(m["F_cam"], info.F_cam * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
         np.testing.assert_allclose(m["F_lm"], info.F_lm * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
         np.testing.assert_allclose(m["Fbar_cam"], info.Fbar_cam * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
