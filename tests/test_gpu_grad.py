@@ -230,3 +230,36 @@ def test_unrolled_autograd_matches_central_differences():
             an = float((gc * v[0]).sum() + (gl * v[1]).sum() + (gu * v[2]).sum())
             assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (part, rep)
     d.close()
+
+
+def test_unrolled_grad_differentiation_workload_k50():
+    """The differentiation workload (street generator scaled to 200 cameras, ~150k observations)
+    with K = 50 (five checkpoint segments): the product is finite and linear in the seed, and the
+    state left after it is bit-identical to daba_run(50). (Element-wise comparison with the
+    oracle's autograd is done on the smaller scenes above: at this size the oracle's graph needs
+    tens of GB and some restart decisions sit within 1e-11 of a tie.)"""
+    from paper_2305_07026_b300 import _lib as L
+    sc = cached_scene("street", scale=0.2)
+    opts = dict(loss="huber", loss_scale_px=1.0, prec="fp64")
+    rng = np.random.default_rng(8)
+    s1 = (rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape))
+    s2 = (rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape))
+
+    def vjp(seed):
+        with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
+            d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+            d.set_state(sc.cams, sc.lms)
+            g = d.unrolled_grad(50, *seed)
+            return g, d.get_state()
+    (a, st_a), (b, _) = vjp(s1), vjp(s2)
+    (c, _) = vjp((s1[0] + 3.0 * s2[0], s1[1] + 3.0 * s2[1]))
+    for x, y, z in zip(a, b, c):
+        assert np.all(np.isfinite(x))
+        np.testing.assert_allclose(z, x + 3.0 * y, rtol=1e-9, atol=1e-9 * np.abs(z).max())
+    with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        d.run(50)
+        cams, lms = d.get_state()
+    np.testing.assert_array_equal(st_a[0], cams)
+    np.testing.assert_array_equal(st_a[1], lms)
