@@ -59,11 +59,12 @@ def test_objective_grad_matches_oracle(workload, scale, prec):
 
 
 def test_autograd_matches_central_differences():
-    """Differentiation workload: 200 cameras of the street generator, FP64 path; autograd
-    gradient against FP64 central differences (h = 1e-6 relative) on 64 random directions."""
+    """Differentiation workload: 200 cameras of the street generator, Huber 1 px, FP64 path;
+    autograd gradient against FP64 central differences (h = 1e-6 relative) on 64 random
+    directions."""
     from paper_2305_07026_b300.autograd import objective
     sc = cached_scene("street", scale=0.2)
-    d = _ctx(sc, "fp64")
+    d = _ctx(sc, "fp64", loss="huber", loss_scale_px=1.0)
     dev = "cuda"
     cams = torch.tensor(sc.cams, device=dev, requires_grad=True)
     lms = torch.tensor(sc.lms, device=dev, requires_grad=True)
