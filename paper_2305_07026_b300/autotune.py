@@ -19,7 +19,7 @@ def time_schedule(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmu
     try:
         d.set_observations(cam_idx, lm_idx, uv)
         d.set_state(cams, lms)
-        d.run(warmup)
+        d.run(max(warmup, iters))   # a warm-up of the timed length captures its graph
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()

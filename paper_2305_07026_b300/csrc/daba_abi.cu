@@ -28,6 +28,7 @@ constexpr int CHUNK_OBS = 2048;   // camera-sorted pass: default observations pe
 constexpr int GSEG = 1024;        // iterations per run segment (device gamma / trace buffers)
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
 constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
+constexpr int RUN_GRAPH_MAX = 256;   // a run of at most this many iterations is one graph launch
 constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
@@ -84,6 +85,11 @@ struct daba_ctx {
   cudaEvent_t ev_cap0 = nullptr, ev_cap1 = nullptr;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [GRAPH_ITERS or 1][k & 1]
   int64_t graph_nl[2] = {0, 0};                                                // kernel launches per graph
+  // a whole run (the first-iteration prepare and n iterations) as one graph, per start parity;
+  // recaptured when a run of another length comes
+  cudaGraphExec_t run_graph[2] = {nullptr, nullptr};
+  int run_graph_n[2] = {0, 0};
+  int64_t run_graph_nl[2] = {0, 0};
   // a batch of independent scenes: camera ranges, chunk ranges per scene (device), outputs
   int n_scenes = 1;
   std::vector<int32_t> h_scene_cam;
@@ -452,6 +458,11 @@ void drop_graphs(daba_ctx* ctx) {
       if (g) cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (int p = 0; p < 2; ++p) {
+    if (ctx->run_graph[p]) cudaGraphExecDestroy(ctx->run_graph[p]);
+    ctx->run_graph[p] = nullptr;
+    ctx->run_graph_n[p] = 0;
+  }
 }
 
 // Enqueues n iterations of Algorithm 1 starting at an iteration of parity k0 & 1 on stream st
@@ -519,6 +530,39 @@ daba_status ensure_graphs(daba_ctx* ctx) {
       }
     }
   ctx->timing = timing;
+  return DABA_OK;
+}
+
+// The graph of a whole run of n iterations from an iteration of the current parity: the
+// prepare kernel, then the n iterations (captured once per parity and length).
+daba_status ensure_run_graph(daba_ctx* ctx, int n) {
+  const int par = (int)(ctx->k & 1);
+  if (ctx->run_graph[par] && ctx->run_graph_n[par] == n) return DABA_OK;
+  if (ctx->run_graph[par]) cudaGraphExecDestroy(ctx->run_graph[par]);
+  ctx->run_graph[par] = nullptr;
+  ctx->run_graph_n[par] = 0;
+  const bool timing = ctx->timing;
+  ctx->timing = false;
+  const int64_t l0 = ctx->launches;
+  cudaError_t e = cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = launch_prepare(ctx, ctx->s_cap, ctx->k);
+    if (e1 == cudaSuccess) e1 = enqueue_iters(ctx, ctx->s_cap, ctx->k, n, 0);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->run_graph[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+  }
+  ctx->run_graph_nl[par] = ctx->launches - l0;
+  ctx->launches = l0;
+  ctx->timing = timing;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->run_graph[par] = nullptr;
+    return fail(ctx, DABA_ERR_CUDA, "capturing the run graph: %s", cudaGetErrorString(e));
+  }
+  ctx->run_graph_n[par] = n;
   return DABA_OK;
 }
 
@@ -1205,12 +1249,22 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(ctx->s_dev, &s_start, 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
-    if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
-    CK(launch_prepare(ctx, st, ctx->k));
-    if (ctx->timing) CK(cudaEventRecord(ev(ctx, evi++), st));
     if (ctx->timing) {   // direct launches with per-kernel events
+      CK(cudaEventRecord(ev(ctx, evi++), st));
+      CK(launch_prepare(ctx, st, ctx->k));
+      CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(enqueue_iters(ctx, st, ctx->k, seg, evi));
-    } else {   // captured graphs on s_cap, joined to st
+    } else if (seg <= RUN_GRAPH_MAX) {   // the whole run as one graph launch on s_cap, joined to st
+      if ((s = ensure_run_graph(ctx, seg)) != DABA_OK) return s;
+      const int par = (int)(ctx->k & 1);
+      CK(cudaEventRecord(ctx->ev_cap0, st));
+      CK(cudaStreamWaitEvent(ctx->s_cap, ctx->ev_cap0, 0));
+      CK(cudaGraphLaunch(ctx->run_graph[par], ctx->s_cap));
+      ctx->launches += ctx->run_graph_nl[par];
+      CK(cudaEventRecord(ctx->ev_cap1, ctx->s_cap));
+      CK(cudaStreamWaitEvent(st, ctx->ev_cap1, 0));
+    } else {   // longer runs: the prepare kernel, then 8-iteration graphs on s_cap, joined to st
+      CK(launch_prepare(ctx, st, ctx->k));
       if ((s = ensure_graphs(ctx)) != DABA_OK) return s;
       CK(cudaEventRecord(ctx->ev_cap0, st));
       CK(cudaStreamWaitEvent(ctx->s_cap, ctx->ev_cap0, 0));
