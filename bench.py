@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-scenes", type=int, default=512, help="scenes of the batch workload")
+    ap.add_argument("--no-autotune", action="store_true", help="batch workload: the default schedule, not tuned")
     return ap.parse_args()
 
 
@@ -508,7 +509,10 @@ def run_batch(args, rank, world, local):
     opts = dict(loss="huber", loss_scale_px=1.0, prec="mixed", pixel_scale=650.0)
     # schedule autotuning (untimed setup): chunk and tile sizes by coordinate descent
     from paper_2305_07026_b300 import autotune
-    sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv, opts)
+    if args.no_autotune:
+        sched, tried = {}, {}
+    else:
+        sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv, opts)
 
     d = L.Daba(b.M, b.N, b.nnz, **opts, **sched)
     d.set_observations(b.cam_idx, b.lm_idx, b.uv, stream=sp)

@@ -1150,8 +1150,11 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
 // Camera block solves in FP64: the statistics summed over the camera's chunks, the
 // accelerated S-CAM solve, the restart metrics and test, the MM solve, and the extrapolated
 // rotation and pack of iteration k+1.
+// The FP32 S-CAM path is held to 5 CTAs per SM (at most 168 registers, a few hundred bytes of
+// spills): batches of many small scenes fill more than one wave of CTAs, and 10 instead of 8
+// resident warps per SM shorten the second. The FP64 and LM paths would spill heavily and keep 255.
 template <class Real, int SOLVER>
-__global__ void __launch_bounds__(CAMSOLVE_THREADS)
+__global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER == CAM_SCAM) ? 5 : 1)
     k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
                double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
                double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
