@@ -198,29 +198,50 @@ struct CamAcc<float> {
     f += 0.5f * ev.rho;
     g += ev.gap;
   }
+  // Warp reduction of the 40 pairs (the 39 statistics and (f, g)) as a reduce-scatter:
+  // over the lane offsets 16, 8 and 4 each lane keeps half of its pairs and adds its partner's
+  // copy of them, then offsets 2 and 1 add the last five pairs across the group of four lanes.
+  // Each addition pairs the same lanes, in the same order, as a plain butterfly reduction of
+  // every pair, so the sums are the same bits; it takes about 300 instead of 700
+  // warp-instructions and 10 stores from 8 lanes instead of 84 from lane 0.
   __device__ __forceinline__ void reduce_store(int lane, float* out) {
+    float2 u[40];
 #pragma unroll
-    for (int k = 0; k < 39; ++k) {
-      float2 v = s[k];
+    for (int k = 0; k < 39; ++k) u[k] = s[k];
+    u[39] = make_float2(f, g);
+    int base = 0;   // first pair index held by this lane after the scatter levels
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1)
-        v = __fadd2_rn(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, off), __shfl_xor_sync(0xffffffffu, v.y, off)));
-      s[k] = v;
-    }
+    for (int half = 20, off = 16; half >= 5; half >>= 1, off >>= 1) {
+      const bool up = (lane & off) != 0;
+      if (up) base += half;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      f += __shfl_xor_sync(0xffffffffu, f, off);
-      g += __shfl_xor_sync(0xffffffffu, g, off);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 39; ++k) {
-        out[PART_XB + k] = s[k].x;
-        out[PART_XK + k] = s[k].y;
+      for (int i = 0; i < half; ++i) {
+        const float2 keep = up ? u[i + half] : u[i];
+        float2 send = up ? u[i] : u[i + half];
+        send.x = __shfl_xor_sync(0xffffffffu, send.x, off);
+        send.y = __shfl_xor_sync(0xffffffffu, send.y, off);
+        u[i] = __fadd2_rn(keep, send);
       }
-      out[PART_F] = f;
-      out[PART_G] = g;
-      out[39] = out[79] = out[82] = out[83] = 0.f;
+    }
+#pragma unroll
+    for (int off = 2; off > 0; off >>= 1)
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        u[i] = __fadd2_rn(u[i], make_float2(__shfl_xor_sync(0xffffffffu, u[i].x, off),
+                                            __shfl_xor_sync(0xffffffffu, u[i].y, off)));
+    if ((lane & 3) == 0) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        const int k = base + i;
+        if (k < 39) {
+          out[PART_XB + k] = u[i].x;
+          out[PART_XK + k] = u[i].y;
+        } else {
+          out[PART_F] = u[i].x;
+          out[PART_G] = u[i].y;
+          out[39] = out[79] = out[82] = out[83] = 0.f;
+        }
+      }
     }
   }
 };
