@@ -86,10 +86,12 @@ struct daba_ctx {
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [GRAPH_ITERS or 1][k & 1]
   int64_t graph_nl[2] = {0, 0};                                                // kernel launches per graph
   // a whole run (the first-iteration prepare and n iterations) as one graph, per start parity;
-  // recaptured when a run of another length comes
+  // recaptured when a run of another length comes, or with timing switched on or off (the
+  // timing graph also holds the per-kernel event records)
   cudaGraphExec_t run_graph[2] = {nullptr, nullptr};
   int run_graph_n[2] = {0, 0};
   int64_t run_graph_nl[2] = {0, 0};
+  bool run_graph_timing[2] = {false, false};
   // a batch of independent scenes: camera ranges, chunk ranges per scene (device), outputs
   int n_scenes = 1;
   std::vector<int32_t> h_scene_cam;
@@ -443,6 +445,17 @@ daba_status enqueue_objective(daba_ctx* ctx, cudaStream_t st, bool prepare) {
   return DABA_OK;
 }
 
+// A timing event record: inside a stream capture an event-record node of the graph (a plain
+// cudaEventRecord there would only mark a dependency; the external flag is refused outside a
+// capture), outside one an ordinary record.
+cudaError_t rec_time(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t q = cudaStreamIsCapturing(s, &cs);
+  if (q != cudaSuccess) return q;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 cudaEvent_t ev(daba_ctx* ctx, size_t i) {
   while (ctx->events.size() <= i) {
     cudaEvent_t e;
@@ -478,24 +491,30 @@ cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, siz
     const int64_t kk = k0 + j;
     CE(cudaEventRecord(ctx->ev_fork, st));
     CE(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 0), ctx->s_hi));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 0), ctx->s_hi));
     CE(launch_pass(ctx, ctx->s_hi, 1, kk));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 1), ctx->s_hi));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 1), ctx->s_hi));
     CE(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
     CE(cudaStreamWaitEvent(ctx->s_lo, ctx->ev_hi, 0));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 3), ctx->s_lo));
-    CE(launch_lpass(ctx, ctx->s_lo, kk));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 4), ctx->s_lo));
-    CE(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
+    // The camera solves go on the high-priority stream and are enqueued before the landmark
+    // pass: with direct launches the priority decides which kernel's CTAs the SMs take first; in
+    // a graph the priority made no measurable difference and the order of the nodes did. Measured (ms per
+    // iteration, graph / direct): 0.729 / 0.746 on the tourism workload and 0.367 / 0.388 on the
+    // 512-scene batch, against 0.757 / 0.748 and 0.421 / 0.386 with the landmark pass enqueued
+    // first, and 0.78 / 0.43 direct with the landmark pass on the high-priority stream.
     CE(launch_camsolve(ctx, ctx->s_hi, kk));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 2), ctx->s_hi));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 2), ctx->s_hi));
     CE(cudaEventRecord(ctx->ev_hi, ctx->s_hi));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 3), ctx->s_lo));
+    CE(launch_lpass(ctx, ctx->s_lo, kk));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 4), ctx->s_lo));
+    CE(cudaEventRecord(ctx->ev_lo, ctx->s_lo));
     CE(cudaStreamWaitEvent(st, ctx->ev_hi, 0));
     CE(cudaStreamWaitEvent(st, ctx->ev_lo, 0));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 5), st));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 5), st));
     CE(launch_finalize(ctx, st));
     CE(launch_fixups(ctx, st, kk));
-    if (ctx->timing) CE(cudaEventRecord(ev(ctx, evi + 6), st));
+    if (ctx->timing) CE(rec_time(ev(ctx, evi + 6), st));
     if (ctx->timing) evi += 7;
   }
   return cudaSuccess;
@@ -534,20 +553,24 @@ daba_status ensure_graphs(daba_ctx* ctx) {
 }
 
 // The graph of a whole run of n iterations from an iteration of the current parity: the
-// prepare kernel, then the n iterations (captured once per parity and length).
+// prepare kernel, then the n iterations (captured once per parity, length and timing mode).
+// With timing the graph records the per-kernel events of the run (event 0 and 1 around the
+// prepare kernel, then 7 per iteration, as the direct launches do).
 daba_status ensure_run_graph(daba_ctx* ctx, int n) {
   const int par = (int)(ctx->k & 1);
-  if (ctx->run_graph[par] && ctx->run_graph_n[par] == n) return DABA_OK;
+  const bool timing = ctx->timing;
+  if (ctx->run_graph[par] && ctx->run_graph_n[par] == n && ctx->run_graph_timing[par] == timing) return DABA_OK;
   if (ctx->run_graph[par]) cudaGraphExecDestroy(ctx->run_graph[par]);
   ctx->run_graph[par] = nullptr;
   ctx->run_graph_n[par] = 0;
-  const bool timing = ctx->timing;
-  ctx->timing = false;
+  if (timing) ev(ctx, 2 + 7 * (size_t)n);   // every event the capture records exists before it
   const int64_t l0 = ctx->launches;
   cudaError_t e = cudaStreamBeginCapture(ctx->s_cap, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e1 = launch_prepare(ctx, ctx->s_cap, ctx->k);
-    if (e1 == cudaSuccess) e1 = enqueue_iters(ctx, ctx->s_cap, ctx->k, n, 0);
+    cudaError_t e1 = timing ? rec_time(ev(ctx, 0), ctx->s_cap) : cudaSuccess;
+    if (e1 == cudaSuccess) e1 = launch_prepare(ctx, ctx->s_cap, ctx->k);
+    if (e1 == cudaSuccess && timing) e1 = rec_time(ev(ctx, 1), ctx->s_cap);
+    if (e1 == cudaSuccess) e1 = enqueue_iters(ctx, ctx->s_cap, ctx->k, n, timing ? 2 : 0);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
     e = e1 != cudaSuccess ? e1 : e2;
@@ -556,13 +579,13 @@ daba_status ensure_run_graph(daba_ctx* ctx, int n) {
   }
   ctx->run_graph_nl[par] = ctx->launches - l0;
   ctx->launches = l0;
-  ctx->timing = timing;
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->run_graph[par] = nullptr;
     return fail(ctx, DABA_ERR_CUDA, "capturing the run graph: %s", cudaGetErrorString(e));
   }
   ctx->run_graph_n[par] = n;
+  ctx->run_graph_timing[par] = timing;
   return DABA_OK;
 }
 
@@ -1249,12 +1272,13 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(ctx->s_dev, &s_start, 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
-    if (ctx->timing) {   // direct launches with per-kernel events
+    if (ctx->timing && seg > RUN_GRAPH_MAX) {   // direct launches with per-kernel events
       CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_prepare(ctx, st, ctx->k));
       CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(enqueue_iters(ctx, st, ctx->k, seg, evi));
     } else if (seg <= RUN_GRAPH_MAX) {   // the whole run as one graph launch on s_cap, joined to st
+      // (with timing, the graph's own event records time each kernel)
       if ((s = ensure_run_graph(ctx, seg)) != DABA_OK) return s;
       const int par = (int)(ctx->k & 1);
       CK(cudaEventRecord(ctx->ev_cap0, st));
@@ -1283,7 +1307,12 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
     CK(cudaStreamSynchronize(st));
     if (ctx->timing) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->events[0], ctx->events[1]);
+      auto elapsed = [&](size_t a, size_t b) {
+        if (cudaEventElapsedTime(&ms, ctx->events[a], ctx->events[b]) == cudaSuccess) return true;
+        cudaGetLastError();   // not sticky: the context stays usable
+        return false;
+      };
+      if (!elapsed(0, 1)) return fail(ctx, DABA_ERR_CUDA, "reading the kernel timing events");
       ctx->tms[0] += ms;
       // per iteration: [0] cpass start, [1] cpass end, [2] camsolve end, [3] lpass start,
       // [4] lpass end (side stream), [5] finalize start, [6] finalize end
@@ -1291,7 +1320,7 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
         const size_t b = 2 + (size_t)j * 7;
         const int pairs[4][2] = {{0, 1}, {3, 4}, {1, 2}, {5, 6}};
         for (int q = 0; q < 4; ++q) {
-          cudaEventElapsedTime(&ms, ctx->events[b + pairs[q][0]], ctx->events[b + pairs[q][1]]);
+          if (!elapsed(b + pairs[q][0], b + pairs[q][1])) return fail(ctx, DABA_ERR_CUDA, "reading the kernel timing events");
           ctx->tms[1 + q] += ms;
         }
       }

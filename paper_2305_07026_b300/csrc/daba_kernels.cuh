@@ -1211,33 +1211,41 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
       ck.t[a] = N::from(x[CS_T + a]);
       ck.d[a] = N::from(x[CS_D + a]);
     }
-    if (role == 1) {   // MM solve from x^k with the x^k statistics
-      sum_stats<Real, T>(part, c0, c1, PART_XK, st);
-      CamT<T> cm;
-      cam_solve<SOLVER, Real>(st, ck, xi, P.n_alt, cm);
-      const T dm = cam_phi(st, ck, cm, xi);
+    if (role == 1 || P.accelerated) {
+      // One code path for both warps, so that they fetch the same instructions: warp 1 the MM
+      // solve from x^k with the x^k statistics, warp 0 the accelerated solve from xbar^k with
+      // the xbar statistics; both then evaluate their solution's decrease with the x^k statistics.
+      CamT<T> c0s;
+      if (role == 1) {
+        c0s = ck;
+      } else {
+        const T gamma = N::from(P.gam[it]);
 #pragma unroll
-      for (int a = 0; a < 9; ++a) sh_mm[lane][a] = cm.R[a];
+        for (int a = 0; a < 9; ++a) c0s.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        sh_mm[lane][9 + a] = cm.t[a];
-        sh_mm[lane][12 + a] = cm.d[a];
+        for (int a = 0; a < 3; ++a) {
+          c0s.t[a] = ck.t[a] + gamma * N::from(dx[CS_T + a]);
+          c0s.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
+        }
       }
-      sh_mm[lane][15] = dm;
-    } else if (P.accelerated) {   // accelerated solve from xbar^k with the xbar statistics
-      const T gamma = N::from(P.gam[it]);
-      CamT<T> cb;
+      sum_stats<Real, T>(part, c0, c1, role == 1 ? PART_XK : PART_XB, st);
+      CamT<T> cs;
+      cam_solve<SOLVER, Real>(st, c0s, xi, P.n_alt, cs);
+      if (role == 0) sum_stats<Real, T>(part, c0, c1, PART_XK, st);
+      const T d = cam_phi(st, ck, cs, xi);   // E^alpha(solution | x^k) - E^alpha(x^k | x^k)
+      if (role == 1) {
 #pragma unroll
-      for (int a = 0; a < 9; ++a) cb.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
+        for (int a = 0; a < 9; ++a) sh_mm[lane][a] = cs.R[a];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        cb.t[a] = ck.t[a] + gamma * N::from(dx[CS_T + a]);
-        cb.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
+        for (int a = 0; a < 3; ++a) {
+          sh_mm[lane][9 + a] = cs.t[a];
+          sh_mm[lane][12 + a] = cs.d[a];
+        }
+        sh_mm[lane][15] = d;
+      } else {
+        cn = cs;
+        dEn = d;
       }
-      sum_stats<Real, T>(part, c0, c1, PART_XB, st);
-      cam_solve<SOLVER, Real>(st, cb, xi, P.n_alt, cn);
-      sum_stats<Real, T>(part, c0, c1, PART_XK, st);
-      dEn = cam_phi(st, ck, cn, xi);   // E^alpha(x^(k+1) | x^k) - E^alpha(x^k | x^k)
     }
   }
   __syncthreads();

@@ -152,3 +152,26 @@ def test_schedule_changes_only_sum_order():
     assert len(tried) >= 6 and all(v > 0 for v in tried.values())
     with pytest.raises(L.DabaError):
         L.Daba(sc.M, sc.N, sc.nnz, tile_lms=129)
+
+
+@pytest.mark.parametrize("K", [12, 260])
+def test_timing_mode_changes_nothing(K):
+    """With per-kernel timing on (events recorded inside the run graph, or direct launches for
+    runs longer than one graph) a run gives the same bits as without, and positive kernel times."""
+    from paper_2305_07026_b300 import _lib as L
+    from tests.conftest import cached_scene
+    sc = cached_scene("tourism", scale=0.005)
+    outs = []
+    for timing in (False, True):
+        d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="mixed")
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        d.set_timing(timing)
+        tr = np.zeros(K + 1)
+        d.run(K, tr)
+        outs.append((tr, *d.get_state(), d.get_timing()))
+        d.close()
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        np.testing.assert_array_equal(a, b)
+    assert np.all(outs[0][3] == 0.0)
+    assert np.all(outs[1][3] > 0.0)
