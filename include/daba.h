@@ -227,7 +227,10 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
  * iterations) for the kernels of one iteration, in the order:
  * [0] camera prepare of the first iteration (extrapolation, Eq. nesterov_x), [1] camera-sorted observation pass,
  * [2] landmark-sorted observation pass + landmark solves, [3] camera solves + next extrapolation, [4] reduction.
- * Timing is recorded only when enabled with daba_set_timing(ctx, 1). */
+ * Timing is recorded only when enabled with daba_set_timing(ctx, 1): a run of at most 256
+ * iterations is then its own graph with an event-record node around every kernel (the nodes
+ * lengthen each iteration by some tens of microseconds), a longer run is launched directly with
+ * events. Results do not depend on it. */
 daba_status daba_set_timing(daba_ctx* ctx, int enable);
 daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
 
