@@ -240,6 +240,21 @@ def sub_problem(sc, frac_obs, seed=0):
     return sc.cams[cu], sc.lms[lu], ci_r.astype(np.int32), li_r.astype(np.int32), sc.uv[mask]
 
 
+def tourism_config(sc, world, prec, l2="inputs larger than L2 (working set > 1 GB vs 126 MB L2), no flush"):
+    """The config object of a single-problem workload line (both arms)."""
+    return {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
+                        f"power-law tracks, {sc.loss} loss {sc.loss_scale_px} px",
+            "M": sc.M, "N": sc.N, "nnz": sc.nnz, "prec": prec, "parallelism": f"replicas x{world}", "l2": l2}
+
+
+def batch_config(n, M, N, nnz, world, prec, l2="working set > 126 MB L2, no flush"):
+    """The config object of a batch workload line (both arms)."""
+    return {"workload": f"batch: {n} circle scenes, cameras log-uniform [5, 200], landmarks log-uniform "
+                        f"[100, 20000], geometric tracks (mean 4): {M} cameras, {N} landmarks, "
+                        f"{nnz} observations", "M": M, "N": N, "nnz": nnz, "prec": prec,
+            "parallelism": f"replicas x{world}", "l2": l2}
+
+
 def cpu_oracle(sc, target_seconds, steps=None, warmup=0):
     """Times oracle iterations on a sample sized for ~target_seconds; returns (value, info)."""
     import contextlib
@@ -487,10 +502,7 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 per observation, f64 reductions/solves", "data": "synthetic",
-        "config": {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
-                               f"power-law tracks, {sc.loss} loss {sc.loss_scale_px} px",
-                   "M": sc.M, "N": sc.N, "nnz": sc.nnz, "prec": "mixed", "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (working set > 1 GB vs 126 MB L2), no flush"},
+        "config": tourism_config(sc, world, "mixed"),
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / Kf,
                       "mixed_speedup": value / world / fp64_value},
         "accuracy": accuracy,
@@ -576,10 +588,7 @@ def run_batch(args, rank, world, local):
         "unit": "scenes/s", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 per observation, f64 reductions/solves", "data": "synthetic",
-        "config": {"workload": f"batch: {n} circle scenes, cameras log-uniform [5, 200], landmarks log-uniform "
-                               f"[100, 20000], geometric tracks (mean 4): {b.M} cameras, {b.N} landmarks, "
-                               f"{b.nnz} observations", "M": b.M, "N": b.N, "nnz": b.nnz, "prec": "mixed",
-                   "parallelism": f"replicas x{world}", "l2": "working set > 126 MB L2, no flush"},
+        "config": batch_config(n, b.M, b.N, b.nnz, world, "mixed"),
         "obs_updates_per_s": world * b.nnz * K / (ms / 1e3),
         "schedule": {"chosen": sched, "ms_per_iteration_tried": tried},
         "latency_ms": {"p50": ms, "p99": ms, "note": "every scene of the batch completes with the batch"},
@@ -620,12 +629,16 @@ def run_reference_batch(args, world):
             obs += sc.nnz
     per_scene_iter = t_used / (done * iters)
     value = 1.0 / (per_scene_iter * args.steps)
+    n = len(scs)
     return {
         "metric": f"scenes/s ({args.steps} DABA iterations per scene, batched)", "value": value, "unit": "scenes/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        # one step is one iteration of every scene of the batch, at the sampled rate
+        "ms_per_step": 1e3 * n * per_scene_iter,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": f"batch: {len(scs)} circle scenes (the batch workload of the GPU arm)", "prec": "fp64 (oracle)"},
+        "config": batch_config(n, sum(c.M for c in scs), sum(c.N for c in scs), sum(c.nnz for c in scs), world,
+                               "fp64 (oracle)", l2="host cores"),
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "scenes/s",
                          "sample": f"the first {done} scenes ({obs} observations), {iters} oracle iterations each, "
                                    f"{t_used:.1f} s, scaled to {args.steps} iterations per scene"},
@@ -646,11 +659,10 @@ def run_reference(args, rank, world):
     info["value"] = value
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        # one step is one iteration over the whole workload, at the sampled rate
+        "warmup": args.warmup, "ms_per_step": 1e3 * sc.nnz / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
-                               f"power-law tracks, {sc.loss} loss {sc.loss_scale_px} px",
-                   "M": sc.M, "N": sc.N, "nnz": sc.nnz, "prec": "fp64 (oracle)"},
+        "config": tourism_config(sc, world, "fp64 (oracle)", l2="host cores"),
         "cpu_baseline": info,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
