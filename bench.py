@@ -18,6 +18,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -240,6 +241,20 @@ def sub_problem(sc, frac_obs, seed=0):
     return sc.cams[cu], sc.lms[lu], ci_r.astype(np.int32), li_r.astype(np.int32), sc.uv[mask]
 
 
+def host_cpu():
+    """The host the oracle ran on: logical CPUs and the CPU model (from /proc/cpuinfo when present)."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def tourism_config(sc, world, prec, l2="inputs larger than L2 (working set > 1 GB vs 126 MB L2), no flush"):
     """The config object of a single-problem workload line (both arms)."""
     return {"workload": f"{sc.name}: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations, "
@@ -280,7 +295,7 @@ def cpu_oracle(sc, target_seconds, steps=None, warmup=0):
             st, _ = O.step(prob, st)
         dt = time.perf_counter() - t0
     value = ci.size * n_steps / dt
-    return value, {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT,
+    return value, {"kind": "oracle", "cores": 1, "value": value, "unit": UNIT, "host": host_cpu(),
                    "sample": f"{ci.size} observations of {cams.shape[0]} randomly chosen cameras of the "
                              f"{sc.name} workload ({lms.shape[0]} landmarks), {n_steps} oracle iterations "
                              f"(FP64 numpy, 1 thread), {dt:.1f} s"}
@@ -639,7 +654,7 @@ def run_reference_batch(args, world):
         "impl": "reference",
         "config": batch_config(n, sum(c.M for c in scs), sum(c.N for c in scs), sum(c.nnz for c in scs), world,
                                "fp64 (oracle)", l2="host cores"),
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "scenes/s",
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "scenes/s", "host": host_cpu(),
                          "sample": f"the first {done} scenes ({obs} observations), {iters} oracle iterations each, "
                                    f"{t_used:.1f} s, scaled to {args.steps} iterations per scene"},
         "e2e": {"value": value, "unit": "scenes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -28,6 +28,7 @@ def test_reference_arm_line(workload, extra):
     assert line["value"] > 0 and line["ms_per_step"] > 0
     cb, e2e = line["cpu_baseline"], line["e2e"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["cpu_model"]
     assert e2e == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cfg = line["config"]
     assert {"workload", "M", "N", "nnz", "prec", "parallelism"} <= set(cfg)
