@@ -1,0 +1,68 @@
+"""Parity of the camera block solves on the CPU: the library's FP64 camera statistics
+(eval_obs + accumulate_cam of the camera pass), S-CAM solve (cam_scam), surrogate decrease
+(cam_phi) and Levenberg-Marquardt step (cam_lm), built for the host with g++, against the
+oracle's majorizer (Proposition 1), solve_cameras (block-exact alternation on Eq. Ealpha),
+E_cam and solve_cameras_lm on the same seeded camera. No GPU."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+from tests.test_host_device_math import FLAGS, HOST
+
+LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
+
+
+@pytest.fixture(scope="module")
+def cam_solve(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path_factory.mktemp("cam_solve") / "cam_solve")
+    build = subprocess.run([gxx, *FLAGS, os.path.join(HOST, "cam_solve.cpp"), "-o", exe], capture_output=True, text=True)
+    assert build.returncode == 0, build.stderr[-4000:]
+    return exe
+
+
+def _camera(seed, m, c):
+    """One camera and m landmarks in front of it along its rays, with residuals on both sides of
+    the loss scale (internal units)."""
+    rng = np.random.default_rng(seed)
+    R = O.so3_exp(rng.uniform(-1.0, 1.0, (1, 3)))
+    t = rng.uniform(-1.0, 1.0, (1, 3))
+    d = np.array([[1.0 + 0.1 * rng.uniform(-1, 1), 0.1 * rng.uniform(-1, 1), 0.05 * rng.uniform(-1, 1)]])
+    u = rng.uniform(-0.5, 0.5, (m, 2))
+    lam_t = rng.uniform(2.0, 6.0, m)
+    spread = np.where(np.arange(m) % 2 == 0, 2.5, 0.25) * c
+    Rm, tm, dm = np.repeat(R, m, 0), np.repeat(t, m, 0), np.repeat(d, m, 0)
+    l = tm + np.einsum("nab,nb->na", Rm, O.ray(u, dm)) / lam_t[:, None] + spread[:, None] * rng.uniform(-1, 1, (m, 3))
+    return R, t, d, l, u
+
+
+@pytest.mark.parametrize("loss", sorted(LOSSES))
+@pytest.mark.parametrize("xi, n_alt", [(1e-10, 2), (0.5, 1), (0.5, 3)])
+def test_camera_solves_match_oracle(cam_solve, loss, xi, n_alt):
+    m, c = 40, 0.02
+    R, t, d, l, u = _camera(100 + LOSSES[loss] + int(10 * xi) + n_alt, m, c)
+    stdin = (f"{LOSSES[loss]} {c!r} {xi!r} {n_alt} {m}\n"
+             + " ".join(repr(float(x)) for x in np.concatenate([R.ravel(), t.ravel(), d.ravel()])) + "\n"
+             + "\n".join(" ".join(repr(float(x)) for x in row) for row in np.concatenate([l, u], 1)) + "\n")
+    run = subprocess.run([cam_solve], input=stdin, capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr[-2000:]
+    dev = np.array([[float(x) for x in line.split()] for line in run.stdout.splitlines()])
+    assert dev.shape == (2, 16)
+
+    idx = np.zeros(m, dtype=np.int64)
+    mj = O.majorizer(loss, c, np.repeat(R, m, 0), np.repeat(t, m, 0), np.repeat(d, m, 0), l, u)
+    E0 = O.E_cam(xi, mj, R, t, d, R, t, d, idx, u, 1)[0]
+    for row, (Rn, tn, dn) in zip(dev, (O.solve_cameras(xi, mj, R, t, d, idx, u, 1, n_alt),
+                                       O.solve_cameras_lm(xi, mj, R, t, d, idx, u, 1))):
+        ora = np.concatenate([Rn.ravel(), tn.ravel(), dn.ravel()])
+        np.testing.assert_allclose(row[:15], ora, rtol=0, atol=1e-9)
+        dec = O.E_cam(xi, mj, Rn, tn, dn, R, t, d, idx, u, 1)[0] - E0
+        # the oracle's decrease is a difference of two sums of size E0; the library forms it directly
+        np.testing.assert_allclose(row[15], dec, rtol=0, atol=1e-11 * max(1.0, abs(E0)))
+        assert row[15] <= 1e-12   # a block solve never raises its surrogate (Eq. Ealpha)
