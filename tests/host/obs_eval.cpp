@@ -1,51 +1,65 @@
-// The library's per-observation evaluation (eval_obs, FP64 instantiation) compiled for the host,
-// driven from stdin so that a test can compare it with the oracle on the same inputs.
-// stdin: "loss c n" (loss 0 trivial, 1 Huber, 2 Cauchy, 3 Welsch; c the loss scale), then n lines
-// of 48 numbers: R^k (9, row-major), t^k (3), d^k (3), R^(k-1) (9), t^(k-1) (3), d^(k-1) (3),
-// Rbar (9), l^k (3), l^(k-1) (3), u (2), gamma.
+// The library's per-observation evaluation (eval_obs, as the camera pass calls it, in FP64 or
+// in FP32) compiled for the host and driven from stdin, so that a test can compare it with the
+// oracle on the same inputs. The camera pack is written by the library's own write_pack_t; the
+// FP32 landmark position is its high part and its displacement is rounded to FP32, as in the
+// pass's landmark records.
+// stdin: "bits loss c n" (bits 64 or 32; loss 0 trivial, 1 Huber, 2 Cauchy, 3 Welsch; c the loss
+// scale), then n lines of 48 numbers: R^k (9, row-major), t^k (3), d^k (3), R^(k-1) (9),
+// t^(k-1) (3), d^(k-1) (3), Rbar (9), l^k (3), l^(k-1) (3), u (2), gamma.
 // stdout per observation: lambda, R e (3), r = |e|^2, rho(r), w at x^k; lambda, Rbar ebar (3),
 // w at the extrapolated iterate; the surrogate gap.
-#include "../../paper_2305_07026_b300/csrc/daba_device.cuh"
+#include "../../paper_2305_07026_b300/csrc/daba_kernels.cuh"
 
 #include <cstdio>
 
 using namespace daba;
 
-template <int LOSS>
-void run(const LossC<double>& L, int n) {
+template <int LOSS, class Real>
+void run(double c, int n) {
+  LossC<Real> L;
+  L.c = Real(c), L.c2 = Real(c * c), L.inv_c2 = Real(1.0 / (c * c));
   for (int o = 0; o < n; ++o) {
     double v[48];
     for (double& x : v)
       if (std::scanf("%lf", &x) != 1) return;
     const double *Rk = v, *tk = v + 9, *dk = v + 12, *Rp = v + 15, *tp = v + 24, *dp = v + 27, *Rb = v + 30,
                  *lk = v + 39, *lp = v + 42, *u = v + 45;
-    const double gamma = v[47];
-    // the camera pack as the library writes it (FP64: no low parts)
-    V4<double> pk[P4N];
-    for (int r = 0; r < 3; ++r) {
-      pk[P4_RK + r] = {Rk[3 * r], Rk[3 * r + 1], Rk[3 * r + 2], tk[r]};
-      pk[P4_RB + r] = {Rb[3 * r], Rb[3 * r + 1], Rb[3 * r + 2], tk[r] - tp[r]};
-      pk[P4_DR + r] = {Rk[3 * r] - Rp[3 * r], Rk[3 * r + 1] - Rp[3 * r + 1], Rk[3 * r + 2] - Rp[3 * r + 2], 0.0};
+    CamT<double> x, dx;
+    for (int a = 0; a < 9; ++a) x.R[a] = Rk[a], dx.R[a] = Rk[a] - Rp[a];
+    for (int a = 0; a < 3; ++a) x.t[a] = tk[a], dx.t[a] = tk[a] - tp[a], x.d[a] = dk[a], dx.d[a] = dk[a] - dp[a];
+    V4<Real> pk[P4N];
+    write_pack_t<Real>(x, dx, Rb, pk);
+    Real l[3], lo[3], dl[3];
+    for (int a = 0; a < 3; ++a) {
+      split_real(lk[a], l[a], lo[a]);
+      dl[a] = to_real<Real>(lk[a] - lp[a]);
     }
-    pk[P4_D] = {dk[0], dk[1], dk[2], 0.0};
-    pk[P4_DD] = {dk[0] - dp[0], dk[1] - dp[1], dk[2] - dp[2], 0.0};
-    ObsEval<double> ev;
-    eval_obs<LOSS, double>(pk, lk[0], lk[1], lk[2], 0.0, 0.0, 0.0, lk[0] - lp[0], lk[1] - lp[1], lk[2] - lp[2], u[0],
-                           u[1], gamma, L, ev);
-    std::printf("%.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g\n", ev.lam, ev.Re0,
-                ev.Re1, ev.Re2, ev.r, ev.rho, ev.w, ev.lamb, ev.Reb0, ev.Reb1, ev.Reb2, ev.wb, ev.gap);
+    ObsEval<Real> ev;
+    eval_obs<LOSS, Real>(pk, l[0], l[1], l[2], Real(0), Real(0), Real(0), dl[0], dl[1], dl[2], to_real<Real>(u[0]),
+                         to_real<Real>(u[1]), Real(v[47]), L, ev);
+    const double out[13] = {double(ev.lam), double(ev.Re0), double(ev.Re1), double(ev.Re2), double(ev.r),
+                            double(ev.rho), double(ev.w),   double(ev.lamb), double(ev.Reb0), double(ev.Reb1),
+                            double(ev.Reb2), double(ev.wb), double(ev.gap)};
+    for (int k = 0; k < 13; ++k) std::printf(k ? " %.17g" : "%.17g", out[k]);
+    std::printf("\n");
   }
 }
 
+template <class Real>
+void dispatch(int loss, double c, int n) {
+  if (loss == LOSS_TRIVIAL) run<LOSS_TRIVIAL, Real>(c, n);
+  if (loss == LOSS_HUBER) run<LOSS_HUBER, Real>(c, n);
+  if (loss == LOSS_CAUCHY) run<LOSS_CAUCHY, Real>(c, n);
+  if (loss == LOSS_WELSCH) run<LOSS_WELSCH, Real>(c, n);
+}
+
 int main() {
-  int loss = 0, n = 0;
+  int bits = 64, loss = 0, n = 0;
   double c = 1.0;
-  if (std::scanf("%d %lf %d", &loss, &c, &n) != 3) return 1;
-  LossC<double> L;
-  L.c = c, L.c2 = c * c, L.inv_c2 = 1.0 / (c * c);
-  if (loss == LOSS_TRIVIAL) run<LOSS_TRIVIAL>(L, n);
-  if (loss == LOSS_HUBER) run<LOSS_HUBER>(L, n);
-  if (loss == LOSS_CAUCHY) run<LOSS_CAUCHY>(L, n);
-  if (loss == LOSS_WELSCH) run<LOSS_WELSCH>(L, n);
+  if (std::scanf("%d %d %lf %d", &bits, &loss, &c, &n) != 4) return 1;
+  if (bits == 32)
+    dispatch<float>(loss, c, n);
+  else
+    dispatch<double>(loss, c, n);
   return 0;
 }
