@@ -320,8 +320,8 @@ __device__ __forceinline__ double widen(double d) { return d; }
 // FP64 -> FP32 conversions with integer operations on the IEEE-754 encodings (no FP64
 // instruction). narrow(d) = the float nearest to d (ties to even); split_df(d) also gives
 // lo = the float nearest to d - hi, so that hi + lo carries d to about 2^-48 relative.
-// Magnitudes below the FP32 normal range give signed zero, above it infinity; a low part
-// that would be subnormal is flushed to zero.
+// Magnitudes below the FP32 normal range give signed zero, above it infinity; the low part is
+// zero for |d| < 2^-74, where the remainder's unit 2^(e-52) falls below the FP32 normal range.
 __device__ __forceinline__ void split_df_impl(double d, float& hi, float& lo, bool want_lo) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned sgn = (unsigned)(b >> 63) << 31;

@@ -1,0 +1,99 @@
+"""Bit-exact check of the library's integer-only FP64 <-> FP32 conversions (the MIXED path's
+narrow, split_df and widen, which keep conversions off the FP64 unit), built for the host with
+g++, against IEEE-754 conversions in numpy: narrow(d) is the float nearest to d, ties to even;
+split_df gives that float and the float nearest to the remainder; widen is exact. Documented
+exceptions: magnitudes below the FP32 normal range give signed zero (numpy gives subnormals),
+and so does widen of an FP32 subnormal; the low part is zero for |d| < 2^-74 (its unit would be
+subnormal). No GPU."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from tests.test_host_device_math import FLAGS, HOST
+
+F32_MIN_NORMAL = float(np.finfo(np.float32).tiny)
+
+
+def _doubles(rng, n):
+    """Doubles across the FP32 range and beyond, exact FP32 ties, and special values."""
+    e = rng.integers(-140, 140, n)
+    d = rng.uniform(1.0, 2.0, n) * np.exp2(e.astype(np.float64)) * rng.choice([-1.0, 1.0], n)
+    # exact ties: a float plus half its ulp (both parities of the last mantissa bit)
+    f = rng.uniform(1.0, 2.0, n // 4).astype(np.float32) * np.exp2(rng.integers(-100, 100, n // 4)).astype(np.float32)
+    ulp = np.spacing(f).astype(np.float64)
+    ties = f.astype(np.float64) + 0.5 * ulp
+    specials = np.array([0.0, -0.0, np.inf, -np.inf, 1.0, -1.0, float(np.finfo(np.float32).max),
+                         float(np.finfo(np.float32).max) * (1 + 2 ** -25), float(np.finfo(np.float32).max) * (1 + 2 ** -23),
+                         F32_MIN_NORMAL, -F32_MIN_NORMAL, F32_MIN_NORMAL * (1 - 2 ** -30), 2.0 ** 127, 2.0 ** 128,
+                         1.0 + 2 ** -24, 1.0 + 2 ** -24 + 2 ** -50, 1.0 - 2 ** -25, 3.0 * 2 ** -150])
+    return np.concatenate([d, ties, specials])
+
+
+@pytest.fixture(scope="module")
+def converted(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path_factory.mktemp("conversions") / "conversions")
+    build = subprocess.run([gxx, *FLAGS, os.path.join(HOST, "conversions.cpp"), "-o", exe], capture_output=True,
+                           text=True)
+    assert build.returncode == 0, build.stderr[-4000:]
+    rng = np.random.default_rng(9)
+    d = _doubles(rng, 20000)
+    f = np.concatenate([rng.standard_normal(d.size - 6).astype(np.float32) * np.exp2(rng.integers(-120, 120, d.size - 6)).astype(np.float32),
+                        np.array([0.0, -0.0, np.inf, -np.inf, 1e-40, -3e-39], dtype=np.float32)])
+    db = d.view(np.uint64)
+    fb = f.view(np.uint32)
+    stdin = f"{d.size}\n" + "\n".join(f"{int(a):016x} {int(b):08x}" for a, b in zip(db, fb)) + "\n"
+    run = subprocess.run([exe], input=stdin, capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0, run.stderr[-2000:]
+    rows = [line.split() for line in run.stdout.splitlines()]
+    assert len(rows) == d.size
+    narrow = np.array([int(r[0], 16) for r in rows], dtype=np.uint32).view(np.float32)
+    hi = np.array([int(r[1], 16) for r in rows], dtype=np.uint32).view(np.float32)
+    lo = np.array([int(r[2], 16) for r in rows], dtype=np.uint32).view(np.float32)
+    wide = np.array([int(r[3], 16) for r in rows], dtype=np.uint64).view(np.float64)
+    return d, f, narrow, hi, lo, wide
+
+
+def _same_bits(a, b):
+    return np.array_equal(np.asarray(a).view(np.uint32 if a.dtype == np.float32 else np.uint64),
+                          np.asarray(b).view(np.uint32 if b.dtype == np.float32 else np.uint64))
+
+
+def test_narrow_is_round_to_nearest_even(converted):
+    d, _, narrow, hi, _, _ = converted
+    with np.errstate(over="ignore"):
+        ref = d.astype(np.float32)   # IEEE round to nearest, ties to even; overflow to infinity
+    tiny = np.abs(d) < F32_MIN_NORMAL
+    ref[tiny] = np.copysign(np.float32(0.0), d[tiny]).astype(np.float32)
+    assert _same_bits(narrow, ref)
+    assert _same_bits(hi, ref)
+
+
+def test_split_low_part(converted):
+    d, _, _, hi, lo, _ = converted
+    fin = np.isfinite(hi) & (hi != 0)
+    rem = d[fin] - hi[fin].astype(np.float64)          # exact in FP64
+    ref = rem.astype(np.float32)
+    ref[np.abs(d[fin]) < 2.0 ** -74] = np.float32(0.0)   # the remainder's unit is below the normal range
+    got = lo[fin].copy()
+    got[got == 0] = np.float32(0.0)                     # compare zeros without their sign
+    ref[ref == 0] = np.float32(0.0)
+    assert _same_bits(got, ref)
+    # hi + lo carries d to about 2^-48 relative where the low part is representable
+    ok = np.abs(d[fin]) >= 2.0 ** -74
+    carried = hi[fin][ok].astype(np.float64) + lo[fin][ok].astype(np.float64)
+    assert np.all(np.abs(carried - d[fin][ok]) <= 2.0 ** -47 * np.abs(d[fin][ok]))
+    assert np.all(lo[~fin] == 0)
+
+
+def test_widen_is_exact(converted):
+    _, f, _, _, _, wide = converted
+    ref = f.astype(np.float64)
+    sub = (np.abs(f) < F32_MIN_NORMAL) & (f != 0)
+    ref[sub] = np.copysign(0.0, f[sub].astype(np.float64))
+    assert _same_bits(wide, ref)
