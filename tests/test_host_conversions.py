@@ -97,3 +97,24 @@ def test_widen_is_exact(converted):
     sub = (np.abs(f) < F32_MIN_NORMAL) & (f != 0)
     ref[sub] = np.copysign(0.0, f[sub].astype(np.float64))
     assert _same_bits(wide, ref)
+
+
+def test_device_nesterov_scalar_is_the_oracles(tmp_path):
+    """nesterov_next (Eq. nesterov_scalar on the device, each operation rounded separately) gives
+    the oracle's s^(k) bit for bit over 5,000 iterations, so that a run whose momentum reset keeps
+    s on the device takes the same extrapolation ratios as the host-computed table."""
+    from oracle import daba_oracle as O
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path / "scalars")
+    build = subprocess.run([gxx, *FLAGS, os.path.join(HOST, "scalars.cpp"), "-o", exe], capture_output=True, text=True)
+    assert build.returncode == 0, build.stderr[-4000:]
+    n = 5000
+    run = subprocess.run([exe], input=f"{n}\n", capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0
+    dev = np.array([int(x, 16) for x in run.stdout.split()], dtype=np.uint64).view(np.float64)
+    ref = [1.0]
+    for _ in range(n):
+        ref.append(float(O.nesterov(ref[-1])[0]))
+    assert _same_bits(dev, np.array(ref))
