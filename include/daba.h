@@ -49,7 +49,8 @@ typedef enum {
   DABA_ERR_NONFINITE = 4,   /* non-finite input value, or the iterate became non-finite */
   DABA_ERR_CUDA = 5,        /* a CUDA runtime call failed */
   DABA_ERR_OOM = 6,         /* device allocation failed */
-  DABA_ERR_STATE = 7        /* call out of order (e.g. run before observations and state are set) */
+  DABA_ERR_STATE = 7,       /* call out of order (e.g. run before observations and state are set) */
+  DABA_ERR_TIMEOUT = 8      /* a bounded wait inside a kernel ran out (see daba_set_wait_limit) */
 } daba_status;
 
 /* Robust losses of Assumption 1 (App. B); `loss_scale_px` is c below, in pixels.
@@ -137,7 +138,12 @@ daba_status daba_set_state(daba_ctx* ctx, const double* cams, const double* lms,
  * restarts (iters int32, host or device, may be NULL): number of blocks whose
  *   adaptive restart fired in each iteration (Algorithm 1, restart test).
  * Requires observations and state to be set (DABA_ERR_STATE otherwise). Returns
- * DABA_ERR_NONFINITE if the objective became non-finite (state is then undefined).
+ * DABA_ERR_NONFINITE if the objective became non-finite and DABA_ERR_TIMEOUT if a landmark-pass
+ * wait on its tile copies ran out (daba_set_wait_limit). Any failure after the first launch puts
+ * back the entry state: the iterate x^k, x^(k-1), s^k, k, the restart metrics and the per-block
+ * diagnostics of daba_get_block_metrics are then those from before the call. To do so the call
+ * copies that state (device to device, on `stream`) before its first launch; a run of one
+ * iteration copies only the camera part, because it does not overwrite the landmark buffer of x^k.
  * Waits for the stream before returning (the status needs the device's answer). */
 daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, void* stream);
 
@@ -234,15 +240,25 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
 daba_status daba_set_timing(daba_ctx* ctx, int enable);
 daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
 
+/* Limit of the landmark pass's first wait on its tile copies (the bulk copies into shared
+ * memory complete on an mbarrier that the CTA polls against the %globaltimer clock), in
+ * nanoseconds; default 1e9 (1 s). When the limit runs out the CTA records it, waits up to 2 s more
+ * for its copies to land, skips its tile and daba_run returns DABA_ERR_TIMEOUT with the entry
+ * state restored; the context stays usable. 0 gives up before the first poll, which makes every
+ * landmark pass report a timeout (a test of that path). DABA_ERR_ARG if first_wait_ns < 0. */
+daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
+
 /* Number of kernel launches the library issued in the last daba_run. */
 int64_t daba_last_launch_count(const daba_ctx* ctx);
 
-/* Objective F(x) in pixel^2 (Eq. Fobj) of caller-provided device arrays, allocating no
- * device memory. The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc (a framework whose memory pool owns the device, a real-time loop
- * that must not allocate, a plugin limited to the buffers it is handed).
+/* The objective in pixel^2 of caller-provided device arrays (the value daba_objective returns
+ * for a context holding the same cameras, landmarks and observations), allocating no device
+ * memory. The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (a framework whose memory pool owns the device, a real-time loop that must not
+ * allocate, a plugin limited to the buffers it is handed).
  *   cams (M x 9), lms (N x 3), cam_idx, lm_idx (nnz), uv (nnz x 2): as in daba_set_state and
- *   daba_set_observations, but all of them, and `out` (one double), must be device memory.
+ *   daba_set_observations, but all of them, and `out` (one double), must be managed memory or
+ *   device memory of the current device (device memory of another GPU is DABA_ERR_ARG).
  *   loss is a daba_loss value; pixel_scale > 0 is the internal unit in pixels (the result
  *   depends on it only through rounding).
  * Its scratch is one file-scope __device__ array of about 2.4 MB that every GPU which loads
@@ -251,7 +267,7 @@ int64_t daba_last_launch_count(const daba_ctx* ctx);
  * that array's address with cudaGetSymbolAddress, so make the first call before any stream
  * capture. All calls share the array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller. Observation indices out of range, or a
- * landmark at a camera centre (Assumption 2), make *out NaN instead of returning an error
+ * landmark at a camera centre, make *out NaN instead of returning an error
  * (the call does not wait for the GPU). Returns DABA_ERR_CUDA if a launch fails. */
 daba_status daba_objective_noalloc(int32_t M, int32_t N, int64_t nnz, const double* cams, const double* lms,
                                    const int32_t* cam_idx, const int32_t* lm_idx, const double* uv, int32_t loss,

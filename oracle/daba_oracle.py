@@ -19,7 +19,7 @@ and notation of the paper:
               (Eqs. DEalpha, Fainit, Fak, lFak, Eak).
 * Sec. 6   -- Algorithm 1 (DABA) and its unaccelerated ablation DUBA (Sec. 7.2).
 
-Readings where the paper is silent (each is also listed in the design notes):
+Readings where the paper is silent:
 
 * Blocks: every camera and every landmark is its own block, so every
   reprojection pair is inter-block (E' is empty) and E^alpha of a camera is

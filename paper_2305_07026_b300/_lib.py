@@ -16,8 +16,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdaba_b300.so")
 
 DABA_OK, DABA_ERR_ARG, DABA_ERR_INDEX, DABA_ERR_DEGENERATE, DABA_ERR_NONFINITE, DABA_ERR_CUDA, DABA_ERR_OOM, \
-    DABA_ERR_STATE = range(8)
-STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_DEGENERATE", "ERR_NONFINITE", "ERR_CUDA", "ERR_OOM", "ERR_STATE"]
+    DABA_ERR_STATE, DABA_ERR_TIMEOUT = range(9)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_INDEX", "ERR_DEGENERATE", "ERR_NONFINITE", "ERR_CUDA", "ERR_OOM", "ERR_STATE",
+                "ERR_TIMEOUT"]
 LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
 PREC = {"fp64": 0, "mixed": 1}
 RESTART = {"block": 0, "global": 1}
@@ -56,6 +57,7 @@ _SIGS = {
     "daba_scene_objectives": (_st, [_p, _p, _p]),
     "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
+    "daba_set_wait_limit": (_st, [_p, _i64]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
@@ -247,6 +249,9 @@ class Daba:
     def import_checkpoint(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(daba_import_checkpoint(self._h, buf, len(data)))
+
+    def set_wait_limit(self, first_wait_ns):
+        self._check(daba_set_wait_limit(self._h, int(first_wait_ns)))
 
     def set_timing(self, enable=True):
         self._check(daba_set_timing(self._h, int(bool(enable))))

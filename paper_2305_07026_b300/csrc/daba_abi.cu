@@ -48,6 +48,7 @@ struct daba_ctx {
   double s_k = 1.0;   // Nesterov s^(k)
   int64_t k = 0;      // iteration index
   bool timing = false;
+  long long wait_ns = 1000000000ll;   // landmark pass: limit of the first wait on the tile copies
   double tms[5] = {0, 0, 0, 0, 0};
   int64_t launches = 0;
   // host copies (setup data and boundary state)
@@ -109,6 +110,8 @@ struct daba_ctx {
   // the MM alternatives, the decision and the device Nesterov scalar
   void *g_cam = nullptr, *g_tile = nullptr, *cam_alt = nullptr, *lm_alt = nullptr, *g_fire = nullptr,
        *s_dev = nullptr;
+  // the entry state of daba_run, put back when the run fails
+  void* bk = nullptr;
 };
 
 namespace {
@@ -271,6 +274,7 @@ IterParams iter_params(daba_ctx* ctx) {
   P.accelerated = ctx->opt.accelerated;
   P.n_alt = ctx->opt.cam_alternations;
   P.flag = (int*)ctx->d_flag;
+  P.wait_ns = ctx->wait_ns;
   P.restart_global = ctx->opt.restart_mode == DABA_RESTART_GLOBAL ? 1 : 0;
   P.reset_s = ctx->opt.momentum_reset;
   P.g_cam = (double*)ctx->g_cam;
@@ -742,6 +746,71 @@ cudaError_t restore_state(daba_ctx* ctx, const void* slot, int64_t k, double s_k
   return cudaMemcpyAsync(ctx->d_first, b + L.first, sizeof(int), cudaMemcpyDeviceToDevice, st);
 }
 
+// The entry state of daba_run: everything an iteration changes and a later call reads. It is
+// copied (device to device, on the run's stream) before the first launch and put back when the
+// run fails, so that a failing daba_run leaves the iterate and the restart metrics unchanged.
+// The landmark records of x^k live in the buffer of k's parity, which a run of one iteration
+// does not write: that run keeps no copy of them.
+struct BackupLayout {
+  size_t x, dx, S, E, F, Fb, crs, lm, lo, lrs, lF, lFb, first, bytes;
+};
+BackupLayout backup_layout(const daba_ctx* c) {
+  BackupLayout L;
+  const size_t M = c->M, N = c->N;
+  size_t o = 0;
+  auto take = [&](size_t& f, size_t b) {
+    f = o;
+    o = align256(o + b);
+  };
+  take(L.x, M * CSTRIDE * 8);
+  take(L.dx, M * CSTRIDE * 8);
+  take(L.S, M * 8);
+  take(L.E, M * 8);
+  take(L.F, M * 8);
+  take(L.Fb, M * 8);
+  take(L.crs, M);
+  take(L.lm, N * LREC * real_sz(c));
+  take(L.lo, N * 16);
+  take(L.lrs, N);
+  take(L.lF, is_mixed(c) ? 0 : N * 8);
+  take(L.lFb, is_mixed(c) ? 0 : N * 8);
+  take(L.first, 16);
+  L.bytes = o;
+  return L;
+}
+
+// copies between the live buffers and the backup (to_backup: live -> backup); lm_too: the
+// landmark records and their low parts of iteration k as well
+cudaError_t backup_copy(daba_ctx* ctx, bool to_backup, int64_t k, bool lm_too, cudaStream_t st) {
+  const BackupLayout L = backup_layout(ctx);
+  char* b = (char*)ctx->bk;
+  const size_t M = ctx->M, N = ctx->N;
+  struct Item {
+    void* live;
+    size_t off, bytes;
+  };
+  std::vector<Item> items = {{ctx->cam_x, L.x, M * CSTRIDE * 8}, {ctx->cam_dx, L.dx, M * CSTRIDE * 8},
+                             {ctx->cam_S, L.S, M * 8},          {ctx->cam_E, L.E, M * 8},
+                             {ctx->cam_F, L.F, M * 8},          {ctx->cam_Fb, L.Fb, M * 8},
+                             {ctx->cam_rs, L.crs, M},           {ctx->lm_rs, L.lrs, N},
+                             {ctx->d_first, L.first, sizeof(int)}};
+  if (!is_mixed(ctx)) {
+    items.push_back({ctx->lm_Fd, L.lF, N * 8});
+    items.push_back({ctx->lm_Fbd, L.lFb, N * 8});
+  }
+  if (lm_too) {
+    items.push_back({lmrec_at(ctx, k), L.lm, N * LREC * real_sz(ctx)});
+    items.push_back({lmlo_at(ctx, k), L.lo, N * 16});
+  }
+  for (const Item& it : items) {
+    void* dst = to_backup ? (void*)(b + it.off) : it.live;
+    const void* src = to_backup ? (const void*)it.live : (const void*)(b + it.off);
+    cudaError_t e = cudaMemcpyAsync(dst, src, it.bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // n iterations from the current state with direct launches (as daba_run without its
 // synchronisation and objective trace)
 cudaError_t advance(daba_ctx* ctx, cudaStream_t st, int n) {
@@ -825,6 +894,8 @@ cudaError_t adjoint_iter_by_loss(daba_ctx* ctx, cudaStream_t st, int64_t k, doub
     default: return adjoint_iter<LOSS_WELSCH>(ctx, st, k, gamma, slot, itslot, a1, a0, am);
   }
 }
+
+daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, cudaStream_t st);
 
 }  // namespace
 
@@ -973,6 +1044,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   }
   AL(d_lperm, (size_t)N * 4);
   AL(d_scene_f, (size_t)M * 8);
+  AL(bk, backup_layout(ctx).bytes);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -1248,6 +1320,31 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   daba_status s;
   if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
   if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  // keep the entry state; a failed run puts it back (a run of one iteration leaves the landmark
+  // buffer of x^k untouched, so only longer runs copy the landmarks)
+  const int64_t k0 = ctx->k;
+  const double s0 = ctx->s_k;
+  const bool lm_too = iters > 1;
+  CK(backup_copy(ctx, true, k0, lm_too, st));
+  s = run_iterations(ctx, iters, obj_trace, restarts, st);
+  if (s != DABA_OK) {
+    const std::string why = ctx->err;
+    ctx->k = k0;
+    ctx->s_k = s0;
+    cudaError_t e = backup_copy(ctx, false, k0, lm_too, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      return fail(ctx, s, "%s (restoring the entry state also failed: %s)", why.c_str(), cudaGetErrorString(e));
+    ctx->err = why;
+  }
+  return s;
+}
+
+}  // extern "C"
+
+namespace {
+daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, cudaStream_t st) {
+  daba_status s;
   ctx->launches = 0;
   for (double& t : ctx->tms) t = 0.0;
   std::vector<double> trace((size_t)iters + 1);
@@ -1337,12 +1434,15 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (flag & 2) return fail(ctx, DABA_ERR_CUDA, "a landmark-pass copy did not complete (bounded wait ran out)");
+  if (flag & 2) return fail(ctx, DABA_ERR_TIMEOUT, "a landmark-pass copy did not complete in time (bounded wait ran out)");
   if (flag || !std::isfinite(trace[iters])) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
   if (obj_trace && (s = deliver(ctx, obj_trace, trace.data(), ((size_t)iters + 1) * 8, st)) != DABA_OK) return s;
   if (restarts && iters > 0 && (s = deliver(ctx, restarts, rs.data(), (size_t)iters * 4, st)) != DABA_OK) return s;
   return DABA_OK;
 }
+}  // namespace
+
+extern "C" {
 
 daba_status daba_objective(daba_ctx* ctx, double* out, void* stream) {
   if (!ctx || !out) return ctx ? fail(ctx, DABA_ERR_ARG, "null output") : DABA_ERR_ARG;
@@ -1587,7 +1687,7 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (flag & 2) return fail(ctx, DABA_ERR_CUDA, "a landmark-pass copy did not complete (bounded wait ran out)");
+  if (flag & 2) return fail(ctx, DABA_ERR_TIMEOUT, "a landmark-pass copy did not complete in time (bounded wait ran out)");
   if (flag) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
   return DABA_OK;
 }
@@ -1777,6 +1877,16 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
   ctx->state_set = true;
   // host copies used by the Assumption 2 check: rebuild from the imported iterate
   ctx->checked = true;
+  return DABA_OK;
+}
+
+daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (first_wait_ns < 0) return fail(ctx, DABA_ERR_ARG, "first_wait_ns < 0");
+  if (first_wait_ns != ctx->wait_ns) {
+    ctx->wait_ns = first_wait_ns;
+    drop_graphs(ctx);   // the captured launches hold the old limit
+  }
   return DABA_OK;
 }
 

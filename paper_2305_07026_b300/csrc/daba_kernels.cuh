@@ -67,6 +67,7 @@ struct IterParams {
   int accelerated;
   int n_alt;
   int* flag;           // error bits: 1 non-finite objective, 2 a bounded wait ran out
+  long long wait_ns;   // limit of the landmark pass's first wait on its tile copies (ns)
   // global restart variant (restart_global = 1): one test on the sums of the block metrics.
   // The block kernels take the accelerated update and keep the MM alternative; the reduction
   // decides; the fix-up kernels apply the MM alternative everywhere if the test fired.
@@ -406,7 +407,13 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
 // ranges and of its slice of t_inv into shared memory, completing on an mbarrier; each thread
 // then reduces its landmark's records through t_inv. Reads the landmark state of iteration k
 // and writes that of k+1 to the other buffer.
-constexpr long long LPASS_WAIT_LIMIT = 1ll << 26;   // mbarrier polls before giving up
+// Bounded waits on the tile copies, measured with the %globaltimer nanosecond clock. The first
+// wait lasts at most IterParams::wait_ns (a runtime option, 1 s by default; 0 gives up before
+// the first poll). If it runs out, the CTA sets flag bit 2 (the host returns DABA_ERR_TIMEOUT),
+// waits up to LPASS_DRAIN_NS more so that no copy lands in shared memory after the CTA has
+// exited, and skips its tile. Both waits also stop after LPASS_MAX_POLLS polls.
+constexpr long long LPASS_DRAIN_NS = 2000000000ll;
+constexpr long long LPASS_MAX_POLLS = 1ll << 30;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
@@ -425,6 +432,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0u;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// polls the mbarrier phase until it completes (true) or limit_ns have passed (false)
+__device__ __forceinline__ bool mbar_wait_for(unsigned long long* bar, unsigned parity, long long limit_ns) {
+  if (limit_ns <= 0) return false;
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long w = 0; w < LPASS_MAX_POLLS; ++w) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((long long)(globaltimer_ns() - t0) >= limit_ns) return false;
+  }
+  return false;
 }
 // 1D bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -528,11 +550,9 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     s1 = lm_ptr[lb + jl + 1] - ob;
   }
   __syncthreads();   // the mbarrier is initialised
-  bool done = false;
-  for (long long w = 0; w < LPASS_WAIT_LIMIT && !done; ++w) done = mbar_try_wait(bar, 0u);
-  if (!done) {   // copies did not complete: report, wait (bounded) once more, give up the tile
+  if (!mbar_wait_for(bar, 0u, P.wait_ns)) {   // copies not complete in time: report, let them land, skip the tile
     atomicOr(P.flag, 2);
-    for (long long w = 0; w < LPASS_WAIT_LIMIT && !done; ++w) done = mbar_try_wait(bar, 0u);
+    mbar_wait_for(bar, 0u, LPASS_DRAIN_NS);
     return;
   }
 

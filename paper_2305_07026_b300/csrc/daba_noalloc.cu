@@ -53,13 +53,15 @@ daba_status scratch_for_current_device(double** out) {
   return DABA_OK;
 }
 
-bool on_device(const void* p) {
+// true for managed memory and for device memory of GPU `dev` (memory of another GPU is
+// rejected: the kernels would reach it without peer access)
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 // boundary camera (axis-angle, centre, f, k1, k2) -> internal (R, t, d) in units of s pixels
@@ -155,8 +157,13 @@ extern "C" daba_status daba_objective_noalloc(int32_t M, int32_t N, int64_t nnz,
   if (loss < 0 || loss > 3 || !(pixel_scale > 0) || (loss != DABA_LOSS_TRIVIAL && !(loss_scale_px > 0)))
     return DABA_ERR_ARG;
   if (!cams || !lms || !cam_idx || !lm_idx || !uv || !out) return DABA_ERR_ARG;
-  if (!on_device(cams) || !on_device(lms) || !on_device(cam_idx) || !on_device(lm_idx) || !on_device(uv) ||
-      !on_device(out))
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return DABA_ERR_CUDA;
+  }
+  if (!on_device(cams, dev) || !on_device(lms, dev) || !on_device(cam_idx, dev) || !on_device(lm_idx, dev) ||
+      !on_device(uv, dev) || !on_device(out, dev))
     return DABA_ERR_ARG;
   double* scratch = nullptr;
   daba_status s = scratch_for_current_device(&scratch);

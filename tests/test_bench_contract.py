@@ -5,6 +5,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -31,12 +32,33 @@ def test_reference_arm_line(workload, extra):
     assert cb["host"]["nproc"] >= 1 and cb["host"]["cpu_model"]
     assert e2e == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cfg = line["config"]
-    assert {"workload", "M", "N", "nnz", "prec", "parallelism"} <= set(cfg)
+    assert {"workload", "M", "N", "nnz", "parallelism", "l2"} <= set(cfg)
     if workload == "circle":
         assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
-        assert line["ms_per_step"] == pytest.approx(1e3 * cfg["nnz"] / line["value"], rel=1e-9)
+        # the step is one oracle iteration over the sample: its measured time, and beside it the
+        # whole workload's step at the same rate, labelled as extrapolated
+        assert line["ms_per_step_whole_workload_extrapolated"] == pytest.approx(1e3 * cfg["nnz"] / line["value"],
+                                                                               rel=1e-9)
+        assert line["ms_per_step"] * line["steps"] < 1e3 * 120
+        assert cfg == bench.tourism_config(_circle(), 1)
     else:
         assert line["unit"] == "scenes/s" and cfg["workload"].startswith("batch: 3 circle scenes")
+
+
+def _circle():
+    from paper_2305_07026_b300 import scenes
+    return scenes.make_scene("circle")
+
+
+def test_oracle_on_all_cores():
+    """The all-cores leg: spawned processes, each on a disjoint camera block of the workload."""
+    import bench
+    sc = _circle()
+    blocks = bench.camera_blocks(sc, 3, sc.nnz // 4)
+    seen = np.concatenate(blocks)
+    assert len(seen) == len(np.unique(seen)) and len(blocks) == 3
+    out = bench.cpu_oracle_all_cores(sc, 0.02, 2, n_steps=1)
+    assert out["kind"] == "oracle" and out["cores"] == 2 and out["value"] > 0 and out["sample"]
 
 
 def test_gpu_arm_fails_without_a_gpu():
