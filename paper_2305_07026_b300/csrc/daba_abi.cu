@@ -324,22 +324,27 @@ cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
 }
 
 // landmark pass: small tiles, then the one-landmark tiles of long tracks
+// landmark pass: small tiles, then the one-landmark tiles of long tracks
 template <class Real, class Real2, bool HAS_LO>
 cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   const IterParams P = iter_params(ctx);
+  LpassOut<Real> O;
+  O.lmrec_out = (V4<Real>*)lmrec_at(ctx, k + 1);
+  O.lm_lo_out = (V4<float>*)lmlo_at(ctx, k + 1);
+  O.lm_rs = (uint8_t*)ctx->lm_rs;
+  O.lm_Fdiag = (double*)ctx->lm_Fd;
+  O.lm_Fbdiag = (double*)ctx->lm_Fbd;
+  O.lm_alt = (V4<Real>*)ctx->lm_alt;
+  O.lm_sums = (double*)ctx->lm_sums_out;
   const int caps[2] = {ctx->opt.tile_obs, BIG_TILE_OBS};
-  auto kern = k_lpass<Real, Real2, HAS_LO>;
   int t0 = 0;
   for (int c = 0; c < 2; ++c) {
     const int nt = ctx->tile_class_end[c] - t0;
     if (nt > 0) {
-      const size_t smem = lpass_smem_bytes<Real>(caps[c]);
-      kern<<<nt, LPASS_THREADS, smem, st>>>(
-          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
-          (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k),
-          (V4<Real>*)lmrec_at(ctx, k + 1), (V4<float>*)lmlo_at(ctx, k + 1), P, (int*)ctx->tile_rs,
-          (uint8_t*)ctx->lm_rs, (double*)ctx->lm_Fd, (double*)ctx->lm_Fbd, (V4<Real>*)ctx->lm_alt,
-          (double*)ctx->lm_sums_out);
+      k_lpass<Real, Real2, HAS_LO><<<nt, LPASS_THREADS, lpass_smem_bytes<Real>(caps[c]), st>>>(
+          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv,
+          (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b, (const typename RecC<Real>::type*)ctx->rec_c,
+          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), P, (int*)ctx->tile_rs, O);
       ctx->launches++;
     }
     t0 = ctx->tile_class_end[c];

@@ -492,15 +492,162 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
   hi = h2;
 }
 
+// Outputs of the landmark pass (one set per launch).
+template <class Real>
+struct LpassOut {
+  V4<Real>* lmrec_out;
+  V4<float>* lm_lo_out;
+  uint8_t* lm_rs;
+  double* lm_Fdiag;
+  double* lm_Fbdiag;
+  V4<Real>* lm_alt;
+  double* lm_sums;
+};
+
+// One landmark of the landmark pass: sums its records (slots s0 .. s1 of the tile, through the
+// slot map) and runs Eqs. DEalpha, Fak, lFak in slack form, the accelerated update, the restart
+// test and the MM re-solve, then writes the landmark's state of iteration k+1. A, B, lo0: its
+// state of iteration k. Returns whether it restarted (counted for accelerated runs only); gsum
+// receives its term of the global restart test.
+template <class Real, bool HAS_LO>
+__device__ __forceinline__ int lpass_landmark(const V4<Real>* __restrict__ sca, const V4<Real>* __restrict__ scb,
+                                              const typename RecC<Real>::type* __restrict__ cc,
+                                              const uint16_t* __restrict__ inv, int s0, int s1, const V4<Real>& A,
+                                              const V4<Real>& B, const V4<float>& lo0, size_t g, Real gamma, int first,
+                                              const IterParams& P, const LpassOut<Real>& O, double& gsum) {
+  using RC = typename RecC<Real>::type;
+  const bool global = P.accelerated && P.restart_global;
+  const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
+  Real st[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) st[k] = Real(0);
+  for (int s = s0; s < s1; ++s) {
+    const int q = inv[s];
+    const V4<Real> a = sca[q], b = scb[q];
+    const RC c = cc[q];
+    st[0] += a.x;
+    st[1] += a.y;
+    st[2] += a.z;
+    st[3] += a.w;
+    st[4] += b.x;
+    st[5] += b.y;
+    st[6] += b.z;
+    st[7] += b.w;
+    st[8] += RecC<Real>::F(c);
+    st[9] += RecC<Real>::gap(c);
+  }
+  const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
+  // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
+  //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
+  const Real dE = -hx * (dl0 * dl0 + dl1 * dl1 + dl2 * dl2) + Real(0.5) * st[9];
+  const Real S = first ? Real(0) : B.z;
+  const Real thr = eta1 * (S - dE);
+  // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), as a step from l^k
+  const Real ib = fdiv(Real(1), st[0] + hx);
+  const Real sa0 = gamma * dl0 - st[1] * ib, sa1 = gamma * dl1 - st[2] * ib, sa2 = gamma * dl2 - st[3] * ib;
+  // E^alpha(l | x^k) - E^alpha(l^k | x^k) = (a + xi/2)|dl|^2 + 2 dl . b
+  const Real ak = st[4] + hx;
+  Real step0 = sa0, step1 = sa1, step2 = sa2;
+  Real dEn = ak * (sa0 * sa0 + sa1 * sa1 + sa2 * sa2) + Real(2) * (sa0 * st[5] + sa1 * st[6] + sa2 * st[7]);
+  const bool rs = P.accelerated ? (!global && dEn > thr) : true;
+  if (rs || global) {   // adaptive restart: MM update (Eq. update_mm) from l^k
+    const Real ik = fdiv(Real(1), ak);
+    const Real m0 = -st[5] * ik, m1 = -st[6] * ik, m2 = -st[7] * ik;
+    const Real dEm = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
+    if (rs) {
+      step0 = m0;
+      step1 = m1;
+      step2 = m2;
+      dEn = dEm;
+    } else {   // global variant: keep the MM alternative and this block's term of the test
+      V4<Real> a0, a1;
+      a0.x = m0, a0.y = m1, a0.z = m2, a0.w = thr - dEm;
+      a1.x = a1.y = a1.z = a1.w = Real(0);
+      if (!HAS_LO) {
+        const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
+        a1.x = Real(E + double(dE) + double(dEm));
+      }
+      O.lm_alt[2 * g] = a0;
+      O.lm_alt[2 * g + 1] = a1;
+      gsum = double(dEn) - double(thr);
+    }
+  }
+  V4<Real> nA, nB;
+  if (HAS_LO) {
+    float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
+    float o0 = lo0.x, o1 = lo0.y, o2 = lo0.z;
+    df_add(h0, o0, float(step0));
+    df_add(h1, o1, float(step1));
+    df_add(h2, o2, float(step2));
+    nA.x = Real(h0);
+    nA.y = Real(h1);
+    nA.z = Real(h2);
+    V4<float> nlo;
+    nlo.x = o0;
+    nlo.y = o1;
+    nlo.z = o2;
+    nlo.w = 0.f;
+    O.lm_lo_out[g] = nlo;
+  } else {
+    nA.x = A.x + step0;
+    nA.y = A.y + step1;
+    nA.z = A.z + step2;
+  }
+  nA.w = step0;
+  nB.x = step1;
+  nB.y = step2;
+  nB.z = thr - dEn;
+  nB.w = B.w;
+  if (!HAS_LO) {   // FP64 path: E^(k) and the diagnostics F^(k), Fbar^(k)
+    const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
+    const double F = E + double(dE);
+    O.lm_Fdiag[g] = F;
+    O.lm_Fbdiag[g] = F + double(thr);
+    nB.w = Real(F + double(dEn));
+    if (O.lm_sums) {   // the reverse mode keeps (a, b) at x̄ and at x^k of every landmark
+#pragma unroll
+      for (int k = 0; k < 8; ++k) O.lm_sums[g * 8 + k] = double(st[k]);
+    }
+  }
+  O.lmrec_out[2 * g] = nA;
+  O.lmrec_out[2 * g + 1] = nB;
+  O.lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
+  return (rs && P.accelerated) ? 1 : 0;
+}
+
+// restart count of a tile and, for the global variant, its sum of the test terms (fixed order)
+__device__ __forceinline__ void lpass_tile_sums(int nrs, double gsum, bool global, int tile, int* tile_rs,
+                                                double* g_tile) {
+  __shared__ int redi[LPASS_THREADS / 32];
+  __shared__ double redg[LPASS_THREADS / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
+  if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = nrs;
+  if (global) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
+    if ((threadIdx.x & 31) == 0) redg[threadIdx.x >> 5] = gsum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int w = 0; w < LPASS_THREADS / 32; ++w) n += redi[w];
+    tile_rs[tile] = n;
+    if (global) {
+      double t = 0.0;
+      for (int w = 0; w < LPASS_THREADS / 32; ++w) t += redg[w];
+      g_tile[tile] = t;
+    }
+  }
+}
+
 template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
     k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
             const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
             const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
-            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, V4<Real>* __restrict__ lmrec_out,
-            V4<float>* __restrict__ lm_lo_out, IterParams P, int* __restrict__ tile_rs, uint8_t* __restrict__ lm_rs,
-            double* __restrict__ lm_Fdiag, double* __restrict__ lm_Fbdiag, V4<Real>* __restrict__ lm_alt,
-            double* __restrict__ lm_sums) {
+            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, IterParams P,
+            int* __restrict__ tile_rs, LpassOut<Real> O) {
   using RC = typename RecC<Real>::type;
   using SM = LpassSmem<Real>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -555,133 +702,12 @@ __global__ void __launch_bounds__(LPASS_THREADS)
     mbar_wait_for(bar, 0u, LPASS_DRAIN_NS);
     return;
   }
-
   int nrs = 0;
   double gsum = 0.0;   // global restart variant: this thread's E(k+1) - Fbar(k)
-  const bool global = P.accelerated && P.restart_global;
-  const Real hx = hxi_of<Real>(P), eta1 = eta1_of<Real>(P);
-  if (jl < nl) {
-    Real st[10];
-#pragma unroll
-    for (int k = 0; k < 10; ++k) st[k] = Real(0);
-    const uint16_t* inv = sinv + (ob - is);
-    const RC* cc = scc + (ob - cs);
-    for (int s = s0; s < s1; ++s) {
-      const int q = inv[s];
-      const V4<Real> a = sca[q], b = scb[q];
-      const RC c = cc[q];
-      st[0] += a.x;
-      st[1] += a.y;
-      st[2] += a.z;
-      st[3] += a.w;
-      st[4] += b.x;
-      st[5] += b.y;
-      st[6] += b.z;
-      st[7] += b.w;
-      st[8] += RecC<Real>::F(c);
-      st[9] += RecC<Real>::gap(c);
-    }
-    const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
-    // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
-    //   Fbar^(k) - F^(k) = (1 - eta)(S - dE), and E^(k+1) > Fbar^(k)  <=>  dE_next > (1 - eta)(S - dE)
-    const Real dE = -hx * (dl0 * dl0 + dl1 * dl1 + dl2 * dl2) + Real(0.5) * st[9];
-    const Real S = first ? Real(0) : B.z;
-    const Real thr = eta1 * (S - dE);
-    // accelerated update (Eq. update_amm): l = lbar - bbar / (abar + xi/2), as a step from l^k
-    const Real ib = fdiv(Real(1), st[0] + hx);
-    const Real sa0 = gamma * dl0 - st[1] * ib, sa1 = gamma * dl1 - st[2] * ib, sa2 = gamma * dl2 - st[3] * ib;
-    // E^alpha(l | x^k) - E^alpha(l^k | x^k) = (a + xi/2)|dl|^2 + 2 dl . b
-    const Real ak = st[4] + hx;
-    Real step0 = sa0, step1 = sa1, step2 = sa2;
-    Real dEn = ak * (sa0 * sa0 + sa1 * sa1 + sa2 * sa2) + Real(2) * (sa0 * st[5] + sa1 * st[6] + sa2 * st[7]);
-    const bool rs = P.accelerated ? (!global && dEn > thr) : true;
-    if (rs || global) {   // adaptive restart: MM update (Eq. update_mm) from l^k
-      const Real ik = fdiv(Real(1), ak);
-      const Real m0 = -st[5] * ik, m1 = -st[6] * ik, m2 = -st[7] * ik;
-      const Real dEm = -(st[5] * st[5] + st[6] * st[6] + st[7] * st[7]) * ik;
-      if (rs) {
-        step0 = m0;
-        step1 = m1;
-        step2 = m2;
-        dEn = dEm;
-      } else {   // global variant: keep the MM alternative and this block's term of the test
-        V4<Real> a0, a1;
-        a0.x = m0, a0.y = m1, a0.z = m2, a0.w = thr - dEm;
-        a1.x = a1.y = a1.z = a1.w = Real(0);
-        if (!HAS_LO) {
-          const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
-          a1.x = Real(E + double(dE) + double(dEm));
-        }
-        lm_alt[2 * g] = a0;
-        lm_alt[2 * g + 1] = a1;
-        gsum = double(dEn) - double(thr);
-      }
-    }
-    nrs += (rs && P.accelerated) ? 1 : 0;
-    V4<Real> nA, nB;
-    if (HAS_LO) {
-      float h0 = float(A.x), h1 = float(A.y), h2 = float(A.z);
-      float o0 = lo0.x, o1 = lo0.y, o2 = lo0.z;
-      df_add(h0, o0, float(step0));
-      df_add(h1, o1, float(step1));
-      df_add(h2, o2, float(step2));
-      nA.x = Real(h0);
-      nA.y = Real(h1);
-      nA.z = Real(h2);
-      V4<float> nlo;
-      nlo.x = o0;
-      nlo.y = o1;
-      nlo.z = o2;
-      nlo.w = 0.f;
-      lm_lo_out[g] = nlo;
-    } else {
-      nA.x = A.x + step0;
-      nA.y = A.y + step1;
-      nA.z = A.z + step2;
-    }
-    nA.w = step0;
-    nB.x = step1;
-    nB.y = step2;
-    nB.z = thr - dEn;
-    nB.w = B.w;
-    if (!HAS_LO) {   // FP64 path: E^(k) and the diagnostics F^(k), Fbar^(k)
-      const double E = first ? double(Real(0.5) * st[8]) : double(B.w);
-      const double F = E + double(dE);
-      lm_Fdiag[g] = F;
-      lm_Fbdiag[g] = F + double(thr);
-      nB.w = Real(F + double(dEn));
-      if (lm_sums) {   // the reverse mode keeps (a, b) at x̄ and at x^k of every landmark
-#pragma unroll
-        for (int k = 0; k < 8; ++k) lm_sums[g * 8 + k] = double(st[k]);
-      }
-    }
-    lmrec_out[2 * g] = nA;
-    lmrec_out[2 * g + 1] = nB;
-    lm_rs[g] = (rs && P.accelerated) ? 1 : 0;
-  }
-  // restart count of the tile
-  __shared__ int redi[LPASS_THREADS / 32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) nrs += __shfl_xor_sync(0xffffffffu, nrs, off);
-  if ((threadIdx.x & 31) == 0) redi[threadIdx.x >> 5] = nrs;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int n = 0;
-    for (int w = 0; w < LPASS_THREADS / 32; ++w) n += redi[w];
-    tile_rs[tile] = n;
-  }
-  if (global) {   // the tile's sum for the global test (fixed order)
-    __shared__ double redg[LPASS_THREADS / 32];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
-    if ((threadIdx.x & 31) == 0) redg[threadIdx.x >> 5] = gsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < LPASS_THREADS / 32; ++w) t += redg[w];
-      P.g_tile[tile] = t;
-    }
-  }
+  if (jl < nl)
+    nrs = lpass_landmark<Real, HAS_LO>(sca, scb, scc + (ob - cs), sinv + (ob - is), s0, s1, A, B, lo0, g, gamma, first,
+                                       P, O, gsum);
+  lpass_tile_sums(nrs, gsum, P.accelerated && P.restart_global, tile, tile_rs, P.g_tile);
 }
 
 // ---------------------------------------------------------------------------

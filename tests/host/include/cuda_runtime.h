@@ -16,6 +16,7 @@ struct float4 { float x, y, z, w; };
 struct int4 { int x, y, z, w; };
 inline double2 make_double2(double a, double b) { return {a, b}; }
 inline float2 make_float2(float a, float b) { return {a, b}; }
+inline int4 make_int4(int a, int b, int c, int d) { return {a, b, c, d}; }
 struct host_dim3 { unsigned x = 0, y = 0, z = 0; };
 static host_dim3 threadIdx, blockIdx, blockDim, gridDim;
 inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }

@@ -1,0 +1,283 @@
+"""The CUDA path against the FP64 oracle on the workloads at their specified sizes and lengths.
+
+* circle (20 cameras, 2,000 landmarks, Huber 1 px), 200 iterations: the FP64 GPU trace against
+  the oracle's (1e-10 for iterations 0-20, then as far as no restart decision sits at a
+  near-tie), the final objective and parameters, and the MIXED path reaching the oracle's
+  200-iteration objective within 1e-5.
+* street (1,000 cameras, 200k landmarks, ~1M observations, Cauchy 2 px), 300 iterations, and
+  the same generator at scale 0.2: against the oracle's results stored by
+  tests/golden/make_street_golden.py (the oracle takes about 40 minutes at full size).
+* a batch of independent scenes run as one problem: per-scene iterates after 12 iterations
+  against the oracle run on each scene alone.
+* the differentiation workload (street at scale 0.2): the reverse-mode product of 50 FP64
+  iterations against central differences (h = 1e-6) of the library's own 50-iteration map on 64
+  random directions (where the map is differentiable: see the test).
+
+A restart decision is a comparison of two FP64 numbers; where they differ by about 1e-12
+relative, two correct evaluation orders (the oracle's numpy sums, the GPU's fixed-order warp
+sums) can decide differently, and from there the two trajectories are different correct runs
+of Algorithm 1. The tests therefore hold the strict tolerances up to the first such near-tie
+(the oracle records the smallest margin of every iteration) and compare objectives only after it.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import daba_oracle as O
+from tests.conftest import cached_scene
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+NEAR_TIE = 1e-9   # restart-test margin (relative to |F^alpha|) below which either decision is correct
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2305_07026_b300 import build
+    build.build()
+
+
+def _ctx(sc, prec, **kw):
+    from paper_2305_07026_b300 import _lib as L
+    opts = dict(loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec)
+    opts.update(kw)
+    d = L.Daba(sc.M, sc.N, sc.nnz, **opts)
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    d.set_state(sc.cams, sc.lms)
+    return d
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+def _oracle_run(sc, iters, keep_at=()):
+    """The oracle's trace, restart counts, smallest restart margins and states at keep_at."""
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    st = O.init_state(prob, R, t, d, l)
+    s2 = prob.s_norm ** 2
+    trace, rs, margin, kept = [], [], [], {}
+    for k in range(iters):
+        st, info = O.step(prob, st)
+        trace.append(info.F * s2)
+        rs.append(int(info.restart_cam.sum() + info.restart_lm.sum()))
+        mc = np.abs(info.Etest_cam - info.Fbar_cam) / np.maximum(np.abs(info.F_cam), 1e-300)
+        ml = np.abs(info.Etest_lm - info.Fbar_lm) / np.maximum(np.abs(info.F_lm), 1e-300)
+        margin.append(float(min(mc.min(), ml.min())))
+        if k + 1 in keep_at:
+            kept[k + 1] = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+    trace.append(O.objective(prob.loss, prob.c, st.R, st.t, st.d, st.l, prob.cam_idx, prob.lm_idx, prob.u) * s2)
+    kept[iters] = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+    return np.array(trace), np.array(rs), np.array(margin), kept
+
+
+def _check_fp64_trace(tr, rs, o_tr, o_rs, o_margin, final_obj_rel):
+    """The GPU's and the oracle's runs take the same restart decisions (compared as the number
+    of restarted blocks per iteration) until the first iteration where they differ, which must
+    be one whose smallest restart margin is a near-tie; up to there the objectives agree to
+    1e-10 (first 20 iterations) and 1e-8; afterwards only the final objectives are compared.
+    Returns the index of the first differing iteration (len(rs) if none)."""
+    diff = np.flatnonzero(np.asarray(rs) != np.asarray(o_rs))
+    div = int(diff[0]) if diff.size else len(rs)
+    if div < len(rs):
+        assert o_margin[div] < NEAR_TIE, (div, o_margin[div], rs[div], o_rs[div])
+    n = min(div + 1, 21)
+    np.testing.assert_allclose(tr[:n], o_tr[:n], rtol=1e-10)
+    np.testing.assert_allclose(tr[:div + 1], o_tr[:div + 1], rtol=1e-8)
+    assert _rel(tr[-1], o_tr[-1]) <= final_obj_rel, (tr[-1], o_tr[-1], div)
+    return div
+
+
+# ----------------------------------------------------------------------------
+# circle, 200 iterations
+# ----------------------------------------------------------------------------
+
+def test_circle_200_iterations_against_oracle():
+    sc = cached_scene("circle")
+    K = 200
+    o_tr, o_rs, o_margin, kept = _oracle_run(sc, K)
+    d = _ctx(sc, "fp64")
+    tr, rs = np.zeros(K + 1), np.zeros(K, np.int32)
+    d.run(K, tr, rs)
+    cams, lms = d.get_state()
+    d.close()
+    div = _check_fp64_trace(tr, rs, o_tr, o_rs, o_margin, 1e-8)
+    print(f"circle: decisions differ first at iteration {div} (near-ties below {NEAR_TIE}: "
+          f"{int(np.sum(o_margin < NEAR_TIE))}); final objective rel {_rel(tr[-1], o_tr[-1]):.2e}")
+    if div == K:   # the same decisions throughout: the iterates agree
+        np.testing.assert_allclose(cams, kept[K][0], rtol=1e-7, atol=1e-7)
+        np.testing.assert_allclose(lms, kept[K][1], rtol=1e-7, atol=1e-7)
+    dm = _ctx(sc, "mixed")
+    trm = np.zeros(K + 1)
+    dm.run(K, trm)
+    dm.close()
+    assert trm.min() <= o_tr[-1] * (1 + 1e-5), (trm[-3:], o_tr[-1])
+    assert trm[-1] == pytest.approx(o_tr[-1], rel=1e-3)
+
+
+# ----------------------------------------------------------------------------
+# street, 300 iterations, against the stored oracle results
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scale", [0.2, 1.0])
+def test_street_300_iterations_against_oracle(scale):
+    path = os.path.join(GOLDEN, f"street_oracle_{scale:g}.json")
+    g = json.load(open(path))
+    sc = cached_scene("street", scale=scale)
+    assert (sc.M, sc.N, sc.nnz) == (g["workload"]["M"], g["workload"]["N"], g["workload"]["nnz"])
+    K = g["iters"]
+    o_tr = np.array(g["trace_px2"])
+    cs, ls = np.array(g["sample_cams"]), np.array(g["sample_lms"])
+    d = _ctx(sc, "fp64")
+    tr1, rs1 = np.zeros(21), np.zeros(20, np.int32)
+    d.run(20, tr1, rs1)
+    c20, l20 = d.get_state()
+    tr2, rs2 = np.zeros(K - 19), np.zeros(K - 20, np.int32)
+    d.run(K - 20, tr2, rs2)
+    cK, lK = d.get_state()
+    d.close()
+    tr = np.concatenate([tr1[:20], tr2])
+    rs = np.concatenate([rs1, rs2])
+    o_margin = np.array(g["min_restart_margin"])
+    div = _check_fp64_trace(tr, rs, o_tr, np.array(g["restarts"]), o_margin, 1e-6)
+    print(f"street {scale}: decisions differ first at iteration {div} (near-ties below {NEAR_TIE}: "
+          f"{int(np.sum(o_margin < NEAR_TIE))}); final objective rel {_rel(tr[-1], o_tr[-1]):.2e}")
+    if div >= 20:   # the same decisions for 20 iterations: the iterates agree
+        np.testing.assert_allclose(c20[cs], np.array(g["at_20"]["cams"]), rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(l20[ls], np.array(g["at_20"]["lms"]), rtol=1e-8, atol=1e-8)
+    if div == K:
+        np.testing.assert_allclose(cK[cs], np.array(g["final"]["cams"]), rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(lK[ls], np.array(g["final"]["lms"]), rtol=1e-6, atol=1e-6)
+    dm = _ctx(sc, "mixed")
+    trm = np.zeros(K + 1)
+    dm.run(K, trm)
+    dm.close()
+    assert trm.min() <= o_tr[-1] * (1 + 1e-5), (trm[-3:], o_tr[-1])
+
+
+# ----------------------------------------------------------------------------
+# batch of independent scenes: per-scene iterates against the oracle
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_scenes_against_oracle(prec):
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch, scenes
+    scs = scenes.batch_scenes(48)
+    b = batch.merge(scs)
+    K = 12
+    d = L.Daba(b.M, b.N, b.nnz, loss="huber", loss_scale_px=1.0, prec=prec, pixel_scale=650.0)
+    d.set_observations(b.cam_idx, b.lm_idx, b.uv)
+    d.set_state(b.cams, b.lms)
+    d.set_scenes(b.cam_begin)
+    d.run(K)
+    fK = d.scene_objectives()
+    parts = batch.split(b, *d.get_state())
+    d.close()
+    sizes = np.array([sc.nnz for sc in scs])
+    rng = np.random.default_rng(3)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes))] + list(rng.choice(len(scs), 3, replace=False))
+    for i in pick:
+        sc = scs[i]
+        res = O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv,
+                     O.Options(loss="huber", loss_scale_px=1.0, pixel_scale=650.0), K)
+        cams_o, lms_o = O.boundary_state(res)
+        dc = np.abs(parts[i][0] - cams_o).max()
+        dl = np.abs(parts[i][1] - lms_o).max()
+        print(f"batch {prec} scene {i} ({sc.M} cams, {sc.nnz} obs): objective rel "
+              f"{_rel(fK[i], res.trace_px2[-1]):.2e}, max |cam diff| {dc:.2e}, max |lm diff| {dl:.2e}")
+        if prec == "fp64":
+            assert fK[i] == pytest.approx(res.trace_px2[-1], rel=1e-10), f"scene {i}"
+            np.testing.assert_allclose(parts[i][0], cams_o, rtol=1e-8, atol=1e-8, err_msg=f"scene {i}")
+            np.testing.assert_allclose(parts[i][1], lms_o, rtol=1e-8, atol=1e-8, err_msg=f"scene {i}")
+        else:   # FP32 per observation: the objective, and the iterate to the FP32 path's accuracy
+            assert fK[i] == pytest.approx(res.trace_px2[-1], rel=1e-4), f"scene {i}"
+            assert dc < 1e-2 and dl < 1e-2, f"scene {i}"
+
+
+# ----------------------------------------------------------------------------
+# differentiation workload: K = 50 reverse mode against central differences
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["duba", "daba_global_restart"])
+def test_unrolled_k50_central_differences(variant):
+    """d<w, x^50>/d(x^0, u) from daba_unrolled_grad against (y(x + h v) - y(x - h v)) / 2h of the
+    library's own 50-iteration FP64 map, h = 1e-6, on 64 random directions in all inputs at once
+    (cameras, landmarks and pixels, each coordinate in its natural unit). The bound applies to
+    the Richardson combination of the central differences at h and h/2 (the map's curvature
+    along camera directions makes the central difference's own O(h^2) error reach 1e-2 on
+    some directions); the central difference's error is printed beside it.
+
+    The map is differentiable only where no restart decision changes and no residual crosses a
+    kink of the loss. The Huber loss's second derivative jumps at |e| = delta, and at this size a
+    perturbation of 1e-6 moves a few of the 150k residuals across it in 50 iterations, so the
+    check uses the street workload's own smooth Cauchy loss (2 px). With one decision per
+    block (Algorithm 1 as printed) this workload has thousands of decisions per iteration and
+    some sit within 1e-12 of a tie in every run, so every perturbation of 1e-6 flips one of
+    them somewhere in 50 iterations and central differences straddle a jump; the per-block
+    reverse mode is therefore checked against the oracle's autograd on smaller scenes
+    (test_gpu_grad.py). Here: the unaccelerated iteration (DUBA, no decisions) and Algorithm 1
+    with the global restart test (one decision per iteration, on the summed block metrics), both
+    through the same adjoint kernels; a direction whose perturbed runs restart in a different
+    iteration is replaced by a new one."""
+    from paper_2305_07026_b300 import _lib as L
+    sc = cached_scene("street", scale=0.2)
+    K, h = 50, 1e-6
+    kw = dict(accelerated=False) if variant == "duba" else dict(restart="global")
+    d = L.Daba(sc.M, sc.N, sc.nnz, loss="cauchy", loss_scale_px=2.0, prec="fp64", **kw)
+    d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    rng = np.random.default_rng(21)
+    wc, wl = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
+    d.set_state(sc.cams, sc.lms)
+    gc, gl, gu = d.unrolled_grad(K, wc, wl)
+
+    def y(c, l, u):
+        d.set_pixels(u)
+        d.set_state(c, l)
+        rs = np.zeros(K, np.int32)
+        d.run(K, None, rs)
+        a, b = d.get_state()
+        return float(np.sum(a * wc) + np.sum(b * wl)), rs
+
+    _, rs0 = y(sc.cams, sc.lms, sc.uv)
+    if variant == "daba_global_restart":
+        assert 0 < np.count_nonzero(rs0) < K   # the decision both fires and holds within the run
+    cscale = np.array([1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 10.0, 1e-2, 1e-3])
+    rows, tried = [], 0
+    while len(rows) < 64 and tried < 96:
+        tried += 1
+        vc = rng.normal(size=sc.cams.shape) * cscale
+        vl = rng.normal(size=sc.lms.shape)
+        vu = rng.normal(size=sc.uv.shape)
+        fd, same = [], True
+        for hh in (h, h / 2):
+            yp, rp = y(sc.cams + hh * vc, sc.lms + hh * vl, sc.uv + hh * vu)
+            ym, rm = y(sc.cams - hh * vc, sc.lms - hh * vl, sc.uv - hh * vu)
+            same = same and np.array_equal(rp, rs0) and np.array_equal(rm, rs0)
+            fd.append((yp - ym) / (2 * hh))
+        if not same:
+            continue
+        an = float(np.sum(gc * vc) + np.sum(gl * vl) + np.sum(gu * vu))
+        # central difference at h, and Richardson's combination of h and h/2, which cancels the
+        # O(h^2) term of the central difference (the unaccelerated map is strongly curved along
+        # camera directions: its error at h = 1e-6 is O(h^2), shrinking 100-fold per 10-fold h)
+        rows.append((an, fd[0], (4.0 * fd[1] - fd[0]) / 3.0))
+    d.close()
+    a = np.array(rows).reshape(-1, 3)
+    rel_c = np.abs(a[:, 0] - a[:, 1]) / np.maximum(np.abs(a[:, 1]), 1e-300)
+    rel_r = np.abs(a[:, 0] - a[:, 2]) / np.maximum(np.abs(a[:, 2]), 1e-300)
+    if rel_c.size:
+        print(f"unrolled K=50 {variant}: {len(rows)} directions of {tried} tried; relative error of the central "
+              f"difference (h = 1e-6) median {np.median(rel_c):.2e} max {rel_c.max():.2e}; of its Richardson "
+              f"extrapolation median {np.median(rel_r):.2e} max {rel_r.max():.2e}; |derivative| median "
+              f"{np.median(np.abs(a[:, 1])):.3e}")
+    assert len(rows) == 64
+    assert np.median(rel_r) < 2e-5 and rel_r.max() < 2e-3

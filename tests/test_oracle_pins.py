@@ -342,6 +342,46 @@ def test_nesterov_scalars():
     assert s == pytest.approx(2001 / 2, rel=5e-3)    # s^k ~ (k + 1)/2 asymptotically
 
 
+def _axis_rot(axis, phi):
+    """Rotation by angle phi about the unit axis (Rodrigues' formula, written out here)."""
+    K = np.array([[0.0, -axis[2], axis[1]], [axis[2], 0.0, -axis[0]], [-axis[1], axis[0], 0.0]])
+    return np.eye(3) + np.sin(phi) * K + (1.0 - np.cos(phi)) * (K @ K)
+
+
+def test_extrapolate_closed_form():
+    """Eq. nesterov_x on a one-parameter subgroup. With R^(k-1) = R^k Exp(-theta a) (unit axis a),
+    R^k + gamma (R^k - R^(k-1)) = R^k A with A = I + gamma (I - Exp(-theta a)), a polynomial in
+    [a]x that fixes a and acts on the plane normal to a as (1 + gamma (1 - cos theta)) I
+    + gamma sin theta J (J the quarter turn): a positive multiple of the rotation by
+    phi = atan2(gamma sin theta, 1 + gamma (1 - cos theta)). Its projection onto SO(3) is
+    therefore R^k Exp(phi a), exactly. t, d and l extrapolate affinely in gamma, and gamma = 0
+    returns x^k."""
+    rng = np.random.default_rng(12)
+    Rk = _rand_rot(rng, 40)
+    axes = rng.normal(size=(40, 3))
+    axes /= np.linalg.norm(axes, axis=1, keepdims=True)
+    theta = rng.uniform(0.0, 2.5, 40)
+    gamma = rng.uniform(0.0, 0.99, 40)
+    Rp = np.stack([Rk[n] @ _axis_rot(axes[n], -theta[n]) for n in range(40)])
+    t, tp = rng.normal(size=(40, 3)), rng.normal(size=(40, 3))
+    d, dp = rng.normal(size=(40, 3)), rng.normal(size=(40, 3))
+    l, lp = rng.normal(size=(40, 3)), rng.normal(size=(40, 3))
+    for n in range(40):
+        g = gamma[n]
+        Rb, tb, db, lb = O.extrapolate(Rk[n:n + 1], t[n:n + 1], d[n:n + 1], l[n:n + 1], Rp[n:n + 1], tp[n:n + 1],
+                                       dp[n:n + 1], lp[n:n + 1], g)
+        phi = np.arctan2(g * np.sin(theta[n]), 1.0 + g * (1.0 - np.cos(theta[n])))
+        np.testing.assert_allclose(Rb[0], Rk[n] @ _axis_rot(axes[n], phi), atol=1e-12)
+        np.testing.assert_allclose(tb[0], (1 + g) * t[n] - g * tp[n], atol=1e-13)
+        np.testing.assert_allclose(db[0], (1 + g) * d[n] - g * dp[n], atol=1e-13)
+        np.testing.assert_allclose(lb[0], (1 + g) * l[n] - g * lp[n], atol=1e-13)
+    Rb, tb, db, lb = O.extrapolate(Rk, t, d, l, Rp, tp, dp, lp, 0.0)
+    np.testing.assert_allclose(Rb, Rk, atol=1e-13)
+    assert np.array_equal(tb, t) and np.array_equal(db, d) and np.array_equal(lb, l)
+    # a wrong sign (x^(k-1) - x^k) would turn the other way: phi has the sign of gamma theta
+    assert np.all(np.arctan2(gamma * np.sin(theta), 1.0 + gamma * (1.0 - np.cos(theta))) >= 0)
+
+
 # ----------------------------------------------------------------------------
 # subproblem solvers
 # ----------------------------------------------------------------------------
