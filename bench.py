@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-scenes", type=int, default=512, help="scenes of the batch workload")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: the default schedule, not tuned")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch leg of the default line")
     return ap.parse_args()
 
 
@@ -224,6 +225,18 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return None
+
+
+def committed_value(name, key):
+    """A number recorded in a committed ncu summary under profiles/ (None if absent)."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", name)):
+            if line.startswith(key + ":"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
 
 
 def committed_traffic(kernel, workload):
@@ -478,6 +491,17 @@ def run_ours(args, rank, world, local):
                                                if gate_ok and reach[0] > 0 else None),
                 "fp64_ms_per_step": fp64_ms_iter, "fp64_value": sc.nnz / (fp64_ms_iter / 1e3),
                 "initial_px2": float(tr64[0])}
+    # the FP64 path against the FP64 pipe: FP64 operations per observation and iteration counted
+    # by ncu (DFMA as 2) over its three iteration kernels, against the FMA rate measured here
+    f64_peak = L.probe_fma_rate("f64")
+    f64_per_obs = committed_value(f"fp64_path_{args.workload}.md", "fp64_flop_per_observation")
+    fp64_roofline = {"bound": "alu", "peak": f64_peak / 1e12, "unit": "TFLOP/s",
+                     "peak_source": "measured FP64 FMA chains (daba_probe_fma_rate)",
+                     "achieved": None, "frac": None}
+    if f64_per_obs is not None:
+        fp64_roofline["achieved"] = f64_per_obs * sc.nnz / (fp64_ms_iter / 1e3) / 1e12
+        fp64_roofline["frac"] = fp64_roofline["achieved"] * 1e12 / f64_peak
+        fp64_roofline["flop_per_observation"] = f64_per_obs
 
     # ---- roofline of the whole iteration (the step: one graph of cpass, lpass | camsolve,
     # finalize) against the measured copy bandwidth, with the method's bytes (each datum the
@@ -538,6 +562,23 @@ def run_ours(args, rank, world, local):
         if not args.no_variants:
             extra["variants"] = variants_leg(L, sc, Ka, trm, stream, sp)
 
+    # the batch workload (512 independent circle-generator scenes, 100 iterations each, the default
+    # schedule) as one problem, against one context per scene
+    batch_line = None
+    if not args.no_batch:
+        from paper_2305_07026_b300 import batch as B, scenes as S
+        scs = S.batch_scenes(args.n_scenes)
+        bb = B.merge(scs)
+        r = batch_leg(L, scs, bb, 100, W, stream, {}, world=world, local=local)
+        batch_line = {"scenes": len(scs), "iterations": 100, "nnz": bb.nnz, "scenes_per_s": r["scenes_per_s"],
+                      "ms_per_batch": r["ms"], "latency_ms_p50_p99": [r["ms"], r["ms"]],
+                      "separate_scenes_per_s": r["separate"]["value"],
+                      "separate_isolated_ms_p50_p99": [r["separate"]["isolated_ms"]["p50"],
+                                                       r["separate"]["isolated_ms"]["p99"]],
+                      "separate_queued_ms_p50_p99": [r["separate"]["queued_ms"]["p50"],
+                                                     r["separate"]["queued_ms"]["p99"]],
+                      "schedule": "default (bench.py --workload batch autotunes)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         _, cpu, _ = cpu_oracle(sc, args.cpu_seconds)
@@ -555,6 +596,8 @@ def run_ours(args, rank, world, local):
     }
     out.update(extra)
     # the accuracy gate last, so that it stays in view at the end of the line
+    out["batch"] = batch_line
+    out["fp64_roofline"] = fp64_roofline
     out["accuracy"] = accuracy
     out["gate"] = "pass: mixed reaches the FP64 path's objective within 1e-5" if gate_ok else \
         "FAIL: mixed does not reach the FP64 path's objective within 1e-5 (value does not count)"
@@ -633,30 +676,14 @@ def variants_leg(L, sc, Kf, trm, stream, sp):
     return variants
 
 
-def run_batch(args, rank, world, local):
-    """Many small independent scenes: one problem with a scene partition (one launch sequence per
-    iteration for all scenes, captured as CUDA graphs) against one context per scene run one
-    after another. Reports scenes/s for ``--steps`` iterations per scene and per-scene latency."""
+def batch_leg(L, scs, b, K, W, stream, sched, clocks=None, world=1, local=0):
+    """The batch as one problem with a scene partition (one graph launch per run for all scenes),
+    K iterations timed with CUDA events, then one context per scene run one after another.
+    Returns a dict of the measurements."""
     import torch
-    from paper_2305_07026_b300 import build
-    build.build()
-    from paper_2305_07026_b300 import _lib as L
-    from paper_2305_07026_b300 import batch, scenes
-    torch.cuda.set_device(local)
-    scs = scenes.batch_scenes(args.n_scenes)
-    b = batch.merge(scs)
-    K, W = args.steps, args.warmup
-    stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     opts = dict(loss="huber", loss_scale_px=1.0, prec="mixed", pixel_scale=650.0)
-    # schedule autotuning (untimed setup): chunk and tile sizes by coordinate descent
-    from paper_2305_07026_b300 import autotune
-    if args.no_autotune:
-        sched, tried = {}, {}
-    else:
-        sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv, opts)
-
     d = L.Daba(b.M, b.N, b.nnz, **opts, **sched)
     d.set_observations(b.cam_idx, b.lm_idx, b.uv, stream=sp)
     d.set_scenes(b.cam_begin)
@@ -664,22 +691,21 @@ def run_batch(args, rank, world, local):
     d.run(max(W, K), stream=sp)   # warm-up of the timed length: its graph is captured here
     d.set_state(b.cams, b.lms, stream=sp)
     f0 = d.scene_objectives(stream=sp)
-    clocks = Clocks()
     torch.cuda.synchronize()
     barrier(world)
-    clocks.start()
-    t_wall0 = clocks.mark()
+    t_wall0 = time.time()
+    if clocks:
+        clocks.start()
+        t_wall0 = clocks.mark()
     e0.record(stream)
     d.run(K, stream=sp)
     e1.record(stream)
     e1.synchronize()
-    t_wall1 = clocks.mark()
-    ck = clocks.stop(local, t_wall0, t_wall1)
+    ck = clocks.stop(local, t_wall0, time.time()) if clocks else None
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     launches = d.last_launch_count()
     fK = d.scene_objectives(stream=sp)
     d.close()
-
     # one context per scene, run one after another (setup outside the timed regions)
     sep_ms = []
     for sc in scs:
@@ -698,24 +724,55 @@ def run_batch(args, rank, world, local):
     sep_ms = np.array(sep_ms)
     queue_ms = np.cumsum(sep_ms)   # completion time of each scene when served one after another
     n = len(scs)
+    return {"ms": ms, "f0": f0, "fK": fK, "launches": launches, "clocks": ck,
+            "scenes_per_s": world * n / (ms / 1e3), "obs_updates_per_s": world * b.nnz * K / (ms / 1e3),
+            "separate": {"value": n / (sep_ms.sum() / 1e3), "unit": "scenes/s",
+                         "isolated_ms": {"p50": float(np.percentile(sep_ms, 50)),
+                                         "p99": float(np.percentile(sep_ms, 99))},
+                         "queued_ms": {"p50": float(np.percentile(queue_ms, 50)),
+                                       "p99": float(np.percentile(queue_ms, 99))},
+                         "what": "one context per scene, scenes run one after another on one stream"}}
+
+
+def run_batch(args, rank, world, local):
+    """Many small independent scenes: one problem with a scene partition (one launch sequence per
+    iteration for all scenes, captured as CUDA graphs) against one context per scene run one
+    after another. Reports scenes/s for ``--steps`` iterations per scene and per-scene latency."""
+    import torch
+    from paper_2305_07026_b300 import build
+    build.build()
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import batch, scenes
+    torch.cuda.set_device(local)
+    scs = scenes.batch_scenes(args.n_scenes)
+    b = batch.merge(scs)
+    K, W = args.steps, args.warmup
+    stream = torch.cuda.Stream()
+    # schedule autotuning (untimed setup): chunk and tile sizes by coordinate descent
+    from paper_2305_07026_b300 import autotune
+    if args.no_autotune:
+        sched, tried = {}, {}
+    else:
+        sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv,
+                                     dict(loss="huber", loss_scale_px=1.0, prec="mixed", pixel_scale=650.0))
+    r = batch_leg(L, scs, b, K, W, stream, sched, clocks=Clocks(), world=world, local=local)
+    n = len(scs)
     if rank != 0:
         return None
+    ms = r["ms"]
     return {
-        "metric": f"scenes/s ({K} DABA iterations per scene, batched)", "value": world * n / (ms / 1e3),
+        "metric": f"scenes/s ({K} DABA iterations per scene, batched)", "value": r["scenes_per_s"],
         "unit": "scenes/s", "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 per observation, f64 reductions/solves", "data": "synthetic",
         "config": batch_config(n, b.M, b.N, b.nnz, world),
-        "obs_updates_per_s": world * b.nnz * K / (ms / 1e3),
+        "obs_updates_per_s": r["obs_updates_per_s"],
         "schedule": {"chosen": sched, "ms_per_iteration_tried": tried},
         "latency_ms": {"p50": ms, "p99": ms, "note": "every scene of the batch completes with the batch"},
-        "separate": {"value": n / (sep_ms.sum() / 1e3), "unit": "scenes/s",
-                     "isolated_ms": {"p50": float(np.percentile(sep_ms, 50)), "p99": float(np.percentile(sep_ms, 99))},
-                     "queued_ms": {"p50": float(np.percentile(queue_ms, 50)), "p99": float(np.percentile(queue_ms, 99))},
-                     "what": "one context per scene, scenes run one after another on one stream"},
-        "objective_px2": {"initial_sum": float(f0.sum()), "final_sum": float(fK.sum()),
-                          "scenes_decreased": int((fK < f0).sum())},
-        "gpu_launches": int(launches), "clocks": ck,
+        "separate": r["separate"],
+        "objective_px2": {"initial_sum": float(r["f0"].sum()), "final_sum": float(r["fK"].sum()),
+                          "scenes_decreased": int((r["fK"] < r["f0"]).sum())},
+        "gpu_launches": int(r["launches"]), "clocks": r["clocks"],
     }
 
 

@@ -63,6 +63,7 @@ _SIGS = {
     "daba_last_launch_count": (_i64, [_p]),
     "daba_objective_noalloc": (_st, [_i32, _i32, _i64, _p, _p, _p, _p, _p, _i32, ctypes.c_double, ctypes.c_double,
                                      _p, _p]),
+    "daba_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "daba_last_error": (ctypes.c_char_p, [_p]),
     "daba_destroy": (None, [_p]),
 }
@@ -263,3 +264,13 @@ class Daba:
 
     def last_launch_count(self) -> int:
         return int(daba_last_launch_count(self._h))
+
+
+def probe_fma_rate(kind):
+    """Measured FMA rate of the current GPU in FLOP/s (daba_probe_fma_rate): kind "f32", "f32x2"
+    (packed FP32) or "f64"."""
+    out = ctypes.c_double(0.0)
+    rc = daba_probe_fma_rate({"f32": 0, "f32x2": 1, "f64": 2}[kind], ctypes.byref(out))
+    if rc != 0:
+        raise RuntimeError(f"daba_probe_fma_rate({kind}) failed with code {rc}")
+    return out.value

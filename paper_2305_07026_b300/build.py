@@ -9,8 +9,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libdaba_b300.so")
-SOURCES = ["daba_abi.cu", "daba_noalloc.cu"]
-DEPS = ["daba_abi.cu", "daba_noalloc.cu", "daba_kernels.cuh", "daba_device.cuh", "daba_state.cuh", "daba_grad.cuh", "daba_adjoint.cuh"]
+SOURCES = ["daba_abi.cu", "daba_noalloc.cu", "daba_probe.cu"]
+DEPS = ["daba_abi.cu", "daba_noalloc.cu", "daba_probe.cu", "daba_kernels.cuh", "daba_device.cuh", "daba_state.cuh", "daba_grad.cuh", "daba_adjoint.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -25,7 +25,7 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(ROOT, "include", "daba.h")]
+    deps = [os.path.join(CSRC, d) for d in DEPS] + [os.path.join(ROOT, "include", h) for h in ("daba.h", "daba_probe.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
