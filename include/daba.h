@@ -248,6 +248,21 @@ daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
  * landmark pass report a timeout (a test of that path). DABA_ERR_ARG if first_wait_ns < 0. */
 daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
 
+/* Persistent path (enable = 1): daba_run then launches, after the prepare kernel of its first
+ * iteration, all its iterations (up to 1024 per launch) as ONE cooperative kernel whose CTAs
+ * are all resident and loop over the work of every iteration, with grid-wide barriers (bounded
+ * by a 2 s clock limit each; a run-out gives DABA_ERR_TIMEOUT) between the camera pass, the
+ * camera solves with the landmark tiles, and the reduction; a batch of scenes set with
+ * daba_set_scenes then runs all its iterations in one launch. The iterates, per-block metrics and
+ * objective trace are the same bits as on the default path (CUDA graphs of the separate
+ * kernels). The default path is the faster one on B300: one kernel must hold the largest register
+ * footprint of the three phases (168 registers, 3 CTAs of 128 threads per SM), which starves the
+ * landmark pass of the CTAs that keep its copies in flight (512-scene batch, 100 iterations:
+ * 70.4 ms persistent against 38.0 ms; 26M-observation scene: 1.28 against 0.76 ms per
+ * iteration). MIXED contexts with per-block restart and S-CAM only (DABA_ERR_ARG otherwise);
+ * per-kernel timing does not apply. */
+daba_status daba_set_persistent(daba_ctx* ctx, int enable);
+
 /* Number of kernel launches the library issued in the last daba_run. */
 int64_t daba_last_launch_count(const daba_ctx* ctx);
 

@@ -58,6 +58,7 @@ _SIGS = {
     "daba_export_checkpoint": (_st, [_p, _p, ctypes.POINTER(ctypes.c_size_t)]),
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
     "daba_set_wait_limit": (_st, [_p, _i64]),
+    "daba_set_persistent": (_st, [_p, ctypes.c_int]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
@@ -250,6 +251,9 @@ class Daba:
     def import_checkpoint(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(daba_import_checkpoint(self._h, buf, len(data)))
+
+    def set_persistent(self, enable=True):
+        self._check(daba_set_persistent(self._h, int(bool(enable))))
 
     def set_wait_limit(self, first_wait_ns):
         self._check(daba_set_wait_limit(self._h, int(first_wait_ns)))

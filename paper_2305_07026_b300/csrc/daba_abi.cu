@@ -112,6 +112,9 @@ struct daba_ctx {
        *s_dev = nullptr;
   // the entry state of daba_run, put back when the run fails
   void* bk = nullptr;
+  // persistent path (daba_set_persistent): a run's iterations in one cooperative launch
+  bool persistent = false;
+  void* d_gbar = nullptr;   // grid-barrier counter and generation
 };
 
 namespace {
@@ -405,6 +408,86 @@ cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
                                                   (double*)ctx->fin_blk, (unsigned int*)ctx->fin_ticket,
                                                   (double*)ctx->d_trace, (int*)ctx->d_rs, (int*)ctx->d_flag);
   return cudaGetLastError();
+}
+
+// persistent path: n iterations from iteration index k0 as one cooperative launch on st (after
+// the prepare kernel of the run's first iteration)
+size_t pers_smem(const daba_ctx* ctx) {
+  const bool big = ctx->tile_class_end[1] > ctx->tile_class_end[0];
+  size_t b = std::max((size_t)4 * sizeof(CpassWarpSmem<float, float2>), (size_t)2 * 32 * 16 * sizeof(double));
+  b = std::max(b, lpass_smem_bytes<float>(ctx->opt.tile_obs));
+  if (big) b = std::max(b, lpass_smem_bytes<float>(BIG_TILE_OBS));
+  return b;
+}
+
+template <int LOSS>
+cudaError_t launch_persistent_t(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n) {
+  auto kern = k_run_persistent<LOSS>;
+  const size_t smem = pers_smem(ctx);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, n_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PERS_THREADS, smem)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, ctx->dev)) != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  PersArgs A;
+  A.M = ctx->M;
+  A.n_chunks = ctx->n_chunks;
+  A.n_tiles = ctx->tile_class_end[1];
+  A.tile_obs = ctx->opt.tile_obs;
+  A.n_small = ctx->tile_class_end[0];
+  A.chunk_cam = (const int*)ctx->chunk_cam;
+  A.chunk_beg = (const int*)ctx->chunk_beg;
+  A.c_lm = (const int*)ctx->c_lm;
+  A.c_rpos = (const int*)ctx->c_rpos;
+  A.cam_chunk_ptr = (const int*)ctx->cam_chunk_ptr;
+  A.tile_lm = (const int*)ctx->tile_lm;
+  A.lm_ptr = (const int*)ctx->lm_ptr;
+  A.c_u = (const float2*)ctx->c_u;
+  A.t_inv = (const uint16_t*)ctx->t_inv;
+  for (int q = 0; q < 2; ++q) {
+    A.pack[q] = (V4<float>*)ctx->pack2[q];
+    A.lmrec[q] = (V4<float>*)ctx->lmrec2[q];
+    A.lmlo[q] = (V4<float>*)ctx->lm_lo2[q];
+  }
+  A.part = (float*)ctx->chunk_part;
+  A.rec_a = (V4<float>*)ctx->rec_a;
+  A.rec_b = (V4<float>*)ctx->rec_b;
+  A.rec_c = (float*)ctx->rec_c;
+  A.cam_x = (double*)ctx->cam_x;
+  A.cam_dx = (double*)ctx->cam_dx;
+  A.cam_Rbar = (double*)ctx->cam_Rbar;
+  A.cam_S = (double*)ctx->cam_S;
+  A.cam_E = (double*)ctx->cam_E;
+  A.cam_F = (double*)ctx->cam_F;
+  A.cam_Fb = (double*)ctx->cam_Fb;
+  A.cam_Fsum = (double*)ctx->cam_Fsum;
+  A.cam_rs = (uint8_t*)ctx->cam_rs;
+  A.lm_rs = (uint8_t*)ctx->lm_rs;
+  A.tile_rs = (int*)ctx->tile_rs;
+  A.fin_blk = (double*)ctx->fin_blk;
+  A.trace = (double*)ctx->d_trace;
+  A.restarts = (int*)ctx->d_rs;
+  A.bar_count = (unsigned*)ctx->d_gbar;
+  A.bar_gen = (unsigned*)ctx->d_gbar + 1;
+  A.s2 = ctx->s_norm * ctx->s_norm;
+  IterParams P = iter_params(ctx);
+  LossC<float> L = loss_consts<float>(ctx);
+  int n_iter = n, par0 = (int)(k0 & 1);
+  if ((e = cudaMemsetAsync(ctx->d_gbar, 0, 8, st)) != cudaSuccess) return e;
+  void* args[] = {&A, &P, &L, &n_iter, &par0};
+  e = cudaLaunchCooperativeKernel((const void*)kern, dim3(per_sm * n_sm), dim3(PERS_THREADS), args, smem, st);
+  ctx->launches++;
+  return e;
+}
+
+cudaError_t launch_persistent(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n) {
+  switch (ctx->opt.loss) {
+    case DABA_LOSS_TRIVIAL: return launch_persistent_t<LOSS_TRIVIAL>(ctx, st, k0, n);
+    case DABA_LOSS_HUBER: return launch_persistent_t<LOSS_HUBER>(ctx, st, k0, n);
+    case DABA_LOSS_CAUCHY: return launch_persistent_t<LOSS_CAUCHY>(ctx, st, k0, n);
+    default: return launch_persistent_t<LOSS_WELSCH>(ctx, st, k0, n);
+  }
 }
 
 // global restart variant: apply the MM alternatives when the reduction's test fired (the
@@ -1050,6 +1133,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_lperm, (size_t)N * 4);
   AL(d_scene_f, (size_t)M * 8);
   AL(bk, backup_layout(ctx).bytes);
+  AL(d_gbar, 16);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -1374,7 +1458,10 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(ctx->s_dev, &s_start, 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
-    if (ctx->timing && seg > RUN_GRAPH_MAX) {   // direct launches with per-kernel events
+    if (ctx->persistent) {   // the prepare kernel, then every iteration of the segment in one cooperative launch
+      CK(launch_prepare(ctx, st, ctx->k));
+      CK(launch_persistent(ctx, st, ctx->k, seg));
+    } else if (ctx->timing && seg > RUN_GRAPH_MAX) {   // direct launches with per-kernel events
       CK(cudaEventRecord(ev(ctx, evi++), st));
       CK(launch_prepare(ctx, st, ctx->k));
       CK(cudaEventRecord(ev(ctx, evi++), st));
@@ -1407,7 +1494,7 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(&ctx->s_k, ctx->s_dev, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (ctx->timing) {
+    if (ctx->timing && !ctx->persistent) {
       float ms = 0.f;
       auto elapsed = [&](size_t a, size_t b) {
         if (cudaEventElapsedTime(&ms, ctx->events[a], ctx->events[b]) == cudaSuccess) return true;
@@ -1440,6 +1527,7 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
   CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (flag & 2) return fail(ctx, DABA_ERR_TIMEOUT, "a landmark-pass copy did not complete in time (bounded wait ran out)");
+  if (flag & 4) return fail(ctx, DABA_ERR_TIMEOUT, "a grid barrier of the persistent launch ran out");
   if (flag || !std::isfinite(trace[iters])) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
   if (obj_trace && (s = deliver(ctx, obj_trace, trace.data(), ((size_t)iters + 1) * 8, st)) != DABA_OK) return s;
   if (restarts && iters > 0 && (s = deliver(ctx, restarts, rs.data(), (size_t)iters * 4, st)) != DABA_OK) return s;
@@ -1882,6 +1970,14 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
   ctx->state_set = true;
   // host copies used by the Assumption 2 check: rebuild from the imported iterate
   ctx->checked = true;
+  return DABA_OK;
+}
+
+daba_status daba_set_persistent(daba_ctx* ctx, int enable) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (enable && (!is_mixed(ctx) || ctx->opt.restart_mode != DABA_RESTART_BLOCK || ctx->opt.cam_solver != DABA_CAM_SCAM))
+    return fail(ctx, DABA_ERR_ARG, "the persistent path runs MIXED contexts with per-block restart and S-CAM");
+  ctx->persistent = enable != 0;
   return DABA_OK;
 }
 

@@ -33,6 +33,13 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float frsqrt(float a) { return rsqrtf(a); }
 __device__ __forceinline__ double frsqrt(double a) { return 1.0 / sqrt(a); }
 
+// Multiply and add rounded separately (never contracted into a fused multiply-add), so that
+// every kernel that inlines the loss evaluates it to the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 // rho(r) and rho'(r) of the robust losses of Assumption 1 (App. B).
 template <int LOSS, class Real>
 __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, Real& w) {
@@ -49,12 +56,12 @@ __device__ __forceinline__ void rho_w(const LossC<Real>& L, Real r, Real& rho, R
       w = Real(1);
     }
   } else if (LOSS == LOSS_CAUCHY) {
-    Real x = r * L.inv_c2;
-    rho = L.c2 * log1p(x);
-    w = fdiv(Real(1), Real(1) + x);
+    const Real x = mul_rn(r, L.inv_c2);
+    rho = mul_rn(L.c2, log1p(x));
+    w = fdiv(Real(1), add_rn(Real(1), x));
   } else {
-    Real ex = exp(-r * L.inv_c2);
-    rho = L.c2 * (Real(1) - ex);
+    const Real ex = exp(-mul_rn(r, L.inv_c2));
+    rho = mul_rn(L.c2, add_rn(Real(1), -ex));
     w = ex;
   }
 }

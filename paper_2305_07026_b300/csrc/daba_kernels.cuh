@@ -300,27 +300,56 @@ struct CpassStage {
 //   rec_a = (wb lamb^2, -wb lamb (Rbar ebar) / 2)   terms of sum_i Q_ij(l | xbar^k)
 //   rec_b = (w lam^2, -w lam (R e) / 2)             terms of sum_i Q_ij(l | x^k)
 //   rec_c = (F_ij(x^k), surrogate gap), MIXED the gap only (RecC)
-template <int LOSS, class Real, class Real2>
-__global__ void __launch_bounds__(CPASS_WARPS * 32)
-    k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
-            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
-            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
-            const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b,
-            typename RecC<Real>::type* __restrict__ rec_c) {
-  __shared__ V4<Real> spk[CPASS_WARPS][P4N];
-  __shared__ CpassStage<Real, Real2> sbuf[CPASS_WARPS][CPASS_STAGES][32];
-  __shared__ Real2 su[CPASS_WARPS][CPASS_STAGES][32];
-  __shared__ int srp[CPASS_WARPS][CPASS_STAGES][32];
-  const int wib = threadIdx.x >> 5;
-  const int warp = blockIdx.x * CPASS_WARPS + wib;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_chunks) return;
+// Shared memory of one camera-pass warp: the camera pack, and the staging ring of the landmark
+// records, pixels and record positions.
+template <class Real, class Real2>
+struct CpassWarpSmem {
+  V4<Real> pk[P4N];
+  CpassStage<Real, Real2> sbuf[CPASS_STAGES][32];
+  Real2 su[CPASS_STAGES][32];
+  int srp[CPASS_STAGES][32];
+};
+
+// Loads of data that the same launch wrote earlier (COH: the persistent kernel, whose phases
+// follow one another inside one launch) go to L2 (ld.global.cg), past the SM's incoherent L1
+// and read-only caches; the kernels of the graph path read them with plain loads.
+template <bool COH, class T>
+__device__ __forceinline__ T ld_mut(const T* p) {
+  if constexpr (COH) {
+    if constexpr (sizeof(T) == 16) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+      T r;
+      memcpy(&r, &v, 16);
+      return r;
+    } else if constexpr (sizeof(T) == 32) {
+      const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+      T r;
+      memcpy(&r, &a, 16);
+      memcpy(reinterpret_cast<char*>(&r) + 16, &b, 16);
+      return r;
+    } else {
+      return __ldcg(p);
+    }
+  } else {
+    return *p;
+  }
+}
+
+// One chunk of the camera-sorted pass (camera chunk_cam[warp], observations chunk_beg[warp] ..
+// chunk_beg[warp + 1]) by one warp; gamma of Eq. nesterov_x for this iteration.
+template <int LOSS, class Real, class Real2, bool COH>
+__device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Real, Real2>& sm, Real gamma,
+                                            const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
+                                            const int* __restrict__ c_lm, const Real2* __restrict__ c_u,
+                                            const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec,
+                                            const LossC<Real>& L, Real* __restrict__ part,
+                                            const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a,
+                                            V4<Real>* __restrict__ rec_b, typename RecC<Real>::type* __restrict__ rec_c) {
   const int cam = chunk_cam[warp];
   const int b = chunk_beg[warp], e = chunk_beg[warp + 1];
-  if (lane < P4N) spk[wib][lane] = pack[(size_t)cam * P4N + lane];
+  if (lane < P4N) sm.pk[lane] = ld_mut<COH>(pack + (size_t)cam * P4N + lane);
   __syncwarp();
-  const V4<Real>* pk = spk[wib];
-  const Real gamma = Real(P.gam[*P.it]);
+  const V4<Real>* pk = sm.pk;
   CamAcc<Real> acc;
   acc.zero();
   // Pipeline over batches t of 32 observations (one per lane) in a ring of four: the landmark
@@ -328,7 +357,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   // (their landmark indices loaded a step earlier) while two batches are evaluated. Each lane
   // only touches its own staging slots.
   const int nb = (e - b + 31) >> 5;
-  CpassStage<Real, Real2>(*stg)[32] = sbuf[wib];
+  CpassStage<Real, Real2>(*stg)[32] = sm.sbuf;
   auto issue = [&](int t, int j) {
     const int o = b + 32 * t + lane;
     if (o < e) {
@@ -338,10 +367,10 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       for (int q = 0; q < (int)(2 * sizeof(V4<Real>) / 16); ++q)
         cp_async16(reinterpret_cast<char*>(d.rec) + 16 * q, reinterpret_cast<const char*>(src) + 16 * q);
       if (sizeof(Real2) == 16)
-        cp_async16(&su[wib][t % CPASS_STAGES][lane], c_u + o);
+        cp_async16(&sm.su[t % CPASS_STAGES][lane], c_u + o);
       else
-        cp_async8(&su[wib][t % CPASS_STAGES][lane], c_u + o);
-      cp_async4(&srp[wib][t % CPASS_STAGES][lane], c_rpos + o);
+        cp_async8(&sm.su[t % CPASS_STAGES][lane], c_u + o);
+      cp_async4(&sm.srp[t % CPASS_STAGES][lane], c_rpos + o);
     }
     cp_async_commit();
   };
@@ -354,7 +383,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
     if (o < e) {
       const CpassStage<Real, Real2>& d = stg[t % CPASS_STAGES][lane];
       const V4<Real> r0 = d.rec[0], r1 = d.rec[1];
-      const Real2 uu = su[wib][t % CPASS_STAGES][lane];
+      const Real2 uu = sm.su[t % CPASS_STAGES][lane];
       ObsEval<Real> ev;
       eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
@@ -369,7 +398,7 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
       rb.y = Real(-0.5) * wl * ev.Re0;
       rb.z = Real(-0.5) * wl * ev.Re1;
       rb.w = Real(-0.5) * wl * ev.Re2;
-      const int rp = srp[wib][t % CPASS_STAGES][lane];
+      const int rp = sm.srp[t % CPASS_STAGES][lane];
       rec_a[rp] = ra;
       rec_b[rp] = rb;
       rec_c[rp] = RecC<Real>::make(Real(0.5) * ev.rho, ev.gap);
@@ -395,6 +424,22 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   // warp reduction; the partial is stored in the pass precision and summed over the
   // camera's chunks in FP64 by the camera solve
   acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE);
+}
+
+template <int LOSS, class Real, class Real2>
+__global__ void __launch_bounds__(CPASS_WARPS * 32)
+    k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
+            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
+            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
+            const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b,
+            typename RecC<Real>::type* __restrict__ rec_c) {
+  __shared__ CpassWarpSmem<Real, Real2> sm[CPASS_WARPS];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * CPASS_WARPS + wib;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_chunks) return;
+  cpass_chunk<LOSS, Real, Real2, false>(warp, lane, sm[wib], Real(P.gam[*P.it]), chunk_cam, chunk_beg, c_lm, c_u,
+                                        pack, lmrec, L, part, c_rpos, rec_a, rec_b, rec_c);
 }
 
 // ---------------------------------------------------------------------------
@@ -423,6 +468,9 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned coun
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
   unsigned ok;
@@ -641,17 +689,19 @@ __device__ __forceinline__ void lpass_tile_sums(int nrs, double gsum, bool globa
   }
 }
 
-template <class Real, class Real2, bool HAS_LO>
-__global__ void __launch_bounds__(LPASS_THREADS)
-    k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-            const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
-            const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
-            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, IterParams P,
-            int* __restrict__ tile_rs, LpassOut<Real> O) {
+// One tile of the landmark pass by the CTA's LPASS_THREADS threads (smem_raw: the tile's shared
+// memory; gamma and first of this iteration). Every thread of the CTA calls it. Returns false if
+// a bounded wait ran out (the tile is then skipped, flag bit 2 set).
+template <class Real, class Real2, bool HAS_LO, bool COH>
+__device__ __forceinline__ bool lpass_tile(int tile, int no_cap, unsigned char* smem_raw, Real gamma, int first,
+                                           const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
+                                           const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
+                                           const V4<Real>* __restrict__ rec_b,
+                                           const typename RecC<Real>::type* __restrict__ rec_c,
+                                           const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo,
+                                           const IterParams& P, int* __restrict__ tile_rs, const LpassOut<Real>& O) {
   using RC = typename RecC<Real>::type;
   using SM = LpassSmem<Real>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int tile = tile0 + blockIdx.x;
   const int lb = tile_lm[tile], le = tile_lm[tile + 1];
   const int nl = le - lb;
   const int ob = lm_ptr[lb], oe = lm_ptr[le];
@@ -679,8 +729,6 @@ __global__ void __launch_bounds__(LPASS_THREADS)
       mbar_arrive_expect_tx(bar, 0u);
     }
   }
-  const Real gamma = Real(P.gam[*P.it]);
-  const int first = *P.first;
   // the landmark state of this thread's landmark (at most one: nl <= blockDim.x) is loaded
   // while the copies are in flight
   static_assert(TILE_LMS <= LPASS_THREADS, "one landmark per thread");
@@ -690,24 +738,38 @@ __global__ void __launch_bounds__(LPASS_THREADS)
   V4<float> lo0;
   int s0 = 0, s1 = 0;
   if (jl < nl) {
-    A = lmrec[2 * g];
-    B = lmrec[2 * g + 1];
-    if (HAS_LO) lo0 = lm_lo[g];
+    A = ld_mut<COH>(lmrec + 2 * g);
+    B = ld_mut<COH>(lmrec + 2 * g + 1);
+    if (HAS_LO) lo0 = ld_mut<COH>(lm_lo + g);
     s0 = lm_ptr[lb + jl] - ob;
     s1 = lm_ptr[lb + jl + 1] - ob;
   }
   __syncthreads();   // the mbarrier is initialised
-  if (!mbar_wait_for(bar, 0u, P.wait_ns)) {   // copies not complete in time: report, let them land, skip the tile
+  bool ok = mbar_wait_for(bar, 0u, P.wait_ns);
+  if (!ok) {   // copies not complete in time: report, let them land, skip the tile
     atomicOr(P.flag, 2);
     mbar_wait_for(bar, 0u, LPASS_DRAIN_NS);
-    return;
   }
   int nrs = 0;
   double gsum = 0.0;   // global restart variant: this thread's E(k+1) - Fbar(k)
-  if (jl < nl)
+  if (ok && jl < nl)
     nrs = lpass_landmark<Real, HAS_LO>(sca, scb, scc + (ob - cs), sinv + (ob - is), s0, s1, A, B, lo0, g, gamma, first,
                                        P, O, gsum);
-  lpass_tile_sums(nrs, gsum, P.accelerated && P.restart_global, tile, tile_rs, P.g_tile);
+  lpass_tile_sums(nrs, gsum, P.accelerated && P.restart_global, tile, tile_rs, P.g_tile);   // ends every thread's reads
+  if (COH && threadIdx.x == 0) mbar_inval(bar);   // the CTA initialises it again for its next tile
+  return ok;
+}
+
+template <class Real, class Real2, bool HAS_LO>
+__global__ void __launch_bounds__(LPASS_THREADS)
+    k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
+            const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
+            const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
+            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, IterParams P,
+            int* __restrict__ tile_rs, LpassOut<Real> O) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  lpass_tile<Real, Real2, HAS_LO, false>(tile0 + blockIdx.x, no_cap, smem_raw, Real(P.gam[*P.it]), *P.first, tile_lm,
+                                         lm_ptr, t_inv, rec_a, rec_b, rec_c, lmrec, lm_lo, P, tile_rs, O);
 }
 
 // ---------------------------------------------------------------------------
@@ -1089,38 +1151,32 @@ __device__ __forceinline__ void cam_solve(const double* st, const CamT<double>& 
 __device__ __forceinline__ void acc_add(double& a, float x) { a += widen(x); }
 __device__ __forceinline__ void acc_add(double& a, double x) { a += x; }
 
-// Sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial
-template <class Real, class T>
-__device__ __forceinline__ void sum_stats(const Real* __restrict__ part, int c0, int c1, int off, T* st);
-template <>
-__device__ __forceinline__ void sum_stats<float, double>(const float* __restrict__ part, int c0, int c1, int off,
-                                                         double* st) {
+// Sum over chunks [c0, c1) of the 39 statistics at offset `off` of each partial (COH: the
+// partials were written earlier in the same launch, so they are read from L2)
+template <class Real, class T, bool COH = false>
+__device__ __forceinline__ void sum_stats(const Real* __restrict__ part, int c0, int c1, int off, T* st) {
+  static_assert(sizeof(T) == 8, "FP64 sums");
 #pragma unroll
   for (int k = 0; k < 39; ++k) st[k] = 0.0;
   for (int c = c0; c < c1; ++c) {
-    const float4* p = reinterpret_cast<const float4*>(part + (size_t)c * CP_STRIDE + off);
+    if constexpr (sizeof(Real) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(part + (size_t)c * CP_STRIDE + off);
 #pragma unroll
-    for (int v = 0; v < 10; ++v) {
-      const float4 x = __ldg(p + v);
-      acc_add(st[4 * v + 0], x.x);
-      acc_add(st[4 * v + 1], x.y);
-      acc_add(st[4 * v + 2], x.z);
-      if (v < 9) acc_add(st[4 * v + 3], x.w);
-    }
-  }
-}
-template <>
-__device__ __forceinline__ void sum_stats<double, double>(const double* __restrict__ part, int c0, int c1, int off,
-                                                          double* st) {
+      for (int v = 0; v < 10; ++v) {
+        const float4 x = COH ? __ldcg(p + v) : __ldg(p + v);
+        acc_add(st[4 * v + 0], x.x);
+        acc_add(st[4 * v + 1], x.y);
+        acc_add(st[4 * v + 2], x.z);
+        if (v < 9) acc_add(st[4 * v + 3], x.w);
+      }
+    } else {
+      const double2* p = reinterpret_cast<const double2*>(part + (size_t)c * CP_STRIDE + off);
 #pragma unroll
-  for (int k = 0; k < 39; ++k) st[k] = 0.0;
-  for (int c = c0; c < c1; ++c) {
-    const double2* p = reinterpret_cast<const double2*>(part + (size_t)c * CP_STRIDE + off);
-#pragma unroll
-    for (int v = 0; v < 20; ++v) {
-      const double2 x = __ldg(p + v);
-      st[2 * v] += x.x;
-      if (v < 19) st[2 * v + 1] += x.y;
+      for (int v = 0; v < 20; ++v) {
+        const double2 x = COH ? __ldcg(p + v) : __ldg(p + v);
+        st[2 * v] += x.x;
+        if (v < 19) st[2 * v + 1] += x.y;
+      }
     }
   }
 }
@@ -1220,13 +1276,18 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
 // The FP32 S-CAM path is held to 5 CTAs per SM (at most 168 registers, a few hundred bytes of
 // spills): batches of many small scenes fill more than one wave of CTAs, and 10 instead of 8
 // resident warps per SM shorten the second. The FP64 and LM paths would spill heavily and keep 255.
-template <class Real, int SOLVER>
-__global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER == CAM_SCAM) ? 5 : 1)
-    k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
-               double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
-               double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
-               double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs, double* __restrict__ cam_Fsum,
-               V4<Real>* __restrict__ pack_next) {
+// One group of 32 cameras (cameras 32 grp .. 32 grp + 31) by two warps (role 0 and 1, lanes
+// 0..31 each); sh_mm is the group's hand-over buffer in shared memory. Both warps of the CTA
+// pass the barrier inside, so every thread of the CTA calls it the same number of times.
+template <class Real, int SOLVER, bool COH>
+__device__ __forceinline__ void camsolve_group(int grp, int role, int lane, double (*sh_mm)[16], int it, int first,
+                                               int M, const int* __restrict__ cam_chunk_ptr,
+                                               const Real* __restrict__ part, double* __restrict__ cam_x,
+                                               double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
+                                               const IterParams& P, double* __restrict__ cam_S,
+                                               double* __restrict__ cam_E, double* __restrict__ cam_F,
+                                               double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs,
+                                               double* __restrict__ cam_Fsum, V4<Real>* __restrict__ pack_next) {
   // 32 cameras per CTA, two warps: warp 0 takes the accelerated solve (Eq. update_amm) and
   // the restart test, warp 1 the MM solve (Eq. update_mm) of the same cameras; the MM solve is
   // computed whether or not the camera restarts, so that the two FP64 chains run side by side
@@ -1234,11 +1295,8 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
   static_assert(CAMSOLVE_THREADS == 64, "two warps per CTA");
   using T = double;
   using N = Num<T>;
-  __shared__ T sh_mm[32][16];   // MM solution R(9) t(3) d(3) and its dEn
-  const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
+  const int i = grp * 32 + lane;
   const bool valid = i < M;
-  const int it = *P.it;
   const T xi = N::from(P.xi);
   CamT<T> ck, cn;
   T st[39];
@@ -1251,11 +1309,11 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
     x = cam_x + (size_t)i * CSTRIDE;
     dx = cam_dx + (size_t)i * CSTRIDE;
 #pragma unroll
-    for (int a = 0; a < 9; ++a) ck.R[a] = N::from(x[CS_R + a]);
+    for (int a = 0; a < 9; ++a) ck.R[a] = N::from(ld_mut<COH>(x + CS_R + a));
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      ck.t[a] = N::from(x[CS_T + a]);
-      ck.d[a] = N::from(x[CS_D + a]);
+      ck.t[a] = N::from(ld_mut<COH>(x + CS_T + a));
+      ck.d[a] = N::from(ld_mut<COH>(x + CS_D + a));
     }
     if (role == 1 || P.accelerated) {
       // One code path for both warps, so that they fetch the same instructions: warp 1 the MM
@@ -1267,17 +1325,17 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
       } else {
         const T gamma = N::from(P.gam[it]);
 #pragma unroll
-        for (int a = 0; a < 9; ++a) c0s.R[a] = N::from(cam_Rbar[(size_t)i * 9 + a]);
+        for (int a = 0; a < 9; ++a) c0s.R[a] = N::from(ld_mut<COH>(cam_Rbar + (size_t)i * 9 + a));
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          c0s.t[a] = ck.t[a] + gamma * N::from(dx[CS_T + a]);
-          c0s.d[a] = ck.d[a] + gamma * N::from(dx[CS_D + a]);
+          c0s.t[a] = ck.t[a] + gamma * N::from(ld_mut<COH>(dx + CS_T + a));
+          c0s.d[a] = ck.d[a] + gamma * N::from(ld_mut<COH>(dx + CS_D + a));
         }
       }
-      sum_stats<Real, T>(part, c0, c1, role == 1 ? PART_XK : PART_XB, st);
+      sum_stats<Real, T, COH>(part, c0, c1, role == 1 ? PART_XK : PART_XB, st);
       CamT<T> cs;
       cam_solve<SOLVER, Real>(st, c0s, xi, P.n_alt, cs);
-      if (role == 0) sum_stats<Real, T>(part, c0, c1, PART_XK, st);
+      if (role == 0) sum_stats<Real, T, COH>(part, c0, c1, PART_XK, st);
       const T d = cam_phi(st, ck, cs, xi);   // E^alpha(solution | x^k) - E^alpha(x^k | x^k)
       if (role == 1) {
 #pragma unroll
@@ -1298,27 +1356,26 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
   if (role != 0 || !valid) return;
 #pragma unroll
   for (int a = 0; a < 9; ++a) {
-    const T d = N::from(dx[CS_R + a]);
+    const T d = N::from(ld_mut<COH>(dx + CS_R + a));
     dx2 = dx2 + d * d;
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const T dt = N::from(dx[CS_T + a]), dd = N::from(dx[CS_D + a]);
+    const T dt = N::from(ld_mut<COH>(dx + CS_T + a)), dd = N::from(ld_mut<COH>(dx + CS_D + a));
     dx2 = dx2 + dt * dt + dd * dd;
   }
   T sF = N::c(0.f), sG = N::c(0.f);
   for (int c = c0; c < c1; ++c) {
-    acc_add(sF, part[(size_t)c * CP_STRIDE + PART_F]);
-    acc_add(sG, part[(size_t)c * CP_STRIDE + PART_G]);
+    acc_add(sF, ld_mut<COH>(part + (size_t)c * CP_STRIDE + PART_F));
+    acc_add(sG, ld_mut<COH>(part + (size_t)c * CP_STRIDE + PART_G));
   }
   // Eq. DEalpha and the slack form of Eqs. Fak, lFak (see k_lpass)
-  const int first = *P.first;
   const T dE = N::c(-0.5f) * xi * dx2 + N::c(0.5f) * sG;
-  const T S = first ? N::c(0.f) : N::from(cam_S[i]);
+  const T S = first ? N::c(0.f) : N::from(ld_mut<COH>(cam_S + i));
   const T thr = N::from(P.eta1) * (S - dE);
   const bool global = P.accelerated && P.restart_global;
   const bool rs = P.accelerated ? (!global && dEn > thr) : true;
-  const T E = first ? N::c(0.5f) * sF : N::from(cam_E[i]);
+  const T E = first ? N::c(0.5f) * sF : N::from(ld_mut<COH>(cam_E + i));
   const T F = E + dE;
   if (global) {   // keep the MM alternative (warp 1's) and this block's term of the global test
     double* alt = P.cam_alt + (size_t)i * 32;
@@ -1383,6 +1440,19 @@ __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER
 #pragma unroll
   for (int a = 0; a < 9; ++a) cam_Rbar[(size_t)i * 9 + a] = N::to_double(Rb[a]);
   write_pack_t<Real>(cn, ndx, Rb, pack_next + (size_t)i * P4N);
+}
+
+template <class Real, int SOLVER>
+__global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER == CAM_SCAM) ? 5 : 1)
+    k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
+               double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
+               double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
+               double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs, double* __restrict__ cam_Fsum,
+               V4<Real>* __restrict__ pack_next) {
+  __shared__ double sh_mm[32][16];   // MM solution R(9) t(3) d(3) and its dEn
+  camsolve_group<Real, SOLVER, false>(blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31, sh_mm, *P.it, *P.first, M,
+                                      cam_chunk_ptr, part, cam_x, cam_dx, cam_Rbar, P, cam_S, cam_E, cam_F, cam_Fb,
+                                      cam_rs, cam_Fsum, pack_next);
 }
 
 // ---------------------------------------------------------------------------
@@ -1492,6 +1562,182 @@ __global__ void __launch_bounds__(FIN_THREADS)
     *P.it = k + 1;
     *P.first = 0;
     *ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. persistent path: the iterations of a run in one cooperative launch (MIXED, Algorithm 1 with
+//    per-block restart and S-CAM). Every CTA is resident; grid barriers separate the camera
+//    pass, the camera solves and landmark tiles, and the reduction. Data written earlier in the
+//    launch is read through L2 (COH loads; TMA and cp.async.cg read L2 already).
+// ---------------------------------------------------------------------------
+constexpr int PERS_THREADS = 128;                    // 4 camera-pass warps / 2 camera-solve groups / 1 tile
+constexpr long long GRID_BAR_NS = 2000000000ll;     // a grid barrier gives up after 2 s (flag bit 4)
+
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+
+// Barrier over the grid of a cooperative launch: thread 0 of each CTA arrives on a counter; the
+// last arrival resets it and advances the generation, the others poll the generation, at most
+// GRID_BAR_NS (then flag bit 4 is set and the CTA goes on, so the launch always ends).
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = *(volatile unsigned*)gen;
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (*(volatile unsigned*)gen == g) {
+        if ((long long)(globaltimer_ns() - t0) >= GRID_BAR_NS) {
+          atomicOr(flag, 4);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct PersArgs {
+  int M, n_chunks, n_tiles, tile_obs, n_small;   // tiles [0, n_small) hold up to tile_obs observations, the rest one long track
+  const int *chunk_cam, *chunk_beg, *c_lm, *c_rpos, *cam_chunk_ptr, *tile_lm, *lm_ptr;
+  const float2* c_u;
+  const uint16_t* t_inv;
+  V4<float>*pack[2];
+  V4<float>*lmrec[2];
+  V4<float>*lmlo[2];
+  float* part;
+  V4<float>*rec_a;
+  V4<float>*rec_b;
+  float* rec_c;
+  double *cam_x, *cam_dx, *cam_Rbar, *cam_S, *cam_E, *cam_F, *cam_Fb, *cam_Fsum;
+  uint8_t *cam_rs, *lm_rs;
+  int* tile_rs;
+  double *fin_blk, *trace;
+  int* restarts;
+  unsigned *bar_count, *bar_gen;
+  double s2;   // s_norm^2
+};
+
+template <int LOSS>
+__global__ void __launch_bounds__(PERS_THREADS, 3)
+    k_run_persistent(PersArgs A, IterParams P, LossC<float> L, int n_iter, int par0) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sf[PERS_THREADS / 32], sf2[PERS_THREADS / 32];
+  __shared__ long long sn[PERS_THREADS / 32], sn2[PERS_THREADS / 32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  const int first0 = *P.first;
+  const int n_cs = (A.M + 63) / 64;   // camera-solve items: two groups of 32 cameras
+  for (int j = 0; j < n_iter; ++j) {
+    const int par = (par0 + j) & 1;
+    const float gamma = float(P.gam[j]);
+    const int first = j == 0 ? first0 : 0;
+    // ---- camera pass: the grid's warps take the chunks
+    {
+      CpassWarpSmem<float, float2>* cw = reinterpret_cast<CpassWarpSmem<float, float2>*>(smem) + wib;
+      for (int w = blockIdx.x * 4 + wib; w < A.n_chunks; w += G * 4)
+        cpass_chunk<LOSS, float, float2, true>(w, lane, *cw, gamma, A.chunk_cam, A.chunk_beg, A.c_lm, A.c_u,
+                                               A.pack[par], A.lmrec[par], L, A.part, A.c_rpos, A.rec_a, A.rec_b,
+                                               A.rec_c);
+    }
+    fence_proxy_async_global();   // the records written above are read by bulk copies (async proxy)
+    grid_barrier(A.bar_count, A.bar_gen, P.flag);
+    fence_proxy_async_global();
+    // ---- camera solves (items 0 .. n_cs) and landmark tiles (the rest), strided over the CTAs
+    {
+      LpassOut<float> O;
+      O.lmrec_out = A.lmrec[par ^ 1];
+      O.lm_lo_out = A.lmlo[par ^ 1];
+      O.lm_rs = A.lm_rs;
+      O.lm_Fdiag = nullptr;
+      O.lm_Fbdiag = nullptr;
+      O.lm_alt = nullptr;
+      O.lm_sums = nullptr;
+      for (int item = blockIdx.x; item < n_cs + A.n_tiles; item += G) {
+        if (item < n_cs) {
+          double(*sh)[16] = reinterpret_cast<double(*)[16]>(smem) + (wib >> 1) * 32;
+          camsolve_group<float, CAM_SCAM, true>(2 * item + (wib >> 1), wib & 1, lane, sh, j, first, A.M,
+                                                A.cam_chunk_ptr, A.part, A.cam_x, A.cam_dx, A.cam_Rbar, P, A.cam_S,
+                                                A.cam_E, A.cam_F, A.cam_Fb, A.cam_rs, A.cam_Fsum, A.pack[par ^ 1]);
+          __syncthreads();   // the hand-over buffers are read before the next item reuses the memory
+        } else {
+          const int tile = item - n_cs;
+          lpass_tile<float, float2, true, true>(tile, tile < A.n_small ? A.tile_obs : BIG_TILE_OBS, smem, gamma, first,
+                                                A.tile_lm, A.lm_ptr, A.t_inv, A.rec_a, A.rec_b, A.rec_c, A.lmrec[par], A.lmlo[par], P,
+                                                A.tile_rs, O);
+        }
+      }
+    }
+    grid_barrier(A.bar_count, A.bar_gen, P.flag);
+    // ---- reduction: F(x^k) and the restart count in the order of k_finalize (FIN_BLOCKS blocks
+    // of FIN_THREADS threads: each of these threads computes two of them, and the warp trees run
+    // over the same lanes, so the trace has the same bits as on the graph path)
+    static_assert(FIN_THREADS == 2 * PERS_THREADS, "two reduction threads per thread");
+    for (int fb = blockIdx.x; fb < FIN_BLOCKS; fb += G) {   // the reduction block fb of k_finalize
+      double f[2] = {0.0, 0.0};
+      long long n[2] = {0, 0};
+      const int stride = FIN_BLOCKS * FIN_THREADS;
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int vt = threadIdx.x + v * PERS_THREADS;   // the k_finalize thread emulated
+        for (int i = fb * FIN_THREADS + vt; i < A.M; i += stride) {
+          f[v] += ld_mut<true>(A.cam_Fsum + i);
+          n[v] += ld_mut<true>(A.cam_rs + i);
+        }
+        for (int t = fb * FIN_THREADS + vt; t < A.n_tiles; t += stride) n[v] += ld_mut<true>(A.tile_rs + t);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          f[v] += __shfl_xor_sync(0xffffffffu, f[v], off);
+          n[v] += __shfl_xor_sync(0xffffffffu, n[v], off);
+        }
+      }
+      if (lane == 0) {   // warp results of the emulated warps wib and wib + 4
+        sf[wib] = f[0];
+        sn[wib] = n[0];
+        sf2[wib] = f[1];
+        sn2[wib] = n[1];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double ft = 0.0;
+        long long nt = 0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) {
+          ft += w < 4 ? sf[w] : sf2[w - 4];
+          nt += w < 4 ? sn[w] : sn2[w - 4];
+        }
+        A.fin_blk[3 * fb] = ft;
+        A.fin_blk[3 * fb + 1] = (double)nt;
+      }
+      __syncthreads();   // sf / sn are read before the next block's warps write them
+    }
+    grid_barrier(A.bar_count, A.bar_gen, P.flag);
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+      double ft = 0.0, nt = 0.0;
+      for (int b = threadIdx.x; b < FIN_BLOCKS; b += 32) {
+        ft += ld_mut<true>(A.fin_blk + 3 * b);
+        nt += ld_mut<true>(A.fin_blk + 3 * b + 1);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        ft += __shfl_xor_sync(0xffffffffu, ft, off);
+        nt += __shfl_xor_sync(0xffffffffu, nt, off);
+      }
+      if (threadIdx.x == 0) {
+        A.trace[j] = ft * A.s2;
+        A.restarts[j] = (int)nt;
+        if (!isfinite(ft)) atomicOr(P.flag, 1);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *P.it = n_iter;
+    *P.first = 0;
   }
 }
 

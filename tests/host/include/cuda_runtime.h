@@ -25,6 +25,9 @@ inline long long __double_as_longlong(double d) { long long u; std::memcpy(&u, &
 inline double __longlong_as_double(long long u) { double d; std::memcpy(&d, &u, 8); return d; }
 template <class T> T __shfl_xor_sync(unsigned, T v, int) { return v; }
 template <class T> T __ldg(const T* p) { return *p; }
+template <class T> T __ldcg(const T* p) { return *p; }
+inline void __nanosleep(unsigned) {}
+inline unsigned atomicExch(unsigned* p, unsigned v) { const unsigned o = *p; *p = v; return o; }
 inline void __syncwarp() {}
 inline void __syncthreads() {}
 inline void __threadfence() {}
@@ -36,6 +39,8 @@ inline float rsqrtf(float a) { return 1.0f / std::sqrt(a); }
 inline size_t __cvta_generic_to_shared(const void*) { return 0; }
 typedef int cudaError_t;
 inline double __dmul_rn(double a, double b) { return a * b; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fadd_rn(float a, float b) { return a + b; }
 inline double __dadd_rn(double a, double b) { return a + b; }
 inline double __dsub_rn(double a, double b) { return a - b; }
 inline double __ddiv_rn(double a, double b) { return a / b; }
