@@ -572,6 +572,7 @@ def run_ours(args, rank, world, local):
         r = batch_leg(L, scs, bb, 100, W, stream, {}, world=world, local=local)
         batch_line = {"scenes": len(scs), "iterations": 100, "nnz": bb.nnz, "scenes_per_s": r["scenes_per_s"],
                       "ms_per_batch": r["ms"], "latency_ms_p50_p99": [r["ms"], r["ms"]],
+                      "persistent_ms_per_batch": r["persistent_ms"],
                       "separate_scenes_per_s": r["separate"]["value"],
                       "separate_isolated_ms_p50_p99": [r["separate"]["isolated_ms"]["p50"],
                                                        r["separate"]["isolated_ms"]["p99"]],
@@ -705,6 +706,18 @@ def batch_leg(L, scs, b, K, W, stream, sched, clocks=None, world=1, local=0):
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     launches = d.last_launch_count()
     fK = d.scene_objectives(stream=sp)
+    # the same K iterations as one persistent cooperative launch (daba_set_persistent), for comparison
+    pers_ms = None
+    d.set_persistent(True)
+    d.set_state(b.cams, b.lms, stream=sp)
+    d.run(K, stream=sp)
+    d.set_state(b.cams, b.lms, stream=sp)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    d.run(K, stream=sp)
+    e1.record(stream)
+    e1.synchronize()
+    pers_ms = e0.elapsed_time(e1)
     d.close()
     # one context per scene, run one after another (setup outside the timed regions)
     sep_ms = []
@@ -724,7 +737,7 @@ def batch_leg(L, scs, b, K, W, stream, sched, clocks=None, world=1, local=0):
     sep_ms = np.array(sep_ms)
     queue_ms = np.cumsum(sep_ms)   # completion time of each scene when served one after another
     n = len(scs)
-    return {"ms": ms, "f0": f0, "fK": fK, "launches": launches, "clocks": ck,
+    return {"ms": ms, "f0": f0, "fK": fK, "launches": launches, "clocks": ck, "persistent_ms": pers_ms,
             "scenes_per_s": world * n / (ms / 1e3), "obs_updates_per_s": world * b.nnz * K / (ms / 1e3),
             "separate": {"value": n / (sep_ms.sum() / 1e3), "unit": "scenes/s",
                          "isolated_ms": {"p50": float(np.percentile(sep_ms, 50)),
@@ -769,6 +782,8 @@ def run_batch(args, rank, world, local):
         "obs_updates_per_s": r["obs_updates_per_s"],
         "schedule": {"chosen": sched, "ms_per_iteration_tried": tried},
         "latency_ms": {"p50": ms, "p99": ms, "note": "every scene of the batch completes with the batch"},
+        "persistent": {"ms_per_batch": r["persistent_ms"], "scenes_per_s": world * n / (r["persistent_ms"] / 1e3),
+                       "what": "the same iterations as one cooperative launch (daba_set_persistent)"},
         "separate": r["separate"],
         "objective_px2": {"initial_sum": float(r["f0"].sum()), "final_sum": float(r["fK"].sum()),
                           "scenes_decreased": int((r["fK"] < r["f0"]).sum())},
