@@ -173,7 +173,8 @@ def test_duba_with_blocks_is_monotone(n_blocks):
 
 
 def test_noise_free_and_truth_with_blocks():
-    sc = cached_scene("circle", noise_free=True)
+    from paper_2305_07026_b300 import scenes
+    sc = scenes.circle_scene(n_lms=240, noise_free=True)
     part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 4)
     res = B.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, part, O.Options(loss="trivial"), 40)
     assert res.trace_px2[-1] < 1e-3 * res.trace_px2[0]
