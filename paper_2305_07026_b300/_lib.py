@@ -59,6 +59,8 @@ _SIGS = {
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
     "daba_set_wait_limit": (_st, [_p, _i64]),
     "daba_set_persistent": (_st, [_p, ctypes.c_int]),
+    "daba_set_partition": (_st, [_p, _i32, _p, _p]),
+    "daba_get_partition_metrics": (_st, [_p, _p, _p, _p, _p]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
@@ -251,6 +253,23 @@ class Daba:
     def import_checkpoint(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(daba_import_checkpoint(self._h, buf, len(data)))
+
+    def set_partition(self, cam_block=None, lm_block=None):
+        """Coarse blocks (one camera per block with the landmarks of lm_block); None clears."""
+        if cam_block is None:
+            self._check(daba_set_partition(self._h, 0, None, None))
+            self.n_blocks = 0
+            return
+        cb = np.ascontiguousarray(cam_block, dtype=np.int32)
+        lb = np.ascontiguousarray(lm_block, dtype=np.int32)
+        self._check(daba_set_partition(self._h, int(cb.size), ptr(cb), ptr(lb)))
+        self.n_blocks = int(cb.size)
+
+    def get_partition_metrics(self, stream=None):
+        F, Fb, rs = np.zeros(self.n_blocks), np.zeros(self.n_blocks), np.zeros(self.n_blocks, np.uint8)
+        self._check(daba_get_partition_metrics(self._h, ptr(F), ptr(Fb), ptr(rs),
+                                               current_stream() if stream is None else stream))
+        return F, Fb, rs
 
     def set_persistent(self, enable=True):
         self._check(daba_set_persistent(self._h, int(bool(enable))))

@@ -19,6 +19,7 @@
 #include "daba_kernels.cuh"
 #include "daba_state.cuh"
 #include "daba_adjoint.cuh"
+#include "daba_blocks.cuh"
 
 using namespace daba;
 
@@ -115,6 +116,11 @@ struct daba_ctx {
   // persistent path (daba_set_persistent): a run's iterations in one cooperative launch
   bool persistent = false;
   void* d_gbar = nullptr;   // grid-barrier counter and generation
+  // coarse blocks (daba_set_partition): one camera per block with any landmarks, FP64
+  int n_blocks = 0;
+  void *c_intra = nullptr, *blk_cam = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr, *blk_obs = nullptr,
+       *blk_sums = nullptr, *blk_scr = nullptr, *blk_E = nullptr, *blk_Fbar = nullptr, *blk_F = nullptr,
+       *blk_rs = nullptr, *blk_bk = nullptr;
 };
 
 namespace {
@@ -339,6 +345,7 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   O.lm_Fbdiag = (double*)ctx->lm_Fbd;
   O.lm_alt = (V4<Real>*)ctx->lm_alt;
   O.lm_sums = (double*)ctx->lm_sums_out;
+  O.blk_sums = ctx->n_blocks > 0 ? (double*)ctx->blk_sums : nullptr;
   const int caps[2] = {ctx->opt.tile_obs, BIG_TILE_OBS};
   int t0 = 0;
   for (int c = 0; c < 2; ++c) {
@@ -408,6 +415,62 @@ cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
                                                   (double*)ctx->fin_blk, (unsigned int*)ctx->fin_ticket,
                                                   (double*)ctx->d_trace, (int*)ctx->d_rs, (int*)ctx->d_flag);
   return cudaGetLastError();
+}
+
+// coarse blocks: one iteration k (direct launches on st): the camera pass in block mode, the
+// landmark pass in sum mode, the block solves, the reduction
+template <int LOSS>
+cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  const IterParams P = iter_params(ctx);
+  const LossC<double> L = loss_consts<double>(ctx);
+  cudaError_t e;
+  if (ctx->n_chunks > 0) {
+    k_cpass_blk<LOSS><<<ctx->n_chunks, CPASS_WARPS * 32, 0, st>>>(
+        ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+        (const double2*)ctx->c_u, (const V4<double>*)pack_at(ctx, k), (const V4<double>*)lmrec_at(ctx, k), L, P,
+        (double*)ctx->chunk_part, (const int*)ctx->c_rpos, (V4<double>*)ctx->rec_a, (V4<double>*)ctx->rec_b,
+        (double2*)ctx->rec_c, (const uint8_t*)ctx->c_intra);
+    ctx->launches++;
+  }
+  if ((e = launch_lpass(ctx, st, k)) != cudaSuccess) return e;   // sum mode while blk_sums is set
+  BlkArgs A;
+  A.S = ctx->n_blocks;
+  A.blk_cam = (const int*)ctx->blk_cam;
+  A.blk_lm_ptr = (const int*)ctx->blk_lm_ptr;
+  A.blk_lms = (const int*)ctx->blk_lms;
+  A.blk_obs = (const int*)ctx->blk_obs;
+  A.c_lm = (const int*)ctx->c_lm;
+  A.c_u = (const double2*)ctx->c_u;
+  A.cam_chunk_ptr = (const int*)ctx->cam_chunk_ptr;
+  A.part = (const double*)ctx->chunk_part;
+  A.lm_sums = (const double*)ctx->blk_sums;
+  A.cam_x = (double*)ctx->cam_x;
+  A.cam_dx = (double*)ctx->cam_dx;
+  A.cam_Rbar = (double*)ctx->cam_Rbar;
+  A.cam_Fsum = (double*)ctx->cam_Fsum;
+  A.cam_rs = (uint8_t*)ctx->cam_rs;
+  A.lmrec = (const V4<double>*)lmrec_at(ctx, k);
+  A.lmrec_out = (V4<double>*)lmrec_at(ctx, k + 1);
+  A.blk_E = (double*)ctx->blk_E;
+  A.blk_Fbar = (double*)ctx->blk_Fbar;
+  A.blk_F = (double*)ctx->blk_F;
+  A.blk_rs = (uint8_t*)ctx->blk_rs;
+  A.scr = (double*)ctx->blk_scr;
+  A.pack_next = (V4<double>*)pack_at(ctx, k + 1);
+  A.L = L;
+  k_blk_solve<<<(ctx->n_blocks + 3) / 4, 128, 0, st>>>(A, P, (int)LOSS);
+  ctx->launches++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_finalize(ctx, st);
+}
+
+cudaError_t launch_blk_iter(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+  switch (ctx->opt.loss) {
+    case DABA_LOSS_TRIVIAL: return launch_blk_iter_t<LOSS_TRIVIAL>(ctx, st, k);
+    case DABA_LOSS_HUBER: return launch_blk_iter_t<LOSS_HUBER>(ctx, st, k);
+    case DABA_LOSS_CAUCHY: return launch_blk_iter_t<LOSS_CAUCHY>(ctx, st, k);
+    default: return launch_blk_iter_t<LOSS_WELSCH>(ctx, st, k);
+  }
 }
 
 // persistent path: n iterations from iteration index k0 as one cooperative launch on st (after
@@ -1323,6 +1386,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_scene_cam.clear();
   ctx->n_scenes = 1;
   ctx->obs_set = true;
+  ctx->n_blocks = 0;   // a partition refers to the previous observations' numbering
   ctx->checked = false;
   if (ctx->state_set) {
     std::vector<double> cams((size_t)M * 9);
@@ -1415,12 +1479,25 @@ daba_status daba_run(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* r
   const double s0 = ctx->s_k;
   const bool lm_too = iters > 1;
   CK(backup_copy(ctx, true, k0, lm_too, st));
+  const size_t nb = (size_t)ctx->n_blocks;
+  if (nb) {   // coarse blocks: their E, Fbar, F and restart flags too
+    CK(cudaMemcpyAsync(ctx->blk_bk, ctx->blk_E, nb * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)ctx->blk_bk + nb * 8, ctx->blk_Fbar, nb * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)ctx->blk_bk + nb * 16, ctx->blk_F, nb * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)ctx->blk_bk + nb * 24, ctx->blk_rs, nb, cudaMemcpyDeviceToDevice, st));
+  }
   s = run_iterations(ctx, iters, obj_trace, restarts, st);
   if (s != DABA_OK) {
     const std::string why = ctx->err;
     ctx->k = k0;
     ctx->s_k = s0;
     cudaError_t e = backup_copy(ctx, false, k0, lm_too, st);
+    if (nb) {
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->blk_E, ctx->blk_bk, nb * 8, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->blk_Fbar, (char*)ctx->blk_bk + nb * 8, nb * 8, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->blk_F, (char*)ctx->blk_bk + nb * 16, nb * 8, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->blk_rs, (char*)ctx->blk_bk + nb * 24, nb, cudaMemcpyDeviceToDevice, st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
       return fail(ctx, s, "%s (restoring the entry state also failed: %s)", why.c_str(), cudaGetErrorString(e));
@@ -1458,7 +1535,10 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(ctx->s_dev, &s_start, 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st));
     size_t evi = 0;
-    if (ctx->persistent) {   // the prepare kernel, then every iteration of the segment in one cooperative launch
+    if (ctx->n_blocks > 0) {   // coarse blocks: the prepare kernel, then direct launches per iteration
+      CK(launch_prepare(ctx, st, ctx->k));
+      for (int j = 0; j < seg; ++j) CK(launch_blk_iter(ctx, st, ctx->k + j));
+    } else if (ctx->persistent) {   // the prepare kernel, then every iteration of the segment in one cooperative launch
       CK(launch_prepare(ctx, st, ctx->k));
       CK(launch_persistent(ctx, st, ctx->k, seg));
     } else if (ctx->timing && seg > RUN_GRAPH_MAX) {   // direct launches with per-kernel events
@@ -1494,7 +1574,7 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
     CK(cudaMemcpyAsync(rs.data() + done, ctx->d_rs, seg * 4, cudaMemcpyDeviceToHost, st));
     if (ctx->opt.momentum_reset) CK(cudaMemcpyAsync(&ctx->s_k, ctx->s_dev, 8, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (ctx->timing && !ctx->persistent) {
+    if (ctx->timing && !ctx->persistent && ctx->n_blocks == 0) {
       float ms = 0.f;
       auto elapsed = [&](size_t a, size_t b) {
         if (cudaEventElapsedTime(&ms, ctx->events[a], ctx->events[b]) == cudaSuccess) return true;
@@ -1667,6 +1747,7 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   if (K < 1) return fail(ctx, DABA_ERR_ARG, "K must be >= 1");
   if (!seed_cams || !seed_lms) return fail(ctx, DABA_ERR_ARG, "null seed pointer");
   if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient needs an FP64 context");
+  if (ctx->n_blocks) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient covers one block per camera and landmark");
   if (ctx->opt.momentum_reset)
     return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
   if (ctx->opt.cam_solver != DABA_CAM_SCAM)
@@ -1909,6 +1990,7 @@ size_t ckpt_bytes(const daba_ctx* c) {
 daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
   if (!ctx || !bytes) return DABA_ERR_ARG;
   if (!ctx->state_set) return fail(ctx, DABA_ERR_STATE, "state not set");
+  if (ctx->n_blocks) return fail(ctx, DABA_ERR_STATE, "checkpoints cover one block per camera and landmark only");
   const size_t need = ckpt_bytes(ctx);
   if (!buf) {
     *bytes = need;
@@ -1942,6 +2024,7 @@ daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
 
 daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes) {
   if (!ctx || !buf) return DABA_ERR_ARG;
+  if (ctx->n_blocks) return fail(ctx, DABA_ERR_STATE, "checkpoints cover one block per camera and landmark only");
   if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations must be set before importing a checkpoint");
   if (bytes < ckpt_bytes(ctx)) return fail(ctx, DABA_ERR_ARG, "checkpoint too small");
   CkptHeader h;
@@ -1970,6 +2053,105 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
   ctx->state_set = true;
   // host copies used by the Assumption 2 check: rebuild from the imported iterate
   ctx->checked = true;
+  return DABA_OK;
+}
+
+daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* cam_block, const int32_t* lm_block) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations must be set first");
+  if (n_blocks == 0) {   // back to one block per camera and per landmark
+    ctx->n_blocks = 0;
+    return DABA_OK;
+  }
+  if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "coarse blocks run on FP64 contexts");
+  if (ctx->opt.restart_mode != DABA_RESTART_BLOCK)
+    return fail(ctx, DABA_ERR_ARG, "coarse blocks use the per-block restart of Algorithm 1");
+  const int M = ctx->M, N = ctx->N;
+  if (n_blocks != M || !cam_block || !lm_block)
+    return fail(ctx, DABA_ERR_ARG, "every block holds one camera: n_blocks must be M, with both block arrays given");
+  std::vector<int32_t> cb(M), lb(N);
+  daba_status s;
+  if ((s = fetch(ctx, cb.data(), cam_block, (size_t)M * 4, nullptr)) != DABA_OK) return s;
+  if ((s = fetch(ctx, lb.data(), lm_block, (size_t)N * 4, nullptr)) != DABA_OK) return s;
+  std::vector<int32_t> blk_cam(n_blocks, -1);
+  for (int i = 0; i < M; ++i) {
+    if (cb[i] < 0 || cb[i] >= n_blocks || blk_cam[cb[i]] >= 0)
+      return fail(ctx, DABA_ERR_ARG, "cam_block must give every block exactly one camera (camera %d)", i);
+    blk_cam[cb[i]] = i;
+  }
+  for (int j = 0; j < N; ++j)
+    if (lb[j] < 0 || lb[j] >= n_blocks) return fail(ctx, DABA_ERR_ARG, "lm_block[%d] out of range", j);
+  // owned landmarks per block in internal numbering, and the intra pair of each (camera-sorted
+  // position), at most one per landmark
+  const int64_t n = ctx->nnz;
+  std::vector<uint8_t> intra(n, 0);
+  std::vector<int32_t> lm_obs(N, -1);
+  for (int64_t o = 0; o < n; ++o) {
+    const int32_t in = ctx->h_ci_order[o];   // input index of the camera-sorted observation o
+    const int i = ctx->h_cam_idx[in], j = ctx->h_lm_idx[in];
+    if (cb[i] == lb[j]) {
+      const int ji = (int)lm_internal(ctx, j);
+      if (lm_obs[ji] >= 0) return fail(ctx, DABA_ERR_ARG, "camera %d observes landmark %d twice", i, j);
+      lm_obs[ji] = (int32_t)o;
+      intra[o] = 1;
+    }
+  }
+  std::vector<int32_t> ptr(n_blocks + 1, 0), lms(N), obs(N);
+  for (int ji = 0; ji < N; ++ji) ptr[lb[ctx->h_lperm[ji]] + 1]++;
+  for (int b = 0; b < n_blocks; ++b) ptr[b + 1] += ptr[b];
+  std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
+  for (int ji = 0; ji < N; ++ji) {   // ascending internal id within each block
+    const int b = lb[ctx->h_lperm[ji]];
+    lms[pos[b]] = ji;
+    obs[pos[b]++] = lm_obs[ji];
+  }
+  if (!ctx->c_intra) {
+    if ((s = dalloc(ctx, &ctx->c_intra, (size_t)n)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_cam, (size_t)M * 4)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_lm_ptr, (size_t)(M + 1) * 4)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_lms, (size_t)N * 4)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_obs, (size_t)N * 4)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_sums, (size_t)N * LS_N * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_scr, (size_t)N * BS_N * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_E, (size_t)M * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_Fbar, (size_t)M * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_F, (size_t)M * 8)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_rs, (size_t)M)) != DABA_OK) return s;
+    if ((s = dalloc(ctx, &ctx->blk_bk, (size_t)M * 32)) != DABA_OK) return s;
+  }
+  CK(cudaMemcpy(ctx->c_intra, intra.data(), (size_t)n, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_cam, blk_cam.data(), (size_t)M * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_lm_ptr, ptr.data(), (size_t)(M + 1) * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_lms, lms.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_obs, obs.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemset(ctx->blk_rs, 0, (size_t)M));
+  ctx->n_blocks = n_blocks;
+  drop_graphs(ctx);
+  return DABA_OK;
+}
+
+daba_status daba_get_partition_metrics(daba_ctx* ctx, double* F_blk, double* Fbar_blk, uint8_t* rs_blk, void* stream) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (ctx->n_blocks == 0) return fail(ctx, DABA_ERR_STATE, "no partition set");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int S = ctx->n_blocks;
+  const double s2 = ctx->s_norm * ctx->s_norm;
+  std::vector<double> h(S);
+  daba_status s;
+  for (int q = 0; q < 2; ++q) {
+    double* dst = q == 0 ? F_blk : Fbar_blk;
+    if (!dst) continue;
+    CK(cudaMemcpyAsync(h.data(), q == 0 ? ctx->blk_F : ctx->blk_Fbar, (size_t)S * 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (double& v : h) v *= s2;
+    if ((s = deliver(ctx, dst, h.data(), (size_t)S * 8, st)) != DABA_OK) return s;
+  }
+  if (rs_blk) {
+    std::vector<uint8_t> r(S);
+    CK(cudaMemcpyAsync(r.data(), ctx->blk_rs, (size_t)S, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((s = deliver(ctx, rs_blk, r.data(), (size_t)S, st)) != DABA_OK) return s;
+  }
   return DABA_OK;
 }
 

@@ -38,7 +38,8 @@ namespace daba {
 enum { CP_HB = 0, CP_BB = 21, CP_H = 39, CP_B = 60, CP_F = 78, CP_G = 79, CP_NACC = 80 };
 // ---- chunk partial in memory (pass precision), each statistics set padded to 40 so that
 //      it starts on a 16-byte boundary: [Hbar Bbar pad] [H B pad] sumF sumGap pad pad
-enum { PART_XB = 0, PART_XK = 40, PART_F = 80, PART_G = 81, CP_STRIDE = 84 };
+enum { PART_XB = 0, PART_XK = 40, PART_F = 80, PART_G = 81, PART_FI = 82, CP_STRIDE = 84 };
+// (PART_FI: with coarse blocks, the F_ij sum of the chunk's intra-block pairs)
 __host__ __device__ constexpr int part_slot(int k) { return k < 39 ? k : (k < 78 ? k + 1 : k + 2); }
 // ---- tile partial layout (doubles): sumF restarts pad pad
 enum { TP_F = 0, TP_RS = 1, TP_STRIDE = 4 };
@@ -143,12 +144,18 @@ __device__ __forceinline__ void accumulate_cam(Real* acc, const ObsEval<Real>& e
 template <class Real>
 struct CamAcc {
   Real a[CP_NACC];
+  Real fi;   // coarse blocks: F_ij of the intra-block pairs
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < CP_NACC; ++k) a[k] = Real(0);
+    fi = Real(0);
   }
   __device__ __forceinline__ void add(const ObsEval<Real>& ev, Real u0, Real u1) { accumulate_cam<Real>(a, ev, u0, u1); }
-  __device__ __forceinline__ void reduce_store(int lane, Real* out) {
+  __device__ __forceinline__ void add_intra(Real F) {
+    a[CP_F] += F;
+    fi += F;
+  }
+  __device__ __forceinline__ void reduce_store(int lane, Real* out, bool with_fi = false) {
 #pragma unroll
     for (int k = 0; k < CP_NACC; ++k) {
       Real v = a[k];
@@ -156,10 +163,15 @@ struct CamAcc {
       for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       a[k] = v;
     }
+    if (with_fi) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) fi += __shfl_xor_sync(0xffffffffu, fi, off);
+    }
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < CP_NACC; ++k) out[part_slot(k)] = a[k];
-      out[39] = out[79] = out[82] = out[83] = Real(0);
+      out[39] = out[79] = out[83] = Real(0);
+      out[PART_FI] = with_fi ? fi : Real(0);
     }
   }
 };
@@ -337,14 +349,15 @@ __device__ __forceinline__ T ld_mut(const T* p) {
 
 // One chunk of the camera-sorted pass (camera chunk_cam[warp], observations chunk_beg[warp] ..
 // chunk_beg[warp + 1]) by one warp; gamma of Eq. nesterov_x for this iteration.
-template <int LOSS, class Real, class Real2, bool COH>
+template <int LOSS, class Real, class Real2, bool COH, bool BLK = false>
 __device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Real, Real2>& sm, Real gamma,
                                             const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
                                             const int* __restrict__ c_lm, const Real2* __restrict__ c_u,
                                             const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec,
                                             const LossC<Real>& L, Real* __restrict__ part,
                                             const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a,
-                                            V4<Real>* __restrict__ rec_b, typename RecC<Real>::type* __restrict__ rec_c) {
+                                            V4<Real>* __restrict__ rec_b, typename RecC<Real>::type* __restrict__ rec_c,
+                                            const uint8_t* __restrict__ c_intra = nullptr) {
   const int cam = chunk_cam[warp];
   const int b = chunk_beg[warp], e = chunk_beg[warp + 1];
   if (lane < P4N) sm.pk[lane] = ld_mut<COH>(pack + (size_t)cam * P4N + lane);
@@ -387,6 +400,18 @@ __device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Re
       ObsEval<Real> ev;
       eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
+      if constexpr (BLK) {   // coarse blocks: an intra pair keeps its exact F_ij, no statistics or record
+        if (c_intra[o]) {
+          acc.add_intra(Real(0.5) * ev.rho);
+          const int rp = sm.srp[t % CPASS_STAGES][lane];
+          V4<Real> z;
+          z.x = z.y = z.z = z.w = Real(0);
+          rec_a[rp] = z;
+          rec_b[rp] = z;
+          rec_c[rp] = RecC<Real>::make(Real(0), Real(0));
+          return;
+        }
+      }
       acc.add(ev, uu.x, uu.y);
       const Real wlb = ev.wb * ev.lamb, wl = ev.w * ev.lam;
       V4<Real> ra, rb;
@@ -423,7 +448,10 @@ __device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Re
   cp_async_wait<0>();
   // warp reduction; the partial is stored in the pass precision and summed over the
   // camera's chunks in FP64 by the camera solve
-  acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE);
+  if constexpr (BLK)
+    acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE, true);
+  else
+    acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE);
 }
 
 template <int LOSS, class Real, class Real2>
@@ -440,6 +468,24 @@ __global__ void __launch_bounds__(CPASS_WARPS * 32)
   if (warp >= n_chunks) return;
   cpass_chunk<LOSS, Real, Real2, false>(warp, lane, sm[wib], Real(P.gam[*P.it]), chunk_cam, chunk_beg, c_lm, c_u,
                                         pack, lmrec, L, part, c_rpos, rec_a, rec_b, rec_c);
+}
+
+// The camera pass with coarse blocks (FP64): c_intra[o] marks the camera-sorted observations
+// whose camera and landmark share a block.
+template <int LOSS>
+__global__ void __launch_bounds__(CPASS_WARPS * 32)
+    k_cpass_blk(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
+                const int* __restrict__ c_lm, const double2* __restrict__ c_u, const V4<double>* __restrict__ pack,
+                const V4<double>* __restrict__ lmrec, LossC<double> L, IterParams P, double* __restrict__ part,
+                const int* __restrict__ c_rpos, V4<double>* __restrict__ rec_a, V4<double>* __restrict__ rec_b,
+                double2* __restrict__ rec_c, const uint8_t* __restrict__ c_intra) {
+  __shared__ CpassWarpSmem<double, double2> sm[CPASS_WARPS];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * CPASS_WARPS + wib;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_chunks) return;
+  cpass_chunk<LOSS, double, double2, false, true>(warp, lane, sm[wib], P.gam[*P.it], chunk_cam, chunk_beg, c_lm, c_u,
+                                                 pack, lmrec, L, part, c_rpos, rec_a, rec_b, rec_c, c_intra);
 }
 
 // ---------------------------------------------------------------------------
@@ -550,6 +596,7 @@ struct LpassOut {
   double* lm_Fbdiag;
   V4<Real>* lm_alt;
   double* lm_sums;
+  double* blk_sums;   // coarse blocks: the 10 sums of every landmark, nothing else (sum mode)
 };
 
 // One landmark of the landmark pass: sums its records (slots s0 .. s1 of the tile, through the
@@ -583,6 +630,11 @@ __device__ __forceinline__ int lpass_landmark(const V4<Real>* __restrict__ sca, 
     st[7] += b.w;
     st[8] += RecC<Real>::F(c);
     st[9] += RecC<Real>::gap(c);
+  }
+  if (O.blk_sums) {   // coarse blocks: the block solve takes it from here
+#pragma unroll
+    for (int k = 0; k < 10; ++k) O.blk_sums[g * 10 + k] = double(st[k]);
+    return 0;
   }
   const Real dl0 = A.w, dl1 = B.x, dl2 = B.y;
   // Eq. DEalpha, Eq. Fak, Eq. lFak in slack form (S = Fbar^(k-1) - E^(k)):
