@@ -589,14 +589,14 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
 // Outputs of the landmark pass (one set per launch).
 template <class Real>
 struct LpassOut {
-  V4<Real>* lmrec_out;
-  V4<float>* lm_lo_out;
-  uint8_t* lm_rs;
-  double* lm_Fdiag;
-  double* lm_Fbdiag;
-  V4<Real>* lm_alt;
-  double* lm_sums;
-  double* blk_sums;   // coarse blocks: the 10 sums of every landmark, nothing else (sum mode)
+  V4<Real>* lmrec_out = nullptr;
+  V4<float>* lm_lo_out = nullptr;
+  uint8_t* lm_rs = nullptr;
+  double* lm_Fdiag = nullptr;
+  double* lm_Fbdiag = nullptr;
+  V4<Real>* lm_alt = nullptr;
+  double* lm_sums = nullptr;
+  double* blk_sums = nullptr;   // coarse blocks: the 10 sums of every landmark, nothing else (sum mode)
 };
 
 // One landmark of the landmark pass: sums its records (slots s0 .. s1 of the tile, through the
