@@ -249,22 +249,26 @@ daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
 daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
 
 /* Coarse blocks (Sec. 4, Eq. Ealpha with E' not empty; FP64 contexts with the per-block restart):
- * block b holds camera i with cam_block[i] = b (every block exactly one camera, so n_blocks = M)
- * and the landmarks j with lm_block[j] = b (host or device int32 arrays, block ids in [0, M)). A
- * reprojection pair whose camera and landmark share a block keeps its exact F_ij in the block's
- * surrogate; every other pair is split by the majorizer of Proposition 1 into P_ij (camera's
- * block) and Q_ij (landmark's block). Each iteration of Algorithm 1 then takes, per block, one
- * successful Levenberg-Marquardt step on E^alpha(. | xbar^k) from xbar^k (Sec. 7.1 reports one
- * successful inner LM step per subproblem), the per-block restart test of Eq. Eak, and where it
- * fires the LM step on E^alpha(. | x^k) from x^k. LM step: R = R_z Exp(phi), t = t_z + tau,
- * d = d_z + delta, l = l_z + epsilon; Gauss-Newton model of the block surrogate (the intra pairs
- * reweighted with w = rho'(|e|^2) at z, the proximal term to second order); damping 1e-3 x diag,
- * raised tenfold up to 8 times; taken only if E^alpha(. | z) decreases; the camera's 9 x 9 Schur
- * complement is solved with every landmark's 3 x 3 block eliminated. The restart metrics of
- * Eqs. DEalpha-Eak are per block (daba_get_partition_metrics). A camera may observe each landmark
- * of its block at most once (DABA_ERR_ARG otherwise). Call after daba_set_observations (which
- * clears the partition); n_blocks = 0 returns to one block per camera and per landmark.
- * Checkpoints and the unrolled gradient are not available while a partition is set. */
+ * block b holds the cameras i with cam_block[i] = b (at most 8 per block, none allowed) and the
+ * landmarks j with lm_block[j] = b (host or device int32 arrays of M and N entries, block ids in
+ * [0, n_blocks), 1 <= n_blocks <= M + N). A reprojection pair whose camera and landmark share a
+ * block keeps its exact F_ij in the block's surrogate; every other pair is split by the majorizer
+ * of Proposition 1 into P_ij (camera's block) and Q_ij (landmark's block). Each iteration of
+ * Algorithm 1 then takes, per block, one successful Levenberg-Marquardt step on
+ * E^alpha(. | xbar^k) from xbar^k (Sec. 7.1 reports one successful inner LM step per
+ * subproblem), the per-block restart test of Eq. Eak, and where it fires the LM step on
+ * E^alpha(. | x^k) from x^k. LM step: R = R_z Exp(phi), t = t_z + tau, d = d_z + delta,
+ * l = l_z + epsilon; Gauss-Newton model of the block surrogate (the intra pairs reweighted with
+ * w = rho'(|e|^2) at z, the proximal term to second order); damping 1e-3 x diag, raised tenfold
+ * up to 8 times; taken only if E^alpha(. | z) decreases. The damped system is solved through the
+ * Schur complement of the block's cameras (9 per camera; every landmark's 3 x 3 block
+ * eliminated), one CTA per block. The restart metrics of Eqs. DEalpha-Eak are per block
+ * (daba_get_partition_metrics); the restart count of daba_run counts the blocks that hold a
+ * camera. A camera may observe each landmark of its block at most once (DABA_ERR_ARG otherwise,
+ * as for a block id out of range or a block of more than 8 cameras). Call after daba_set_observations (which clears the
+ * partition); n_blocks = 0 returns to one block per camera and per landmark (the arrays are then
+ * ignored). The device scratch grows with the partition: 448 bytes per intra pair, 248 per
+ * landmark. Checkpoints and the unrolled gradient are not available while a partition is set. */
 daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* cam_block, const int32_t* lm_block);
 
 /* Per-block metrics of the last iteration with a partition (each pointer may be NULL, n_blocks

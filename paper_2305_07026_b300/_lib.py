@@ -23,6 +23,7 @@ LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
 PREC = {"fp64": 0, "mixed": 1}
 RESTART = {"block": 0, "global": 1}
 CAM_SOLVERS = {"scam": 0, "lm": 1}
+BLK_MAX_CAMS = 8   # cameras per coarse block (daba_set_partition)
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_07026_b300.build`")
@@ -254,16 +255,20 @@ class Daba:
         buf = ctypes.create_string_buffer(data, len(data))
         self._check(daba_import_checkpoint(self._h, buf, len(data)))
 
-    def set_partition(self, cam_block=None, lm_block=None):
-        """Coarse blocks (one camera per block with the landmarks of lm_block); None clears."""
+    def set_partition(self, cam_block=None, lm_block=None, n_blocks=None):
+        """Coarse blocks: camera i in block cam_block[i] (at most BLK_MAX_CAMS per block), landmark
+        j in block lm_block[j]; n_blocks defaults to one more than the largest block id. None
+        clears (one block per camera and per landmark)."""
         if cam_block is None:
             self._check(daba_set_partition(self._h, 0, None, None))
             self.n_blocks = 0
             return
         cb = np.ascontiguousarray(cam_block, dtype=np.int32)
         lb = np.ascontiguousarray(lm_block, dtype=np.int32)
-        self._check(daba_set_partition(self._h, int(cb.size), ptr(cb), ptr(lb)))
-        self.n_blocks = int(cb.size)
+        if n_blocks is None:
+            n_blocks = int(max(cb.max(initial=-1), lb.max(initial=-1))) + 1
+        self._check(daba_set_partition(self._h, int(n_blocks), ptr(cb), ptr(lb)))
+        self.n_blocks = int(n_blocks)
 
     def get_partition_metrics(self, stream=None):
         F, Fb, rs = np.zeros(self.n_blocks), np.zeros(self.n_blocks), np.zeros(self.n_blocks, np.uint8)

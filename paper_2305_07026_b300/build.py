@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libdaba_b300.so")
 SOURCES = ["daba_abi.cu", "daba_noalloc.cu", "daba_probe.cu"]
-DEPS = ["daba_abi.cu", "daba_noalloc.cu", "daba_probe.cu", "daba_kernels.cuh", "daba_device.cuh", "daba_state.cuh", "daba_grad.cuh", "daba_adjoint.cuh"]
+DEPS = ["daba_abi.cu", "daba_noalloc.cu", "daba_probe.cu", "daba_kernels.cuh", "daba_device.cuh", "daba_state.cuh", "daba_grad.cuh", "daba_adjoint.cuh", "daba_blocks.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -116,11 +116,15 @@ struct daba_ctx {
   // persistent path (daba_set_persistent): a run's iterations in one cooperative launch
   bool persistent = false;
   void* d_gbar = nullptr;   // grid-barrier counter and generation
-  // coarse blocks (daba_set_partition): one camera per block with any landmarks, FP64
+  // coarse blocks (daba_set_partition): up to BLK_MAX_CAMS cameras and any landmarks per block,
+  // FP64; the buffers grow with the partition (blk_cap: bytes held per buffer)
   int n_blocks = 0;
-  void *c_intra = nullptr, *blk_cam = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr, *blk_obs = nullptr,
-       *blk_sums = nullptr, *blk_scr = nullptr, *blk_E = nullptr, *blk_Fbar = nullptr, *blk_F = nullptr,
-       *blk_rs = nullptr, *blk_bk = nullptr;
+  int blk_ld = 0;   // row stride of a block's Schur matrix: 9 x the most cameras in one block
+  void *c_intra = nullptr, *blk_cam_ptr = nullptr, *blk_cams = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr,
+       *blk_io_ptr = nullptr, *blk_io_cam = nullptr, *blk_io_obs = nullptr, *blk_ci_ptr = nullptr,
+       *blk_ci_obs = nullptr, *blk_ci_lm = nullptr, *blk_sums = nullptr, *blk_lsc = nullptr, *blk_isc = nullptr,
+       *blk_E = nullptr, *blk_Fbar = nullptr, *blk_F = nullptr, *blk_rs = nullptr, *blk_bk = nullptr;
+  std::vector<std::pair<void*, size_t>> blk_cap;
 };
 
 namespace {
@@ -161,6 +165,23 @@ daba_status dalloc(daba_ctx* ctx, void** p, size_t bytes) {
   }
   ctx->allocs.push_back(*p);
   return DABA_OK;
+}
+
+// *p holds at least `bytes` afterwards; a smaller buffer is freed and replaced (contents dropped)
+daba_status dgrow(daba_ctx* ctx, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  auto& cap = ctx->blk_cap;
+  auto it = std::find_if(cap.begin(), cap.end(), [&](const std::pair<void*, size_t>& c) { return c.first == *p; });
+  if (*p && it != cap.end() && it->second >= bytes) return DABA_OK;
+  if (*p) {
+    if (it != cap.end()) cap.erase(it);
+    ctx->allocs.erase(std::remove(ctx->allocs.begin(), ctx->allocs.end(), *p), ctx->allocs.end());
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  daba_status s = dalloc(ctx, p, bytes);
+  if (s == DABA_OK) cap.emplace_back(*p, bytes);
+  return s;
 }
 
 // copy `bytes` from a host or device source into host memory
@@ -435,11 +456,17 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   if ((e = launch_lpass(ctx, st, k)) != cudaSuccess) return e;   // sum mode while blk_sums is set
   BlkArgs A;
   A.S = ctx->n_blocks;
-  A.blk_cam = (const int*)ctx->blk_cam;
-  A.blk_lm_ptr = (const int*)ctx->blk_lm_ptr;
-  A.blk_lms = (const int*)ctx->blk_lms;
-  A.blk_obs = (const int*)ctx->blk_obs;
-  A.c_lm = (const int*)ctx->c_lm;
+  A.ld = ctx->blk_ld;
+  A.cam_ptr = (const int*)ctx->blk_cam_ptr;
+  A.cams = (const int*)ctx->blk_cams;
+  A.lm_ptr = (const int*)ctx->blk_lm_ptr;
+  A.lms = (const int*)ctx->blk_lms;
+  A.io_ptr = (const int*)ctx->blk_io_ptr;
+  A.io_cam = (const int*)ctx->blk_io_cam;
+  A.io_obs = (const int*)ctx->blk_io_obs;
+  A.ci_ptr = (const int*)ctx->blk_ci_ptr;
+  A.ci_obs = (const int*)ctx->blk_ci_obs;
+  A.ci_lm = (const int*)ctx->blk_ci_lm;
   A.c_u = (const double2*)ctx->c_u;
   A.cam_chunk_ptr = (const int*)ctx->cam_chunk_ptr;
   A.part = (const double*)ctx->chunk_part;
@@ -455,10 +482,12 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   A.blk_Fbar = (double*)ctx->blk_Fbar;
   A.blk_F = (double*)ctx->blk_F;
   A.blk_rs = (uint8_t*)ctx->blk_rs;
-  A.scr = (double*)ctx->blk_scr;
+  A.lsc = (double*)ctx->blk_lsc;
+  A.isc = (double*)ctx->blk_isc;
   A.pack_next = (V4<double>*)pack_at(ctx, k + 1);
   A.L = L;
-  k_blk_solve<<<(ctx->n_blocks + 3) / 4, 128, 0, st>>>(A, P, (int)LOSS);
+  A.loss = LOSS;
+  k_blk_solve<<<ctx->n_blocks, BLK_THREADS, (size_t)ctx->blk_ld * ctx->blk_ld * 8, st>>>(A, P);
   ctx->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_finalize(ctx, st);
@@ -2067,65 +2096,121 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   if (ctx->opt.restart_mode != DABA_RESTART_BLOCK)
     return fail(ctx, DABA_ERR_ARG, "coarse blocks use the per-block restart of Algorithm 1");
   const int M = ctx->M, N = ctx->N;
-  if (n_blocks != M || !cam_block || !lm_block)
-    return fail(ctx, DABA_ERR_ARG, "every block holds one camera: n_blocks must be M, with both block arrays given");
+  if (n_blocks < 0 || (int64_t)n_blocks > (int64_t)M + N || !cam_block || !lm_block)
+    return fail(ctx, DABA_ERR_ARG, "n_blocks must lie in 1 .. M + N, with both block arrays given");
+  const int S = n_blocks;
   std::vector<int32_t> cb(M), lb(N);
   daba_status s;
   if ((s = fetch(ctx, cb.data(), cam_block, (size_t)M * 4, nullptr)) != DABA_OK) return s;
   if ((s = fetch(ctx, lb.data(), lm_block, (size_t)N * 4, nullptr)) != DABA_OK) return s;
-  std::vector<int32_t> blk_cam(n_blocks, -1);
+  // cameras per block (ascending), their position in that list and their local index
+  std::vector<int32_t> cam_ptr(S + 1, 0), cams(M), cpos(M), cloc(M);
   for (int i = 0; i < M; ++i) {
-    if (cb[i] < 0 || cb[i] >= n_blocks || blk_cam[cb[i]] >= 0)
-      return fail(ctx, DABA_ERR_ARG, "cam_block must give every block exactly one camera (camera %d)", i);
-    blk_cam[cb[i]] = i;
+    if (cb[i] < 0 || cb[i] >= S) return fail(ctx, DABA_ERR_ARG, "cam_block[%d] out of range", i);
+    cam_ptr[cb[i] + 1]++;
   }
-  for (int j = 0; j < N; ++j)
-    if (lb[j] < 0 || lb[j] >= n_blocks) return fail(ctx, DABA_ERR_ARG, "lm_block[%d] out of range", j);
-  // owned landmarks per block in internal numbering, and the intra pair of each (camera-sorted
-  // position), at most one per landmark
+  int most = 0;
+  for (int b = 0; b < S; ++b) {
+    if (cam_ptr[b + 1] > BLK_MAX_CAMS)
+      return fail(ctx, DABA_ERR_ARG, "block %d holds %d cameras (at most %d)", b, cam_ptr[b + 1], BLK_MAX_CAMS);
+    most = std::max(most, cam_ptr[b + 1]);
+    cam_ptr[b + 1] += cam_ptr[b];
+  }
+  {
+    std::vector<int32_t> pos(cam_ptr.begin(), cam_ptr.end() - 1);
+    for (int i = 0; i < M; ++i) {
+      cloc[i] = pos[cb[i]] - cam_ptr[cb[i]];
+      cpos[i] = pos[cb[i]];
+      cams[pos[cb[i]]++] = i;
+    }
+  }
+  // landmarks per block (internal ids, ascending) and the position of each in that list
+  std::vector<int32_t> lm_ptr(S + 1, 0), lms(N), lpos(N);
+  for (int j = 0; j < N; ++j) {
+    if (lb[j] < 0 || lb[j] >= S) return fail(ctx, DABA_ERR_ARG, "lm_block[%d] out of range", j);
+  }
+  for (int ji = 0; ji < N; ++ji) lm_ptr[lb[ctx->h_lperm[ji]] + 1]++;
+  for (int b = 0; b < S; ++b) lm_ptr[b + 1] += lm_ptr[b];
+  {
+    std::vector<int32_t> pos(lm_ptr.begin(), lm_ptr.end() - 1);
+    for (int ji = 0; ji < N; ++ji) {
+      const int b = lb[ctx->h_lperm[ji]];
+      lpos[ji] = pos[b];
+      lms[pos[b]++] = ji;
+    }
+  }
+  // the intra pairs (E'), camera-sorted: per landmark entry by camera, per camera entry by observation
   const int64_t n = ctx->nnz;
   std::vector<uint8_t> intra(n, 0);
-  std::vector<int32_t> lm_obs(N, -1);
+  std::vector<int32_t> io_ptr(N + 1, 0), ci_ptr(M + 1, 0);
+  int64_t n_in = 0;
   for (int64_t o = 0; o < n; ++o) {
     const int32_t in = ctx->h_ci_order[o];   // input index of the camera-sorted observation o
     const int i = ctx->h_cam_idx[in], j = ctx->h_lm_idx[in];
-    if (cb[i] == lb[j]) {
-      const int ji = (int)lm_internal(ctx, j);
-      if (lm_obs[ji] >= 0) return fail(ctx, DABA_ERR_ARG, "camera %d observes landmark %d twice", i, j);
-      lm_obs[ji] = (int32_t)o;
-      intra[o] = 1;
+    if (cb[i] != lb[j]) continue;
+    intra[o] = 1;
+    io_ptr[lpos[lm_internal(ctx, j)] + 1]++;
+    ci_ptr[cpos[i] + 1]++;
+    n_in++;
+  }
+  for (int e = 0; e < N; ++e) io_ptr[e + 1] += io_ptr[e];
+  for (int e = 0; e < M; ++e) ci_ptr[e + 1] += ci_ptr[e];
+  std::vector<int32_t> io_cam(n_in), io_obs(n_in), ci_obs(n_in), ci_lm(n_in);
+  {
+    std::vector<int32_t> ip(io_ptr.begin(), io_ptr.end() - 1), cp(ci_ptr.begin(), ci_ptr.end() - 1);
+    for (int64_t o = 0; o < n; ++o) {
+      if (!intra[o]) continue;
+      const int32_t in = ctx->h_ci_order[o];
+      const int i = ctx->h_cam_idx[in], j = ctx->h_lm_idx[in];
+      const int ji = (int)lm_internal(ctx, j), e = lpos[ji];
+      // observations run by camera, so a landmark's pairs arrive by ascending camera
+      if (ip[e] > io_ptr[e] && io_cam[ip[e] - 1] == cloc[i])
+        return fail(ctx, DABA_ERR_ARG, "camera %d observes landmark %d twice inside a block", i, j);
+      io_cam[ip[e]] = cloc[i];
+      io_obs[ip[e]++] = (int32_t)o;
+      ci_lm[cp[cpos[i]]] = ji;
+      ci_obs[cp[cpos[i]]++] = (int32_t)o;
     }
   }
-  std::vector<int32_t> ptr(n_blocks + 1, 0), lms(N), obs(N);
-  for (int ji = 0; ji < N; ++ji) ptr[lb[ctx->h_lperm[ji]] + 1]++;
-  for (int b = 0; b < n_blocks; ++b) ptr[b + 1] += ptr[b];
-  std::vector<int32_t> pos(ptr.begin(), ptr.end() - 1);
-  for (int ji = 0; ji < N; ++ji) {   // ascending internal id within each block
-    const int b = lb[ctx->h_lperm[ji]];
-    lms[pos[b]] = ji;
-    obs[pos[b]++] = lm_obs[ji];
-  }
-  if (!ctx->c_intra) {
-    if ((s = dalloc(ctx, &ctx->c_intra, (size_t)n)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_cam, (size_t)M * 4)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_lm_ptr, (size_t)(M + 1) * 4)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_lms, (size_t)N * 4)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_obs, (size_t)N * 4)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_sums, (size_t)N * LS_N * 8)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_scr, (size_t)N * BS_N * 8)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_E, (size_t)M * 8)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_Fbar, (size_t)M * 8)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_F, (size_t)M * 8)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_rs, (size_t)M)) != DABA_OK) return s;
-    if ((s = dalloc(ctx, &ctx->blk_bk, (size_t)M * 32)) != DABA_OK) return s;
-  }
+  const int ld = 9 * most;
+  const size_t smem = (size_t)ld * ld * 8;
+  CK(cudaFuncSetAttribute(k_blk_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t ni = (size_t)n_in;
+  if ((s = dgrow(ctx, &ctx->c_intra, (size_t)n)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_cam_ptr, (size_t)(S + 1) * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_cams, (size_t)M * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_lm_ptr, (size_t)(S + 1) * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_lms, (size_t)N * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_io_ptr, (size_t)(N + 1) * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_io_cam, ni * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_io_obs, ni * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_ci_ptr, (size_t)(M + 1) * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_ci_obs, ni * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_ci_lm, ni * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_sums, (size_t)N * LS_N * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_lsc, (size_t)N * BL_N * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_isc, ni * BI_N * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_E, (size_t)S * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_Fbar, (size_t)S * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_F, (size_t)S * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_rs, (size_t)S)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_bk, (size_t)S * 32)) != DABA_OK) return s;
   CK(cudaMemcpy(ctx->c_intra, intra.data(), (size_t)n, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->blk_cam, blk_cam.data(), (size_t)M * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->blk_lm_ptr, ptr.data(), (size_t)(M + 1) * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_cam_ptr, cam_ptr.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_cams, cams.data(), (size_t)M * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_lm_ptr, lm_ptr.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->blk_lms, lms.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(ctx->blk_obs, obs.data(), (size_t)N * 4, cudaMemcpyHostToDevice));
-  CK(cudaMemset(ctx->blk_rs, 0, (size_t)M));
-  ctx->n_blocks = n_blocks;
+  CK(cudaMemcpy(ctx->blk_io_ptr, io_ptr.data(), (size_t)(N + 1) * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->blk_ci_ptr, ci_ptr.data(), (size_t)(M + 1) * 4, cudaMemcpyHostToDevice));
+  if (ni) {
+    CK(cudaMemcpy(ctx->blk_io_cam, io_cam.data(), ni * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_io_obs, io_obs.data(), ni * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_ci_obs, ci_obs.data(), ni * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_ci_lm, ci_lm.data(), ni * 4, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemset(ctx->blk_rs, 0, (size_t)S));
+  ctx->n_blocks = S;
+  ctx->blk_ld = ld;
   drop_graphs(ctx);
   return DABA_OK;
 }

@@ -1,38 +1,48 @@
 // daba_blocks.cuh -- Algorithm 1 with coarse blocks (Eq. Ealpha with E' not empty), FP64.
 //
-// A block holds at most one camera and any set of landmarks. Pairs whose camera and landmark
-// share a block (E') keep their exact F_ij in the block surrogate; the others are split by the
-// majorizer of Proposition 1. Per iteration:
+// A block holds up to BLK_MAX_CAMS cameras and any set of landmarks. Pairs whose camera and
+// landmark share a block (E') keep their exact F_ij in the block surrogate; the others are split
+// by the majorizer of Proposition 1. Per iteration:
 //   1. the camera pass in block mode (k_cpass_blk): as k_cpass, but an intra pair adds to no
 //      statistics, gap or landmark record; it adds F_ij to the camera's F sums;
 //   2. the landmark pass in sum mode: every landmark's sums of its inter records (a, b at x̄^k
 //      and at x^k, F_ij and the surrogate gap);
-//   3. k_blk_solve, one warp per block: the restart metrics (Eqs. DEalpha, Fak, lFak), one
+//   3. k_blk_solve, one CTA per block: the restart metrics (Eqs. DEalpha, Fak, lFak), one
 //      successful Levenberg-Marquardt step on E^alpha(. | x̄^k) from x̄^k, the restart test
 //      (Eq. Eak) and, where it fires, the LM step on E^alpha(. | x^k) from x^k.
-// LM step: parameters (phi, tau, delta) of the camera (R = R_z Exp(phi), t = t_z + tau,
-// d = d_z + delta) and epsilon of each landmark (l = l_z + epsilon). Gauss-Newton model: the
-// camera's inter pairs and proximal term from its statistics (cam_lm_model); each landmark's
-// inter pairs 2 a I and 2 b, proximal xi I; each intra pair the reweighted Gauss-Newton terms of
+// LM step: parameters (phi, tau, delta) of each camera (R = R_z Exp(phi), t = t_z + tau,
+// d = d_z + delta) and epsilon of each landmark (l = l_z + epsilon). Gauss-Newton model: each
+// camera's inter pairs and proximal term from its statistics (cam_lm_model); each landmark's inter
+// pairs 2 a I and 2 b, proximal xi I; each intra pair the reweighted Gauss-Newton terms of
 // R e = (I - q q^T/|q|^2) R p with w = rho'(|e|^2) at z. The damped system (H + mu diag H) is
-// solved through the 9 x 9 Schur complement of the camera (each landmark's 3 x 3 block
-// eliminated); the step is taken if E^alpha decreases (surrogate differences term by term),
-// otherwise mu grows tenfold, at most LM_TRIES times.
+// solved through the Schur complement of the cameras (9 per camera, every landmark's 3 x 3 block
+// eliminated; dense Cholesky in shared memory); the step is taken if E^alpha decreases
+// (surrogate differences term by term), otherwise mu grows tenfold, at most LM_TRIES times.
+// Every sum runs in a fixed order, so results do not depend on the schedule.
 #pragma once
 
 #include "daba_kernels.cuh"
 
 namespace daba {
 
+constexpr int BLK_MAX_CAMS = 8;
+constexpr int BLK_NP = 9 * BLK_MAX_CAMS;   // camera parameters of a block
+constexpr int BLK_THREADS = 128;
+
 // landmark sums written by the landmark pass in sum mode (per internal landmark)
 enum { LS_AB = 0, LS_BB = 1, LS_AK = 4, LS_BK = 5, LS_F = 8, LS_G = 9, LS_N = 10 };
-// per owned landmark scratch of the block solve
-enum { BS_C = 0, BS_G = 6, BS_B = 9, BS_FZ = 36, BS_L = 37, BS_N = 40 };
+// per landmark scratch of the block solve: C (packed), C^-1 of the damped system, gradient,
+// the solution, the F_ij at z of its intra pairs
+enum { BL_C = 0, BL_CI = 6, BL_G = 12, BL_L = 15, BL_FZ = 18, BL_N = 20 };
+// per intra pair scratch: B = w Jc^T Jl (9 x 3) and B C^-1
+enum { BI_B = 0, BI_BC = 27, BI_N = 54 };
 
 struct BlkArgs {
-  int S;
-  const int *blk_cam, *blk_lm_ptr, *blk_lms, *blk_obs;   // block camera (-1: none); owned landmarks; their intra pair (-1: none)
-  const int* c_lm;
+  int S, ld;                          // blocks; row stride of the Schur matrix (9 x the most cameras in a block)
+  const int *cam_ptr, *cams;          // cameras of each block (ascending)
+  const int *lm_ptr, *lms;            // landmarks of each block (internal ids, ascending)
+  const int *io_ptr, *io_cam, *io_obs;   // per landmark entry: its intra pairs (local camera, observation), by camera
+  const int *ci_ptr, *ci_obs, *ci_lm;    // per camera entry: its intra pairs (observation, landmark), by observation
   const double2* c_u;
   const int* cam_chunk_ptr;
   const double* part;
@@ -43,10 +53,24 @@ struct BlkArgs {
   V4<double>* lmrec_out;     // of iteration k + 1
   double *blk_E, *blk_Fbar, *blk_F;
   uint8_t* blk_rs;
-  double* scr;     // BS_N per internal landmark
+  double *lsc, *isc;   // BL_N per internal landmark, BI_N per intra pair
   V4<double>* pack_next;
   LossC<double> L;
+  int loss;
 };
+
+template <int LOSS>
+__device__ __forceinline__ void blk_rho(const LossC<double>& L, double r, double& rho, double& w) {
+  rho_w<LOSS, double>(L, r, rho, w);
+}
+__device__ __forceinline__ void blk_rho_any(int loss, const LossC<double>& L, double r, double& rho, double& w) {
+  switch (loss) {
+    case LOSS_TRIVIAL: blk_rho<LOSS_TRIVIAL>(L, r, rho, w); break;
+    case LOSS_HUBER: blk_rho<LOSS_HUBER>(L, r, rho, w); break;
+    case LOSS_CAUCHY: blk_rho<LOSS_CAUCHY>(L, r, rho, w); break;
+    default: blk_rho<LOSS_WELSCH>(L, r, rho, w); break;
+  }
+}
 
 // R e = (I - q q^T/|q|^2) R p and its Jacobian: Jc (3 x 9: phi, tau, delta) and Jl (3 x 3)
 __device__ inline void blk_intra_jac(const CamT<double>& c, const double* l, double u0, double u1, double* f,
@@ -71,7 +95,7 @@ __device__ inline void blk_intra_jac(const CamT<double>& c, const double* l, dou
       Pi[r][k] = (r == k ? 1.0 : 0.0) - q[r] * q[k] / qq;
       Dq[r][k] = (r == k ? -lam : 0.0) - q[r] * (v[k] - 2.0 * lam * q[k]) / qq;
     }
-  // -R [p]x, column k: -R (e_k x p)... [p]x = [[0,-p2,p1],[p2,0,-p0],[-p1,p0,0]]
+  // d(R Exp(phi) p)/dphi = -R [p]x with [p]x the cross-product matrix of p
   const double px[3][3] = {{0.0, -p[2], p[1]}, {p[2], 0.0, -p[0]}, {-p[1], p[0], 0.0}};
   double Mr[3][3];
 #pragma unroll
@@ -115,29 +139,15 @@ __device__ inline double blk_F(const CamT<double>& c, const double* l, double u0
     r2 += e * e;
   }
   double rho, w;
-  switch (loss) {
-    case LOSS_TRIVIAL: rho_w<LOSS_TRIVIAL, double>(L, r2, rho, w); break;
-    case LOSS_HUBER: rho_w<LOSS_HUBER, double>(L, r2, rho, w); break;
-    case LOSS_CAUCHY: rho_w<LOSS_CAUCHY, double>(L, r2, rho, w); break;
-    default: rho_w<LOSS_WELSCH, double>(L, r2, rho, w); break;
-  }
+  blk_rho_any(loss, L, r2, rho, w);
   return 0.5 * rho;
 }
 
-// sum over the warp, lane 0's result on every lane (the butterfly's lanes associate the sums in
-// different orders; the block's decisions must be the same on every lane)
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return __shfl_sync(0xffffffffu, v, 0);
-}
-
-// 3 x 3 symmetric (packed xx, yx, yy, zx, zy, zz) inverse
+// 3 x 3 symmetric (packed xx, yx, yy, zx, zy, zz) inverse and product
 __device__ __forceinline__ void sym3_inv(const double* C, double* I) {
   const double a = C[0], b = C[1], c = C[2], d = C[3], e = C[4], f = C[5];
   const double A0 = c * f - e * e, A1 = -(b * f - e * d), A3 = b * e - c * d;
-  const double det = a * A0 + b * A1 + d * A3;
-  const double id = 1.0 / det;
+  const double id = 1.0 / (a * A0 + b * A1 + d * A3);
   I[0] = A0 * id;
   I[1] = A1 * id;
   I[2] = (a * f - d * d) * id;
@@ -151,7 +161,7 @@ __device__ __forceinline__ void sym3_mul(const double* S, const double* x, doubl
   y[2] = S[3] * x[0] + S[4] * x[1] + S[5] * x[2];
 }
 
-// Landmark position of the conditioning iterate: x^k or x̄^k = l + gamma (l - l^(k-1))
+// landmark position of the conditioning iterate: x^k, or x̄^k = l + gamma (l - l^(k-1))
 __device__ __forceinline__ void blk_lpos(const V4<double>* lmrec, int j, double gamma, bool bar, double* l) {
   const V4<double> A = lmrec[2 * (size_t)j], B = lmrec[2 * (size_t)j + 1];
   l[0] = A.x + (bar ? gamma * A.w : 0.0);
@@ -159,365 +169,383 @@ __device__ __forceinline__ void blk_lpos(const V4<double>* lmrec, int j, double 
   l[2] = A.z + (bar ? gamma * B.y : 0.0);
 }
 
-// One LM step of block b (its warp) on E^alpha(. | z), z = x̄^k (bar) or x^k, from z. The
-// solution's landmarks go to scratch scr + BS_L, the camera to *cs. Returns nothing; a block whose
-// step is never taken stays at z.
-__device__ inline void blk_lm(const BlkArgs& A, int b, int lane, bool bar, double gamma, int cam, const double* stz,
-                              const CamT<double>& cz, double xi, double* scr, CamT<double>& cs, int loss) {
-  const int l0 = A.blk_lm_ptr[b], l1 = A.blk_lm_ptr[b + 1];
+// shared memory of a block solve besides the dynamic Schur matrix
+struct BlkSmem {
+  CamT<double> ck[BLK_MAX_CAMS], cz[BLK_MAX_CAMS], cs[BLK_MAX_CAMS], cb[BLK_MAX_CAMS];
+  double stb[BLK_MAX_CAMS][39], stk[BLK_MAX_CAMS][39];
+  double A[BLK_MAX_CAMS][45], g[BLK_MAX_CAMS][9];
+  double dc[BLK_NP], rhs[BLK_NP];
+  double red[BLK_THREADS];
+  double val;
+  int flag;
+};
+
+// sum over the CTA in thread order (thread 0 adds the 128 partials), the result on every thread
+__device__ __forceinline__ double blk_reduce(BlkSmem& sh, double v) {
+  __syncthreads();
+  sh.red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < BLK_THREADS; ++k) t += sh.red[k];
+    sh.val = t;
+  }
+  __syncthreads();
+  return sh.val;
+}
+
+// One LM step of block b on E^alpha(. | z), z = x̄^k (bar) or x^k, from z: the cameras' solution
+// to sh.cs, the landmarks' to lsc + BL_L (both stay at z if no step is taken).
+__device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, double xi, BlkSmem& sh, double* S) {
+  const int tid = threadIdx.x;
+  const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
+  const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
+  const int np = 9 * nc, ld = A.ld;
   const int ao = bar ? LS_AB : LS_AK, bo = bar ? LS_BB : LS_BK;
-  double Am[45], g[9];
-  if (cam >= 0) cam_lm_model(stz, cz, xi, Am, g);
-  double Ai[45], gi[9];
-#pragma unroll
-  for (int k = 0; k < 45; ++k) Ai[k] = 0.0;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) gi[k] = 0.0;
-  // ---- per landmark: its 3 x 3 block, gradient, coupling to the camera, F at z of its intra pair
-  for (int e = l0 + lane; e < l1; e += 32) {
-    const int j = A.blk_lms[e];
-    double* s = scr + (size_t)j * BS_N;
+  // ---- cameras: the model of their inter pairs and proximal term, plus their intra pairs (a
+  //      thread per camera, its intra pairs in order)
+  if (tid < nc) {
+    const CamT<double>& cz = sh.cz[tid];
+    cam_lm_model(bar ? sh.stb[tid] : sh.stk[tid], cz, xi, sh.A[tid], sh.g[tid]);
+    for (int q = A.ci_ptr[cp0 + tid]; q < A.ci_ptr[cp0 + tid + 1]; ++q) {
+      double lz[3];
+      blk_lpos(A.lmrec, A.ci_lm[q], gamma, bar, lz);
+      const double2 u = A.c_u[A.ci_obs[q]];
+      double f[3], Jc[3][9], Jl[3][3];
+      blk_intra_jac(cz, lz, u.x, u.y, f, Jc, Jl);
+      double rho, w;
+      blk_rho_any(A.loss, A.L, f[0] * f[0] + f[1] * f[1] + f[2] * f[2], rho, w);
+      for (int i = 0; i < 9; ++i) {
+        sh.g[tid][i] += w * (Jc[0][i] * f[0] + Jc[1][i] * f[1] + Jc[2][i] * f[2]);
+        for (int k = 0; k <= i; ++k)
+          sh.A[tid][lt9(i, k)] += w * (Jc[0][i] * Jc[0][k] + Jc[1][i] * Jc[1][k] + Jc[2][i] * Jc[2][k]);
+      }
+    }
+    sh.cs[tid] = cz;
+  }
+  // ---- landmarks: their 3 x 3 block, gradient, couplings B = w Jc^T Jl and F at z of their intra pairs
+  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    const int j = A.lms[e];
+    double* s = A.lsc + (size_t)j * BL_N;
     double lz[3];
     blk_lpos(A.lmrec, j, gamma, bar, lz);
     const double* sm = A.lm_sums + (size_t)j * LS_N;
     const double a2 = 2.0 * sm[ao];
     double C[6] = {a2 + xi, 0.0, a2 + xi, 0.0, 0.0, a2 + xi};
     double gl[3] = {2.0 * sm[bo], 2.0 * sm[bo + 1], 2.0 * sm[bo + 2]};
-    double Bm[27];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) Bm[k] = 0.0;
     double Fz = 0.0;
-    const int o = A.blk_obs[e];
-    if (o >= 0 && cam >= 0) {
-      const double2 u = A.c_u[o];
+    for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+      const double2 u = A.c_u[A.io_obs[p]];
       double f[3], Jc[3][9], Jl[3][3];
-      blk_intra_jac(cz, lz, u.x, u.y, f, Jc, Jl);
-      const double r = f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+      blk_intra_jac(sh.cz[A.io_cam[p]], lz, u.x, u.y, f, Jc, Jl);
       double rho, w;
-      switch (loss) {
-        case LOSS_TRIVIAL: rho_w<LOSS_TRIVIAL, double>(A.L, r, rho, w); break;
-        case LOSS_HUBER: rho_w<LOSS_HUBER, double>(A.L, r, rho, w); break;
-        case LOSS_CAUCHY: rho_w<LOSS_CAUCHY, double>(A.L, r, rho, w); break;
-        default: rho_w<LOSS_WELSCH, double>(A.L, r, rho, w); break;
-      }
-      Fz = 0.5 * rho;
+      blk_rho_any(A.loss, A.L, f[0] * f[0] + f[1] * f[1] + f[2] * f[2], rho, w);
+      Fz += 0.5 * rho;
       int q = 0;
-#pragma unroll
       for (int r1 = 0; r1 < 3; ++r1)
-#pragma unroll
-        for (int c1 = 0; c1 <= r1; ++c1, ++q) {
-          double v = 0.0;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) v += Jl[k][r1] * Jl[k][c1];
-          C[q] += w * v;
-        }
-#pragma unroll
+        for (int c1 = 0; c1 <= r1; ++c1, ++q) C[q] += w * (Jl[0][r1] * Jl[0][c1] + Jl[1][r1] * Jl[1][c1] + Jl[2][r1] * Jl[2][c1]);
       for (int r1 = 0; r1 < 3; ++r1) gl[r1] += w * (Jl[0][r1] * f[0] + Jl[1][r1] * f[1] + Jl[2][r1] * f[2]);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) Bm[i * 3 + k] = w * (Jc[0][i] * Jl[0][k] + Jc[1][i] * Jl[1][k] + Jc[2][i] * Jl[2][k]);
-        gi[i] += w * (Jc[0][i] * f[0] + Jc[1][i] * f[1] + Jc[2][i] * f[2]);
-#pragma unroll
-        for (int k = 0; k <= i; ++k) Ai[lt9(i, k)] += w * (Jc[0][i] * Jc[0][k] + Jc[1][i] * Jc[1][k] + Jc[2][i] * Jc[2][k]);
-      }
+      double* bi = A.isc + (size_t)p * BI_N;
+      for (int i = 0; i < 9; ++i)
+        for (int k = 0; k < 3; ++k) bi[BI_B + 3 * i + k] = w * (Jc[0][i] * Jl[0][k] + Jc[1][i] * Jl[1][k] + Jc[2][i] * Jl[2][k]);
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s[BS_C + k] = C[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s[BS_G + k] = gl[k];
-#pragma unroll
-    for (int k = 0; k < 27; ++k) s[BS_B + k] = Bm[k];
-    s[BS_FZ] = Fz;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s[BS_L + k] = lz[k];   // the landmark stays at z unless a step is taken
+    for (int k = 0; k < 6; ++k) s[BL_C + k] = C[k];
+    for (int k = 0; k < 3; ++k) {
+      s[BL_G + k] = gl[k];
+      s[BL_L + k] = lz[k];
+    }
+    s[BL_FZ] = Fz;
   }
-  if (cam >= 0) {
-#pragma unroll
-    for (int k = 0; k < 45; ++k) Am[k] += warp_sum(Ai[k]);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) g[k] += warp_sum(gi[k]);
-  }
-  cs = cz;
+  __syncthreads();
   double mu = LM_MU0;
   for (int tr = 0; tr < LM_TRIES; ++tr, mu *= 10.0) {
-    // ---- Schur complement of the damped system onto the camera
-    double Sacc[45], racc[9];
-#pragma unroll
-    for (int k = 0; k < 45; ++k) Sacc[k] = 0.0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) racc[k] = 0.0;
-    for (int e = l0 + lane; e < l1; e += 32) {
-      if (cam < 0 || A.blk_obs[e] < 0) continue;
-      const double* s = scr + (size_t)A.blk_lms[e] * BS_N;
-      double Cm[6], Ci[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Cm[k] = s[BS_C + k];
+    // ---- damped landmark blocks: C^-1 and B C^-1 of every intra pair
+    for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+      double* s = A.lsc + (size_t)A.lms[e] * BL_N;
+      double Cm[6];
+      for (int k = 0; k < 6; ++k) Cm[k] = s[BL_C + k];
       Cm[0] *= 1.0 + mu;
       Cm[2] *= 1.0 + mu;
       Cm[5] *= 1.0 + mu;
-      sym3_inv(Cm, Ci);
-      double BC[9][3];   // B C^-1
-#pragma unroll
-      for (int i = 0; i < 9; ++i) sym3_mul(Ci, s + BS_B + 3 * i, BC[i]);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-#pragma unroll
-        for (int k = 0; k <= i; ++k)
-          Sacc[lt9(i, k)] -= BC[i][0] * s[BS_B + 3 * k] + BC[i][1] * s[BS_B + 3 * k + 1] + BC[i][2] * s[BS_B + 3 * k + 2];
-        racc[i] += BC[i][0] * s[BS_G] + BC[i][1] * s[BS_G + 1] + BC[i][2] * s[BS_G + 2];
+      sym3_inv(Cm, s + BL_CI);
+      for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+        double* bi = A.isc + (size_t)p * BI_N;
+        for (int i = 0; i < 9; ++i) sym3_mul(s + BL_CI, bi + BI_B + 3 * i, bi + BI_BC + 3 * i);
       }
     }
-    double dc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    bool ok = true;
-    if (cam >= 0) {
-      double L9[45];
-#pragma unroll
-      for (int k = 0; k < 45; ++k) L9[k] = warp_sum(Sacc[k]);
-      double rhs[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) rhs[k] = -g[k] + warp_sum(racc[k]);
-      // Cholesky of (A + mu diag A) - sum B C^-1 B^T, every lane the same
-      for (int i = 0; i < 9; ++i) {
-        for (int j = 0; j <= i; ++j) {
-          double v = Am[lt9(i, j)] * (i == j ? 1.0 + mu : 1.0) + L9[lt9(i, j)];
-          for (int k = 0; k < j; ++k) v -= L9[lt9(i, k)] * L9[lt9(j, k)];
-          if (i == j) {
-            if (!(v > 0.0)) ok = false;
-            L9[lt9(i, i)] = sqrt(ok ? v : 1.0);
-          } else {
-            L9[lt9(i, j)] = v / L9[lt9(j, j)];
-          }
+    __syncthreads();
+    // ---- Schur complement S = (A + mu diag A) - sum_j B_j C_j^-1 B_j^T (lower triangle) and its
+    //      right-hand side -g + sum_j B_j C_j^-1 g_j; a thread per entry, landmarks in order
+    for (int rc = tid; rc < np * np; rc += BLK_THREADS) {
+      const int r = rc / np, c = rc % np;
+      if (c > r) continue;
+      const int ca = r / 9, ra = r % 9, cbb = c / 9, rb = c % 9;
+      double v = ca == cbb ? sh.A[ca][lt9(ra, rb)] * (ra == rb ? 1.0 + mu : 1.0) : 0.0;
+      for (int e = l0; e < l1; ++e) {
+        int pa = -1, pb = -1;
+        for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+          if (A.io_cam[p] == ca) pa = p;
+          if (A.io_cam[p] == cbb) pb = p;
         }
+        if (pa < 0 || pb < 0) continue;
+        const double* x = A.isc + (size_t)pa * BI_N + BI_BC + 3 * ra;
+        const double* y = A.isc + (size_t)pb * BI_N + BI_B + 3 * rb;
+        v -= x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
       }
-      double y[9];
-      for (int i = 0; i < 9; ++i) {
-        double v = rhs[i];
-        for (int k = 0; k < i; ++k) v -= L9[lt9(i, k)] * y[k];
-        y[i] = v / L9[lt9(i, i)];
+      S[r * ld + c] = v;
+    }
+    for (int r = tid; r < np; r += BLK_THREADS) {
+      const int ca = r / 9, ra = r % 9;
+      double v = -sh.g[ca][ra];
+      for (int e = l0; e < l1; ++e) {
+        const double* gl = A.lsc + (size_t)A.lms[e] * BL_N + BL_G;
+        for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p)
+          if (A.io_cam[p] == ca) {
+            const double* x = A.isc + (size_t)p * BI_N + BI_BC + 3 * ra;
+            v += x[0] * gl[0] + x[1] * gl[1] + x[2] * gl[2];
+          }
       }
-      for (int i = 8; i >= 0; --i) {
+      sh.rhs[r] = v;
+    }
+    if (tid == 0) sh.flag = 1;
+    __syncthreads();
+    // ---- Cholesky of S in place (column by column), then the two triangular solves
+    for (int k = 0; k < np; ++k) {
+      if (tid == 0) {
+        const double d = S[k * ld + k];
+        if (!(d > 0.0)) sh.flag = 0;
+        S[k * ld + k] = sqrt(d > 0.0 ? d : 1.0);
+      }
+      __syncthreads();
+      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) S[i * ld + k] /= S[k * ld + k];
+      __syncthreads();
+      const int m = np - k - 1;
+      for (int q = tid; q < m * m; q += BLK_THREADS) {
+        const int i = k + 1 + q / m, jj = k + 1 + q % m;
+        if (jj <= i) S[i * ld + jj] -= S[i * ld + k] * S[jj * ld + k];
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && sh.flag) {
+      double y[BLK_NP];
+      for (int i = 0; i < np; ++i) {
+        double v = sh.rhs[i];
+        for (int k = 0; k < i; ++k) v -= S[i * ld + k] * y[k];
+        y[i] = v / S[i * ld + i];
+      }
+      for (int i = np - 1; i >= 0; --i) {
         double v = y[i];
-        for (int k = i + 1; k < 9; ++k) v -= L9[lt9(k, i)] * dc[k];
-        dc[i] = v / L9[lt9(i, i)];
+        for (int k = i + 1; k < np; ++k) v -= S[k * ld + i] * sh.dc[k];
+        sh.dc[i] = v / S[i * ld + i];
       }
     }
-    if (!ok) continue;
-    // ---- candidate: the camera, then each landmark's back substitution, and E^alpha's decrease
-    CamT<double> cc = cz;
-    double dEc = 0.0;
-    if (cam >= 0) {
+    __syncthreads();
+    if (!sh.flag) continue;
+    // ---- the candidate: cameras (a thread each), landmarks by back substitution, and the
+    //      decrease of E^alpha(. | z) term by term
+    double part = 0.0;
+    CamT<double> cc;
+    if (tid < nc) {
+      const CamT<double>& cz = sh.cz[tid];
+      const double* th = sh.dc + 9 * tid;
       double Ex[9];
-      rodrigues(dc, Ex);
-#pragma unroll
+      rodrigues(th, Ex);
       for (int r = 0; r < 3; ++r)
-#pragma unroll
         for (int k = 0; k < 3; ++k)
           cc.R[r * 3 + k] = cz.R[r * 3 + 0] * Ex[0 * 3 + k] + cz.R[r * 3 + 1] * Ex[1 * 3 + k] + cz.R[r * 3 + 2] * Ex[2 * 3 + k];
-#pragma unroll
       for (int k = 0; k < 3; ++k) {
-        cc.t[k] = cz.t[k] + dc[3 + k];
-        cc.d[k] = cz.d[k] + dc[6 + k];
+        cc.t[k] = cz.t[k] + th[3 + k];
+        cc.d[k] = cz.d[k] + th[6 + k];
       }
-      dEc = cam_phi(stz, cz, cc, xi);   // inter pairs' P and the camera's proximal term
+      part += cam_phi(bar ? sh.stb[tid] : sh.stk[tid], cz, cc, xi);   // inter pairs' P and the proximal term
+      sh.cb[tid] = cc;   // candidate (sh.cs keeps the accepted solution)
     }
-    double dEl = 0.0;
-    for (int e = l0 + lane; e < l1; e += 32) {
-      const int j = A.blk_lms[e];
-      const double* s = scr + (size_t)j * BS_N;
-      double Cm[6], Ci[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) Cm[k] = s[BS_C + k];
-      Cm[0] *= 1.0 + mu;
-      Cm[2] *= 1.0 + mu;
-      Cm[5] *= 1.0 + mu;
-      sym3_inv(Cm, Ci);
-      double rr[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        rr[k] = s[BS_G + k];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) rr[k] += s[BS_B + 3 * i + k] * dc[i];
+    __syncthreads();
+    for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+      const int j = A.lms[e];
+      const double* s = A.lsc + (size_t)j * BL_N;
+      double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
+      for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+        const double* bi = A.isc + (size_t)p * BI_N + BI_B;
+        const double* th = sh.dc + 9 * A.io_cam[p];
+        for (int k = 0; k < 3; ++k)
+          for (int i = 0; i < 9; ++i) rr[k] += bi[3 * i + k] * th[i];
       }
       double dl[3];
-      sym3_mul(Ci, rr, dl);
-      dl[0] = -dl[0], dl[1] = -dl[1], dl[2] = -dl[2];
+      sym3_mul(s + BL_CI, rr, dl);
       double lz[3];
       blk_lpos(A.lmrec, j, gamma, bar, lz);
       const double* sm = A.lm_sums + (size_t)j * LS_N;
       const double dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-      dEl += sm[ao] * dd + 2.0 * (dl[0] * sm[bo] + dl[1] * sm[bo + 1] + dl[2] * sm[bo + 2]) + 0.5 * xi * dd;
-      const int o = A.blk_obs[e];
-      if (o >= 0 && cam >= 0) {
-        const double2 u = A.c_u[o];
-        const double lc[3] = {lz[0] + dl[0], lz[1] + dl[1], lz[2] + dl[2]};
-        dEl += blk_F(cc, lc, u.x, u.y, A.L, loss) - s[BS_FZ];
+      part += sm[ao] * dd - 2.0 * (dl[0] * sm[bo] + dl[1] * sm[bo + 1] + dl[2] * sm[bo + 2]) + 0.5 * xi * dd;
+      const double lc[3] = {lz[0] - dl[0], lz[1] - dl[1], lz[2] - dl[2]};
+      double Fc = 0.0;
+      for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+        const double2 u = A.c_u[A.io_obs[p]];
+        Fc += blk_F(sh.cb[A.io_cam[p]], lc, u.x, u.y, A.L, A.loss);
       }
+      part += Fc - s[BL_FZ];
     }
-    const double dE = dEc + warp_sum(dEl);
-    if (dE < 0.0) {   // the step is taken: landmarks to the scratch, the camera to cs
-      for (int e = l0 + lane; e < l1; e += 32) {
-        const int j = A.blk_lms[e];
-        double* s = scr + (size_t)j * BS_N;
-        double Cm[6], Ci[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Cm[k] = s[BS_C + k];
-        Cm[0] *= 1.0 + mu;
-        Cm[2] *= 1.0 + mu;
-        Cm[5] *= 1.0 + mu;
-        sym3_inv(Cm, Ci);
-        double rr[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          rr[k] = s[BS_G + k];
-#pragma unroll
-          for (int i = 0; i < 9; ++i) rr[k] += s[BS_B + 3 * i + k] * dc[i];
+    const double dE = blk_reduce(sh, part);
+    if (dE < 0.0) {   // the step is taken
+      for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+        double* s = A.lsc + (size_t)A.lms[e] * BL_N;
+        double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
+        for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+          const double* bi = A.isc + (size_t)p * BI_N + BI_B;
+          const double* th = sh.dc + 9 * A.io_cam[p];
+          for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 9; ++i) rr[k] += bi[3 * i + k] * th[i];
         }
         double dl[3];
-        sym3_mul(Ci, rr, dl);
-        s[BS_L + 0] -= dl[0];
-        s[BS_L + 1] -= dl[1];
-        s[BS_L + 2] -= dl[2];
+        sym3_mul(s + BL_CI, rr, dl);
+        s[BL_L + 0] -= dl[0];
+        s[BL_L + 1] -= dl[1];
+        s[BL_L + 2] -= dl[2];
       }
-      cs = cc;
+      if (tid < nc) sh.cs[tid] = sh.cb[tid];
+      __syncthreads();
       return;
     }
   }
+  __syncthreads();
 }
 
-// E^alpha(x | x^k) - E^alpha(x^k | x^k) of block b for the solution in scratch scr (landmarks at
-// BS_L) and camera cs: the camera's P terms and proximal term from its x^k statistics, each
-// landmark's Q terms and proximal term from its x^k sums, and the intra pairs' F_ij differences.
-__device__ inline double blk_dE_k(const BlkArgs& A, int b, int lane, int cam, const double* stk, const CamT<double>& ck,
-                                  const CamT<double>& cs, double xi, const double* scr, int loss) {
-  const int l0 = A.blk_lm_ptr[b], l1 = A.blk_lm_ptr[b + 1];
-  double dEl = 0.0;
-  for (int e = l0 + lane; e < l1; e += 32) {
-    const int j = A.blk_lms[e];
-    const double* s = scr + (size_t)j * BS_N;
+// E^alpha(x | x^k) - E^alpha(x^k | x^k) of block b for the solution in sh.cs and lsc + BL_L
+__device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& sh) {
+  const int tid = threadIdx.x;
+  const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
+  const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
+  double part = 0.0;
+  if (tid < nc) part += cam_phi(sh.stk[tid], sh.ck[tid], sh.cs[tid], xi);
+  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    const int j = A.lms[e];
+    const double* s = A.lsc + (size_t)j * BL_N;
     double lk[3];
     blk_lpos(A.lmrec, j, 0.0, false, lk);
-    const double dl[3] = {s[BS_L] - lk[0], s[BS_L + 1] - lk[1], s[BS_L + 2] - lk[2]};
+    const double dl[3] = {s[BL_L] - lk[0], s[BL_L + 1] - lk[1], s[BL_L + 2] - lk[2]};
     const double* sm = A.lm_sums + (size_t)j * LS_N;
     const double dd = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-    dEl += sm[LS_AK] * dd + 2.0 * (dl[0] * sm[LS_BK] + dl[1] * sm[LS_BK + 1] + dl[2] * sm[LS_BK + 2]) + 0.5 * xi * dd;
-    const int o = A.blk_obs[e];
-    if (o >= 0 && cam >= 0) {
-      const double2 u = A.c_u[o];
-      dEl += blk_F(cs, s + BS_L, u.x, u.y, A.L, loss) - blk_F(ck, lk, u.x, u.y, A.L, loss);
+    part += sm[LS_AK] * dd + 2.0 * (dl[0] * sm[LS_BK] + dl[1] * sm[LS_BK + 1] + dl[2] * sm[LS_BK + 2]) + 0.5 * xi * dd;
+    for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+      const double2 u = A.c_u[A.io_obs[p]];
+      const int c = A.io_cam[p];
+      part += blk_F(sh.cs[c], s + BL_L, u.x, u.y, A.L, A.loss) - blk_F(sh.ck[c], lk, u.x, u.y, A.L, A.loss);
     }
   }
-  return (cam >= 0 ? cam_phi(stk, ck, cs, xi) : 0.0) + warp_sum(dEl);
+  return blk_reduce(sh, part);
 }
 
-__global__ void __launch_bounds__(128) k_blk_solve(BlkArgs A, IterParams P, int loss) {
-  const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * 4 + (threadIdx.x >> 5);
-  if (b >= A.S) return;
+__global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams P) {
+  extern __shared__ __align__(16) double blk_S[];   // the Schur matrix, ld x ld
+  __shared__ BlkSmem sh;
+  const int b = blockIdx.x;
+  const int tid = threadIdx.x;
   const int it = *P.it, first = *P.first;
   const double gamma = P.gam[it], xi = P.xi;
-  const int cam = A.blk_cam[b];
-  const int l0 = A.blk_lm_ptr[b], l1 = A.blk_lm_ptr[b + 1];
-  // ---- the camera's x^k, x^(k-1) displacement, statistics and F sums
-  CamT<double> ck, cb;
-  double st_b[39], st_k[39];
-  double Fall = 0.0, Fin = 0.0, Gc = 0.0, disp = 0.0;
-  double* x = nullptr;
-  double* dx = nullptr;
-  if (cam >= 0) {
-    x = A.cam_x + (size_t)cam * CSTRIDE;
-    dx = A.cam_dx + (size_t)cam * CSTRIDE;
-#pragma unroll
+  const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
+  const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
+  // ---- cameras: x^k, x̄^k, statistics, F sums, displacement (a thread each)
+  double part_disp = 0.0, part_Fall = 0.0, part_Fin = 0.0, part_G = 0.0;
+  if (tid < nc) {
+    const int cam = A.cams[cp0 + tid];
+    const double* x = A.cam_x + (size_t)cam * CSTRIDE;
+    const double* dx = A.cam_dx + (size_t)cam * CSTRIDE;
+    CamT<double> ck, cb;
     for (int a = 0; a < 9; ++a) {
       ck.R[a] = x[CS_R + a];
       cb.R[a] = A.cam_Rbar[(size_t)cam * 9 + a];
-      disp += dx[CS_R + a] * dx[CS_R + a];
+      part_disp += dx[CS_R + a] * dx[CS_R + a];
     }
-#pragma unroll
     for (int a = 0; a < 3; ++a) {
       ck.t[a] = x[CS_T + a];
       ck.d[a] = x[CS_D + a];
       cb.t[a] = ck.t[a] + gamma * dx[CS_T + a];
       cb.d[a] = ck.d[a] + gamma * dx[CS_D + a];
-      disp += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
+      part_disp += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
     }
+    sh.ck[tid] = ck;
+    sh.cz[tid] = cb;   // the accelerated step's conditioning iterate, first
     const int c0 = A.cam_chunk_ptr[cam], c1 = A.cam_chunk_ptr[cam + 1];
-    sum_stats<double, double>(A.part, c0, c1, PART_XB, st_b);
-    sum_stats<double, double>(A.part, c0, c1, PART_XK, st_k);
+    sum_stats<double, double>(A.part, c0, c1, PART_XB, sh.stb[tid]);
+    sum_stats<double, double>(A.part, c0, c1, PART_XK, sh.stk[tid]);
     for (int c = c0; c < c1; ++c) {
-      Fall += A.part[(size_t)c * CP_STRIDE + PART_F];
-      Gc += A.part[(size_t)c * CP_STRIDE + PART_G];
-      Fin += A.part[(size_t)c * CP_STRIDE + PART_FI];
+      part_Fall += A.part[(size_t)c * CP_STRIDE + PART_F];
+      part_G += A.part[(size_t)c * CP_STRIDE + PART_G];
+      part_Fin += A.part[(size_t)c * CP_STRIDE + PART_FI];
     }
+    A.cam_Fsum[cam] = part_Fall;   // F_ij(x^k) of the camera's observations (objective trace)
   }
-  // ---- the landmarks' displacements, gaps and inter F sums
-  double dl2 = 0.0, Gl = 0.0, Fl = 0.0;
-  for (int e = l0 + lane; e < l1; e += 32) {
-    const int j = A.blk_lms[e];
+  // ---- landmarks: displacement, gaps and inter F sums
+  double part_dl = 0.0, part_Gl = 0.0, part_Fl = 0.0;
+  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    const int j = A.lms[e];
     const V4<double> LA = A.lmrec[2 * (size_t)j], LB = A.lmrec[2 * (size_t)j + 1];
-    dl2 += LA.w * LA.w + LB.x * LB.x + LB.y * LB.y;
-    Gl += A.lm_sums[(size_t)j * LS_N + LS_G];
-    Fl += A.lm_sums[(size_t)j * LS_N + LS_F];
+    part_dl += LA.w * LA.w + LB.x * LB.x + LB.y * LB.y;
+    part_Gl += A.lm_sums[(size_t)j * LS_N + LS_G];
+    part_Fl += A.lm_sums[(size_t)j * LS_N + LS_F];
   }
-  dl2 = warp_sum(dl2);
-  Gl = warp_sum(Gl);
-  Fl = warp_sum(Fl);
-  // Eq. DEalpha, Eq. Fainit, Eq. Fak, Eq. lFak: E^alpha(x^k | x^k) = sum_E' F + (1/2) sum_E'' F
+  const double disp = blk_reduce(sh, part_disp) + blk_reduce(sh, part_dl);
+  const double Fall = blk_reduce(sh, part_Fall), Fin = blk_reduce(sh, part_Fin);
+  const double G = blk_reduce(sh, part_G) + blk_reduce(sh, part_Gl);
+  const double Fl = blk_reduce(sh, part_Fl);
+  // Eq. DEalpha, Eq. Fainit, Eq. Fak, Eq. lFak, with E^alpha(x^k | x^k) = sum_E' F + (1/2) sum_E'' F
   const double E0 = Fin + 0.5 * (Fall - Fin) + 0.5 * Fl;
-  const double dE = -0.5 * xi * (disp + dl2) + 0.5 * (Gc + Gl);
+  const double dE = -0.5 * xi * disp + 0.5 * G;
   const double E = first ? E0 : A.blk_E[b];
   const double Fb_prev = first ? E0 : A.blk_Fbar[b];
   const double F = E + dE;
   const double Fbar = (1.0 - P.eta) * Fb_prev + P.eta * F;
-  // ---- accelerated LM step from x̄^k, then the restart test; the MM step from x^k where it fires
-  CamT<double> cs = ck;
-  double* scr_acc = A.scr;   // the landmark solutions of the step in use (the MM step reuses it)
+  // ---- accelerated step from x̄^k, restart test (Eq. Eak, strict), MM step from x^k where it fires
   bool rs = true;
   double Enext = 0.0;
   if (P.accelerated) {
-    blk_lm(A, b, lane, true, gamma, cam, st_b, cb, xi, scr_acc, cs, loss);
-    const double dEa = blk_dE_k(A, b, lane, cam, st_k, ck, cs, xi, scr_acc, loss);
-    Enext = F + dEa;
-    rs = Enext > Fbar;   // Eq. Eak, restart test (strict)
+    blk_lm(A, b, true, gamma, xi, sh, blk_S);
+    Enext = F + blk_dE_k(A, b, xi, sh);
+    rs = Enext > Fbar;
   }
   if (rs) {
-    blk_lm(A, b, lane, false, gamma, cam, st_k, ck, xi, scr_acc, cs, loss);
-    Enext = F + blk_dE_k(A, b, lane, cam, st_k, ck, cs, xi, scr_acc, loss);
+    if (tid < nc) sh.cz[tid] = sh.ck[tid];
+    __syncthreads();
+    blk_lm(A, b, false, gamma, xi, sh, blk_S);
+    Enext = F + blk_dE_k(A, b, xi, sh);
   }
-  // ---- new state: landmarks (x^(k+1), displacement), camera, pack of k+1
-  for (int e = l0 + lane; e < l1; e += 32) {
-    const int j = A.blk_lms[e];
-    const double* s = scr_acc + (size_t)j * BS_N;
+  // ---- new state
+  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    const int j = A.lms[e];
+    const double* s = A.lsc + (size_t)j * BL_N;
     const V4<double> LA = A.lmrec[2 * (size_t)j];
     V4<double> nA, nB;
-    nA.x = s[BS_L];
-    nA.y = s[BS_L + 1];
-    nA.z = s[BS_L + 2];
-    nA.w = s[BS_L] - LA.x;
-    nB.x = s[BS_L + 1] - LA.y;
-    nB.y = s[BS_L + 2] - LA.z;
+    nA.x = s[BL_L];
+    nA.y = s[BL_L + 1];
+    nA.z = s[BL_L + 2];
+    nA.w = s[BL_L] - LA.x;
+    nB.x = s[BL_L + 1] - LA.y;
+    nB.y = s[BL_L + 2] - LA.z;
     nB.z = 0.0;
     nB.w = 0.0;
     A.lmrec_out[2 * (size_t)j] = nA;
     A.lmrec_out[2 * (size_t)j + 1] = nB;
   }
-  if (lane == 0) {
+  if (tid == 0) {
     A.blk_E[b] = Enext;
     A.blk_Fbar[b] = Fbar;
     A.blk_F[b] = F;
     A.blk_rs[b] = (rs && P.accelerated) ? 1 : 0;
   }
-  if (cam >= 0 && lane == 0) {
-    A.cam_Fsum[cam] = Fall;
-    A.cam_rs[cam] = (rs && P.accelerated) ? 1 : 0;
+  if (tid < nc) {
+    const int cam = A.cams[cp0 + tid];
+    const CamT<double>& cs = sh.cs[tid];
+    const CamT<double>& ck = sh.ck[tid];
+    double* x = A.cam_x + (size_t)cam * CSTRIDE;
+    double* dx = A.cam_dx + (size_t)cam * CSTRIDE;
+    A.cam_rs[cam] = (tid == 0 && rs && P.accelerated) ? 1 : 0;   // the block's restart, counted once
     CamT<double> ndx;
-#pragma unroll
     for (int a = 0; a < 9; ++a) {
       ndx.R[a] = cs.R[a] - ck.R[a];
       x[CS_R + a] = cs.R[a];
       dx[CS_R + a] = ndx.R[a];
     }
-#pragma unroll
     for (int a = 0; a < 3; ++a) {
       ndx.t[a] = cs.t[a] - ck.t[a];
       ndx.d[a] = cs.d[a] - ck.d[a];
@@ -528,10 +556,8 @@ __global__ void __launch_bounds__(128) k_blk_solve(BlkArgs A, IterParams P, int 
     }
     const double gn = P.gam[it + 1];
     double K[9], Rb[9];
-#pragma unroll
     for (int a = 0; a < 9; ++a) K[a] = cs.R[a] + gn * ndx.R[a];
     extrap_rotation<double>(K, Rb);
-#pragma unroll
     for (int a = 0; a < 9; ++a) A.cam_Rbar[(size_t)cam * 9 + a] = Rb[a];
     write_pack_t<double>(cs, ndx, Rb, A.pack_next + (size_t)cam * P4N);
   }

@@ -1,8 +1,8 @@
-"""Coarse blocks on the GPU (daba_set_partition: every block one camera and the landmarks it
-owns, Eq. Ealpha with the intra-block pairs exact, one successful LM step per block) against the
-oracle of Algorithm 1 with the same blocks (oracle/daba_blocks.py), per iteration: the objective
-trace, the per-block restart metrics F^alpha and Fbar^alpha, the restart decisions and the
-iterate."""
+"""Coarse blocks on the GPU (daba_set_partition: contiguous groups of one to eight cameras and
+the landmarks they see first, Eq. Ealpha with the intra-block pairs exact, one successful LM step
+per block) against the oracle of Algorithm 1 with the same blocks (oracle/daba_blocks.py), per
+iteration: the objective trace, the per-block restart metrics F^alpha and Fbar^alpha, the restart
+decisions and the iterate."""
 import numpy as np
 import pytest
 
@@ -33,19 +33,24 @@ def _scene(name):
     return cached_scene(name, scale={"street": 0.05, "tourism": 0.005}[name])
 
 
-@pytest.mark.parametrize("name,accel,K", [("circle", True, 20), ("circle_small", False, 12), ("street", True, 12),
-                                          ("tourism", True, 10)])
-def test_blocks_match_oracle_per_iteration(name, accel, K):
+@pytest.mark.parametrize("name,accel,K,n_blocks", [
+    ("circle", True, 20, None), ("circle_small", False, 12, None), ("street", True, 12, None),
+    ("tourism", True, 10, None),
+    # several cameras per block: the Schur complement couples the block's cameras
+    ("circle", True, 12, 4), ("circle_small", False, 12, 3), ("circle_small", True, 12, 6),
+    ("street", True, 4, 25), ("tourism", True, 3, 30)])
+def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     from paper_2305_07026_b300 import _lib as L
     sc = _scene(name)
-    part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, sc.M)   # one camera per block
+    part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n_blocks or sc.M)
+    assert np.bincount(part.cam_block).max() <= L.BLK_MAX_CAMS
     opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, accelerated=accel)
     prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
     st = B.init_state(prob, part, R, t, d, l)
     s2 = prob.s_norm ** 2
     g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64", accelerated=accel)
     g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
-    g.set_partition(part.cam_block, part.lm_block)
+    g.set_partition(part.cam_block, part.lm_block, part.S)
     g.set_state(sc.cams, sc.lms)
     compared = 0
     for k in range(K):
@@ -65,7 +70,7 @@ def test_blocks_match_oracle_per_iteration(name, accel, K):
         compared = k + 1
         if (rs_blk.astype(bool) != info.restart).any():
             break
-    assert compared >= min(K, 10)
+    assert compared >= min(K, 3 if n_blocks else 10)
     if compared == K:
         cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
         cams_g, lms_g = g.get_state()
@@ -120,13 +125,16 @@ def test_blocks_arguments():
     m.close()
     d = L.Daba(sc.M, sc.N, sc.nnz, prec="fp64")
     d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
-    with pytest.raises(L.DabaError) as e:   # two cameras in one block
+    with pytest.raises(L.DabaError) as e:   # all cameras in one block: more than BLK_MAX_CAMS
         d.set_partition(np.zeros(sc.M, np.int32), part.lm_block)
     assert e.value.status == L.DABA_ERR_ARG
     bad = part.lm_block.copy()
     bad[3] = sc.M
-    with pytest.raises(L.DabaError) as e:
-        d.set_partition(part.cam_block, bad)
+    with pytest.raises(L.DabaError) as e:   # a landmark's block out of range
+        d.set_partition(part.cam_block, bad, sc.M)
+    assert e.value.status == L.DABA_ERR_ARG
+    with pytest.raises(L.DabaError) as e:   # more blocks than cameras and landmarks
+        d.set_partition(part.cam_block, part.lm_block, sc.M + sc.N + 1)
     assert e.value.status == L.DABA_ERR_ARG
     d.set_partition(part.cam_block, part.lm_block)
     d.set_state(sc.cams, sc.lms)
@@ -134,3 +142,36 @@ def test_blocks_arguments():
         d.export_checkpoint()
     assert e.value.status == L.DABA_ERR_STATE
     d.close()
+
+
+def test_blocks_without_cameras_and_regrown_partition():
+    """Landmark-only and empty blocks (n_blocks above the largest id), then a partition with
+    larger blocks on the same context (its buffers grow): both against the oracle."""
+    from paper_2305_07026_b300 import _lib as L
+    sc = _scene("circle_small")
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    s2 = prob.s_norm ** 2
+    g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
+    g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    one = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, sc.M)
+    lm_only = one.lm_block.copy()
+    lm_only[::3] = sc.M + (np.arange(sc.N)[::3] % 4)   # a third of the landmarks in four camera-less blocks
+    parts = [B.Partition(one.cam_block, lm_only, sc.M + 6),   # the last two blocks hold nothing
+             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 3)]
+    for part in parts:
+        g.set_partition(part.cam_block, part.lm_block, part.S)
+        g.set_state(sc.cams, sc.lms)
+        st = B.init_state(prob, part, R, t, d, l)
+        for k in range(6):
+            st, info = B.step(prob, part, st)
+            tr = np.zeros(2)
+            g.run(1, tr)
+            assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
+            F_blk, Fb_blk, _ = g.get_partition_metrics()
+            np.testing.assert_allclose(F_blk, info.F_blk * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+        cams_g, lms_g = g.get_state()
+        np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
+        np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    g.close()
