@@ -37,6 +37,8 @@ from __future__ import annotations
 import dataclasses
 
 import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from oracle import daba_oracle as O
 
@@ -150,33 +152,39 @@ def block_params(part, alpha):
 
 def block_model(prob, part, isin, mj, Rz, tz, dz, lz, alpha):
     """Gauss-Newton model (H, g) of E^alpha(. | z) at z over the block's parameters, ordered
-    [9 per camera (ascending index) | 3 per landmark (ascending index)]."""
+    [9 per camera (ascending index) | 3 per landmark (ascending index)]; H is a sparse matrix
+    (scipy CSC) whose entries are the sums of the per-term blocks below."""
     ci, li, u = prob.cam_idx, prob.lm_idx, prob.u
     xi = prob.opts.xi
     cams, lms = block_params(part, alpha)
     nc, nl = cams.size, lms.size
     n = 9 * nc + 3 * nl
-    cpos = {int(c): k for k, c in enumerate(cams)}
-    lpos = {int(j): k for k, j in enumerate(lms)}
-    H = np.zeros((n, n))
+    cpos = np.full(part.cam_block.size, -1)
+    cpos[cams] = np.arange(nc)
+    lpos = np.full(part.lm_block.size, -1)
+    lpos[lms] = np.arange(nl)
+    rows, cols, vals = [], [], []
     g = np.zeros(n)
-    for k in range(nc):
-        H[9 * k:9 * k + 3, 9 * k:9 * k + 3] += 2.0 * xi * np.eye(3)
-        H[9 * k + 3:9 * k + 9, 9 * k + 3:9 * k + 9] += xi * np.eye(6)
-    for k in range(nl):
-        H[9 * nc + 3 * k:9 * nc + 3 * k + 3, 9 * nc + 3 * k:9 * nc + 3 * k + 3] += xi * np.eye(3)
+
+    def add(idx, blocks):   # idx (m, k) parameter indices, blocks (m, k, k) Hessian terms
+        rows.append(np.broadcast_to(idx[:, :, None], blocks.shape).ravel())
+        cols.append(np.broadcast_to(idx[:, None, :], blocks.shape).ravel())
+        vals.append(blocks.ravel())
+
+    # proximal term: 2 xi on phi, xi on tau, delta and epsilon
+    rows.append(np.arange(n))
+    cols.append(np.arange(n))
+    vals.append(np.concatenate([np.tile(np.r_[np.full(3, 2.0 * xi), np.full(6, xi)], nc), np.full(3 * nl, xi)]))
+    r9, r3 = np.arange(9), np.arange(3)
     # intra pairs: reweighted Gauss-Newton on R e
     ii = np.flatnonzero(isin & (part.cam_block[ci] == alpha))
     if ii.size:
         f, J = intra_residual_jacobian(Rz[ci[ii]], tz[ci[ii]], dz[ci[ii]], lz[li[ii]], u[ii])
         r = np.einsum("na,na->n", f, f)
         _, w = O.rho(prob.loss, prob.c, r)
-        for o in range(ii.size):
-            a = 9 * cpos[int(ci[ii[o]])]
-            b = 9 * nc + 3 * lpos[int(li[ii[o]])]
-            idx = np.r_[a:a + 9, b:b + 3]
-            H[np.ix_(idx, idx)] += w[o] * J[o].T @ J[o]
-            g[idx] += w[o] * J[o].T @ f[o]
+        idx = np.concatenate([9 * cpos[ci[ii]][:, None] + r9, 9 * nc + 3 * lpos[li[ii]][:, None] + r3], 1)
+        add(idx, w[:, None, None] * np.einsum("nai,naj->nij", J, J))
+        np.add.at(g, idx, w[:, None] * np.einsum("nai,na->ni", J, f))
     # inter pairs, camera side: P_ij residual R p(d) + lambda t - g (as in the camera LM model)
     oc = np.flatnonzero(~isin & (part.cam_block[ci] == alpha))
     if oc.size:
@@ -189,18 +197,33 @@ def block_model(prob, part, isin, mj, Rz, tz, dz, lz, alpha):
         JP[:, :, 0:3] = -np.einsum("nab,nbc->nac", Rz[c], O.skew(p0))
         JP[:, 0, 3] = JP[:, 1, 4] = JP[:, 2, 5] = mj.lam[oc]
         JP[:, :, 6:9] = Rz[c][:, :, 2][:, :, None] * phi_u[:, None, :]
-        for o in range(oc.size):
-            a = 9 * cpos[int(c[o])]
-            H[a:a + 9, a:a + 9] += 2.0 * mj.w[oc[o]] * JP[o].T @ JP[o]
-            g[a:a + 9] += 2.0 * mj.w[oc[o]] * JP[o].T @ r0[o]
+        idx = 9 * cpos[c][:, None] + r9
+        w2 = 2.0 * mj.w[oc]
+        add(idx, w2[:, None, None] * np.einsum("nai,naj->nij", JP, JP))
+        np.add.at(g, idx, w2[:, None] * np.einsum("nai,na->ni", JP, r0))
     # inter pairs, landmark side: Q_ij residual lambda l - g
     ol = np.flatnonzero(~isin & (part.lm_block[li] == alpha))
-    for o in ol:
-        b = 9 * nc + 3 * lpos[int(li[o])]
-        w, lam = mj.w[o], mj.lam[o]
-        H[b:b + 3, b:b + 3] += 2.0 * w * lam * lam * np.eye(3)
-        g[b:b + 3] += 2.0 * w * lam * (lam * lz[li[o]] - mj.g[o])
+    if ol.size:
+        w, lam = mj.w[ol], mj.lam[ol]
+        idx = 9 * nc + 3 * lpos[li[ol]][:, None] + r3
+        rows.append(idx.ravel())
+        cols.append(idx.ravel())
+        vals.append(np.repeat(2.0 * w * lam * lam, 3))
+        np.add.at(g, idx, (2.0 * w * lam)[:, None] * (lam[:, None] * lz[li[ol]] - mj.g[ol]))
+    H = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsc()
     return H, g, cams, lms
+
+
+def dE_block(prob, part, isin, mj, Rx, tx, dx, lx, Rz, tz, dz, lz, alpha):
+    """E^alpha(x | z) - E^alpha(z | z) of block alpha alone: dE_blocks restricted to the terms of
+    the block (the same sums, over the block's own cameras, landmarks and pairs, in order)."""
+    ci, li = prob.cam_idx, prob.lm_idx
+    cm, lm = part.cam_block == alpha, part.lm_block == alpha
+    ob = np.flatnonzero(cm[ci] | lm[li])
+    sub = O.Problem(**{**prob.__dict__, "cam_idx": ci[ob], "lm_idx": li[ob], "u": prob.u[ob]})
+    one = Partition(cam_block=np.where(cm, 0, 1), lm_block=np.where(lm, 0, 1), S=2)
+    mjo = O.Majorizer(**{k: v[ob] for k, v in mj.__dict__.items()})
+    return dE_blocks(sub, one, isin[ob], mjo, Rx, tx, dx, lx, Rz, tz, dz, lz)[0]
 
 
 def solve_blocks_lm(prob, part, isin, mj, Rz, tz, dz, lz):
@@ -213,9 +236,10 @@ def solve_blocks_lm(prob, part, isin, mj, Rz, tz, dz, lz):
         if g.size == 0:
             continue
         nc = cams.size
+        D = sp.diags(H.diagonal())
         mu = LM_MU0
         for _ in range(LM_TRIES):
-            th = np.linalg.solve(H + mu * np.diag(np.diag(H)), -g)
+            th = spla.spsolve((H + mu * D).tocsc(), -g)
             Rc, tc, dc, lc = R.copy(), t.copy(), d.copy(), l.copy()
             for k, i in enumerate(cams):
                 Rc[i] = Rz[i] @ O.so3_exp(th[9 * k:9 * k + 3][None])[0]
@@ -223,7 +247,7 @@ def solve_blocks_lm(prob, part, isin, mj, Rz, tz, dz, lz):
                 dc[i] = dz[i] + th[9 * k + 6:9 * k + 9]
             for k, j in enumerate(lms):
                 lc[j] = lz[j] + th[9 * nc + 3 * k:9 * nc + 3 * k + 3]
-            dE = dE_blocks(prob, part, isin, mj, Rc, tc, dc, lc, Rz, tz, dz, lz)[alpha]
+            dE = dE_block(prob, part, isin, mj, Rc, tc, dc, lc, Rz, tz, dz, lz, alpha)
             if dE < 0.0:
                 R[cams], t[cams], d[cams], l[lms] = Rc[cams], tc[cams], dc[cams], lc[lms]
                 taken += 1

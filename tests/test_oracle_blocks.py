@@ -104,7 +104,7 @@ def test_block_model_gradient(loss):
     for alpha in (0, 3):
         H, g, cams, lms = B.block_model(prob, part, isin, mj, R, t, d, l, alpha)
         nc = cams.size
-        assert np.all(np.linalg.eigvalsh(H) > 0)   # the damped system is solvable
+        assert np.all(np.linalg.eigvalsh(H.toarray()) > 0)   # the damped system is solvable
         for _ in range(3):
             v = rng.normal(size=g.size)
             h = 1e-6
@@ -193,3 +193,19 @@ def test_coarse_blocks_beat_singletons_per_iteration():
     coarse = B.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, part, opts, 10)
     single = O.daba(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts, 10)
     assert coarse.trace_px2[-1] < single.trace_px2[-1]
+
+
+def test_block_decrease_restricted_to_the_block():
+    """The LM acceptance test's per-block decrease (dE_block: the block's own cameras, landmarks
+    and pairs) equals that block's entry of the decrease of every block at once."""
+    rng = np.random.default_rng(5)
+    sc = _scene()
+    prob, part, R, t, d, l = _problem(sc, 4)
+    ci, li = prob.cam_idx, prob.lm_idx
+    isin = B.intra(part, ci, li)
+    Rz, tz, dz, lz = _perturb(rng, R, t, d, l, 1e-2)
+    mj = O.majorizer(prob.loss, prob.c, Rz[ci], tz[ci], dz[ci], lz[li], prob.u)
+    all_blocks = B.dE_blocks(prob, part, isin, mj, R, t, d, l, Rz, tz, dz, lz)
+    for alpha in range(part.S):
+        one = B.dE_block(prob, part, isin, mj, R, t, d, l, Rz, tz, dz, lz, alpha)
+        assert one == pytest.approx(all_blocks[alpha], rel=1e-13, abs=1e-16)
