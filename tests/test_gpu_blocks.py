@@ -24,6 +24,13 @@ def _need_gpu():
     build.build()
 
 
+def _residuals(prob, cams, lms):
+    """The reprojection error vectors (Eq. error) of every observation at a boundary state."""
+    R, t, d, l = O.to_internal(cams, lms, prob.s_norm)
+    ci, li = prob.cam_idx, prob.lm_idx
+    return O.reproj_error(R[ci], t[ci], l[li], O.ray(prob.u, d[ci]))
+
+
 def _scene(name):
     from paper_2305_07026_b300 import scenes
     if name == "circle":
@@ -35,10 +42,14 @@ def _scene(name):
 
 @pytest.mark.parametrize("name,accel,K,n_blocks", [
     ("circle", True, 20, None), ("circle_small", False, 12, None), ("street", True, 12, None),
-    ("tourism", True, 10, None),
-    # several cameras per block: the Schur complement couples the block's cameras
-    ("circle", True, 12, 4), ("circle_small", False, 12, 3), ("circle_small", True, 12, 6),
-    ("street", True, 4, 25), ("tourism", True, 3, 30)])
+    ("tourism", True, 20, None),
+    # several cameras per block: the Schur complement couples the block's cameras. Such a block
+    # is a small bundle adjustment whose gauge only the inter pairs and xi hold, and two correct
+    # solves of its damped system part at ~1e-10 after one step; the parting grows about threefold
+    # per iteration, so the trajectory is compared for 12 iterations and the iterate not at all
+    # (test_multi_camera_blocks_step_from_common_state compares every step from the GPU's state)
+    ("circle", True, 12, 4), ("circle", True, 12, 8), ("circle_small", False, 12, 3), ("circle_small", True, 12, 6),
+    ("street", True, 8, 25), ("tourism", True, 12, 8), ("tourism", True, 12, 32)])
 def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     from paper_2305_07026_b300 import _lib as L
     sc = _scene(name)
@@ -70,12 +81,66 @@ def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
         compared = k + 1
         if (rs_blk.astype(bool) != info.restart).any():
             break
-    assert compared >= min(K, 3 if n_blocks else 10)
-    if compared == K:
+    assert compared >= min(K, 10)
+    if compared == K and (n_blocks is None or name == "circle_small"):
         cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
         cams_g, lms_g = g.get_state()
         np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
         np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    g.close()
+
+
+@pytest.mark.parametrize("name,n_blocks", [("circle", 4), ("circle", 8), ("tourism", 8), ("tourism", 32)])
+def test_multi_camera_blocks_step_from_common_state(name, n_blocks):
+    """Every one of 20 iterations from the same state: before each GPU iteration the oracle takes
+    the GPU's x^k and x^(k-1) (through the boundary) and its Fbar^alpha(k-1); the oracle's Nesterov
+    scalar and E^alpha carry over from its own previous step. Compared after the step: the block
+    metrics F^alpha(k), Fbar^alpha(k) (which hold the previous step's E^alpha(x^k | x^(k-1))), the
+    restart decisions and x^(k+1)."""
+    import dataclasses
+    from paper_2305_07026_b300 import _lib as L
+    sc = _scene(name)
+    part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n_blocks)
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    st = B.init_state(prob, part, R, t, d, l)
+    s2 = prob.s_norm ** 2
+    g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
+    g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    g.set_partition(part.cam_block, part.lm_block, part.S)
+    g.set_state(sc.cams, sc.lms)
+    prev = g.get_state()
+    worst = {"F_blk": 0.0, "cams": 0.0, "lms": 0.0}
+    for k in range(20):
+        if k > 0:   # the oracle continues from the GPU's state
+            cur = g.get_state()
+            Rk, tk, dk, lk = O.to_internal(*cur, prob.s_norm)
+            Rp, tp, dp, lp = O.to_internal(*prev, prob.s_norm)
+            st = dataclasses.replace(st, R=Rk, t=tk, d=dk, l=lk, Rp=Rp, tp=tp, dp=dp, lp=lp, Fbar=Fb_blk / s2)
+            prev = cur
+        st, info = B.step(prob, part, st)
+        tr = np.zeros(2)
+        g.run(1, tr)
+        assert tr[0] == pytest.approx(info.F * s2, rel=1e-12), f"iteration {k}"
+        F_blk, Fb_blk, rs_blk = g.get_partition_metrics()
+        np.testing.assert_allclose(F_blk, info.F_blk * s2, rtol=1e-10, atol=1e-13 * info.F * s2)
+        np.testing.assert_allclose(Fb_blk, info.Fbar_blk * s2, rtol=1e-10, atol=1e-13 * info.F * s2)
+        tie = np.abs(info.Etest - info.Fbar_blk) <= NEAR_TIE * np.abs(info.F_blk)
+        assert not ((rs_blk.astype(bool) != info.restart) & ~tie).any(), f"iteration {k}"
+        cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+        cams_g, lms_g = g.get_state()
+        # landmarks in the residual space: a landmark that two near-parallel rays fix has a depth
+        # the objective hardly sees, and the two solves may place it ~1e-8 apart along the rays
+        e_o, e_g = _residuals(prob, cams_o, lms_o), _residuals(prob, cams_g, lms_g)
+        rms = np.sqrt(np.mean(np.sum(e_o ** 2, axis=1)))
+        worst["F_blk"] = max(worst["F_blk"], float(np.max(np.abs(F_blk / (info.F_blk * s2) - 1))))
+        worst["cams"] = max(worst["cams"], float(np.max(np.abs(cams_g - cams_o) / (1 + np.abs(cams_o)))))
+        worst["lms"] = max(worst["lms"], float(np.max(np.abs(lms_g - lms_o) / (1 + np.abs(lms_o)))))
+        worst["resid"] = max(worst.get("resid", 0.0), float(np.max(np.abs(e_g - e_o)) / rms))
+        np.testing.assert_allclose(cams_g, cams_o, rtol=1e-9, atol=1e-9, err_msg=f"iteration {k}")
+        assert np.max(np.abs(e_g - e_o)) <= 1e-7 * rms, f"iteration {k}"
+        np.testing.assert_allclose(lms_g, lms_o, rtol=1e-6, atol=1e-6, err_msg=f"iteration {k}")
+    print(name, n_blocks, worst)
     g.close()
 
 
