@@ -1,5 +1,6 @@
 """Host-side logic that needs no GPU: option validation in daba_create (before any device
-call), the batch merge/split of independent scenes, and the autotuner's coordinate descent."""
+call), the batch merge/split of independent scenes, the autotuner's coordinate descent and the
+coarse-block partition helper."""
 import numpy as np
 import pytest
 
@@ -61,3 +62,19 @@ def test_autotune_coordinate_descent(monkeypatch):
     assert best == {"chunk_obs": 4096, "tile_obs": 256, "tile_lms": 64}
     assert all(v == 1 for v in cost.values())
     assert len(tried) == len(cost)
+
+
+def test_camera_group_partition_helper():
+    """The package's partition helper gives the blocks the block oracle's helper gives, and
+    refuses blocks of more cameras than the library takes."""
+    import numpy as np
+    from oracle import daba_blocks as B
+    from paper_2305_07026_b300 import partition, scenes
+    sc = scenes.circle_scene(n_lms=300)
+    for n in (3, 4, 20):
+        cb, lb = partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n)
+        ref = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n)
+        np.testing.assert_array_equal(cb, ref.cam_block)
+        np.testing.assert_array_equal(lb, ref.lm_block)
+    with pytest.raises(ValueError):
+        partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 2)   # 10 cameras per block
