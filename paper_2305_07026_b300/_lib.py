@@ -39,6 +39,11 @@ class daba_options(ctypes.Structure):
                 ("momentum_reset", ctypes.c_int32), ("cam_solver", ctypes.c_int32)]
 
 
+class daba_pipeline(ctypes.Structure):
+    _fields_ = [("split", ctypes.c_double), ("cpass_b_warps", ctypes.c_int32), ("lpass_a_ctas", ctypes.c_int32),
+                ("prio", ctypes.c_int32 * 6)]
+
+
 _p = ctypes.c_void_p
 _i32, _i64, _st = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
 _SIGS = {
@@ -60,6 +65,7 @@ _SIGS = {
     "daba_import_checkpoint": (_st, [_p, _p, ctypes.c_size_t]),
     "daba_set_wait_limit": (_st, [_p, _i64]),
     "daba_set_persistent": (_st, [_p, ctypes.c_int]),
+    "daba_set_pipeline": (_st, [_p, ctypes.POINTER(daba_pipeline)]),
     "daba_set_partition": (_st, [_p, _i32, _p, _p]),
     "daba_get_partition_metrics": (_st, [_p, _p, _p, _p, _p]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
@@ -278,6 +284,10 @@ class Daba:
 
     def set_persistent(self, enable=True):
         self._check(daba_set_persistent(self._h, int(bool(enable))))
+
+    def set_pipeline(self, split=0.0, cpass_b_warps=0, lpass_a_ctas=0, prio=(0, 0, 1, 1, 0, 1)):
+        p = daba_pipeline(float(split), int(cpass_b_warps), int(lpass_a_ctas), (ctypes.c_int32 * 6)(*prio))
+        self._check(daba_set_pipeline(self._h, ctypes.byref(p)))
 
     def set_wait_limit(self, first_wait_ns):
         self._check(daba_set_wait_limit(self._h, int(first_wait_ns)))

@@ -30,6 +30,7 @@ constexpr int GSEG = 1024;        // iterations per run segment (device gamma / 
 constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (delta1, delta2, S, E)
 constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
 constexpr int RUN_GRAPH_MAX = 256;   // a run of at most this many iterations is one graph launch
+constexpr int64_t PIPE_MIN_NNZ = 1 << 20;   // two-range schedule by default from this many observations
 constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
@@ -125,6 +126,18 @@ struct daba_ctx {
        *blk_ci_obs = nullptr, *blk_ci_lm = nullptr, *blk_sums = nullptr, *blk_lsc = nullptr, *blk_isc = nullptr,
        *blk_E = nullptr, *blk_Fbar = nullptr, *blk_F = nullptr, *blk_rs = nullptr, *blk_bk = nullptr;
   std::vector<std::pair<void*, size_t>> blk_cap;
+  // two-range schedule (daba_set_pipeline): the cut (first camera and chunk of range B, 0 when
+  // there is none), the landmark tiles in launch order (range A small tiles, range A one-landmark
+  // tiles, the other small tiles, the other one-landmark tiles: pipe_nt of each), the counters of
+  // the bounded grids, one stream per kernel role and the events between them
+  daba_pipeline pipe{};
+  int pipe_cam = 0, pipe_chunk = 0;
+  int pipe_nt[4] = {0, 0, 0, 0};
+  void *d_tlist = nullptr, *d_ctr = nullptr;
+  cudaStream_t s_pipe[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_pipe[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n_sm = 0;
+  std::vector<int32_t> h_tile_lm, h_lmi_ptr, h_cam_chunk_ptr;
 };
 
 namespace {
@@ -315,16 +328,26 @@ IterParams iter_params(daba_ctx* ctx) {
   return P;
 }
 
+// Kernel ranges of one launch: the camera pass takes chunks c0 .. c1 - 1 (c1 < 0: all), with a
+// bounded grid of `grid` one-warp CTAs when ctr is set.
+struct PassRange {
+  int c0 = 0, c1 = -1;
+  unsigned* ctr = nullptr;
+  int grid = 0;
+};
+
 template <int LOSS, class Real, class Real2, bool HAS_LO>
-cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
+cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k, PassRange r = PassRange()) {
   const LossC<Real> L = loss_consts<Real>(ctx);
   const IterParams P = iter_params(ctx);
   const int threads = CPASS_WARPS * 32;
-  const int blocks = (ctx->n_chunks + CPASS_WARPS - 1) / CPASS_WARPS;
-  if (blocks == 0) return cudaSuccess;
+  const int c1 = r.c1 < 0 ? ctx->n_chunks : r.c1;
+  int blocks = (c1 - r.c0 + CPASS_WARPS - 1) / CPASS_WARPS;
+  if (blocks <= 0) return cudaSuccess;
   if (which == 1) {
+    if (r.ctr) blocks = std::min(blocks, r.grid);
     k_cpass<LOSS, Real, Real2><<<blocks, threads, 0, st>>>(
-        ctx->n_chunks, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
+        r.c0, c1, r.ctr, (const int*)ctx->chunk_cam, (const int*)ctx->chunk_beg, (const int*)ctx->c_lm,
         (const Real2*)ctx->c_u, (const V4<Real>*)pack_at(ctx, k), (const V4<Real>*)lmrec_at(ctx, k), L, P,
         (Real*)ctx->chunk_part, (const int*)ctx->c_rpos, (V4<Real>*)ctx->rec_a, (V4<Real>*)ctx->rec_b,
         (typename RecC<Real>::type*)ctx->rec_c);
@@ -338,25 +361,34 @@ cudaError_t launch_passes(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) 
 }
 
 template <class Real, class Real2, bool HAS_LO>
-cudaError_t launch_by_loss(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
+cudaError_t launch_by_loss(daba_ctx* ctx, cudaStream_t st, int which, int64_t k, PassRange r) {
   switch (ctx->opt.loss) {
-    case DABA_LOSS_TRIVIAL: return launch_passes<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st, which, k);
-    case DABA_LOSS_HUBER: return launch_passes<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st, which, k);
-    case DABA_LOSS_CAUCHY: return launch_passes<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st, which, k);
-    default: return launch_passes<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st, which, k);
+    case DABA_LOSS_TRIVIAL: return launch_passes<LOSS_TRIVIAL, Real, Real2, HAS_LO>(ctx, st, which, k, r);
+    case DABA_LOSS_HUBER: return launch_passes<LOSS_HUBER, Real, Real2, HAS_LO>(ctx, st, which, k, r);
+    case DABA_LOSS_CAUCHY: return launch_passes<LOSS_CAUCHY, Real, Real2, HAS_LO>(ctx, st, which, k, r);
+    default: return launch_passes<LOSS_WELSCH, Real, Real2, HAS_LO>(ctx, st, which, k, r);
   }
 }
 
-cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k) {
+cudaError_t launch_pass(daba_ctx* ctx, cudaStream_t st, int which, int64_t k, PassRange r = PassRange()) {
   ctx->launches++;
-  if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which, k);
-  return launch_by_loss<double, double2, false>(ctx, st, which, k);
+  if (is_mixed(ctx)) return launch_by_loss<float, float2, true>(ctx, st, which, k, r);
+  return launch_by_loss<double, double2, false>(ctx, st, which, k, r);
 }
 
-// landmark pass: small tiles, then the one-landmark tiles of long tracks
+// Tiles of one landmark-pass launch: positions q[c] .. q[c] + n[c] - 1 of the tile order (tlist, or
+// the tiles themselves when it is null) for the small (c = 0) and one-landmark (c = 1) tiles; the
+// small tiles with a bounded grid of `grid` CTAs when ctr is set.
+struct TileRange {
+  const int* tlist = nullptr;
+  int q[2] = {0, 0}, n[2] = {-1, -1};   // n < 0: every tile of the class
+  unsigned* ctr = nullptr;
+  int grid = 0;
+};
+
 // landmark pass: small tiles, then the one-landmark tiles of long tracks
 template <class Real, class Real2, bool HAS_LO>
-cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k, const TileRange& r) {
   const IterParams P = iter_params(ctx);
   LpassOut<Real> O;
   O.lmrec_out = (V4<Real>*)lmrec_at(ctx, k + 1);
@@ -370,12 +402,16 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   const int caps[2] = {ctx->opt.tile_obs, BIG_TILE_OBS};
   int t0 = 0;
   for (int c = 0; c < 2; ++c) {
-    const int nt = ctx->tile_class_end[c] - t0;
+    const int q0 = r.n[c] < 0 ? t0 : r.q[c];
+    const int nt = r.n[c] < 0 ? ctx->tile_class_end[c] - t0 : r.n[c];
     if (nt > 0) {
-      k_lpass<Real, Real2, HAS_LO><<<nt, LPASS_THREADS, lpass_smem_bytes<Real>(caps[c]), st>>>(
-          t0, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr, (const uint16_t*)ctx->t_inv,
-          (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b, (const typename RecC<Real>::type*)ctx->rec_c,
-          (const V4<Real>*)lmrec_at(ctx, k), (const V4<float>*)lmlo_at(ctx, k), P, (int*)ctx->tile_rs, O);
+      unsigned* ctr = c == 0 ? r.ctr : nullptr;
+      const int grid = ctr ? std::min(nt, r.grid) : nt;
+      k_lpass<Real, Real2, HAS_LO><<<grid, LPASS_THREADS, lpass_smem_bytes<Real>(caps[c]), st>>>(
+          q0, nt, r.tlist, ctr, caps[c], (const int*)ctx->tile_lm, (const int*)ctx->lm_ptr,
+          (const uint16_t*)ctx->t_inv, (const V4<Real>*)ctx->rec_a, (const V4<Real>*)ctx->rec_b,
+          (const typename RecC<Real>::type*)ctx->rec_c, (const V4<Real>*)lmrec_at(ctx, k),
+          (const V4<float>*)lmlo_at(ctx, k), P, (int*)ctx->tile_rs, O);
       ctx->launches++;
     }
     t0 = ctx->tile_class_end[c];
@@ -383,9 +419,9 @@ cudaError_t launch_lpass_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_lpass(daba_ctx* ctx, cudaStream_t st, int64_t k) {
-  if (is_mixed(ctx)) return launch_lpass_t<float, float2, true>(ctx, st, k);
-  return launch_lpass_t<double, double2, false>(ctx, st, k);
+cudaError_t launch_lpass(daba_ctx* ctx, cudaStream_t st, int64_t k, const TileRange& r = TileRange()) {
+  if (is_mixed(ctx)) return launch_lpass_t<float, float2, true>(ctx, st, k, r);
+  return launch_lpass_t<double, double2, false>(ctx, st, k, r);
 }
 
 cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
@@ -401,19 +437,22 @@ cudaError_t launch_prepare(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   return cudaGetLastError();
 }
 
+// camera solves of cameras i0 .. i1 - 1 (i1 < 0: all)
 template <int SOLVER>
-cudaError_t launch_camsolve_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
+cudaError_t launch_camsolve_t(daba_ctx* ctx, cudaStream_t st, int64_t k, int i0, int i1) {
+  if (i1 < 0) i1 = ctx->M;
+  if (i1 <= i0) return cudaSuccess;
   ctx->launches++;
   const IterParams P = iter_params(ctx);
-  const int blocks = (ctx->M + 31) / 32;   // 32 cameras per CTA (two warps)
+  const int blocks = (i1 - i0 + 31) / 32;   // 32 cameras per CTA (two warps)
   if (is_mixed(ctx))
-    k_camsolve<float, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
+    k_camsolve<float, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(i0, i1, (const int*)ctx->cam_chunk_ptr, (const float*)ctx->chunk_part,
                                              (double*)ctx->cam_x, (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P,
                                              (double*)ctx->cam_S, (double*)ctx->cam_E, (double*)ctx->cam_F,
                                              (double*)ctx->cam_Fb, (uint8_t*)ctx->cam_rs, (double*)ctx->cam_Fsum,
                                              (V4<float>*)pack_at(ctx, k + 1));
   else
-    k_camsolve<double, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(ctx->M, (const int*)ctx->cam_chunk_ptr,
+    k_camsolve<double, SOLVER><<<blocks, CAMSOLVE_THREADS, 0, st>>>(i0, i1, (const int*)ctx->cam_chunk_ptr,
                                               (const double*)ctx->chunk_part, (double*)ctx->cam_x,
                                               (double*)ctx->cam_dx, (double*)ctx->cam_Rbar, P, (double*)ctx->cam_S,
                                               (double*)ctx->cam_E, (double*)ctx->cam_F, (double*)ctx->cam_Fb,
@@ -422,9 +461,9 @@ cudaError_t launch_camsolve_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k) {
-  if (ctx->opt.cam_solver == DABA_CAM_LM) return launch_camsolve_t<CAM_LM>(ctx, st, k);
-  return launch_camsolve_t<CAM_SCAM>(ctx, st, k);
+cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k, int i0 = 0, int i1 = -1) {
+  if (ctx->opt.cam_solver == DABA_CAM_LM) return launch_camsolve_t<CAM_LM>(ctx, st, k, i0, i1);
+  return launch_camsolve_t<CAM_SCAM>(ctx, st, k, i0, i1);
 }
 
 cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
@@ -649,6 +688,63 @@ cudaEvent_t ev(daba_ctx* ctx, size_t i) {
   return ctx->events[i];
 }
 
+void pipe_streams_free(daba_ctx* ctx) {
+  for (int r = 0; r < 6; ++r) {
+    if (ctx->s_pipe[r]) {
+      cudaStreamSynchronize(ctx->s_pipe[r]);
+      cudaStreamDestroy(ctx->s_pipe[r]);
+    }
+    if (ctx->ev_pipe[r]) cudaEventDestroy(ctx->ev_pipe[r]);
+    ctx->s_pipe[r] = nullptr;
+    ctx->ev_pipe[r] = nullptr;
+  }
+}
+
+// The cut of the two-range schedule for the current observations (daba_set_pipeline): range A
+// holds the cameras before the first camera whose observations start at or after split * nnz.
+// Tiles whose landmarks only range-A cameras observe come first in the tile order of d_tlist.
+daba_status pipe_cut(daba_ctx* ctx, cudaStream_t st) {
+  ctx->pipe_cam = ctx->pipe_chunk = 0;
+  for (int& v : ctx->pipe_nt) v = 0;
+  if (!(ctx->pipe.split > 0.0) || ctx->h_tile_lm.empty()) return DABA_OK;
+  const int M = ctx->M;
+  const double at = ctx->pipe.split * (double)ctx->nnz;
+  int cut = M;
+  for (int i = 0; i < M; ++i)
+    if ((double)ctx->h_cam_ptr[i] >= at) {
+      cut = i;
+      break;
+    }
+  if (cut <= 0 || cut >= M || ctx->h_cam_chunk_ptr[cut] <= 0 || ctx->h_cam_chunk_ptr[cut] >= ctx->n_chunks)
+    return DABA_OK;
+  // per tile: does a camera of range B observe one of its landmarks?
+  const int n_tiles = ctx->n_tiles;
+  std::vector<uint8_t> tile_b(n_tiles, 0);
+  for (int t = 0; t < n_tiles; ++t) {
+    const int ob = ctx->h_lmi_ptr[ctx->h_tile_lm[t]], oe = ctx->h_lmi_ptr[ctx->h_tile_lm[t + 1]];
+    for (int o = ob; o < oe && !tile_b[t]; ++o)
+      if (ctx->h_cam_idx[ctx->h_li_order[o]] >= cut) tile_b[t] = 1;
+  }
+  std::vector<int32_t> tl;
+  tl.reserve(n_tiles);
+  int nt[4] = {0, 0, 0, 0};
+  for (int b = 0; b < 2; ++b)
+    for (int c = 0; c < 2; ++c) {
+      const int t0 = c == 0 ? 0 : ctx->tile_class_end[0], t1 = ctx->tile_class_end[c];
+      for (int t = t0; t < t1; ++t)
+        if (tile_b[t] == b) {
+          tl.push_back(t);
+          ++nt[2 * b + c];
+        }
+    }
+  CK(cudaMemcpyAsync(ctx->d_tlist, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->pipe_cam = cut;
+  ctx->pipe_chunk = ctx->h_cam_chunk_ptr[cut];
+  for (int q = 0; q < 4; ++q) ctx->pipe_nt[q] = nt[q];
+  return DABA_OK;
+}
+
 void drop_graphs(daba_ctx* ctx) {
   for (auto& row : ctx->graph)
     for (cudaGraphExec_t& g : row) {
@@ -662,17 +758,91 @@ void drop_graphs(daba_ctx* ctx) {
   }
 }
 
-// Enqueues n iterations of Algorithm 1 starting at an iteration of parity k0 & 1 on stream st
-// (the camera pass, then the landmark pass and the camera solves on two priority streams,
-// joined before the reduction); with timing, records the per-kernel events from index evi.
-cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, size_t evi) {
 #define CE(call)                             \
   do {                                       \
     cudaError_t e_ = (call);                 \
     if (e_ != cudaSuccess) return e_;        \
   } while (0)
+
+// The two-range schedule applies (daba_set_pipeline): a cut is set and the iteration is the
+// default one (per-block restart, no coarse blocks, no per-kernel timing).
+bool pipe_active(const daba_ctx* ctx) {
+  return ctx->pipe_cam > 0 && !ctx->timing && ctx->n_blocks == 0 && !ctx->persistent &&
+         ctx->opt.restart_mode == DABA_RESTART_BLOCK;
+}
+
+// One iteration k on the two-range schedule. Streams by role (daba_set_pipeline's order):
+//   0: camera pass A ----+--> 1: camera solves A
+//                        +--> 2: landmark tiles observed by range A only
+//   3: camera pass B ----+--> 4: camera solves B
+//                        +--> 5: the other landmark tiles (after both camera passes)
+// then st waits for 1, 2, 4 and 5 and runs the reduction. Every kernel reads and writes what it
+// does in the one-range order; each camera solve and landmark tile only waits for the camera-pass
+// chunks it reads, so the results are the same bits.
+cudaError_t enqueue_iter_split(daba_ctx* ctx, cudaStream_t st, int64_t kk) {
+  cudaStream_t* S = ctx->s_pipe;
+  cudaEvent_t* E = ctx->ev_pipe;
+  unsigned* ctr = (unsigned*)ctx->d_ctr;
+  CE(cudaEventRecord(ctx->ev_fork, st));
+  CE(cudaStreamWaitEvent(S[0], ctx->ev_fork, 0));
+  CE(cudaStreamWaitEvent(S[3], ctx->ev_fork, 0));
+  PassRange ra;
+  ra.c1 = ctx->pipe_chunk;
+  CE(launch_pass(ctx, S[0], 1, kk, ra));
+  CE(cudaEventRecord(E[0], S[0]));
+  PassRange rb;
+  rb.c0 = ctx->pipe_chunk;
+  if (ctx->pipe.cpass_b_warps > 0) {
+    rb.ctr = ctr;
+    rb.grid = ctx->pipe.cpass_b_warps * ctx->n_sm / CPASS_WARPS;
+  }
+  CE(launch_pass(ctx, S[3], 1, kk, rb));
+  CE(cudaEventRecord(E[3], S[3]));
+  CE(cudaStreamWaitEvent(S[1], E[0], 0));
+  CE(launch_camsolve(ctx, S[1], kk, 0, ctx->pipe_cam));
+  CE(cudaEventRecord(E[1], S[1]));
+  CE(cudaStreamWaitEvent(S[2], E[0], 0));
+  TileRange ta;
+  ta.tlist = (const int*)ctx->d_tlist;
+  ta.q[0] = 0;
+  ta.n[0] = ctx->pipe_nt[0];
+  ta.q[1] = ctx->pipe_nt[0];
+  ta.n[1] = ctx->pipe_nt[1];
+  if (ctx->pipe.lpass_a_ctas > 0) {
+    ta.ctr = ctr + 2;
+    ta.grid = ctx->pipe.lpass_a_ctas * ctx->n_sm;
+  }
+  CE(launch_lpass(ctx, S[2], kk, ta));
+  CE(cudaEventRecord(E[2], S[2]));
+  CE(cudaStreamWaitEvent(S[4], E[3], 0));
+  CE(launch_camsolve(ctx, S[4], kk, ctx->pipe_cam, ctx->M));
+  CE(cudaEventRecord(E[4], S[4]));
+  CE(cudaStreamWaitEvent(S[5], E[3], 0));
+  CE(cudaStreamWaitEvent(S[5], E[0], 0));
+  TileRange tb;
+  tb.tlist = (const int*)ctx->d_tlist;
+  tb.q[0] = ctx->pipe_nt[0] + ctx->pipe_nt[1];
+  tb.n[0] = ctx->pipe_nt[2];
+  tb.q[1] = tb.q[0] + ctx->pipe_nt[2];
+  tb.n[1] = ctx->pipe_nt[3];
+  CE(launch_lpass(ctx, S[5], kk, tb));
+  CE(cudaEventRecord(E[5], S[5]));
+  for (int r : {1, 2, 4, 5}) CE(cudaStreamWaitEvent(st, E[r], 0));
+  CE(launch_finalize(ctx, st));
+  return cudaSuccess;
+}
+
+// Enqueues n iterations of Algorithm 1 starting at an iteration of parity k0 & 1 on stream st
+// (the camera pass, then the landmark pass and the camera solves on two priority streams,
+// joined before the reduction; or the two-range schedule); with timing, records the per-kernel
+// events from index evi.
+cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, size_t evi) {
   for (int j = 0; j < n; ++j) {
     const int64_t kk = k0 + j;
+    if (pipe_active(ctx)) {
+      CE(enqueue_iter_split(ctx, st, kk));
+      continue;
+    }
     CE(cudaEventRecord(ctx->ev_fork, st));
     CE(cudaStreamWaitEvent(ctx->s_hi, ctx->ev_fork, 0));
     if (ctx->timing) CE(rec_time(ev(ctx, evi + 0), ctx->s_hi));
@@ -702,7 +872,13 @@ cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, siz
     if (ctx->timing) evi += 7;
   }
   return cudaSuccess;
+}
 #undef CE
+
+// Graph instantiation: on the two-range schedule the kernel nodes keep the priorities of the
+// streams they were captured on (otherwise a graph ignores them).
+cudaError_t instantiate(const daba_ctx* ctx, cudaGraphExec_t* exec, cudaGraph_t g) {
+  return cudaGraphInstantiateWithFlags(exec, g, pipe_active(ctx) ? cudaGraphInstantiateFlagUseNodePriority : 0);
 }
 
 // Captures the four iteration graphs (GRAPH_ITERS and 1 iterations, even and odd start) on
@@ -720,7 +896,7 @@ daba_status ensure_graphs(daba_ctx* ctx) {
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
         e = e1 != cudaSuccess ? e1 : e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph[gi][par], g, 0);
+        if (e == cudaSuccess) e = instantiate(ctx, &ctx->graph[gi][par], g);
         if (g) cudaGraphDestroy(g);
       }
       ctx->graph_nl[gi] = ctx->launches - l0;
@@ -758,7 +934,7 @@ daba_status ensure_run_graph(daba_ctx* ctx, int n) {
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(ctx->s_cap, &g);
     e = e1 != cudaSuccess ? e1 : e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->run_graph[par], g, 0);
+    if (e == cudaSuccess) e = instantiate(ctx, &ctx->run_graph[par], g);
     if (g) cudaGraphDestroy(g);
   }
   ctx->run_graph_nl[par] = ctx->launches - l0;
@@ -1076,6 +1252,7 @@ cudaError_t adjoint_iter_by_loss(daba_ctx* ctx, cudaStream_t st, int64_t k, doub
 }
 
 daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int32_t* restarts, cudaStream_t st);
+daba_status pipe_apply(daba_ctx* ctx, const daba_pipeline& p);
 
 }  // namespace
 
@@ -1116,6 +1293,7 @@ void daba_destroy(daba_ctx* ctx) {
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_hi, ctx->ev_lo, ctx->ev_cap0, ctx->ev_cap1})
     if (e) cudaEventDestroy(e);
+  pipe_streams_free(ctx);
   if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
   if (ctx->s_lo) cudaStreamDestroy(ctx->s_lo);
   if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
@@ -1226,6 +1404,8 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(d_scene_f, (size_t)M * 8);
   AL(bk, backup_layout(ctx).bytes);
   AL(d_gbar, 16);
+  AL(d_tlist, (size_t)(ctx->max_tiles + 1) * 4);
+  AL(d_ctr, 64);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -1252,10 +1432,23 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_linv);   // identity numbering until observations are set
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_lperm);
   cudaMemset(ctx->fin_ticket, 0, 16);
+  cudaMemset(ctx->d_ctr, 0, 64);
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->dev);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
+    daba_destroy(ctx);
+    return DABA_ERR_CUDA;
+  }
+  // default schedule: two camera ranges cut at half the observations for problems of at least
+  // PIPE_MIN_NNZ observations (measured on B300, 100 MIXED iterations: 26M observations 0.749 to
+  // 0.706 ms per iteration, 8M in 512 scenes 0.367 to 0.363, 1M 83.1 to 82.1 us)
+  daba_pipeline dp{};
+  dp.split = nnz >= PIPE_MIN_NNZ ? 0.5 : 0.0;
+  const int32_t ranks[6] = {0, 0, 1, 1, 0, 1};
+  for (int r = 0; r < 6; ++r) dp.prio[r] = ranks[r];
+  if (pipe_apply(ctx, dp) != DABA_OK) {
     daba_destroy(ctx);
     return DABA_ERR_CUDA;
   }
@@ -1409,6 +1602,10 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_ci_order.swap(ci_order);
   ctx->h_lperm.swap(lperm);
   ctx->h_linv.swap(linv);
+  ctx->h_tile_lm.swap(tile_lm);
+  ctx->h_lmi_ptr.swap(lmi_ptr);
+  ctx->h_cam_chunk_ptr.swap(cam_chunk_ptr);
+  if ((s = pipe_cut(ctx, st)) != DABA_OK) return s;
   ctx->u_scale_uploaded = -1.0;
   ctx->h_uv_stale = false;
   drop_graphs(ctx);   // the graphs hold the old schedule sizes
@@ -1547,6 +1744,7 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
   int done = 0;
   std::vector<double> gam(GSEG + 1);
   CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_ctr, 0, 64, st));   // bounded-grid counters (two-range schedule)
   while (done < iters) {
     const int seg = std::min(GSEG, iters - done);
     // gamma^(k) .. gamma^(k+seg) (Eq. nesterov_scalar); the last one is the look-ahead used
@@ -2239,6 +2437,45 @@ daba_status daba_get_partition_metrics(daba_ctx* ctx, double* F_blk, double* Fba
   }
   return DABA_OK;
 }
+
+daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (!p) return fail(ctx, DABA_ERR_ARG, "null schedule");
+  if (!(p->split >= 0.0 && p->split < 1.0)) return fail(ctx, DABA_ERR_ARG, "split must lie in [0, 1)");
+  if (p->cpass_b_warps < 0 || p->cpass_b_warps > 64 || p->lpass_a_ctas < 0 || p->lpass_a_ctas > 64)
+    return fail(ctx, DABA_ERR_ARG, "grid bounds must lie in [0, 64]");
+  for (int r = 0; r < 6; ++r)
+    if (p->prio[r] < 0 || p->prio[r] > 2) return fail(ctx, DABA_ERR_ARG, "priority ranks must lie in [0, 2]");
+  return pipe_apply(ctx, *p);
+}
+
+}  // extern "C"
+
+namespace {
+// Sets the two-range schedule (arguments checked by the caller): one stream per kernel role at
+// its priority, the events between them, and the cut for the current observations.
+daba_status pipe_apply(daba_ctx* ctx, const daba_pipeline& p) {
+  pipe_streams_free(ctx);
+  drop_graphs(ctx);
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  for (int r = 0; r < 6; ++r) {
+    const int prio = std::min(least, greatest + p.prio[r]);   // greater numbers are lower priorities
+    if (cudaStreamCreateWithPriority(&ctx->s_pipe[r], cudaStreamNonBlocking, prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_pipe[r], cudaEventDisableTiming) != cudaSuccess) {
+      const cudaError_t e = cudaGetLastError();
+      pipe_streams_free(ctx);
+      ctx->pipe = daba_pipeline{};
+      ctx->pipe_cam = 0;
+      return fail(ctx, DABA_ERR_CUDA, "creating the schedule's streams: %s", cudaGetErrorString(e));
+    }
+  }
+  ctx->pipe = p;
+  return pipe_cut(ctx, nullptr);
+}
+}  // namespace
+
+extern "C" {
 
 daba_status daba_set_persistent(daba_ctx* ctx, int enable) {
   if (!ctx) return DABA_ERR_ARG;

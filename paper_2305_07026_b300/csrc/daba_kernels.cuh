@@ -454,20 +454,43 @@ __device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Re
     acc.reduce_store(lane, part + (size_t)warp * CP_STRIDE);
 }
 
+// Chunks c0 .. c1 - 1. Without a counter (ctr null) one warp per chunk. With one, a bounded grid
+// whose warps take the chunks in order from ctr[0]; the warp that leaves last (ctr[1] counts the
+// warps out) sets both back to zero for the next launch. No warp waits on another.
 template <int LOSS, class Real, class Real2>
 __global__ void __launch_bounds__(CPASS_WARPS * 32)
-    k_cpass(int n_chunks, const int* __restrict__ chunk_cam, const int* __restrict__ chunk_beg,
-            const int* __restrict__ c_lm, const Real2* __restrict__ c_u, const V4<Real>* __restrict__ pack,
-            const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P, Real* __restrict__ part,
-            const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a, V4<Real>* __restrict__ rec_b,
-            typename RecC<Real>::type* __restrict__ rec_c) {
+    k_cpass(int c0, int c1, unsigned* __restrict__ ctr, const int* __restrict__ chunk_cam,
+            const int* __restrict__ chunk_beg, const int* __restrict__ c_lm, const Real2* __restrict__ c_u,
+            const V4<Real>* __restrict__ pack, const V4<Real>* __restrict__ lmrec, LossC<Real> L, IterParams P,
+            Real* __restrict__ part, const int* __restrict__ c_rpos, V4<Real>* __restrict__ rec_a,
+            V4<Real>* __restrict__ rec_b, typename RecC<Real>::type* __restrict__ rec_c) {
   __shared__ CpassWarpSmem<Real, Real2> sm[CPASS_WARPS];
   const int wib = threadIdx.x >> 5;
-  const int warp = blockIdx.x * CPASS_WARPS + wib;
   const int lane = threadIdx.x & 31;
-  if (warp >= n_chunks) return;
-  cpass_chunk<LOSS, Real, Real2, false>(warp, lane, sm[wib], Real(P.gam[*P.it]), chunk_cam, chunk_beg, c_lm, c_u,
-                                        pack, lmrec, L, part, c_rpos, rec_a, rec_b, rec_c);
+  const Real gamma = Real(P.gam[*P.it]);
+  if (ctr == nullptr) {
+    const int warp = c0 + blockIdx.x * CPASS_WARPS + wib;
+    if (warp >= c1) return;
+    cpass_chunk<LOSS, Real, Real2, false>(warp, lane, sm[wib], gamma, chunk_cam, chunk_beg, c_lm, c_u, pack, lmrec, L,
+                                          part, c_rpos, rec_a, rec_b, rec_c);
+    return;
+  }
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = c0 + (int)atomicAdd(ctr, 1u);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= c1) break;
+    __syncwarp();   // every lane is done with the previous chunk's shared memory
+    cpass_chunk<LOSS, Real, Real2, false>(c, lane, sm[wib], gamma, chunk_cam, chunk_beg, c_lm, c_u, pack, lmrec, L,
+                                          part, c_rpos, rec_a, rec_b, rec_c);
+  }
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1u) == gridDim.x * CPASS_WARPS - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+    }
+  }
 }
 
 // The camera pass with coarse blocks (FP64): c_intra[o] marks the camera-sorted observations
@@ -744,7 +767,7 @@ __device__ __forceinline__ void lpass_tile_sums(int nrs, double gsum, bool globa
 // One tile of the landmark pass by the CTA's LPASS_THREADS threads (smem_raw: the tile's shared
 // memory; gamma and first of this iteration). Every thread of the CTA calls it. Returns false if
 // a bounded wait ran out (the tile is then skipped, flag bit 2 set).
-template <class Real, class Real2, bool HAS_LO, bool COH>
+template <class Real, class Real2, bool HAS_LO, bool COH, bool REINIT = COH>
 __device__ __forceinline__ bool lpass_tile(int tile, int no_cap, unsigned char* smem_raw, Real gamma, int first,
                                            const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
                                            const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
@@ -808,20 +831,46 @@ __device__ __forceinline__ bool lpass_tile(int tile, int no_cap, unsigned char* 
     nrs = lpass_landmark<Real, HAS_LO>(sca, scb, scc + (ob - cs), sinv + (ob - is), s0, s1, A, B, lo0, g, gamma, first,
                                        P, O, gsum);
   lpass_tile_sums(nrs, gsum, P.accelerated && P.restart_global, tile, tile_rs, P.g_tile);   // ends every thread's reads
-  if (COH && threadIdx.x == 0) mbar_inval(bar);   // the CTA initialises it again for its next tile
+  if (REINIT && threadIdx.x == 0) mbar_inval(bar);   // the CTA initialises it again for its next tile
   return ok;
 }
 
+// Tiles q0 .. q0 + nq - 1 of the launch's tile order (tile q, or tlist[q] with a list). Without a
+// counter (ctr null) one CTA per tile; with one, a bounded grid whose CTAs take the tiles in order
+// from ctr[0], reset by the CTA that leaves last as in k_cpass.
 template <class Real, class Real2, bool HAS_LO>
 __global__ void __launch_bounds__(LPASS_THREADS)
-    k_lpass(int tile0, int no_cap, const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr,
-            const uint16_t* __restrict__ t_inv, const V4<Real>* __restrict__ rec_a,
-            const V4<Real>* __restrict__ rec_b, const typename RecC<Real>::type* __restrict__ rec_c,
-            const V4<Real>* __restrict__ lmrec, const V4<float>* __restrict__ lm_lo, IterParams P,
-            int* __restrict__ tile_rs, LpassOut<Real> O) {
+    k_lpass(int q0, int nq, const int* __restrict__ tlist, unsigned* __restrict__ ctr, int no_cap,
+            const int* __restrict__ tile_lm, const int* __restrict__ lm_ptr, const uint16_t* __restrict__ t_inv,
+            const V4<Real>* __restrict__ rec_a, const V4<Real>* __restrict__ rec_b,
+            const typename RecC<Real>::type* __restrict__ rec_c, const V4<Real>* __restrict__ lmrec,
+            const V4<float>* __restrict__ lm_lo, IterParams P, int* __restrict__ tile_rs, LpassOut<Real> O) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  lpass_tile<Real, Real2, HAS_LO, false>(tile0 + blockIdx.x, no_cap, smem_raw, Real(P.gam[*P.it]), *P.first, tile_lm,
-                                         lm_ptr, t_inv, rec_a, rec_b, rec_c, lmrec, lm_lo, P, tile_rs, O);
+  const Real gamma = Real(P.gam[*P.it]);
+  const int first = *P.first;
+  if (ctr == nullptr) {
+    const int q = q0 + blockIdx.x;
+    lpass_tile<Real, Real2, HAS_LO, false>(tlist ? tlist[q] : q, no_cap, smem_raw, gamma, first, tile_lm, lm_ptr,
+                                           t_inv, rec_a, rec_b, rec_c, lmrec, lm_lo, P, tile_rs, O);
+    return;
+  }
+  __shared__ int s_q;
+  for (;;) {
+    if (threadIdx.x == 0) s_q = (int)atomicAdd(ctr, 1u);
+    __syncthreads();
+    const int q = s_q;   // read by every thread before the barriers inside the tile let thread 0 on
+    if (q >= nq) break;
+    lpass_tile<Real, Real2, HAS_LO, false, true>(tlist ? tlist[q0 + q] : q0 + q, no_cap, smem_raw, gamma, first,
+                                                 tile_lm, lm_ptr, t_inv, rec_a, rec_b, rec_c, lmrec, lm_lo, P,
+                                                 tile_rs, O);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1328,12 +1377,12 @@ __global__ void k_cam_prepare(int M, const double* __restrict__ cam_x, const dou
 // The FP32 S-CAM path is held to 5 CTAs per SM (at most 168 registers, a few hundred bytes of
 // spills): batches of many small scenes fill more than one wave of CTAs, and 10 instead of 8
 // resident warps per SM shorten the second. The FP64 and LM paths would spill heavily and keep 255.
-// One group of 32 cameras (cameras 32 grp .. 32 grp + 31) by two warps (role 0 and 1, lanes
-// 0..31 each); sh_mm is the group's hand-over buffer in shared memory. Both warps of the CTA
+// One group of 32 cameras (cameras i0 + 32 grp .. i0 + 32 grp + 31, those below M) by two warps
+// (role 0 and 1, lanes 0..31 each); sh_mm is the group's hand-over buffer in shared memory. Both warps of the CTA
 // pass the barrier inside, so every thread of the CTA calls it the same number of times.
 template <class Real, int SOLVER, bool COH>
 __device__ __forceinline__ void camsolve_group(int grp, int role, int lane, double (*sh_mm)[16], int it, int first,
-                                               int M, const int* __restrict__ cam_chunk_ptr,
+                                               int i0, int M, const int* __restrict__ cam_chunk_ptr,
                                                const Real* __restrict__ part, double* __restrict__ cam_x,
                                                double* __restrict__ cam_dx, double* __restrict__ cam_Rbar,
                                                const IterParams& P, double* __restrict__ cam_S,
@@ -1347,7 +1396,7 @@ __device__ __forceinline__ void camsolve_group(int grp, int role, int lane, doub
   static_assert(CAMSOLVE_THREADS == 64, "two warps per CTA");
   using T = double;
   using N = Num<T>;
-  const int i = grp * 32 + lane;
+  const int i = i0 + grp * 32 + lane;
   const bool valid = i < M;
   const T xi = N::from(P.xi);
   CamT<T> ck, cn;
@@ -1496,13 +1545,14 @@ __device__ __forceinline__ void camsolve_group(int grp, int role, int lane, doub
 
 template <class Real, int SOLVER>
 __global__ void __launch_bounds__(CAMSOLVE_THREADS, (sizeof(Real) == 4 && SOLVER == CAM_SCAM) ? 5 : 1)
-    k_camsolve(int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
+    k_camsolve(int i0, int M, const int* __restrict__ cam_chunk_ptr, const Real* __restrict__ part,
                double* __restrict__ cam_x, double* __restrict__ cam_dx, double* __restrict__ cam_Rbar, IterParams P,
                double* __restrict__ cam_S, double* __restrict__ cam_E, double* __restrict__ cam_F,
                double* __restrict__ cam_Fb, uint8_t* __restrict__ cam_rs, double* __restrict__ cam_Fsum,
                V4<Real>* __restrict__ pack_next) {
+  // cameras i0 .. M - 1, 32 per CTA
   __shared__ double sh_mm[32][16];   // MM solution R(9) t(3) d(3) and its dEn
-  camsolve_group<Real, SOLVER, false>(blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31, sh_mm, *P.it, *P.first, M,
+  camsolve_group<Real, SOLVER, false>(blockIdx.x, threadIdx.x >> 5, threadIdx.x & 31, sh_mm, *P.it, *P.first, i0, M,
                                       cam_chunk_ptr, part, cam_x, cam_dx, cam_Rbar, P, cam_S, cam_E, cam_F, cam_Fb,
                                       cam_rs, cam_Fsum, pack_next);
 }
@@ -1714,7 +1764,7 @@ __global__ void __launch_bounds__(PERS_THREADS, 3)
       for (int item = blockIdx.x; item < n_cs + A.n_tiles; item += G) {
         if (item < n_cs) {
           double(*sh)[16] = reinterpret_cast<double(*)[16]>(smem) + (wib >> 1) * 32;
-          camsolve_group<float, CAM_SCAM, true>(2 * item + (wib >> 1), wib & 1, lane, sh, j, first, A.M,
+          camsolve_group<float, CAM_SCAM, true>(2 * item + (wib >> 1), wib & 1, lane, sh, j, first, 0, A.M,
                                                 A.cam_chunk_ptr, A.part, A.cam_x, A.cam_dx, A.cam_Rbar, P, A.cam_S,
                                                 A.cam_E, A.cam_F, A.cam_Fb, A.cam_rs, A.cam_Fsum, A.pack[par ^ 1]);
           __syncthreads();   // the hand-over buffers are read before the next item reuses the memory

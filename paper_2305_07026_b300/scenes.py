@@ -287,7 +287,7 @@ def _finish(name, rng, R, t, f, k1, k2, L, cam_idx, lm_idx, outlier_frac, loss, 
 
 
 # ----------------------------------------------------------------------------
-# workload 0: circle of cameras around a cube of points
+# circle workload: cameras on a circle around a cube of points
 # ----------------------------------------------------------------------------
 
 def circle_scene(seed=0, n_cams=20, n_lms=2000, radius=10.0, half=2.0, cap=8,

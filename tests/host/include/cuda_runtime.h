@@ -24,6 +24,7 @@ inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); retu
 inline long long __double_as_longlong(double d) { long long u; std::memcpy(&u, &d, 8); return u; }
 inline double __longlong_as_double(long long u) { double d; std::memcpy(&d, &u, 8); return d; }
 template <class T> T __shfl_xor_sync(unsigned, T v, int) { return v; }
+template <class T> T __shfl_sync(unsigned, T v, int) { return v; }
 template <class T> T __ldg(const T* p) { return *p; }
 template <class T> T __ldcg(const T* p) { return *p; }
 inline void __nanosleep(unsigned) {}
