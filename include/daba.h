@@ -291,27 +291,27 @@ daba_status daba_get_partition_metrics(daba_ctx* ctx, double* F_blk, double* Fba
  * per-kernel timing does not apply. */
 daba_status daba_set_persistent(daba_ctx* ctx, int enable);
 
-/* Two-range schedule of each iteration (a schedule option like chunk_obs: the iterates, metrics
- * and objective trace are the same bits with it and without it; no paper counterpart). The
- * cameras are cut at the first camera whose observations, in camera order, start at or after
- * split * nnz. The camera pass over the cameras before the cut (range A) runs first; when it is
- * done, the camera solves of range A and the landmark tiles observed by range-A cameras only run
- * beside the camera pass over range B, whose solves and the remaining tiles follow it. Kernels
- * that run beside one another can be held to bounded grids, so that both keep CTAs on every SM:
- *   split          0 (no cut, the default) or a fraction in (0, 1)
- *   cpass_b_warps  resident warps per SM of the range-B camera pass (0: one CTA per chunk)
- *   lpass_a_ctas   resident CTAs per SM of the range-A landmark pass (0: one CTA per tile)
- *   prio[6]        stream-priority rank, 0 (highest) to 2, of: camera pass A, camera solves A,
- *                  landmark pass A, camera pass B, camera solves B, landmark pass B
- * It applies to the graph path (runs without per-kernel timing) of contexts with the per-block
- * restart, no coarse blocks and the persistent path off, and is ignored elsewhere; the cut is
- * recomputed when the observations change. A cut that leaves a range empty runs one range.
- * DABA_ERR_ARG if split is outside [0, 1), a bound is outside [0, 64] or a rank outside [0, 2]. */
+/* Range schedule of each iteration (a schedule option like chunk_obs: the iterates, metrics and
+ * objective trace are the same bits with it and without it; no paper counterpart). The cameras
+ * are cut into `ranges` ranges of about equal observation counts (camera order; a camera is never
+ * split, so heavy cameras can leave fewer ranges). The camera pass runs range by range; the camera
+ * solves of a range start as soon as its chunks are done, beside the camera passes of the later
+ * ranges, and the landmark tiles whose observing cameras all lie in ranges 0 .. r start when the
+ * camera passes of those ranges are done.
+ *   ranges       1 (one range) .. 64
+ *   cpass_warps  resident warps per SM of each camera-pass launch (0: one CTA per chunk)
+ *   lpass_ctas   resident CTAs per SM of each landmark-pass launch of small tiles (0: one per tile)
+ *   prio[3]      stream-priority rank, 0 (highest) to 2, of the camera passes, the camera solves
+ *                and the landmark passes
+ * Defaults: 2 ranges, ranks (1, 0, 1), no bounds, for problems of at least 2^20 observations;
+ * 1 range below. It applies to the graph path (runs without per-kernel timing) of contexts with
+ * the per-block restart, no coarse blocks and the persistent path off, and is ignored elsewhere;
+ * the ranges are recomputed when the observations change. DABA_ERR_ARG for a value out of range. */
 typedef struct {
-  double split;
-  int32_t cpass_b_warps;
-  int32_t lpass_a_ctas;
-  int32_t prio[6];
+  int32_t ranges;
+  int32_t cpass_warps;
+  int32_t lpass_ctas;
+  int32_t prio[3];
 } daba_pipeline;
 daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p);
 

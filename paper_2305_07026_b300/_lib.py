@@ -40,8 +40,8 @@ class daba_options(ctypes.Structure):
 
 
 class daba_pipeline(ctypes.Structure):
-    _fields_ = [("split", ctypes.c_double), ("cpass_b_warps", ctypes.c_int32), ("lpass_a_ctas", ctypes.c_int32),
-                ("prio", ctypes.c_int32 * 6)]
+    _fields_ = [("ranges", ctypes.c_int32), ("cpass_warps", ctypes.c_int32), ("lpass_ctas", ctypes.c_int32),
+                ("prio", ctypes.c_int32 * 3)]
 
 
 _p = ctypes.c_void_p
@@ -285,8 +285,8 @@ class Daba:
     def set_persistent(self, enable=True):
         self._check(daba_set_persistent(self._h, int(bool(enable))))
 
-    def set_pipeline(self, split=0.0, cpass_b_warps=0, lpass_a_ctas=0, prio=(0, 0, 1, 1, 0, 1)):
-        p = daba_pipeline(float(split), int(cpass_b_warps), int(lpass_a_ctas), (ctypes.c_int32 * 6)(*prio))
+    def set_pipeline(self, ranges=1, cpass_warps=0, lpass_ctas=0, prio=(1, 0, 1)):
+        p = daba_pipeline(int(ranges), int(cpass_warps), int(lpass_ctas), (ctypes.c_int32 * 3)(*prio))
         self._check(daba_set_pipeline(self._h, ctypes.byref(p)))
 
     def set_wait_limit(self, first_wait_ns):

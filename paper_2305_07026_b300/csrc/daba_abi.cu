@@ -31,6 +31,8 @@ constexpr int LREC = 8;           // landmark record: two V4 (l[3], delta0), (de
 constexpr int GRAPH_ITERS = 8;    // iterations per captured graph (even: keeps the buffer parity)
 constexpr int RUN_GRAPH_MAX = 256;   // a run of at most this many iterations is one graph launch
 constexpr int64_t PIPE_MIN_NNZ = 1 << 20;   // two-range schedule by default from this many observations
+constexpr int PIPE_MAX_RANGES = 64;
+constexpr int PIPE_POOL = 8;   // streams per kernel role of the range schedule
 constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
 
 }  // namespace
@@ -126,16 +128,17 @@ struct daba_ctx {
        *blk_ci_obs = nullptr, *blk_ci_lm = nullptr, *blk_sums = nullptr, *blk_lsc = nullptr, *blk_isc = nullptr,
        *blk_E = nullptr, *blk_Fbar = nullptr, *blk_F = nullptr, *blk_rs = nullptr, *blk_bk = nullptr;
   std::vector<std::pair<void*, size_t>> blk_cap;
-  // two-range schedule (daba_set_pipeline): the cut (first camera and chunk of range B, 0 when
-  // there is none), the landmark tiles in launch order (range A small tiles, range A one-landmark
-  // tiles, the other small tiles, the other one-landmark tiles: pipe_nt of each), the counters of
-  // the bounded grids, one stream per kernel role and the events between them
+  // range schedule (daba_set_pipeline): the R ranges in use (1: the one-range iteration), their
+  // camera and chunk bounds, the landmark tiles in launch order (per class r, the tiles whose
+  // observing cameras all lie in ranges <= r, some in range r: small tiles, then one-landmark
+  // tiles, pipe_nt of each) and each class's lowest observing range, the counters of the bounded
+  // grids, stream pools per role (camera pass, camera solves, landmark pass) and events per range
   daba_pipeline pipe{};
-  int pipe_cam = 0, pipe_chunk = 0;
-  int pipe_nt[4] = {0, 0, 0, 0};
+  int pipe_R = 1;
+  std::vector<int> pipe_cam, pipe_chunk, pipe_nt, pipe_minr;
   void *d_tlist = nullptr, *d_ctr = nullptr;
-  cudaStream_t s_pipe[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t ev_pipe[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t s_pool[3][PIPE_POOL] = {};
+  std::vector<cudaEvent_t> ev_rng;   // 3 per range: camera pass, camera solves, landmark pass done
   int n_sm = 0;
   std::vector<int32_t> h_tile_lm, h_lmi_ptr, h_cam_chunk_ptr;
 };
@@ -689,59 +692,78 @@ cudaEvent_t ev(daba_ctx* ctx, size_t i) {
 }
 
 void pipe_streams_free(daba_ctx* ctx) {
-  for (int r = 0; r < 6; ++r) {
-    if (ctx->s_pipe[r]) {
-      cudaStreamSynchronize(ctx->s_pipe[r]);
-      cudaStreamDestroy(ctx->s_pipe[r]);
+  for (auto& pool : ctx->s_pool)
+    for (cudaStream_t& q : pool) {
+      if (q) {
+        cudaStreamSynchronize(q);
+        cudaStreamDestroy(q);
+      }
+      q = nullptr;
     }
-    if (ctx->ev_pipe[r]) cudaEventDestroy(ctx->ev_pipe[r]);
-    ctx->s_pipe[r] = nullptr;
-    ctx->ev_pipe[r] = nullptr;
-  }
+  for (cudaEvent_t e : ctx->ev_rng)
+    if (e) cudaEventDestroy(e);
+  ctx->ev_rng.clear();
 }
 
-// The cut of the two-range schedule for the current observations (daba_set_pipeline): range A
-// holds the cameras before the first camera whose observations start at or after split * nnz.
-// Tiles whose landmarks only range-A cameras observe come first in the tile order of d_tlist.
+// The ranges of the range schedule for the current observations (daba_set_pipeline): camera
+// bounds at the first cameras whose observations start at or after r nnz / R (a camera is never
+// split; empty ranges are dropped), the landmark tiles grouped by the last range observing them.
 daba_status pipe_cut(daba_ctx* ctx, cudaStream_t st) {
-  ctx->pipe_cam = ctx->pipe_chunk = 0;
-  for (int& v : ctx->pipe_nt) v = 0;
-  if (!(ctx->pipe.split > 0.0) || ctx->h_tile_lm.empty()) return DABA_OK;
+  ctx->pipe_R = 1;
+  const int R = ctx->pipe.ranges;
+  if (R <= 1 || ctx->h_tile_lm.empty()) return DABA_OK;
   const int M = ctx->M;
-  const double at = ctx->pipe.split * (double)ctx->nnz;
-  int cut = M;
-  for (int i = 0; i < M; ++i)
-    if ((double)ctx->h_cam_ptr[i] >= at) {
-      cut = i;
-      break;
-    }
-  if (cut <= 0 || cut >= M || ctx->h_cam_chunk_ptr[cut] <= 0 || ctx->h_cam_chunk_ptr[cut] >= ctx->n_chunks)
-    return DABA_OK;
-  // per tile: does a camera of range B observe one of its landmarks?
+  std::vector<int> cb{0};
+  int i = 0;
+  for (int r = 1; r < R; ++r) {
+    const double at = (double)r * (double)ctx->nnz / R;
+    while (i < M && (double)ctx->h_cam_ptr[i] < at) ++i;
+    if (i > cb.back() && i < M && ctx->h_cam_chunk_ptr[i] > ctx->h_cam_chunk_ptr[cb.back()]) cb.push_back(i);
+  }
+  if (ctx->h_cam_chunk_ptr[M] <= ctx->h_cam_chunk_ptr[cb.back()]) cb.pop_back();   // no chunks after the last bound
+  cb.push_back(M);
+  const int Rn = (int)cb.size() - 1;
+  if (Rn <= 1) return DABA_OK;
+  std::vector<int> rng_of(M);
+  for (int r = 0; r < Rn; ++r)
+    for (int c = cb[r]; c < cb[r + 1]; ++c) rng_of[c] = r;
+  // per tile the lowest and the highest range of its observing cameras
   const int n_tiles = ctx->n_tiles;
-  std::vector<uint8_t> tile_b(n_tiles, 0);
+  std::vector<int> tlo(n_tiles), thi(n_tiles);
   for (int t = 0; t < n_tiles; ++t) {
+    int lo = Rn, hi = 0;
     const int ob = ctx->h_lmi_ptr[ctx->h_tile_lm[t]], oe = ctx->h_lmi_ptr[ctx->h_tile_lm[t + 1]];
-    for (int o = ob; o < oe && !tile_b[t]; ++o)
-      if (ctx->h_cam_idx[ctx->h_li_order[o]] >= cut) tile_b[t] = 1;
+    for (int o = ob; o < oe; ++o) {
+      const int r = rng_of[ctx->h_cam_idx[ctx->h_li_order[o]]];
+      lo = std::min(lo, r);
+      hi = std::max(hi, r);
+    }
+    tlo[t] = oe > ob ? lo : 0;
+    thi[t] = oe > ob ? hi : 0;
   }
   std::vector<int32_t> tl;
   tl.reserve(n_tiles);
-  int nt[4] = {0, 0, 0, 0};
-  for (int b = 0; b < 2; ++b)
+  std::vector<int> nt(2 * Rn, 0), minr(Rn);
+  for (int r = 0; r < Rn; ++r) {
+    minr[r] = r;
     for (int c = 0; c < 2; ++c) {
       const int t0 = c == 0 ? 0 : ctx->tile_class_end[0], t1 = ctx->tile_class_end[c];
       for (int t = t0; t < t1; ++t)
-        if (tile_b[t] == b) {
+        if (thi[t] == r) {
           tl.push_back(t);
-          ++nt[2 * b + c];
+          ++nt[2 * r + c];
+          minr[r] = std::min(minr[r], tlo[t]);
         }
     }
+  }
   CK(cudaMemcpyAsync(ctx->d_tlist, tl.data(), tl.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
-  ctx->pipe_cam = cut;
-  ctx->pipe_chunk = ctx->h_cam_chunk_ptr[cut];
-  for (int q = 0; q < 4; ++q) ctx->pipe_nt[q] = nt[q];
+  ctx->pipe_cam = cb;
+  ctx->pipe_chunk.resize(Rn + 1);
+  for (int r = 0; r <= Rn; ++r) ctx->pipe_chunk[r] = ctx->h_cam_chunk_ptr[cb[r]];
+  ctx->pipe_nt = nt;
+  ctx->pipe_minr = minr;
+  ctx->pipe_R = Rn;
   return DABA_OK;
 }
 
@@ -764,83 +786,83 @@ void drop_graphs(daba_ctx* ctx) {
     if (e_ != cudaSuccess) return e_;        \
   } while (0)
 
-// The two-range schedule applies (daba_set_pipeline): a cut is set and the iteration is the
+// The range schedule applies (daba_set_pipeline): more than one range and the iteration is the
 // default one (per-block restart, no coarse blocks, no per-kernel timing).
 bool pipe_active(const daba_ctx* ctx) {
-  return ctx->pipe_cam > 0 && !ctx->timing && ctx->n_blocks == 0 && !ctx->persistent &&
+  return ctx->pipe_R > 1 && !ctx->timing && ctx->n_blocks == 0 && !ctx->persistent &&
          ctx->opt.restart_mode == DABA_RESTART_BLOCK;
 }
 
-// One iteration k on the two-range schedule. Streams by role (daba_set_pipeline's order):
-//   0: camera pass A ----+--> 1: camera solves A
-//                        +--> 2: landmark tiles observed by range A only
-//   3: camera pass B ----+--> 4: camera solves B
-//                        +--> 5: the other landmark tiles (after both camera passes)
-// then st waits for 1, 2, 4 and 5 and runs the reduction. Every kernel reads and writes what it
-// does in the one-range order; each camera solve and landmark tile only waits for the camera-pass
-// chunks it reads, so the results are the same bits.
-cudaError_t enqueue_iter_split(daba_ctx* ctx, cudaStream_t st, int64_t kk) {
-  cudaStream_t* S = ctx->s_pipe;
-  cudaEvent_t* E = ctx->ev_pipe;
+// One iteration k on the range schedule, with pools of PIPE_POOL streams per role:
+//   camera pass of range r (after the fork) --> camera solves of range r
+//   camera passes of ranges minr[r] .. r -----> landmark tiles of class r
+// then st waits for every camera solve and landmark launch and runs the reduction. Every kernel
+// reads and writes what it does in the one-range order, and each camera solve and landmark tile
+// waits for the camera-pass chunks it reads, so the results are the same bits.
+cudaError_t enqueue_iter_ranges(daba_ctx* ctx, cudaStream_t st, int64_t kk) {
+  const int R = ctx->pipe_R;
+  while ((int)ctx->ev_rng.size() < 3 * R) {
+    cudaEvent_t e = nullptr;
+    CE(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->ev_rng.push_back(e);
+  }
+  cudaEvent_t* E = ctx->ev_rng.data();
   unsigned* ctr = (unsigned*)ctx->d_ctr;
   CE(cudaEventRecord(ctx->ev_fork, st));
-  CE(cudaStreamWaitEvent(S[0], ctx->ev_fork, 0));
-  CE(cudaStreamWaitEvent(S[3], ctx->ev_fork, 0));
-  PassRange ra;
-  ra.c1 = ctx->pipe_chunk;
-  CE(launch_pass(ctx, S[0], 1, kk, ra));
-  CE(cudaEventRecord(E[0], S[0]));
-  PassRange rb;
-  rb.c0 = ctx->pipe_chunk;
-  if (ctx->pipe.cpass_b_warps > 0) {
-    rb.ctr = ctr;
-    rb.grid = ctx->pipe.cpass_b_warps * ctx->n_sm / CPASS_WARPS;
+  for (int r = 0; r < R; ++r) {   // camera passes
+    cudaStream_t q = ctx->s_pool[0][r % PIPE_POOL];
+    if (r < PIPE_POOL) CE(cudaStreamWaitEvent(q, ctx->ev_fork, 0));
+    PassRange pr;
+    pr.c0 = ctx->pipe_chunk[r];
+    pr.c1 = ctx->pipe_chunk[r + 1];
+    if (ctx->pipe.cpass_warps > 0) {
+      pr.ctr = ctr + 4 * r;
+      pr.grid = ctx->pipe.cpass_warps * ctx->n_sm / CPASS_WARPS;
+    }
+    CE(launch_pass(ctx, q, 1, kk, pr));
+    CE(cudaEventRecord(E[3 * r], q));
   }
-  CE(launch_pass(ctx, S[3], 1, kk, rb));
-  CE(cudaEventRecord(E[3], S[3]));
-  CE(cudaStreamWaitEvent(S[1], E[0], 0));
-  CE(launch_camsolve(ctx, S[1], kk, 0, ctx->pipe_cam));
-  CE(cudaEventRecord(E[1], S[1]));
-  CE(cudaStreamWaitEvent(S[2], E[0], 0));
-  TileRange ta;
-  ta.tlist = (const int*)ctx->d_tlist;
-  ta.q[0] = 0;
-  ta.n[0] = ctx->pipe_nt[0];
-  ta.q[1] = ctx->pipe_nt[0];
-  ta.n[1] = ctx->pipe_nt[1];
-  if (ctx->pipe.lpass_a_ctas > 0) {
-    ta.ctr = ctr + 2;
-    ta.grid = ctx->pipe.lpass_a_ctas * ctx->n_sm;
+  for (int r = 0; r < R; ++r) {   // camera solves
+    cudaStream_t q = ctx->s_pool[1][r % PIPE_POOL];
+    CE(cudaStreamWaitEvent(q, E[3 * r], 0));
+    CE(launch_camsolve(ctx, q, kk, ctx->pipe_cam[r], ctx->pipe_cam[r + 1]));
+    CE(cudaEventRecord(E[3 * r + 1], q));
   }
-  CE(launch_lpass(ctx, S[2], kk, ta));
-  CE(cudaEventRecord(E[2], S[2]));
-  CE(cudaStreamWaitEvent(S[4], E[3], 0));
-  CE(launch_camsolve(ctx, S[4], kk, ctx->pipe_cam, ctx->M));
-  CE(cudaEventRecord(E[4], S[4]));
-  CE(cudaStreamWaitEvent(S[5], E[3], 0));
-  CE(cudaStreamWaitEvent(S[5], E[0], 0));
-  TileRange tb;
-  tb.tlist = (const int*)ctx->d_tlist;
-  tb.q[0] = ctx->pipe_nt[0] + ctx->pipe_nt[1];
-  tb.n[0] = ctx->pipe_nt[2];
-  tb.q[1] = tb.q[0] + ctx->pipe_nt[2];
-  tb.n[1] = ctx->pipe_nt[3];
-  CE(launch_lpass(ctx, S[5], kk, tb));
-  CE(cudaEventRecord(E[5], S[5]));
-  for (int r : {1, 2, 4, 5}) CE(cudaStreamWaitEvent(st, E[r], 0));
+  int q0 = 0;
+  for (int r = 0; r < R; ++r) {   // landmark tiles by class
+    cudaStream_t q = ctx->s_pool[2][r % PIPE_POOL];
+    for (int c = ctx->pipe_minr[r]; c <= r; ++c) CE(cudaStreamWaitEvent(q, E[3 * c], 0));
+    TileRange tr;
+    tr.tlist = (const int*)ctx->d_tlist;
+    tr.q[0] = q0;
+    tr.n[0] = ctx->pipe_nt[2 * r];
+    tr.q[1] = q0 + tr.n[0];
+    tr.n[1] = ctx->pipe_nt[2 * r + 1];
+    q0 = tr.q[1] + tr.n[1];
+    if (ctx->pipe.lpass_ctas > 0) {
+      tr.ctr = ctr + 4 * r + 2;
+      tr.grid = ctx->pipe.lpass_ctas * ctx->n_sm;
+    }
+    CE(launch_lpass(ctx, q, kk, tr));
+    CE(cudaEventRecord(E[3 * r + 2], q));
+  }
+  for (int r = 0; r < R; ++r) {
+    CE(cudaStreamWaitEvent(st, E[3 * r + 1], 0));
+    CE(cudaStreamWaitEvent(st, E[3 * r + 2], 0));
+  }
   CE(launch_finalize(ctx, st));
   return cudaSuccess;
 }
 
 // Enqueues n iterations of Algorithm 1 starting at an iteration of parity k0 & 1 on stream st
 // (the camera pass, then the landmark pass and the camera solves on two priority streams,
-// joined before the reduction; or the two-range schedule); with timing, records the per-kernel
+// joined before the reduction; or the range schedule); with timing, records the per-kernel
 // events from index evi.
 cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, size_t evi) {
   for (int j = 0; j < n; ++j) {
     const int64_t kk = k0 + j;
     if (pipe_active(ctx)) {
-      CE(enqueue_iter_split(ctx, st, kk));
+      CE(enqueue_iter_ranges(ctx, st, kk));
       continue;
     }
     CE(cudaEventRecord(ctx->ev_fork, st));
@@ -875,7 +897,7 @@ cudaError_t enqueue_iters(daba_ctx* ctx, cudaStream_t st, int64_t k0, int n, siz
 }
 #undef CE
 
-// Graph instantiation: on the two-range schedule the kernel nodes keep the priorities of the
+// Graph instantiation: on the range schedule the kernel nodes keep the priorities of the
 // streams they were captured on (otherwise a graph ignores them).
 cudaError_t instantiate(const daba_ctx* ctx, cudaGraphExec_t* exec, cudaGraph_t g) {
   return cudaGraphInstantiateWithFlags(exec, g, pipe_active(ctx) ? cudaGraphInstantiateFlagUseNodePriority : 0);
@@ -1405,7 +1427,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   AL(bk, backup_layout(ctx).bytes);
   AL(d_gbar, 16);
   AL(d_tlist, (size_t)(ctx->max_tiles + 1) * 4);
-  AL(d_ctr, 64);
+  AL(d_ctr, 16 * PIPE_MAX_RANGES);
 #undef AL
   cudaMemset(ctx->lm_lo2[0], 0, (size_t)N * 16);
   cudaMemset(ctx->lm_lo2[1], 0, (size_t)N * 16);
@@ -1432,7 +1454,7 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_linv);   // identity numbering until observations are set
   k_iota<<<(N + 255) / 256, 256>>>(N, (int*)ctx->d_lperm);
   cudaMemset(ctx->fin_ticket, 0, 16);
-  cudaMemset(ctx->d_ctr, 0, 64);
+  cudaMemset(ctx->d_ctr, 0, 16 * PIPE_MAX_RANGES);
   cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, ctx->dev);
   cudaMemset(ctx->cam_rs, 0, (size_t)M);
   cudaMemset(ctx->lm_rs, 0, (size_t)N);
@@ -1441,13 +1463,15 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     daba_destroy(ctx);
     return DABA_ERR_CUDA;
   }
-  // default schedule: two camera ranges cut at half the observations for problems of at least
-  // PIPE_MIN_NNZ observations (measured on B300, 100 MIXED iterations: 26M observations 0.749 to
-  // 0.706 ms per iteration, 8M in 512 scenes 0.367 to 0.363, 1M 83.1 to 82.1 us)
+  // default schedule: two camera ranges for problems of at least PIPE_MIN_NNZ observations
+  // (measured on B300, 100 MIXED iterations: 26M observations 0.742 to 0.698 ms per iteration,
+  // against 0.702 with 4 ranges and 0.73 with 16; 8M in 512 scenes 0.367 to 0.363; 1M 83.1 to
+  // 82.1 us)
   daba_pipeline dp{};
-  dp.split = nnz >= PIPE_MIN_NNZ ? 0.5 : 0.0;
-  const int32_t ranks[6] = {0, 0, 1, 1, 0, 1};
-  for (int r = 0; r < 6; ++r) dp.prio[r] = ranks[r];
+  dp.ranges = nnz >= PIPE_MIN_NNZ ? 2 : 1;
+  dp.prio[0] = 1;
+  dp.prio[1] = 0;
+  dp.prio[2] = 1;
   if (pipe_apply(ctx, dp) != DABA_OK) {
     daba_destroy(ctx);
     return DABA_ERR_CUDA;
@@ -1744,7 +1768,7 @@ daba_status run_iterations(daba_ctx* ctx, int32_t iters, double* obj_trace, int3
   int done = 0;
   std::vector<double> gam(GSEG + 1);
   CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
-  CK(cudaMemsetAsync(ctx->d_ctr, 0, 64, st));   // bounded-grid counters (two-range schedule)
+  CK(cudaMemsetAsync(ctx->d_ctr, 0, 16 * PIPE_MAX_RANGES, st));   // bounded-grid counters (range schedule)
   while (done < iters) {
     const int seg = std::min(GSEG, iters - done);
     // gamma^(k) .. gamma^(k+seg) (Eq. nesterov_scalar); the last one is the look-ahead used
@@ -2441,10 +2465,10 @@ daba_status daba_get_partition_metrics(daba_ctx* ctx, double* F_blk, double* Fba
 daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p) {
   if (!ctx) return DABA_ERR_ARG;
   if (!p) return fail(ctx, DABA_ERR_ARG, "null schedule");
-  if (!(p->split >= 0.0 && p->split < 1.0)) return fail(ctx, DABA_ERR_ARG, "split must lie in [0, 1)");
-  if (p->cpass_b_warps < 0 || p->cpass_b_warps > 64 || p->lpass_a_ctas < 0 || p->lpass_a_ctas > 64)
+  if (p->ranges < 1 || p->ranges > PIPE_MAX_RANGES) return fail(ctx, DABA_ERR_ARG, "ranges must lie in [1, 64]");
+  if (p->cpass_warps < 0 || p->cpass_warps > 64 || p->lpass_ctas < 0 || p->lpass_ctas > 64)
     return fail(ctx, DABA_ERR_ARG, "grid bounds must lie in [0, 64]");
-  for (int r = 0; r < 6; ++r)
+  for (int r = 0; r < 3; ++r)
     if (p->prio[r] < 0 || p->prio[r] > 2) return fail(ctx, DABA_ERR_ARG, "priority ranks must lie in [0, 2]");
   return pipe_apply(ctx, *p);
 }
@@ -2452,23 +2476,23 @@ daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p) {
 }  // extern "C"
 
 namespace {
-// Sets the two-range schedule (arguments checked by the caller): one stream per kernel role at
-// its priority, the events between them, and the cut for the current observations.
+// Sets the range schedule (arguments checked by the caller): the stream pools at the roles'
+// priorities and the ranges for the current observations.
 daba_status pipe_apply(daba_ctx* ctx, const daba_pipeline& p) {
   pipe_streams_free(ctx);
   drop_graphs(ctx);
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  for (int r = 0; r < 6; ++r) {
-    const int prio = std::min(least, greatest + p.prio[r]);   // greater numbers are lower priorities
-    if (cudaStreamCreateWithPriority(&ctx->s_pipe[r], cudaStreamNonBlocking, prio) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_pipe[r], cudaEventDisableTiming) != cudaSuccess) {
-      const cudaError_t e = cudaGetLastError();
-      pipe_streams_free(ctx);
-      ctx->pipe = daba_pipeline{};
-      ctx->pipe_cam = 0;
-      return fail(ctx, DABA_ERR_CUDA, "creating the schedule's streams: %s", cudaGetErrorString(e));
-    }
+  for (int role = 0; role < 3; ++role) {
+    const int prio = std::min(least, greatest + p.prio[role]);   // greater numbers are lower priorities
+    for (cudaStream_t& q : ctx->s_pool[role])
+      if (cudaStreamCreateWithPriority(&q, cudaStreamNonBlocking, prio) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        pipe_streams_free(ctx);
+        ctx->pipe = daba_pipeline{};
+        ctx->pipe_R = 1;
+        return fail(ctx, DABA_ERR_CUDA, "creating the schedule's streams: %s", cudaGetErrorString(e));
+      }
   }
   ctx->pipe = p;
   return pipe_cut(ctx, nullptr);

@@ -1,10 +1,11 @@
-"""The two-range schedule (daba_set_pipeline) against the one-range iteration through the C ABI.
+"""The range schedule (daba_set_pipeline) against the one-range iteration through the C ABI.
 
-The cut only changes which kernels run beside one another: every camera solve and landmark tile
-still reads the camera-pass chunks it read before, in the same order. So the objective trace,
-restart counts, per-block metrics and iterate must be the same bits for every cut, grid bound and
-priority order, on single scenes (FP64 and MIXED, every loss), on a batch of scenes, across the
-8-iteration graphs of long runs, and on a run that fails and restores its entry state."""
+Camera ranges only change which kernels run beside one another: every camera solve and landmark
+tile still reads the camera-pass chunks it read before, in the same order. So the objective trace,
+restart counts, per-block metrics and iterate must be the same bits for every number of ranges,
+grid bound and priority order, on single scenes (FP64 and MIXED, every loss), on a batch of
+scenes, across the 8-iteration graphs of long runs, and on a run that fails and restores its entry
+state."""
 import numpy as np
 import pytest
 
@@ -13,13 +14,13 @@ from tests.conftest import cached_scene
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ONE = (0.0, 0, 0, (0, 0, 1, 1, 0, 1))
+ONE = (1, 0, 0, (1, 0, 1))
 CUTS = [
-    (0.5, 0, 0, (0, 0, 1, 1, 0, 1)),           # the default for large problems
-    (0.3, 0, 0, (0, 2, 0, 1, 2, 1)),
-    (0.8, 4, 2, (0, 1, 1, 2, 1, 2)),           # both bounded grids
-    (1e-9, 0, 3, (2, 2, 2, 0, 0, 0)),          # range A of one camera
-    (0.999999, 8, 0, (1, 0, 0, 1, 0, 0)),      # a cut past the last camera: one range
+    (2, 0, 0, (1, 0, 1)),          # the default for large problems
+    (3, 0, 0, (1, 0, 0)),
+    (4, 4, 2, (2, 1, 0)),          # both bounded grids
+    (64, 0, 3, (0, 2, 2)),         # more ranges than small scenes have cameras to cut at
+    (9, 8, 0, (0, 0, 0)),
 ]
 
 
@@ -134,12 +135,12 @@ def test_pipeline_argument_checks():
     from paper_2305_07026_b300 import _lib as L
     sc = cached_scene("circle")
     d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px)
-    for bad in [(1.0, 0, 0, ONE[3]), (-0.1, 0, 0, ONE[3]), (0.5, 65, 0, ONE[3]), (0.5, 0, -1, ONE[3]),
-                (0.5, 0, 0, (0, 0, 3, 0, 0, 0)), (0.5, 0, 0, (0, 0, 0, 0, 0, -1))]:
+    for bad in [(0, 0, 0, ONE[3]), (65, 0, 0, ONE[3]), (2, 65, 0, ONE[3]), (2, 0, -1, ONE[3]),
+                (2, 0, 0, (0, 0, 3)), (2, 0, 0, (0, -1, 0))]:
         with pytest.raises(L.DabaError) as e:
             d.set_pipeline(*bad)
         assert e.value.status == L.DABA_ERR_ARG
-    d.set_pipeline(0.5)   # before the observations: the cut is made when they come
+    d.set_pipeline(2)   # before the observations: the ranges are cut when they come
     d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
     d.set_state(sc.cams, sc.lms)
     d.run(3)

@@ -48,24 +48,24 @@ def test_batch_merge_split_round_trip():
 
 def test_autotune_coordinate_descent(monkeypatch):
     """The tuner walks chunk, then observations per tile, then landmarks per tile, then the
-    two-range cut, keeping the best of each and timing every schedule once."""
+    number of camera ranges, keeping the best of each and timing every schedule once."""
     from paper_2305_07026_b300 import autotune
     cost = {}
 
     def fake(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2):
-        key = (sched["chunk_obs"], sched["tile_obs"], sched["tile_lms"], sched["split"])
+        key = (sched["chunk_obs"], sched["tile_obs"], sched["tile_lms"], sched["ranges"])
         cost[key] = cost.get(key, 0) + 1
-        return abs(key[0] - 4096) / 1e3 + abs(key[1] - 256) / 1e2 + abs(key[2] - 64) / 10.0 + abs(key[3] - 0.3)
+        return abs(key[0] - 4096) / 1e3 + abs(key[1] - 256) / 1e2 + abs(key[2] - 64) / 10.0 + abs(key[3] - 4)
     monkeypatch.setattr(autotune, "time_schedule", fake)
     z = np.zeros((1, 9))
     best, tried = autotune.tune(z, np.zeros((1, 3)), np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros((1, 2)))
-    assert best == {"chunk_obs": 4096, "tile_obs": 256, "tile_lms": 64, "split": 0.3}
+    assert best == {"chunk_obs": 4096, "tile_obs": 256, "tile_lms": 64, "ranges": 4}
     assert all(v == 1 for v in cost.values())
     assert len(tried) == len(cost)
 
 
 def test_autotune_context_takes_the_cut(monkeypatch):
-    """A schedule's cut goes to daba_set_pipeline, its sizes to the context options."""
+    """A schedule's camera ranges go to daba_set_pipeline, its sizes to the context options."""
     from paper_2305_07026_b300 import autotune
     calls = []
 
@@ -73,13 +73,13 @@ def test_autotune_context_takes_the_cut(monkeypatch):
         def __init__(self, M, N, nnz, **kw):
             calls.append(("create", kw))
 
-        def set_pipeline(self, split):
-            calls.append(("pipeline", split))
+        def set_pipeline(self, ranges):
+            calls.append(("pipeline", ranges))
 
     class FakeL:
         Daba = FakeDaba
-    autotune.make_context(FakeL, 1, 1, 1, {"prec": "mixed"}, {"chunk_obs": 1024, "split": 0.3})
-    assert calls == [("create", {"prec": "mixed", "chunk_obs": 1024}), ("pipeline", 0.3)]
+    autotune.make_context(FakeL, 1, 1, 1, {"prec": "mixed"}, {"chunk_obs": 1024, "ranges": 4})
+    assert calls == [("create", {"prec": "mixed", "chunk_obs": 1024}), ("pipeline", 4)]
     calls.clear()
     autotune.make_context(FakeL, 1, 1, 1, {}, {})
     assert calls == [("create", {})]
