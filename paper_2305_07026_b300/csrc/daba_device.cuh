@@ -91,32 +91,34 @@ struct ObsEval {
 };
 
 // Evaluates one observation at x^k, xbar^k and x^(k-1).
-//   pk: camera pack; (l0,l1,l2) + (o0,o1,o2): landmark position l^k as high and low parts
-//   (the low part is zero in FP64); dl = l^k - l^(k-1); u: pixel (internal units);
+//   pk: camera pack; (l0,l1,l2): landmark position l^k (in MIXED its high part: the camera pass
+//   reads no low part); dl = l^k - l^(k-1); u: pixel (internal units);
 //   gamma: extrapolation ratio of Eq. nesterov_scalar.
-// q^k = l^k - t^k is formed from high and low parts so that it keeps FP32 relative accuracy.
+// q^k = l^k - t^k is formed with the camera centre's high and low parts, so that it keeps FP32
+// relative accuracy far from the origin.
 // xbar: Rbar, dbar = d + gamma dd, qbar = q + gamma (dl - dt) (Eq. nesterov_x).
-// x^(k-1): R', d' = d - dd, q' = q - (dl - dt).
+// x^(k-1): R' = R^k - dR, d' = d - dd, q' = q - (dl - dt); R' p' is formed as R^k p^k - G with
+// G = dR p^k + R' e3 (phi . dd) (p' = p^k - e3 (phi . dd)), which the gap below needs anyway.
 // The surrogate gap of Eq. DEalpha is written in displacement form: with X = R^k p^k +
 // lambda' t^k, Y = lambda' l^k and g' of Eq. g at x^(k-1),
 //   |X - g'|^2 + |Y - g'|^2 = |X - Y|^2 / 2 + 2 |(X + Y)/2 - g'|^2,
 //   |X - Y|^2 = r^k + |q^k|^2 (lambda' - lambda^k)^2,
-//   2 ((X + Y)/2 - g') = dR p^k + R' e3 (phi . dd) + lambda' (dt + dl) =: D,
+//   2 ((X + Y)/2 - g') = dR p^k + R' e3 (phi . dd) + lambda' (dt + dl) = G + lambda' (dt + dl) =: D,
 // so gap = [rho(r^k) - rho(r') - w'(r^k - r')]/2 - w' |q^k|^2 (lambda' - lambda^k)^2 / 2
 //          - w' |D|^2 / 2, every term of which is formed without cancellation of O(1) values.
 template <int LOSS, class Real>
-__device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l0, Real l1, Real l2, Real o0,
-                                         Real o1, Real o2, Real dl0, Real dl1, Real dl2, Real u0, Real u1,
-                                         Real gamma, const LossC<Real>& L, ObsEval<Real>& o) {
+__device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l0, Real l1, Real l2, Real dl0,
+                                         Real dl1, Real dl2, Real u0, Real u1, Real gamma, const LossC<Real>& L,
+                                         ObsEval<Real>& o) {
   const V4<Real> a0 = pk[P4_RK + 0], a1 = pk[P4_RK + 1], a2 = pk[P4_RK + 2];
   const V4<Real> g0 = pk[P4_DR + 0], g1 = pk[P4_DR + 1], g2 = pk[P4_DR + 2];
   const V4<Real> b0 = pk[P4_RB + 0], b1 = pk[P4_RB + 1], b2 = pk[P4_RB + 2];
   const V4<Real> dd = pk[P4_DD], d = pk[P4_D];
   const Real s = u0 * u0 + u1 * u1;
   const Real s2 = s * s;
-  const Real q0 = (l0 - a0.w) + (o0 - g0.w);
-  const Real q1 = (l1 - a1.w) + (o1 - g1.w);
-  const Real q2 = (l2 - a2.w) + (o2 - g2.w);
+  const Real q0 = (l0 - a0.w) - g0.w;
+  const Real q1 = (l1 - a1.w) - g1.w;
+  const Real q2 = (l2 - a2.w) - g2.w;
   // ---- x^k
   const Real pz = d.x + d.y * s + d.z * s2;
   const Real Rp0 = a0.x * u0 + a0.y * u1 + a0.z * pz;
@@ -150,24 +152,22 @@ __device__ __forceinline__ void eval_obs(const V4<Real>* __restrict__ pk, Real l
   }
   // ---- x^(k-1) and the surrogate gap
   {
-    V4<Real> c0, c1, c2;   // rows of R' = R^k - dR
-    c0.x = a0.x - g0.x, c0.y = a0.y - g0.y, c0.z = a0.z - g0.z;
-    c1.x = a1.x - g1.x, c1.y = a1.y - g1.y, c1.z = a1.z - g1.z;
-    c2.x = a2.x - g2.x, c2.y = a2.y - g2.y, c2.z = a2.z - g2.z;
-    const Real pzp = pz - phidd;
+    // R' e3 (the third column of R' = R^k - dR) and G = dR p^k + R' e3 (phi . dd)
+    const Real c0z = a0.z - g0.z, c1z = a1.z - g1.z, c2z = a2.z - g2.z;
+    const Real G0 = g0.x * u0 + g0.y * u1 + g0.z * pz + c0z * phidd;
+    const Real G1 = g1.x * u0 + g1.y * u1 + g1.z * pz + c1z * phidd;
+    const Real G2 = g2.x * u0 + g2.y * u1 + g2.z * pz + c2z * phidd;
     const Real qp0 = q0 - e0, qp1 = q1 - e1, qp2 = q2 - e2;
-    const Real Rpp0 = c0.x * u0 + c0.y * u1 + c0.z * pzp;
-    const Real Rpp1 = c1.x * u0 + c1.y * u1 + c1.z * pzp;
-    const Real Rpp2 = c2.x * u0 + c2.y * u1 + c2.z * pzp;
+    const Real Rpp0 = Rp0 - G0, Rpp1 = Rp1 - G1, Rpp2 = Rp2 - G2;
     const Real qqp = qp0 * qp0 + qp1 * qp1 + qp2 * qp2;
     const Real lamp = fdiv(qp0 * Rpp0 + qp1 * Rpp1 + qp2 * Rpp2, qqp);
     const Real Rep0 = Rpp0 - lamp * qp0, Rep1 = Rpp1 - lamp * qp1, Rep2 = Rpp2 - lamp * qp2;
     const Real rp = Rep0 * Rep0 + Rep1 * Rep1 + Rep2 * Rep2;
     Real rhop, wp;
     rho_w<LOSS, Real>(L, rp, rhop, wp);
-    const Real D0 = g0.x * u0 + g0.y * u1 + g0.z * pz + c0.z * phidd + lamp * (b0.w + dl0);
-    const Real D1 = g1.x * u0 + g1.y * u1 + g1.z * pz + c1.z * phidd + lamp * (b1.w + dl1);
-    const Real D2 = g2.x * u0 + g2.y * u1 + g2.z * pz + c2.z * phidd + lamp * (b2.w + dl2);
+    const Real D0 = G0 + lamp * (b0.w + dl0);
+    const Real D1 = G1 + lamp * (b1.w + dl1);
+    const Real D2 = G2 + lamp * (b2.w + dl2);
     const Real dlam = lamp - o.lam;
     o.gap = Real(0.5) * (o.rho - rhop - wp * (o.r - rp)) - Real(0.5) * wp * qq * dlam * dlam -
             Real(0.5) * wp * (D0 * D0 + D1 * D1 + D2 * D2);

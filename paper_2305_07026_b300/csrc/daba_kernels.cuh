@@ -398,7 +398,7 @@ __device__ __forceinline__ void cpass_chunk(int warp, int lane, CpassWarpSmem<Re
       const V4<Real> r0 = d.rec[0], r1 = d.rec[1];
       const Real2 uu = sm.su[t % CPASS_STAGES][lane];
       ObsEval<Real> ev;
-      eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, Real(0), Real(0), Real(0), r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
+      eval_obs<LOSS, Real>(pk, r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, uu.x, uu.y, gamma, L,
                            ev);
       if constexpr (BLK) {   // coarse blocks: an intra pair keeps its exact F_ij, no statistics or record
         if (c_intra[o]) {

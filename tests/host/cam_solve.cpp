@@ -32,7 +32,7 @@ void stats(double c, const CamT<double>& z, int m, double* st) {
     for (int a = 0; a < 3; ++a) split_real(v[a], l[a], lo[a]);
     const Real u0 = to_real<Real>(v[3]), u1 = to_real<Real>(v[4]);
     ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, l[0], l[1], l[2], Real(0), Real(0), Real(0), Real(0), Real(0), Real(0), u0, u1, Real(0), L,
+    eval_obs<LOSS, Real>(pk, l[0], l[1], l[2], Real(0), Real(0), Real(0), u0, u1, Real(0), L,
                          ev);
     accumulate_cam<Real>(acc, ev, u0, u1);
   }

@@ -184,7 +184,7 @@ double obs_L(const double* R, const double* t, const double* d, const double* l,
   pk[P4_D] = {d[0], d[1], d[2], 0.0};
   pk[P4_DD] = {0.0, 0.0, 0.0, 0.0};
   ObsEval<double> ev;
-  eval_obs<LOSS, double>(pk, l[0], l[1], l[2], 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, u0, u1, 0.0, L, ev);
+  eval_obs<LOSS, double>(pk, l[0], l[1], l[2], 0.0, 0.0, 0.0, u0, u1, 0.0, L, ev);
   double acc[80] = {0};
   accumulate_cam<double>(acc, ev, u0, u1);
   double f = 0;

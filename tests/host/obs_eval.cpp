@@ -35,7 +35,7 @@ void run(double c, int n) {
       dl[a] = to_real<Real>(lk[a] - lp[a]);
     }
     ObsEval<Real> ev;
-    eval_obs<LOSS, Real>(pk, l[0], l[1], l[2], Real(0), Real(0), Real(0), dl[0], dl[1], dl[2], to_real<Real>(u[0]),
+    eval_obs<LOSS, Real>(pk, l[0], l[1], l[2], dl[0], dl[1], dl[2], to_real<Real>(u[0]),
                          to_real<Real>(u[1]), Real(v[47]), L, ev);
     const double out[13] = {double(ev.lam), double(ev.Re0), double(ev.Re1), double(ev.Re2), double(ev.r),
                             double(ev.rho), double(ev.w),   double(ev.lamb), double(ev.Reb0), double(ev.Reb1),
