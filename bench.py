@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--n-scenes", type=int, default=512, help="scenes of the batch workload")
     ap.add_argument("--no-autotune", action="store_true", help="batch workload: the default schedule, not tuned")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch leg of the default line")
+    ap.add_argument("--ranges", type=int, default=0,
+                    help="camera ranges of the range schedule (daba_set_pipeline); 0: the library's default")
     return ap.parse_args()
 
 
@@ -409,6 +411,8 @@ def run_ours(args, rank, world, local):
 
     def make(prec, **kw):
         d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec=prec, **kw)
+        if args.ranges:
+            d.set_pipeline(args.ranges)
         d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv, stream=sp)
         d.set_state(sc.cams, sc.lms, stream=sp)
         return d
@@ -769,6 +773,8 @@ def run_batch(args, rank, world, local):
     else:
         sched, tried = autotune.tune(b.cams, b.lms, b.cam_idx, b.lm_idx, b.uv,
                                      dict(loss="huber", loss_scale_px=1.0, prec="mixed", pixel_scale=650.0))
+    if args.ranges:
+        sched = dict(sched, ranges=args.ranges)
     r = batch_leg(L, scs, b, K, W, stream, sched, clocks=Clocks(), world=world, local=local)
     n = len(scs)
     if rank != 0:
