@@ -166,20 +166,20 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
 
 /* Reverse-mode derivative of K >= 1 iterations of Algorithm 1 (Eqs. nesterov_scalar,
  * nesterov_x, nesterov_R, the majorizer of Proposition 1, the closed-form landmark update and
- * S-CAM for the cameras) from the state last set by daba_set_state (x^0 = x^(-1)).
+ * S-CAM, or with cam_solver = DABA_CAM_LM the LM step, for the cameras) from the state last set
+ * by daba_set_state (x^0 = x^(-1)).
  * With y = <seed_cams, cams_K> + <seed_lms, lms_K> for the boundary state (cams_K, lms_K)
  * after K iterations (the layout of daba_get_state), writes
  *   g_cams: M x 9, dy / d cams_0 (the layout of daba_set_state);
  *   g_lms:  N x 3, dy / d lms_0;
  *   g_uv:   nnz x 2, dy / d u_ij (input observation order).
- * The per-block restart decisions are piecewise constant and are held at those of the
- * forward run. Runs the K iterations itself (leaving the state at x^K, as daba_run(K)
+ * The per-block restart decisions, and with the LM solver the damping trial each camera's step
+ * took (or that it took none), are piecewise constant and are held at those of the forward run. Runs the K iterations itself (leaving the state at x^K, as daba_run(K)
  * would), keeps the state every 10 iterations and, per segment of 10 iterations from the last,
  * runs the segment again keeping each iteration's state, camera statistics, landmark sums and
  * decisions; it costs about two forward runs plus the adjoint kernels and holds about K/10 + 11
  * copies of the state and 10 of the per-iteration data (about 64 B per landmark). Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
- * (DABA_ERR_ARG for MIXED, for momentum_reset, whose Nesterov scalars live on the device, and for
- * DABA_CAM_LM, whose step acceptance has no adjoint here);
+ * (DABA_ERR_ARG for MIXED and for momentum_reset, whose Nesterov scalars live on the device);
  * DABA_ERR_STATE if iterations have run since the state was set. */
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream);

@@ -3,8 +3,9 @@
 TEST INFRASTRUCTURE ONLY, like daba_oracle.py. The update of one iteration, written out again
 with plain PyTorch CPU float64 operations so that autograd differentiates it. It follows the
 numpy oracle step by step: Eqs. nesterov_scalar and nesterov_x for the extrapolation, the
-majorizer of Proposition 1 (w, lambda, g), the closed-form landmark solve, S-CAM for the
-cameras and ProjRot3D (Eq. proj_rot3d, as the polar factor). The adaptive-restart decisions are
+majorizer of Proposition 1 (w, lambda, g), the closed-form landmark solve, S-CAM (or, with
+cam_solver = "lm", one successful LM step) for the cameras and ProjRot3D (Eq. proj_rot3d, as the
+polar factor). The adaptive-restart decisions are
 taken from a run of the numpy oracle and held fixed: they are piecewise constant in the
 inputs, so they carry no gradient. The internal unit s (pixels) is held fixed as well: the
 iteration depends on it only through xi, which is given in internal units.
@@ -103,6 +104,49 @@ def _solve_cameras(xi, w, lam, g, Rz, tz, dz, ci, u, M, n_alt):
     return R, t, d
 
 
+def _skew(p):
+    z = torch.zeros_like(p[:, 0])
+    return torch.stack([torch.stack([z, -p[:, 2], p[:, 1]], 1), torch.stack([p[:, 2], z, -p[:, 0]], 1),
+                        torch.stack([-p[:, 1], p[:, 0], z], 1)], 1)
+
+
+def _solve_cameras_lm(xi, w, lam, g, Rz, tz, dz, ci, u, M):
+    """One successful LM step per camera, as daba_oracle.solve_cameras_lm: the Gauss-Newton model
+    (A, b) from the per-observation Jacobians at c_z, theta = -(A + mu diag A)^-1 b for mu = 1e-3,
+    1e-2, ..., the first trial that lowers the block surrogate taken (else the camera stays at c_z).
+    Which trial is taken is decided without gradient (piecewise constant); the taken theta is
+    differentiated through A, b and Exp."""
+    s = u[:, 0] ** 2 + u[:, 1] ** 2
+    phi_u = torch.stack([torch.ones_like(s), s, s * s], 1)
+    p0 = _ray(u, dz[ci])
+    Rzi = Rz[ci]
+    r0 = torch.einsum("nab,nb->na", Rzi, p0) + lam[:, None] * tz[ci] - g
+    eye = torch.eye(3, dtype=F64).expand(u.shape[0], 3, 3)
+    J = torch.cat([-torch.einsum("nab,nbc->nac", Rzi, _skew(p0)), lam[:, None, None] * eye,
+                   Rzi[:, :, 2][:, :, None] * phi_u[:, None, :]], 2)
+    A = 2.0 * _segsum(ci, w[:, None, None] * torch.einsum("nai,naj->nij", J, J), M)
+    A = A + xi * torch.diag(torch.tensor([2.0, 2.0, 2.0, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0], dtype=F64))[None]
+    b = 2.0 * _segsum(ci, w[:, None] * torch.einsum("nai,na->ni", J, r0), M)
+    theta = torch.zeros((M, 9), dtype=F64)
+    done = torch.zeros(M, dtype=torch.bool)
+    mu = O.LM_MU0
+    for _ in range(O.LM_TRIES):
+        Ad = A + mu * torch.diag_embed(torch.diagonal(A, dim1=1, dim2=2))
+        th = torch.linalg.solve(Ad, -b[:, :, None])[:, :, 0]
+        with torch.no_grad():   # the surrogate decrease decides the trial (as the numpy oracle)
+            Rc = Rz @ _exp(th[:, 0:3])
+            tc, dc = tz + th[:, 3:6], dz + th[:, 6:9]
+            dr = (torch.einsum("nab,nb->na", Rc[ci], _ray(u, dc[ci])) - torch.einsum("nab,nb->na", Rzi, p0)
+                  + lam[:, None] * (tc - tz)[ci])
+            dE = _segsum(ci, w * (dr * (dr + 2.0 * r0)).sum(1), M) + 0.5 * xi * (
+                ((Rc - Rz) ** 2).sum((1, 2)) + ((tc - tz) ** 2).sum(1) + ((dc - dz) ** 2).sum(1))
+            take = (~done) & (dE < 0.0)
+        theta = torch.where(take[:, None], th, theta)
+        done = done | take
+        mu *= 10.0
+    return Rz @ _exp(theta[:, 0:3]), tz + theta[:, 3:6], dz + theta[:, 6:9]
+
+
 def _exp(w):
     th = torch.sqrt((w * w).sum(-1) + 1e-300)[..., None, None]
     K = torch.zeros(w.shape[:-1] + (3, 3), dtype=F64)
@@ -139,16 +183,22 @@ def unrolled_state(cams, lms, uv, cam_idx, lm_idx, opts: O.Options, K: int, rest
     l = lms
     Rp, tp, dp, lp = R, t, d, l
     s = 1.0
+
+    def cameras(w, lam, g, Rz, tz, dz):
+        if opts.cam_solver == "lm":
+            return _solve_cameras_lm(xi, w, lam, g, Rz, tz, dz, ci, u, M)
+        return _solve_cameras(xi, w, lam, g, Rz, tz, dz, ci, u, M, opts.cam_alternations)
+
     for k in range(K):
         s, gamma = O.nesterov(s)
         w, lam, g = _majorizer(opts.loss, c, R[ci], t[ci], d[ci], l[li], u)
-        Rm, tm, dm = _solve_cameras(xi, w, lam, g, R, t, d, ci, u, M, opts.cam_alternations)
+        Rm, tm, dm = cameras(w, lam, g, R, t, d)
         lmm = _solve_landmarks(xi, w, lam, g, l, li, N)
         if opts.accelerated:
             Rb = _proj_rot3d(R + gamma * (R - Rp))
             tb, db, lb = t + gamma * (t - tp), d + gamma * (d - dp), l + gamma * (l - lp)
             wb, lamb, gb = _majorizer(opts.loss, c, Rb[ci], tb[ci], db[ci], lb[li], u)
-            Ra, ta, da = _solve_cameras(xi, wb, lamb, gb, Rb, tb, db, ci, u, M, opts.cam_alternations)
+            Ra, ta, da = cameras(wb, lamb, gb, Rb, tb, db)
             la = _solve_landmarks(xi, wb, lamb, gb, lb, li, N)
             rc = torch.as_tensor(np.asarray(restart_cam[k], bool))
             rl = torch.as_tensor(np.asarray(restart_lm[k], bool))

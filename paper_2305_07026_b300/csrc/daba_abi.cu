@@ -1235,6 +1235,7 @@ cudaError_t adjoint_iter(daba_ctx* ctx, cudaStream_t st, int64_t k, double gamma
   if (M > 0)
     k_adj_cams<<<(M + 63) / 64, 64, 0, st>>>(M, (const int*)ctx->cam_chunk_ptr, part, sx, sdx,
                                              gamma, rs_cam, acc, xi, ctx->opt.cam_alternations,
+                                             ctx->opt.cam_solver == DABA_CAM_LM ? 1 : 0,
                                              (const double*)ctx->adj_c[a1], (double*)ctx->st_bar,
                                              (double*)ctx->zb_c[0], (double*)ctx->zb_c[1]);
   if (N > 0)
@@ -2001,8 +2002,6 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   if (ctx->n_blocks) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient covers one block per camera and landmark");
   if (ctx->opt.momentum_reset)
     return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
-  if (ctx->opt.cam_solver != DABA_CAM_SCAM)
-    return fail(ctx, DABA_ERR_ARG, "the unrolled gradient supports the S-CAM camera solver only");
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   if (ctx->k != 0) return fail(ctx, DABA_ERR_STATE, "iterations have run since the state was set");
   cudaStream_t st = (cudaStream_t)stream;

@@ -367,6 +367,218 @@ __device__ inline void scam_adjoint(const double* st, const CamT<double>& z, dou
   }
 }
 
+// Reverse sweep of the LM camera step (cam_lm): from the adjoint of its result (cb: R ambient,
+// t, d) to the adjoint of the statistics (Hb full 6x6, Bb 6x3) and of the conditioning point (zb).
+// The forward step is replayed with the same arithmetic to find the damping trial it took; the
+// choice is piecewise constant and carries no derivative. Taken step: c = (z.R Exp(phi),
+// z.t + tau, z.d + delta) with theta = -(A + mu diag A)^-1 g, so with v = (A_mu)^-1 theta_bar,
+// g_bar = -v and A_mu_bar = -v theta^T; no step taken: c = z.
+__device__ inline void lm_model_adjoint(const double* st, const CamT<double>& z, const double* Ab, const double* gb,
+                                        double Hb[6][6], double Bb[6][3], CamT<double>& zb);
+
+__device__ inline void lm_adjoint(const double* st, const CamT<double>& z, double xi, const CamT<double>& cb,
+                                  double Hb[6][6], double Bb[6][3], CamT<double>& zb) {
+  for (int a = 0; a < 6; ++a)
+    for (int b = 0; b < 6; ++b) Hb[a][b] = 0.0;
+  for (int a = 0; a < 6; ++a)
+    for (int c = 0; c < 3; ++c) Bb[a][c] = 0.0;
+  for (int a = 0; a < 9; ++a) zb.R[a] = 0.0;
+  for (int k = 0; k < 3; ++k) zb.t[k] = zb.d[k] = 0.0;
+  double A[45], g[9], L[45], th[9], mu = LM_MU0;
+  cam_lm_model(st, z, xi, A, g);
+  bool taken = false;
+  for (int tr = 0; tr < LM_TRIES && !taken; ++tr, mu *= 10.0) {   // replay of cam_lm
+    bool ok = true;
+    for (int i = 0; i < 9; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double v = A[lt9(i, j)] * (i == j ? 1.0 + mu : 1.0);
+        for (int k = 0; k < j; ++k) v -= L[lt9(i, k)] * L[lt9(j, k)];
+        if (i == j) {
+          if (!(v > 0.0)) ok = false;
+          L[lt9(i, i)] = sqrt(ok ? v : 1.0);
+        } else {
+          L[lt9(i, j)] = v / L[lt9(j, j)];
+        }
+      }
+    if (!ok) continue;
+    double y[9];
+    for (int i = 0; i < 9; ++i) {
+      double v = -g[i];
+      for (int k = 0; k < i; ++k) v -= L[lt9(i, k)] * y[k];
+      y[i] = v / L[lt9(i, i)];
+    }
+    for (int i = 8; i >= 0; --i) {
+      double v = y[i];
+      for (int k = i + 1; k < 9; ++k) v -= L[lt9(k, i)] * th[k];
+      th[i] = v / L[lt9(i, i)];
+    }
+    CamT<double> cand;
+    double E[9];
+    rodrigues(th, E);
+    for (int r = 0; r < 3; ++r)
+      for (int cc = 0; cc < 3; ++cc)
+        cand.R[r * 3 + cc] = z.R[r * 3 + 0] * E[0 * 3 + cc] + z.R[r * 3 + 1] * E[1 * 3 + cc] + z.R[r * 3 + 2] * E[2 * 3 + cc];
+    for (int k = 0; k < 3; ++k) {
+      cand.t[k] = z.t[k] + th[3 + k];
+      cand.d[k] = z.d[k] + th[6 + k];
+    }
+    if (cam_phi(st, z, cand, xi) < 0.0) {
+      taken = true;
+      break;
+    }
+  }
+  if (!taken) {   // the camera stayed at c_z
+    for (int a = 0; a < 9; ++a) zb.R[a] = cb.R[a];
+    for (int k = 0; k < 3; ++k) zb.t[k] = cb.t[k], zb.d[k] = cb.d[k];
+    return;
+  }
+  // R = z.R E(phi): z.R_bar = R_bar E^T; E_bar = z.R^T R_bar, then phi_bar = J_r(phi)^T vee(E^T E_bar)
+  double E[9];
+  rodrigues(th, E);
+  for (int r = 0; r < 3; ++r)
+    for (int cc = 0; cc < 3; ++cc)
+      zb.R[r * 3 + cc] = cb.R[r * 3 + 0] * E[cc * 3 + 0] + cb.R[r * 3 + 1] * E[cc * 3 + 1] + cb.R[r * 3 + 2] * E[cc * 3 + 2];
+  double Eb[9], Mx[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      Eb[i * 3 + j] = z.R[0 * 3 + i] * cb.R[0 * 3 + j] + z.R[1 * 3 + i] * cb.R[1 * 3 + j] + z.R[2 * 3 + i] * cb.R[2 * 3 + j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      Mx[i * 3 + j] = E[0 * 3 + i] * Eb[0 * 3 + j] + E[1 * 3 + i] * Eb[1 * 3 + j] + E[2 * 3 + i] * Eb[2 * 3 + j];
+  const double v2[3] = {Mx[7] - Mx[5], Mx[2] - Mx[6], Mx[3] - Mx[1]};
+  // J_r(phi)^T = I + b [phi]x + c [phi]x^2, b = (1 - cos t)/t^2, c = (t - sin t)/t^3
+  const double t2 = th[0] * th[0] + th[1] * th[1] + th[2] * th[2], tn = sqrt(t2);
+  double bj, cj;
+  if (tn < 1e-4) {
+    bj = 0.5 - t2 / 24.0;
+    cj = 1.0 / 6.0 - t2 / 120.0;
+  } else {
+    bj = (1.0 - cos(tn)) / t2;
+    cj = (tn - sin(tn)) / (t2 * tn);
+  }
+  const double px[3] = {th[1] * v2[2] - th[2] * v2[1], th[2] * v2[0] - th[0] * v2[2], th[0] * v2[1] - th[1] * v2[0]};
+  const double ppx[3] = {th[1] * px[2] - th[2] * px[1], th[2] * px[0] - th[0] * px[2], th[0] * px[1] - th[1] * px[0]};
+  double thb[9];
+  for (int k = 0; k < 3; ++k) thb[k] = v2[k] + bj * px[k] + cj * ppx[k];
+  for (int k = 0; k < 3; ++k) {
+    thb[3 + k] = cb.t[k];
+    thb[6 + k] = cb.d[k];
+    zb.t[k] = cb.t[k];
+    zb.d[k] = cb.d[k];
+  }
+  // theta = -(A_mu)^-1 g: v = (A_mu)^-1 theta_bar by the Cholesky factor of the taken trial
+  double y[9], v[9];
+  for (int i = 0; i < 9; ++i) {
+    double s = thb[i];
+    for (int k = 0; k < i; ++k) s -= L[lt9(i, k)] * y[k];
+    y[i] = s / L[lt9(i, i)];
+  }
+  for (int i = 8; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < 9; ++k) s -= L[lt9(k, i)] * v[k];
+    v[i] = s / L[lt9(i, i)];
+  }
+  double gbar[9], Abp[45];   // adjoints of g and of the packed lower A (A_mu = A (1 + mu on the diagonal))
+  for (int i = 0; i < 9; ++i) {
+    gbar[i] = -v[i];
+    for (int j = 0; j <= i; ++j)
+      Abp[lt9(i, j)] = i == j ? -v[i] * th[i] * (1.0 + mu) : -(v[i] * th[j] + v[j] * th[i]);
+  }
+  lm_model_adjoint(st, z, Abp, gbar, Hb, Bb, zb);
+}
+
+// Adjoint of cam_lm_model: from the adjoints of the packed lower model Hessian (Ab) and of its
+// gradient (gb) to the statistics (added to Hb[a][b] for st_H(a, b), Bb) and to z.R, z.d (added
+// to zb; the model does not depend on z.t). Each block below reverses the matching forward line.
+__device__ inline void lm_model_adjoint(const double* st, const CamT<double>& z, const double* Ab, const double* gb,
+                                        double Hb[6][6], double Bb[6][3], CamT<double>& zb) {
+  double q[6][3];
+  for (int b = 0; b < 6; ++b) {
+    q[b][0] = st_H(st, 0, b);
+    q[b][1] = st_H(st, 1, b);
+    q[b][2] = z.d[0] * st_H(st, 2, b) + z.d[1] * st_H(st, 3, b) + z.d[2] * st_H(st, 4, b);
+  }
+  double qb[6][3] = {}, Qb[3][3] = {};
+  // gradient: g[3+k] = 2 B5k; g[6+n] = 2 sum_r R[r][2] B(2+n, r); g[0..2] from bc = R^T B_a
+  for (int k = 0; k < 3; ++k) Bb[5][k] += 2.0 * gb[3 + k];
+  for (int n = 0; n < 3; ++n)
+    for (int r = 0; r < 3; ++r) {
+      Bb[2 + n][r] += 2.0 * gb[6 + n] * z.R[r * 3 + 2];
+      zb.R[r * 3 + 2] += 2.0 * gb[6 + n] * st_B(st, 2 + n, r);
+    }
+  double bc[5][3], bcb[5][3] = {};
+  for (int a = 0; a < 5; ++a)
+    for (int k = 0; k < 3; ++k)
+      bc[a][k] = z.R[0 * 3 + k] * st_B(st, a, 0) + z.R[1 * 3 + k] * st_B(st, a, 1) + z.R[2 * 3 + k] * st_B(st, a, 2);
+  const double g0 = 2.0 * gb[0], g1 = 2.0 * gb[1], g2 = 2.0 * gb[2];
+  bcb[1][2] += g0;
+  bcb[0][2] -= g1;
+  bcb[0][1] += g2;
+  bcb[1][0] -= g2;
+  for (int m = 0; m < 3; ++m) {
+    bcb[2 + m][1] -= z.d[m] * g0;
+    bcb[2 + m][0] += z.d[m] * g1;
+    zb.d[m] += -g0 * bc[2 + m][1] + g1 * bc[2 + m][0];
+  }
+  for (int a = 0; a < 5; ++a)
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) {
+        Bb[a][r] += bcb[a][k] * z.R[r * 3 + k];
+        zb.R[r * 3 + k] += bcb[a][k] * st_B(st, a, r);
+      }
+  // phi block: A_ij = 2 (delta_ij tr Q - (Q_ij + Q_ji) / 2) + 2 xi delta_ij
+  double trQb = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j <= i; ++j) {
+      const double a = Ab[lt9(i, j)];
+      if (i == j) trQb += 2.0 * a;
+      Qb[i][j] -= a;
+      Qb[j][i] -= a;
+    }
+  for (int r = 0; r < 3; ++r) Qb[r][r] += trQb;
+  // tau rows: A[3+c][.] = -2 r_c x q_5 (r_c row c of R_z), diagonal 2 H55 + xi
+  for (int cc = 0; cc < 3; ++cc) {
+    const double r0 = z.R[cc * 3 + 0], r1 = z.R[cc * 3 + 1], r2 = z.R[cc * 3 + 2];
+    const double a0 = Ab[lt9(3 + cc, 0)], a1 = Ab[lt9(3 + cc, 1)], a2 = Ab[lt9(3 + cc, 2)];
+    zb.R[cc * 3 + 1] += -2.0 * a0 * q[5][2] + 2.0 * a2 * q[5][0];
+    zb.R[cc * 3 + 2] += 2.0 * a0 * q[5][1] - 2.0 * a1 * q[5][0];
+    zb.R[cc * 3 + 0] += 2.0 * a1 * q[5][2] - 2.0 * a2 * q[5][1];
+    qb[5][2] += -2.0 * a0 * r1 + 2.0 * a1 * r0;
+    qb[5][1] += 2.0 * a0 * r2 - 2.0 * a2 * r0;
+    qb[5][0] += -2.0 * a1 * r2 + 2.0 * a2 * r1;
+    Hb[5][5] += 2.0 * Ab[lt9(3 + cc, 3 + cc)];
+  }
+  // delta rows: A[6+n][0] = 2 q[2+n][1], A[6+n][1] = -2 q[2+n][0], A[6+n][3+c] = 2 H(5, 2+n) R[c][2],
+  // A[6+n][6+m] = 2 H(2+n, 2+m) (+ xi on the diagonal)
+  for (int n = 0; n < 3; ++n) {
+    qb[2 + n][1] += 2.0 * Ab[lt9(6 + n, 0)];
+    qb[2 + n][0] -= 2.0 * Ab[lt9(6 + n, 1)];
+    for (int cc = 0; cc < 3; ++cc) {
+      const double a = Ab[lt9(6 + n, 3 + cc)];
+      Hb[5][2 + n] += 2.0 * a * z.R[cc * 3 + 2];
+      zb.R[cc * 3 + 2] += 2.0 * a * st_H(st, 5, 2 + n);
+    }
+    for (int m = 0; m <= n; ++m) Hb[2 + n][2 + m] += 2.0 * Ab[lt9(6 + n, 6 + m)];
+  }
+  // Q[r] = (q0_r, q1_r, sum_m d_m q(2+m)_r), then q from H
+  for (int r = 0; r < 3; ++r) {
+    qb[0][r] += Qb[r][0];
+    qb[1][r] += Qb[r][1];
+    for (int m = 0; m < 3; ++m) {
+      qb[2 + m][r] += z.d[m] * Qb[r][2];
+      zb.d[m] += Qb[r][2] * q[2 + m][r];
+    }
+  }
+  for (int b = 0; b < 6; ++b) {
+    Hb[0][b] += qb[b][0];
+    Hb[1][b] += qb[b][1];
+    for (int m = 0; m < 3; ++m) {
+      Hb[2 + m][b] += z.d[m] * qb[b][2];
+      zb.d[m] += qb[b][2] * st_H(st, 2 + m, b);
+    }
+  }
+}
+
 // Adjoint buffers: per camera 16 doubles (R ambient 9, t 3, d 3, pad), per landmark 4 (l, pad).
 enum { AC_R = 0, AC_T = 9, AC_D = 12, AC_N = 16, AL_N = 4 };
 
@@ -388,11 +600,12 @@ __device__ inline void cam_bar(const CamT<double>& ck, const double* dx, double 
   }
 }
 
-// 1. S-CAM reversed per camera: adjoint of the chosen statistics (packed, 40 per camera) and of
-//    the conditioning point (added to zb_bar or zb_k by the camera's decision).
+// 1. The camera solve reversed per camera (S-CAM, or with lm the LM step): adjoint of the chosen
+//    statistics (packed, 40 per camera) and of the conditioning point (added to zb_bar or zb_k by
+//    the camera's decision).
 __global__ void k_adj_cams(int M, const int* __restrict__ cam_chunk_ptr, const double* __restrict__ part,
                            const double* __restrict__ sx, const double* __restrict__ sdx, double gamma,
-                           const uint8_t* __restrict__ rs_cam, int accelerated, double xi, int n_alt,
+                           const uint8_t* __restrict__ rs_cam, int accelerated, double xi, int n_alt, int lm,
                            const double* __restrict__ a_next, double* __restrict__ st_bar,
                            double* __restrict__ zb_bar, double* __restrict__ zb_k) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -409,8 +622,6 @@ __global__ void k_adj_cams(int M, const int* __restrict__ cam_chunk_ptr, const d
     double Kx[9];
     cam_bar(ck, sdx + (size_t)i * CSTRIDE, gamma, z, Kx);
   }
-  ScamTape tp[4];
-  scam_tape(st, z, xi, n_alt, cn, tp);
   CamT<double> cb, zb;
   const double* an = a_next + (size_t)i * AC_N;
   for (int a = 0; a < 9; ++a) cb.R[a] = an[AC_R + a];
@@ -419,7 +630,13 @@ __global__ void k_adj_cams(int M, const int* __restrict__ cam_chunk_ptr, const d
     cb.d[k] = an[AC_D + k];
   }
   double Hb[6][6], Bb[6][3];
-  scam_adjoint(st, z, xi, n_alt, tp, cb, Hb, Bb, zb);
+  if (lm) {   // the LM camera solver variant
+    lm_adjoint(st, z, xi, cb, Hb, Bb, zb);
+  } else {
+    ScamTape tp[4];
+    scam_tape(st, z, xi, n_alt, cn, tp);
+    scam_adjoint(st, z, xi, n_alt, tp, cb, Hb, Bb, zb);
+  }
   double* so = st_bar + (size_t)i * 40;
   for (int a = 0; a < 6; ++a)
     for (int b = a; b < 6; ++b) so[tri6(a, b)] = a == b ? Hb[a][a] : Hb[a][b] + Hb[b][a];

@@ -372,6 +372,77 @@ void check_lm(Group& grad, Group& hess, Group& fails) {
   fails.cases = 10;
 }
 
+// <cb, c> for the camera c of one LM step (cam_lm) from c_z
+double lm_L(const double* st, const CamT<double>& z, double xi, const CamT<double>& cb) {
+  CamT<double> c;
+  cam_lm(st, z, xi, c);
+  double f = 0;
+  for (int a = 0; a < 9; ++a) f += cb.R[a] * c.R[a];
+  for (int k = 0; k < 3; ++k) f += cb.t[k] * c.t[k] + cb.d[k] * c.d[k];
+  return f;
+}
+
+// the reverse sweep of the LM step (lm_adjoint) against central differences of lm_L in the 39
+// statistics, the tangent directions of z.R and z.t, z.d; taken counts the cases with a step
+void check_lm_adjoint(Group& g, Group& taken) {
+  int steps = 0;
+  for (int rep = 0; rep < 16; ++rep) {
+    double st[39];
+    make_stats_b(st, 40 + rep * 5, 0.02 + 0.02 * (rep % 4));
+    const double xi = rep % 2 ? 1e-3 : 0.2;
+    CamT<double> z, cb, zb, c;
+    double w[3] = {U(), U(), U()};
+    rodrigues(w, z.R);
+    for (int k = 0; k < 3; ++k) z.t[k] = U();
+    z.d[0] = 1.0 + 0.1 * U(), z.d[1] = 0.1 * U(), z.d[2] = 0.05 * U();
+    for (int a = 0; a < 9; ++a) cb.R[a] = U();
+    for (int k = 0; k < 3; ++k) cb.t[k] = U(), cb.d[k] = U();
+    cam_lm(st, z, xi, c);
+    if (c.t[0] != z.t[0]) ++steps;
+    double Hb[6][6], Bb[6][3];
+    lm_adjoint(st, z, xi, cb, Hb, Bb, zb);
+    double sb[39];
+    for (int a = 0; a < 6; ++a)
+      for (int b = a; b < 6; ++b) sb[tri6(a, b)] = a == b ? Hb[a][a] : Hb[a][b] + Hb[b][a];
+    for (int a = 0; a < 6; ++a)
+      for (int cc = 0; cc < 3; ++cc) sb[21 + a * 3 + cc] = Bb[a][cc];
+    std::vector<double> an, fd;
+    for (int k = 0; k < 39; ++k) {
+      const double h = 1e-6 * std::max(1.0, std::fabs(st[k]));
+      double sp[39], sm[39];
+      for (int q = 0; q < 39; ++q) sp[q] = sm[q] = st[q];
+      sp[k] += h, sm[k] -= h;
+      an.push_back(sb[k]);
+      fd.push_back((lm_L(sp, z, xi, cb) - lm_L(sm, z, xi, cb)) / (2 * h));
+    }
+    const double h = 1e-6;
+    for (int a = 0; a < 3; ++a) {   // z.R along z.R Exp(h e_a)
+      double ph[3] = {0, 0, 0}, mh[3] = {0, 0, 0}, Ep[9], Em[9], P[9], dR[9];
+      ph[a] = h, mh[a] = -h;
+      rodrigues(ph, Ep), rodrigues(mh, Em);
+      CamT<double> zp = z, zm = z;
+      matmul3(z.R, Ep, zp.R), matmul3(z.R, Em, zm.R);
+      skew_unit(a, P);
+      matmul3(z.R, P, dR);
+      double d = 0;
+      for (int q = 0; q < 9; ++q) d += zb.R[q] * dR[q];
+      an.push_back(d);
+      fd.push_back((lm_L(st, zp, xi, cb) - lm_L(st, zm, xi, cb)) / (2 * h));
+    }
+    for (int a = 0; a < 6; ++a) {
+      CamT<double> zp = z, zm = z;
+      double* vp = a < 3 ? &zp.t[a] : &zp.d[a - 3];
+      double* vm = a < 3 ? &zm.t[a] : &zm.d[a - 3];
+      *vp += h, *vm -= h;
+      an.push_back(a < 3 ? zb.t[a] : zb.d[a - 3]);
+      fd.push_back((lm_L(st, zp, xi, cb) - lm_L(st, zm, xi, cb)) / (2 * h));
+    }
+    g.add(an, fd);
+  }
+  taken.worst = -steps;   // reported negated: the test wants most cases to have taken a step
+  taken.cases = 16;
+}
+
 }  // namespace
 
 int main() {
@@ -386,6 +457,8 @@ int main() {
   check_boundary(bnd);
   Group lmg{"lm_gradient"}, lmh{"lm_hessian"}, lmf{"lm_no_decrease"};
   check_lm(lmg, lmh, lmf);
-  for (const Group* g : {&polar, &scam, &tape, &triv, &hub, &cau, &wel, &bnd, &lmg, &lmh, &lmf}) g->print();
+  Group lma{"lm_adjoint"}, lms{"lm_adjoint_steps"};
+  check_lm_adjoint(lma, lms);
+  for (const Group* g : {&polar, &scam, &tape, &triv, &hub, &cau, &wel, &bnd, &lmg, &lmh, &lmf, &lma, &lms}) g->print();
   return 0;
 }

@@ -118,7 +118,8 @@ def _rel_err(a, b):
 
 
 @pytest.mark.parametrize("case", ["small-huber-6", "small-cauchy-12", "small-trivial-mm-8", "small-huber-50",
-                                  "circle-tiles-12", "circle-welsch-20", "street-12"])
+                                  "circle-tiles-12", "circle-welsch-20", "street-12", "small-huber-lm-6",
+                                  "small-cauchy-mm-lm-5", "street-lm-8"])
 def test_unrolled_grad_matches_oracle(case):
     """Vector-Jacobian product of K iterations (the CUDA adjoint kernels, states kept every 10
     iterations and recomputed) against autograd through the oracle's PyTorch restatement of the
@@ -140,8 +141,10 @@ def test_unrolled_grad_matches_oracle(case):
         loss, K, accel, scale_px = "welsch", 20, True, 60.0   # no saturated block (no exact restart ties)
     else:
         sc = cached_scene("street", scale=0.05)
-        loss, K, accel, scale_px = sc.loss, 12, True, sc.loss_scale_px
-    o = O.Options(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0)
+        loss, K, accel, scale_px = sc.loss, int(case.split("-")[-1]), True, sc.loss_scale_px
+    solver = "lm" if "-lm-" in case else "scam"   # the LM camera solver variant
+    kw["cam_solver"] = solver
+    o = O.Options(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0, cam_solver=solver)
     rng = np.random.default_rng(4)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)

@@ -199,12 +199,15 @@ def test_lm_camera_solver_mixed_reaches_fp64_objective():
     _mixed_reaches_fp64(cached_scene("tourism", scale=0.005), cam_solver="lm")
 
 
-def test_lm_camera_solver_not_differentiated():
+def test_lm_camera_solver_reverse_mode_needs_fp64():
+    """The reverse mode covers the LM camera solver on FP64 contexts (parity in test_gpu_grad.py);
+    a MIXED context, and an unknown solver, are refused."""
     from paper_2305_07026_b300 import _lib as L
     sc = cached_scene("circle")
-    d = _ctx(sc, "fp64", cam_solver="lm")
-    with pytest.raises(L.DabaError):
+    d = _ctx(sc, "mixed", cam_solver="lm")
+    with pytest.raises(L.DabaError) as e:
         d.unrolled_grad(3, np.zeros((sc.M, 9)), np.zeros((sc.N, 3)))
+    assert e.value.status == L.DABA_ERR_ARG
     d.close()
     with pytest.raises(L.DabaError):
         L.Daba(4, 4, 8, cam_solver=5)

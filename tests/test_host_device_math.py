@@ -1,7 +1,8 @@
 """The library's device math compiled for the host with g++ (the CUDA names it uses are replaced
 by their definitions in tests/host/include) and checked against central differences: the
-reverse-mode pullbacks (ProjRot3D, the S-CAM camera solve, the per-observation terms for every
-loss, the boundary conversions) and the Levenberg-Marquardt camera model. No GPU is used; the
+reverse-mode pullbacks (ProjRot3D, the S-CAM camera solve, the LM camera step, the
+per-observation terms for every loss, the boundary conversions) and the Levenberg-Marquardt camera
+model. No GPU is used; the
 same source files are what nvcc compiles for sm_103a."""
 import os
 import shutil
@@ -19,7 +20,7 @@ FLAGS = ["-std=c++17", "-O1", "-I", os.path.join(HOST, "include"), "-D__device__
 # step 1e-6..1e-7 in FP64 leave about 1e-8; second differences for the Hessian about 1e-9)
 LIMITS = {"polar": 1e-6, "scam": 1e-5, "scam_tape": 0.0, "obs_trivial": 1e-6, "obs_huber": 1e-6,
           "obs_cauchy": 1e-6, "obs_welsch": 1e-6, "boundary": 1e-6, "lm_gradient": 1e-6, "lm_hessian": 1e-5,
-          "lm_no_decrease": 0.0}
+          "lm_no_decrease": 0.0, "lm_adjoint": 1e-5, "lm_adjoint_steps": -12.0}
 
 
 @pytest.fixture(scope="module")

@@ -680,15 +680,18 @@ def test_boundary_gradient_fd(loss):
         assert np.sum(gc * v) == pytest.approx(fd, rel=1e-5, abs=1e-12 * abs(F)), k
 
 
-@pytest.mark.parametrize("loss,accel,K", [("huber", True, 6), ("cauchy", True, 12), ("trivial", False, 8)])
-def test_unrolled_gradient_fd(loss, accel, K):
+@pytest.mark.parametrize("loss,accel,K,solver", [("huber", True, 6, "scam"), ("cauchy", True, 12, "scam"),
+                                                 ("trivial", False, 8, "scam"), ("huber", True, 6, "lm"),
+                                                 ("cauchy", False, 5, "lm")])
+def test_unrolled_gradient_fd(loss, accel, K, solver):
     """Gradient of a linear functional of the state after K iterations (autograd through the
-    PyTorch restatement of the update, restart decisions fixed) against FP64 central
-    differences of the numpy oracle's K-iteration map along random directions."""
+    PyTorch restatement of the update, restart decisions and, with the LM camera solver, the
+    taken damping trials fixed) against FP64 central differences of the numpy oracle's
+    K-iteration map along random directions."""
     from oracle import daba_unrolled as U
     from paper_2305_07026_b300 import scenes
     sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
-    o = O.Options(loss=loss, loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0)
+    o = O.Options(loss=loss, loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0, cam_solver=solver)
     rng = np.random.default_rng(4)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
