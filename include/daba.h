@@ -303,8 +303,8 @@ daba_status daba_set_persistent(daba_ctx* ctx, int enable);
  *   lpass_ctas   resident CTAs per SM of each landmark-pass launch of small tiles (0: one per tile)
  *   prio[3]      stream-priority rank, 0 (highest) to 2, of the camera passes, the camera solves
  *                and the landmark passes
- * Defaults: 2 ranges, ranks (1, 0, 1), no bounds, for problems of at least 2^20 observations;
- * 1 range below. It applies to the graph path (runs without per-kernel timing) of contexts with
+ * Defaults for problems of at least 2^20 observations: 2 ranges, or 6 when the camera solves
+ * (32 cameras per CTA) need more CTAs than 5 per SM, ranks (1, 0, 1), no bounds; 1 range below. It applies to the graph path (runs without per-kernel timing) of contexts with
  * the per-block restart, no coarse blocks and the persistent path off, and is ignored elsewhere;
  * the ranges are recomputed when the observations change. DABA_ERR_ARG for a value out of range. */
 typedef struct {

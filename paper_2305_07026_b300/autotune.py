@@ -11,7 +11,7 @@ import numpy as np
 CHUNKS = (1024, 2048, 4096)
 TILE_OBS = (256, 512, 1024)
 TILE_LMS = (64, 128)
-RANGES = (1, 2, 4)
+RANGES = (1, 2, 4, 6)
 OPTION_KEYS = ("chunk_obs", "tile_obs", "tile_lms")
 
 

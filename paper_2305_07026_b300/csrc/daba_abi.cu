@@ -1464,12 +1464,15 @@ daba_status daba_create(int32_t M, int32_t N, int64_t nnz, const daba_options* o
     daba_destroy(ctx);
     return DABA_ERR_CUDA;
   }
-  // default schedule: two camera ranges for problems of at least PIPE_MIN_NNZ observations
-  // (measured on B300, 100 MIXED iterations: 26M observations 0.742 to 0.698 ms per iteration,
-  // against 0.702 with 4 ranges and 0.73 with 16; 8M in 512 scenes 0.367 to 0.363; 1M 83.1 to
-  // 82.1 us)
+  // default schedule for problems of at least PIPE_MIN_NNZ observations: two camera ranges, or six
+  // when the camera solves need more than one wave of CTAs (5 per SM), since later ranges then hide
+  // more of them. Measured on B300, 100 MIXED iterations (ms per iteration): 26M observations and
+  // 10k cameras (one wave) 0.742 with one range, 0.698 with 2, 0.702 with 4, 0.73 with 16; 8M
+  // observations of 512 scenes and 29,784 cameras (1.3 waves) 0.361 / 0.356 with 2 / 0.359 with 4 /
+  // 0.342 with 6 / 0.342 with 8; 1M observations 83.1 to 82.1 us with 2.
   daba_pipeline dp{};
-  dp.ranges = nnz >= PIPE_MIN_NNZ ? 2 : 1;
+  const bool solve_waves = (M + 31) / 32 > 5 * std::max(ctx->n_sm, 1);
+  dp.ranges = nnz >= PIPE_MIN_NNZ ? (solve_waves ? 6 : 2) : 1;
   dp.prio[0] = 1;
   dp.prio[1] = 0;
   dp.prio[2] = 1;
