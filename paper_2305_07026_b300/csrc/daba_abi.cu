@@ -2479,13 +2479,13 @@ daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p) {
 
 namespace {
 // Sets the range schedule (arguments checked by the caller): the stream pools at the roles'
-// priorities and the ranges for the current observations.
+// priorities (only for more than one range) and the ranges for the current observations.
 daba_status pipe_apply(daba_ctx* ctx, const daba_pipeline& p) {
   pipe_streams_free(ctx);
   drop_graphs(ctx);
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
-  for (int role = 0; role < 3; ++role) {
+  for (int role = 0; role < 3 && p.ranges > 1; ++role) {   // one range needs no pools
     const int prio = std::min(least, greatest + p.prio[role]);   // greater numbers are lower priorities
     for (cudaStream_t& q : ctx->s_pool[role])
       if (cudaStreamCreateWithPriority(&q, cudaStreamNonBlocking, prio) != cudaSuccess) {
