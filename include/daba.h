@@ -178,8 +178,14 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
  * would), keeps the state every 10 iterations and, per segment of 10 iterations from the last,
  * runs the segment again keeping each iteration's state, camera statistics, landmark sums and
  * decisions; it costs about two forward runs plus the adjoint kernels and holds about K/10 + 11
- * copies of the state and 10 of the per-iteration data (about 64 B per landmark). Seeds and outputs: host or device memory; outputs may be NULL. FP64 contexts only
- * (DABA_ERR_ARG for MIXED and for momentum_reset, whose Nesterov scalars live on the device);
+ * copies of the state and 10 of the per-iteration data (about 64 B per landmark). Seeds and
+ * outputs: host or device memory; outputs may be NULL. A MIXED context differentiates its own
+ * trajectory: its forward run keeps all K + 1 iterates (widened to FP64) and every iteration's
+ * restart decisions; then, per iteration from the last, an FP64 context that it owns (same
+ * observations and pixel unit, created on first use, kept until destroy) re-forms that
+ * iteration's statistics in FP64 at the MIXED iterate and runs the FP64 adjoint kernels with the
+ * MIXED decisions. It needs pixels set from host memory (DABA_ERR_STATE otherwise) and holds
+ * K + 1 FP64 states. DABA_ERR_ARG for momentum_reset, whose Nesterov scalars live on the device;
  * DABA_ERR_STATE if iterations have run since the state was set. */
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream);

@@ -116,6 +116,13 @@ struct daba_ctx {
        *s_dev = nullptr;
   // the entry state of daba_run, put back when the run fails
   void* bk = nullptr;
+  // reverse mode of a MIXED context: an FP64 context with the same observations and unit that
+  // replays each iteration from the MIXED iterate (created at first use, refreshed when the
+  // observations or pixels change: obs_version), and the MIXED run's restart decisions
+  daba_ctx* shadow = nullptr;
+  int64_t obs_version = 0, shadow_version = -1;
+  void* mx_dec = nullptr;
+  size_t mx_dec_bytes = 0;
   // persistent path (daba_set_persistent): a run's iterations in one cooperative launch
   bool persistent = false;
   void* d_gbar = nullptr;   // grid-barrier counter and generation
@@ -1318,6 +1325,7 @@ void daba_destroy(daba_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   pipe_streams_free(ctx);
   if (ctx->s_hi) cudaStreamDestroy(ctx->s_hi);
+  if (ctx->shadow) daba_destroy(ctx->shadow);
   if (ctx->s_lo) cudaStreamDestroy(ctx->s_lo);
   if (ctx->s_cap) cudaStreamDestroy(ctx->s_cap);
   delete ctx;
@@ -1640,6 +1648,7 @@ daba_status daba_set_observations(daba_ctx* ctx, const int32_t* cam_idx, const i
   ctx->h_scene_cam.clear();
   ctx->n_scenes = 1;
   ctx->obs_set = true;
+  ++ctx->obs_version;
   ctx->n_blocks = 0;   // a partition refers to the previous observations' numbering
   ctx->checked = false;
   if (ctx->state_set) {
@@ -1996,12 +2005,171 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
   return DABA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The state of a MIXED context at its iteration ctx->k into a state slot of the FP64 layout of
+// `sh` (cameras as they are, landmarks widened: k_lm_widen).
+cudaError_t save_mixed_state(daba_ctx* ctx, daba_ctx* sh, void* slot, cudaStream_t st) {
+  const SlotLayout L = slot_layout(sh);
+  char* b = (char*)slot;
+  const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b + L.x, ctx->cam_x, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(b + L.dx, ctx->cam_dx, cb, cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(b + L.S, ctx->cam_S, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(b + L.E, ctx->cam_E, (size_t)ctx->M * 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+    return e;
+  if (ctx->N > 0)
+    k_lm_widen<<<(ctx->N + 255) / 256, 256, 0, st>>>(ctx->N, (const V4<float>*)lmrec_at(ctx, ctx->k),
+                                                     (const V4<float>*)lmlo_at(ctx, ctx->k), (V4<double>*)(b + L.lm));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaMemcpyAsync(b + L.first, ctx->d_first, sizeof(int), cudaMemcpyDeviceToDevice, st);
+}
+
+// Reverse mode of a MIXED context (daba_unrolled_grad): the vector-Jacobian product of the
+// iteration map along the MIXED run's own iterates and decisions, with FP64 adjoint arithmetic.
+// The MIXED forward keeps every iterate (widened to the FP64 layout) and its restart decisions;
+// then, per iteration from the last, an FP64 context with the same observations and unit (the
+// shadow) starts from the MIXED iterate, runs the iteration once to form, in FP64, the
+// statistics and landmark sums the adjoint reads, takes the MIXED run's decisions, and runs
+// the FP64 adjoint kernels.
+daba_status unrolled_grad_mixed(daba_ctx* ctx, int K, const double* seed_cams, const double* seed_lms, double* g_cams,
+                                double* g_lms, double* g_uv, cudaStream_t st) {
+  const int M = ctx->M, N = ctx->N;
+  const size_t nnz = (size_t)ctx->nnz;
+  daba_status s;
+  if (ctx->h_uv_stale)
+    return fail(ctx, DABA_ERR_STATE, "the reverse mode of a MIXED context needs its pixels set from host memory");
+  if (ctx->shadow && ctx->shadow->s_norm != ctx->s_norm) {   // a new unit: a new shadow
+    daba_destroy(ctx->shadow);
+    ctx->shadow = nullptr;
+  }
+  if (!ctx->shadow || ctx->shadow_version != ctx->obs_version) {
+    if (!ctx->shadow) {
+      daba_options o = ctx->opt;
+      o.prec = DABA_FP64;
+      o.pixel_scale = ctx->s_norm;
+      daba_ctx* sh = nullptr;
+      if ((s = daba_create(M, N, ctx->nnz, &o, &sh)) != DABA_OK)
+        return fail(ctx, s, "creating the FP64 context of the reverse mode failed");
+      ctx->shadow = sh;
+    }
+    daba_ctx* sh = ctx->shadow;
+    if ((s = daba_set_observations(sh, ctx->h_cam_idx.data(), ctx->h_lm_idx.data(), ctx->h_uv.data(), st)) != DABA_OK)
+      return fail(ctx, s, "the reverse mode's FP64 context: %s", sh->err.c_str());
+    std::vector<double> cams((size_t)M * 9), lms((size_t)N * 3);
+    if ((s = daba_get_state(ctx, cams.data(), lms.data(), st)) != DABA_OK) return s;
+    if ((s = daba_set_state(sh, cams.data(), lms.data(), st)) != DABA_OK)
+      return fail(ctx, s, "the reverse mode's FP64 context: %s", sh->err.c_str());
+    ctx->shadow_version = ctx->obs_version;
+  }
+  daba_ctx* sh = ctx->shadow;
+  if ((s = ensure_u(sh, st)) != DABA_OK) return fail(ctx, s, "the reverse mode's FP64 context: %s", sh->err.c_str());
+  if ((s = ensure_adjoint(sh, (size_t)K + 1)) != DABA_OK) return fail(ctx, s, "the reverse mode's FP64 context: out of memory");
+  if ((s = dgrow(ctx, &ctx->mx_dec, (size_t)K * (M + N))) != DABA_OK) return s;
+  char* dec = (char*)ctx->mx_dec;
+  std::vector<double> s_hist((size_t)K + 1);
+  CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(sh->d_flag, 0, sizeof(int), st));
+  // MIXED forward: every iterate and every iteration's decisions
+  for (int k = 0; k < K; ++k) {
+    CK(save_mixed_state(ctx, sh, sh->slots[k], st));
+    s_hist[k] = ctx->s_k;
+    CK(advance(ctx, st, 1));
+    CK(cudaMemcpyAsync(dec + (size_t)k * (M + N), ctx->cam_rs, (size_t)M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(dec + (size_t)k * (M + N) + M, ctx->lm_rs, (size_t)N, cudaMemcpyDeviceToDevice, st));
+  }
+  s_hist[K] = ctx->s_k;
+  CK(save_mixed_state(ctx, sh, sh->slots[K], st));
+  // seed: adjoint of x^K (its camera parameterisation read at x^K)
+  CK(restore_state(sh, sh->slots[K], K, s_hist[K], st));
+  const bool cdev = is_device_ptr(seed_cams), ldev = is_device_ptr(seed_lms);
+  const double* dsc = cdev ? seed_cams : (const double*)sh->st_cam;
+  const double* dsl = ldev ? seed_lms : (const double*)sh->st_lm;
+  if (!cdev) CK(cudaMemcpyAsync(sh->st_cam, seed_cams, (size_t)M * 9 * 8, cudaMemcpyHostToDevice, st));
+  if (!ldev) CK(cudaMemcpyAsync(sh->st_lm, seed_lms, (size_t)N * 3 * 8, cudaMemcpyHostToDevice, st));
+  int i1 = 0, i0 = 1, im = 2;
+  for (int q = 0; q < 3; ++q) {
+    CK(cudaMemsetAsync(sh->adj_c[q], 0, (size_t)M * AC_N * 8, st));
+    CK(cudaMemsetAsync(sh->adj_l[q], 0, (size_t)N * AL_N * 8, st));
+  }
+  CK(cudaMemsetAsync(sh->g_u, 0, nnz * 16, st));
+  if (M > 0)
+    k_adj_seed_cams<<<(M + 127) / 128, 128, 0, st>>>(M, (const double*)sh->cam_x, dsc, sh->s_norm,
+                                                     (double*)sh->adj_c[i1]);
+  if (N > 0)
+    k_adj_seed_lms<<<(N + 255) / 256, 256, 0, st>>>(N, dsl, (const int*)sh->d_linv, (double*)sh->adj_l[i1]);
+  CK(cudaGetLastError());
+  const ItLayout Li = it_layout(sh);
+  void* its = sh->itslots[0];
+  for (int k = K - 1; k >= 0; --k) {
+    void* slot = sh->slots[k];
+    // the iteration once in FP64 from the MIXED iterate: statistics and landmark sums at its points
+    CK(restore_state(sh, slot, k, s_hist[k], st));
+    sh->lm_sums_out = (char*)its + Li.sums;
+    const cudaError_t e = advance(sh, st, 1);
+    sh->lm_sums_out = nullptr;
+    CK(e);
+    CK(save_iteration(sh, its, st));
+    CK(cudaMemcpyAsync((char*)its + Li.rs_cam, dec + (size_t)k * (M + N), (size_t)M, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync((char*)its + Li.rs_lm, dec + (size_t)k * (M + N) + M, (size_t)N, cudaMemcpyDeviceToDevice, st));
+    // its adjoint at the MIXED iterate with the MIXED decisions
+    const double sk = s_hist[k];
+    const double gamma = (sk - 1.0) / ((std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0);
+    CK(restore_state(sh, slot, k, sk, st));
+    CK(cudaMemcpyAsync(sh->d_gam, &gamma, 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(sh->d_it, 0, sizeof(int), st));
+    CK(launch_prepare(sh, st, k));
+    CK(adjoint_iter_by_loss(sh, st, k, gamma, slot, its, i1, i0, im));
+    if (k > 0) {
+      const int t = i1;
+      i1 = i0;
+      i0 = im;
+      im = t;
+      CK(cudaMemsetAsync(sh->adj_c[im], 0, (size_t)M * AC_N * 8, st));
+      CK(cudaMemsetAsync(sh->adj_l[im], 0, (size_t)N * AL_N * 8, st));
+    }
+  }
+  // adjoint of x^0 = x^(-1) to the boundary
+  const SlotLayout Ly = slot_layout(sh);
+  const bool gcdev = g_cams && is_device_ptr(g_cams), gldev = g_lms && is_device_ptr(g_lms);
+  double* gc = gcdev ? g_cams : (double*)sh->st_cam;
+  double* gl = gldev ? g_lms : (double*)sh->st_lm;
+  if (M > 0)
+    k_adj_out_cams<<<(M + 127) / 128, 128, 0, st>>>(M, (const double*)((const char*)sh->slots[0] + Ly.x),
+                                                    (const double*)sh->adj_c[i0], (const double*)sh->adj_c[im],
+                                                    sh->s_norm, gc);
+  if (N > 0)
+    k_adj_out_lms<<<(N + 255) / 256, 256, 0, st>>>(N, (const double*)sh->adj_l[i0], (const double*)sh->adj_l[im],
+                                                   (const int*)sh->d_lperm, gl);
+  CK(cudaGetLastError());
+  if (g_cams && !gcdev) CK(cudaMemcpyAsync(g_cams, gc, (size_t)M * 9 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_lms && !gldev) CK(cudaMemcpyAsync(g_lms, gl, (size_t)N * 3 * 8, cudaMemcpyDeviceToHost, st));
+  if (g_uv)
+    CK(cudaMemcpyAsync(g_uv, sh->g_u, nnz * 16, is_device_ptr(g_uv) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+  int flag = 0, flag_sh = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&flag_sh, sh->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if ((flag | flag_sh) & 2)
+    return fail(ctx, DABA_ERR_TIMEOUT, "a landmark-pass copy did not complete in time (bounded wait ran out)");
+  if (flag | flag_sh) return fail(ctx, DABA_ERR_NONFINITE, "the objective became non-finite");
+  return DABA_OK;   // the MIXED context is left at x^K by its forward run
+}
+
+}  // namespace
+
+extern "C" {
+
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream) {
   if (!ctx) return DABA_ERR_ARG;
   if (K < 1) return fail(ctx, DABA_ERR_ARG, "K must be >= 1");
   if (!seed_cams || !seed_lms) return fail(ctx, DABA_ERR_ARG, "null seed pointer");
-  if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient needs an FP64 context");
   if (ctx->n_blocks) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient covers one block per camera and landmark");
   if (ctx->opt.momentum_reset)
     return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
@@ -2011,6 +2179,13 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   daba_status s;
   if ((s = check_degenerate(ctx, st)) != DABA_OK) return s;
   if ((s = ensure_u(ctx, st)) != DABA_OK) return s;
+  if (is_mixed(ctx)) {   // the MIXED trajectory with FP64 adjoint arithmetic (direct launches)
+    const bool was = ctx->timing;
+    ctx->timing = false;
+    s = unrolled_grad_mixed(ctx, K, seed_cams, seed_lms, g_cams, g_lms, g_uv, st);
+    ctx->timing = was;
+    return s;
+  }
   const int C = ADJ_CKPT;
   const int n_seg = (K + C - 1) / C;
   // slots: [0, n_seg) the states at k = 0, C, 2C, ...; [n_seg, n_seg + C) the states of one
@@ -2146,6 +2321,7 @@ daba_status daba_set_pixels(daba_ctx* ctx, const double* uv, void* stream) {
   CK(cudaStreamSynchronize(st));
   ctx->u_scale_uploaded = ctx->s_norm;
   if (dev) ctx->h_uv_stale = true;
+  ++ctx->obs_version;
   if (bad != INT_MAX) return fail(ctx, DABA_ERR_NONFINITE, "observation %d has a non-finite pixel", bad);
   return DABA_OK;
 }

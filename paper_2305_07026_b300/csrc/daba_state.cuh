@@ -135,6 +135,28 @@ __global__ void k_get_lms(int N, const V4<Real>* __restrict__ rec, const V4<floa
   lms[(size_t)j * 3 + 2] = v2;
 }
 
+// A MIXED landmark state (float records, float low parts) as the FP64 path's records: l = high +
+// low part (exact in FP64), the displacement and the slack S widened, E (kept by the FP64 path
+// only) zero. Internal order is kept. The reverse mode of MIXED contexts runs its FP64 adjoint
+// on these.
+__global__ void k_lm_widen(int N, const V4<float>* __restrict__ rec, const V4<float>* __restrict__ lo,
+                           V4<double>* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const V4<float> A = rec[2 * (size_t)q], B = rec[2 * (size_t)q + 1], L = lo[q];
+  V4<double> a, b;
+  a.x = double(A.x) + double(L.x);
+  a.y = double(A.y) + double(L.y);
+  a.z = double(A.z) + double(L.z);
+  a.w = double(A.w);
+  b.x = double(B.x);
+  b.y = double(B.y);
+  b.z = double(B.z);
+  b.w = 0.0;
+  out[2 * (size_t)q] = a;
+  out[2 * (size_t)q + 1] = b;
+}
+
 // Assumption 2 on the current iterate: |l_j - t_i|^2 > 1e-24 max(1, |t_i|^2) for every
 // observation; one block per camera chunk, the smallest failing device position kept.
 // FP64 path: in FP64. MIXED: l and t as FP32 high + low parts and q = (l_hi - t_hi) +

@@ -267,3 +267,51 @@ def test_unrolled_grad_differentiation_workload_k50():
         cams, lms = d.get_state()
     np.testing.assert_array_equal(st_a[0], cams)
     np.testing.assert_array_equal(st_a[1], lms)
+
+
+@pytest.mark.parametrize("accel,K", [(False, 8), (True, 4), (True, 12)])
+def test_unrolled_grad_mixed_context(accel, K):
+    """Reverse mode of a MIXED context: the product along the MIXED run's iterates and decisions
+    with FP64 adjoint arithmetic. Its trajectory differs from the FP64 one by FP32 rounding only
+    (checked: the same restart counts), so the two products agree to FP32-level relative error;
+    the product is linear in the seed, and the context is left at x^K bit for bit as run(K)."""
+    from paper_2305_07026_b300 import _lib as L, scenes
+    sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
+    rng = np.random.default_rng(21)
+    g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
+    opts = dict(loss="huber", loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0)
+
+    def ctx(prec):
+        d = L.Daba(sc.M, sc.N, sc.nnz, prec=prec, **opts)
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_state(sc.cams, sc.lms)
+        return d
+
+    rs = {}
+    for prec in ("fp64", "mixed"):
+        with ctx(prec) as d:
+            r = np.zeros(K, np.int32)
+            d.run(K, restarts=r)
+            rs[prec] = r
+    assert rs["mixed"].tolist() == rs["fp64"].tolist()
+    with ctx("fp64") as d:
+        gc64, gl64, gu64 = d.unrolled_grad(K, g_c, g_l)
+    with ctx("mixed") as d:
+        gcm, glm, gum = d.unrolled_grad(K, g_c, g_l)
+        cams_m, lms_m = d.get_state()
+        gcm2, glm2, gum2 = None, None, None
+    with ctx("mixed") as d:
+        d.run(K)
+        cams_r, lms_r = d.get_state()
+    np.testing.assert_array_equal(cams_m, cams_r)
+    np.testing.assert_array_equal(lms_m, lms_r)
+    errs = {"cams": _rel_err(gcm, gc64), "lms": _rel_err(glm, gl64), "uv": _rel_err(gum, gu64)}
+    assert max(errs.values()) < 2e-3, errs
+    with ctx("mixed") as d:   # linear in the seed
+        gcm2, glm2, gum2 = d.unrolled_grad(K, 2.0 * g_c, -3.0 * g_l)
+    with ctx("mixed") as d:
+        gcl, gll, gul = d.unrolled_grad(K, g_c, np.zeros_like(g_l))
+    with ctx("mixed") as d:
+        gcr, glr, gur = d.unrolled_grad(K, np.zeros_like(g_c), g_l)
+    for a, b, c in ((gcm2, gcl, gcr), (glm2, gll, glr), (gum2, gul, gur)):
+        np.testing.assert_allclose(a, 2.0 * b - 3.0 * c, rtol=1e-9, atol=1e-9 * np.max(np.abs(a)))

@@ -199,16 +199,22 @@ def test_lm_camera_solver_mixed_reaches_fp64_objective():
     _mixed_reaches_fp64(cached_scene("tourism", scale=0.005), cam_solver="lm")
 
 
-def test_lm_camera_solver_reverse_mode_needs_fp64():
-    """The reverse mode covers the LM camera solver on FP64 contexts (parity in test_gpu_grad.py);
-    a MIXED context, and an unknown solver, are refused."""
+def test_lm_camera_solver_reverse_mode_mixed():
+    """The reverse mode covers the LM camera solver on MIXED contexts too (FP64 parity in
+    test_gpu_grad.py): along the MIXED run, its product agrees with the FP64 context's to
+    FP32-level relative error; an unknown solver is refused."""
     from paper_2305_07026_b300 import _lib as L
     sc = cached_scene("circle")
-    d = _ctx(sc, "mixed", cam_solver="lm")
-    with pytest.raises(L.DabaError) as e:
-        d.unrolled_grad(3, np.zeros((sc.M, 9)), np.zeros((sc.N, 3)))
-    assert e.value.status == L.DABA_ERR_ARG
-    d.close()
+    rng = np.random.default_rng(5)
+    seed = (rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape))
+    out = {}
+    for prec in ("fp64", "mixed"):
+        d = _ctx(sc, prec, cam_solver="lm")
+        out[prec] = d.unrolled_grad(3, *seed)
+        d.close()
+    for a, b in zip(out["mixed"], out["fp64"]):
+        assert np.all(np.isfinite(a))
+        np.testing.assert_allclose(a, b, rtol=2e-3, atol=2e-3 * np.abs(b).max())
     with pytest.raises(L.DabaError):
         L.Daba(4, 4, 8, cam_solver=5)
 
