@@ -185,8 +185,9 @@ daba_status daba_objective_grad(daba_ctx* ctx, double* F, double* g_cams, double
  * observations and pixel unit, created on first use, kept until destroy) re-forms that
  * iteration's statistics in FP64 at the MIXED iterate and runs the FP64 adjoint kernels with the
  * MIXED decisions. It needs pixels set from host memory (DABA_ERR_STATE otherwise) and holds
- * K + 1 FP64 states. DABA_ERR_ARG for momentum_reset, whose Nesterov scalars live on the device;
- * DABA_ERR_STATE if iterations have run since the state was set. */
+ * K + 1 FP64 states. With momentum_reset, the Nesterov scalars the device continued (s = 1 after
+ * a global restart) are read back after every forward iteration and replayed with the restart
+ * decisions. DABA_ERR_STATE if iterations have run since the state was set. */
 daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams, const double* seed_lms,
                                double* g_cams, double* g_lms, double* g_uv, void* stream);
 

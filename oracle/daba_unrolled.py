@@ -206,6 +206,8 @@ def unrolled_state(cams, lms, uv, cam_idx, lm_idx, opts: O.Options, K: int, rest
             tn = torch.where(rc[:, None], tm, ta)
             dn = torch.where(rc[:, None], dm, da)
             ln = torch.where(rl[:, None], lmm, la)
+            if opts.momentum_reset and opts.restart == "global" and bool(np.all(restart_cam[k])):
+                s = 1.0   # the Nesterov scalar restarts with a global restart (the momentum reset)
         else:
             Rn, tn, dn, ln = Rm, tm, dm, lmm
         Rp, tp, dp, lp = R, t, d, l

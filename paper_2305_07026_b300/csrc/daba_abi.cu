@@ -1200,7 +1200,8 @@ cudaError_t backup_copy(daba_ctx* ctx, bool to_backup, int64_t k, bool lm_too, c
 // synchronisation and objective trace)
 cudaError_t advance(daba_ctx* ctx, cudaStream_t st, int n) {
   std::vector<double> gam((size_t)n + 1);
-  double sk = ctx->s_k;
+  const double s_from = ctx->s_k;
+  double sk = s_from;
   for (int j = 0; j <= n; ++j) {
     const double s_next = (std::sqrt(4.0 * sk * sk + 1.0) + 1.0) / 2.0;
     gam[j] = (sk - 1.0) / s_next;
@@ -1210,10 +1211,18 @@ cudaError_t advance(daba_ctx* ctx, cudaStream_t st, int n) {
   cudaError_t e;
   if ((e = cudaMemcpyAsync(ctx->d_gam, gam.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
+  // momentum reset: the reduction continues s on the device from s^(k); s^(k+n) is read back
+  if (ctx->opt.momentum_reset &&
+      (e = cudaMemcpyAsync(ctx->s_dev, &s_from, 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
   if ((e = cudaMemsetAsync(ctx->d_it, 0, sizeof(int), st)) != cudaSuccess) return e;
   if ((e = launch_prepare(ctx, st, ctx->k)) != cudaSuccess) return e;
   if ((e = enqueue_iters(ctx, st, ctx->k, n, 0)) != cudaSuccess) return e;
   ctx->k += n;
+  if (ctx->opt.momentum_reset) {
+    if ((e = cudaMemcpyAsync(&ctx->s_k, ctx->s_dev, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  }
   return cudaSuccess;
 }
 
@@ -2171,8 +2180,6 @@ daba_status daba_unrolled_grad(daba_ctx* ctx, int32_t K, const double* seed_cams
   if (K < 1) return fail(ctx, DABA_ERR_ARG, "K must be >= 1");
   if (!seed_cams || !seed_lms) return fail(ctx, DABA_ERR_ARG, "null seed pointer");
   if (ctx->n_blocks) return fail(ctx, DABA_ERR_ARG, "the unrolled gradient covers one block per camera and landmark");
-  if (ctx->opt.momentum_reset)
-    return fail(ctx, DABA_ERR_ARG, "the unrolled gradient does not support momentum_reset");
   if (!ctx->obs_set || !ctx->state_set) return fail(ctx, DABA_ERR_STATE, "observations and state must be set first");
   if (ctx->k != 0) return fail(ctx, DABA_ERR_STATE, "iterations have run since the state was set");
   cudaStream_t st = (cudaStream_t)stream;

@@ -119,7 +119,8 @@ def _rel_err(a, b):
 
 @pytest.mark.parametrize("case", ["small-huber-6", "small-cauchy-12", "small-trivial-mm-8", "small-huber-50",
                                   "circle-tiles-12", "circle-welsch-20", "street-12", "small-huber-lm-6",
-                                  "small-cauchy-mm-lm-5", "street-lm-8"])
+                                  "small-cauchy-mm-lm-5", "street-lm-8", "small-huber-reset-15",
+                                  "small-trivial-lm-reset-14"])
 def test_unrolled_grad_matches_oracle(case):
     """Vector-Jacobian product of K iterations (the CUDA adjoint kernels, states kept every 10
     iterations and recomputed) against autograd through the oracle's PyTorch restatement of the
@@ -144,7 +145,11 @@ def test_unrolled_grad_matches_oracle(case):
         loss, K, accel, scale_px = sc.loss, int(case.split("-")[-1]), True, sc.loss_scale_px
     solver = "lm" if "-lm-" in case else "scam"   # the LM camera solver variant
     kw["cam_solver"] = solver
-    o = O.Options(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0, cam_solver=solver)
+    ok = {}
+    if "-reset-" in case:   # global restart with the momentum reset (one restart fires within K)
+        kw.update(restart="global", momentum_reset=True)
+        ok = dict(restart="global", momentum_reset=True)
+    o = O.Options(loss=loss, loss_scale_px=scale_px, accelerated=accel, pixel_scale=650.0, cam_solver=solver, **ok)
     rng = np.random.default_rng(4)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
@@ -157,6 +162,8 @@ def test_unrolled_grad_matches_oracle(case):
         d.run(K, restarts=rs)
         want = [int(np.sum(i.restart_cam)) + int(np.sum(i.restart_lm)) for i in res.infos] if accel else [0] * K
         assert rs.tolist() == want
+        if ok:
+            assert any(want[:K - 1])
     with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
         d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
         d.set_state(sc.cams, sc.lms)
@@ -269,8 +276,8 @@ def test_unrolled_grad_differentiation_workload_k50():
     np.testing.assert_array_equal(st_a[1], lms)
 
 
-@pytest.mark.parametrize("accel,K", [(False, 8), (True, 4), (True, 12)])
-def test_unrolled_grad_mixed_context(accel, K):
+@pytest.mark.parametrize("accel,K,reset", [(False, 8, False), (True, 4, False), (True, 12, False), (True, 15, True)])
+def test_unrolled_grad_mixed_context(accel, K, reset):
     """Reverse mode of a MIXED context: the product along the MIXED run's iterates and decisions
     with FP64 adjoint arithmetic. Its trajectory differs from the FP64 one by FP32 rounding only
     (checked: the same restart counts), so the two products agree to FP32-level relative error;
@@ -280,6 +287,8 @@ def test_unrolled_grad_mixed_context(accel, K):
     rng = np.random.default_rng(21)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     opts = dict(loss="huber", loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0)
+    if reset:   # global restart with the momentum reset
+        opts.update(restart="global", momentum_reset=True)
 
     def ctx(prec):
         d = L.Daba(sc.M, sc.N, sc.nnz, prec=prec, **opts)

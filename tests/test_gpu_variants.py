@@ -127,29 +127,31 @@ def test_global_restart_monotone_at_eta_one():
     d.close()
 
 
-def test_global_restart_unrolled_grad():
-    """The reverse mode replays the global decisions (set on every block by the fix-up)."""
+@pytest.mark.parametrize("reset", [False, True])
+def test_global_restart_unrolled_grad(reset):
+    """The reverse mode replays the global decisions (set on every block by the fix-up); with the
+    momentum reset, also the Nesterov scalars the device continued (s <- 1 after a restart)."""
     from oracle import daba_unrolled as U
     from paper_2305_07026_b300 import _lib as L, scenes
     sc = scenes.circle_scene(seed=3)
     K = 15
-    o = O.Options(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, restart="global", eta=1.0)
+    o = O.Options(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, restart="global", eta=1.0,
+                  momentum_reset=reset)
     rng = np.random.default_rng(4)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
     assert any(i.restart_cam.all() for i in res.infos)
-    opts = dict(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, prec="fp64", restart="global", eta=1.0)
+    opts = dict(loss="huber", loss_scale_px=2.0, pixel_scale=650.0, prec="fp64", restart="global", eta=1.0,
+                momentum_reset=reset)
     with L.Daba(sc.M, sc.N, sc.nnz, **opts) as d:
         d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
         d.set_state(sc.cams, sc.lms)
         gcg, glg, gug = d.unrolled_grad(K, g_c, g_l)
+        cams, lms = d.get_state()
+    np.testing.assert_allclose(cams, oc, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(lms, ol, rtol=1e-8, atol=1e-8)
     for a, b in ((gcg, gc), (glg, gl), (gug, gu)):
         assert np.max(np.abs(a - b)) <= 1e-7 * np.max(np.abs(b))
-    with L.Daba(sc.M, sc.N, sc.nnz, **dict(opts, momentum_reset=True)) as d:
-        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
-        d.set_state(sc.cams, sc.lms)
-        with pytest.raises(L.DabaError):
-            d.unrolled_grad(K, g_c, g_l)
 
 
 def test_variant_options_validated():

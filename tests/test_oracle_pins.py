@@ -682,7 +682,8 @@ def test_boundary_gradient_fd(loss):
 
 @pytest.mark.parametrize("loss,accel,K,solver", [("huber", True, 6, "scam"), ("cauchy", True, 12, "scam"),
                                                  ("trivial", False, 8, "scam"), ("huber", True, 6, "lm"),
-                                                 ("cauchy", False, 5, "lm")])
+                                                 ("cauchy", False, 5, "lm"), ("huber", True, 15, "scam-reset"),
+                                                 ("trivial", True, 14, "lm-reset")])
 def test_unrolled_gradient_fd(loss, accel, K, solver):
     """Gradient of a linear functional of the state after K iterations (autograd through the
     PyTorch restatement of the update, restart decisions and, with the LM camera solver, the
@@ -691,10 +692,16 @@ def test_unrolled_gradient_fd(loss, accel, K, solver):
     from oracle import daba_unrolled as U
     from paper_2305_07026_b300 import scenes
     sc = scenes.circle_scene(seed=11, n_cams=6, n_lms=40, cap=6)
-    o = O.Options(loss=loss, loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0, cam_solver=solver)
+    kw = {}
+    if solver.endswith("-reset"):   # global restart with the momentum reset: one restart fires within K
+        solver = solver[:-6]
+        kw = dict(restart="global", momentum_reset=True)
+    o = O.Options(loss=loss, loss_scale_px=2.0, accelerated=accel, pixel_scale=650.0, cam_solver=solver, **kw)
     rng = np.random.default_rng(4)
     g_c, g_l = rng.normal(size=sc.cams.shape), rng.normal(size=sc.lms.shape)
     gc, gl, gu, oc, ol, res = U.unrolled_grad(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, o, K, g_c, g_l)
+    if kw:
+        assert any(np.all(i.restart_cam) for i in res.infos[:K - 1])
     cams_o, lms_o = O.boundary_state(res)
     np.testing.assert_allclose(oc, cams_o, rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(ol, lms_o, rtol=1e-9, atol=1e-9)
