@@ -564,6 +564,7 @@ def run_ours(args, rank, world, local):
         extra["unrolled_gradient"] = unrolled
         if not args.no_variants:
             extra["variants"] = variants_leg(L, sc, Ka, trm, stream, sp)
+            extra["coarse_blocks"] = blocks_leg(L, stream, sp)
 
     # the batch workload (512 independent circle-generator scenes, 100 iterations each, the default
     # schedule) as one problem, against one context per scene
@@ -678,6 +679,35 @@ def variants_leg(L, sc, Kf, trm, stream, sp):
                           "final_rel_to_reference": float((trv[Kf] - trm[Kf]) / trm[Kf]),
                           "restart_iterations": int(np.count_nonzero(rsv))}
     return variants
+
+
+def blocks_leg(L, stream, sp, K=5):
+    """Coarse blocks (FP64): the street generator at a quarter of its size (250 cameras) cut into
+    contiguous groups of 1 to 128 cameras with the landmarks they see first; K iterations from the
+    same x^0 per partition, time per iteration and the objective reached."""
+    import torch
+    from paper_2305_07026_b300 import partition, scenes
+    sc = scenes.make_scene("street", scale=0.25)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"scene": f"street-0.25: {sc.M} cameras, {sc.N} landmarks, {sc.nnz} observations", "iters": K}
+    for cpb in (1, 8, 16, 32, 64, 128):
+        nb = -(-sc.M // cpb)
+        cb, lb = partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, nb)
+        d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv, stream=sp)
+        d.set_partition(cb, lb)
+        d.set_state(sc.cams, sc.lms, stream=sp)
+        d.run(1, stream=sp)   # first launches; then x^0 again
+        d.set_state(sc.cams, sc.lms, stream=sp)
+        tr = np.zeros(K + 1)
+        e0.record(stream)
+        d.run(K, tr, stream=sp)
+        e1.record(stream)
+        e1.synchronize()
+        d.close()
+        out[f"{cpb}_cameras_per_block"] = {"blocks": int(nb), "ms_per_iteration": e0.elapsed_time(e1) / K,
+                                            "objective_px2": [float(tr[0]), float(tr[K])]}
+    return out
 
 
 def batch_leg(L, scs, b, K, W, stream, sched, clocks=None, world=1, local=0):

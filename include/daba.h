@@ -269,13 +269,17 @@ daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
  * w = rho'(|e|^2) at z, the proximal term to second order); damping 1e-3 x diag, raised tenfold
  * up to 8 times; taken only if E^alpha(. | z) decreases. The damped system is solved through the
  * Schur complement of the block's cameras (9 per camera; every landmark's 3 x 3 block
- * eliminated), one CTA per block. The restart metrics of Eqs. DEalpha-Eak are per block
+ * eliminated), one CTA per block, with a dense Cholesky factorisation: up to 16 cameras per block
+ * in shared memory, above that in global memory (a cost of about (9 n_c)^3 / 3 FP64 multiply-adds
+ * per damping trial on one SM). The restart metrics of Eqs. DEalpha-Eak are per block
  * (daba_get_partition_metrics); the restart count of daba_run counts the blocks that hold a
  * camera. A camera may observe each landmark of its block at most once (DABA_ERR_ARG otherwise,
- * as for a block id out of range or a block of more than 8 cameras). Call after daba_set_observations (which clears the
- * partition); n_blocks = 0 returns to one block per camera and per landmark (the arrays are then
- * ignored). The device scratch grows with the partition: 448 bytes per intra pair, 248 per
- * landmark. Checkpoints and the unrolled gradient are not available while a partition is set. */
+ * as for a block id out of range or a block of more than 128 cameras). Call after
+ * daba_set_observations (which clears the partition); n_blocks = 0 returns to one block per
+ * camera and per landmark (the arrays are then ignored). The device scratch grows with the
+ * partition: 888 bytes per intra pair, 248 per landmark, and with blocks of more than 16 cameras
+ * 1680 bytes per camera plus (9 n_c)^2 x 8 bytes per block. Checkpoints and the unrolled gradient
+ * are not available while a partition is set. */
 daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* cam_block, const int32_t* lm_block);
 
 /* Per-block metrics of the last iteration with a partition (each pointer may be NULL, n_blocks

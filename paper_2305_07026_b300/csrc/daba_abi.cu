@@ -129,7 +129,10 @@ struct daba_ctx {
   // coarse blocks (daba_set_partition): up to BLK_MAX_CAMS cameras and any landmarks per block,
   // FP64; the buffers grow with the partition (blk_cap: bytes held per buffer)
   int n_blocks = 0;
-  int blk_ld = 0;   // row stride of a block's Schur matrix: 9 x the most cameras in one block
+  int blk_ld = 0;        // 9 x the most cameras in one block with the scratch in shared memory, else 0
+  size_t blk_smem = 0;   // dynamic shared memory of the block solve
+  void *blk_ci_e = nullptr, *blk_ci_io = nullptr, *blk_gcam = nullptr, *blk_gvec = nullptr, *blk_gS = nullptr,
+       *blk_soff = nullptr;
   void *c_intra = nullptr, *blk_cam_ptr = nullptr, *blk_cams = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr,
        *blk_io_ptr = nullptr, *blk_io_cam = nullptr, *blk_io_obs = nullptr, *blk_ci_ptr = nullptr,
        *blk_ci_obs = nullptr, *blk_ci_lm = nullptr, *blk_sums = nullptr, *blk_lsc = nullptr, *blk_isc = nullptr,
@@ -516,6 +519,12 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   A.ci_ptr = (const int*)ctx->blk_ci_ptr;
   A.ci_obs = (const int*)ctx->blk_ci_obs;
   A.ci_lm = (const int*)ctx->blk_ci_lm;
+  A.ci_e = (const int*)ctx->blk_ci_e;
+  A.ci_io = (const int*)ctx->blk_ci_io;
+  A.g_cam = (BlkCam*)ctx->blk_gcam;
+  A.g_vec = (double*)ctx->blk_gvec;
+  A.g_S = (double*)ctx->blk_gS;
+  A.g_soff = (const long long*)ctx->blk_soff;
   A.c_u = (const double2*)ctx->c_u;
   A.cam_chunk_ptr = (const int*)ctx->cam_chunk_ptr;
   A.part = (const double*)ctx->chunk_part;
@@ -536,7 +545,7 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   A.pack_next = (V4<double>*)pack_at(ctx, k + 1);
   A.L = L;
   A.loss = LOSS;
-  k_blk_solve<<<ctx->n_blocks, BLK_THREADS, (size_t)ctx->blk_ld * ctx->blk_ld * 8, st>>>(A, P);
+  k_blk_solve<<<ctx->n_blocks, BLK_THREADS, ctx->blk_smem, st>>>(A, P);
   ctx->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_finalize(ctx, st);
@@ -2562,7 +2571,7 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   }
   for (int e = 0; e < N; ++e) io_ptr[e + 1] += io_ptr[e];
   for (int e = 0; e < M; ++e) ci_ptr[e + 1] += ci_ptr[e];
-  std::vector<int32_t> io_cam(n_in), io_obs(n_in), ci_obs(n_in), ci_lm(n_in);
+  std::vector<int32_t> io_cam(n_in), io_obs(n_in), ci_obs(n_in), ci_lm(n_in), ci_e(n_in), ci_io(n_in);
   {
     std::vector<int32_t> ip(io_ptr.begin(), io_ptr.end() - 1), cp(ci_ptr.begin(), ci_ptr.end() - 1);
     for (int64_t o = 0; o < n; ++o) {
@@ -2573,16 +2582,36 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
       // observations run by camera, so a landmark's pairs arrive by ascending camera
       if (ip[e] > io_ptr[e] && io_cam[ip[e] - 1] == cloc[i])
         return fail(ctx, DABA_ERR_ARG, "camera %d observes landmark %d twice inside a block", i, j);
+      ci_e[cp[cpos[i]]] = e;
+      ci_io[cp[cpos[i]]] = ip[e];
       io_cam[ip[e]] = cloc[i];
       io_obs[ip[e]++] = (int32_t)o;
       ci_lm[cp[cpos[i]]] = ji;
       ci_obs[cp[cpos[i]]++] = (int32_t)o;
     }
   }
+  // the block scratch: in shared memory when every block has at most BLK_SMEM_CAMS cameras (per
+  // camera scratch, two vectors and the Schur matrix of the largest block), else in global memory
+  // (per camera entry, and each block's Schur matrix of stride 9 x its cameras)
+  const bool in_smem = most <= BLK_SMEM_CAMS;
   const int ld = 9 * most;
-  const size_t smem = (size_t)ld * ld * 8;
+  const size_t smem = in_smem ? (size_t)most * sizeof(BlkCam) + (size_t)(2 * ld + ld * ld) * 8 : 0;
+  std::vector<long long> soff(S + 1, 0);
+  for (int b = 0; b < S; ++b) {
+    const long long nb = 9LL * (cam_ptr[b + 1] - cam_ptr[b]);
+    soff[b + 1] = soff[b] + (in_smem ? 0 : nb * nb);
+  }
   CK(cudaFuncSetAttribute(k_blk_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const size_t ni = (size_t)n_in;
+  if (!in_smem) {
+    if ((s = dgrow(ctx, &ctx->blk_gcam, (size_t)M * sizeof(BlkCam))) != DABA_OK) return s;
+    if ((s = dgrow(ctx, &ctx->blk_gvec, (size_t)M * 18 * 8)) != DABA_OK) return s;
+    if ((s = dgrow(ctx, &ctx->blk_gS, (size_t)std::max(soff[S], 1LL) * 8)) != DABA_OK) return s;
+  }
+  if ((s = dgrow(ctx, &ctx->blk_soff, (size_t)(S + 1) * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_ci_e, std::max(ni, (size_t)1) * 4)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_ci_io, std::max(ni, (size_t)1) * 4)) != DABA_OK) return s;
+  CK(cudaMemcpy(ctx->blk_soff, soff.data(), (size_t)(S + 1) * 8, cudaMemcpyHostToDevice));
   if ((s = dgrow(ctx, &ctx->c_intra, (size_t)n)) != DABA_OK) return s;
   if ((s = dgrow(ctx, &ctx->blk_cam_ptr, (size_t)(S + 1) * 4)) != DABA_OK) return s;
   if ((s = dgrow(ctx, &ctx->blk_cams, (size_t)M * 4)) != DABA_OK) return s;
@@ -2614,10 +2643,13 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
     CK(cudaMemcpy(ctx->blk_io_obs, io_obs.data(), ni * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->blk_ci_obs, ci_obs.data(), ni * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->blk_ci_lm, ci_lm.data(), ni * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_ci_e, ci_e.data(), ni * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_ci_io, ci_io.data(), ni * 4, cudaMemcpyHostToDevice));
   }
   CK(cudaMemset(ctx->blk_rs, 0, (size_t)S));
   ctx->n_blocks = S;
-  ctx->blk_ld = ld;
+  ctx->blk_ld = in_smem ? ld : 0;
+  ctx->blk_smem = smem;
   drop_graphs(ctx);
   return DABA_OK;
 }

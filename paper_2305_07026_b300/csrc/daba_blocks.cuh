@@ -25,8 +25,8 @@
 
 namespace daba {
 
-constexpr int BLK_MAX_CAMS = 8;
-constexpr int BLK_NP = 9 * BLK_MAX_CAMS;   // camera parameters of a block
+constexpr int BLK_MAX_CAMS = 128;    // cameras per block (a Schur matrix of 1152 x 1152)
+constexpr int BLK_SMEM_CAMS = 16;    // up to this many in every block: the block scratch in shared memory
 constexpr int BLK_THREADS = 128;
 
 // landmark sums written by the landmark pass in sum mode (per internal landmark)
@@ -34,15 +34,30 @@ enum { LS_AB = 0, LS_BB = 1, LS_AK = 4, LS_BK = 5, LS_F = 8, LS_G = 9, LS_N = 10
 // per landmark scratch of the block solve: C (packed), C^-1 of the damped system, gradient,
 // the solution, the F_ij at z of its intra pairs
 enum { BL_C = 0, BL_CI = 6, BL_G = 12, BL_L = 15, BL_FZ = 18, BL_N = 20 };
-// per intra pair scratch: B = w Jc^T Jl (9 x 3) and B C^-1
-enum { BI_B = 0, BI_BC = 27, BI_N = 54 };
+// per intra pair scratch: B = w Jc^T Jl (9 x 3), B C^-1, and the camera-side terms w Jc^T Jc
+// (packed lower 9 x 9) and w Jc^T f
+enum { BI_B = 0, BI_BC = 27, BI_A = 54, BI_GC = 99, BI_N = 108 };
+
+// per camera scratch of the block solve: x^k, the conditioning iterate z, the solution, the
+// candidate; the statistics at x̄^k and x^k; the LM model (packed lower 9 x 9 and gradient)
+struct BlkCam {
+  CamT<double> ck, cz, cs, cb;
+  double stb[39], stk[39];
+  double A[45], g[9];
+};
 
 struct BlkArgs {
-  int S, ld;                          // blocks; row stride of the Schur matrix (9 x the most cameras in a block)
+  int S, ld;   // blocks; row stride of the shared-memory Schur matrix (9 x the most cameras in a
+               // block), 0 when the block scratch is in global memory (row stride 9 x the block's cameras)
   const int *cam_ptr, *cams;          // cameras of each block (ascending)
   const int *lm_ptr, *lms;            // landmarks of each block (internal ids, ascending)
   const int *io_ptr, *io_cam, *io_obs;   // per landmark entry: its intra pairs (local camera, observation), by camera
   const int *ci_ptr, *ci_obs, *ci_lm;    // per camera entry: its intra pairs (observation, landmark), by observation
+  const int *ci_e, *ci_io;               // ... and the pair's landmark entry and its index in the landmark lists
+  BlkCam* g_cam;                         // global scratch (ld = 0): per camera entry
+  double* g_vec;                         // ... two vectors of 9 per camera entry (step and right-hand side)
+  double* g_S;                           // ... the Schur matrices, block b's at g_soff[b]
+  const long long* g_soff;
   const double2* c_u;
   const int* cam_chunk_ptr;
   const double* part;
@@ -169,12 +184,16 @@ __device__ __forceinline__ void blk_lpos(const V4<double>* lmrec, int j, double 
   l[2] = A.z + (bar ? gamma * B.y : 0.0);
 }
 
-// shared memory of a block solve besides the dynamic Schur matrix
+// the block's scratch: per camera (C), the step dc and right-hand side rhs (9 per camera), the
+// Schur matrix S (row stride ld); in dynamic shared memory or in global memory
+struct BlkWork {
+  BlkCam* C;
+  double *dc, *rhs, *S;
+  int ld;
+};
+
+// static shared memory of a block solve
 struct BlkSmem {
-  CamT<double> ck[BLK_MAX_CAMS], cz[BLK_MAX_CAMS], cs[BLK_MAX_CAMS], cb[BLK_MAX_CAMS];
-  double stb[BLK_MAX_CAMS][39], stk[BLK_MAX_CAMS][39];
-  double A[BLK_MAX_CAMS][45], g[BLK_MAX_CAMS][9];
-  double dc[BLK_NP], rhs[BLK_NP];
   double red[BLK_THREADS];
   double val;
   int flag;
@@ -195,35 +214,24 @@ __device__ __forceinline__ double blk_reduce(BlkSmem& sh, double v) {
 }
 
 // One LM step of block b on E^alpha(. | z), z = x̄^k (bar) or x^k, from z: the cameras' solution
-// to sh.cs, the landmarks' to lsc + BL_L (both stay at z if no step is taken).
-__device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, double xi, BlkSmem& sh, double* S) {
+// to W.C[.].cs, the landmarks' to lsc + BL_L (both stay at z if no step is taken).
+__device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, double xi, BlkSmem& sh,
+                              const BlkWork& W) {
   const int tid = threadIdx.x;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
-  const int np = 9 * nc, ld = A.ld;
+  const int np = 9 * nc, ld = W.ld;
   const int ao = bar ? LS_AB : LS_AK, bo = bar ? LS_BB : LS_BK;
-  // ---- cameras: the model of their inter pairs and proximal term, plus their intra pairs (a
-  //      thread per camera, its intra pairs in order)
-  if (tid < nc) {
-    const CamT<double>& cz = sh.cz[tid];
-    cam_lm_model(bar ? sh.stb[tid] : sh.stk[tid], cz, xi, sh.A[tid], sh.g[tid]);
-    for (int q = A.ci_ptr[cp0 + tid]; q < A.ci_ptr[cp0 + tid + 1]; ++q) {
-      double lz[3];
-      blk_lpos(A.lmrec, A.ci_lm[q], gamma, bar, lz);
-      const double2 u = A.c_u[A.ci_obs[q]];
-      double f[3], Jc[3][9], Jl[3][3];
-      blk_intra_jac(cz, lz, u.x, u.y, f, Jc, Jl);
-      double rho, w;
-      blk_rho_any(A.loss, A.L, f[0] * f[0] + f[1] * f[1] + f[2] * f[2], rho, w);
-      for (int i = 0; i < 9; ++i) {
-        sh.g[tid][i] += w * (Jc[0][i] * f[0] + Jc[1][i] * f[1] + Jc[2][i] * f[2]);
-        for (int k = 0; k <= i; ++k)
-          sh.A[tid][lt9(i, k)] += w * (Jc[0][i] * Jc[0][k] + Jc[1][i] * Jc[1][k] + Jc[2][i] * Jc[2][k]);
-      }
-    }
-    sh.cs[tid] = cz;
+  BlkCam* C = W.C;
+  double* S = W.S;
+  // ---- cameras: the model of their inter pairs and proximal term (a thread per camera)
+  for (int c = tid; c < nc; c += BLK_THREADS) {
+    BlkCam& bc = C[c];
+    cam_lm_model(bar ? bc.stb : bc.stk, bc.cz, xi, bc.A, bc.g);
+    bc.cs = bc.cz;
   }
-  // ---- landmarks: their 3 x 3 block, gradient, couplings B = w Jc^T Jl and F at z of their intra pairs
+  // ---- landmarks: their 3 x 3 block, gradient, couplings B = w Jc^T Jl and F at z of their
+  //      intra pairs, and each pair's camera-side terms (summed per camera below)
   for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
     const int j = A.lms[e];
     double* s = A.lsc + (size_t)j * BL_N;
@@ -231,30 +239,47 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
     blk_lpos(A.lmrec, j, gamma, bar, lz);
     const double* sm = A.lm_sums + (size_t)j * LS_N;
     const double a2 = 2.0 * sm[ao];
-    double C[6] = {a2 + xi, 0.0, a2 + xi, 0.0, 0.0, a2 + xi};
+    double Cm[6] = {a2 + xi, 0.0, a2 + xi, 0.0, 0.0, a2 + xi};
     double gl[3] = {2.0 * sm[bo], 2.0 * sm[bo + 1], 2.0 * sm[bo + 2]};
     double Fz = 0.0;
     for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
       const double2 u = A.c_u[A.io_obs[p]];
       double f[3], Jc[3][9], Jl[3][3];
-      blk_intra_jac(sh.cz[A.io_cam[p]], lz, u.x, u.y, f, Jc, Jl);
+      blk_intra_jac(C[A.io_cam[p]].cz, lz, u.x, u.y, f, Jc, Jl);
       double rho, w;
       blk_rho_any(A.loss, A.L, f[0] * f[0] + f[1] * f[1] + f[2] * f[2], rho, w);
       Fz += 0.5 * rho;
       int q = 0;
       for (int r1 = 0; r1 < 3; ++r1)
-        for (int c1 = 0; c1 <= r1; ++c1, ++q) C[q] += w * (Jl[0][r1] * Jl[0][c1] + Jl[1][r1] * Jl[1][c1] + Jl[2][r1] * Jl[2][c1]);
+        for (int c1 = 0; c1 <= r1; ++c1, ++q)
+          Cm[q] += w * (Jl[0][r1] * Jl[0][c1] + Jl[1][r1] * Jl[1][c1] + Jl[2][r1] * Jl[2][c1]);
       for (int r1 = 0; r1 < 3; ++r1) gl[r1] += w * (Jl[0][r1] * f[0] + Jl[1][r1] * f[1] + Jl[2][r1] * f[2]);
       double* bi = A.isc + (size_t)p * BI_N;
-      for (int i = 0; i < 9; ++i)
+      for (int i = 0; i < 9; ++i) {
         for (int k = 0; k < 3; ++k) bi[BI_B + 3 * i + k] = w * (Jc[0][i] * Jl[0][k] + Jc[1][i] * Jl[1][k] + Jc[2][i] * Jl[2][k]);
+        for (int k = 0; k <= i; ++k)
+          bi[BI_A + lt9(i, k)] = w * (Jc[0][i] * Jc[0][k] + Jc[1][i] * Jc[1][k] + Jc[2][i] * Jc[2][k]);
+        bi[BI_GC + i] = w * (Jc[0][i] * f[0] + Jc[1][i] * f[1] + Jc[2][i] * f[2]);
+      }
     }
-    for (int k = 0; k < 6; ++k) s[BL_C + k] = C[k];
+    for (int k = 0; k < 6; ++k) s[BL_C + k] = Cm[k];
     for (int k = 0; k < 3; ++k) {
       s[BL_G + k] = gl[k];
       s[BL_L + k] = lz[k];
     }
     s[BL_FZ] = Fz;
+  }
+  __syncthreads();
+  // ---- each camera's intra pairs added to its model: a thread per (camera, model entry), the
+  //      camera's pairs in order
+  for (int it = tid; it < nc * 54; it += BLK_THREADS) {
+    const int c = it / 54, en = it - 54 * c;
+    double v = 0.0;
+    for (int q = A.ci_ptr[cp0 + c]; q < A.ci_ptr[cp0 + c + 1]; ++q) v += A.isc[(size_t)A.ci_io[q] * BI_N + BI_A + en];
+    if (en < 45)
+      C[c].A[en] += v;
+    else
+      C[c].g[en - 45] += v;
   }
   __syncthreads();
   double mu = LM_MU0;
@@ -274,82 +299,107 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       }
     }
     __syncthreads();
-    // ---- Schur complement S = (A + mu diag A) - sum_j B_j C_j^-1 B_j^T (lower triangle) and its
-    //      right-hand side -g + sum_j B_j C_j^-1 g_j; a thread per entry, landmarks in order
-    for (int rc = tid; rc < np * np; rc += BLK_THREADS) {
-      const int r = rc / np, c = rc % np;
-      if (c > r) continue;
-      const int ca = r / 9, ra = r % 9, cbb = c / 9, rb = c % 9;
-      double v = ca == cbb ? sh.A[ca][lt9(ra, rb)] * (ra == rb ? 1.0 + mu : 1.0) : 0.0;
-      for (int e = l0; e < l1; ++e) {
-        int pa = -1, pb = -1;
-        for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
-          if (A.io_cam[p] == ca) pa = p;
-          if (A.io_cam[p] == cbb) pb = p;
-        }
-        if (pa < 0 || pb < 0) continue;
-        const double* x = A.isc + (size_t)pa * BI_N + BI_BC + 3 * ra;
-        const double* y = A.isc + (size_t)pb * BI_N + BI_B + 3 * rb;
-        v -= x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
-      }
-      S[r * ld + c] = v;
-    }
-    for (int r = tid; r < np; r += BLK_THREADS) {
-      const int ca = r / 9, ra = r % 9;
-      double v = -sh.g[ca][ra];
-      for (int e = l0; e < l1; ++e) {
-        const double* gl = A.lsc + (size_t)A.lms[e] * BL_N + BL_G;
-        for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p)
-          if (A.io_cam[p] == ca) {
-            const double* x = A.isc + (size_t)p * BI_N + BI_BC + 3 * ra;
-            v += x[0] * gl[0] + x[1] * gl[1] + x[2] * gl[2];
+    // ---- Schur complement S = (A + mu diag A) - sum_j B_j C_j^-1 B_j^T (lower triangle): a
+    //      thread per camera pair (a >= b) and row of camera a, over camera a's intra pairs in
+    //      order; the landmark's pair with camera b is looked up in its list (ascending cameras)
+    const int n_item = nc * (nc + 1) / 2 * 9;
+    for (int it = tid; it < n_item; it += BLK_THREADS) {
+      const int pi = it / 9, ra = it - 9 * pi;
+      int ca = (int)((sqrt(8.0 * pi + 1.0) - 1.0) * 0.5);
+      while ((ca + 1) * (ca + 2) / 2 <= pi) ++ca;
+      while (ca * (ca + 1) / 2 > pi) --ca;
+      const int cbb = pi - ca * (ca + 1) / 2;
+      const int nrb = ca == cbb ? ra + 1 : 9;
+      double v[9];
+#pragma unroll
+      for (int rb = 0; rb < 9; ++rb) v[rb] = (ca == cbb && rb <= ra) ? C[ca].A[lt9(ra, rb)] * (ra == rb ? 1.0 + mu : 1.0) : 0.0;
+      for (int q = A.ci_ptr[cp0 + ca]; q < A.ci_ptr[cp0 + ca + 1]; ++q) {
+        int pb = -1;
+        if (ca == cbb) {
+          pb = A.ci_io[q];
+        } else {
+          const int e = A.ci_e[q];
+          for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
+            const int c = A.io_cam[p];
+            if (c >= cbb) {
+              if (c == cbb) pb = p;
+              break;
+            }
           }
+        }
+        if (pb < 0) continue;
+        const double* x = A.isc + (size_t)A.ci_io[q] * BI_N + BI_BC + 3 * ra;
+        const double x0 = x[0], x1 = x[1], x2 = x[2];
+        const double* y = A.isc + (size_t)pb * BI_N + BI_B;
+#pragma unroll
+        for (int rb = 0; rb < 9; ++rb)
+          if (rb < nrb) v[rb] -= x0 * y[3 * rb] + x1 * y[3 * rb + 1] + x2 * y[3 * rb + 2];
       }
-      sh.rhs[r] = v;
+      double* Sr = S + (size_t)(9 * ca + ra) * ld + 9 * cbb;
+#pragma unroll
+      for (int rb = 0; rb < 9; ++rb)
+        if (rb < nrb) Sr[rb] = v[rb];
+    }
+    // ... and its right-hand side -g + sum_j B_j C_j^-1 g_j (a thread per row, camera a's intra pairs in order)
+    for (int r = tid; r < np; r += BLK_THREADS) {
+      const int ca = r / 9, ra = r - 9 * ca;
+      double v = -C[ca].g[ra];
+      for (int q = A.ci_ptr[cp0 + ca]; q < A.ci_ptr[cp0 + ca + 1]; ++q) {
+        const double* gl = A.lsc + (size_t)A.ci_lm[q] * BL_N + BL_G;
+        const double* x = A.isc + (size_t)A.ci_io[q] * BI_N + BI_BC + 3 * ra;
+        v += x[0] * gl[0] + x[1] * gl[1] + x[2] * gl[2];
+      }
+      W.rhs[r] = v;
     }
     if (tid == 0) sh.flag = 1;
     __syncthreads();
-    // ---- Cholesky of S in place (column by column), then the two triangular solves
+    // ---- Cholesky of S in place (column by column; the trailing update a warp per row, its
+    //      lanes along the row), then the two triangular solves (column-oriented)
+    const int warp = tid >> 5, lane = tid & 31;
     for (int k = 0; k < np; ++k) {
       if (tid == 0) {
-        const double d = S[k * ld + k];
+        const double d = S[(size_t)k * ld + k];
         if (!(d > 0.0)) sh.flag = 0;
-        S[k * ld + k] = sqrt(d > 0.0 ? d : 1.0);
+        S[(size_t)k * ld + k] = sqrt(d > 0.0 ? d : 1.0);
       }
       __syncthreads();
-      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) S[i * ld + k] /= S[k * ld + k];
+      const double dk = S[(size_t)k * ld + k];
+      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) S[(size_t)i * ld + k] /= dk;
       __syncthreads();
-      const int m = np - k - 1;
-      for (int q = tid; q < m * m; q += BLK_THREADS) {
-        const int i = k + 1 + q / m, jj = k + 1 + q % m;
-        if (jj <= i) S[i * ld + jj] -= S[i * ld + k] * S[jj * ld + k];
+      for (int i = k + 1 + warp; i < np; i += BLK_THREADS / 32) {
+        double* Si = S + (size_t)i * ld;
+        const double lik = Si[k];
+        for (int jj = k + 1 + lane; jj <= i; jj += 32) Si[jj] -= lik * S[(size_t)jj * ld + k];
       }
       __syncthreads();
     }
-    if (tid == 0 && sh.flag) {
-      double y[BLK_NP];
-      for (int i = 0; i < np; ++i) {
-        double v = sh.rhs[i];
-        for (int k = 0; k < i; ++k) v -= S[i * ld + k] * y[k];
-        y[i] = v / S[i * ld + i];
-      }
-      for (int i = np - 1; i >= 0; --i) {
-        double v = y[i];
-        for (int k = i + 1; k < np; ++k) v -= S[k * ld + i] * sh.dc[k];
-        sh.dc[i] = v / S[i * ld + i];
-      }
-    }
-    __syncthreads();
     if (!sh.flag) continue;
+    // L y = rhs (y to dc), then L^T x = y (x to rhs), then x to dc
+    for (int k = 0; k < np; ++k) {
+      const double yk = W.rhs[k] / S[(size_t)k * ld + k];
+      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) W.rhs[i] -= S[(size_t)i * ld + k] * yk;
+      if (tid == 0) W.dc[k] = yk;
+      __syncthreads();
+    }
+    for (int i = np - 1; i >= 0; --i) {
+      const double xv = W.dc[i] / S[(size_t)i * ld + i];
+      const double* Si = S + (size_t)i * ld;
+      for (int k = tid; k < i; k += BLK_THREADS) W.dc[k] -= Si[k] * xv;
+      if (tid == 0) W.rhs[i] = xv;
+      __syncthreads();
+    }
+    for (int r = tid; r < np; r += BLK_THREADS) W.dc[r] = W.rhs[r];
+    __syncthreads();
     // ---- the candidate: cameras (a thread each), landmarks by back substitution, and the
     //      decrease of E^alpha(. | z) term by term
     double part = 0.0;
-    CamT<double> cc;
-    if (tid < nc) {
-      const CamT<double>& cz = sh.cz[tid];
-      const double* th = sh.dc + 9 * tid;
+    for (int c = tid; c < nc; c += BLK_THREADS) {
+      BlkCam& bc = C[c];
+      const CamT<double>& cz = bc.cz;
+      const double* th = W.dc + 9 * c;
       double Ex[9];
       rodrigues(th, Ex);
+      CamT<double> cc;
       for (int r = 0; r < 3; ++r)
         for (int k = 0; k < 3; ++k)
           cc.R[r * 3 + k] = cz.R[r * 3 + 0] * Ex[0 * 3 + k] + cz.R[r * 3 + 1] * Ex[1 * 3 + k] + cz.R[r * 3 + 2] * Ex[2 * 3 + k];
@@ -357,8 +407,8 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         cc.t[k] = cz.t[k] + th[3 + k];
         cc.d[k] = cz.d[k] + th[6 + k];
       }
-      part += cam_phi(bar ? sh.stb[tid] : sh.stk[tid], cz, cc, xi);   // inter pairs' P and the proximal term
-      sh.cb[tid] = cc;   // candidate (sh.cs keeps the accepted solution)
+      part += cam_phi(bar ? bc.stb : bc.stk, cz, cc, xi);   // inter pairs' P and the proximal term
+      bc.cb = cc;   // candidate (cs keeps the accepted solution)
     }
     __syncthreads();
     for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
@@ -367,7 +417,7 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
       for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
         const double* bi = A.isc + (size_t)p * BI_N + BI_B;
-        const double* th = sh.dc + 9 * A.io_cam[p];
+        const double* th = W.dc + 9 * A.io_cam[p];
         for (int k = 0; k < 3; ++k)
           for (int i = 0; i < 9; ++i) rr[k] += bi[3 * i + k] * th[i];
       }
@@ -382,7 +432,7 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       double Fc = 0.0;
       for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
         const double2 u = A.c_u[A.io_obs[p]];
-        Fc += blk_F(sh.cb[A.io_cam[p]], lc, u.x, u.y, A.L, A.loss);
+        Fc += blk_F(C[A.io_cam[p]].cb, lc, u.x, u.y, A.L, A.loss);
       }
       part += Fc - s[BL_FZ];
     }
@@ -393,7 +443,7 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
         for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
           const double* bi = A.isc + (size_t)p * BI_N + BI_B;
-          const double* th = sh.dc + 9 * A.io_cam[p];
+          const double* th = W.dc + 9 * A.io_cam[p];
           for (int k = 0; k < 3; ++k)
             for (int i = 0; i < 9; ++i) rr[k] += bi[3 * i + k] * th[i];
         }
@@ -403,7 +453,7 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         s[BL_L + 1] -= dl[1];
         s[BL_L + 2] -= dl[2];
       }
-      if (tid < nc) sh.cs[tid] = sh.cb[tid];
+      for (int c = tid; c < nc; c += BLK_THREADS) C[c].cs = C[c].cb;
       __syncthreads();
       return;
     }
@@ -411,13 +461,14 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
   __syncthreads();
 }
 
-// E^alpha(x | x^k) - E^alpha(x^k | x^k) of block b for the solution in sh.cs and lsc + BL_L
-__device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& sh) {
+// E^alpha(x | x^k) - E^alpha(x^k | x^k) of block b for the solution in C[.].cs and lsc + BL_L
+__device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& sh, const BlkWork& W) {
   const int tid = threadIdx.x;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
+  const BlkCam* C = W.C;
   double part = 0.0;
-  if (tid < nc) part += cam_phi(sh.stk[tid], sh.ck[tid], sh.cs[tid], xi);
+  for (int c = tid; c < nc; c += BLK_THREADS) part += cam_phi(C[c].stk, C[c].ck, C[c].cs, xi);
   for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
     const int j = A.lms[e];
     const double* s = A.lsc + (size_t)j * BL_N;
@@ -430,14 +481,14 @@ __device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& s
     for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
       const double2 u = A.c_u[A.io_obs[p]];
       const int c = A.io_cam[p];
-      part += blk_F(sh.cs[c], s + BL_L, u.x, u.y, A.L, A.loss) - blk_F(sh.ck[c], lk, u.x, u.y, A.L, A.loss);
+      part += blk_F(C[c].cs, s + BL_L, u.x, u.y, A.L, A.loss) - blk_F(C[c].ck, lk, u.x, u.y, A.L, A.loss);
     }
   }
   return blk_reduce(sh, part);
 }
 
 __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams P) {
-  extern __shared__ __align__(16) double blk_S[];   // the Schur matrix, ld x ld
+  extern __shared__ __align__(16) double blk_dyn[];   // the block scratch (ld > 0)
   __shared__ BlkSmem sh;
   const int b = blockIdx.x;
   const int tid = threadIdx.x;
@@ -445,10 +496,27 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
   const double gamma = P.gam[it], xi = P.xi;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
+  BlkWork W;
+  if (A.ld > 0) {   // shared memory: per camera scratch of the most cameras, dc, rhs, then S
+    const int mc = A.ld / 9;
+    W.C = reinterpret_cast<BlkCam*>(blk_dyn);
+    W.dc = blk_dyn + (size_t)mc * (sizeof(BlkCam) / 8);
+    W.rhs = W.dc + A.ld;
+    W.S = W.rhs + A.ld;
+    W.ld = A.ld;
+  } else {   // global memory at the block's camera entries and Schur offset
+    W.C = A.g_cam + cp0;
+    W.dc = A.g_vec + (size_t)18 * cp0;
+    W.rhs = W.dc + 9 * nc;
+    W.S = A.g_S + A.g_soff[b];
+    W.ld = 9 * nc;
+  }
+  BlkCam* C = W.C;
   // ---- cameras: x^k, x̄^k, statistics, F sums, displacement (a thread each)
   double part_disp = 0.0, part_Fall = 0.0, part_Fin = 0.0, part_G = 0.0;
-  if (tid < nc) {
-    const int cam = A.cams[cp0 + tid];
+  for (int c = tid; c < nc; c += BLK_THREADS) {
+    const int cam = A.cams[cp0 + c];
+    double pF = 0.0;
     const double* x = A.cam_x + (size_t)cam * CSTRIDE;
     const double* dx = A.cam_dx + (size_t)cam * CSTRIDE;
     CamT<double> ck, cb;
@@ -464,17 +532,18 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
       cb.d[a] = ck.d[a] + gamma * dx[CS_D + a];
       part_disp += dx[CS_T + a] * dx[CS_T + a] + dx[CS_D + a] * dx[CS_D + a];
     }
-    sh.ck[tid] = ck;
-    sh.cz[tid] = cb;   // the accelerated step's conditioning iterate, first
+    C[c].ck = ck;
+    C[c].cz = cb;   // the accelerated step's conditioning iterate, first
     const int c0 = A.cam_chunk_ptr[cam], c1 = A.cam_chunk_ptr[cam + 1];
-    sum_stats<double, double>(A.part, c0, c1, PART_XB, sh.stb[tid]);
-    sum_stats<double, double>(A.part, c0, c1, PART_XK, sh.stk[tid]);
-    for (int c = c0; c < c1; ++c) {
-      part_Fall += A.part[(size_t)c * CP_STRIDE + PART_F];
-      part_G += A.part[(size_t)c * CP_STRIDE + PART_G];
-      part_Fin += A.part[(size_t)c * CP_STRIDE + PART_FI];
+    sum_stats<double, double>(A.part, c0, c1, PART_XB, C[c].stb);
+    sum_stats<double, double>(A.part, c0, c1, PART_XK, C[c].stk);
+    for (int q = c0; q < c1; ++q) {
+      pF += A.part[(size_t)q * CP_STRIDE + PART_F];
+      part_G += A.part[(size_t)q * CP_STRIDE + PART_G];
+      part_Fin += A.part[(size_t)q * CP_STRIDE + PART_FI];
     }
-    A.cam_Fsum[cam] = part_Fall;   // F_ij(x^k) of the camera's observations (objective trace)
+    part_Fall += pF;
+    A.cam_Fsum[cam] = pF;   // F_ij(x^k) of the camera's observations (objective trace)
   }
   // ---- landmarks: displacement, gaps and inter F sums
   double part_dl = 0.0, part_Gl = 0.0, part_Fl = 0.0;
@@ -500,15 +569,15 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
   bool rs = true;
   double Enext = 0.0;
   if (P.accelerated) {
-    blk_lm(A, b, true, gamma, xi, sh, blk_S);
-    Enext = F + blk_dE_k(A, b, xi, sh);
+    blk_lm(A, b, true, gamma, xi, sh, W);
+    Enext = F + blk_dE_k(A, b, xi, sh, W);
     rs = Enext > Fbar;
   }
   if (rs) {
-    if (tid < nc) sh.cz[tid] = sh.ck[tid];
+    for (int c = tid; c < nc; c += BLK_THREADS) C[c].cz = C[c].ck;
     __syncthreads();
-    blk_lm(A, b, false, gamma, xi, sh, blk_S);
-    Enext = F + blk_dE_k(A, b, xi, sh);
+    blk_lm(A, b, false, gamma, xi, sh, W);
+    Enext = F + blk_dE_k(A, b, xi, sh, W);
   }
   // ---- new state
   for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
@@ -533,13 +602,13 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
     A.blk_F[b] = F;
     A.blk_rs[b] = (rs && P.accelerated) ? 1 : 0;
   }
-  if (tid < nc) {
-    const int cam = A.cams[cp0 + tid];
-    const CamT<double>& cs = sh.cs[tid];
-    const CamT<double>& ck = sh.ck[tid];
+  for (int c = tid; c < nc; c += BLK_THREADS) {
+    const int cam = A.cams[cp0 + c];
+    const CamT<double>& cs = C[c].cs;
+    const CamT<double>& ck = C[c].ck;
     double* x = A.cam_x + (size_t)cam * CSTRIDE;
     double* dx = A.cam_dx + (size_t)cam * CSTRIDE;
-    A.cam_rs[cam] = (tid == 0 && rs && P.accelerated) ? 1 : 0;   // the block's restart, counted once
+    A.cam_rs[cam] = (c == 0 && rs && P.accelerated) ? 1 : 0;   // the block's restart, counted once
     CamT<double> ndx;
     for (int a = 0; a < 9; ++a) {
       ndx.R[a] = cs.R[a] - ck.R[a];

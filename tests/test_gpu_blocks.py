@@ -1,5 +1,6 @@
-"""Coarse blocks on the GPU (daba_set_partition: contiguous groups of one to eight cameras and
-the landmarks they see first, Eq. Ealpha with the intra-block pairs exact, one successful LM step
+"""Coarse blocks on the GPU (daba_set_partition: contiguous groups of one to BLK_MAX_CAMS cameras
+and the landmarks they see first; the block scratch in shared memory up to 16 cameras per block,
+in global memory above, Eq. Ealpha with the intra-block pairs exact, one successful LM step
 per block) against the oracle of Algorithm 1 with the same blocks (oracle/daba_blocks.py), per
 iteration: the objective trace, the per-block restart metrics F^alpha and Fbar^alpha, the restart
 decisions and the iterate."""
@@ -49,7 +50,10 @@ def _scene(name):
     # per iteration, so the trajectory is compared for 12 iterations and the iterate not at all
     # (test_multi_camera_blocks_step_from_common_state compares every step from the GPU's state)
     ("circle", True, 12, 4), ("circle", True, 12, 8), ("circle_small", False, 12, 3), ("circle_small", True, 12, 6),
-    ("street", True, 8, 25), ("tourism", True, 12, 8), ("tourism", True, 12, 32)])
+    ("street", True, 8, 25), ("tourism", True, 12, 8), ("tourism", True, 12, 32),
+    # blocks of 10 and 15 cameras (shared-memory scratch), 20 and 25 (global scratch); the
+    # oracle takes seconds per iteration on the larger ones
+    ("circle", True, 12, 2), ("tourism", True, 4, 4), ("circle", True, 12, 1), ("street", True, 4, 2)])
 def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     from paper_2305_07026_b300 import _lib as L
     sc = _scene(name)
@@ -90,9 +94,11 @@ def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     g.close()
 
 
-@pytest.mark.parametrize("name,n_blocks", [("circle", 4), ("circle", 8), ("tourism", 8), ("tourism", 32)])
-def test_multi_camera_blocks_step_from_common_state(name, n_blocks):
-    """Every one of 20 iterations from the same state: before each GPU iteration the oracle takes
+@pytest.mark.parametrize("name,n_blocks,iters", [("circle", 4, 20), ("circle", 8, 20), ("tourism", 8, 20),
+                                                 ("tourism", 32, 20), ("circle", 2, 20), ("circle", 1, 20),
+                                                 ("street", 2, 4), ("tourism", 1, 3)])
+def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters):
+    """Every one of `iters` iterations (blocks of up to 60 cameras) from the same state: before each GPU iteration the oracle takes
     the GPU's x^k and x^(k-1) (through the boundary) and its Fbar^alpha(k-1); the oracle's Nesterov
     scalar and E^alpha carry over from its own previous step. Compared after the step: the block
     metrics F^alpha(k), Fbar^alpha(k) (which hold the previous step's E^alpha(x^k | x^(k-1))), the
@@ -111,7 +117,7 @@ def test_multi_camera_blocks_step_from_common_state(name, n_blocks):
     g.set_state(sc.cams, sc.lms)
     prev = g.get_state()
     worst = {"F_blk": 0.0, "cams": 0.0, "lms": 0.0}
-    for k in range(20):
+    for k in range(iters):
         if k > 0:   # the oracle continues from the GPU's state
             cur = g.get_state()
             Rk, tk, dk, lk = O.to_internal(*cur, prob.s_norm)
@@ -188,11 +194,15 @@ def test_blocks_arguments():
         m.set_partition(part.cam_block, part.lm_block)
     assert e.value.status == L.DABA_ERR_ARG
     m.close()
+    from paper_2305_07026_b300 import scenes
+    big = scenes.circle_scene(n_cams=L.BLK_MAX_CAMS + 2, n_lms=400, cap=4)
+    with L.Daba(big.M, big.N, big.nnz, prec="fp64") as d:
+        d.set_observations(big.cam_idx, big.lm_idx, big.uv)
+        with pytest.raises(L.DabaError) as e:   # all cameras in one block: more than BLK_MAX_CAMS
+            d.set_partition(np.zeros(big.M, np.int32), np.zeros(big.N, np.int32), 1)
+        assert e.value.status == L.DABA_ERR_ARG
     d = L.Daba(sc.M, sc.N, sc.nnz, prec="fp64")
     d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
-    with pytest.raises(L.DabaError) as e:   # all cameras in one block: more than BLK_MAX_CAMS
-        d.set_partition(np.zeros(sc.M, np.int32), part.lm_block)
-    assert e.value.status == L.DABA_ERR_ARG
     bad = part.lm_block.copy()
     bad[3] = sc.M
     with pytest.raises(L.DabaError) as e:   # a landmark's block out of range
@@ -223,7 +233,9 @@ def test_blocks_without_cameras_and_regrown_partition():
     lm_only = one.lm_block.copy()
     lm_only[::3] = sc.M + (np.arange(sc.N)[::3] % 4)   # a third of the landmarks in four camera-less blocks
     parts = [B.Partition(one.cam_block, lm_only, sc.M + 6),   # the last two blocks hold nothing
-             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 3)]
+             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 3),
+             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 1),   # global-memory scratch
+             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 2)]   # and back to shared memory
     for part in parts:
         g.set_partition(part.cam_block, part.lm_block, part.S)
         g.set_state(sc.cams, sc.lms)

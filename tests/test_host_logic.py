@@ -92,10 +92,12 @@ def test_camera_group_partition_helper():
     from oracle import daba_blocks as B
     from paper_2305_07026_b300 import partition, scenes
     sc = scenes.circle_scene(n_lms=300)
-    for n in (3, 4, 20):
+    for n in (1, 2, 3, 4, 20):
         cb, lb = partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n)
         ref = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n)
         np.testing.assert_array_equal(cb, ref.cam_block)
         np.testing.assert_array_equal(lb, ref.lm_block)
+    big = scenes.circle_scene(n_cams=260, n_lms=300, cap=4)
+    partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 3)   # 87 cameras per block
     with pytest.raises(ValueError):
-        partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 2)   # 10 cameras per block
+        partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 2)   # 130 cameras per block
