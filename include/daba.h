@@ -269,18 +269,28 @@ daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
  * w = rho'(|e|^2) at z, the proximal term to second order); damping 1e-3 x diag, raised tenfold
  * up to 8 times; taken only if E^alpha(. | z) decreases. The damped system is solved through the
  * Schur complement of the block's cameras (9 per camera; every landmark's 3 x 3 block
- * eliminated), one CTA per block, with a dense Cholesky factorisation: up to 16 cameras per block
- * in shared memory, above that in global memory (a cost of about (9 n_c)^3 / 3 FP64 multiply-adds
- * per damping trial on one SM). The restart metrics of Eqs. DEalpha-Eak are per block
+ * eliminated), with a dense Cholesky factorisation, by one CTA per block (scratch in shared memory
+ * up to 16 cameras, in global memory above) or by a thread-block cluster per block over global
+ * scratch (daba_set_block_ctas; about (9 n_c)^3 / 3 FP64 multiply-adds per damping trial). The restart metrics of Eqs. DEalpha-Eak are per block
  * (daba_get_partition_metrics); the restart count of daba_run counts the blocks that hold a
  * camera. A camera may observe each landmark of its block at most once (DABA_ERR_ARG otherwise,
  * as for a block id out of range or a block of more than 128 cameras). Call after
  * daba_set_observations (which clears the partition); n_blocks = 0 returns to one block per
  * camera and per landmark (the arrays are then ignored). The device scratch grows with the
- * partition: 888 bytes per intra pair, 248 per landmark, and with blocks of more than 16 cameras
- * 1680 bytes per camera plus (9 n_c)^2 x 8 bytes per block. Checkpoints and the unrolled gradient
+ * partition: 888 bytes per intra pair, 248 per landmark, and with global scratch 1752 bytes per
+ * camera plus (9 n_c)^2 x 8 bytes per block. Checkpoints and the unrolled gradient
  * are not available while a partition is set. */
 daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* cam_block, const int32_t* lm_block);
+
+/* How the next daba_set_partition spreads a block over CTAs (Algorithm 1 with coarse blocks, its
+ * results the same up to the rounding order of the block's sums): 0 (default) automatic: one CTA
+ * per block, its scratch in shared memory, when every block has at most 16 cameras and there are
+ * more than n_SM / 2 blocks, else a thread-block cluster of up to 16 CTAs per block (as many as
+ * keep the grid within two CTAs per SM) over global scratch; 1: one CTA per block (shared
+ * scratch up to 16 cameras, global above); 2..16: a cluster of at most that many CTAs per block
+ * over global scratch (the largest of 16, 8, 4, 2 not above it that the device can place).
+ * DABA_ERR_ARG outside 0..16. Takes effect at the next daba_set_partition. */
+daba_status daba_set_block_ctas(daba_ctx* ctx, int32_t ctas);
 
 /* Per-block metrics of the last iteration with a partition (each pointer may be NULL, n_blocks
  * entries, host or device): F^alpha(k) (Eq. Fak) and Fbar^alpha(k) (Eq. lFak) in pixel^2 and the

@@ -68,6 +68,7 @@ _SIGS = {
     "daba_set_pipeline": (_st, [_p, ctypes.POINTER(daba_pipeline)]),
     "daba_set_partition": (_st, [_p, _i32, _p, _p]),
     "daba_get_partition_metrics": (_st, [_p, _p, _p, _p, _p]),
+    "daba_set_block_ctas": (_st, [_p, _i32]),
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
@@ -275,6 +276,11 @@ class Daba:
             n_blocks = int(max(cb.max(initial=-1), lb.max(initial=-1))) + 1
         self._check(daba_set_partition(self._h, int(n_blocks), ptr(cb), ptr(lb)))
         self.n_blocks = int(n_blocks)
+
+    def set_block_ctas(self, ctas=0):
+        """CTAs per coarse block at the next set_partition: 0 automatic, 1 one CTA per block,
+        2..16 a thread-block cluster of at most that many."""
+        self._check(daba_set_block_ctas(self._h, int(ctas)))
 
     def get_partition_metrics(self, stream=None):
         F, Fb, rs = np.zeros(self.n_blocks), np.zeros(self.n_blocks), np.zeros(self.n_blocks, np.uint8)

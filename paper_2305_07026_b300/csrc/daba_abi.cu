@@ -131,6 +131,8 @@ struct daba_ctx {
   int n_blocks = 0;
   int blk_ld = 0;        // 9 x the most cameras in one block with the scratch in shared memory, else 0
   size_t blk_smem = 0;   // dynamic shared memory of the block solve
+  int blk_cs = 1;        // CTAs per block (a thread-block cluster when above 1; global scratch only)
+  int blk_pref = 0;      // daba_set_block_ctas: 0 automatic, 1 one CTA per block, 2..16 a cluster
   void *blk_ci_e = nullptr, *blk_ci_io = nullptr, *blk_gcam = nullptr, *blk_gvec = nullptr, *blk_gS = nullptr,
        *blk_soff = nullptr;
   void *c_intra = nullptr, *blk_cam_ptr = nullptr, *blk_cams = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr,
@@ -545,7 +547,23 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   A.pack_next = (V4<double>*)pack_at(ctx, k + 1);
   A.L = L;
   A.loss = LOSS;
-  k_blk_solve<<<ctx->n_blocks, BLK_THREADS, ctx->blk_smem, st>>>(A, P);
+  if (ctx->blk_cs > 1) {   // a cluster of blk_cs CTAs per block
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->n_blocks * ctx->blk_cs));
+    cfg.blockDim = dim3(BLK_THREADS);
+    cfg.dynamicSmemBytes = ctx->blk_smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)ctx->blk_cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_blk_solve, A, P)) != cudaSuccess) return e;
+  } else {
+    k_blk_solve<<<ctx->n_blocks, BLK_THREADS, ctx->blk_smem, st>>>(A, P);
+  }
   ctx->launches++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return launch_finalize(ctx, st);
@@ -2593,19 +2611,48 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   // the block scratch: in shared memory when every block has at most BLK_SMEM_CAMS cameras (per
   // camera scratch, two vectors and the Schur matrix of the largest block), else in global memory
   // (per camera entry, and each block's Schur matrix of stride 9 x its cameras)
-  const bool in_smem = most <= BLK_SMEM_CAMS;
+  // automatic: one CTA per block with shared scratch when the blocks are small and one CTA per
+  // block already gives every SM at least half a CTA; otherwise clusters over the global scratch
+  const int pref = ctx->blk_pref;
+  const bool in_smem = most <= BLK_SMEM_CAMS && (pref == 1 || (pref == 0 && (int64_t)S * 4 > 2LL * ctx->n_sm));
   const int ld = 9 * most;
-  const size_t smem = in_smem ? (size_t)most * sizeof(BlkCam) + (size_t)(2 * ld + ld * ld) * 8 : 0;
+  const size_t smem = in_smem ? (size_t)most * sizeof(BlkCam) + (size_t)(3 * ld + ld * ld) * 8 : 0;
   std::vector<long long> soff(S + 1, 0);
   for (int b = 0; b < S; ++b) {
     const long long nb = 9LL * (cam_ptr[b + 1] - cam_ptr[b]);
     soff[b + 1] = soff[b] + (in_smem ? 0 : nb * nb);
   }
   CK(cudaFuncSetAttribute(k_blk_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // global scratch: a cluster of CTAs per block, the largest of 16, 8, 4, 2 that the device can
+  // place and that keeps the grid within two CTAs per SM (else one CTA per block)
+  int csz = 1;
+  if (!in_smem && pref != 1) {
+    CK(cudaFuncSetAttribute(k_blk_solve, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int c : {16, 8, 4, 2}) {
+      if (pref > 1 ? c > pref : (int64_t)S * c > 2LL * ctx->n_sm) continue;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(S * c));
+      cfg.blockDim = dim3(BLK_THREADS);
+      cfg.dynamicSmemBytes = 0;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)c;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n_cl = 0;
+      if (cudaOccupancyMaxActiveClusters(&n_cl, k_blk_solve, &cfg) == cudaSuccess && n_cl > 0) {
+        csz = c;
+        break;
+      }
+      cudaGetLastError();   // not sticky
+    }
+  }
   const size_t ni = (size_t)n_in;
   if (!in_smem) {
     if ((s = dgrow(ctx, &ctx->blk_gcam, (size_t)M * sizeof(BlkCam))) != DABA_OK) return s;
-    if ((s = dgrow(ctx, &ctx->blk_gvec, (size_t)M * 18 * 8)) != DABA_OK) return s;
+    if ((s = dgrow(ctx, &ctx->blk_gvec, (size_t)M * 27 * 8)) != DABA_OK) return s;
     if ((s = dgrow(ctx, &ctx->blk_gS, (size_t)std::max(soff[S], 1LL) * 8)) != DABA_OK) return s;
   }
   if ((s = dgrow(ctx, &ctx->blk_soff, (size_t)(S + 1) * 8)) != DABA_OK) return s;
@@ -2650,7 +2697,15 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   ctx->n_blocks = S;
   ctx->blk_ld = in_smem ? ld : 0;
   ctx->blk_smem = smem;
+  ctx->blk_cs = csz;
   drop_graphs(ctx);
+  return DABA_OK;
+}
+
+daba_status daba_set_block_ctas(daba_ctx* ctx, int32_t ctas) {
+  if (!ctx) return DABA_ERR_ARG;
+  if (ctas < 0 || ctas > 16) return fail(ctx, DABA_ERR_ARG, "ctas must lie in 0 .. 16");
+  ctx->blk_pref = ctas;
   return DABA_OK;
 }
 

@@ -21,6 +21,8 @@
 // Every sum runs in a fixed order, so results do not depend on the schedule.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "daba_kernels.cuh"
 
 namespace daba {
@@ -184,23 +186,35 @@ __device__ __forceinline__ void blk_lpos(const V4<double>* lmrec, int j, double 
   l[2] = A.z + (bar ? gamma * B.y : 0.0);
 }
 
-// the block's scratch: per camera (C), the step dc and right-hand side rhs (9 per camera), the
-// Schur matrix S (row stride ld); in dynamic shared memory or in global memory
+// the block's scratch: per camera (C), the step dc, right-hand side rhs and the Cholesky
+// diagonal diag (9 per camera), the Schur matrix S (row stride ld); in dynamic shared memory or
+// in global memory. A block is solved by one CTA or by a cluster of `cs` CTAs (global scratch):
+// rank, thread index in the cluster gt, threads in the cluster GT.
 struct BlkWork {
   BlkCam* C;
-  double *dc, *rhs, *S;
+  double *dc, *rhs, *diag, *S;
   int ld;
+  int rank, cs, gt, GT;
 };
 
 // static shared memory of a block solve
 struct BlkSmem {
   double red[BLK_THREADS];
   double val;
-  int flag;
 };
 
-// sum over the CTA in thread order (thread 0 adds the 128 partials), the result on every thread
-__device__ __forceinline__ double blk_reduce(BlkSmem& sh, double v) {
+// a barrier of the CTA, or of the cluster (release and acquire at cluster scope: the global
+// scratch written before it is seen after it by every CTA of the block)
+__device__ __forceinline__ void blk_sync(const BlkWork& W) {
+  if (W.cs > 1)
+    cooperative_groups::this_cluster().sync();
+  else
+    __syncthreads();
+}
+
+// sum over the block's threads: each CTA in thread order (thread 0 adds the 128 partials), then
+// the CTAs' sums in rank order (read from each CTA's shared memory); the result on every thread
+__device__ __forceinline__ double blk_reduce(BlkSmem& sh, const BlkWork& W, double v) {
   __syncthreads();
   sh.red[threadIdx.x] = v;
   __syncthreads();
@@ -209,15 +223,23 @@ __device__ __forceinline__ double blk_reduce(BlkSmem& sh, double v) {
     for (int k = 0; k < BLK_THREADS; ++k) t += sh.red[k];
     sh.val = t;
   }
-  __syncthreads();
-  return sh.val;
+  if (W.cs == 1) {
+    __syncthreads();
+    return 0.0 + sh.val;
+  }
+  auto cl = cooperative_groups::this_cluster();
+  cl.sync();
+  double t = 0.0;
+  for (int r = 0; r < W.cs; ++r) t += *cl.map_shared_rank(&sh.val, r);
+  cl.sync();   // every CTA has read the sums before the next reduction writes them
+  return t;
 }
 
 // One LM step of block b on E^alpha(. | z), z = x̄^k (bar) or x^k, from z: the cameras' solution
 // to W.C[.].cs, the landmarks' to lsc + BL_L (both stay at z if no step is taken).
 __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, double xi, BlkSmem& sh,
                               const BlkWork& W) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, gt = W.gt, GT = W.GT;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
   const int np = 9 * nc, ld = W.ld;
@@ -225,14 +247,14 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
   BlkCam* C = W.C;
   double* S = W.S;
   // ---- cameras: the model of their inter pairs and proximal term (a thread per camera)
-  for (int c = tid; c < nc; c += BLK_THREADS) {
+  for (int c = gt; c < nc; c += GT) {
     BlkCam& bc = C[c];
     cam_lm_model(bar ? bc.stb : bc.stk, bc.cz, xi, bc.A, bc.g);
     bc.cs = bc.cz;
   }
   // ---- landmarks: their 3 x 3 block, gradient, couplings B = w Jc^T Jl and F at z of their
   //      intra pairs, and each pair's camera-side terms (summed per camera below)
-  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+  for (int e = l0 + gt; e < l1; e += GT) {
     const int j = A.lms[e];
     double* s = A.lsc + (size_t)j * BL_N;
     double lz[3];
@@ -269,10 +291,10 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
     }
     s[BL_FZ] = Fz;
   }
-  __syncthreads();
+  blk_sync(W);
   // ---- each camera's intra pairs added to its model: a thread per (camera, model entry), the
   //      camera's pairs in order
-  for (int it = tid; it < nc * 54; it += BLK_THREADS) {
+  for (int it = gt; it < nc * 54; it += GT) {
     const int c = it / 54, en = it - 54 * c;
     double v = 0.0;
     for (int q = A.ci_ptr[cp0 + c]; q < A.ci_ptr[cp0 + c + 1]; ++q) v += A.isc[(size_t)A.ci_io[q] * BI_N + BI_A + en];
@@ -281,11 +303,11 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
     else
       C[c].g[en - 45] += v;
   }
-  __syncthreads();
+  blk_sync(W);
   double mu = LM_MU0;
   for (int tr = 0; tr < LM_TRIES; ++tr, mu *= 10.0) {
     // ---- damped landmark blocks: C^-1 and B C^-1 of every intra pair
-    for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    for (int e = l0 + gt; e < l1; e += GT) {
       double* s = A.lsc + (size_t)A.lms[e] * BL_N;
       double Cm[6];
       for (int k = 0; k < 6; ++k) Cm[k] = s[BL_C + k];
@@ -298,12 +320,12 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         for (int i = 0; i < 9; ++i) sym3_mul(s + BL_CI, bi + BI_B + 3 * i, bi + BI_BC + 3 * i);
       }
     }
-    __syncthreads();
+    blk_sync(W);
     // ---- Schur complement S = (A + mu diag A) - sum_j B_j C_j^-1 B_j^T (lower triangle): a
     //      thread per camera pair (a >= b) and row of camera a, over camera a's intra pairs in
     //      order; the landmark's pair with camera b is looked up in its list (ascending cameras)
     const int n_item = nc * (nc + 1) / 2 * 9;
-    for (int it = tid; it < n_item; it += BLK_THREADS) {
+    for (int it = gt; it < n_item; it += GT) {
       const int pi = it / 9, ra = it - 9 * pi;
       int ca = (int)((sqrt(8.0 * pi + 1.0) - 1.0) * 0.5);
       while ((ca + 1) * (ca + 2) / 2 <= pi) ++ca;
@@ -341,7 +363,7 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         if (rb < nrb) Sr[rb] = v[rb];
     }
     // ... and its right-hand side -g + sum_j B_j C_j^-1 g_j (a thread per row, camera a's intra pairs in order)
-    for (int r = tid; r < np; r += BLK_THREADS) {
+    for (int r = gt; r < np; r += GT) {
       const int ca = r / 9, ra = r - 9 * ca;
       double v = -C[ca].g[ra];
       for (int q = A.ci_ptr[cp0 + ca]; q < A.ci_ptr[cp0 + ca + 1]; ++q) {
@@ -351,49 +373,50 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       }
       W.rhs[r] = v;
     }
-    if (tid == 0) sh.flag = 1;
-    __syncthreads();
-    // ---- Cholesky of S in place (column by column; the trailing update a warp per row, its
-    //      lanes along the row), then the two triangular solves (column-oriented)
-    const int warp = tid >> 5, lane = tid & 31;
+    blk_sync(W);
+    // ---- Cholesky of S in place (column by column: every thread takes the pivot, the column is
+    //      scaled, the trailing update a warp per row with its lanes along the row; the pivots'
+    //      square roots go to diag, so S[k][k] is only read); a non-positive pivot fails the trial
+    const int gw = (gt >> 5), GW = GT >> 5, lane = tid & 31;
+    bool ok = true;
     for (int k = 0; k < np; ++k) {
-      if (tid == 0) {
-        const double d = S[(size_t)k * ld + k];
-        if (!(d > 0.0)) sh.flag = 0;
-        S[(size_t)k * ld + k] = sqrt(d > 0.0 ? d : 1.0);
-      }
-      __syncthreads();
-      const double dk = S[(size_t)k * ld + k];
-      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) S[(size_t)i * ld + k] /= dk;
-      __syncthreads();
-      for (int i = k + 1 + warp; i < np; i += BLK_THREADS / 32) {
+      const double d = S[(size_t)k * ld + k];
+      ok = ok && d > 0.0;
+      const double dk = sqrt(d > 0.0 ? d : 1.0);
+      if (gt == 0) W.diag[k] = dk;
+      for (int i = k + 1 + gt; i < np; i += GT) S[(size_t)i * ld + k] /= dk;
+      blk_sync(W);
+      for (int i = k + 1 + gw; i < np; i += GW) {
         double* Si = S + (size_t)i * ld;
         const double lik = Si[k];
         for (int jj = k + 1 + lane; jj <= i; jj += 32) Si[jj] -= lik * S[(size_t)jj * ld + k];
       }
-      __syncthreads();
+      blk_sync(W);
     }
-    if (!sh.flag) continue;
-    // L y = rhs (y to dc), then L^T x = y (x to rhs), then x to dc
-    for (int k = 0; k < np; ++k) {
-      const double yk = W.rhs[k] / S[(size_t)k * ld + k];
-      for (int i = k + 1 + tid; i < np; i += BLK_THREADS) W.rhs[i] -= S[(size_t)i * ld + k] * yk;
-      if (tid == 0) W.dc[k] = yk;
-      __syncthreads();
+    if (!ok) continue;
+    // L y = rhs (y to dc), then L^T x = y (x to rhs), then x to dc; column-oriented, by the
+    // block's first CTA
+    if (W.rank == 0) {
+      for (int k = 0; k < np; ++k) {
+        const double yk = W.rhs[k] / W.diag[k];
+        for (int i = k + 1 + tid; i < np; i += BLK_THREADS) W.rhs[i] -= S[(size_t)i * ld + k] * yk;
+        if (tid == 0) W.dc[k] = yk;
+        __syncthreads();
+      }
+      for (int i = np - 1; i >= 0; --i) {
+        const double xv = W.dc[i] / W.diag[i];
+        const double* Si = S + (size_t)i * ld;
+        for (int k = tid; k < i; k += BLK_THREADS) W.dc[k] -= Si[k] * xv;
+        if (tid == 0) W.rhs[i] = xv;
+        __syncthreads();
+      }
+      for (int r = tid; r < np; r += BLK_THREADS) W.dc[r] = W.rhs[r];
     }
-    for (int i = np - 1; i >= 0; --i) {
-      const double xv = W.dc[i] / S[(size_t)i * ld + i];
-      const double* Si = S + (size_t)i * ld;
-      for (int k = tid; k < i; k += BLK_THREADS) W.dc[k] -= Si[k] * xv;
-      if (tid == 0) W.rhs[i] = xv;
-      __syncthreads();
-    }
-    for (int r = tid; r < np; r += BLK_THREADS) W.dc[r] = W.rhs[r];
-    __syncthreads();
+    blk_sync(W);
     // ---- the candidate: cameras (a thread each), landmarks by back substitution, and the
     //      decrease of E^alpha(. | z) term by term
     double part = 0.0;
-    for (int c = tid; c < nc; c += BLK_THREADS) {
+    for (int c = gt; c < nc; c += GT) {
       BlkCam& bc = C[c];
       const CamT<double>& cz = bc.cz;
       const double* th = W.dc + 9 * c;
@@ -410,8 +433,8 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       part += cam_phi(bar ? bc.stb : bc.stk, cz, cc, xi);   // inter pairs' P and the proximal term
       bc.cb = cc;   // candidate (cs keeps the accepted solution)
     }
-    __syncthreads();
-    for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+    blk_sync(W);
+    for (int e = l0 + gt; e < l1; e += GT) {
       const int j = A.lms[e];
       const double* s = A.lsc + (size_t)j * BL_N;
       double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
@@ -436,9 +459,9 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
       }
       part += Fc - s[BL_FZ];
     }
-    const double dE = blk_reduce(sh, part);
+    const double dE = blk_reduce(sh, W, part);
     if (dE < 0.0) {   // the step is taken
-      for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+      for (int e = l0 + gt; e < l1; e += GT) {
         double* s = A.lsc + (size_t)A.lms[e] * BL_N;
         double rr[3] = {s[BL_G], s[BL_G + 1], s[BL_G + 2]};
         for (int p = A.io_ptr[e]; p < A.io_ptr[e + 1]; ++p) {
@@ -453,23 +476,23 @@ __device__ inline void blk_lm(const BlkArgs& A, int b, bool bar, double gamma, d
         s[BL_L + 1] -= dl[1];
         s[BL_L + 2] -= dl[2];
       }
-      for (int c = tid; c < nc; c += BLK_THREADS) C[c].cs = C[c].cb;
-      __syncthreads();
+      for (int c = gt; c < nc; c += GT) C[c].cs = C[c].cb;
+      blk_sync(W);
       return;
     }
   }
-  __syncthreads();
+  blk_sync(W);
 }
 
 // E^alpha(x | x^k) - E^alpha(x^k | x^k) of block b for the solution in C[.].cs and lsc + BL_L
 __device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& sh, const BlkWork& W) {
-  const int tid = threadIdx.x;
+  const int gt = W.gt, GT = W.GT;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
   const BlkCam* C = W.C;
   double part = 0.0;
-  for (int c = tid; c < nc; c += BLK_THREADS) part += cam_phi(C[c].stk, C[c].ck, C[c].cs, xi);
-  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+  for (int c = gt; c < nc; c += GT) part += cam_phi(C[c].stk, C[c].ck, C[c].cs, xi);
+  for (int e = l0 + gt; e < l1; e += GT) {
     const int j = A.lms[e];
     const double* s = A.lsc + (size_t)j * BL_N;
     double lk[3];
@@ -484,37 +507,45 @@ __device__ inline double blk_dE_k(const BlkArgs& A, int b, double xi, BlkSmem& s
       part += blk_F(C[c].cs, s + BL_L, u.x, u.y, A.L, A.loss) - blk_F(C[c].ck, lk, u.x, u.y, A.L, A.loss);
     }
   }
-  return blk_reduce(sh, part);
+  return blk_reduce(sh, W, part);
 }
 
 __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams P) {
   extern __shared__ __align__(16) double blk_dyn[];   // the block scratch (ld > 0)
   __shared__ BlkSmem sh;
-  const int b = blockIdx.x;
+  const int cs = (int)cooperative_groups::this_cluster().num_blocks();
+  const int b = blockIdx.x / cs;   // a block per cluster of cs CTAs (cs = 1: a CTA per block)
   const int tid = threadIdx.x;
   const int it = *P.it, first = *P.first;
   const double gamma = P.gam[it], xi = P.xi;
   const int cp0 = A.cam_ptr[b], nc = A.cam_ptr[b + 1] - cp0;
   const int l0 = A.lm_ptr[b], l1 = A.lm_ptr[b + 1];
   BlkWork W;
-  if (A.ld > 0) {   // shared memory: per camera scratch of the most cameras, dc, rhs, then S
+  W.cs = cs;
+  W.rank = (int)(blockIdx.x - (unsigned)b * cs);
+  W.gt = W.rank * BLK_THREADS + tid;
+  W.GT = cs * BLK_THREADS;
+  if (A.ld > 0) {   // shared memory (cs = 1): per camera scratch of the most cameras, dc, rhs, diag, then S
     const int mc = A.ld / 9;
     W.C = reinterpret_cast<BlkCam*>(blk_dyn);
     W.dc = blk_dyn + (size_t)mc * (sizeof(BlkCam) / 8);
     W.rhs = W.dc + A.ld;
-    W.S = W.rhs + A.ld;
+    W.diag = W.rhs + A.ld;
+    W.S = W.diag + A.ld;
     W.ld = A.ld;
   } else {   // global memory at the block's camera entries and Schur offset
     W.C = A.g_cam + cp0;
-    W.dc = A.g_vec + (size_t)18 * cp0;
+    W.dc = A.g_vec + (size_t)27 * cp0;
     W.rhs = W.dc + 9 * nc;
+    W.diag = W.rhs + 9 * nc;
     W.S = A.g_S + A.g_soff[b];
     W.ld = 9 * nc;
   }
+  const int gt = W.gt, GT = W.GT;
   BlkCam* C = W.C;
   // ---- cameras: x^k, x̄^k, statistics, F sums, displacement (a thread each)
   double part_disp = 0.0, part_Fall = 0.0, part_Fin = 0.0, part_G = 0.0;
-  for (int c = tid; c < nc; c += BLK_THREADS) {
+  for (int c = gt; c < nc; c += GT) {
     const int cam = A.cams[cp0 + c];
     double pF = 0.0;
     const double* x = A.cam_x + (size_t)cam * CSTRIDE;
@@ -547,17 +578,17 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
   }
   // ---- landmarks: displacement, gaps and inter F sums
   double part_dl = 0.0, part_Gl = 0.0, part_Fl = 0.0;
-  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+  for (int e = l0 + gt; e < l1; e += GT) {
     const int j = A.lms[e];
     const V4<double> LA = A.lmrec[2 * (size_t)j], LB = A.lmrec[2 * (size_t)j + 1];
     part_dl += LA.w * LA.w + LB.x * LB.x + LB.y * LB.y;
     part_Gl += A.lm_sums[(size_t)j * LS_N + LS_G];
     part_Fl += A.lm_sums[(size_t)j * LS_N + LS_F];
   }
-  const double disp = blk_reduce(sh, part_disp) + blk_reduce(sh, part_dl);
-  const double Fall = blk_reduce(sh, part_Fall), Fin = blk_reduce(sh, part_Fin);
-  const double G = blk_reduce(sh, part_G) + blk_reduce(sh, part_Gl);
-  const double Fl = blk_reduce(sh, part_Fl);
+  const double disp = blk_reduce(sh, W, part_disp) + blk_reduce(sh, W, part_dl);
+  const double Fall = blk_reduce(sh, W, part_Fall), Fin = blk_reduce(sh, W, part_Fin);
+  const double G = blk_reduce(sh, W, part_G) + blk_reduce(sh, W, part_Gl);
+  const double Fl = blk_reduce(sh, W, part_Fl);
   // Eq. DEalpha, Eq. Fainit, Eq. Fak, Eq. lFak, with E^alpha(x^k | x^k) = sum_E' F + (1/2) sum_E'' F
   const double E0 = Fin + 0.5 * (Fall - Fin) + 0.5 * Fl;
   const double dE = -0.5 * xi * disp + 0.5 * G;
@@ -574,13 +605,13 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
     rs = Enext > Fbar;
   }
   if (rs) {
-    for (int c = tid; c < nc; c += BLK_THREADS) C[c].cz = C[c].ck;
-    __syncthreads();
+    for (int c = gt; c < nc; c += GT) C[c].cz = C[c].ck;
+    blk_sync(W);
     blk_lm(A, b, false, gamma, xi, sh, W);
     Enext = F + blk_dE_k(A, b, xi, sh, W);
   }
   // ---- new state
-  for (int e = l0 + tid; e < l1; e += BLK_THREADS) {
+  for (int e = l0 + gt; e < l1; e += GT) {
     const int j = A.lms[e];
     const double* s = A.lsc + (size_t)j * BL_N;
     const V4<double> LA = A.lmrec[2 * (size_t)j];
@@ -596,13 +627,13 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
     A.lmrec_out[2 * (size_t)j] = nA;
     A.lmrec_out[2 * (size_t)j + 1] = nB;
   }
-  if (tid == 0) {
+  if (gt == 0) {
     A.blk_E[b] = Enext;
     A.blk_Fbar[b] = Fbar;
     A.blk_F[b] = F;
     A.blk_rs[b] = (rs && P.accelerated) ? 1 : 0;
   }
-  for (int c = tid; c < nc; c += BLK_THREADS) {
+  for (int c = gt; c < nc; c += GT) {
     const int cam = A.cams[cp0 + c];
     const CamT<double>& cs = C[c].cs;
     const CamT<double>& ck = C[c].ck;

@@ -41,9 +41,9 @@ def _scene(name):
     return cached_scene(name, scale={"street": 0.05, "tourism": 0.005}[name])
 
 
-@pytest.mark.parametrize("name,accel,K,n_blocks", [
+@pytest.mark.parametrize("name,accel,K,n_blocks,ctas", [(*c, 0) if len(c) == 4 else c for c in [
     ("circle", True, 20, None), ("circle_small", False, 12, None), ("street", True, 12, None),
-    ("tourism", True, 20, None),
+    ("tourism", True, 20, None), ("tourism", True, 12, None, 1),
     # several cameras per block: the Schur complement couples the block's cameras. Such a block
     # is a small bundle adjustment whose gauge only the inter pairs and xi hold, and two correct
     # solves of its damped system part at ~1e-10 after one step; the parting grows about threefold
@@ -51,10 +51,13 @@ def _scene(name):
     # (test_multi_camera_blocks_step_from_common_state compares every step from the GPU's state)
     ("circle", True, 12, 4), ("circle", True, 12, 8), ("circle_small", False, 12, 3), ("circle_small", True, 12, 6),
     ("street", True, 8, 25), ("tourism", True, 12, 8), ("tourism", True, 12, 32),
-    # blocks of 10 and 15 cameras (shared-memory scratch), 20 and 25 (global scratch); the
-    # oracle takes seconds per iteration on the larger ones
-    ("circle", True, 12, 2), ("tourism", True, 4, 4), ("circle", True, 12, 1), ("street", True, 4, 2)])
-def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
+    # blocks of 10 and 15 cameras on one CTA each (shared-memory scratch) and on clusters; 20 and
+    # 25 cameras on one CTA (global scratch) and on clusters; the oracle takes seconds per
+    # iteration on the larger ones
+    ("circle", True, 12, 4, 1), ("circle", True, 12, 2, 1), ("circle", True, 12, 2), ("tourism", True, 4, 4, 1),
+    ("tourism", True, 4, 4), ("circle", True, 12, 1, 1), ("circle", True, 12, 1), ("circle", True, 12, 1, 4),
+    ("street", True, 4, 2)]])
+def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks, ctas):
     from paper_2305_07026_b300 import _lib as L
     sc = _scene(name)
     part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n_blocks or sc.M)
@@ -65,6 +68,7 @@ def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     s2 = prob.s_norm ** 2
     g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64", accelerated=accel)
     g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    g.set_block_ctas(ctas)
     g.set_partition(part.cam_block, part.lm_block, part.S)
     g.set_state(sc.cams, sc.lms)
     compared = 0
@@ -94,10 +98,11 @@ def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks):
     g.close()
 
 
-@pytest.mark.parametrize("name,n_blocks,iters", [("circle", 4, 20), ("circle", 8, 20), ("tourism", 8, 20),
-                                                 ("tourism", 32, 20), ("circle", 2, 20), ("circle", 1, 20),
-                                                 ("street", 2, 4), ("tourism", 1, 3)])
-def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters):
+@pytest.mark.parametrize("name,n_blocks,iters,ctas", [("circle", 4, 20, 1), ("circle", 8, 20, 0), ("tourism", 8, 20, 1),
+                                                      ("tourism", 8, 6, 0), ("tourism", 32, 20, 0),
+                                                      ("circle", 2, 20, 0), ("circle", 1, 20, 1), ("circle", 1, 20, 0),
+                                                      ("street", 2, 4, 0), ("tourism", 1, 3, 0)])
+def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas):
     """Every one of `iters` iterations (blocks of up to 60 cameras) from the same state: before each GPU iteration the oracle takes
     the GPU's x^k and x^(k-1) (through the boundary) and its Fbar^alpha(k-1); the oracle's Nesterov
     scalar and E^alpha carry over from its own previous step. Compared after the step: the block
@@ -113,6 +118,7 @@ def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters):
     s2 = prob.s_norm ** 2
     g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
     g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    g.set_block_ctas(ctas)
     g.set_partition(part.cam_block, part.lm_block, part.S)
     g.set_state(sc.cams, sc.lms)
     prev = g.get_state()
@@ -186,6 +192,11 @@ def test_blocks_run_segments_and_clear():
 
 def test_blocks_arguments():
     from paper_2305_07026_b300 import _lib as L
+    with L.Daba(4, 4, 8, prec="fp64") as d:
+        for bad in (-1, 17):
+            with pytest.raises(L.DabaError) as e:
+                d.set_block_ctas(bad)
+            assert e.value.status == L.DABA_ERR_ARG
     sc = _scene("circle_small")
     part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, sc.M)
     m = L.Daba(sc.M, sc.N, sc.nnz, prec="mixed")
@@ -232,11 +243,13 @@ def test_blocks_without_cameras_and_regrown_partition():
     one = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, sc.M)
     lm_only = one.lm_block.copy()
     lm_only[::3] = sc.M + (np.arange(sc.N)[::3] % 4)   # a third of the landmarks in four camera-less blocks
-    parts = [B.Partition(one.cam_block, lm_only, sc.M + 6),   # the last two blocks hold nothing
-             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 3),
-             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 1),   # global-memory scratch
-             B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 2)]   # and back to shared memory
-    for part in parts:
+    parts = [(B.Partition(one.cam_block, lm_only, sc.M + 6), 1),   # the last two blocks hold nothing
+             (B.Partition(one.cam_block, lm_only, sc.M + 6), 8),   # ... on clusters of 8 CTAs
+             (B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 3), 1),
+             (B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 1), 1),   # global-memory scratch
+             (B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 2), 1)]   # and back to shared memory
+    for part, ctas in parts:
+        g.set_block_ctas(ctas)
         g.set_partition(part.cam_block, part.lm_block, part.S)
         g.set_state(sc.cams, sc.lms)
         st = B.init_state(prob, part, R, t, d, l)
