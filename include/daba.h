@@ -230,9 +230,10 @@ daba_status daba_set_scenes(daba_ctx* ctx, int32_t n_scenes, const int32_t* cam_
 daba_status daba_scene_objectives(daba_ctx* ctx, double* out, void* stream);
 
 /* Checkpoint of the full method state (x^k, x^k - x^(k-1), s^k, k and the per-block
- * restart metrics) into a host buffer. With buf == NULL only *bytes is set to the
- * required size. Importing it into a context with the same sizes, options and
- * observations resumes bit-identically. */
+ * restart metrics; with coarse blocks also E^alpha, Fbar^alpha, F^alpha and the restart flag of
+ * every block, and a fingerprint of the partition) into a host buffer. With buf == NULL only
+ * *bytes is set to the required size. Importing it into a context with the same sizes, options,
+ * observations and partition resumes bit-identically (DABA_ERR_ARG for another partition). */
 daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes);
 daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes);
 
@@ -278,8 +279,8 @@ daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
  * daba_set_observations (which clears the partition); n_blocks = 0 returns to one block per
  * camera and per landmark (the arrays are then ignored). The device scratch grows with the
  * partition: 888 bytes per intra pair, 248 per landmark, and with global scratch 1752 bytes per
- * camera plus (9 n_c)^2 x 8 bytes per block. Checkpoints and the unrolled gradient
- * are not available while a partition is set. */
+ * camera plus (9 n_c)^2 x 8 bytes per block. Checkpoints carry the partition's block metrics;
+ * the unrolled gradient is not available while a partition is set. */
 daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* cam_block, const int32_t* lm_block);
 
 /* How the next daba_set_partition spreads a block over CTAs (Algorithm 1 with coarse blocks, its

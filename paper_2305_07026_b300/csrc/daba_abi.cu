@@ -33,7 +33,7 @@ constexpr int RUN_GRAPH_MAX = 256;   // a run of at most this many iterations is
 constexpr int64_t PIPE_MIN_NNZ = 1 << 20;   // two-range schedule by default from this many observations
 constexpr int PIPE_MAX_RANGES = 64;
 constexpr int PIPE_POOL = 8;   // streams per kernel role of the range schedule
-constexpr uint64_t CKPT_MAGIC = 0x44414241434b5032ull;   // "DABACKP2"
+constexpr uint64_t CKPT_MAGIC = 0x44414241434b5033ull;   // "DABACKP3"
 
 }  // namespace
 
@@ -133,6 +133,7 @@ struct daba_ctx {
   size_t blk_smem = 0;   // dynamic shared memory of the block solve
   int blk_cs = 1;        // CTAs per block (a thread-block cluster when above 1; global scratch only)
   int blk_pref = 0;      // daba_set_block_ctas: 0 automatic, 1 one CTA per block, 2..16 a cluster
+  uint64_t blk_hash = 0;   // FNV-1a of the partition (n_blocks, cam_block, lm_block): checkpoints carry it
   void *blk_ci_e = nullptr, *blk_ci_io = nullptr, *blk_gcam = nullptr, *blk_gvec = nullptr, *blk_gS = nullptr,
        *blk_soff = nullptr;
   void *c_intra = nullptr, *blk_cam_ptr = nullptr, *blk_cams = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr,
@@ -2443,17 +2444,22 @@ struct CkptHeader {
   int64_t M, N, nnz, prec, k;
   double s_k, s_norm;
   int64_t first;
+  int64_t n_blocks;    // coarse blocks: their number and the partition's fingerprint (0, 0 without)
+  uint64_t blk_hash;
 };
+// the block section (coarse blocks): E^alpha, Fbar^alpha, F^alpha and the restart flags per block
+size_t ckpt_blk_bytes(const daba_ctx* c) {
+  return c->n_blocks ? (size_t)c->n_blocks * 24 + (((size_t)c->n_blocks + 7) & ~(size_t)7) : 0;
+}
 size_t ckpt_bytes(const daba_ctx* c) {
   return sizeof(CkptHeader) + (size_t)c->M * CSTRIDE * 8 * 2 + (size_t)c->M * 8 * 2 + (size_t)c->N * LREC * real_sz(c) +
-         (size_t)c->N * 16;
+         (size_t)c->N * 16 + ckpt_blk_bytes(c);
 }
 }  // namespace
 
 daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
   if (!ctx || !bytes) return DABA_ERR_ARG;
   if (!ctx->state_set) return fail(ctx, DABA_ERR_STATE, "state not set");
-  if (ctx->n_blocks) return fail(ctx, DABA_ERR_STATE, "checkpoints cover one block per camera and landmark only");
   const size_t need = ckpt_bytes(ctx);
   if (!buf) {
     *bytes = need;
@@ -2461,7 +2467,8 @@ daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
   }
   if (*bytes < need) return fail(ctx, DABA_ERR_ARG, "checkpoint buffer too small (%zu < %zu)", *bytes, need);
   CK(cudaDeviceSynchronize());
-  CkptHeader h{CKPT_MAGIC, ctx->M, ctx->N, ctx->nnz, (int64_t)ctx->opt.prec, ctx->k, ctx->s_k, ctx->s_norm, 0};
+  CkptHeader h{CKPT_MAGIC, ctx->M, ctx->N, ctx->nnz, (int64_t)ctx->opt.prec, ctx->k, ctx->s_k, ctx->s_norm, 0,
+               ctx->n_blocks, ctx->n_blocks ? ctx->blk_hash : 0};
   int first = 0;
   CK(cudaMemcpy(&first, ctx->d_first, sizeof(int), cudaMemcpyDeviceToHost));
   h.first = first;
@@ -2481,19 +2488,28 @@ daba_status daba_export_checkpoint(daba_ctx* ctx, void* buf, size_t* bytes) {
   CK(cudaMemcpy(p, lmrec_at(ctx, ctx->k), lb, cudaMemcpyDeviceToHost));
   p += lb;
   CK(cudaMemcpy(p, lmlo_at(ctx, ctx->k), (size_t)ctx->N * 16, cudaMemcpyDeviceToHost));
+  p += (size_t)ctx->N * 16;
+  if (ctx->n_blocks) {
+    const size_t sb = (size_t)ctx->n_blocks * 8;
+    CK(cudaMemcpy(p, ctx->blk_E, sb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p + sb, ctx->blk_Fbar, sb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p + 2 * sb, ctx->blk_F, sb, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(p + 3 * sb, ctx->blk_rs, (size_t)ctx->n_blocks, cudaMemcpyDeviceToHost));
+  }
   *bytes = need;
   return DABA_OK;
 }
 
 daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes) {
   if (!ctx || !buf) return DABA_ERR_ARG;
-  if (ctx->n_blocks) return fail(ctx, DABA_ERR_STATE, "checkpoints cover one block per camera and landmark only");
   if (!ctx->obs_set) return fail(ctx, DABA_ERR_STATE, "observations must be set before importing a checkpoint");
   if (bytes < ckpt_bytes(ctx)) return fail(ctx, DABA_ERR_ARG, "checkpoint too small");
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   if (h.magic != CKPT_MAGIC || h.M != ctx->M || h.N != ctx->N || h.nnz != ctx->nnz || h.prec != (int64_t)ctx->opt.prec)
     return fail(ctx, DABA_ERR_ARG, "checkpoint does not match this context");
+  if (h.n_blocks != ctx->n_blocks || h.blk_hash != (ctx->n_blocks ? ctx->blk_hash : 0))
+    return fail(ctx, DABA_ERR_ARG, "checkpoint was taken with another partition into blocks");
   const char* p = (const char*)buf + sizeof(h);
   const size_t cb = (size_t)ctx->M * CSTRIDE * 8;
   CK(cudaMemcpy(ctx->cam_x, p, cb, cudaMemcpyHostToDevice));
@@ -2508,6 +2524,14 @@ daba_status daba_import_checkpoint(daba_ctx* ctx, const void* buf, size_t bytes)
   CK(cudaMemcpy(lmrec_at(ctx, h.k), p, lb, cudaMemcpyHostToDevice));
   p += lb;
   CK(cudaMemcpy(lmlo_at(ctx, h.k), p, (size_t)ctx->N * 16, cudaMemcpyHostToDevice));
+  p += (size_t)ctx->N * 16;
+  if (ctx->n_blocks) {
+    const size_t sb = (size_t)ctx->n_blocks * 8;
+    CK(cudaMemcpy(ctx->blk_E, p, sb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_Fbar, p + sb, sb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_F, p + 2 * sb, sb, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->blk_rs, p + 3 * sb, (size_t)ctx->n_blocks, cudaMemcpyHostToDevice));
+  }
   int first = (int)h.first;
   CK(cudaMemcpy(ctx->d_first, &first, sizeof(int), cudaMemcpyHostToDevice));
   ctx->k = h.k;
@@ -2698,6 +2722,17 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   ctx->blk_ld = in_smem ? ld : 0;
   ctx->blk_smem = smem;
   ctx->blk_cs = csz;
+  {   // the partition's fingerprint (FNV-1a over n_blocks and both block arrays)
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](const void* d, size_t n) {
+      const unsigned char* q = (const unsigned char*)d;
+      for (size_t i = 0; i < n; ++i) hsh = (hsh ^ q[i]) * 1099511628211ull;
+    };
+    mix(&S, sizeof(S));
+    mix(cb.data(), (size_t)M * 4);
+    mix(lb.data(), (size_t)N * 4);
+    ctx->blk_hash = hsh;
+  }
   drop_graphs(ctx);
   return DABA_OK;
 }

@@ -222,12 +222,57 @@ def test_blocks_arguments():
     with pytest.raises(L.DabaError) as e:   # more blocks than cameras and landmarks
         d.set_partition(part.cam_block, part.lm_block, sc.M + sc.N + 1)
     assert e.value.status == L.DABA_ERR_ARG
-    d.set_partition(part.cam_block, part.lm_block)
-    d.set_state(sc.cams, sc.lms)
-    with pytest.raises(L.DabaError) as e:
-        d.export_checkpoint()
-    assert e.value.status == L.DABA_ERR_STATE
     d.close()
+
+
+@pytest.mark.parametrize("n_blocks,ctas", [(20, 1), (3, 1), (2, 0)])
+def test_blocks_checkpoint_resume(n_blocks, ctas):
+    """A checkpoint taken after 5 iterations with a partition (state, Nesterov scalar and the
+    per-block E^alpha, Fbar^alpha, F^alpha and restart flags) resumes bit for bit in another
+    context with the same partition; a context with another partition, or none, refuses it."""
+    from paper_2305_07026_b300 import _lib as L
+    sc = _scene("circle_small")
+    part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n_blocks)
+
+    def ctx(p):
+        d = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
+        d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+        d.set_block_ctas(ctas)
+        if p is not None:
+            d.set_partition(p.cam_block, p.lm_block, p.S)
+        d.set_state(sc.cams, sc.lms)
+        return d
+    a = ctx(part)
+    ta = np.zeros(13)
+    ra = np.zeros(12, np.int32)
+    a.run(5, ta[:6], ra[:5])
+    ck = a.export_checkpoint()
+    F5, Fb5, rs5 = a.get_partition_metrics()
+    t7 = np.zeros(8)
+    r7 = np.zeros(7, np.int32)
+    a.run(7, t7, r7)
+    b = ctx(part)
+    b.import_checkpoint(ck)
+    F, Fb, rs = b.get_partition_metrics()
+    np.testing.assert_array_equal(F, F5)
+    np.testing.assert_array_equal(Fb, Fb5)
+    np.testing.assert_array_equal(rs, rs5)
+    tb = np.zeros(8)
+    rb = np.zeros(7, np.int32)
+    b.run(7, tb, rb)
+    np.testing.assert_array_equal(tb, t7)
+    np.testing.assert_array_equal(rb, r7)
+    for x, y in zip(a.get_state(), b.get_state()):
+        np.testing.assert_array_equal(x, y)
+    other = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 5 if n_blocks != 5 else 4)
+    for p in (other, None):
+        c = ctx(p)
+        with pytest.raises(L.DabaError) as e:
+            c.import_checkpoint(ck)
+        assert e.value.status == L.DABA_ERR_ARG
+        c.close()
+    for x in (a, b):
+        x.close()
 
 
 def test_blocks_without_cameras_and_regrown_partition():
