@@ -256,8 +256,8 @@ daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
  * landmark pass report a timeout (a test of that path). DABA_ERR_ARG if first_wait_ns < 0. */
 daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
 
-/* Coarse blocks (Sec. 4, Eq. Ealpha with E' not empty; FP64 contexts with the per-block restart):
- * block b holds the cameras i with cam_block[i] = b (at most 8 per block, none allowed) and the
+/* Coarse blocks (Sec. 4, Eq. Ealpha with E' not empty; FP64 contexts):
+ * block b holds the cameras i with cam_block[i] = b (at most 128 per block, none allowed) and the
  * landmarks j with lm_block[j] = b (host or device int32 arrays of M and N entries, block ids in
  * [0, n_blocks), 1 <= n_blocks <= M + N). A reprojection pair whose camera and landmark share a
  * block keeps its exact F_ij in the block's surrogate; every other pair is split by the majorizer
@@ -265,7 +265,9 @@ daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
  * Algorithm 1 then takes, per block, one successful Levenberg-Marquardt step on
  * E^alpha(. | xbar^k) from xbar^k (Sec. 7.1 reports one successful inner LM step per
  * subproblem), the per-block restart test of Eq. Eak, and where it fires the LM step on
- * E^alpha(. | x^k) from x^k. LM step: R = R_z Exp(phi), t = t_z + tau, d = d_z + delta,
+ * E^alpha(. | x^k) from x^k. With restart_mode = DABA_RESTART_GLOBAL one test on the sums over
+ * the blocks decides for all of them (every block's accelerated step is kept, the test runs, then
+ * every block commits its kept step or takes the MM step), with momentum_reset also s <- 1. LM step: R = R_z Exp(phi), t = t_z + tau, d = d_z + delta,
  * l = l_z + epsilon; Gauss-Newton model of the block surrogate (the intra pairs reweighted with
  * w = rho'(|e|^2) at z, the proximal term to second order); damping 1e-3 x diag, raised tenfold
  * up to 8 times; taken only if E^alpha(. | z) decreases. The damped system is solved through the

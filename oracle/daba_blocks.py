@@ -30,6 +30,10 @@ decrease is evaluated term by term (residual differences for P and Q), so that n
 cancel. Start point and proximal centre are the conditioning iterate (x_bar^k for the accelerated
 update, x^k for the MM update).
 
+Global restart (Options.restart = "global"): one restart test on the sums over all blocks, every
+block taking the MM update when it fires; with Options.momentum_reset the Nesterov scalar restarts
+too (s <- 1), as in the singleton oracle.
+
 Parity unpinned: the paper's own LM details (damping, parameterisation) are not given.
 """
 from __future__ import annotations
@@ -320,7 +324,15 @@ def step(prob, part, st: BlockState):
     if o.accelerated:
         Ra, ta, da, la, _ = solve_blocks_lm(prob, part, isin, mj_b, Rb, tb, db, lb)
         Ea = F_blk + dE_blocks(prob, part, isin, mj_k, Ra, ta, da, la, st.R, st.t, st.d, st.l)
-        rs = Ea > Fbar
+        if o.restart == "global":
+            # the test of Algorithm 1 for the one block made of all blocks; with the momentum
+            # reset the Nesterov scalar restarts with it
+            fire = bool(np.sum(Ea) > np.sum(Fbar))
+            rs = np.full(part.S, fire)
+            if fire and o.momentum_reset:
+                s_next = 1.0
+        else:
+            rs = Ea > Fbar
     else:
         Ra, ta, da, la, Ea = Rm, tm, dm, lm_, Emm
         rs = np.ones(part.S, dtype=bool)

@@ -134,6 +134,8 @@ struct daba_ctx {
   int blk_cs = 1;        // CTAs per block (a thread-block cluster when above 1; global scratch only)
   int blk_pref = 0;      // daba_set_block_ctas: 0 automatic, 1 one CTA per block, 2..16 a cluster
   uint64_t blk_hash = 0;   // FNV-1a of the partition (n_blocks, cam_block, lm_block): checkpoints carry it
+  int blk_ncam = 0;        // blocks that hold a camera (the restart count of an iteration)
+  void *blk_g = nullptr, *blk_Ealt = nullptr;   // global restart over blocks: test terms, kept E(k+1)
   void *blk_ci_e = nullptr, *blk_ci_io = nullptr, *blk_gcam = nullptr, *blk_gvec = nullptr, *blk_gS = nullptr,
        *blk_soff = nullptr;
   void *c_intra = nullptr, *blk_cam_ptr = nullptr, *blk_cams = nullptr, *blk_lm_ptr = nullptr, *blk_lms = nullptr,
@@ -341,6 +343,7 @@ IterParams iter_params(daba_ctx* ctx) {
   P.cam_alt = (double*)ctx->cam_alt;
   P.g_fire = (int*)ctx->g_fire;
   P.s_dev = (double*)ctx->s_dev;
+  P.fire_given = 0;
   return P;
 }
 
@@ -482,11 +485,15 @@ cudaError_t launch_camsolve(daba_ctx* ctx, cudaStream_t st, int64_t k, int i0 = 
   return launch_camsolve_t<CAM_SCAM>(ctx, st, k, i0, i1);
 }
 
-cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st) {
+// fire_given: the global restart was decided over coarse blocks (g_fire), counted as n_restart
+// blocks when it fired
+cudaError_t launch_finalize(daba_ctx* ctx, cudaStream_t st, bool fire_given = false, int n_restart = -1) {
   ctx->launches++;
-  const IterParams P = iter_params(ctx);
+  IterParams P = iter_params(ctx);
+  P.fire_given = fire_given ? 1 : 0;
   k_finalize<<<FIN_BLOCKS, FIN_THREADS, 0, st>>>(ctx->M, (const double*)ctx->cam_Fsum, (const uint8_t*)ctx->cam_rs,
-                                                  ctx->n_tiles, (const int*)ctx->tile_rs, ctx->M + ctx->N,
+                                                  ctx->n_tiles, (const int*)ctx->tile_rs,
+                                                  n_restart >= 0 ? n_restart : ctx->M + ctx->N,
                                                   ctx->s_norm * ctx->s_norm, P,
                                                   (double*)ctx->fin_blk, (unsigned int*)ctx->fin_ticket,
                                                   (double*)ctx->d_trace, (int*)ctx->d_rs, (int*)ctx->d_flag);
@@ -548,25 +555,40 @@ cudaError_t launch_blk_iter_t(daba_ctx* ctx, cudaStream_t st, int64_t k) {
   A.pack_next = (V4<double>*)pack_at(ctx, k + 1);
   A.L = L;
   A.loss = LOSS;
-  if (ctx->blk_cs > 1) {   // a cluster of blk_cs CTAs per block
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(ctx->n_blocks * ctx->blk_cs));
-    cfg.blockDim = dim3(BLK_THREADS);
-    cfg.dynamicSmemBytes = ctx->blk_smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = (unsigned)ctx->blk_cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&cfg, k_blk_solve, A, P)) != cudaSuccess) return e;
-  } else {
+  A.blk_g = (double*)ctx->blk_g;
+  A.blk_Ealt = (double*)ctx->blk_Ealt;
+  auto solve = [&](int pass) -> cudaError_t {
+    A.pass = pass;
+    ctx->launches++;
+    if (ctx->blk_cs > 1) {   // a cluster of blk_cs CTAs per block
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(ctx->n_blocks * ctx->blk_cs));
+      cfg.blockDim = dim3(BLK_THREADS);
+      cfg.dynamicSmemBytes = ctx->blk_smem;
+      cfg.stream = st;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)ctx->blk_cs;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_blk_solve, A, P);
+    }
     k_blk_solve<<<ctx->n_blocks, BLK_THREADS, ctx->blk_smem, st>>>(A, P);
+    return cudaGetLastError();
+  };
+  if (ctx->opt.accelerated && ctx->opt.restart_mode == DABA_RESTART_GLOBAL) {
+    // global restart: every block's accelerated step kept, the test over the blocks, then the
+    // MM step everywhere or the kept steps committed; the reduction takes the decision
+    if ((e = solve(1)) != cudaSuccess) return e;
+    k_blk_fire<<<1, 32, 0, st>>>(ctx->n_blocks, (const double*)ctx->blk_g, (int*)ctx->g_fire);
+    ctx->launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = solve(2)) != cudaSuccess) return e;
+    return launch_finalize(ctx, st, true, ctx->blk_ncam);
   }
-  ctx->launches++;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = solve(0)) != cudaSuccess) return e;
   return launch_finalize(ctx, st);
 }
 
@@ -2551,8 +2573,6 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
     return DABA_OK;
   }
   if (is_mixed(ctx)) return fail(ctx, DABA_ERR_ARG, "coarse blocks run on FP64 contexts");
-  if (ctx->opt.restart_mode != DABA_RESTART_BLOCK)
-    return fail(ctx, DABA_ERR_ARG, "coarse blocks use the per-block restart of Algorithm 1");
   const int M = ctx->M, N = ctx->N;
   if (n_blocks < 0 || (int64_t)n_blocks > (int64_t)M + N || !cam_block || !lm_block)
     return fail(ctx, DABA_ERR_ARG, "n_blocks must lie in 1 .. M + N, with both block arrays given");
@@ -2701,6 +2721,8 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   if ((s = dgrow(ctx, &ctx->blk_Fbar, (size_t)S * 8)) != DABA_OK) return s;
   if ((s = dgrow(ctx, &ctx->blk_F, (size_t)S * 8)) != DABA_OK) return s;
   if ((s = dgrow(ctx, &ctx->blk_rs, (size_t)S)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_g, (size_t)S * 8)) != DABA_OK) return s;
+  if ((s = dgrow(ctx, &ctx->blk_Ealt, (size_t)S * 8)) != DABA_OK) return s;
   if ((s = dgrow(ctx, &ctx->blk_bk, (size_t)S * 32)) != DABA_OK) return s;
   CK(cudaMemcpy(ctx->c_intra, intra.data(), (size_t)n, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->blk_cam_ptr, cam_ptr.data(), (size_t)(S + 1) * 4, cudaMemcpyHostToDevice));
@@ -2722,6 +2744,8 @@ daba_status daba_set_partition(daba_ctx* ctx, int32_t n_blocks, const int32_t* c
   ctx->blk_ld = in_smem ? ld : 0;
   ctx->blk_smem = smem;
   ctx->blk_cs = csz;
+  ctx->blk_ncam = 0;
+  for (int b = 0; b < S; ++b) ctx->blk_ncam += cam_ptr[b + 1] > cam_ptr[b] ? 1 : 0;
   {   // the partition's fingerprint (FNV-1a over n_blocks and both block arrays)
     uint64_t hsh = 1469598103934665603ull;
     auto mix = [&](const void* d, size_t n) {

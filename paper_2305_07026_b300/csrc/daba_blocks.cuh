@@ -60,6 +60,12 @@ struct BlkArgs {
   double* g_vec;                         // ... two vectors of 9 per camera entry (step and right-hand side)
   double* g_S;                           // ... the Schur matrices, block b's at g_soff[b]
   const long long* g_soff;
+  // global restart: pass 1 takes the accelerated step and keeps it (cameras in the iteration's
+  // cam_alt, landmarks in lsc), with the block's test term blk_g = E(k+1) - Fbar(k) and blk_Ealt =
+  // E(k+1); pass 2, after the decision (g_fire), commits the kept step or the MM step. pass 0:
+  // the per-block restart in one launch.
+  int pass;
+  double *blk_g, *blk_Ealt;
   const double2* c_u;
   const int* cam_chunk_ptr;
   const double* part;
@@ -599,9 +605,26 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
   // ---- accelerated step from x̄^k, restart test (Eq. Eak, strict), MM step from x^k where it fires
   bool rs = true;
   double Enext = 0.0;
-  if (P.accelerated) {
+  if (A.pass == 2) {   // global restart, decided: the MM step in every block, or the kept step
+    rs = *P.g_fire != 0;
+    if (!rs) {
+      for (int c = gt; c < nc; c += GT)
+        C[c].cs = *reinterpret_cast<const CamT<double>*>(P.cam_alt + (size_t)A.cams[cp0 + c] * 32);
+      Enext = A.blk_Ealt[b];
+      blk_sync(W);
+    }
+  } else if (P.accelerated) {
     blk_lm(A, b, true, gamma, xi, sh, W);
     Enext = F + blk_dE_k(A, b, xi, sh, W);
+    if (A.pass == 1) {   // global restart: keep the accelerated step and the block's test term
+      for (int c = gt; c < nc; c += GT)
+        *reinterpret_cast<CamT<double>*>(P.cam_alt + (size_t)A.cams[cp0 + c] * 32) = C[c].cs;
+      if (gt == 0) {
+        A.blk_g[b] = Enext - Fbar;
+        A.blk_Ealt[b] = Enext;
+      }
+      return;
+    }
     rs = Enext > Fbar;
   }
   if (rs) {
@@ -654,13 +677,26 @@ __global__ void __launch_bounds__(BLK_THREADS) k_blk_solve(BlkArgs A, IterParams
       x[CS_D + a] = cs.d[a];
       dx[CS_D + a] = ndx.d[a];
     }
-    const double gn = P.gam[it + 1];
+    // the next extrapolation; after a global restart with the momentum reset s^(k+1) = 1, so
+    // gamma^(k+1) = 0 (the reduction sets the table to the same after this kernel)
+    const double gn = (A.pass == 2 && rs && P.reset_s) ? 0.0 : P.gam[it + 1];
     double K[9], Rb[9];
     for (int a = 0; a < 9; ++a) K[a] = cs.R[a] + gn * ndx.R[a];
     extrap_rotation<double>(K, Rb);
     for (int a = 0; a < 9; ++a) A.cam_Rbar[(size_t)cam * 9 + a] = Rb[a];
     write_pack_t<double>(cs, ndx, Rb, A.pack_next + (size_t)cam * P4N);
   }
+}
+
+// The global restart's test over the blocks (Algorithm 1 for the one block made of all): the sum
+// of E(k+1) - Fbar(k) over the blocks in a fixed order (lane l takes blocks l, l + 32, ..., then a
+// shuffle tree) and the decision.
+__global__ void k_blk_fire(int S, const double* __restrict__ blk_g, int* __restrict__ g_fire) {
+  double g = 0.0;
+  for (int b = threadIdx.x; b < S; b += 32) g += blk_g[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
+  if (threadIdx.x == 0) *g_fire = g > 0.0 ? 1 : 0;
 }
 
 }  // namespace daba

@@ -79,6 +79,7 @@ struct IterParams {
   double* cam_alt;     // per camera (32 doubles): MM alternative R t d, its dx, E(k+1), S(k+1)
   int* g_fire;         // 1 if the global test fired in the current iteration
   double* s_dev;       // Nesterov s^(k) on the device (reset_s)
+  int fire_given;      // the reduction takes g_fire as decided (coarse blocks) instead of testing
 };
 
 template <class Real>
@@ -1611,7 +1612,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
   block_sum2(f, n, sf, sn);
   const bool global = P.accelerated && P.restart_global;
   double g = 0.0;
-  if (global) {   // global restart variant: sum over every block of E(k+1) - Fbar(k)
+  if (global && !P.fire_given) {   // global restart variant: sum over every block of E(k+1) - Fbar(k)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) g += P.g_cam[i];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += stride) g += P.g_tile[t];
     __syncthreads();   // thread 0 has read the first sums out of sf / sn
@@ -1647,7 +1648,7 @@ __global__ void __launch_bounds__(FIN_THREADS)
     trace[k] = ft * s2;
     if (global) {
       // the test of Algorithm 1 for the block made of everything: sum E(k+1) > sum Fbar(k)
-      const int fire = gt > 0.0 ? 1 : 0;
+      const int fire = P.fire_given ? *P.g_fire : (gt > 0.0 ? 1 : 0);
       *P.g_fire = fire;
       restarts[k] = fire ? n_blocks : 0;
       if (P.reset_s) {   // Eq. nesterov_scalar continued on the device, s <- 1 after a restart

@@ -98,11 +98,54 @@ def test_blocks_match_oracle_per_iteration(name, accel, K, n_blocks, ctas):
     g.close()
 
 
-@pytest.mark.parametrize("name,n_blocks,iters,ctas", [("circle", 4, 20, 1), ("circle", 8, 20, 0), ("tourism", 8, 20, 1),
-                                                      ("tourism", 8, 6, 0), ("tourism", 32, 20, 0),
-                                                      ("circle", 2, 20, 0), ("circle", 1, 20, 1), ("circle", 1, 20, 0),
-                                                      ("street", 2, 4, 0), ("tourism", 1, 3, 0)])
-def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas):
+@pytest.mark.parametrize("ctas,reset", [(1, False), (1, True), (4, True)])
+def test_blocks_global_restart_trajectory(ctas, reset):
+    """The global restart over coarse blocks (one camera each, with the landmarks it sees first):
+    the objective trace, block metrics and the one decision per iteration against the block
+    oracle for 16 iterations (a restart fires at iteration 12), with and without the momentum
+    reset (s <- 1 after it), on one CTA per block and on clusters; then the iterate."""
+    from paper_2305_07026_b300 import _lib as L
+    sc = _scene("circle_small")
+    part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, sc.M)
+    kw = dict(restart="global", momentum_reset=reset)
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, **kw)
+    prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
+    st = B.init_state(prob, part, R, t, d, l)
+    s2 = prob.s_norm ** 2
+    g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64", **kw)
+    g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+    g.set_block_ctas(ctas)
+    g.set_partition(part.cam_block, part.lm_block, part.S)
+    g.set_state(sc.cams, sc.lms)
+    n_cam_blocks = len(np.unique(part.cam_block))
+    fired = []
+    for k in range(16):
+        st, info = B.step(prob, part, st)
+        tr = np.zeros(2)
+        rs = np.zeros(1, np.int32)
+        g.run(1, tr, rs)
+        assert tr[0] == pytest.approx(info.F * s2, rel=1e-10), f"iteration {k}"
+        F_blk, Fb_blk, rs_blk = g.get_partition_metrics()
+        np.testing.assert_allclose(F_blk, info.F_blk * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_allclose(Fb_blk, info.Fbar_blk * s2, rtol=1e-9, atol=1e-12 * info.F * s2)
+        np.testing.assert_array_equal(rs_blk.astype(bool), info.restart)
+        assert rs[0] == (n_cam_blocks if info.restart.any() else 0)
+        if info.restart.any():
+            fired.append(k)
+    assert fired and fired[0] < 15
+    cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
+    cams_g, lms_g = g.get_state()
+    np.testing.assert_allclose(cams_g, cams_o, rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(lms_g, lms_o, rtol=1e-8, atol=1e-8)
+    g.close()
+
+
+@pytest.mark.parametrize("name,n_blocks,iters,ctas,restart", [(*c, "block") if len(c) == 4 else c for c in [
+    ("circle", 4, 20, 1), ("circle", 8, 20, 0), ("tourism", 8, 20, 1), ("tourism", 8, 6, 0), ("tourism", 32, 20, 0),
+    ("circle", 2, 20, 0), ("circle", 1, 20, 1), ("circle", 1, 20, 0), ("street", 2, 4, 0), ("tourism", 1, 3, 0),
+    # the global restart (fires at iteration 12 on this scene), with and without the momentum reset
+    ("circle_small", 4, 16, 1, "global"), ("circle_small", 2, 16, 0, "reset")]])
+def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas, restart):
     """Every one of `iters` iterations (blocks of up to 60 cameras) from the same state: before each GPU iteration the oracle takes
     the GPU's x^k and x^(k-1) (through the boundary) and its Fbar^alpha(k-1); the oracle's Nesterov
     scalar and E^alpha carry over from its own previous step. Compared after the step: the block
@@ -112,11 +155,13 @@ def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas)
     from paper_2305_07026_b300 import _lib as L
     sc = _scene(name)
     part = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n_blocks)
-    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px)
+    kw = {"block": {}, "global": {"restart": "global"}, "reset": {"restart": "global", "momentum_reset": True}}[restart]
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, **kw)
     prob, R, t, d, l = O.make_problem(sc.cams, sc.lms, sc.cam_idx, sc.lm_idx, sc.uv, opts)
     st = B.init_state(prob, part, R, t, d, l)
     s2 = prob.s_norm ** 2
-    g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64")
+    fired = 0
+    g = L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64", **kw)
     g.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
     g.set_block_ctas(ctas)
     g.set_partition(part.cam_block, part.lm_block, part.S)
@@ -138,6 +183,9 @@ def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas)
         np.testing.assert_allclose(F_blk, info.F_blk * s2, rtol=1e-10, atol=1e-13 * info.F * s2)
         np.testing.assert_allclose(Fb_blk, info.Fbar_blk * s2, rtol=1e-10, atol=1e-13 * info.F * s2)
         tie = np.abs(info.Etest - info.Fbar_blk) <= NEAR_TIE * np.abs(info.F_blk)
+        if restart != "block":   # one decision for all blocks
+            tie[:] = abs(info.Etest.sum() - info.Fbar_blk.sum()) <= NEAR_TIE * abs(info.F_blk.sum())
+            fired += int(info.restart.any())
         assert not ((rs_blk.astype(bool) != info.restart) & ~tie).any(), f"iteration {k}"
         cams_o, lms_o = O.to_boundary(st.R, st.t, st.d, st.l, prob.s_norm)
         cams_g, lms_g = g.get_state()
@@ -153,6 +201,7 @@ def test_multi_camera_blocks_step_from_common_state(name, n_blocks, iters, ctas)
         assert np.max(np.abs(e_g - e_o)) <= 1e-7 * rms, f"iteration {k}"
         np.testing.assert_allclose(lms_g, lms_o, rtol=1e-6, atol=1e-6, err_msg=f"iteration {k}")
     print(name, n_blocks, worst)
+    assert restart == "block" or fired > 0
     g.close()
 
 

@@ -136,11 +136,15 @@ def test_lm_step_never_raises_a_block_surrogate():
     assert np.all(dE <= 0.0) and taken == part.S and np.all(dE < 0.0)
 
 
-@pytest.mark.parametrize("n_blocks,eta", [(4, 0.5), (2, 1.0), (20, 0.5)])
-def test_algorithm1_invariants_with_blocks(n_blocks, eta):
-    """Lemma 1a-c, Eq. FakplFk1 and Eq. FklFk0 every iteration with multi-element blocks."""
+@pytest.mark.parametrize("n_blocks,eta,restart", [(4, 0.5, "block"), (2, 1.0, "block"), (20, 0.5, "block"),
+                                                   (4, 0.5, "global"), (20, 1.0, "global"), (4, 0.5, "reset")])
+def test_algorithm1_invariants_with_blocks(n_blocks, eta, restart):
+    """Lemma 1a-c, Eq. FakplFk1 and Eq. FklFk0 every iteration with multi-element blocks; with the
+    global restart Lemma 1c holds for the sums over the blocks (the test of Algorithm 1 for the one
+    block made of all), every block restarts together, and a restart fires within 15 iterations."""
     sc = _scene()
-    prob, part, R, t, d, l = _problem(sc, n_blocks, eta=eta, xi=1e-8)
+    kw = {"block": {}, "global": {"restart": "global"}, "reset": {"restart": "global", "momentum_reset": True}}[restart]
+    prob, part, R, t, d, l = _problem(sc, n_blocks, eta=eta, xi=1e-8, **kw)
     st = B.init_state(prob, part, R, t, d, l)
     Fbar_global = O.objective(prob.loss, prob.c, R, t, d, l, prob.cam_idx, prob.lm_idx, prob.u)
     nrs = 0
@@ -152,7 +156,13 @@ def test_algorithm1_invariants_with_blocks(n_blocks, eta):
         Fbar_global = (1 - eta) * Fbar_global + eta * F
         assert info.Fbar_blk.sum() == pytest.approx(Fbar_global, rel=1e-11)
         assert np.all(info.F_blk <= prev.E + 1e-12 * np.abs(prev.E))
-        assert np.all(st.E <= info.Fbar_blk + 1e-12 * np.abs(info.Fbar_blk))
+        if restart == "block":
+            assert np.all(st.E <= info.Fbar_blk + 1e-12 * np.abs(info.Fbar_blk))
+        else:
+            assert st.E.sum() <= info.Fbar_blk.sum() * (1 + 1e-12)
+            assert info.restart.all() or not info.restart.any()
+            if restart == "reset" and info.restart.any():
+                assert st.s == 1.0
         Fn = O.objective(prob.loss, prob.c, st.R, st.t, st.d, st.l, prob.cam_idx, prob.lm_idx, prob.u)
         dx2 = O.cam_sqdist(st.R, st.t, st.d, prev.R, prev.t, prev.d).sum() + np.sum((st.l - prev.l) ** 2)
         assert Fn - Fbar_global <= -0.5 * prob.opts.xi * dx2 + 1e-12 * Fbar_global
@@ -160,6 +170,8 @@ def test_algorithm1_invariants_with_blocks(n_blocks, eta):
         if k == 0:
             assert info.gamma == 0.0 and nrs == 0
     assert st.Fbar.sum() < 0.9 * O.objective(prob.loss, prob.c, R, t, d, l, prob.cam_idx, prob.lm_idx, prob.u)
+    if restart != "block":
+        assert nrs > 0
 
 
 @pytest.mark.parametrize("n_blocks", [1, 4])
