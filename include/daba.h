@@ -257,7 +257,7 @@ daba_status daba_get_timing(daba_ctx* ctx, double* ms5);
 daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
 
 /* Coarse blocks (Sec. 4, Eq. Ealpha with E' not empty; FP64 contexts):
- * block b holds the cameras i with cam_block[i] = b (at most 128 per block, none allowed) and the
+ * block b holds the cameras i with cam_block[i] = b (at most 512 per block, none allowed) and the
  * landmarks j with lm_block[j] = b (host or device int32 arrays of M and N entries, block ids in
  * [0, n_blocks), 1 <= n_blocks <= M + N). A reprojection pair whose camera and landmark share a
  * block keeps its exact F_ij in the block's surrogate; every other pair is split by the majorizer
@@ -277,7 +277,7 @@ daba_status daba_set_wait_limit(daba_ctx* ctx, int64_t first_wait_ns);
  * scratch (daba_set_block_ctas; about (9 n_c)^3 / 3 FP64 multiply-adds per damping trial). The restart metrics of Eqs. DEalpha-Eak are per block
  * (daba_get_partition_metrics); the restart count of daba_run counts the blocks that hold a
  * camera. A camera may observe each landmark of its block at most once (DABA_ERR_ARG otherwise,
- * as for a block id out of range or a block of more than 128 cameras). Call after
+ * as for a block id out of range or a block of more than 512 cameras). Call after
  * daba_set_observations (which clears the partition); n_blocks = 0 returns to one block per
  * camera and per landmark (the arrays are then ignored). The device scratch grows with the
  * partition: 888 bytes per intra pair, 248 per landmark, and with global scratch 1752 bytes per

@@ -23,7 +23,7 @@ LOSSES = {"trivial": 0, "huber": 1, "cauchy": 2, "welsch": 3}
 PREC = {"fp64": 0, "mixed": 1}
 RESTART = {"block": 0, "global": 1}
 CAM_SOLVERS = {"scam": 0, "lm": 1}
-BLK_MAX_CAMS = 128   # cameras per coarse block (daba_set_partition)
+BLK_MAX_CAMS = 512   # cameras per coarse block (daba_set_partition)
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"CUDA library {LIB_PATH} is not built; run `python -m paper_2305_07026_b300.build`")

@@ -27,7 +27,7 @@
 
 namespace daba {
 
-constexpr int BLK_MAX_CAMS = 128;    // cameras per block (a Schur matrix of 1152 x 1152)
+constexpr int BLK_MAX_CAMS = 512;    // cameras per block (a Schur matrix of 4608 x 4608, 170 MB)
 constexpr int BLK_SMEM_CAMS = 16;    // up to this many in every block: the block scratch in shared memory
 constexpr int BLK_THREADS = 128;
 

@@ -255,7 +255,8 @@ def test_blocks_arguments():
     assert e.value.status == L.DABA_ERR_ARG
     m.close()
     from paper_2305_07026_b300 import scenes
-    big = scenes.circle_scene(n_cams=L.BLK_MAX_CAMS + 2, n_lms=400, cap=4)
+    big = scenes.circle_scene(n_cams=L.BLK_MAX_CAMS + 100, n_lms=2000, cap=4)
+    assert big.M > L.BLK_MAX_CAMS
     with L.Daba(big.M, big.N, big.nnz, prec="fp64") as d:
         d.set_observations(big.cam_idx, big.lm_idx, big.uv)
         with pytest.raises(L.DabaError) as e:   # all cameras in one block: more than BLK_MAX_CAMS
@@ -272,6 +273,36 @@ def test_blocks_arguments():
         d.set_partition(part.cam_block, part.lm_block, sc.M + sc.N + 1)
     assert e.value.status == L.DABA_ERR_ARG
     d.close()
+
+
+def test_large_block_cluster_matches_one_cta():
+    """A block beyond the oracle's reach (street at a quarter size: 250 cameras and all landmarks
+    in one block, a 2250 x 2250 Schur matrix): a cluster of 16 CTAs against one CTA per block (the
+    same arithmetic up to the rounding order of the block sums) for 3 iterations, Lemma 1a
+    (F^alpha sums to F), and the unaccelerated iteration's monotone objective."""
+    from paper_2305_07026_b300 import _lib as L, partition, scenes
+    sc = scenes.make_scene("street", scale=0.25)
+    cb, lb = partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, 1)
+    out = {}
+    for ctas, accel in ((16, True), (1, True), (16, False)):
+        with L.Daba(sc.M, sc.N, sc.nnz, loss=sc.loss, loss_scale_px=sc.loss_scale_px, prec="fp64",
+                    accelerated=accel) as d:
+            d.set_observations(sc.cam_idx, sc.lm_idx, sc.uv)
+            d.set_block_ctas(ctas)
+            d.set_partition(cb, lb)
+            d.set_state(sc.cams, sc.lms)
+            tr = np.zeros(4)
+            d.run(3, tr)
+            F_blk, _, _ = d.get_partition_metrics()
+            assert F_blk.sum() == pytest.approx(tr[2], rel=1e-11)   # F^alpha(k) of the last iteration
+            out[(ctas, accel)] = (tr, d.get_state())
+    t16, s16 = out[(16, True)]
+    t1, s1 = out[(1, True)]
+    np.testing.assert_allclose(t16, t1, rtol=1e-9)
+    for a, b in zip(s16, s1):
+        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-6)
+    tm = out[(16, False)][0]
+    assert np.all(np.diff(tm) < 0.0)
 
 
 @pytest.mark.parametrize("n_blocks,ctas", [(20, 1), (3, 1), (2, 0)])

@@ -97,7 +97,8 @@ def test_camera_group_partition_helper():
         ref = B.camera_group_partition(sc.M, sc.cam_idx, sc.lm_idx, sc.N, n)
         np.testing.assert_array_equal(cb, ref.cam_block)
         np.testing.assert_array_equal(lb, ref.lm_block)
-    big = scenes.circle_scene(n_cams=260, n_lms=300, cap=4)
-    partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 3)   # 87 cameras per block
+    big = scenes.circle_scene(n_cams=1100, n_lms=2000, cap=4)
+    assert big.M > 2 * partition.BLK_MAX_CAMS
+    partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 3)   # at most 512 cameras per block
     with pytest.raises(ValueError):
-        partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 2)   # 130 cameras per block
+        partition.camera_groups(big.M, big.cam_idx, big.lm_idx, big.N, 2)   # more than 512
