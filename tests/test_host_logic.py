@@ -52,7 +52,7 @@ def test_autotune_coordinate_descent(monkeypatch):
     from paper_2305_07026_b300 import autotune
     cost = {}
 
-    def fake(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2):
+    def fake(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2, repeats=1):
         key = (sched["chunk_obs"], sched["tile_obs"], sched["tile_lms"], sched["ranges"])
         cost[key] = cost.get(key, 0) + 1
         return abs(key[0] - 4096) / 1e3 + abs(key[1] - 256) / 1e2 + abs(key[2] - 64) / 10.0 + abs(key[3] - 4)
@@ -62,6 +62,29 @@ def test_autotune_coordinate_descent(monkeypatch):
     assert best == {"chunk_obs": 4096, "tile_obs": 256, "tile_lms": 64, "ranges": 4}
     assert all(v == 1 for v in cost.values())
     assert len(tried) == len(cost)
+
+
+def test_autotune_sweeps_until_no_axis_changes(monkeypatch):
+    """Interacting axes: the best chunk depends on the number of ranges, which the first sweep
+    settles last. A second sweep moves the chunk, a third changes nothing and ends the search;
+    the result is the grid's optimum and no schedule is timed twice."""
+    from paper_2305_07026_b300 import autotune
+    cost = {}
+
+    def fake(L, cams, lms, cam_idx, lm_idx, uv, opts, sched, iters=8, warmup=2, repeats=1):
+        key = (sched["chunk_obs"], sched["tile_obs"], sched["tile_lms"], sched["ranges"])
+        cost[key] = cost.get(key, 0) + 1
+        want_chunk = 2048 if key[3] < 4 else 4096
+        return abs(key[3] - 4) + abs(key[0] - want_chunk) / 1e4 + abs(key[1] - 512) / 1e5 + abs(key[2] - 128) / 1e5
+    monkeypatch.setattr(autotune, "time_schedule", fake)
+    z = np.zeros((1, 9))
+    args = (z, np.zeros((1, 3)), np.zeros(1, np.int32), np.zeros(1, np.int32), np.zeros((1, 2)))
+    best, tried = autotune.tune(*args)
+    assert best == {"chunk_obs": 4096, "tile_obs": 512, "tile_lms": 128, "ranges": 4}
+    assert all(v == 1 for v in cost.values()) and len(tried) == len(cost)
+    cost.clear()
+    one, _ = autotune.tune(*args, max_sweeps=1)   # a single sweep stops at the first chunk
+    assert one == {"chunk_obs": 2048, "tile_obs": 512, "tile_lms": 128, "ranges": 4}
 
 
 def test_autotune_context_takes_the_cut(monkeypatch):
