@@ -422,6 +422,7 @@ def run_ours(args, rank, world, local):
     # ---- timed region: K iterations of the mixed path, inputs resident in HBM
     d = make("mixed")
     d.run(max(W, K), stream=sp)   # warm-up of the timed length: captures its graph
+    mem_bytes, mem_peak = d.device_bytes()
     d.set_state(sc.cams, sc.lms, stream=sp)   # the timed run starts again from x^(0)
     clocks = Clocks()
     torch.cuda.synchronize()
@@ -626,7 +627,10 @@ def run_ours(args, rank, world, local):
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 per observation, f64 reductions/solves", "data": "synthetic",
         "config": tourism_config(sc, world), "gpu_launches": int(launches), "clocks": ck,
-        "cpu_baseline": cpu, "e2e": e2e, "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e,
+        "memory": {"context_bytes": mem_bytes, "peak_bytes": mem_peak, "bytes_per_observation": mem_bytes / sc.nnz,
+                   "what": "device buffers of the MIXED context (daba_device_bytes)"},
+        "roofline": roofline,
     }
     out.update(extra)
     # the accuracy gate last, so that it stays in view at the end of the line

@@ -342,6 +342,17 @@ daba_status daba_set_pipeline(daba_ctx* ctx, const daba_pipeline* p);
 /* Number of kernel launches the library issued in the last daba_run. */
 int64_t daba_last_launch_count(const daba_ctx* ctx);
 
+/* Device memory of a context (Sec. 7, memory and communication: the paper reports the most
+ * memory a device uses). *bytes = the bytes of the device buffers the context holds now (its
+ * own, plus those of the FP64 context it creates for the reverse mode of a MIXED context);
+ * *peak = the most it has held at once (with such an FP64 context, the sum of both peaks, an
+ * upper bound). Counts the library's own allocations, not the CUDA runtime's memory for
+ * graphs, streams and module code. Buffers are allocated by daba_create (sized by M, N and
+ * nnz) and by the calls that first need more (daba_set_partition and
+ * daba_unrolled_grad); daba_run allocates none. Either pointer may be NULL (not both:
+ * DABA_ERR_ARG, as for a NULL context). Host pointers; no GPU work. */
+daba_status daba_device_bytes(const daba_ctx* ctx, int64_t* bytes, int64_t* peak);
+
 /* The objective in pixel^2 of caller-provided device arrays (the value daba_objective returns
  * for a context holding the same cameras, landmarks and observations), allocating no device
  * memory. The paper has no counterpart: this entry point exists for callers that cannot call

@@ -72,6 +72,7 @@ _SIGS = {
     "daba_set_timing": (_st, [_p, ctypes.c_int]),
     "daba_get_timing": (_st, [_p, _p]),
     "daba_last_launch_count": (_i64, [_p]),
+    "daba_device_bytes": (_st, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "daba_objective_noalloc": (_st, [_i32, _i32, _i64, _p, _p, _p, _p, _p, _i32, ctypes.c_double, ctypes.c_double,
                                      _p, _p]),
     "daba_probe_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
@@ -308,6 +309,12 @@ class Daba:
 
     def last_launch_count(self) -> int:
         return int(daba_last_launch_count(self._h))
+
+    def device_bytes(self):
+        """(bytes of device buffers held now, the most held at once) by this context."""
+        b, pk = ctypes.c_int64(), ctypes.c_int64()
+        self._check(daba_device_bytes(self._h, ctypes.byref(b), ctypes.byref(pk)))
+        return int(b.value), int(pk.value)
 
 
 def probe_fma_rate(kind):

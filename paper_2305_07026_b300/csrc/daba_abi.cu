@@ -80,7 +80,8 @@ struct daba_ctx {
   // device copies of the camera order (device position -> input index) and of the internal ->
   // external landmark map (gradient outputs, pixel updates)
   void *d_ci_order = nullptr, *d_lperm = nullptr;
-  std::vector<void*> allocs;
+  std::vector<std::pair<void*, size_t>> allocs;   // device buffers of this context and their sizes
+  size_t dev_bytes = 0, dev_peak = 0;              // bytes they hold now, and the most held at once
   std::vector<cudaEvent_t> events;
   cudaStream_t s_hi = nullptr, s_lo = nullptr;   // camera pass + solves (high priority), landmark pass
   cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
@@ -194,7 +195,9 @@ daba_status dalloc(daba_ctx* ctx, void** p, size_t bytes) {
     *p = nullptr;
     return fail(ctx, DABA_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
   }
-  ctx->allocs.push_back(*p);
+  ctx->allocs.emplace_back(*p, bytes);
+  ctx->dev_bytes += bytes;
+  ctx->dev_peak = std::max(ctx->dev_peak, ctx->dev_bytes);
   return DABA_OK;
 }
 
@@ -206,7 +209,12 @@ daba_status dgrow(daba_ctx* ctx, void** p, size_t bytes) {
   if (*p && it != cap.end() && it->second >= bytes) return DABA_OK;
   if (*p) {
     if (it != cap.end()) cap.erase(it);
-    ctx->allocs.erase(std::remove(ctx->allocs.begin(), ctx->allocs.end(), *p), ctx->allocs.end());
+    auto a = std::find_if(ctx->allocs.begin(), ctx->allocs.end(),
+                          [&](const std::pair<void*, size_t>& x) { return x.first == *p; });
+    if (a != ctx->allocs.end()) {
+      ctx->dev_bytes -= a->second;
+      ctx->allocs.erase(a);
+    }
     cudaFree(*p);
     *p = nullptr;
   }
@@ -1372,13 +1380,25 @@ const char* daba_last_error(const daba_ctx* ctx) { return ctx ? ctx->err.c_str()
 
 int64_t daba_last_launch_count(const daba_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+daba_status daba_device_bytes(const daba_ctx* ctx, int64_t* bytes, int64_t* peak) {
+  if (!ctx || (!bytes && !peak)) return DABA_ERR_ARG;
+  size_t b = ctx->dev_bytes, pk = ctx->dev_peak;
+  if (ctx->shadow) {   // the FP64 context owned for the reverse mode of a MIXED context
+    b += ctx->shadow->dev_bytes;
+    pk += ctx->shadow->dev_peak;
+  }
+  if (bytes) *bytes = (int64_t)b;
+  if (peak) *peak = (int64_t)pk;
+  return DABA_OK;
+}
+
 void daba_destroy(daba_ctx* ctx) {
   if (!ctx) return;
   if (ctx->s_hi) cudaStreamSynchronize(ctx->s_hi);
   if (ctx->s_lo) cudaStreamSynchronize(ctx->s_lo);
   if (ctx->s_cap) cudaStreamSynchronize(ctx->s_cap);
   drop_graphs(ctx);
-  for (void* p : ctx->allocs) cudaFree(p);
+  for (const auto& a : ctx->allocs) cudaFree(a.first);
   for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
   for (cudaEvent_t e : {ctx->ev_fork, ctx->ev_hi, ctx->ev_lo, ctx->ev_cap0, ctx->ev_cap1})
     if (e) cudaEventDestroy(e);

@@ -113,3 +113,38 @@ def test_nonfinite_iterate_leaves_state(prec, iters):
     np.testing.assert_array_equal(d.get_state()[1], ref.get_state()[1])
     d.close()
     ref.close()
+
+
+def test_device_bytes_count_the_context_buffers():
+    """daba_device_bytes: the buffers a context allocates are at least the observation arrays
+    and both landmark buffers, the device's free memory falls by at least that much when they
+    are allocated, daba_run allocates nothing, a coarse-block partition and the reverse mode
+    add their buffers, and the peak never falls below what is held."""
+    from paper_2305_07026_b300 import _lib as L
+    from paper_2305_07026_b300 import partition
+    sc = cached_scene("street", scale=0.2)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    d = _ctx(sc, "fp64")
+    try:
+        b0, p0 = d.device_bytes()
+        free1 = torch.cuda.mem_get_info()[0]
+        # per observation at least its landmark index and pixel; per landmark two FP64 records
+        assert b0 >= sc.nnz * (4 + 16) + sc.N * 2 * 3 * 8
+        assert free0 - free1 >= b0
+        assert p0 == b0
+        d.run(12)
+        assert d.device_bytes() == (b0, p0)
+        cb, lb = partition.camera_groups(sc.M, sc.cam_idx, sc.lm_idx, sc.N, (sc.M + 7) // 8)
+        d.set_partition(cb, lb)
+        b1, p1 = d.device_bytes()
+        assert b1 > b0 and p1 >= b1
+        d.set_partition(None)   # the block buffers stay for the next partition
+        rng = np.random.default_rng(0)
+        d.set_state(sc.cams, sc.lms)   # the reverse mode starts from a state just set
+        d.unrolled_grad(10, rng.normal(size=(sc.M, 9)), rng.normal(size=(sc.N, 3)))
+        b2, p2 = d.device_bytes()
+        assert b2 > b1 and p2 == max(p1, b2)
+    finally:
+        d.close()
+    assert L.daba_device_bytes(None, None, None) == L.DABA_ERR_ARG
