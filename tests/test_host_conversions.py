@@ -118,3 +118,41 @@ def test_device_nesterov_scalar_is_the_oracles(tmp_path):
     for _ in range(n):
         ref.append(float(O.nesterov(ref[-1])[0]))
     assert _same_bits(dev, np.array(ref))
+
+
+def test_double_float_addition_against_exact_sums(tmp_path):
+    """df_add, the (hi, lo) FP32-pair update of the MIXED landmark state: for seeded pairs with
+    |lo| <= ulp(hi)/2 and steps from 1e-9 |hi| to 10 |hi| (both signs, exact cancellation, zero
+    and steps below ulp(lo) included), the new pair sums to hi + lo + x within 2^-46 of the
+    larger of |hi| and |x| (exact rational arithmetic), and its low part is at most half an ulp
+    of its high part."""
+    import struct
+    from fractions import Fraction
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path / "df_add")
+    build = subprocess.run([gxx, *FLAGS, os.path.join(HOST, "df_add.cpp"), "-o", exe], capture_output=True, text=True)
+    assert build.returncode == 0, build.stderr[-4000:]
+    rng = np.random.default_rng(17)
+    n = 4000
+    hi = (rng.uniform(-100, 100, n) * 10.0 ** rng.uniform(-3, 2, n)).astype(np.float32)
+    ulp = np.spacing(np.abs(hi)).astype(np.float32)
+    lo = (rng.uniform(-0.5, 0.5, n) * ulp).astype(np.float32)
+    x = (hi.astype(np.float64) * rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-9, 1, n)).astype(np.float32)
+    x[0::50] = -hi[0::50]                        # exact cancellation of the high part
+    x[1::50] = 0.0
+    x[2::50] = (lo[2::50] * np.float32(1e-3))    # below the low part's ulp
+    bits = lambda a: a.view(np.uint32)
+    stdin = f"{n}\n" + "\n".join(f"{h:08x} {l:08x} {v:08x}" for h, l, v in zip(bits(hi), bits(lo), bits(x))) + "\n"
+    run = subprocess.run([exe], input=stdin, capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr[-2000:]
+    out = np.array([[int(w, 16) for w in line.split()] for line in run.stdout.splitlines()], dtype=np.uint32)
+    h2, l2 = out[:, 0].view(np.float32), out[:, 1].view(np.float32)
+    f = lambda v: Fraction(struct.unpack("<f", struct.pack("<f", float(v)))[0])
+    for i in range(n):
+        exact = f(hi[i]) + f(lo[i]) + f(x[i])
+        got = f(h2[i]) + f(l2[i])
+        bound = Fraction(2) ** -46 * max(abs(f(hi[i])), abs(f(x[i])), Fraction(1, 2 ** 100))
+        assert abs(got - exact) <= bound, (i, float(got - exact), float(bound))
+        assert abs(float(l2[i])) <= 0.5 * float(np.spacing(np.abs(h2[i]))), i
