@@ -57,13 +57,13 @@ def _iteration(scene, opts, k):
     return prob, st, gamma, li, rec, new, info
 
 
-def _device(exe, prob, st, gamma, li, rec, first, opts):
+def _device(exe, prob, st, gamma, li, rec, first, opts, bits=64):
     N = prob.N
     order = np.argsort(li, kind="stable")
     ptr = np.concatenate([[0], np.cumsum(np.bincount(li, minlength=N))])
     dl = st.l - st.lp
     S = np.zeros(N) if first else st.Fbar_lm - st.E_lm
-    lines = [f"{N} {int(first)} {float(gamma)!r} {float(opts.xi)!r} {float(opts.eta)!r} {int(opts.accelerated)}"]
+    lines = [f"{bits} {N} {int(first)} {float(gamma)!r} {float(opts.xi)!r} {float(opts.eta)!r} {int(opts.accelerated)}"]
     for j in range(N):
         rows = rec[order[ptr[j]:ptr[j + 1]]]
         head = [*st.l[j], *dl[j], S[j], st.E_lm[j]]
@@ -104,3 +104,28 @@ def test_landmark_pass_matches_oracle_iteration(lm_pass, k, xi):
     np.testing.assert_allclose(step[same], (new.l - st.l)[same], rtol=0, atol=1e-10)
     np.testing.assert_allclose(E_next[same], new.E_lm[same], rtol=0, atol=1e-12 * scale)
     np.testing.assert_allclose(S_next[same], (new.Fbar_lm - new.E_lm)[same], rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("xi,k", [(1e-10, 0), (1e-10, 8), (0.5, 12)])
+def test_mixed_landmark_pass_within_fp32_bounds(lm_pass, k, xi):
+    """The MIXED instantiation (records, slack and step in FP32; the landmark as an FP32 high
+    and low part) on the same records rounded to FP32: the new landmark within 1e-5 of the
+    oracle's step (measured: at most 1.7e-6, a few FP32 ulps of the step, while the landmark
+    itself keeps the 48-bit precision of its high and low parts), the next slack within 1e-6
+    of the largest Fbar (measured 9e-9), and the restart decisions equal wherever the oracle's
+    test margin is above 1e-5 of the largest Fbar (FP32 sums cannot resolve closer calls)."""
+    sc = cached_scene("circle")
+    opts = O.Options(loss=sc.loss, loss_scale_px=sc.loss_scale_px, xi=xi)
+    prob, st, gamma, li, rec, new, info = _iteration(sc, opts, k)
+    out = _device(lm_pass, prob, st, gamma, li, rec, k == 0, opts, bits=32)
+    lnew, S_next, rs = out[:, 0:3], out[:, 6], out[:, 10].astype(bool)
+    scale = np.abs(info.Fbar_lm).max()
+    clear = np.abs(info.Etest_lm - info.Fbar_lm) > 1e-5 * scale
+    assert clear.mean() > 0.8
+    np.testing.assert_array_equal(rs[clear], info.restart_lm[clear])
+    same = rs == info.restart_lm
+    step = np.abs(new.l - st.l).max(axis=1, keepdims=True)
+    err = np.abs(lnew - new.l)
+    # the FP32 step (1e-5 of its size) added to the high and low parts without further loss
+    assert (err[same] <= 1e-5 * step[same] + 1e-12).all(), (err[same] / (step[same] + 1e-30)).max()
+    np.testing.assert_allclose(S_next[same], (new.Fbar_lm - new.E_lm)[same], rtol=0, atol=1e-6 * scale)
