@@ -30,7 +30,7 @@ def cam_pass(tmp_path_factory):
     return exe
 
 
-def _run(exe, scene, opts, k):
+def _run(exe, scene, opts, k, bits=64):
     prob, R, t, d, l = O.make_problem(scene.cams, scene.lms, scene.cam_idx, scene.lm_idx, scene.uv, opts)
     st = O.init_state(prob, R, t, d, l)
     for _ in range(k):
@@ -44,7 +44,7 @@ def _run(exe, scene, opts, k):
     ptr = np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=M))])
     first = k == 0
     S = np.zeros(M) if first else st.Fbar_cam - st.E_cam
-    head = (f"{LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
+    head = (f"{bits} {LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
             f"{int(opts.accelerated)} {int(first)} {float(gamma)!r} {float(gamma_next)!r} {M}")
     lines = [head]
     for i in range(M):
@@ -89,3 +89,32 @@ def test_camera_half_matches_oracle_iteration(cam_pass, loss, xi, k):
     np.testing.assert_allclose(x[same], want[same], rtol=0, atol=1e-9)
     np.testing.assert_allclose(E_next[same], new.E_cam[same], rtol=0, atol=1e-10 * scale)
     np.testing.assert_allclose(S_next[same], (new.Fbar_cam - new.E_cam)[same], rtol=0, atol=1e-10 * scale)
+
+
+@pytest.mark.parametrize("loss,xi,k", [("huber", 1e-10, 0), ("huber", 1e-10, 12), ("cauchy", 0.5, 6),
+                                       ("huber", 0.5, 16)])
+def test_mixed_camera_half_within_fp32_bounds(cam_pass, loss, xi, k):
+    """The MIXED instantiation (statistics evaluated and accumulated in FP32, the FP32 S-CAM
+    solve on displacements added to the FP64 camera state, FP64 restart metrics) against the
+    same oracle step. Bounds from the FP32 arithmetic, with the measured worst in brackets:
+    camera parameters within 2e-5 (7e-6, the FP32 solve), F^(k) and Fbar^(k) within 5e-6 of the
+    largest Fbar (8e-7, FP32 per-observation terms), E^(k+1) and the next slack within 1e-5
+    (2e-6), the F_ij sums within 5e-6 relative (1e-6), restart decisions equal where the
+    oracle's margin exceeds 1e-4 of the largest Fbar."""
+    sc = cached_scene("circle")
+    opts = O.Options(loss=loss, loss_scale_px=sc.loss_scale_px, xi=xi)
+    st, new, info, out, Fsum = _run(cam_pass, sc, opts, k, bits=32)
+    x = out[:, :15]
+    F, Fbar, E_next, S_next, rs, Fs = out[:, 15], out[:, 16], out[:, 17], out[:, 18], out[:, 19] > 0.5, out[:, 20]
+    scale = np.abs(info.Fbar_cam).max()
+    np.testing.assert_allclose(Fs, Fsum, rtol=5e-6)
+    np.testing.assert_allclose(F, info.F_cam, rtol=0, atol=5e-6 * scale)
+    np.testing.assert_allclose(Fbar, info.Fbar_cam, rtol=0, atol=5e-6 * scale)
+    clear = np.abs(info.Etest_cam - info.Fbar_cam) > 1e-4 * scale
+    assert clear.mean() > 0.8
+    np.testing.assert_array_equal(rs[clear], info.restart_cam[clear])
+    same = rs == info.restart_cam
+    want = np.concatenate([new.R.reshape(-1, 9), new.t, new.d], 1)
+    np.testing.assert_allclose(x[same], want[same], rtol=0, atol=2e-5)
+    np.testing.assert_allclose(E_next[same], new.E_cam[same], rtol=0, atol=1e-5 * scale)
+    np.testing.assert_allclose(S_next[same], (new.Fbar_cam - new.E_cam)[same], rtol=0, atol=1e-5 * scale)
