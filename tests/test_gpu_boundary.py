@@ -122,7 +122,9 @@ def test_device_bytes_count_the_context_buffers():
     add their buffers, and the peak never falls below what is held."""
     from paper_2305_07026_b300 import _lib as L
     from paper_2305_07026_b300 import partition
+    import gc
     sc = cached_scene("street", scale=0.2)
+    gc.collect()   # no earlier context is freed by a finalizer between the two readings below
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     d = _ctx(sc, "fp64")
