@@ -34,6 +34,11 @@ inline void __syncthreads() {}
 inline void __threadfence() {}
 inline int atomicOr(int* p, int v) { const int o = *p; *p |= v; return o; }
 inline int atomicMin(int* p, int v) { const int o = *p; *p = std::min(o, v); return o; }
+inline unsigned long long atomicMin(unsigned long long* p, unsigned long long v) {
+  const unsigned long long o = *p;
+  *p = std::min(o, v);
+  return o;
+}
 inline unsigned atomicAdd(unsigned* p, unsigned v) { const unsigned o = *p; *p += v; return o; }
 inline float __fdividef(float a, float b) { return a / b; }
 inline float rsqrtf(float a) { return 1.0f / std::sqrt(a); }
