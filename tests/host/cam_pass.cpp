@@ -9,10 +9,13 @@
 // With bits = 32 the MIXED instantiation runs: statistics evaluated and accumulated in FP32
 // (one chunk per camera), the FP32 S-CAM solve on displacements added to the FP64 state, FP64
 // restart metrics.
-// stdin: "bits loss c xi eta n_alt accelerated first gamma gamma_next M", then per camera
+// With global = 1 the global restart variant runs: no per-block test, the accelerated solution
+// kept, the MM alternative and E, S after a restart in cam_alt, E^(k+1) - Fbar^(k) in g_cam.
+// stdin: "bits global loss c xi eta n_alt accelerated first gamma gamma_next M", then per camera
 // "m", R^k (9, row-major) t^k (3) d^k (3) R^(k-1) (9) t^(k-1) (3) d^(k-1) (3) Rbar (9) S E,
 // then m lines l^k (3) l^(k-1) (3) u (2). stdout per camera: R t d of x^(k+1) (15), F^(k),
-// Fbar^(k), E^(k+1), the next slack, restarted, sum of F_ij(x^k).
+// Fbar^(k), E^(k+1), the next slack, restarted, sum of F_ij(x^k); with global = 1 also the
+// camera's term of the global test and its MM alternative R t d, E, S (18).
 #include "../../paper_2305_07026_b300/csrc/daba_kernels.cuh"
 
 #include <cstdio>
@@ -46,7 +49,7 @@ bool camera_stats(double c, double gamma, const CamT<double>& x, const CamT<doub
 }
 
 template <class Real>
-int run(int loss, double c, double xi, double eta, int n_alt, int accelerated, int first, double gamma,
+int run(int global, int loss, double c, double xi, double eta, int n_alt, int accelerated, int first, double gamma,
         double gamma_next, int M) {
   std::vector<Real> part((size_t)M * CP_STRIDE, Real(0));
   std::vector<double> cam_x((size_t)M * CSTRIDE, 0.0), cam_dx((size_t)M * CSTRIDE, 0.0), cam_Rbar((size_t)M * 9),
@@ -88,7 +91,9 @@ int run(int loss, double c, double xi, double eta, int n_alt, int accelerated, i
   IterParams P{};
   P.gam = gam, P.xi = xi, P.eta = eta, P.eta1 = 1.0 - eta, P.hxi = 0.5 * xi;
   P.eta1f = float(1.0 - eta), P.hxif = float(0.5 * xi);
-  P.accelerated = accelerated, P.n_alt = n_alt, P.restart_global = 0;
+  P.accelerated = accelerated, P.n_alt = n_alt, P.restart_global = global;
+  std::vector<double> cam_alt((size_t)M * 32, 0.0), g_cam(M, 0.0);
+  P.cam_alt = cam_alt.data(), P.g_cam = g_cam.data();
   double sh_mm[32][16];
   for (int i = 0; i < M; ++i)
     for (int role = 1; role >= 0; --role)
@@ -99,18 +104,25 @@ int run(int loss, double c, double xi, double eta, int n_alt, int accelerated, i
   for (int i = 0; i < M; ++i) {
     const double* xs = &cam_x[(size_t)i * CSTRIDE];
     for (int a = 0; a < 15; ++a) std::printf("%.17g ", xs[a]);
-    std::printf("%.17g %.17g %.17g %.17g %d %.17g\n", cam_F[i], cam_Fb[i], cam_E[i], cam_S[i], (int)cam_rs[i],
+    std::printf("%.17g %.17g %.17g %.17g %d %.17g", cam_F[i], cam_Fb[i], cam_E[i], cam_S[i], (int)cam_rs[i],
                 cam_Fsum[i]);
+    if (global) {
+      const double* a = &cam_alt[(size_t)i * 32];
+      std::printf(" %.17g", g_cam[i]);
+      for (int q = 0; q < 15; ++q) std::printf(" %.17g", a[q]);
+      std::printf(" %.17g %.17g", a[30], a[31]);
+    }
+    std::printf("\n");
   }
   return 0;
 }
 
 int main() {
-  int bits, loss, n_alt, accelerated, first, M;
+  int bits, global, loss, n_alt, accelerated, first, M;
   double c, xi, eta, gamma, gamma_next;
-  if (std::scanf("%d %d %lf %lf %lf %d %d %d %lf %lf %d", &bits, &loss, &c, &xi, &eta, &n_alt, &accelerated, &first,
-                 &gamma, &gamma_next, &M) != 11)
+  if (std::scanf("%d %d %d %lf %lf %lf %d %d %d %lf %lf %d", &bits, &global, &loss, &c, &xi, &eta, &n_alt,
+                 &accelerated, &first, &gamma, &gamma_next, &M) != 12)
     return 1;
-  return bits == 32 ? run<float>(loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M)
-                    : run<double>(loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M);
+  return bits == 32 ? run<float>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M)
+                    : run<double>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M);
 }

@@ -30,7 +30,7 @@ def cam_pass(tmp_path_factory):
     return exe
 
 
-def _run(exe, scene, opts, k, bits=64):
+def _run(exe, scene, opts, k, bits=64, glob=0):
     prob, R, t, d, l = O.make_problem(scene.cams, scene.lms, scene.cam_idx, scene.lm_idx, scene.uv, opts)
     st = O.init_state(prob, R, t, d, l)
     for _ in range(k):
@@ -44,7 +44,7 @@ def _run(exe, scene, opts, k, bits=64):
     ptr = np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=M))])
     first = k == 0
     S = np.zeros(M) if first else st.Fbar_cam - st.E_cam
-    head = (f"{bits} {LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
+    head = (f"{bits} {glob} {LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
             f"{int(opts.accelerated)} {int(first)} {float(gamma)!r} {float(gamma_next)!r} {M}")
     lines = [head]
     for i in range(M):
@@ -57,7 +57,7 @@ def _run(exe, scene, opts, k, bits=64):
     run = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300)
     assert run.returncode == 0, run.stderr[-2000:]
     out = np.array([[float(x) for x in line.split()] for line in run.stdout.splitlines()])
-    assert out.shape == (M, 21)
+    assert out.shape == (M, 39 if glob else 21)
     Fij = O.F_obs(prob.loss, prob.c, st.R[ci], st.t[ci], st.d[ci], st.l[li], u)
     return st, new, info, out, O.segsum(ci, Fij, M)
 

@@ -57,13 +57,13 @@ def _iteration(scene, opts, k):
     return prob, st, gamma, li, rec, new, info
 
 
-def _device(exe, prob, st, gamma, li, rec, first, opts, bits=64):
+def _device(exe, prob, st, gamma, li, rec, first, opts, bits=64, glob=0):
     N = prob.N
     order = np.argsort(li, kind="stable")
     ptr = np.concatenate([[0], np.cumsum(np.bincount(li, minlength=N))])
     dl = st.l - st.lp
     S = np.zeros(N) if first else st.Fbar_lm - st.E_lm
-    lines = [f"{bits} {N} {int(first)} {float(gamma)!r} {float(opts.xi)!r} {float(opts.eta)!r} {int(opts.accelerated)}"]
+    lines = [f"{bits} {glob} {N} {int(first)} {float(gamma)!r} {float(opts.xi)!r} {float(opts.eta)!r} {int(opts.accelerated)}"]
     for j in range(N):
         rows = rec[order[ptr[j]:ptr[j + 1]]]
         head = [*st.l[j], *dl[j], S[j], st.E_lm[j]]
@@ -72,7 +72,7 @@ def _device(exe, prob, st, gamma, li, rec, first, opts, bits=64):
     run = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300)
     assert run.returncode == 0, run.stderr[-2000:]
     out = np.array([[float(x) for x in line.split()] for line in run.stdout.splitlines()])
-    assert out.shape == (N, 11)
+    assert out.shape == (N, 17 if glob else 11)
     return out
 
 
