@@ -11,7 +11,8 @@
 // restart metrics.
 // With global = 1 the global restart variant runs: no per-block test, the accelerated solution
 // kept, the MM alternative and E, S after a restart in cam_alt, E^(k+1) - Fbar^(k) in g_cam.
-// stdin: "bits global loss c xi eta n_alt accelerated first gamma gamma_next M", then per camera
+// With lm = 1 the camera solver is the LM variant (one successful Levenberg-Marquardt step).
+// stdin: "bits global lm loss c xi eta n_alt accelerated first gamma gamma_next M", then per camera
 // "m", R^k (9, row-major) t^k (3) d^k (3) R^(k-1) (9) t^(k-1) (3) d^(k-1) (3) Rbar (9) S E,
 // then m lines l^k (3) l^(k-1) (3) u (2). stdout per camera: R t d of x^(k+1) (15), F^(k),
 // Fbar^(k), E^(k+1), the next slack, restarted, sum of F_ij(x^k); with global = 1 also the
@@ -48,7 +49,7 @@ bool camera_stats(double c, double gamma, const CamT<double>& x, const CamT<doub
   return true;
 }
 
-template <class Real>
+template <class Real, int SOLVER>
 int run(int global, int loss, double c, double xi, double eta, int n_alt, int accelerated, int first, double gamma,
         double gamma_next, int M) {
   std::vector<Real> part((size_t)M * CP_STRIDE, Real(0));
@@ -97,7 +98,7 @@ int run(int global, int loss, double c, double xi, double eta, int n_alt, int ac
   double sh_mm[32][16];
   for (int i = 0; i < M; ++i)
     for (int role = 1; role >= 0; --role)
-      camsolve_group<Real, CAM_SCAM, false>(i / 32, role, i % 32, sh_mm, 0, first, 0, M, chunk_ptr.data(),
+      camsolve_group<Real, SOLVER, false>(i / 32, role, i % 32, sh_mm, 0, first, 0, M, chunk_ptr.data(),
                                             part.data(), cam_x.data(), cam_dx.data(), cam_Rbar.data(), P,
                                             cam_S.data(), cam_E.data(), cam_F.data(), cam_Fb.data(), cam_rs.data(),
                                             cam_Fsum.data(), pack_next.data());
@@ -118,11 +119,14 @@ int run(int global, int loss, double c, double xi, double eta, int n_alt, int ac
 }
 
 int main() {
-  int bits, global, loss, n_alt, accelerated, first, M;
+  int bits, global, lm, loss, n_alt, accelerated, first, M;
   double c, xi, eta, gamma, gamma_next;
-  if (std::scanf("%d %d %d %lf %lf %lf %d %d %d %lf %lf %d", &bits, &global, &loss, &c, &xi, &eta, &n_alt,
-                 &accelerated, &first, &gamma, &gamma_next, &M) != 12)
+  if (std::scanf("%d %d %d %d %lf %lf %lf %d %d %d %lf %lf %d", &bits, &global, &lm, &loss, &c, &xi, &eta, &n_alt,
+                 &accelerated, &first, &gamma, &gamma_next, &M) != 13)
     return 1;
-  return bits == 32 ? run<float>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M)
-                    : run<double>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M);
+  if (lm)
+    return bits == 32 ? run<float, CAM_LM>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M)
+                      : run<double, CAM_LM>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M);
+  return bits == 32 ? run<float, CAM_SCAM>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M)
+                    : run<double, CAM_SCAM>(global, loss, c, xi, eta, n_alt, accelerated, first, gamma, gamma_next, M);
 }

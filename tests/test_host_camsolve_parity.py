@@ -31,6 +31,7 @@ def cam_pass(tmp_path_factory):
 
 
 def _run(exe, scene, opts, k, bits=64, glob=0):
+    lm = int(opts.cam_solver == "lm")
     prob, R, t, d, l = O.make_problem(scene.cams, scene.lms, scene.cam_idx, scene.lm_idx, scene.uv, opts)
     st = O.init_state(prob, R, t, d, l)
     for _ in range(k):
@@ -44,7 +45,7 @@ def _run(exe, scene, opts, k, bits=64, glob=0):
     ptr = np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=M))])
     first = k == 0
     S = np.zeros(M) if first else st.Fbar_cam - st.E_cam
-    head = (f"{bits} {glob} {LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
+    head = (f"{bits} {glob} {lm} {LOSSES[prob.loss]} {float(prob.c)!r} {float(opts.xi)!r} {float(opts.eta)!r} {opts.cam_alternations} "
             f"{int(opts.accelerated)} {int(first)} {float(gamma)!r} {float(gamma_next)!r} {M}")
     lines = [head]
     for i in range(M):
@@ -118,3 +119,30 @@ def test_mixed_camera_half_within_fp32_bounds(cam_pass, loss, xi, k):
     np.testing.assert_allclose(x[same], want[same], rtol=0, atol=2e-5)
     np.testing.assert_allclose(E_next[same], new.E_cam[same], rtol=0, atol=1e-5 * scale)
     np.testing.assert_allclose(S_next[same], (new.Fbar_cam - new.E_cam)[same], rtol=0, atol=1e-5 * scale)
+
+
+@pytest.mark.parametrize("loss,xi,k", [("huber", 1e-10, 0), ("huber", 1e-10, 12), ("cauchy", 0.5, 6),
+                                       ("huber", 0.5, 13)])
+def test_lm_camera_solver_matches_oracle_iteration(cam_pass, loss, xi, k):
+    """The LM camera solver variant (one successful Levenberg-Marquardt step per camera block on
+    the Gauss-Newton model of its surrogate) in the same group function, FP64, against the
+    oracle's step with cam_solver="lm", at the first iteration and at ones where 6-8 camera
+    blocks restart: the same quantities and tolerances as the S-CAM test."""
+    sc = cached_scene("circle")
+    opts = O.Options(loss=loss, loss_scale_px=sc.loss_scale_px, xi=xi, cam_solver="lm")
+    st, new, info, out, Fsum = _run(cam_pass, sc, opts, k)
+    x = out[:, :15]
+    F, Fbar, E_next, S_next, rs = out[:, 15], out[:, 16], out[:, 17], out[:, 18], out[:, 19] > 0.5
+    scale = np.abs(info.Fbar_cam).max()
+    np.testing.assert_allclose(F, info.F_cam, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(Fbar, info.Fbar_cam, rtol=0, atol=1e-11 * scale)
+    clear = np.abs(info.Etest_cam - info.Fbar_cam) > 1e-8 * scale
+    assert clear.mean() > 0.8
+    np.testing.assert_array_equal(rs[clear], info.restart_cam[clear])
+    if k > 0:
+        assert info.restart_cam.sum() >= 5 and (~info.restart_cam).any()
+    same = rs == info.restart_cam
+    want = np.concatenate([new.R.reshape(-1, 9), new.t, new.d], 1)
+    np.testing.assert_allclose(x[same], want[same], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(E_next[same], new.E_cam[same], rtol=0, atol=1e-10 * scale)
+    np.testing.assert_allclose(S_next[same], (new.Fbar_cam - new.E_cam)[same], rtol=0, atol=1e-10 * scale)
