@@ -1,8 +1,8 @@
 """The boundary's state conversions on the CPU: the library's k_set_cams / k_get_cams (boundary
 camera [w, t, f, k1, k2] <-> internal R, t, d in units of s pixels), k_set_lms / k_get_lms (the
 landmark records of the FP64 and MIXED paths, through a reversed internal numbering) and
-k_check_state (the first invalid camera or landmark), built for the host with g++ and run one
-element at a time. The conversions are checked against the oracle's to_internal and
+k_check_state (the first invalid camera or landmark), and k_check_degenerate (Assumption 2 on
+the current iterate), built for the host with g++ and run one element or chunk at a time. The conversions are checked against the oracle's to_internal and
 to_boundary (Sec. 3's camera model with Eq. ray's radial terms scaled by s), the round trips
 against the input, and the check indices against the definition. No GPU."""
 import os
@@ -102,3 +102,63 @@ def test_state_check_reports_the_first_invalid_entries(state_io):
     lms[12, 0] = np.nan
     chk, _, _ = _call(state_io, cams, lms, 650.0)
     assert chk == [5, 12, 9]
+
+
+def _degenerate(exe, t, l, cam, lm):
+    order = np.argsort(cam, kind="stable")
+    cam, lm = cam[order], lm[order]
+    stdin = (f"{t.shape[0]} {l.shape[0]} {cam.size}\n" + "\n".join(" ".join(repr(float(x)) for x in r) for r in t)
+             + "\n" + "\n".join(" ".join(repr(float(x)) for x in r) for r in l) + "\n"
+             + "\n".join(f"{i} {j}" for i, j in zip(cam, lm)) + "\n")
+    run = subprocess.run([exe], input=stdin, capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0, run.stderr[-2000:]
+    return [int(x) for x in run.stdout.split()], cam, lm
+
+
+@pytest.fixture(scope="module")
+def degenerate(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not found")
+    exe = str(tmp_path_factory.mktemp("degenerate") / "degenerate")
+    build = subprocess.run([gxx, *FLAGS, os.path.join(HOST, "degenerate.cpp"), "-o", exe], capture_output=True,
+                           text=True)
+    assert build.returncode == 0, build.stderr[-4000:]
+    return exe
+
+
+@pytest.mark.parametrize("centre_scale", [1.0, 1e3])
+def test_assumption2_check_finds_the_first_degenerate_pair(degenerate, centre_scale):
+    """Assumption 2 (a landmark away from the centre of every camera observing it), as daba_run
+    checks it: an observation fails when |l - t|^2 <= 1e-24 max(1, |t|^2). Landmarks placed on a
+    camera centre, 1e-13 max(1, |t|) from it (fails) and 1e-11 max(1, |t|) from it (passes): both
+    paths report the smallest failing position in camera order, and nothing on a clean scene."""
+    rng = np.random.default_rng(int(centre_scale))
+    M, N, nnz = 20, 300, 2000
+    t = rng.uniform(-1, 1, (M, 3)) * centre_scale
+    l = rng.uniform(-1, 1, (N, 3)) * centre_scale + 5.0
+    cam = rng.integers(0, M, nnz)
+    lm = rng.integers(0, N, nnz)
+    none = 2 ** 64 - 1
+    got, _, _ = _degenerate(degenerate, t, l, cam, lm)
+    assert got == [none, none]
+    order = np.argsort(cam, kind="stable")
+    unit = max(1.0, centre_scale)
+
+    def put(pos, dist):   # landmark of the observation at camera-sorted position pos near its camera
+        o = order[pos]
+        d = rng.normal(size=3)
+        l[lm[o]] = t[cam[o]] + dist * unit * d / np.linalg.norm(d)
+
+    put(1500, 1e-11)           # passes
+    got, _, _ = _degenerate(degenerate, t, l, cam, lm)
+    assert got == [none, none]
+    put(1200, 1e-13)           # fails
+    put(700, 0.0)              # fails, and comes first
+    got, _, lms = _degenerate(degenerate, t, l, cam, lm)
+    sorted_cam = cam[order]
+    q = l[lm[order]] - t[sorted_cam]
+    thr = 1e-24 * np.maximum(1.0, np.sum(t[sorted_cam] ** 2, axis=1))
+    first = int(np.flatnonzero(np.sum(q * q, axis=1) <= thr)[0])
+    assert first <= 700
+    assert got == [first, first]
