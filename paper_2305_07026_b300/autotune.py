@@ -11,8 +11,6 @@ differ at most in the order of FP sums).
 """
 from __future__ import annotations
 
-import numpy as np
-
 CHUNKS = (1024, 1536, 2048, 3072, 4096)
 TILE_OBS = (256, 512, 1024, 2048)
 TILE_LMS = (32, 64, 128)

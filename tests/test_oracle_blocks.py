@@ -10,7 +10,6 @@ import pytest
 
 from oracle import daba_blocks as B
 from oracle import daba_oracle as O
-from tests.conftest import cached_scene
 
 
 def _scene():
