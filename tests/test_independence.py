@@ -73,3 +73,21 @@ def test_native_sources_include_only_their_own_headers():
         for inc in re.findall(r'#include\s+"([^"]+)"', open(os.path.join(csrc, f)).read()):
             path = os.path.realpath(os.path.join(csrc, inc))
             assert os.path.exists(path) and os.path.dirname(path) in dirs, (f, inc)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With no compiled library beside it, the binding raises ImportError at import, and so do
+    the package's loader and the modules that import the binding at load time; the others import
+    it when first used, and no context can be made without it: there is no CPU fallback."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2305_07026_b300"
+    pkg.mkdir()
+    for f in ("__init__.py", "_lib.py", "partition.py"):
+        shutil.copy(os.path.join(PKG, f), pkg / f)
+    for code in ("import paper_2305_07026_b300._lib", "import paper_2305_07026_b300.partition",
+                 "import paper_2305_07026_b300 as p; p.load()"):
+        run = subprocess.run([sys.executable, "-c", code], cwd=tmp_path, capture_output=True, text=True,
+                             env={**os.environ, "PYTHONPATH": str(tmp_path)}, timeout=120)
+        assert run.returncode != 0 and "is not built" in run.stderr, (code, run.stderr[-500:])
